@@ -1,0 +1,854 @@
+/*
+ * rt_oracle.c -- FP64 CPU oracle (test infrastructure only; see rt_oracle.h).
+ *
+ * A plain restatement of the Monte Carlo formal solution on a hierarchical
+ * grid (Lunttila & Juvela, Sect. 2) in double precision, global (root-cell)
+ * coordinates and one packet at a time:
+ *   - the tree is a pointer octree built from the level-ordered description
+ *     (Sect. 2.1: a grid hierarchy whose refined cells are replaced by 2x2x2
+ *     subcells; every crossing looks up the leaf by descending from the
+ *     root, the role of the subgrid identification array of Sect. 2.1);
+ *   - packages carry a photon weight that decays by continuous absorption
+ *     (Sect. 2.3, Lucy 1999) and are removed only at the outer boundary of
+ *     the root grid or by Russian roulette (Sect. 2.3);
+ *   - scattered light is peeled off towards observers after every scattering
+ *     (Sect. 2.4, Yusef-Zadeh et al. 1984);
+ *   - dust temperatures follow from the equilibrium between absorbed and
+ *     emitted energy (Sects. 3.2 and 4: a single dust component in
+ *     equilibrium with the local radiation field).
+ * Random numbers come from Philox4x32-10 (Salmon et al. 2011), implemented
+ * here from the published definition; the stream layout is:
+ *   key     = (seed_lo ^ job, seed_hi ^ iter)
+ *   counter = (pkt_lo, pkt_hi, draw >> 2, stream),  word = draw & 3
+ *   stream  = (source << 16) | wavelength bin
+ *   uniform = (u32 + 0.5) * 2^-32
+ */
+#include "rt_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define C_CGS 2.99792458e10
+#define H_CGS 6.62607015e-27
+#define K_CGS 1.380649e-16
+
+/* ------------------------------------------------------------------------ */
+/* Philox (Salmon, Moraes, Dror, Shaw 2011): an S-P network of 10 rounds.   */
+/* Each round multiplies words 0 and 2 by fixed odd constants, and forms    */
+/* the new block from the high/low halves xor'ed with the other words and   */
+/* the round key; the key is bumped by the Weyl constants between rounds.   */
+/* One macro text instantiates both word widths.                            */
+/* ------------------------------------------------------------------------ */
+static inline void mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+  uint64_t p = (uint64_t)a * (uint64_t)b;
+  *hi = (uint32_t)(p >> 32);
+  *lo = (uint32_t)p;
+}
+static inline void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+  *hi = (uint64_t)(p >> 64);
+  *lo = (uint64_t)p;
+}
+
+#define ORC_PHILOX_DEF(NAME, T, MULHILO, M0, M1, W0, W1)                 \
+  void NAME(const T ctr[4], const T key[2], T out[4]) {                 \
+    T x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];               \
+    T k0 = key[0], k1 = key[1];                                          \
+    for (int r = 0; r < 10; ++r) {                                       \
+      if (r > 0) { k0 += (T)(W0); k1 += (T)(W1); }                       \
+      T hi0, lo0, hi1, lo1;                                              \
+      MULHILO((T)(M0), x0, &hi0, &lo0);                                  \
+      MULHILO((T)(M1), x2, &hi1, &lo1);                                  \
+      T y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;      \
+      x0 = y0; x1 = y1; x2 = y2; x3 = y3;                                \
+    }                                                                    \
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;                  \
+  }
+
+ORC_PHILOX_DEF(orc_philox4x32, uint32_t, mulhilo32, 0xD2511F53u, 0xCD9E8D57u,
+               0x9E3779B9u, 0xBB67AE85u)
+ORC_PHILOX_DEF(orc_philox4x64, uint64_t, mulhilo64, 0xD2E7470EE14C6C93ull,
+               0xCA5A826395121157ull, 0x9E3779B97F4A7C15ull, 0xBB67AE8584CAA73Bull)
+
+uint32_t orc_draw_u32(uint64_t seed, uint32_t job, uint32_t iter, uint32_t stream,
+                      uint64_t pkt, uint64_t j) {
+  uint32_t key[2] = {(uint32_t)seed ^ job, (uint32_t)(seed >> 32) ^ iter};
+  uint32_t ctr[4] = {(uint32_t)pkt, (uint32_t)(pkt >> 32), (uint32_t)(j >> 2), stream};
+  uint32_t out[4];
+  orc_philox4x32(ctr, key, out);
+  return out[j & 3];
+}
+
+typedef struct {
+  uint64_t seed, pkt, next;
+  uint32_t job, iter, stream;
+} rstream;
+
+static double uni(rstream* s) {
+  uint32_t x = orc_draw_u32(s->seed, s->job, s->iter, s->stream, s->pkt, s->next++);
+  return ((double)x + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tree                                                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct orc_node {
+  int64_t id;
+  int level;
+  double lo[3];    /* root-cell units */
+  double size;     /* 2^-level */
+  double rho;      /* g/cm^3 */
+  struct orc_node* child;  /* first of 8 children (octant ox+2oy+4oz), NULL for a leaf */
+} orc_node;
+
+struct orc_tree {
+  int root[3];
+  double box[3];
+  double h0;
+  int n_levels;
+  int64_t n_cells;
+  orc_node* nodes;
+};
+
+orc_tree* orc_tree_build(const orc_tree_desc* d) {
+  if (!d || d->root[0] <= 0 || d->root[1] <= 0 || d->root[2] <= 0 || d->n_levels <= 0) return NULL;
+  double h0 = d->box[0] / d->root[0];
+  for (int a = 1; a < 3; ++a)
+    if (fabs(d->box[a] / d->root[a] - h0) > 1e-12 * h0) return NULL;
+  int64_t n0 = (int64_t)d->root[0] * d->root[1] * d->root[2];
+  int64_t total = n0, level_n = n0;
+  for (int l = 0; l < d->n_levels; ++l) {
+    if (d->n_refined[l] < 0 || d->n_refined[l] > level_n) return NULL;
+    if (l == d->n_levels - 1 && d->n_refined[l] != 0) return NULL;
+    level_n = 8 * d->n_refined[l];
+    total += level_n;
+  }
+  total -= level_n;  /* last level has no children */
+  orc_tree* t = (orc_tree*)calloc(1, sizeof(orc_tree));
+  t->nodes = (orc_node*)calloc((size_t)total, sizeof(orc_node));
+  memcpy(t->root, d->root, sizeof t->root);
+  memcpy(t->box, d->box, sizeof t->box);
+  t->h0 = h0;
+  t->n_levels = d->n_levels;
+  t->n_cells = total;
+  /* root grid, x fastest */
+  for (int iz = 0; iz < d->root[2]; ++iz)
+    for (int iy = 0; iy < d->root[1]; ++iy)
+      for (int ix = 0; ix < d->root[0]; ++ix) {
+        int64_t id = ix + (int64_t)d->root[0] * (iy + (int64_t)d->root[1] * iz);
+        orc_node* n = &t->nodes[id];
+        n->id = id; n->level = 0; n->size = 1.0;
+        n->lo[0] = ix; n->lo[1] = iy; n->lo[2] = iz;
+      }
+  /* breadth-first: the k-th refined cell (in level order) owns cells n0+8k..n0+8k+7 */
+  int64_t next_child = n0, refined_seen = 0;
+  int64_t lvl_begin = 0, lvl_end = n0;
+  for (int l = 0; l < d->n_levels; ++l) {
+    int64_t cnt = 0;
+    for (int64_t id = lvl_begin; id < lvl_end; ++id) {
+      orc_node* n = &t->nodes[id];
+      n->rho = d->density[id];
+      if (d->refine_flags[id]) {
+        if (next_child + 8 > total) { orc_tree_free(t); return NULL; }
+        n->child = &t->nodes[next_child];
+        for (int o = 0; o < 8; ++o) {
+          orc_node* c = &n->child[o];
+          c->id = next_child + o;
+          c->level = l + 1;
+          c->size = 0.5 * n->size;
+          c->lo[0] = n->lo[0] + ((o >> 0) & 1) * c->size;
+          c->lo[1] = n->lo[1] + ((o >> 1) & 1) * c->size;
+          c->lo[2] = n->lo[2] + ((o >> 2) & 1) * c->size;
+        }
+        next_child += 8;
+        ++cnt;
+        ++refined_seen;
+      } else if (!(n->rho >= 0.0) || !isfinite(n->rho)) {
+        orc_tree_free(t);
+        return NULL;
+      }
+    }
+    if (cnt != d->n_refined[l]) { orc_tree_free(t); return NULL; }
+    lvl_begin = lvl_end;
+    lvl_end = next_child;
+  }
+  (void)refined_seen;
+  if (next_child != total) { orc_tree_free(t); return NULL; }
+  return t;
+}
+
+void orc_tree_free(orc_tree* t) {
+  if (!t) return;
+  free(t->nodes);
+  free(t);
+}
+
+int64_t orc_tree_ncells(const orc_tree* t) { return t->n_cells; }
+
+void orc_tree_cells(const orc_tree* t, uint8_t* level, uint8_t* is_leaf) {
+  for (int64_t i = 0; i < t->n_cells; ++i) {
+    if (level) level[i] = (uint8_t)t->nodes[i].level;
+    if (is_leaf) is_leaf[i] = t->nodes[i].child == NULL;
+  }
+}
+
+/* Leaf containing x; a coordinate exactly on a face belongs to the cell the
+ * direction points into (d >= 0: upper cell). NULL outside the root grid. */
+static const orc_node* locate(const orc_tree* t, const double x[3], const double d[3]) {
+  int64_t ic[3];
+  for (int a = 0; a < 3; ++a) {
+    double f = floor(x[a]);
+    int64_t i = (int64_t)f;
+    if (x[a] == f && d[a] < 0) i -= 1;
+    if (i < 0 || i >= t->root[a]) return NULL;
+    ic[a] = i;
+  }
+  const orc_node* n = &t->nodes[ic[0] + t->root[0] * (ic[1] + (int64_t)t->root[1] * ic[2])];
+  while (n->child) {
+    int oct = 0;
+    for (int a = 0; a < 3; ++a) {
+      double mid = n->lo[a] + 0.5 * n->size;
+      int upper = (x[a] > mid) || (x[a] == mid && d[a] >= 0);
+      oct |= upper << a;
+    }
+    n = &n->child[oct];
+  }
+  return n;
+}
+
+/* distance (root units) to the exit face of leaf n; lowest axis wins ties */
+static double exit_dist(const orc_node* n, const double x[3], const double d[3], int* axis) {
+  double best = INFINITY;
+  int ab = -1;
+  for (int a = 0; a < 3; ++a) {
+    double t;
+    if (d[a] > 0) t = (n->lo[a] + n->size - x[a]) / d[a];
+    else if (d[a] < 0) t = (n->lo[a] - x[a]) / d[a];
+    else continue;
+    if (t < 0) t = 0;
+    if (t < best) { best = t; ab = a; }
+  }
+  *axis = ab;
+  return best;
+}
+
+static void move_to_face(const orc_node* n, double x[3], const double d[3], double t, int a) {
+  for (int b = 0; b < 3; ++b)
+    if (b != a) x[b] += t * d[b];
+  x[a] = d[a] > 0 ? n->lo[a] + n->size : n->lo[a];
+}
+
+static double face_margin(const orc_node* n, const double x[3], int a) {
+  double m = INFINITY;
+  for (int b = 0; b < 3; ++b) {
+    if (b == a) continue;
+    double u = (x[b] - n->lo[b]) / n->size;
+    double v = fmin(fabs(u), fabs(1.0 - u));
+    if (v < m) m = v;
+  }
+  return m;
+}
+
+int64_t orc_walk(const orc_tree* t, const double origin[3], const double dir[3], int64_t max_seg,
+                 int64_t* cells, double* lengths, double* margins) {
+  double x[3], d[3];
+  for (int a = 0; a < 3; ++a) { x[a] = origin[a] / t->h0; d[a] = dir[a]; }
+  const orc_node* n = locate(t, x, d);
+  if (!n) return -1;
+  int64_t k = 0;
+  while (n && k < max_seg) {
+    int a;
+    double s = exit_dist(n, x, d, &a);
+    move_to_face(n, x, d, s, a);
+    const orc_node* nn = locate(t, x, d);
+    if (s > 0) {
+      double m = face_margin(n, x, a);
+      if (nn) {
+        double m2 = face_margin(nn, x, a);
+        if (m2 < m) m = m2;
+      }
+      cells[k] = n->id;
+      lengths[k] = s * t->h0;
+      margins[k] = m;
+      ++k;
+    }
+    n = nn;
+  }
+  return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scattering                                                                 */
+/* ------------------------------------------------------------------------ */
+/* Henyey-Greenstein: inverse of the cumulative distribution of mu. */
+double orc_hg_mu(double g, double u) {
+  double mu;
+  if (g == 0.0) {
+    mu = 2.0 * u - 1.0;
+  } else {
+    double s = (1.0 - g * g) / (1.0 - g + 2.0 * g * u);
+    mu = (1.0 + g * g - s * s) / (2.0 * g);
+  }
+  if (mu > 1.0) mu = 1.0;
+  if (mu < -1.0) mu = -1.0;
+  return mu;
+}
+
+double orc_hg_phase(double g, double mu) {
+  double den = 1.0 + g * g - 2.0 * g * mu;
+  return (1.0 - g * g) / (4.0 * ORC_PI * den * sqrt(den));
+}
+
+/* New direction at polar cosine mu and azimuth phi about d (the usual
+ * rotation formula of Monte Carlo photon transport). */
+void orc_scatter_dir(const double d[3], double mu, double phi, double out[3]) {
+  double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+  double cp = cos(phi), sp = sin(phi);
+  if (fabs(d[2]) > 0.99999) {
+    out[0] = st * cp;
+    out[1] = st * sp;
+    out[2] = d[2] > 0 ? mu : -mu;
+  } else {
+    double den = sqrt(1.0 - d[2] * d[2]);
+    out[0] = st * (d[0] * d[2] * cp - d[1] * sp) / den + d[0] * mu;
+    out[1] = st * (d[1] * d[2] * cp + d[0] * sp) / den + d[1] * mu;
+    out[2] = -st * cp * den + d[2] * mu;
+  }
+  double nrm = sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+  out[0] /= nrm; out[1] /= nrm; out[2] /= nrm;
+}
+
+static void iso_dir(double u1, double u2, double d[3]) {
+  double mu = 2.0 * u1 - 1.0, phi = 2.0 * ORC_PI * u2;
+  double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+  d[0] = st * cos(phi);
+  d[1] = st * sin(phi);
+  d[2] = mu;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Trace                                                                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_tree* t;
+  int n_src;
+  const orc_source* src;
+  const orc_optics* op;
+  const orc_params* prm;
+  const orc_observers* obs;
+  int bins;
+  int64_t n_packets;
+  int64_t* seg_begin;      /* [n_src*n_lambda + 1] global packet offset of each (src,bin) */
+  double** cdf;            /* dust: [n_src][n_lambda] -> cumulative emission over cells */
+  double* rec;
+  int shared_atomic;
+  double* absorbed_shared;
+  double* images_shared;
+} trace_job;
+
+typedef struct {
+  trace_job* job;
+  int64_t p0, p1;
+  double* absorbed;
+  double* images;
+  double* sumsq;
+  double* hits;
+  double* pkt_acc;
+  int64_t* stamp;
+  int64_t* touched;
+  int64_t n_touched, cap_touched;
+  orc_ledger led;
+} trace_worker;
+
+static void atomic_add_double(double* p, double v) {
+  uint64_t* q = (uint64_t*)p;
+  uint64_t old = __atomic_load_n(q, __ATOMIC_RELAXED), nw;
+  do {
+    double cur;
+    memcpy(&cur, &old, 8);
+    cur += v;
+    memcpy(&nw, &cur, 8);
+  } while (!__atomic_compare_exchange_n(q, &old, nw, 0, __ATOMIC_RELAXED, __ATOMIC_RELAXED));
+}
+
+static void deposit(trace_worker* w, int64_t slot, int64_t pkt, double v) {
+  if (v == 0.0) return;
+  if (w->job->shared_atomic) atomic_add_double(&w->job->absorbed_shared[slot], v);
+  else w->absorbed[slot] += v;
+  if (w->pkt_acc) {
+    if (w->stamp[slot] != pkt) {
+      w->stamp[slot] = pkt;
+      w->pkt_acc[slot] = 0.0;
+      if (w->n_touched == w->cap_touched) {
+        w->cap_touched = w->cap_touched ? 2 * w->cap_touched : 256;
+        w->touched = (int64_t*)realloc(w->touched, (size_t)w->cap_touched * sizeof(int64_t));
+      }
+      w->touched[w->n_touched++] = slot;
+    }
+    w->pkt_acc[slot] += v;
+  }
+}
+
+static void flush_packet(trace_worker* w) {
+  for (int64_t i = 0; i < w->n_touched; ++i) {
+    int64_t s = w->touched[i];
+    w->sumsq[s] += w->pkt_acc[s] * w->pkt_acc[s];
+    w->hits[s] += 1.0;
+  }
+  w->n_touched = 0;
+}
+
+/* Optical depth along x + s k to the root boundary (Sect. 2.4 peel-off). */
+static double peel_march(trace_worker* w, const double x0[3], const double k[3], int bin, double tau_max,
+                         int* cut) {
+  const orc_tree* t = w->job->t;
+  double x[3] = {x0[0], x0[1], x0[2]};
+  double kext = w->job->op->kappa_ext[bin] * t->h0;
+  double tau = 0.0;
+  *cut = 0;
+  const orc_node* n = locate(t, x, k);
+  while (n) {
+    int a;
+    double s = exit_dist(n, x, k, &a);
+    tau += kext * n->rho * s;
+    if (s > 0) w->led.n_peel_cross += 1;
+    if (tau_max > 0 && tau > tau_max) { *cut = 1; return tau; }
+    move_to_face(n, x, k, s, a);
+    n = locate(t, x, k);
+  }
+  return tau;
+}
+
+static void peel(trace_worker* w, const double x[3], const double din[3], double W, int bin) {
+  const orc_observers* obs = w->job->obs;
+  const orc_tree* t = w->job->t;
+  double g = w->job->op->g_hg[bin];
+  int ob = w->job->bins > 1 ? bin : 0;
+  for (int o = 0; o < obs->n_obs; ++o) {
+    const double* k = &obs->dir[3 * o];
+    double mu = din[0] * k[0] + din[1] * k[1] + din[2] * k[2];
+    int cut;
+    double tau = peel_march(w, x, k, bin, w->job->prm->peel_tau_max, &cut);
+    if (cut) continue;
+    double c = W * orc_hg_phase(g, mu) * exp(-tau);
+    /* image basis: ex = normalise(up x k), ey = k x ex; centred on the box centre */
+    const double* up = &obs->up[3 * o];
+    double ex[3] = {up[1] * k[2] - up[2] * k[1], up[2] * k[0] - up[0] * k[2], up[0] * k[1] - up[1] * k[0]};
+    double nn = sqrt(ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2]);
+    ex[0] /= nn; ex[1] /= nn; ex[2] /= nn;
+    double ey[3] = {k[1] * ex[2] - k[2] * ex[1], k[2] * ex[0] - k[0] * ex[2], k[0] * ex[1] - k[1] * ex[0]};
+    double r[3];
+    for (int a = 0; a < 3; ++a) r[a] = x[a] * t->h0 - 0.5 * t->box[a];
+    double u = r[0] * ex[0] + r[1] * ex[1] + r[2] * ex[2];
+    double v = r[0] * ey[0] + r[1] * ey[1] + r[2] * ey[2];
+    double fx = floor(u / (obs->fov[0] / obs->nx) + 0.5 * obs->nx);
+    double fy = floor(v / (obs->fov[1] / obs->ny) + 0.5 * obs->ny);
+    if (fx < 0 || fy < 0 || fx >= obs->nx || fy >= obs->ny) {
+      w->led.n_peel_out += 1;
+      continue;
+    }
+    int64_t slot = (((int64_t)o * w->job->bins + ob) * obs->ny + (int64_t)fy) * obs->nx + (int64_t)fx;
+    if (w->job->shared_atomic) atomic_add_double(&w->job->images_shared[slot], c);
+    else w->images[slot] += c;
+    w->led.peeled += c;
+  }
+}
+
+static int64_t search_cdf(const double* cdf, int64_t n, double target) {
+  /* first index with cdf[i] > target */
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (cdf[mid] > target) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+static void trace_one(trace_worker* w, int64_t p) {
+  trace_job* J = w->job;
+  const orc_tree* t = J->t;
+  const orc_params* prm = J->prm;
+  int nl = J->op->n_lambda;
+  /* which (source, bin) stream this packet belongs to */
+  int64_t seg = 0;
+  {
+    int64_t lo = 0, hi = (int64_t)J->n_src * nl - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) / 2;
+      if (J->seg_begin[mid] <= p) lo = mid;
+      else hi = mid - 1;
+    }
+    seg = lo;
+  }
+  int si = (int)(seg / nl), bin = (int)(seg % nl);
+  int64_t k = p - J->seg_begin[seg];
+  int64_t npk = J->seg_begin[seg + 1] - J->seg_begin[seg];
+  const orc_source* S = &J->src[si];
+  rstream rs = {prm->seed, (uint64_t)k, 0, prm->job, prm->iter, ((uint32_t)si << 16) | (uint32_t)bin};
+  int ob = J->bins > 1 ? bin : 0;
+  int64_t nc = t->n_cells;
+
+  double x[3], d[3], E;
+  if (S->kind == ORC_SRC_DUST) E = J->cdf[seg][nc - 1];
+  else E = S->bin_energy[bin];
+  double W0 = E / (double)npk, W = W0;
+
+  /* emission (Sect. 2.3: packages from internal sources; root inwards
+   * array for the external field) */
+  if (S->kind == ORC_SRC_POINT) {
+    for (int a = 0; a < 3; ++a) x[a] = S->pos[a] / t->h0;
+    double u1 = uni(&rs), u2 = uni(&rs);
+    iso_dir(u1, u2, d);
+  } else if (S->kind == ORC_SRC_BEAM) {
+    double nn = sqrt(S->dir[0] * S->dir[0] + S->dir[1] * S->dir[1] + S->dir[2] * S->dir[2]);
+    for (int a = 0; a < 3; ++a) { x[a] = S->pos[a] / t->h0; d[a] = S->dir[a] / nn; }
+  } else if (S->kind == ORC_SRC_EXTERNAL) {
+    double area[3] = {t->box[1] * t->box[2], t->box[0] * t->box[2], t->box[0] * t->box[1]};
+    double tot = 2.0 * (area[0] + area[1] + area[2]);
+    double u0 = uni(&rs) * tot, cum = 0.0;
+    int face = 5;
+    for (int f = 0; f < 6; ++f) {
+      cum += area[f / 2];
+      if (u0 < cum) { face = f; break; }
+    }
+    int a = face / 2, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    if (a1 > a2) { int tmp = a1; a1 = a2; a2 = tmp; }
+    double u1 = uni(&rs), u2 = uni(&rs), u3 = uni(&rs), u4 = uni(&rs);
+    x[a] = (face & 1) ? (double)t->root[a] : 0.0;
+    x[a1] = u1 * t->root[a1];
+    x[a2] = u2 * t->root[a2];
+    double mu = sqrt(u3), st = sqrt(fmax(0.0, 1.0 - mu * mu)), phi = 2.0 * ORC_PI * u4;
+    d[a] = (face & 1) ? -mu : mu;
+    d[a1] = st * cos(phi);
+    d[a2] = st * sin(phi);
+  } else { /* dust emission: cell by the cumulative emission of this bin */
+    const double* cdf = J->cdf[seg];
+    double u0 = uni(&rs);
+    int64_t c = search_cdf(cdf, nc, u0 * cdf[nc - 1]);
+    const orc_node* n = &t->nodes[c];
+    double u1 = uni(&rs), u2 = uni(&rs), u3 = uni(&rs);
+    x[0] = n->lo[0] + u1 * n->size;
+    x[1] = n->lo[1] + u2 * n->size;
+    x[2] = n->lo[2] + u3 * n->size;
+    double u4 = uni(&rs), u5 = uni(&rs);
+    iso_dir(u4, u5, d);
+  }
+  w->led.emitted += W0;
+  w->led.n_packets += 1;
+
+  double kext_b = J->op->kappa_ext[bin] * t->h0;   /* per unit density, per root-cell unit */
+  double alb = J->op->albedo[bin], g = J->op->g_hg[bin];
+  int analog = prm->estimator == ORC_EST_ANALOG;
+  double tau = -log(uni(&rs));
+  double nscat = 0, ncross = 0;
+  int fate = 0;
+  int64_t steps = 0;
+  for (;;) {
+    const orc_node* n = locate(t, x, d);
+    if (!n) {  /* left through the outer boundary of the root grid */
+      w->led.escaped += W;
+      fate = 0;
+      break;
+    }
+    if (prm->step_limit > 0 && steps >= prm->step_limit) {
+      w->led.killed += W;
+      w->led.n_killed += 1;
+      fate = 2;
+      W = 0;
+      break;
+    }
+    ++steps;
+    int a;
+    double s = exit_dist(n, x, d, &a);
+    double kext = kext_b * n->rho;
+    int64_t slot = (int64_t)ob * nc + n->id;
+    if (!analog) {
+      double ksca = alb * kext, kabs = (1.0 - alb) * kext;
+      if (ksca > 0 && ksca * s >= tau) {
+        /* scattering inside this cell */
+        double ts = tau / ksca;
+        double dep = W * (1.0 - exp(-kabs * ts));
+        deposit(w, slot, p, dep);
+        w->led.absorbed += dep;
+        W *= exp(-kabs * ts);
+        for (int b = 0; b < 3; ++b) x[b] += ts * d[b];
+        if (ts > 0) { ncross += 1; w->led.n_cross += 1; }
+        nscat += 1;
+        w->led.n_scatter += 1;
+        if (J->obs && J->obs->n_obs > 0) peel(w, x, d, W, bin);
+        double mu = orc_hg_mu(g, uni(&rs));
+        double phi = 2.0 * ORC_PI * uni(&rs);
+        double nd[3];
+        orc_scatter_dir(d, mu, phi, nd);
+        d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
+        if (prm->rr_wmin > 0 && W < prm->rr_wmin * W0) {
+          double ur = uni(&rs);
+          if (ur < prm->rr_p) {
+            w->led.rr_loss += W;
+            W = 0;
+            fate = 1;
+            break;
+          }
+          double Wn = W / (1.0 - prm->rr_p);
+          w->led.rr_gain += Wn - W;
+          W = Wn;
+        }
+        tau = -log(uni(&rs));
+      } else {
+        tau -= ksca * s;
+        double dep = W * (1.0 - exp(-kabs * s));
+        deposit(w, slot, p, dep);
+        w->led.absorbed += dep;
+        W *= exp(-kabs * s);
+        if (s > 0) { ncross += 1; w->led.n_cross += 1; }
+        move_to_face(n, x, d, s, a);
+      }
+    } else {
+      if (kext > 0 && kext * s >= tau) {
+        double ts = tau / kext;
+        for (int b = 0; b < 3; ++b) x[b] += ts * d[b];
+        if (ts > 0) { ncross += 1; w->led.n_cross += 1; }
+        double ua = uni(&rs);
+        if (ua < alb) {
+          nscat += 1;
+          w->led.n_scatter += 1;
+          if (J->obs && J->obs->n_obs > 0) peel(w, x, d, W, bin);
+          double mu = orc_hg_mu(g, uni(&rs));
+          double phi = 2.0 * ORC_PI * uni(&rs);
+          double nd[3];
+          orc_scatter_dir(d, mu, phi, nd);
+          d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
+        } else {
+          deposit(w, slot, p, W);
+          w->led.absorbed += W;
+          W = 0;
+          fate = 3;
+          break;
+        }
+        tau = -log(uni(&rs));
+      } else {
+        tau -= kext * s;
+        if (s > 0) { ncross += 1; w->led.n_cross += 1; }
+        move_to_face(n, x, d, s, a);
+      }
+    }
+  }
+  if (w->pkt_acc) flush_packet(w);
+  if (J->rec) {
+    double* r = &J->rec[p * 10];
+    r[0] = fate == 0 ? W : 0.0;
+    r[1] = nscat;
+    r[2] = ncross;
+    r[3] = fate;
+    for (int a = 0; a < 3; ++a) { r[4 + a] = x[a] * t->h0; r[7 + a] = d[a]; }
+  }
+}
+
+static void* trace_thread(void* arg) {
+  trace_worker* w = (trace_worker*)arg;
+  for (int64_t p = w->p0; p < w->p1; ++p) trace_one(w, p);
+  return NULL;
+}
+
+static void ledger_add(orc_ledger* a, const orc_ledger* b) {
+  a->emitted += b->emitted; a->absorbed += b->absorbed; a->escaped += b->escaped;
+  a->rr_gain += b->rr_gain; a->rr_loss += b->rr_loss; a->killed += b->killed; a->peeled += b->peeled;
+  a->n_packets += b->n_packets; a->n_cross += b->n_cross; a->n_scatter += b->n_scatter;
+  a->n_peel_cross += b->n_peel_cross; a->n_killed += b->n_killed; a->n_peel_out += b->n_peel_out;
+}
+
+int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_optics* op,
+              const orc_params* prm, const orc_observers* obs, double* absorbed, double* images,
+              double* sumsq, double* hits, double* rec, orc_ledger* ledger) {
+  if (!t || n_src <= 0 || !src || !op || !prm || op->n_lambda <= 0) return -1;
+  int nl = op->n_lambda;
+  int bins = prm->per_lambda ? nl : 1;
+  int64_t nc = t->n_cells;
+  trace_job J;
+  memset(&J, 0, sizeof J);
+  J.t = t; J.n_src = n_src; J.src = src; J.op = op; J.prm = prm; J.obs = obs; J.bins = bins; J.rec = rec;
+  J.seg_begin = (int64_t*)calloc((size_t)n_src * nl + 1, sizeof(int64_t));
+  J.cdf = (double**)calloc((size_t)n_src * nl, sizeof(double*));
+  for (int s = 0; s < n_src; ++s)
+    for (int b = 0; b < nl; ++b) {
+      int64_t i = (int64_t)s * nl + b;
+      J.seg_begin[i + 1] = J.seg_begin[i] + src[s].packets[b];
+      if (src[s].kind == ORC_SRC_DUST && src[s].packets[b] > 0) {
+        double* c = (double*)malloc((size_t)nc * sizeof(double));
+        double acc = 0.0;
+        for (int64_t k = 0; k < nc; ++k) { acc += src[s].emission[(int64_t)b * nc + k]; c[k] = acc; }
+        J.cdf[i] = c;
+      }
+    }
+  J.n_packets = J.seg_begin[(int64_t)n_src * nl];
+  int T = prm->n_threads > 0 ? prm->n_threads : 1;
+  if (J.n_packets < T) T = J.n_packets > 0 ? (int)J.n_packets : 1;
+  int64_t n_img = obs && obs->n_obs > 0 ? (int64_t)obs->n_obs * bins * obs->ny * obs->nx : 0;
+  double per_thread_bytes = 8.0 * ((double)bins * nc + (double)n_img);
+  int validation = sumsq && hits;
+  J.shared_atomic = T > 1 && per_thread_bytes * T > 2.0e9;
+  if (validation && J.shared_atomic) T = 1, J.shared_atomic = 0;
+  J.absorbed_shared = absorbed;
+  J.images_shared = images;
+
+  trace_worker* ws = (trace_worker*)calloc((size_t)T, sizeof(trace_worker));
+  pthread_t* th = (pthread_t*)calloc((size_t)T, sizeof(pthread_t));
+  for (int i = 0; i < T; ++i) {
+    trace_worker* w = &ws[i];
+    w->job = &J;
+    w->p0 = J.n_packets * i / T;
+    w->p1 = J.n_packets * (i + 1) / T;
+    if (T == 1 || J.shared_atomic) {
+      w->absorbed = absorbed;
+      w->images = images;
+      w->sumsq = sumsq;
+      w->hits = hits;
+    } else {
+      w->absorbed = (double*)calloc((size_t)bins * nc, sizeof(double));
+      w->images = n_img ? (double*)calloc((size_t)n_img, sizeof(double)) : NULL;
+      if (validation) {
+        w->sumsq = (double*)calloc((size_t)bins * nc, sizeof(double));
+        w->hits = (double*)calloc((size_t)bins * nc, sizeof(double));
+      }
+    }
+    if (validation) {
+      w->pkt_acc = (double*)calloc((size_t)bins * nc, sizeof(double));
+      w->stamp = (int64_t*)malloc((size_t)bins * nc * sizeof(int64_t));
+      for (int64_t k = 0; k < (int64_t)bins * nc; ++k) w->stamp[k] = -1;
+    }
+  }
+  if (T == 1) trace_thread(&ws[0]);
+  else {
+    for (int i = 0; i < T; ++i) pthread_create(&th[i], NULL, trace_thread, &ws[i]);
+    for (int i = 0; i < T; ++i) pthread_join(th[i], NULL);
+  }
+  orc_ledger L;
+  memset(&L, 0, sizeof L);
+  for (int i = 0; i < T; ++i) {
+    trace_worker* w = &ws[i];
+    ledger_add(&L, &w->led);
+    if (T > 1 && !J.shared_atomic) {
+      for (int64_t k = 0; k < (int64_t)bins * nc; ++k) absorbed[k] += w->absorbed[k];
+      for (int64_t k = 0; k < n_img; ++k) images[k] += w->images[k];
+      if (validation)
+        for (int64_t k = 0; k < (int64_t)bins * nc; ++k) { sumsq[k] += w->sumsq[k]; hits[k] += w->hits[k]; }
+      free(w->absorbed); free(w->images); free(w->sumsq); free(w->hits);
+    }
+    free(w->pkt_acc); free(w->stamp); free(w->touched);
+  }
+  if (ledger) *ledger = L;
+  for (int64_t i = 0; i < (int64_t)n_src * nl; ++i) free(J.cdf[i]);
+  free(J.cdf); free(J.seg_begin); free(ws); free(th);
+  return 0;
+}
+
+/* One peel-off contribution from a given scattering point (cm) and incoming
+ * direction, into images [n_obs][bins][ny][nx]. */
+int orc_peel_point(const orc_tree* t, const orc_optics* op, const orc_observers* obs, int bin,
+                   int per_lambda, const double x_cm[3], const double din[3], double W, double* images) {
+  trace_job J;
+  memset(&J, 0, sizeof J);
+  orc_params prm;
+  memset(&prm, 0, sizeof prm);
+  J.t = t; J.op = op; J.obs = obs; J.prm = &prm; J.bins = per_lambda ? op->n_lambda : 1;
+  trace_worker w;
+  memset(&w, 0, sizeof w);
+  w.job = &J;
+  w.images = images;
+  double x[3] = {x_cm[0] / t->h0, x_cm[1] / t->h0, x_cm[2] / t->h0};
+  peel(&w, x, din, W, bin);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dust temperature                                                           */
+/* ------------------------------------------------------------------------ */
+static double planck_nu(double nu, double T) {
+  double x = H_CGS * nu / (K_CGS * T);
+  return 2.0 * H_CGS * nu * nu * nu / (C_CGS * C_CGS) / expm1(x);
+}
+
+double orc_emission_per_mass(const orc_dust* d, double T) {
+  double s = 0.0;
+  for (int i = 0; i < d->n_lambda; ++i) {
+    double nu = C_CGS / (d->lambda_um[i] * 1e-4);
+    s += d->kappa_abs[i] * planck_nu(nu, T) * d->dnu[i];
+  }
+  return 4.0 * ORC_PI * s;
+}
+
+typedef struct {
+  const orc_tree* t;
+  const double* A;
+  const orc_dust* d;
+  double* T;
+  int64_t c0, c1;
+} temp_work;
+
+static void* temp_thread(void* arg) {
+  temp_work* w = (temp_work*)arg;
+  const orc_tree* t = w->t;
+  double Emin = orc_emission_per_mass(w->d, w->d->T_min);
+  double Emax = orc_emission_per_mass(w->d, w->d->T_max);
+  for (int64_t c = w->c0; c < w->c1; ++c) {
+    const orc_node* n = &t->nodes[c];
+    if (n->child) { w->T[c] = 0.0; continue; }
+    double h = t->h0 * n->size;
+    double mass = n->rho * h * h * h;
+    if (!(mass > 0) || !(w->A[c] > 0)) { w->T[c] = w->d->T_min; continue; }
+    double target = w->A[c] / mass;
+    if (target <= Emin) { w->T[c] = w->d->T_min; continue; }
+    if (target >= Emax) { w->T[c] = w->d->T_max; continue; }
+    double lo = w->d->T_min, hi = w->d->T_max;
+    while (hi - lo > 1e-13 * lo) {
+      double mid = 0.5 * (lo + hi);
+      if (orc_emission_per_mass(w->d, mid) < target) lo = mid;
+      else hi = mid;
+    }
+    w->T[c] = 0.5 * (lo + hi);
+  }
+  return NULL;
+}
+
+int orc_dust_temperature(const orc_tree* t, const double* absorbed_total, const orc_dust* d,
+                         int n_threads, double* T) {
+  if (!t || !absorbed_total || !d || !T || d->n_lambda <= 0 || !(d->T_min > 0) || !(d->T_max > d->T_min))
+    return -1;
+  int NT = n_threads > 0 ? n_threads : 1;
+  temp_work* ws = (temp_work*)calloc((size_t)NT, sizeof(temp_work));
+  pthread_t* th = (pthread_t*)calloc((size_t)NT, sizeof(pthread_t));
+  for (int i = 0; i < NT; ++i) {
+    ws[i].t = t; ws[i].A = absorbed_total; ws[i].d = d; ws[i].T = T;
+    ws[i].c0 = t->n_cells * i / NT;
+    ws[i].c1 = t->n_cells * (i + 1) / NT;
+  }
+  if (NT == 1) temp_thread(&ws[0]);
+  else {
+    for (int i = 0; i < NT; ++i) pthread_create(&th[i], NULL, temp_thread, &ws[i]);
+    for (int i = 0; i < NT; ++i) pthread_join(th[i], NULL);
+  }
+  free(ws); free(th);
+  return 0;
+}
+
+int orc_dust_emission(const orc_tree* t, const double* T, const orc_dust* d, double* emission) {
+  if (!t || !T || !d || !emission) return -1;
+  int64_t nc = t->n_cells;
+  for (int b = 0; b < d->n_lambda; ++b) {
+    double nu = C_CGS / (d->lambda_um[b] * 1e-4);
+    for (int64_t c = 0; c < nc; ++c) {
+      const orc_node* n = &t->nodes[c];
+      double v = 0.0;
+      if (!n->child && T[c] > 0) {
+        double h = t->h0 * n->size;
+        v = 4.0 * ORC_PI * n->rho * h * h * h * d->kappa_abs[b] * planck_nu(nu, T[c]) * d->dnu[b];
+      }
+      emission[(int64_t)b * nc + c] = v;
+    }
+  }
+  return 0;
+}
