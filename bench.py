@@ -1,0 +1,352 @@
+"""Benchmark: Monte Carlo radiative transfer on a hierarchical grid, 1 GB300.
+
+Workload (default): the molecular-cloud model -- 256^3 root grid, lognormal
+density (sigma_ln = 1.5) from a seeded k^-4 Gaussian random field, refined 3
+levels by 2x2x2 where density exceeds 4^level x mean; isotropic external
+field at 20 wavelengths (0.1-1000 um), kappa ~ lambda^-1.8, HG g = 0.5;
+1e7 packages per wavelength; peel-off images 256x256 toward 6 observers;
+FP32 tracing with FP64 accumulators.  One step = absorbed-energy trace with
+peel-off (rt_peel) + dust-temperature solve (rt_dust_temperature).
+
+Metric: cell crossings/s (trace + peel-off segments) and packages/s.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell crossings/s & packets/s on 1 GB300 vs roofline; p50/p99 job latency"
+UNIT = "cell crossings/s"
+# algorithmic bytes per unit of tracer work (the packed node word replaces
+# the separate density + child reads: 4 B per visit)
+BYTES_TRACE_CROSS = 4 + 16      # node word + FP64 accumulator read-modify-write
+BYTES_PEEL_CROSS = 4            # node word
+BYTES_IMAGE_DEPOSIT = 16        # FP64 pixel read-modify-write
+# DRAM traffic of the tracer kernel per launch measured by ncu (bytes per
+# trace-equivalent unit); None until a capture of the current kernel exists
+NCU_TRAFFIC_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n-root", type=int, default=256)
+    ap.add_argument("--levels", type=int, default=3)
+    ap.add_argument("--n-lambda", type=int, default=20)
+    ap.add_argument("--packets-per-bin", type=int, default=10_000_000)
+    ap.add_argument("--n-pix", type=int, default=256)
+    ap.add_argument("--precision", type=int, default=32)
+    ap.add_argument("--cpu-packets-per-bin", type=int, default=0, help="oracle sample size (0: auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--block-size", type=int, default=0)
+    ap.add_argument("--refill", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def make_model(a):
+    from paper_1206_3710_gb300 import synth
+    return synth.cloud(n_root=a.n_root, levels=a.levels, n_lambda=a.n_lambda, packets_per_bin=a.packets_per_bin,
+                       n_pix=a.n_pix)
+
+
+def workload_config(a, m):
+    return {"workload": f"molecular cloud: {a.n_root}^3 root, {a.levels} levels (threshold 4^l x mean), "
+                        f"lognormal sigma_ln=1.5, {a.n_lambda} wavelengths, external isotropic field, "
+                        f"{a.packets_per_bin:.0e} packages/wavelength, peel-off {m.observers.n_obs}x"
+                        f"{a.n_pix}^2, FP32 trace + FP64 accumulators",
+            "n_cells": int(m.tree.n_cells), "n_levels": int(m.tree.n_levels),
+            "packets_per_step": int(a.packets_per_bin * a.n_lambda * len(m.sources)),
+            "l2_policy": "inputs larger than L2 (grid + per-wavelength FP64 absorbed arrays)"}
+
+
+def dust_arrays(m):
+    kabs = (1 - m.optics.albedo) * m.optics.kappa_ext
+    return m.optics.lambda_um, kabs, m.optics.dnu
+
+
+def cpu_baseline(a, m, packets_per_bin=None, want_seconds=15.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.Tree(m.tree)
+    t_build = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    ppb = packets_per_bin or 50
+    # grow the sample until it takes a few seconds, capped at want_seconds total
+    while True:
+        t1 = time.perf_counter()
+        r = oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, observers=m.observers, n_threads=cores)
+        dt = time.perf_counter() - t1
+        if packets_per_bin or dt > 0.25 * want_seconds or ppb >= a.packets_per_bin:
+            break
+        ppb = int(ppb * min(8.0, max(2.0, 0.5 * want_seconds / max(dt, 1e-3))))
+    L = r["ledger"]
+    cross = L["n_cross"] + L["n_peel_cross"]
+    return {"value": cross / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "packets_per_s": L["n_packets"] / dt,
+            "sample": f"{ppb} packages per wavelength x {a.n_lambda} wavelengths on the full grid with "
+                      f"{m.observers.n_obs} peel-off observers ({int(L['n_packets'])} packages, "
+                      f"{int(cross)} crossings, {dt:.2f} s; tree build {t_build:.1f} s excluded)"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    m = make_model(a)
+    import oracle
+    tree = oracle.Tree(m.tree)
+    cores = os.cpu_count() or 1
+    ppb = a.cpu_packets_per_bin or max(10, min(200, a.packets_per_bin))
+    for _ in range(a.warmup):
+        oracle.trace(tree, m.sources, m.optics, max(1, ppb // 10), seed=1002, observers=m.observers, n_threads=cores)
+    tot_cross, tot_pk, t = 0.0, 0.0, 0.0
+    for s in range(a.steps):
+        t0 = time.perf_counter()
+        r = oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, iter_=s, observers=m.observers, n_threads=cores)
+        t += time.perf_counter() - t0
+        tot_cross += r["ledger"]["n_cross"] + r["ledger"]["n_peel_cross"]
+        tot_pk += r["ledger"]["n_packets"]
+    v = tot_cross / t
+    sample = f"{ppb} packages per wavelength x {a.n_lambda} wavelengths per step, full grid, peel-off"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded lognormal cloud)",
+            "config": workload_config(a, m), "packets_per_s": tot_pk / t,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_1206_3710_gb300 import rt
+    t_gen = time.perf_counter()
+    m = make_model(a)
+    t_gen = time.perf_counter() - t_gen
+    ctx = rt.Context(local)
+    grid = rt.Grid(ctx, m.tree)
+    nl = m.optics.n_lambda
+    nc = grid.n_cells
+    obs = m.observers
+    absorbed = torch.zeros((nl, nc), dtype=torch.float64, device=dev)
+    images = torch.zeros((obs.n_obs, nl, obs.ny, obs.nx), dtype=torch.float64, device=dev)
+    T = torch.zeros(nc, dtype=torch.float64, device=dev)
+    lam, kabs, dnu = dust_arrays(m)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(seed=1002, job=rank, precision=a.precision, packets_per_bin=a.packets_per_bin,
+              block_size=a.block_size, refill_threshold=a.refill, blocks_per_sm=a.blocks_per_sm)
+
+    def step():
+        absorbed.zero_()
+        images.zero_()
+        led = rt.rt_peel(ctx, grid, m.sources, m.optics, obs, images, absorbed, stream=stream, **kw)
+        rt.rt_dust_temperature(ctx, grid, absorbed, nl, lam, kabs, dnu, T, stream=stream)
+        return led
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0.record(stream)
+    leds = [step() for _ in range(a.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    cross = sum(L["n_cross"] + L["n_peel_cross"] for L in leds)
+    pk = sum(L["n_packets"] for L in leds)
+    if world > 1:
+        ct = torch.tensor([float(cross), float(pk)], dtype=torch.float64, device=dev)
+        dist.all_reduce(ct)
+        cross, pk = float(ct[0]), float(ct[1])
+    value = cross / (t_ms * 1e-3)
+
+    # roofline of the tracer kernel (device time of each launch from the library's events)
+    L0 = leds[-1]
+    kern_ms = statistics.mean(L["kernel_ms"] for L in leds)
+    deposits = L0["n_scatter"] * obs.n_obs - L0["n_peel_out"]
+    alg_bytes = BYTES_TRACE_CROSS * L0["n_cross"] + BYTES_PEEL_CROSS * L0["n_peel_cross"] + BYTES_IMAGE_DEPOSIT * deposits
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": NCU_TRAFFIC_PER_LAUNCH, "peak_kind": peak_kind, "kernel": "trace_kernel<float,true>",
+            "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes,
+            "bytes_per_unit": {"trace_crossing": BYTES_TRACE_CROSS, "peel_crossing": BYTES_PEEL_CROSS,
+                               "image_deposit": BYTES_IMAGE_DEPOSIT}}
+
+    out = None
+    if rank == 0:
+        e2e = None
+        if not a.no_e2e:
+            e2e = e2e_run(a, m, ctx, dev, stream, kw, lam, kabs, dnu)
+        cpu = None
+        if not a.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(a, m, a.cpu_packets_per_bin or None)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32" if a.precision == 32 else "f64",
+               "data": "synthetic (seeded lognormal cloud, random-field density)",
+               "config": workload_config(a, m), "packets_per_s": pk / (t_ms * 1e-3),
+               "crossings_per_step": {"trace": L0["n_cross"], "peel": L0["n_peel_cross"]},
+               "scatterings_per_step": L0["n_scatter"], "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "clocks": clk, "gpu_launches": 3 * a.steps,
+               "energy_balance": (L0["emitted"] - L0["absorbed"] - L0["escaped"]) / L0["emitted"],
+               "model_generation_s": t_gen}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e_run(a, m, ctx, dev, stream, kw, lam, kabs, dnu):
+    """Same metric through the public API from host buffers: host tree ->
+    rt_build_grid -> rt_peel -> rt_dust_temperature -> results to pinned host
+    memory, every step."""
+    import torch
+
+    from paper_1206_3710_gb300 import rt
+    obs = m.observers
+    nl = m.optics.n_lambda
+    nc = m.tree.n_cells
+    host_abs = torch.empty((nl, nc), dtype=torch.float64, pin_memory=True)
+    host_img = torch.empty((obs.n_obs, nl, obs.ny, obs.nx), dtype=torch.float64, pin_memory=True)
+    host_T = torch.empty(nc, dtype=torch.float64, pin_memory=True)
+    absorbed = torch.empty((nl, nc), dtype=torch.float64, device=dev)
+    images = torch.empty((obs.n_obs, nl, obs.ny, obs.nx), dtype=torch.float64, device=dev)
+    T = torch.empty(nc, dtype=torch.float64, device=dev)
+    steps = max(1, min(a.steps, 3))
+    cross = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g = rt.Grid(ctx, m.tree)
+        absorbed.zero_()
+        images.zero_()
+        led = rt.rt_peel(ctx, g, m.sources, m.optics, obs, images, absorbed, stream=stream, **kw)
+        rt.rt_dust_temperature(ctx, g, absorbed, nl, lam, kabs, dnu, T, stream=stream)
+        host_abs.copy_(absorbed, non_blocking=True)
+        host_img.copy_(images, non_blocking=True)
+        host_T.copy_(T, non_blocking=True)
+        torch.cuda.synchronize()
+        g.close()
+        cross += led["n_cross"] + led["n_peel_cross"]
+    dt = time.perf_counter() - t0
+    h2d = m.tree.refine_flags.nbytes + m.tree.density.nbytes + m.tree.n_refined.nbytes
+    d2h = host_abs.numel() * 8 + host_img.numel() * 8 + host_T.numel() * 8
+    return {"value": cross / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": steps, "ms_per_step": 1e3 * dt / steps}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * rt.h -- C ABI of librt.so: GB300 (sm_103a) Monte Carlo continuum radiative
+ * transfer on hierarchical 2x2x2-refined cartesian grids.
+ *
+ * Method: Lunttila & Juvela, "Radiative transfer on hierarchial grids".
+ * Photon packages are emitted by sources (Sect. 2.3), followed cell by cell
+ * through a tree of nested grids (Sect. 2.1) until they leave the outer
+ * boundary of the root grid (Sect. 2.3), losing weight by continuous
+ * absorption and optionally Russian roulette (Sect. 2.3); after every
+ * scattering a peel-off contribution is sent to each observer (Sect. 2.4).
+ * Dust temperatures follow from the balance of absorbed and emitted energy
+ * (Sects. 3.2 and 4), iterated with the Lambda iteration of Eq. 2.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an int status: RT_OK or a negative RT_ERR_* code;
+ *    rt_last_error() returns a message for the calling thread.
+ *  - Host pointers (structs, arrays marked "host") are read only during the
+ *    call.  Pointers marked "device" are CUDA device pointers on the
+ *    context's device; output device buffers belong to the caller.
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Kernels
+ *    run on that stream; calls that return a ledger wait for their own work
+ *    on the stream (bounded by params.timeout_s, RT_ERR_TIMEOUT on expiry).
+ *  - Lengths are cm, densities g/cm^3, opacities cm^2/g (per unit mass).
+ *    The model box is [0, box[0]] x [0, box[1]] x [0, box[2]].
+ *  - Random numbers: Philox4x32-10 (Salmon et al. 2011) with
+ *    key = (seed_lo ^ job, seed_hi ^ iter), counter = (pkt_lo, pkt_hi,
+ *    draw >> 2, (source << 16) | bin); draw j of a package is word j & 3.
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RT_OK = 0,
+  RT_ERR_INVALID = -1,    /* bad argument or inconsistent input */
+  RT_ERR_OOM = -2,        /* device allocation failed */
+  RT_ERR_CUDA = -3,       /* CUDA runtime error */
+  RT_ERR_STEP_LIMIT = -4, /* some package hit the per-package step limit */
+  RT_ERR_TIMEOUT = -5,    /* bounded wait for the device expired */
+  RT_ERR_BUSY = -6        /* server: job does not fit the free budget/slots now */
+};
+
+typedef struct rt_ctx rt_ctx;
+typedef struct rt_grid rt_grid;
+typedef struct rt_server rt_server;
+
+/* Create a context on CUDA device `device`.  Owns scratch memory and
+ * device-side bookkeeping; one context may be used from one host thread at a
+ * time (calls lock it). */
+int rt_ctx_create(int device, rt_ctx** out);
+void rt_ctx_destroy(rt_ctx* ctx);
+/* Message of the last failing call on this thread (static storage, valid
+ * until the next call on the same thread). */
+const char* rt_last_error(void);
+/* Library version string. */
+const char* rt_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Grid (Sect. 2.1 nested grids; Sect. 2.1 subgrid identification array)     */
+/* ------------------------------------------------------------------------ */
+/* Level-ordered tree description (host arrays).  Level 0 is the root grid
+ * in x-fastest order ix + root[0]*(iy + root[1]*iz).  Level l+1 lists, for
+ * each refined level-l cell in order, its 8 children in octant order
+ * ox + 2*oy + 4*oz.  refine_flags: 1 byte per cell (1 = refined).
+ * density: per cell (values of refined cells are ignored).  n_refined[l]:
+ * refined cells on level l (the last level has 0).  Root cells must be
+ * cubic: box[a]/root[a] equal on all axes. */
+typedef struct {
+  int root[3];
+  double box[3];
+  int n_levels;
+  const int64_t* n_refined;
+  const uint8_t* refine_flags;
+  const double* density;
+} rt_tree_desc;
+
+/* Flatten the tree into level-ordered device arrays (structure of arrays):
+ * density (f32; refined cells hold the mean of their children), child
+ * (u32; 0 = leaf, else index of the first of 8 contiguous children), level
+ * (u8), plus the tracer's packed node word (leaf: f32 density scaled to
+ * [0,1]; refined: 0x80000000 | child) and an f64 density copy.  The library
+ * owns the arrays; free with rt_grid_free.  Errors: RT_ERR_INVALID for
+ * inconsistent counts, negative/NaN densities, non-cubic cells, more than
+ * 2^31 cells or a finest lattice above 2^21 cells per axis; RT_ERR_OOM. */
+int rt_build_grid(rt_ctx* ctx, const rt_tree_desc* desc, rt_grid** out);
+
+typedef struct {
+  int64_t n_cells, n_leaves;
+  int depth;               /* deepest level index */
+  int root[3];
+  double box[3];
+  size_t bytes;            /* device bytes held by the grid */
+  const float* density;    /* device [n_cells] */
+  const uint32_t* child;   /* device [n_cells] */
+  const uint8_t* level;    /* device [n_cells] */
+  const uint32_t* node;    /* device [n_cells] packed tracer word */
+  const double* density64; /* device [n_cells] */
+  const uint64_t* coord;   /* device [n_cells] x | y<<21 | z<<42 at the cell's level */
+  double rho_scale;        /* leaf node density = density64 / rho_scale */
+} rt_grid_info;
+int rt_grid_get_info(const rt_grid* grid, rt_grid_info* out);
+void rt_grid_free(rt_grid* grid);
+
+/* ------------------------------------------------------------------------ */
+/* Tracing (Sects. 2.3, 2.4)                                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int n_lambda;            /* 1..256 wavelength bins */
+  const double* kappa_ext; /* host [n_lambda], cm^2/g, >= 0 */
+  const double* albedo;    /* host [n_lambda], in [0,1] */
+  const double* g_hg;      /* host [n_lambda], Henyey-Greenstein g, |g| < 1 */
+} rt_optics;
+
+enum {
+  RT_SRC_POINT = 0,        /* isotropic point source at pos */
+  RT_SRC_EXTERNAL = 1,     /* isotropic external field entering the root box */
+  RT_SRC_DUST = 2,         /* thermal dust emission from temperatures T_dev */
+  RT_SRC_BEAM = 3          /* parallel beam from pos along dir */
+};
+
+typedef struct {
+  int n_lambda;
+  const double* lambda_um; /* host [n_lambda] */
+  const double* kappa_abs; /* host [n_lambda], cm^2/g */
+  const double* dnu;       /* host [n_lambda], Hz, bin widths */
+  double T_min, T_max;     /* K, bracket of the temperature solve */
+} rt_dust;
+
+typedef struct {
+  int kind;
+  double pos[3];            /* cm (point, beam) */
+  double dir[3];            /* beam direction (normalised by the library) */
+  const double* bin_energy; /* host [n_lambda]: energy per bin (point, external, beam) */
+  const double* T_dev;      /* device [n_cells] dust temperatures (dust) */
+  const rt_dust* dust;      /* dust model (dust) */
+} rt_source;
+
+enum { RT_EST_CONTINUOUS = 0, RT_EST_ANALOG = 1 };
+
+typedef struct {
+  uint64_t seed;
+  uint32_t job, iter;       /* mixed into the Philox key */
+  int precision;            /* 32: f32 geometry + f64 accumulators; 64: f64 throughout */
+  int estimator;            /* RT_EST_CONTINUOUS (default) or RT_EST_ANALOG */
+  double rr_wmin;           /* roulette when W < rr_wmin * W0 (after a scattering); <= 0 off */
+  double rr_p;              /* roulette kill probability */
+  int64_t step_limit;       /* max cell segments per package; <= 0: 100000000 */
+  double peel_tau_max;      /* stop a peel-off march once tau exceeds this; <= 0 never */
+  int per_lambda;           /* 1: outputs per bin; 0: summed over bins */
+  int64_t packets_per_bin;  /* > 0: packages for every (source, bin) */
+  const int64_t* packets;   /* host [n_src][n_lambda] when packets_per_bin <= 0 and packets_total <= 0 */
+  int64_t packets_total;    /* > 0: spread over (source, bin) in proportion to energy */
+  double* packet_log_dev;   /* optional device [n_packets][10]: w_escaped, n_scatter, n_cross,
+                               fate (0 escaped, 1 roulette, 2 step limit, 3 analog absorption),
+                               x_exit[3] (cm), d_exit[3] */
+  double timeout_s;         /* bounded wait for completion; <= 0: 3600 s */
+  int block_size;           /* 0: tuned default */
+  int refill_threshold;     /* 0: tuned default; dead lanes per warp before a refill */
+  int blocks_per_sm;        /* 0: occupancy-derived */
+} rt_trace_params;
+
+typedef struct {
+  double emitted, absorbed, escaped, rr_gain, rr_loss, killed, peeled;
+  uint64_t n_packets, n_cross, n_scatter, n_peel_cross, n_killed, n_peel_out;
+  int status;               /* RT_OK or RT_ERR_STEP_LIMIT */
+  double kernel_ms;         /* device time of the tracer launch */
+} rt_ledger;
+
+/* Trace every package of every source and accumulate the absorbed energy
+ * per cell: absorbed_dev (device, [bins][n_cells] f64, bins = n_lambda if
+ * per_lambda else 1) is ADDED to (zero it first).  The ledger (host, may be
+ * NULL) receives the energy balance and counters.  Returns RT_OK,
+ * RT_ERR_STEP_LIMIT if a package was killed by the step limit (results are
+ * still written), or an error. */
+int rt_trace(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
+             const rt_optics* optics, const rt_trace_params* params, double* absorbed_dev,
+             rt_ledger* ledger, void* cuda_stream);
+
+/* Observers for peel-off images (Sect. 2.4): orthographic projection
+ * centred on the box centre; pixel (ix, iy) covers
+ * [(ix - nx/2) fov[0]/nx, ...) along ex = normalise(up x dir), ey = dir x ex. */
+typedef struct {
+  int n_obs;               /* 1..16 */
+  const double* dir;       /* host [n_obs][3] unit vectors towards the observers */
+  const double* up;        /* host [n_obs][3] */
+  int nx, ny;
+  double fov[2];           /* cm */
+} rt_observers;
+
+/* As rt_trace, and after every scattering peel off W p_HG(mu) exp(-tau) to
+ * each observer into images_dev (device, [n_obs][bins][ny][nx] f64, added
+ * to).  absorbed_dev may be NULL. */
+int rt_peel(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
+            const rt_optics* optics, const rt_trace_params* params, const rt_observers* obs,
+            double* images_dev, double* absorbed_dev, rt_ledger* ledger, void* cuda_stream);
+
+/* ------------------------------------------------------------------------ */
+/* Dust (Sects. 3.2, 4)                                                      */
+/* ------------------------------------------------------------------------ */
+/* Per leaf: solve rho V 4 pi sum_i kappa_abs,i B_nu_i(T) dnu_i = A for T in
+ * [T_min, T_max] (clamped), A = sum over n_bins rows of absorbed_dev
+ * (device [n_bins][n_cells]).  T_dev (device [n_cells]) receives T; refined
+ * cells get 0.  FP64 safeguarded Newton on a tabulated bracket. */
+int rt_dust_temperature(rt_ctx* ctx, const rt_grid* grid, const double* absorbed_dev, int n_bins,
+                        const rt_dust* dust, double* T_dev, void* cuda_stream);
+
+/* Dust emission per leaf and bin, 4 pi rho V kappa_abs,i B_nu_i(T) dnu_i,
+ * into emission_dev (device [n_lambda][n_cells]); bin totals to
+ * bin_total_host (host [n_lambda], may be NULL; waits for the stream). */
+int rt_dust_emission(rt_ctx* ctx, const rt_grid* grid, const double* T_dev, const rt_dust* dust,
+                     double* emission_dev, double* bin_total_host, void* cuda_stream);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics used by the parity tests                                      */
+/* ------------------------------------------------------------------------ */
+/* Deterministic walks (Sect. 2.3 cell stepping) of n_rays rays with the
+ * tracer's own stepping code.  origins/dirs: device [n_rays][3] f64 (cm;
+ * converted to the working precision).  Outputs (device): cells
+ * [n_rays][max_seg] int64, lengths [n_rays][max_seg] f64 (cm), counts
+ * [n_rays] int64 (segments of positive length; -1 if the origin is outside). */
+int rt_walk(rt_ctx* ctx, const rt_grid* grid, int64_t n_rays, const double* origins_dev,
+            const double* dirs_dev, int precision, int64_t max_seg, int64_t* cells_dev,
+            double* lengths_dev, int64_t* counts_dev, void* cuda_stream);
+
+/* Philox4x32-10 blocks for n (counter, key) pairs: ctr_dev [n][4], key_dev
+ * [n][2], out_dev [n][4] (device uint32). */
+int rt_philox(rt_ctx* ctx, int64_t n, const uint32_t* ctr_dev, const uint32_t* key_dev,
+              uint32_t* out_dev, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

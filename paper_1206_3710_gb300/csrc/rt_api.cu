@@ -1,0 +1,850 @@
+// rt_api.cu -- the C ABI of librt.so (declared in include/rt.h): contexts,
+// grid flattening, argument validation, job tables, launches, bounded waits.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+using namespace rtk;
+
+// ------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(expr)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+extern "C" const char* rt_last_error(void) { return g_err.c_str(); }
+extern "C" const char* rt_version(void) { return "librt 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------------
+// context
+// ------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  int ensure(size_t bytes) {
+    if (bytes <= n) return RT_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    size_t want = std::max(bytes, (size_t)4096);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(RT_ERR_OOM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    n = want;
+    return RT_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+struct rt_ctx {
+  int device = 0;
+  int sm_count = 0;
+  std::mutex mu;
+  DevBuf table;        // job tables
+  DevBuf small;        // ledgers + counter
+  DevBuf scan_tmp;
+  DevBuf dust_arrays;  // lambda, kappa_abs, dnu, temperature table
+  std::vector<DevBuf> cdf;  // per dust source
+  void* pinned = nullptr;
+  size_t pinned_n = 0;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr;
+};
+
+struct rt_grid {
+  rt_ctx* ctx = nullptr;
+  int device = 0;
+  int root[3] = {0, 0, 0};
+  double box[3] = {0, 0, 0};
+  double h0 = 0;
+  int n_levels = 0;
+  int64_t n_cells = 0, n_leaves = 0, n0 = 0;
+  std::vector<long long> level_off;
+  float* density = nullptr;
+  uint32_t* child = nullptr;
+  uint8_t* level = nullptr;
+  uint32_t* node = nullptr;
+  double* rho64 = nullptr;
+  uint64_t* coord = nullptr;
+  double rho_scale = 1.0;
+  size_t bytes = 0;
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+static int ensure_pinned(rt_ctx* c, size_t bytes) {
+  if (bytes <= c->pinned_n) return RT_OK;
+  if (c->pinned) cudaFreeHost(c->pinned);
+  c->pinned = nullptr;
+  c->pinned_n = 0;
+  size_t want = std::max(bytes, (size_t)65536);
+  cudaError_t e = cudaMallocHost(&c->pinned, want);
+  if (e != cudaSuccess) return fail(RT_ERR_OOM, "cudaMallocHost(%zu): %s", want, cudaGetErrorString(e));
+  c->pinned_n = want;
+  return RT_OK;
+}
+
+extern "C" int rt_ctx_create(int device, rt_ctx** out) {
+  if (!out) return fail(RT_ERR_INVALID, "rt_ctx_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CK(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(RT_ERR_INVALID, "rt_ctx_create: device %d of %d", device, n);
+  DeviceGuard g(device);
+  rt_ctx* c = new rt_ctx();
+  c->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev_a);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev_b);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev_c);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(RT_ERR_CUDA, "rt_ctx_create: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return RT_OK;
+}
+
+extern "C" void rt_ctx_destroy(rt_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  c->table.release();
+  c->small.release();
+  c->scan_tmp.release();
+  c->dust_arrays.release();
+  for (auto& b : c->cdf) b.release();
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->ev_a) cudaEventDestroy(c->ev_a);
+  if (c->ev_b) cudaEventDestroy(c->ev_b);
+  if (c->ev_c) cudaEventDestroy(c->ev_c);
+  delete c;
+}
+
+// wait for an event with a deadline; the device keeps running on timeout
+static int wait_event(cudaEvent_t ev, double timeout_s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return RT_OK;
+    if (e != cudaErrorNotReady) return fail(RT_ERR_CUDA, "device error while waiting: %s", cudaGetErrorString(e));
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > timeout_s) return fail(RT_ERR_TIMEOUT, "device work did not finish within %.3f s", timeout_s);
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+// ------------------------------------------------------------------------
+// grid
+// ------------------------------------------------------------------------
+extern "C" int rt_build_grid(rt_ctx* ctx, const rt_tree_desc* d, rt_grid** out) {
+  if (!ctx || !d || !out) return fail(RT_ERR_INVALID, "rt_build_grid: NULL argument");
+  *out = nullptr;
+  if (d->root[0] <= 0 || d->root[1] <= 0 || d->root[2] <= 0)
+    return fail(RT_ERR_INVALID, "rt_build_grid: root dims must be positive");
+  if (d->n_levels <= 0 || d->n_levels > 24 || !d->n_refined || !d->refine_flags || !d->density)
+    return fail(RT_ERR_INVALID, "rt_build_grid: bad level count or NULL arrays");
+  for (int a = 0; a < 3; ++a)
+    if (!(d->box[a] > 0.0) || !std::isfinite(d->box[a])) return fail(RT_ERR_INVALID, "rt_build_grid: bad box size");
+  const double h0 = d->box[0] / d->root[0];
+  for (int a = 1; a < 3; ++a)
+    if (std::fabs(d->box[a] / d->root[a] - h0) > 1e-12 * h0)
+      return fail(RT_ERR_INVALID, "rt_build_grid: root cells are not cubic");
+  // level sizes
+  std::vector<long long> off(d->n_levels + 1, 0);
+  long long lvl_n = (long long)d->root[0] * d->root[1] * d->root[2];
+  off[1] = lvl_n;
+  for (int l = 0; l < d->n_levels; ++l) {
+    if (d->n_refined[l] < 0 || d->n_refined[l] > lvl_n)
+      return fail(RT_ERR_INVALID, "rt_build_grid: n_refined[%d]=%lld out of range", l, (long long)d->n_refined[l]);
+    if (l == d->n_levels - 1 && d->n_refined[l] != 0)
+      return fail(RT_ERR_INVALID, "rt_build_grid: deepest level has refined cells");
+    if (l + 1 < d->n_levels) {
+      lvl_n = 8ll * d->n_refined[l];
+      off[l + 2] = off[l + 1] + lvl_n;
+    }
+  }
+  const long long n = off[d->n_levels];
+  if (n >= (1ll << 31)) return fail(RT_ERR_INVALID, "rt_build_grid: %lld cells exceed 2^31", n);
+  const int depth = d->n_levels - 1;
+  for (int a = 0; a < 3; ++a)
+    if (((long long)d->root[a] << depth) > (1ll << RT_COORD_BITS))
+      return fail(RT_ERR_INVALID, "rt_build_grid: finest lattice exceeds 2^%d cells per axis", RT_COORD_BITS);
+  // flags are 0/1 and their per-level counts match
+  for (int l = 0; l < d->n_levels; ++l) {
+    long long cnt = 0;
+    for (long long i = off[l]; i < off[l + 1]; ++i) {
+      const uint8_t f = d->refine_flags[i];
+      if (f > 1) return fail(RT_ERR_INVALID, "rt_build_grid: refine flag %d at cell %lld", (int)f, i);
+      cnt += f;
+    }
+    if (cnt != d->n_refined[l])
+      return fail(RT_ERR_INVALID, "rt_build_grid: level %d has %lld refined cells, n_refined says %lld", l, cnt,
+                  (long long)d->n_refined[l]);
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  rt_grid* g = new rt_grid();
+  g->ctx = ctx;
+  g->device = ctx->device;
+  memcpy(g->root, d->root, sizeof g->root);
+  memcpy(g->box, d->box, sizeof g->box);
+  g->h0 = h0;
+  g->n_levels = d->n_levels;
+  g->n_cells = n;
+  g->n0 = off[1];
+  g->level_off = off;
+  auto cleanup = [&](int rc) -> int {
+    rt_grid_free(g);
+    return rc;
+  };
+  uint8_t* flags = nullptr;
+  unsigned long long* excl = nullptr;
+  double* scal = nullptr;
+  int* bad = nullptr;
+  const size_t tmpb = scan_tmp_bytes(n);
+  void* tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes)                                                                    \
+  do {                                                                                       \
+    e = cudaMalloc((void**)&(ptr), (bytes));                                                 \
+    if (e != cudaSuccess) {                                                                  \
+      cudaFree(flags); cudaFree(excl); cudaFree(scal); cudaFree(bad); cudaFree(tmp);         \
+      return cleanup(fail(RT_ERR_OOM, "rt_build_grid: cudaMalloc(%zu): %s", (size_t)(bytes), \
+                          cudaGetErrorString(e)));                                           \
+    }                                                                                        \
+  } while (0)
+  ALLOC(g->density, n * sizeof(float));
+  ALLOC(g->child, n * sizeof(uint32_t));
+  ALLOC(g->level, n * sizeof(uint8_t));
+  ALLOC(g->node, n * sizeof(uint32_t));
+  ALLOC(g->rho64, n * sizeof(double));
+  ALLOC(g->coord, n * sizeof(uint64_t));
+  g->bytes = n * (sizeof(float) + sizeof(uint32_t) * 2 + sizeof(uint8_t) + sizeof(double) + sizeof(uint64_t));
+  ALLOC(flags, n);
+  ALLOC(excl, n * sizeof(unsigned long long));
+  ALLOC(scal, sizeof(double));
+  ALLOC(bad, sizeof(int));
+  ALLOC(tmp, tmpb);
+#undef ALLOC
+  auto finish = [&](int rc) -> int {
+    cudaFree(flags); cudaFree(excl); cudaFree(scal); cudaFree(bad); cudaFree(tmp);
+    if (rc != RT_OK) return cleanup(rc);
+    *out = g;
+    return RT_OK;
+  };
+  cudaStream_t s = nullptr;
+#define CKG(expr)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) return finish(fail(RT_ERR_CUDA, "rt_build_grid: %s: %s", #expr, cudaGetErrorString(e_))); \
+  } while (0)
+  CKG(cudaMemcpyAsync(flags, d->refine_flags, n, cudaMemcpyHostToDevice, s));
+  CKG(cudaMemcpyAsync(g->rho64, d->density, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CKG(scan_flags_u8(flags, n, excl, tmp, tmpb, s));
+  CKG(build_children(flags, excl, n, off[1], g->child, s));
+  CKG(build_levels(off.data(), d->n_levels, g->level, s));
+  for (int l = 0; l < d->n_levels; ++l) CKG(build_coords(g->child, off[l], off[l + 1], l == 0 ? d->root : nullptr, g->coord, s));
+  CKG(validate_leaf_density(g->rho64, g->child, n, bad, s));
+  for (int l = d->n_levels - 2; l >= 0; --l) CKG(build_density(nullptr, g->child, off[l], off[l + 1], g->rho64, s));
+  CKG(reduce_max_leaf(g->rho64, g->child, n, scal, s));
+  int hbad = 0;
+  double hmax = 0.0;
+  CKG(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKG(cudaMemcpyAsync(&hmax, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CKG(cudaStreamSynchronize(s));
+  if (hbad) return finish(fail(RT_ERR_INVALID, "rt_build_grid: negative, NaN or infinite leaf density"));
+  g->rho_scale = hmax > 0.0 ? hmax : 1.0;
+  CKG(build_nodes(g->rho64, g->child, n, 1.0 / g->rho_scale, g->density, g->node, s));
+  CKG(cudaStreamSynchronize(s));
+#undef CKG
+  long long leaves = 0;
+  for (int l = 0; l < d->n_levels; ++l) leaves += (off[l + 1] - off[l]) - d->n_refined[l];
+  g->n_leaves = leaves;
+  return finish(RT_OK);
+}
+
+extern "C" int rt_grid_get_info(const rt_grid* g, rt_grid_info* o) {
+  if (!g || !o) return fail(RT_ERR_INVALID, "rt_grid_get_info: NULL argument");
+  o->n_cells = g->n_cells;
+  o->n_leaves = g->n_leaves;
+  o->depth = g->n_levels - 1;
+  memcpy(o->root, g->root, sizeof o->root);
+  memcpy(o->box, g->box, sizeof o->box);
+  o->bytes = g->bytes;
+  o->density = g->density;
+  o->child = g->child;
+  o->level = g->level;
+  o->node = g->node;
+  o->density64 = g->rho64;
+  o->coord = g->coord;
+  o->rho_scale = g->rho_scale;
+  return RT_OK;
+}
+
+extern "C" void rt_grid_free(rt_grid* g) {
+  if (!g) return;
+  DeviceGuard dg(g->device);
+  cudaFree(g->density);
+  cudaFree(g->child);
+  cudaFree(g->level);
+  cudaFree(g->node);
+  cudaFree(g->rho64);
+  cudaFree(g->coord);
+  delete g;
+}
+
+// ------------------------------------------------------------------------
+// job tables
+// ------------------------------------------------------------------------
+// host-side byte arena mirrored 1:1 into a device buffer
+struct Arena {
+  std::vector<unsigned char> h;
+  size_t put(const void* src, size_t bytes, size_t align = 16) {
+    size_t o = (h.size() + align - 1) / align * align;
+    h.resize(o + bytes);
+    if (src) memcpy(h.data() + o, src, bytes);
+    else memset(h.data() + o, 0, bytes);
+    return o;
+  }
+  template <typename T>
+  T* at(size_t o) {
+    return reinterpret_cast<T*>(h.data() + o);
+  }
+};
+
+static int check_optics(const rt_optics* op) {
+  if (!op || op->n_lambda < 1 || op->n_lambda > RT_MAX_LAMBDA || !op->kappa_ext || !op->albedo || !op->g_hg)
+    return fail(RT_ERR_INVALID, "optics: n_lambda must be 1..%d with non-NULL arrays", RT_MAX_LAMBDA);
+  for (int b = 0; b < op->n_lambda; ++b) {
+    if (!(op->kappa_ext[b] >= 0.0) || !std::isfinite(op->kappa_ext[b]))
+      return fail(RT_ERR_INVALID, "optics: kappa_ext[%d] must be finite and >= 0", b);
+    if (!(op->albedo[b] >= 0.0 && op->albedo[b] <= 1.0)) return fail(RT_ERR_INVALID, "optics: albedo[%d] not in [0,1]", b);
+    if (!(std::fabs(op->g_hg[b]) < 1.0)) return fail(RT_ERR_INVALID, "optics: |g[%d]| must be < 1", b);
+  }
+  return RT_OK;
+}
+
+static int check_dust(const rt_dust* du, int nl) {
+  if (!du || du->n_lambda != nl || !du->lambda_um || !du->kappa_abs || !du->dnu)
+    return fail(RT_ERR_INVALID, "dust: model must have n_lambda = %d and non-NULL arrays", nl);
+  if (!(du->T_min > 0.0) || !(du->T_max > du->T_min) || !std::isfinite(du->T_max))
+    return fail(RT_ERR_INVALID, "dust: need 0 < T_min < T_max");
+  for (int b = 0; b < nl; ++b)
+    if (!(du->lambda_um[b] > 0.0) || !(du->kappa_abs[b] >= 0.0) || !(du->dnu[b] > 0.0) || !std::isfinite(du->kappa_abs[b]))
+      return fail(RT_ERR_INVALID, "dust: bad lambda/kappa_abs/dnu at bin %d", b);
+  return RT_OK;
+}
+
+// upload lambda, kappa_abs, dnu into ctx->dust_arrays (+ table of n_table)
+static int upload_dust(rt_ctx* c, const rt_dust* du, int n_table, double** lam, double** kab, double** dnu,
+                       double** table, cudaStream_t s) {
+  const int nl = du->n_lambda;
+  const size_t bytes = sizeof(double) * (3 * (size_t)nl + (size_t)n_table) + 256;
+  int rc = c->dust_arrays.ensure(bytes);
+  if (rc) return rc;
+  rc = ensure_pinned(c, bytes);
+  if (rc) return rc;
+  double* hp = reinterpret_cast<double*>(c->pinned);
+  memcpy(hp, du->lambda_um, sizeof(double) * nl);
+  memcpy(hp + nl, du->kappa_abs, sizeof(double) * nl);
+  memcpy(hp + 2 * nl, du->dnu, sizeof(double) * nl);
+  double* dp = reinterpret_cast<double*>(c->dust_arrays.p);
+  CK(cudaMemcpyAsync(dp, hp, sizeof(double) * 3 * nl, cudaMemcpyHostToDevice, s));
+  *lam = dp;
+  *kab = dp + nl;
+  *dnu = dp + 2 * nl;
+  *table = dp + 3 * nl;
+  return RT_OK;
+}
+
+struct TraceArgs {
+  const rt_grid* grid;
+  int n_src;
+  const rt_source* src;
+  const rt_optics* optics;
+  const rt_trace_params* prm;
+  const rt_observers* obs;
+  double* images;
+  double* absorbed;
+};
+
+static void cross3(const double* a, const double* b, double* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// build the device job table for a list of jobs; returns total packages
+static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev* led_dev, cudaStream_t s,
+                        Arena& A, std::vector<size_t>& job_off, size_t& items_off, int& n_items, long long& total,
+                        bool& any_peel, int& precision) {
+  // per job: validate, resolve packages per (source, bin), dust CDFs
+  struct Pending {
+    size_t ptr_field;  // offset of a pointer field to patch
+    size_t target;     // arena offset it must point at
+  };
+  std::vector<Pending> patches;
+  std::vector<ItemDev> items;
+  std::vector<std::vector<size_t>> item_patch;  // (bin_prefix, W0) arena offsets per item
+  job_off.assign(n_jobs, 0);
+  total = 0;
+  any_peel = false;
+  precision = 0;
+  int dust_used = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    const TraceArgs& T = jobs[j];
+    const rt_trace_params* p = T.prm;
+    if (!T.grid || !p) return fail(RT_ERR_INVALID, "job %d: NULL grid or params", j);
+    if (T.grid->device != c->device) return fail(RT_ERR_INVALID, "job %d: grid belongs to another device", j);
+    int rc = check_optics(T.optics);
+    if (rc) return rc;
+    const int nl = T.optics->n_lambda;
+    if (T.n_src < 1 || T.n_src > 256 || !T.src) return fail(RT_ERR_INVALID, "job %d: n_src must be 1..256", j);
+    if (p->precision != 32 && p->precision != 64) return fail(RT_ERR_INVALID, "job %d: precision must be 32 or 64", j);
+    if (precision && precision != p->precision) return fail(RT_ERR_INVALID, "jobs of one launch must share precision");
+    precision = p->precision;
+    if (p->estimator != RT_EST_CONTINUOUS && p->estimator != RT_EST_ANALOG)
+      return fail(RT_ERR_INVALID, "job %d: unknown estimator", j);
+    if (p->rr_wmin > 0.0 && !(p->rr_p >= 0.0 && p->rr_p < 1.0)) return fail(RT_ERR_INVALID, "job %d: rr_p must be in [0,1)", j);
+    if (p->estimator == RT_EST_ANALOG && p->rr_wmin > 0.0)
+      return fail(RT_ERR_INVALID, "job %d: roulette applies to the continuous-absorption estimator only", j);
+    if (T.obs) {
+      const rt_observers* o = T.obs;
+      if (o->n_obs < 1 || o->n_obs > RT_MAX_OBS || !o->dir || !o->up || o->nx < 1 || o->ny < 1 || !(o->fov[0] > 0) ||
+          !(o->fov[1] > 0))
+        return fail(RT_ERR_INVALID, "job %d: observers need 1..%d directions, nx, ny, fov > 0", j, RT_MAX_OBS);
+      if (!T.images) return fail(RT_ERR_INVALID, "job %d: images buffer is NULL", j);
+      any_peel = true;
+    }
+    const rt_grid* G = T.grid;
+    const long long nc = G->n_cells;
+    // energies and dust CDFs
+    std::vector<double> energy((size_t)T.n_src * nl, 0.0);
+    std::vector<double*> cdfs(T.n_src, nullptr);
+    for (int si = 0; si < T.n_src; ++si) {
+      const rt_source& S = T.src[si];
+      if (S.kind == RT_SRC_DUST) {
+        if (!S.T_dev) return fail(RT_ERR_INVALID, "job %d source %d: dust source needs T_dev", j, si);
+        rc = check_dust(S.dust, nl);
+        if (rc) return rc;
+        if ((int)c->cdf.size() <= dust_used) c->cdf.resize(dust_used + 1);
+        DevBuf& cb = c->cdf[dust_used++];
+        rc = cb.ensure(sizeof(double) * (size_t)nl * nc);
+        if (rc) return rc;
+        double *lam, *kab, *dnu, *tab;
+        rc = upload_dust(c, S.dust, 0, &lam, &kab, &dnu, &tab, s);
+        if (rc) return rc;
+        double* cdf = reinterpret_cast<double*>(cb.p);
+        CK(dust_emission(S.T_dev, nc, G->child, G->rho64, G->level, G->h0, lam, kab, dnu, nl, cdf, s));
+        const size_t tb = scan_rows_tmp_bytes(nl, nc);
+        rc = c->scan_tmp.ensure(tb);
+        if (rc) return rc;
+        CK(scan_rows_f64(cdf, nl, nc, c->scan_tmp.p, c->scan_tmp.n, s));
+        std::vector<double> last(nl);
+        for (int b = 0; b < nl; ++b)
+          CK(cudaMemcpyAsync(&last[b], cdf + (size_t)b * nc + (nc - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int b = 0; b < nl; ++b) energy[(size_t)si * nl + b] = last[b];
+        cdfs[si] = cdf;
+      } else if (S.kind == RT_SRC_POINT || S.kind == RT_SRC_EXTERNAL || S.kind == RT_SRC_BEAM) {
+        if (!S.bin_energy) return fail(RT_ERR_INVALID, "job %d source %d: bin_energy is NULL", j, si);
+        for (int b = 0; b < nl; ++b) {
+          if (!(S.bin_energy[b] >= 0.0) || !std::isfinite(S.bin_energy[b]))
+            return fail(RT_ERR_INVALID, "job %d source %d: bin_energy[%d] must be finite and >= 0", j, si, b);
+          energy[(size_t)si * nl + b] = S.bin_energy[b];
+        }
+        if (S.kind == RT_SRC_BEAM) {
+          const double n2 = S.dir[0] * S.dir[0] + S.dir[1] * S.dir[1] + S.dir[2] * S.dir[2];
+          if (!(n2 > 0.0) || !std::isfinite(n2)) return fail(RT_ERR_INVALID, "job %d source %d: beam dir is zero", j, si);
+        }
+        for (int a = 0; a < 3; ++a)
+          if (!std::isfinite(S.pos[a])) return fail(RT_ERR_INVALID, "job %d source %d: pos not finite", j, si);
+      } else {
+        return fail(RT_ERR_INVALID, "job %d source %d: unknown kind %d", j, si, S.kind);
+      }
+    }
+    // packages per (source, bin)
+    std::vector<long long> pk((size_t)T.n_src * nl, 0);
+    if (p->packets_per_bin > 0) {
+      std::fill(pk.begin(), pk.end(), (long long)p->packets_per_bin);
+    } else if (p->packets_total > 0) {
+      double tot = 0.0;
+      for (double v : energy) tot += v;
+      for (size_t i = 0; i < pk.size(); ++i) {
+        long long v = tot > 0 ? (long long)std::floor((double)p->packets_total * energy[i] / tot) : 0;
+        if (energy[i] > 0 && v == 0) v = 1;
+        pk[i] = v;
+      }
+    } else if (p->packets) {
+      for (size_t i = 0; i < pk.size(); ++i) {
+        if (p->packets[i] < 0) return fail(RT_ERR_INVALID, "job %d: negative package count", j);
+        pk[i] = p->packets[i];
+      }
+    } else {
+      return fail(RT_ERR_INVALID, "job %d: set packets_per_bin, packets_total or packets", j);
+    }
+    // a dust bin that emits nothing has no cell to sample from: no packages
+    for (int si = 0; si < T.n_src; ++si)
+      if (T.src[si].kind == RT_SRC_DUST)
+        for (int b = 0; b < nl; ++b)
+          if (!(energy[(size_t)si * nl + b] > 0.0)) pk[(size_t)si * nl + b] = 0;
+    // job entry
+    JobDev J;
+    memset(&J, 0, sizeof J);
+    J.node = G->node;
+    J.rho64 = G->rho64;
+    J.coord = G->coord;
+    J.level = G->level;
+    for (int a = 0; a < 3; ++a) J.root[a] = (uint32_t)G->root[a];
+    J.depth = G->n_levels - 1;
+    J.h0 = G->h0;
+    J.n_lambda = nl;
+    J.estimator = p->estimator;
+    J.n_cells = nc;
+    J.absorbed = T.absorbed;
+    J.abs_bins = p->per_lambda ? nl : 1;
+    J.img_bins = p->per_lambda ? nl : 1;
+    J.images = T.images;
+    J.n_obs = T.obs ? T.obs->n_obs : 0;
+    J.packet_log = p->packet_log_dev;
+    J.ledger = led_dev + j;
+    J.seed = p->seed;
+    J.job_id = p->job;
+    J.iter = p->iter;
+    J.rr_wmin = p->rr_wmin;
+    J.rr_p = p->rr_p;
+    J.step_limit = p->step_limit > 0 ? p->step_limit : 100000000ll;
+    J.peel_tau_max = p->peel_tau_max;
+    const size_t jo = A.put(&J, sizeof J);
+    job_off[j] = jo;
+    // bins
+    std::vector<BinDev> bins(nl);
+    for (int b = 0; b < nl; ++b) {
+      BinDev& B = bins[b];
+      memset(&B, 0, sizeof B);
+      B.kext_d = T.optics->kappa_ext[b] * G->h0;
+      B.kext_f = (float)(T.optics->kappa_ext[b] * G->h0 * G->rho_scale);
+      B.albedo = (float)T.optics->albedo[b];
+      B.g = (float)T.optics->g_hg[b];
+      B.albedo_d = T.optics->albedo[b];
+      B.g_d = T.optics->g_hg[b];
+    }
+    const size_t bo = A.put(bins.data(), sizeof(BinDev) * nl);
+    patches.push_back({jo + offsetof(JobDev, bins), bo});
+    // observers
+    if (T.obs) {
+      std::vector<ObsDev> ob(T.obs->n_obs);
+      for (int o = 0; o < T.obs->n_obs; ++o) {
+        ObsDev& O = ob[o];
+        memset(&O, 0, sizeof O);
+        double k[3] = {T.obs->dir[3 * o], T.obs->dir[3 * o + 1], T.obs->dir[3 * o + 2]};
+        const double kn = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        if (!(kn > 0)) return fail(RT_ERR_INVALID, "job %d observer %d: zero direction", j, o);
+        for (double& v : k) v /= kn;
+        double ex[3], ey[3];
+        cross3(&T.obs->up[3 * o], k, ex);
+        const double en = std::sqrt(ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2]);
+        if (!(en > 1e-12)) return fail(RT_ERR_INVALID, "job %d observer %d: up is parallel to dir", j, o);
+        for (double& v : ex) v /= en;
+        cross3(k, ex, ey);
+        for (int a = 0; a < 3; ++a) {
+          O.k[a] = k[a];
+          O.ex[a] = ex[a];
+          O.ey[a] = ey[a];
+          O.c[a] = 0.5 * G->root[a];
+        }
+        O.inv_pix[0] = T.obs->nx * G->h0 / T.obs->fov[0];
+        O.inv_pix[1] = T.obs->ny * G->h0 / T.obs->fov[1];
+        O.nx = T.obs->nx;
+        O.ny = T.obs->ny;
+      }
+      const size_t oo = A.put(ob.data(), sizeof(ObsDev) * ob.size());
+      patches.push_back({jo + offsetof(JobDev, obs), oo});
+    }
+    // items
+    long long log_off = 0;
+    for (int si = 0; si < T.n_src; ++si) {
+      const rt_source& S = T.src[si];
+      ItemDev I;
+      memset(&I, 0, sizeof I);
+      I.job = j;
+      I.kind = S.kind;
+      I.src_index = (uint32_t)si;
+      for (int a = 0; a < 3; ++a) I.pos[a] = S.pos[a] / G->h0;
+      if (S.kind == RT_SRC_BEAM) {
+        const double n2 = std::sqrt(S.dir[0] * S.dir[0] + S.dir[1] * S.dir[1] + S.dir[2] * S.dir[2]);
+        for (int a = 0; a < 3; ++a) I.dir[a] = S.dir[a] / n2;
+      }
+      std::vector<long long> pref(nl + 1, 0);
+      std::vector<double> w0(nl, 0.0);
+      for (int b = 0; b < nl; ++b) {
+        const long long np_ = pk[(size_t)si * nl + b];
+        pref[b + 1] = pref[b] + np_;
+        w0[b] = np_ > 0 ? energy[(size_t)si * nl + b] / (double)np_ : 0.0;
+      }
+      I.pkt_begin = total;
+      I.pkt_end = total + pref[nl];
+      I.log_offset = log_off;
+      I.cdf = cdfs[si];
+      total += pref[nl];
+      log_off += pref[nl];
+      const size_t po = A.put(pref.data(), sizeof(long long) * (nl + 1));
+      const size_t wo = A.put(w0.data(), sizeof(double) * nl);
+      if (pref[nl] == 0) continue;  // nothing to emit
+      items.push_back(I);
+      item_patch.push_back({po, wo});
+    }
+  }
+  // items array
+  n_items = (int)items.size();
+  items_off = A.put(items.data(), sizeof(ItemDev) * std::max<size_t>(items.size(), 1));
+  for (int i = 0; i < n_items; ++i) {
+    patches.push_back({items_off + i * sizeof(ItemDev) + offsetof(ItemDev, bin_prefix), item_patch[i][0]});
+    patches.push_back({items_off + i * sizeof(ItemDev) + offsetof(ItemDev, W0), item_patch[i][1]});
+  }
+  // device copy, pointer fix-ups
+  int rc = c->table.ensure(A.h.size() + 256);
+  if (rc) return rc;
+  char* base = reinterpret_cast<char*>(c->table.p);
+  for (const Pending& pp : patches) {
+    void* v = base + pp.target;
+    memcpy(A.h.data() + pp.ptr_field, &v, sizeof(void*));
+  }
+  rc = ensure_pinned(c, A.h.size());
+  if (rc) return rc;
+  memcpy(c->pinned, A.h.data(), A.h.size());
+  CK(cudaMemcpyAsync(base, c->pinned, A.h.size(), cudaMemcpyHostToDevice, s));
+  return RT_OK;
+}
+
+static int default_refill(int precision, bool peel) {
+  (void)precision;
+  (void)peel;
+  return 8;
+}
+
+static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* ledgers, cudaStream_t s,
+                    const rt_trace_params* launch_prm) {
+  // ledgers + package counter
+  int rc = c->small.ensure(sizeof(LedgerDev) * n_jobs + 256);
+  if (rc) return rc;
+  LedgerDev* led = reinterpret_cast<LedgerDev*>(c->small.p);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(led + n_jobs);
+  Arena A;
+  std::vector<size_t> job_off;
+  size_t items_off = 0;
+  int n_items = 0, precision = 32;
+  long long total = 0;
+  bool peel = false;
+  rc = build_tables(c, n_jobs, jobs, led, s, A, job_off, items_off, n_items, total, peel, precision);
+  if (rc) return rc;
+  char* base = reinterpret_cast<char*>(c->table.p);
+  CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + sizeof(unsigned long long), s));
+  // launch configuration
+  LaunchCfg cfg;
+  cfg.block = launch_prm->block_size > 0 ? launch_prm->block_size : 256;
+  if (cfg.block % 32 || cfg.block > 256) return fail(RT_ERR_INVALID, "block_size must be a multiple of 32 and <= 256");
+  int occ = 0;
+  CK(trace_occupancy(precision, peel, cfg.block, &occ));
+  if (occ < 1) occ = 1;
+  if (launch_prm->blocks_per_sm > 0) occ = std::min(occ, launch_prm->blocks_per_sm);
+  cfg.blocks = c->sm_count * occ;
+  cfg.refill = launch_prm->refill_threshold > 0 ? launch_prm->refill_threshold : default_refill(precision, peel);
+  if (cfg.refill > 32) cfg.refill = 32;
+  CK(cudaEventRecord(c->ev_a, s));
+  if (total > 0 && n_items > 0)
+    CK(launch_trace(precision, peel, reinterpret_cast<const JobDev*>(base + job_off[0]),
+                    reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, s));
+  CK(cudaEventRecord(c->ev_b, s));
+  std::vector<LedgerDev> hl(n_jobs);
+  CK(cudaMemcpyAsync(hl.data(), led, sizeof(LedgerDev) * n_jobs, cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(c->ev_c, s));
+  const double to = launch_prm->timeout_s > 0 ? launch_prm->timeout_s : 3600.0;
+  rc = wait_event(c->ev_c, to);
+  if (rc) return rc;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
+  int status = RT_OK;
+  for (int j = 0; j < n_jobs; ++j) {
+    const LedgerDev& L = hl[j];
+    if (ledgers) {
+      rt_ledger& o = ledgers[j];
+      o.emitted = L.emitted;
+      o.absorbed = L.absorbed;
+      o.escaped = L.escaped;
+      o.rr_gain = L.rr_gain;
+      o.rr_loss = L.rr_loss;
+      o.killed = L.killed;
+      o.peeled = L.peeled;
+      o.n_packets = L.n_packets;
+      o.n_cross = L.n_cross;
+      o.n_scatter = L.n_scatter;
+      o.n_peel_cross = L.n_peel_cross;
+      o.n_killed = L.n_killed;
+      o.n_peel_out = L.n_peel_out;
+      o.status = L.status ? RT_ERR_STEP_LIMIT : RT_OK;
+      o.kernel_ms = ms;
+    }
+    if (L.status) status = RT_ERR_STEP_LIMIT;
+  }
+  if (status != RT_OK) return fail(status, "some packages were killed by the step limit");
+  return RT_OK;
+}
+
+extern "C" int rt_trace(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src, const rt_optics* optics,
+                        const rt_trace_params* params, double* absorbed_dev, rt_ledger* ledger, void* cuda_stream) {
+  if (!ctx || !grid || !params) return fail(RT_ERR_INVALID, "rt_trace: NULL argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  TraceArgs T{grid, n_src, src, optics, params, nullptr, nullptr, absorbed_dev};
+  if (ledger) memset(ledger, 0, sizeof *ledger);
+  return run_jobs(ctx, 1, &T, ledger, (cudaStream_t)cuda_stream, params);
+}
+
+extern "C" int rt_peel(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src, const rt_optics* optics,
+                       const rt_trace_params* params, const rt_observers* obs, double* images_dev,
+                       double* absorbed_dev, rt_ledger* ledger, void* cuda_stream) {
+  if (!ctx || !grid || !params || !obs) return fail(RT_ERR_INVALID, "rt_peel: NULL argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  TraceArgs T{grid, n_src, src, optics, params, obs, images_dev, absorbed_dev};
+  if (ledger) memset(ledger, 0, sizeof *ledger);
+  return run_jobs(ctx, 1, &T, ledger, (cudaStream_t)cuda_stream, params);
+}
+
+// ------------------------------------------------------------------------
+// dust
+// ------------------------------------------------------------------------
+extern "C" int rt_dust_temperature(rt_ctx* ctx, const rt_grid* g, const double* absorbed_dev, int n_bins,
+                                   const rt_dust* dust, double* T_dev, void* cuda_stream) {
+  if (!ctx || !g || !absorbed_dev || !T_dev || n_bins < 1) return fail(RT_ERR_INVALID, "rt_dust_temperature: bad argument");
+  if (!dust) return fail(RT_ERR_INVALID, "rt_dust_temperature: dust is NULL");
+  int rc = check_dust(dust, dust->n_lambda);
+  if (rc) return rc;
+  if (dust->n_lambda < 1 || dust->n_lambda > RT_MAX_LAMBDA) return fail(RT_ERR_INVALID, "dust: n_lambda out of range");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int n_table = 1024;
+  double *lam, *kab, *dnu, *tab;
+  rc = upload_dust(ctx, dust, n_table, &lam, &kab, &dnu, &tab, s);
+  if (rc) return rc;
+  CK(dust_table(lam, kab, dnu, dust->n_lambda, dust->T_min, dust->T_max, n_table, tab, s));
+  CK(dust_temperature(absorbed_dev, n_bins, g->n_cells, g->child, g->rho64, g->level, g->h0, lam, kab, dnu,
+                      dust->n_lambda, dust->T_min, dust->T_max, tab, n_table, T_dev, s));
+  CK(cudaEventRecord(ctx->ev_b, s));
+  return wait_event(ctx->ev_b, 3600.0);
+}
+
+extern "C" int rt_dust_emission(rt_ctx* ctx, const rt_grid* g, const double* T_dev, const rt_dust* dust,
+                                double* emission_dev, double* bin_total_host, void* cuda_stream) {
+  if (!ctx || !g || !T_dev || !emission_dev || !dust) return fail(RT_ERR_INVALID, "rt_dust_emission: bad argument");
+  int rc = check_dust(dust, dust->n_lambda);
+  if (rc) return rc;
+  if (dust->n_lambda < 1 || dust->n_lambda > RT_MAX_LAMBDA) return fail(RT_ERR_INVALID, "dust: n_lambda out of range");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  double *lam, *kab, *dnu, *tab;
+  rc = upload_dust(ctx, dust, 0, &lam, &kab, &dnu, &tab, s);
+  if (rc) return rc;
+  CK(dust_emission(T_dev, g->n_cells, g->child, g->rho64, g->level, g->h0, lam, kab, dnu, dust->n_lambda, emission_dev, s));
+  if (bin_total_host) {
+    rc = ctx->small.ensure(sizeof(double) * dust->n_lambda + 256);
+    if (rc) return rc;
+    double* tot = reinterpret_cast<double*>(ctx->small.p);
+    CK(row_sums_f64(emission_dev, dust->n_lambda, g->n_cells, tot, s));
+    CK(cudaMemcpyAsync(bin_total_host, tot, sizeof(double) * dust->n_lambda, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaEventRecord(ctx->ev_b, s));
+  return wait_event(ctx->ev_b, 3600.0);
+}
+
+// ------------------------------------------------------------------------
+// diagnostics
+// ------------------------------------------------------------------------
+extern "C" int rt_walk(rt_ctx* ctx, const rt_grid* g, int64_t n_rays, const double* origins_dev, const double* dirs_dev,
+                       int precision, int64_t max_seg, int64_t* cells_dev, double* lengths_dev, int64_t* counts_dev,
+                       void* cuda_stream) {
+  if (!ctx || !g || n_rays < 0 || max_seg < 0 || (n_rays > 0 && (!origins_dev || !dirs_dev || !counts_dev)) ||
+      (max_seg > 0 && (!cells_dev || !lengths_dev)))
+    return fail(RT_ERR_INVALID, "rt_walk: bad argument");
+  if (precision != 32 && precision != 64) return fail(RT_ERR_INVALID, "rt_walk: precision must be 32 or 64");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  JobDev J;
+  memset(&J, 0, sizeof J);
+  J.node = g->node;
+  J.rho64 = g->rho64;
+  J.coord = g->coord;
+  J.level = g->level;
+  for (int a = 0; a < 3; ++a) J.root[a] = (uint32_t)g->root[a];
+  J.depth = g->n_levels - 1;
+  J.h0 = g->h0;
+  J.n_cells = g->n_cells;
+  int rc = ctx->table.ensure(sizeof J);
+  if (rc) return rc;
+  rc = ensure_pinned(ctx, sizeof J);
+  if (rc) return rc;
+  memcpy(ctx->pinned, &J, sizeof J);
+  CK(cudaMemcpyAsync(ctx->table.p, ctx->pinned, sizeof J, cudaMemcpyHostToDevice, s));
+  CK(launch_walk(precision, reinterpret_cast<const JobDev*>(ctx->table.p), n_rays, origins_dev, dirs_dev, max_seg,
+                 reinterpret_cast<long long*>(cells_dev), lengths_dev, reinterpret_cast<long long*>(counts_dev), s));
+  CK(cudaEventRecord(ctx->ev_b, s));
+  return wait_event(ctx->ev_b, 3600.0);
+}
+
+extern "C" int rt_philox(rt_ctx* ctx, int64_t n, const uint32_t* ctr_dev, const uint32_t* key_dev, uint32_t* out_dev,
+                         void* cuda_stream) {
+  if (!ctx || n < 0 || (n > 0 && (!ctr_dev || !key_dev || !out_dev))) return fail(RT_ERR_INVALID, "rt_philox: bad argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CK(launch_philox(n, ctr_dev, key_dev, out_dev, s));
+  CK(cudaEventRecord(ctx->ev_b, s));
+  return wait_event(ctx->ev_b, 3600.0);
+}

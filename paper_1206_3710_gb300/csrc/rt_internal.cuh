@@ -1,0 +1,149 @@
+// rt_internal.cuh -- device-side data layout shared by the library's .cu files.
+//
+// The grid lives in HBM as level-ordered arrays (Sect. 2.1 nested grids,
+// octree case).  The tracer reads one 32-bit word per cell visit: a leaf
+// holds its density as a non-negative f32 (scaled by 1/rho_scale), a refined
+// cell holds 0x80000000 | index-of-first-child.  This folds the "subgrid
+// identification array" of Sect. 2.1 into the density array, as the
+// footnote of Sect. 3.4 suggests.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt.h"
+
+#define RT_MAX_OBS 16
+#define RT_MAX_LAMBDA 256
+#define RT_INTERIOR 0x80000000u
+#define RT_CHILD_MASK 0x7FFFFFFFu
+#define RT_COORD_BITS 21
+#define RT_COORD_MASK ((1ull << RT_COORD_BITS) - 1ull)
+
+// per wavelength bin optics, scaled to the tracer's units
+struct BinDev {
+  double kext_d;   // kappa_ext * h0 (multiplies f64 density), per root-cell unit
+  float kext_f;    // kappa_ext * h0 * rho_scale (multiplies the node's f32 density)
+  float albedo;
+  float g;
+  float pad;
+  double albedo_d, g_d;
+};
+
+// observer, in root-cell units
+struct ObsDev {
+  double k[3], ex[3], ey[3];
+  double c[3];        // box centre
+  double inv_pix[2];  // 1 / pixel size
+  int nx, ny;
+};
+
+struct LedgerDev {
+  double emitted, absorbed, escaped, rr_gain, rr_loss, killed, peeled;
+  unsigned long long n_packets, n_cross, n_scatter, n_peel_cross, n_killed, n_peel_out;
+  int status;
+  int pad;
+};
+
+struct JobDev {
+  const uint32_t* node;
+  const double* rho64;
+  const uint64_t* coord;
+  const uint8_t* level;
+  uint32_t root[3];
+  int depth;
+  double h0;
+  int n_lambda;
+  int estimator;
+  const BinDev* bins;
+  long long n_cells;
+  double* absorbed;
+  int abs_bins;     // n_lambda or 1
+  int img_bins;
+  double* images;
+  int n_obs;
+  int pad0;
+  const ObsDev* obs;
+  LedgerDev* ledger;
+  double* packet_log;
+  unsigned long long seed;
+  uint32_t job_id, iter;
+  double rr_wmin, rr_p;
+  long long step_limit;
+  double peel_tau_max;
+};
+
+// one (job, source) work item: a contiguous range of the global package counter
+struct ItemDev {
+  long long pkt_begin, pkt_end;
+  long long log_offset;
+  int job;
+  int kind;
+  uint32_t src_index;
+  int pad;
+  double pos[3];   // root-cell units
+  double dir[3];
+  const long long* bin_prefix;  // [n_lambda + 1] package prefix within the item
+  const double* W0;             // [n_lambda]
+  const double* cdf;            // dust: [n_lambda][n_cells] inclusive cumulative emission
+};
+
+// ------------------------------------------------------------------------
+// host-side helpers implemented in rt_trace.cu / rt_dust.cu / rt_grid.cu
+// ------------------------------------------------------------------------
+namespace rtk {
+
+struct LaunchCfg {
+  int block;
+  int blocks;
+  int refill;
+};
+
+// launch the persistent tracer over n_items items of total packages
+cudaError_t launch_trace(int precision, bool peel, const JobDev* jobs_dev, const ItemDev* items_dev,
+                         int n_items, unsigned long long* counter_dev, long long total,
+                         const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm);
+
+cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, const double* origins,
+                        const double* dirs, long long max_seg, long long* cells, double* lengths,
+                        long long* counts, cudaStream_t s);
+cudaError_t launch_philox(long long n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                          cudaStream_t s);
+
+// grid build kernels
+cudaError_t scan_flags_u8(const uint8_t* flags, long long n, unsigned long long* excl, void* tmp,
+                          size_t tmp_bytes, cudaStream_t s);
+size_t scan_tmp_bytes(long long n);
+cudaError_t build_children(const uint8_t* flags, const unsigned long long* excl, long long n,
+                           long long n0, uint32_t* child, cudaStream_t s);
+cudaError_t build_levels(const long long* level_off, int n_levels, uint8_t* level, cudaStream_t s);
+cudaError_t build_coords(const uint32_t* child, long long lvl_begin, long long lvl_end, const int* root,
+                         uint64_t* coord, cudaStream_t s);
+cudaError_t build_density(const double* dens_in, const uint32_t* child, long long lvl_begin,
+                          long long lvl_end, double* rho64, cudaStream_t s);
+cudaError_t build_nodes(const double* rho64, const uint32_t* child, long long n, double inv_scale,
+                        float* density, uint32_t* node, cudaStream_t s);
+cudaError_t reduce_max_leaf(const double* rho64, const uint32_t* child, long long n, double* out,
+                            cudaStream_t s);
+cudaError_t validate_leaf_density(const double* rho64, const uint32_t* child, long long n, int* bad,
+                                  cudaStream_t s);
+
+// dust kernels
+cudaError_t dust_table(const double* lam_um, const double* kabs, const double* dnu, int nl, double Tmin,
+                       double Tmax, int n_table, double* table, cudaStream_t s);
+cudaError_t dust_temperature(const double* absorbed, int n_bins, long long n_cells, const uint32_t* child,
+                             const double* rho64, const uint8_t* level, double h0, const double* lam_um,
+                             const double* kabs, const double* dnu, int nl, double Tmin, double Tmax,
+                             const double* table, int n_table, double* T, cudaStream_t s);
+cudaError_t dust_emission(const double* T, long long n_cells, const uint32_t* child, const double* rho64,
+                          const uint8_t* level, double h0, const double* lam_um, const double* kabs,
+                          const double* dnu, int nl, double* emission, cudaStream_t s);
+// per-row sums of rows x n (f64) into out[rows] (device)
+cudaError_t row_sums_f64(const double* data, int n_rows, long long n, double* out, cudaStream_t s);
+// inclusive prefix sums of n_rows rows of length n (f64), in place
+cudaError_t scan_rows_f64(double* data, int n_rows, long long n, void* tmp, size_t tmp_bytes,
+                          cudaStream_t s);
+size_t scan_rows_tmp_bytes(int n_rows, long long n);
+
+}  // namespace rtk

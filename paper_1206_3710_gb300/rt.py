@@ -1,0 +1,344 @@
+"""Thin ctypes binding of librt.so (C ABI in include/rt.h).
+
+Argument marshalling only: every step of the transport runs in the CUDA
+library.  Device buffers are torch CUDA tensors passed by pointer; streams
+are torch CUDA streams.  If the compiled library is missing this module
+raises at import time: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt.so")
+
+RT_OK, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_STEP_LIMIT, RT_ERR_TIMEOUT, RT_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6
+RT_SRC_POINT, RT_SRC_EXTERNAL, RT_SRC_DUST, RT_SRC_BEAM = 0, 1, 2, 3
+RT_EST_CONTINUOUS, RT_EST_ANALOG = 0, 1
+SOURCE_KINDS = {"point": RT_SRC_POINT, "external": RT_SRC_EXTERNAL, "dust": RT_SRC_DUST, "beam": RT_SRC_BEAM}
+
+EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "rt_build_grid", "rt_grid_get_info",
+            "rt_grid_free", "rt_trace", "rt_peel", "rt_dust_temperature", "rt_dust_emission", "rt_walk",
+            "rt_philox"]
+
+
+class RtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"librt error {code}: {msg}")
+        self.code = code
+
+
+class rt_tree_desc(C.Structure):
+    _fields_ = [("root", C.c_int * 3), ("box", C.c_double * 3), ("n_levels", C.c_int),
+                ("n_refined", C.POINTER(C.c_int64)), ("refine_flags", C.POINTER(C.c_uint8)),
+                ("density", C.POINTER(C.c_double))]
+
+
+class rt_grid_info(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_leaves", C.c_int64), ("depth", C.c_int), ("root", C.c_int * 3),
+                ("box", C.c_double * 3), ("bytes", C.c_size_t), ("density", C.c_void_p), ("child", C.c_void_p),
+                ("level", C.c_void_p), ("node", C.c_void_p), ("density64", C.c_void_p), ("coord", C.c_void_p),
+                ("rho_scale", C.c_double)]
+
+
+class rt_optics(C.Structure):
+    _fields_ = [("n_lambda", C.c_int), ("kappa_ext", C.POINTER(C.c_double)), ("albedo", C.POINTER(C.c_double)),
+                ("g_hg", C.POINTER(C.c_double))]
+
+
+class rt_dust(C.Structure):
+    _fields_ = [("n_lambda", C.c_int), ("lambda_um", C.POINTER(C.c_double)), ("kappa_abs", C.POINTER(C.c_double)),
+                ("dnu", C.POINTER(C.c_double)), ("T_min", C.c_double), ("T_max", C.c_double)]
+
+
+class rt_source(C.Structure):
+    _fields_ = [("kind", C.c_int), ("pos", C.c_double * 3), ("dir", C.c_double * 3),
+                ("bin_energy", C.POINTER(C.c_double)), ("T_dev", C.c_void_p), ("dust", C.POINTER(rt_dust))]
+
+
+class rt_trace_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("job", C.c_uint32), ("iter", C.c_uint32), ("precision", C.c_int),
+                ("estimator", C.c_int), ("rr_wmin", C.c_double), ("rr_p", C.c_double), ("step_limit", C.c_int64),
+                ("peel_tau_max", C.c_double), ("per_lambda", C.c_int), ("packets_per_bin", C.c_int64),
+                ("packets", C.POINTER(C.c_int64)), ("packets_total", C.c_int64), ("packet_log_dev", C.c_void_p),
+                ("timeout_s", C.c_double), ("block_size", C.c_int), ("refill_threshold", C.c_int),
+                ("blocks_per_sm", C.c_int)]
+
+
+LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
+                 "n_scatter", "n_peel_cross", "n_killed", "n_peel_out", "status", "kernel_ms"]
+
+
+class rt_ledger(C.Structure):
+    _fields_ = [("emitted", C.c_double), ("absorbed", C.c_double), ("escaped", C.c_double),
+                ("rr_gain", C.c_double), ("rr_loss", C.c_double), ("killed", C.c_double), ("peeled", C.c_double),
+                ("n_packets", C.c_uint64), ("n_cross", C.c_uint64), ("n_scatter", C.c_uint64),
+                ("n_peel_cross", C.c_uint64), ("n_killed", C.c_uint64), ("n_peel_out", C.c_uint64),
+                ("status", C.c_int), ("kernel_ms", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n in LEDGER_FIELDS}
+
+
+class rt_observers(C.Structure):
+    _fields_ = [("n_obs", C.c_int), ("dir", C.POINTER(C.c_double)), ("up", C.POINTER(C.c_double)),
+                ("nx", C.c_int), ("ny", C.c_int), ("fov", C.c_double * 2)]
+
+
+_lib = None
+
+
+def lib():
+    """Load librt.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1206_3710_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.rt_ctx_create.argtypes = [C.c_int, C.POINTER(vp)]
+    L.rt_ctx_destroy.argtypes = [vp]
+    L.rt_ctx_destroy.restype = None
+    L.rt_last_error.restype = C.c_char_p
+    L.rt_version.restype = C.c_char_p
+    L.rt_build_grid.argtypes = [vp, C.POINTER(rt_tree_desc), C.POINTER(vp)]
+    L.rt_grid_get_info.argtypes = [vp, C.POINTER(rt_grid_info)]
+    L.rt_grid_free.argtypes = [vp]
+    L.rt_grid_free.restype = None
+    L.rt_trace.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics), C.POINTER(rt_trace_params),
+                           vp, C.POINTER(rt_ledger), vp]
+    L.rt_peel.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics), C.POINTER(rt_trace_params),
+                          C.POINTER(rt_observers), vp, vp, C.POINTER(rt_ledger), vp]
+    L.rt_dust_temperature.argtypes = [vp, vp, vp, C.c_int, C.POINTER(rt_dust), vp, vp]
+    L.rt_dust_emission.argtypes = [vp, vp, vp, C.POINTER(rt_dust), vp, vp, vp]
+    L.rt_walk.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int, C.c_int64, vp, vp, vp, vp]
+    L.rt_philox.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
+    for name in EXPORTED:
+        if name not in ("rt_ctx_destroy", "rt_grid_free", "rt_last_error", "rt_version"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow_step_limit: bool = False) -> int:
+    if rc == RT_OK or (allow_step_limit and rc == RT_ERR_STEP_LIMIT):
+        return rc
+    msg = lib().rt_last_error()
+    raise RtError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a torch tensor (or an int / None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class _Keep:
+    def __init__(self):
+        self.items = []
+
+    def arr(self, a, dtype):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        self.items.append(a)
+        return a
+
+    def dp(self, a, dtype, ct):
+        return self.arr(a, dtype).ctypes.data_as(C.POINTER(ct))
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().rt_ctx_create(device, C.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.rt_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+class Grid:
+    """Device grid built by rt_build_grid from a level-ordered tree desc."""
+
+    def __init__(self, ctx: Context, desc):
+        keep = _Keep()
+        d = rt_tree_desc()
+        d.root = (C.c_int * 3)(*desc.root)
+        d.box = (C.c_double * 3)(*desc.box)
+        d.n_levels = len(desc.n_refined)
+        d.n_refined = keep.dp(desc.n_refined, np.int64, C.c_int64)
+        d.refine_flags = keep.dp(desc.refine_flags, np.uint8, C.c_uint8)
+        d.density = keep.dp(desc.density, np.float64, C.c_double)
+        h = C.c_void_p()
+        _check(lib().rt_build_grid(ctx.handle, C.byref(d), C.byref(h)))
+        self.handle = h
+        self.ctx = ctx
+        self.desc = desc
+        self.info = self.get_info()
+        self.n_cells = int(self.info.n_cells)
+
+    def get_info(self) -> rt_grid_info:
+        inf = rt_grid_info()
+        _check(lib().rt_grid_get_info(self.handle, C.byref(inf)))
+        return inf
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.rt_grid_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def make_optics(optics, keep: _Keep) -> rt_optics:
+    o = rt_optics()
+    o.n_lambda = int(len(optics.kappa_ext))
+    o.kappa_ext = keep.dp(optics.kappa_ext, np.float64, C.c_double)
+    o.albedo = keep.dp(optics.albedo, np.float64, C.c_double)
+    o.g_hg = keep.dp(optics.g_hg, np.float64, C.c_double)
+    return o
+
+
+def make_dust(lambda_um, kappa_abs, dnu, T_min, T_max, keep: _Keep) -> rt_dust:
+    d = rt_dust()
+    d.n_lambda = int(len(lambda_um))
+    d.lambda_um = keep.dp(lambda_um, np.float64, C.c_double)
+    d.kappa_abs = keep.dp(kappa_abs, np.float64, C.c_double)
+    d.dnu = keep.dp(dnu, np.float64, C.c_double)
+    d.T_min, d.T_max = float(T_min), float(T_max)
+    return d
+
+
+def make_sources(sources: Sequence, n_lambda: int, keep: _Keep):
+    arr = (rt_source * len(sources))()
+    for i, s in enumerate(sources):
+        S = arr[i]
+        S.kind = SOURCE_KINDS[s.kind]
+        S.pos = (C.c_double * 3)(*getattr(s, "pos", (0.0, 0.0, 0.0)))
+        S.dir = (C.c_double * 3)(*getattr(s, "dir", (0.0, 0.0, 1.0)))
+        be = getattr(s, "bin_energy", None)
+        if be is not None:
+            S.bin_energy = keep.dp(be, np.float64, C.c_double)
+        if s.kind == "dust":
+            S.T_dev = _ptr(s.T_dev)
+            d = make_dust(s.lambda_um, s.kappa_abs, s.dnu, s.T_min, s.T_max, keep)
+            keep.items.append(d)
+            S.dust = C.pointer(d)
+    return arr
+
+
+def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precision: int = 32,
+                estimator: int = RT_EST_CONTINUOUS, rr_wmin: float = 0.0, rr_p: float = 0.9, step_limit: int = 0,
+                peel_tau_max: float = 0.0, per_lambda: bool = True, packets_per_bin: int = 0, packets=None,
+                packets_total: int = 0, packet_log=None, timeout_s: float = 0.0, block_size: int = 0,
+                refill_threshold: int = 0, blocks_per_sm: int = 0) -> rt_trace_params:
+    p = rt_trace_params()
+    p.seed, p.job, p.iter = int(seed), int(job), int(iter_)
+    p.precision, p.estimator = int(precision), int(estimator)
+    p.rr_wmin, p.rr_p, p.step_limit = float(rr_wmin), float(rr_p), int(step_limit)
+    p.peel_tau_max, p.per_lambda = float(peel_tau_max), int(bool(per_lambda))
+    p.packets_per_bin, p.packets_total = int(packets_per_bin), int(packets_total)
+    if packets is not None:
+        p.packets = keep.dp(np.asarray(packets).ravel(), np.int64, C.c_int64)
+    p.packet_log_dev = _ptr(packet_log)
+    p.timeout_s = float(timeout_s)
+    p.block_size, p.refill_threshold, p.blocks_per_sm = int(block_size), int(refill_threshold), int(blocks_per_sm)
+    return p
+
+
+def make_observers(obs, keep: _Keep) -> rt_observers:
+    o = rt_observers()
+    o.n_obs = int(obs.dirs.shape[0])
+    o.dir = keep.dp(obs.dirs, np.float64, C.c_double)
+    o.up = keep.dp(obs.ups, np.float64, C.c_double)
+    o.nx, o.ny = int(obs.nx), int(obs.ny)
+    o.fov = (C.c_double * 2)(*obs.fov)
+    return o
+
+
+def rt_trace(ctx: Context, grid: Grid, sources, optics, absorbed, stream=None, **params) -> dict:
+    keep = _Keep()
+    src = make_sources(sources, len(optics.kappa_ext), keep)
+    op = make_optics(optics, keep)
+    prm = make_params(keep, **params)
+    led = rt_ledger()
+    rc = lib().rt_trace(ctx.handle, grid.handle, len(sources), src, C.byref(op), C.byref(prm), _ptr(absorbed),
+                        C.byref(led), _stream(stream))
+    _check(rc, allow_step_limit=True)
+    return led.as_dict()
+
+
+def rt_peel(ctx: Context, grid: Grid, sources, optics, observers, images, absorbed=None, stream=None,
+            **params) -> dict:
+    keep = _Keep()
+    src = make_sources(sources, len(optics.kappa_ext), keep)
+    op = make_optics(optics, keep)
+    prm = make_params(keep, **params)
+    ob = make_observers(observers, keep)
+    led = rt_ledger()
+    rc = lib().rt_peel(ctx.handle, grid.handle, len(sources), src, C.byref(op), C.byref(prm), C.byref(ob),
+                       _ptr(images), _ptr(absorbed), C.byref(led), _stream(stream))
+    _check(rc, allow_step_limit=True)
+    return led.as_dict()
+
+
+def rt_dust_temperature(ctx: Context, grid: Grid, absorbed, n_bins: int, lambda_um, kappa_abs, dnu, T_out,
+                        T_min: float = 2.7, T_max: float = 3000.0, stream=None) -> None:
+    keep = _Keep()
+    d = make_dust(lambda_um, kappa_abs, dnu, T_min, T_max, keep)
+    _check(lib().rt_dust_temperature(ctx.handle, grid.handle, _ptr(absorbed), int(n_bins), C.byref(d), _ptr(T_out),
+                                     _stream(stream)))
+
+
+def rt_dust_emission(ctx: Context, grid: Grid, T, lambda_um, kappa_abs, dnu, emission, stream=None) -> np.ndarray:
+    keep = _Keep()
+    d = make_dust(lambda_um, kappa_abs, dnu, 2.7, 3000.0, keep)
+    tot = np.zeros(len(lambda_um))
+    _check(lib().rt_dust_emission(ctx.handle, grid.handle, _ptr(T), C.byref(d), _ptr(emission),
+                                  tot.ctypes.data_as(C.c_void_p), _stream(stream)))
+    return tot
+
+
+def rt_walk(ctx: Context, grid: Grid, origins, dirs, precision: int, max_seg: int, cells, lengths, counts,
+            stream=None) -> None:
+    n = int(origins.shape[0])
+    _check(lib().rt_walk(ctx.handle, grid.handle, n, _ptr(origins), _ptr(dirs), int(precision), int(max_seg),
+                         _ptr(cells), _ptr(lengths), _ptr(counts), _stream(stream)))
+
+
+def rt_philox(ctx: Context, ctr, key, out, stream=None) -> None:
+    n = int(ctr.shape[0])
+    _check(lib().rt_philox(ctx.handle, n, _ptr(ctr), _ptr(key), _ptr(out), _stream(stream)))
+
+
+class DustSource:
+    """Thermal dust emission from device temperatures (rt_source kind dust)."""
+    kind = "dust"
+
+    def __init__(self, T_dev, lambda_um, kappa_abs, dnu, T_min=2.7, T_max=3000.0):
+        self.T_dev, self.lambda_um, self.kappa_abs, self.dnu = T_dev, lambda_um, kappa_abs, dnu
+        self.T_min, self.T_max = T_min, T_max
+        self.bin_energy = None

@@ -1,0 +1,448 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Tolerances:
+  * integer work (Philox words, grid arrays, walk cell sequences): bit-exact;
+  * FP64 mode with identical random streams: per-package outcomes equal to
+    1e-9 relative except at boundary ties (< 1e-4 of packages), absorbed
+    energy per cell and image pixels to 1e-8 relative;
+  * FP32 mode: walk lengths to 1e-5 relative; absorbed energy and pixels
+    within 3 sigma of the combined Monte Carlo error (a Gaussian allows
+    0.27% outside; the tests allow 1%), signed mean relative deviation below
+    1% over cells with >= 1e3 hits, energy balance to 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1206_3710_gb300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def rt():
+    from paper_1206_3710_gb300 import build
+    build.build()
+    from paper_1206_3710_gb300 import rt as _rt
+    return _rt
+
+
+@pytest.fixture(scope="module")
+def ctx(rt):
+    return rt.Context(0)
+
+
+DEV = "cuda:0"
+
+
+def _zeros(*shape):
+    return torch.zeros(shape, dtype=torch.float64, device=DEV)
+
+
+# ----------------------------------------------------------------- Philox
+
+def test_philox_bit_exact(rt, ctx, orc):
+    rng = np.random.default_rng(0)
+    n = 4096
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:16] = 0
+    ctr[16:32] = 0xFFFFFFFF
+    tc = torch.from_numpy(ctr.view(np.int32)).to(DEV)
+    tk = torch.from_numpy(key.view(np.int32)).to(DEV)
+    out = torch.zeros((n, 4), dtype=torch.int32, device=DEV)
+    rt.rt_philox(ctx, tc, tk, out)
+    got = out.cpu().numpy().view(np.uint32)
+    for i in range(n):
+        assert np.array_equal(got[i], orc.philox4x32(ctr[i], key[i])), i
+
+
+# ----------------------------------------------------------------- grid build
+
+def _expected_arrays(desc):
+    flags = desc.refine_flags.astype(bool)
+    n0 = int(np.prod(desc.root))
+    excl = np.concatenate([[0], np.cumsum(flags)[:-1]])
+    child = np.where(flags, n0 + 8 * excl, 0).astype(np.uint32)
+    rho = desc.density.copy()
+    off = desc.level_offsets()
+    for l in range(desc.n_levels - 2, -1, -1):
+        idx = np.arange(off[l], off[l + 1])
+        r = idx[flags[idx]]
+        rho[r] = rho[child[r][:, None] + np.arange(8)[None, :]].mean(axis=1)
+    return child, rho
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_grid_build_arrays(rt, ctx, seed):
+    desc = synth.random_refined_tree((5, 3, 4), (5.0, 3.0, 4.0), 3, 0.35, seed)
+    g = rt.Grid(ctx, desc)
+    inf = g.info
+    n = desc.n_cells
+    assert inf.n_cells == n and inf.n_leaves == int((desc.refine_flags == 0).sum()) and inf.depth == desc.n_levels - 1
+
+    child, rho = _expected_arrays(desc)
+    got_child = _copy_dev(inf.child, n, np.uint32)
+    got_level = _copy_dev(inf.level, n, np.uint8)
+    got_rho = _copy_dev(inf.density64, n, np.float64)
+    got_rho32 = _copy_dev(inf.density, n, np.float32)
+    got_node = _copy_dev(inf.node, n, np.uint32)
+    got_coord = _copy_dev(inf.coord, n, np.uint64)
+    np.testing.assert_array_equal(got_child, child)
+    np.testing.assert_array_equal(got_level, desc.cell_levels())
+    np.testing.assert_allclose(got_rho, rho, rtol=1e-15)
+    np.testing.assert_array_equal(got_rho32, rho.astype(np.float32))
+    leaf = child == 0
+    np.testing.assert_array_equal(got_node[~leaf], child[~leaf] | np.uint32(0x80000000))
+    scaled = (rho[leaf] / inf.rho_scale).astype(np.float32)
+    np.testing.assert_array_equal(got_node[leaf].view(np.float32), scaled)
+    # coordinates: cell lower corner at its level reproduces the layout
+    from tests.test_oracle_geometry import leaf_boxes
+    for cid, lo, size in leaf_boxes(desc):
+        lev = int(round(-math.log2(size)))
+        w = int(got_coord[cid])
+        xyz = np.array([w & 0x1FFFFF, (w >> 21) & 0x1FFFFF, (w >> 42) & 0x1FFFFF])
+        np.testing.assert_array_equal(xyz, (lo * 2 ** lev).round().astype(int))
+
+
+def _copy_dev(ptr, count, np_dtype):
+    """Copy `count` elements at a library-owned device address into numpy."""
+    import ctypes
+    host = np.zeros(count, dtype=np_dtype)
+    torch.cuda.synchronize()
+    rc = _cudart().cudaMemcpy(host.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(ptr),
+                              ctypes.c_size_t(host.nbytes), 2)  # cudaMemcpyDeviceToHost
+    assert rc == 0, rc
+    return host
+
+
+_CUDART = None
+
+
+def _cudart():
+    global _CUDART
+    if _CUDART is None:
+        import ctypes
+        import glob
+        import os
+        cands = []
+        for base in [os.path.dirname(torch.__file__)] + list(__import__("sys").path):
+            cands += glob.glob(os.path.join(base, "nvidia", "cuda_runtime", "lib", "libcudart.so*"))
+            cands += glob.glob(os.path.join(base, "nvidia", "cu13", "lib", "libcudart.so*"))
+        cands += glob.glob("/usr/local/cuda/lib64/libcudart.so*")
+        last = None
+        for c in cands:
+            try:
+                _CUDART = ctypes.CDLL(c)
+                break
+            except OSError as e:  # pragma: no cover
+                last = e
+        if _CUDART is None:
+            raise RuntimeError(f"libcudart not found: {last}")
+        _CUDART.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    return _CUDART
+
+
+def test_grid_rejects_invalid(rt, ctx):
+    desc = synth.random_refined_tree((2, 2, 2), (2.0, 2.0, 2.0), 2, 0.5, 3)
+    bad = synth.TreeDesc(desc.root, desc.box, desc.n_refined + np.array([1] + [0] * (desc.n_levels - 1)),
+                         desc.refine_flags, desc.density)
+    with pytest.raises(rt.RtError) as e:
+        rt.Grid(ctx, bad)
+    assert e.value.code == rt.RT_ERR_INVALID
+    dens = desc.density.copy()
+    dens[np.nonzero(desc.refine_flags == 0)[0][0]] = np.nan
+    with pytest.raises(rt.RtError):
+        rt.Grid(ctx, synth.TreeDesc(desc.root, desc.box, desc.n_refined, desc.refine_flags, dens))
+    with pytest.raises(rt.RtError):
+        rt.Grid(ctx, synth.TreeDesc(desc.root, (2.0, 2.0, 3.0), desc.n_refined, desc.refine_flags, desc.density))
+
+
+# ----------------------------------------------------------------- walks
+
+def _walk_compare(rt, ctx, orc, desc, n_rays, precision, seed, length_rtol):
+    g = rt.Grid(ctx, desc)
+    tree = orc.Tree(desc)
+    rng = np.random.default_rng(seed)
+    h0 = desc.box[0] / desc.root[0]
+    o = rng.uniform(0, 1, (n_rays, 3)) * np.array(desc.box)
+    d = rng.normal(size=(n_rays, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    if precision == 32:   # both sides walk the same f32-representable ray
+        o = (o / h0).astype(np.float32).astype(np.float64) * h0
+        o = np.minimum(o, np.array(desc.box) * (1 - 1e-7))
+        d = d.astype(np.float32).astype(np.float64)
+    max_seg = 4 * int(sum(desc.root)) * 2 ** (desc.n_levels - 1) + 16
+    to = torch.from_numpy(o).to(DEV)
+    td = torch.from_numpy(d).to(DEV)
+    cells = torch.zeros((n_rays, max_seg), dtype=torch.int64, device=DEV)
+    lens = torch.zeros((n_rays, max_seg), dtype=torch.float64, device=DEV)
+    cnt = torch.zeros(n_rays, dtype=torch.int64, device=DEV)
+    rt.rt_walk(ctx, g, to, td, precision, max_seg, cells, lens, cnt)
+    cells, lens, cnt = cells.cpu().numpy(), lens.cpu().numpy(), cnt.cpu().numpy()
+    ties = 0
+    for r in range(n_rays):
+        oc, ol, om = orc.walk(tree, o[r], d[r], max_seg)
+        # a ray whose exit points pass within the FP32 position error of
+        # another cell face may legitimately differ (tie ray)
+        margin_thr = 1e-9 if precision == 64 else 3e-6 * np.arange(1, len(om) + 1)
+        if np.any(om < margin_thr):
+            ties += 1
+            continue
+        k = int(cnt[r])
+        assert k == len(oc), (r, k, len(oc))
+        assert np.array_equal(cells[r, :k], oc), r
+        np.testing.assert_allclose(lens[r, :k], ol, rtol=length_rtol, atol=length_rtol * h0 * 1e-3)
+    return ties
+
+
+@pytest.mark.parametrize("precision,rtol", [(64, 1e-12), (32, 1e-5)])
+def test_walks_tiny_grids(rt, ctx, orc, precision, rtol):
+    for seed in range(4):
+        desc = synth.random_refined_tree((4, 3, 4), (4.0, 3.0, 4.0), 2, 0.45, seed)
+        ties = _walk_compare(rt, ctx, orc, desc, 400, precision, 50 + seed, rtol)
+        assert ties <= 400 * (0 if precision == 64 else 0.02)
+
+
+@pytest.mark.parametrize("precision,rtol", [(64, 1e-12), (32, 1e-5)])
+def test_walks_clump_grid(rt, ctx, orc, precision, rtol):
+    m = synth.tiny_clump()
+    ties = _walk_compare(rt, ctx, orc, m.tree, 2000, precision, 77, rtol)
+    assert ties <= 2000 * (1e-4 if precision == 64 else 0.05)
+
+
+def test_walks_deep_grid(rt, ctx, orc):
+    """Ten refinement levels around one point: FP32 local coordinates keep
+    bit-exact cell sequences where global FP32 coordinates could not."""
+    def rho_fn(l, x, y, z):
+        return np.ones(x.size)
+
+    def refine_fn(l, x, y, z, r):
+        s = 2 ** l
+        c = np.array([2.3, 1.7, 2.9]) * s
+        return (np.abs(x + 0.5 - c[0]) < 1.5) & (np.abs(y + 0.5 - c[1]) < 1.5) & (np.abs(z + 0.5 - c[2]) < 1.5)
+
+    desc = synth.grow_tree((4, 4, 4), (4.0,) * 3, 10, rho_fn, refine_fn)
+    assert desc.n_levels == 11
+    for precision, rtol in ((64, 1e-12), (32, 1e-5)):
+        ties = _walk_compare(rt, ctx, orc, desc, 300, precision, 9, rtol)
+        assert ties <= 300 * (0 if precision == 64 else 0.1)
+
+
+# ----------------------------------------------------------------- tracing
+
+def _run_pair(rt, ctx, orc, model, npk, precision, seed, peel=True, record=True, **kw):
+    g = rt.Grid(ctx, model.tree)
+    tree = orc.Tree(model.tree)
+    nl = model.optics.n_lambda
+    per_lambda = kw.pop("per_lambda", True)
+    bins = nl if per_lambda else 1
+    absorbed = _zeros(bins, g.n_cells)
+    n_total = npk * nl * len(model.sources)
+    log = _zeros(n_total, 10) if record else None
+    obs = model.observers if peel else None
+    if obs is not None:
+        images = _zeros(obs.n_obs, bins, obs.ny, obs.nx)
+        led = rt.rt_peel(ctx, g, model.sources, model.optics, obs, images, absorbed, seed=seed, precision=precision,
+                         packets_per_bin=npk, packet_log=log, per_lambda=per_lambda, **kw)
+    else:
+        images = None
+        led = rt.rt_trace(ctx, g, model.sources, model.optics, absorbed, seed=seed, precision=precision,
+                          packets_per_bin=npk, packet_log=log, per_lambda=per_lambda, **kw)
+    torch.cuda.synchronize()
+    ref = orc.trace(tree, model.sources, model.optics, npk, seed=seed, observers=obs, record=record,
+                    validation=True, per_lambda=per_lambda, n_threads=1, **kw)
+    out = dict(led=led, absorbed=absorbed.cpu().numpy(), images=None if images is None else images.cpu().numpy(),
+               log=None if log is None else log.cpu().numpy(), ref=ref)
+    return out
+
+
+def _per_packet(out, tol=1e-9, max_div=1e-4):
+    g, o = out["log"], out["ref"]["rec"]
+    same = (np.isclose(g[:, 0], o[:, 0], rtol=tol, atol=1e-300) & (g[:, 1] == o[:, 1]) & (g[:, 3] == o[:, 3])
+            & np.all(np.isclose(g[:, 4:7], o[:, 4:7], rtol=tol, atol=1e-6 * np.abs(o[:, 4:7]).max()), axis=1))
+    frac = 1 - same.mean()
+    assert frac <= max_div, (frac, np.nonzero(~same)[0][:5])
+    return same
+
+
+def test_fp64_clump_per_packet_and_cells(rt, ctx, orc):
+    m = synth.tiny_clump()
+    out = _run_pair(rt, ctx, orc, m, 100000, 64, seed=11)
+    _per_packet(out)
+    led, ref = out["led"], out["ref"]["ledger"]
+    assert abs(led["emitted"] - ref["emitted"]) < 1e-12
+    assert abs(led["absorbed"] + led["escaped"] - led["emitted"]) <= 1e-12
+    assert led["n_cross"] == ref["n_cross"] and led["n_scatter"] == ref["n_scatter"]
+    assert led["n_peel_cross"] == ref["n_peel_cross"]
+    np.testing.assert_allclose(out["absorbed"], out["ref"]["absorbed"], rtol=1e-8, atol=1e-300)
+    np.testing.assert_allclose(out["images"], out["ref"]["images"], rtol=1e-8, atol=1e-300)
+
+
+def _statistical(gpu, ref, sumsq, hits, npk_total):
+    var = np.maximum(sumsq - ref * ref / npk_total, 0)
+    sig = np.sqrt(2 * var)          # same-variance estimate for both sides
+    ok = sig > 0
+    z = (gpu[ok] - ref[ok]) / sig[ok]
+    assert np.mean(np.abs(z) > 3) < 0.01, np.mean(np.abs(z) > 3)
+    well = hits >= 1000
+    if well.sum():
+        assert abs((gpu[well] / ref[well] - 1).mean()) < 0.01
+
+
+def test_fp32_clump_statistical(rt, ctx, orc):
+    m = synth.tiny_clump()
+    npk = 100000
+    out = _run_pair(rt, ctx, orc, m, npk, 32, seed=12)
+    led = out["led"]
+    assert abs(led["absorbed"] + led["escaped"] - led["emitted"]) <= 1e-5 * led["emitted"]
+    ref = out["ref"]
+    _statistical(out["absorbed"][0], ref["absorbed"][0], ref["sumsq"][0], ref["hits"][0], npk)
+    # peel-off image totals agree within MC error of the image sum
+    gi, oi = out["images"].sum(), ref["images"].sum()
+    assert abs(gi / oi - 1) < 0.02
+    # same streams: most packages follow the same path in f32
+    g, o = out["log"], ref["rec"]
+    assert np.mean(g[:, 1] == o[:, 1]) > 0.95
+
+
+def _small_cloud(n_root=32, levels=2, n_lambda=6, seed=5):
+    m = synth.cloud(n_root=n_root, levels=levels, seed=seed, n_lambda=n_lambda, packets_per_bin=0, n_pix=32)
+    return m
+
+
+def test_fp64_cloud_external_peel(rt, ctx, orc):
+    m = _small_cloud()
+    out = _run_pair(rt, ctx, orc, m, 4000, 64, seed=21)
+    _per_packet(out)
+    np.testing.assert_allclose(out["absorbed"], out["ref"]["absorbed"], rtol=1e-8, atol=1e-300)
+    np.testing.assert_allclose(out["images"], out["ref"]["images"], rtol=1e-8, atol=1e-300)
+    assert out["led"]["n_peel_cross"] == out["ref"]["ledger"]["n_peel_cross"]
+
+
+def test_fp64_roulette_and_summed_bins(rt, ctx, orc):
+    m = _small_cloud(n_root=16, levels=2, n_lambda=4)
+    out = _run_pair(rt, ctx, orc, m, 3000, 64, seed=22, rr_wmin=0.3, rr_p=0.6, per_lambda=False)
+    _per_packet(out)
+    led = out["led"]
+    assert led["rr_loss"] > 0
+    lhs = led["emitted"] + led["rr_gain"]
+    rhs = led["absorbed"] + led["escaped"] + led["rr_loss"]
+    assert abs(lhs - rhs) <= 1e-12 * lhs
+    np.testing.assert_allclose(out["absorbed"], out["ref"]["absorbed"], rtol=1e-8, atol=1e-300)
+
+
+def test_fp64_analog(rt, ctx, orc):
+    m = synth.tiny_clump()
+    out = _run_pair(rt, ctx, orc, m, 20000, 64, seed=23, estimator=1)
+    _per_packet(out)
+    np.testing.assert_allclose(out["absorbed"], out["ref"]["absorbed"], rtol=1e-8, atol=1e-300)
+
+
+def test_beam_and_outside_point(rt, ctx, orc):
+    desc = synth.uniform_tree((4, 4, 4), (4.0,) * 3, 1.0)
+    opt = synth.Optics(np.array([0.55]), np.array([0.3]), np.array([0.0]), np.array([0.0]), np.ones(1))
+
+    class Beam:
+        kind = "beam"
+        pos = (0.0, 1.5, 2.5)
+        dir = (1.0, 0.0, 0.0)
+        bin_energy = np.array([1.0])
+
+    m = synth.Model("beam", desc, opt, [Beam()], None, 100, 1)
+    out = _run_pair(rt, ctx, orc, m, 100, 64, seed=3, peel=False)
+    np.testing.assert_allclose(out["log"][:, 0], 0.01 * math.exp(-1.2), rtol=1e-12)
+    far = synth.Source("point", bin_energy=np.array([1.0]), pos=(10.0, 1.0, 1.0))
+    m2 = synth.Model("far", desc, opt, [far], None, 50, 1)
+    out = _run_pair(rt, ctx, orc, m2, 50, 32, seed=3, peel=False)
+    assert out["led"]["escaped"] == pytest.approx(1.0) and out["led"]["n_cross"] == 0
+
+
+def test_zero_packets_and_empty_medium(rt, ctx, orc):
+    desc = synth.uniform_tree((3, 3, 3), (3.0,) * 3, 0.0)
+    opt = synth.Optics(np.array([0.55]), np.array([1.0]), np.array([0.5]), np.array([0.3]), np.ones(1))
+    src = synth.Source("point", bin_energy=np.array([1.0]), pos=(1.5, 1.5, 1.5))
+    g = rt.Grid(ctx, desc)
+    ab = _zeros(1, g.n_cells)
+    led = rt.rt_trace(ctx, g, [src], opt, ab, seed=1, packets=np.array([0]))
+    assert led["n_packets"] == 0
+    led = rt.rt_trace(ctx, g, [src], opt, ab, seed=1, packets_per_bin=1000)
+    assert led["escaped"] == pytest.approx(1.0, rel=1e-6) and led["absorbed"] == 0 and led["n_scatter"] == 0
+
+
+def test_step_limit_reports_status(rt, ctx):
+    m = synth.tiny_clump()
+    g = rt.Grid(ctx, m.tree)
+    ab = _zeros(1, g.n_cells)
+    led = rt.rt_trace(ctx, g, m.sources, m.optics, ab, seed=1, packets_per_bin=1000, step_limit=3)
+    assert led["status"] == rt.RT_ERR_STEP_LIMIT and led["n_killed"] > 0
+    assert abs(led["absorbed"] + led["escaped"] + led["killed"] - led["emitted"]) < 1e-5
+
+
+def test_invalid_trace_arguments(rt, ctx):
+    m = synth.tiny_clump()
+    g = rt.Grid(ctx, m.tree)
+    ab = _zeros(1, g.n_cells)
+    bad = synth.Optics(m.optics.lambda_um, m.optics.kappa_ext, np.array([1.5]), m.optics.g_hg, m.optics.dnu)
+    with pytest.raises(rt.RtError):
+        rt.rt_trace(ctx, g, m.sources, bad, ab, seed=1, packets_per_bin=10)
+    bad = synth.Optics(m.optics.lambda_um, m.optics.kappa_ext, m.optics.albedo, np.array([1.0]), m.optics.dnu)
+    with pytest.raises(rt.RtError):
+        rt.rt_trace(ctx, g, m.sources, bad, ab, seed=1, packets_per_bin=10)
+    with pytest.raises(rt.RtError):
+        rt.rt_trace(ctx, g, m.sources, m.optics, ab, seed=1, packets_per_bin=10, precision=16)
+    with pytest.raises(rt.RtError):
+        rt.rt_trace(ctx, g, m.sources, m.optics, ab, seed=1)
+
+
+# ----------------------------------------------------------------- dust
+
+def test_dust_temperature_parity(rt, ctx, orc):
+    desc = synth.random_refined_tree((4, 4, 4), (4e16,) * 3, 2, 0.3, 8,
+                                     rho_fn=lambda l, x, y, z: np.random.default_rng(l + 1).uniform(1e-22, 1e-19, x.size))
+    g = rt.Grid(ctx, desc)
+    tree = orc.Tree(desc)
+    lam = synth.log_lambda_grid(30)
+    kabs = 300.0 * (lam / 0.55) ** -1.8
+    dnu = synth.bin_dnu(lam)
+    rng = np.random.default_rng(4)
+    A = rng.uniform(0, 1, (3, desc.n_cells)) * 10.0 ** rng.uniform(20, 34, (3, desc.n_cells))
+    A[:, :5] = 0.0
+    T = _zeros(desc.n_cells)
+    rt.rt_dust_temperature(ctx, g, torch.from_numpy(A).to(DEV), 3, lam, kabs, dnu, T)
+    To = orc.dust_temperature(tree, A.sum(axis=0), lam, kabs, dnu)
+    np.testing.assert_allclose(T.cpu().numpy(), To, rtol=1e-10)
+    em = _zeros(30, desc.n_cells)
+    tot = rt.rt_dust_emission(ctx, g, T, lam, kabs, dnu, em)
+    eo = orc.dust_emission(tree, To, lam, kabs, dnu)
+    np.testing.assert_allclose(em.cpu().numpy(), eo, rtol=1e-9, atol=1e-300)
+    np.testing.assert_allclose(tot, eo.sum(axis=1), rtol=1e-12)
+
+
+def test_fp64_dust_source_per_packet(rt, ctx, orc):
+    L = 20 * synth.AU_CM
+    desc = synth.random_refined_tree((6, 6, 6), (L,) * 3, 2, 0.3, 4,
+                                     rho_fn=lambda l, x, y, z: np.random.default_rng(l + 5).uniform(1e-19, 1e-18, x.size))
+    lam = synth.log_lambda_grid(8)
+    optics = synth.powerlaw_dust(lam, 3.0 / (1e-18 * L), 1.0)
+    kabs = (1 - optics.albedo) * optics.kappa_ext
+    g = rt.Grid(ctx, desc)
+    tree = orc.Tree(desc)
+    rng = np.random.default_rng(2)
+    Tn = rng.uniform(20, 800, desc.n_cells)
+    Tn[desc.refine_flags == 1] = 0
+    Td = torch.from_numpy(Tn).to(DEV)
+    src = rt.DustSource(Td, lam, kabs, optics.dnu)
+    npk = 2000
+    ab = _zeros(len(lam), g.n_cells)
+    log = _zeros(npk * len(lam), 10)
+    led = rt.rt_trace(ctx, g, [src], optics, ab, seed=5, precision=64, packets_per_bin=npk, packet_log=log)
+    em = orc.dust_emission(tree, Tn, lam, kabs, optics.dnu)
+    ref = orc.trace(tree, [orc._DustSource(em)], optics, npk, seed=5, record=True)
+    assert led["emitted"] == pytest.approx(ref["ledger"]["emitted"], rel=1e-10)
+    out = dict(log=log.cpu().numpy(), ref=ref)
+    _per_packet(out, max_div=2e-3)   # CDF prefix sums differ in summation order
+    np.testing.assert_allclose(ab.cpu().numpy().sum(), ref["absorbed"].sum(), rtol=1e-6)
