@@ -571,7 +571,7 @@ static void trace_one(trace_worker* w, int64_t p) {
       if (ksca > 0 && ksca * s >= tau) {
         /* scattering inside this cell */
         double ts = tau / ksca;
-        double dep = W * (1.0 - exp(-kabs * ts));
+        double dep = -W * expm1(-kabs * ts);   /* W (1 - e^-dtau) without cancellation */
         deposit(w, slot, p, dep);
         w->led.absorbed += dep;
         W *= exp(-kabs * ts);
@@ -600,7 +600,7 @@ static void trace_one(trace_worker* w, int64_t p) {
         tau = -log(uni(&rs));
       } else {
         tau -= ksca * s;
-        double dep = W * (1.0 - exp(-kabs * s));
+        double dep = -W * expm1(-kabs * s);
         deposit(w, slot, p, dep);
         w->led.absorbed += dep;
         W *= exp(-kabs * s);
