@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-packets-per-bin", type=int, default=0, help="oracle sample size (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rr-wmin", type=float, default=1e-4, help="Russian roulette below this fraction of W0")
+    ap.add_argument("--rr-p", type=float, default=0.9)
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -158,7 +160,8 @@ def cpu_baseline(a, m, packets_per_bin=None, want_seconds=15.0):
     # grow the sample until it takes a few seconds, capped at want_seconds total
     while True:
         t1 = time.perf_counter()
-        r = oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, observers=m.observers, n_threads=cores)
+        r = oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, observers=m.observers, n_threads=cores,
+                         rr_wmin=a.rr_wmin, rr_p=a.rr_p)
         dt = time.perf_counter() - t1
         if packets_per_bin or dt > 0.25 * want_seconds or ppb >= a.packets_per_bin:
             break
@@ -182,11 +185,13 @@ def run_reference(a):
     cores = os.cpu_count() or 1
     ppb = a.cpu_packets_per_bin or max(10, min(200, a.packets_per_bin))
     for _ in range(a.warmup):
-        oracle.trace(tree, m.sources, m.optics, max(1, ppb // 10), seed=1002, observers=m.observers, n_threads=cores)
+        oracle.trace(tree, m.sources, m.optics, max(1, ppb // 10), seed=1002, observers=m.observers, n_threads=cores,
+                     rr_wmin=a.rr_wmin, rr_p=a.rr_p)
     tot_cross, tot_pk, t = 0.0, 0.0, 0.0
     for s in range(a.steps):
         t0 = time.perf_counter()
-        r = oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, iter_=s, observers=m.observers, n_threads=cores)
+        r = oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, iter_=s, observers=m.observers, n_threads=cores,
+                         rr_wmin=a.rr_wmin, rr_p=a.rr_p)
         t += time.perf_counter() - t0
         tot_cross += r["ledger"]["n_cross"] + r["ledger"]["n_peel_cross"]
         tot_pk += r["ledger"]["n_packets"]
@@ -233,6 +238,7 @@ def main():
     lam, kabs, dnu = dust_arrays(m)
     stream = torch.cuda.current_stream(dev)
     kw = dict(seed=1002, job=rank, precision=a.precision, packets_per_bin=a.packets_per_bin,
+              rr_wmin=a.rr_wmin, rr_p=a.rr_p,
               block_size=a.block_size, refill_threshold=a.refill, blocks_per_sm=a.blocks_per_sm)
 
     def step():

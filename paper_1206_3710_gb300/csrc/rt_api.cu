@@ -420,7 +420,7 @@ static void cross3(const double* a, const double* b, double* o) {
 // build the device job table for a list of jobs; returns total packages
 static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev* led_dev, cudaStream_t s,
                         Arena& A, std::vector<size_t>& job_off, size_t& items_off, int& n_items, long long& total,
-                        bool& any_peel, int& precision) {
+                        bool& any_peel, int& precision, int& estimator) {
   // per job: validate, resolve packages per (source, bin), dust CDFs
   struct Pending {
     size_t ptr_field;  // offset of a pointer field to patch
@@ -448,6 +448,8 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     precision = p->precision;
     if (p->estimator != RT_EST_CONTINUOUS && p->estimator != RT_EST_ANALOG)
       return fail(RT_ERR_INVALID, "job %d: unknown estimator", j);
+    if (j > 0 && p->estimator != estimator) return fail(RT_ERR_INVALID, "jobs of one launch must share the estimator");
+    estimator = p->estimator;
     if (p->rr_wmin > 0.0 && !(p->rr_p >= 0.0 && p->rr_p < 1.0)) return fail(RT_ERR_INVALID, "job %d: rr_p must be in [0,1)", j);
     if (p->estimator == RT_EST_ANALOG && p->rr_wmin > 0.0)
       return fail(RT_ERR_INVALID, "job %d: roulette applies to the continuous-absorption estimator only", j);
@@ -598,6 +600,14 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
         }
         O.inv_pix[0] = T.obs->nx * G->h0 / T.obs->fov[0];
         O.inv_pix[1] = T.obs->ny * G->h0 / T.obs->fov[1];
+        for (int a = 0; a < 3; ++a) {
+          O.kf[a] = (float)O.k[a];
+          O.exf[a] = (float)O.ex[a];
+          O.eyf[a] = (float)O.ey[a];
+          O.cf[a] = (float)O.c[a];
+        }
+        O.inv_pixf[0] = (float)O.inv_pix[0];
+        O.inv_pixf[1] = (float)O.inv_pix[1];
         O.nx = T.obs->nx;
         O.ny = T.obs->ny;
       }
@@ -676,10 +686,10 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   Arena A;
   std::vector<size_t> job_off;
   size_t items_off = 0;
-  int n_items = 0, precision = 32;
+  int n_items = 0, precision = 32, estimator = RT_EST_CONTINUOUS;
   long long total = 0;
   bool peel = false;
-  rc = build_tables(c, n_jobs, jobs, led, s, A, job_off, items_off, n_items, total, peel, precision);
+  rc = build_tables(c, n_jobs, jobs, led, s, A, job_off, items_off, n_items, total, peel, precision, estimator);
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(c->table.p);
   CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + sizeof(unsigned long long), s));
@@ -696,7 +706,7 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   if (cfg.refill > 32) cfg.refill = 32;
   CK(cudaEventRecord(c->ev_a, s));
   if (total > 0 && n_items > 0)
-    CK(launch_trace(precision, peel, reinterpret_cast<const JobDev*>(base + job_off[0]),
+    CK(launch_trace(precision, peel, estimator, reinterpret_cast<const JobDev*>(base + job_off[0]),
                     reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, s));
   CK(cudaEventRecord(c->ev_b, s));
   std::vector<LedgerDev> hl(n_jobs);

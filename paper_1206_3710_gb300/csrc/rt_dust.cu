@@ -20,15 +20,15 @@ namespace rtk {
 // B_nu(T) and its temperature derivative
 __device__ __forceinline__ void planck_and_deriv(double nu, double T, double* B, double* dB) {
   const double x = H_CGS * nu / (K_CGS * T);
-  if (x > 700.0) {
+  const double em1 = expm1(x);
+  if (!(em1 < HUGE_VAL)) {  // Wien tail below the double range
     *B = 0.0;
     *dB = 0.0;
     return;
   }
-  const double em1 = expm1(x);
   const double b = 2.0 * H_CGS * nu * nu * nu / (C_CGS * C_CGS) / em1;
   *B = b;
-  *dB = b * x * (em1 + 1.0) / em1 / T;
+  *dB = b * x * (1.0 + 1.0 / em1) / T;
 }
 
 __device__ __forceinline__ double emission_per_mass(const double* lam, const double* kabs, const double* dnu, int nl,

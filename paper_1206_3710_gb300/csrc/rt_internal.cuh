@@ -35,6 +35,7 @@ struct ObsDev {
   double k[3], ex[3], ey[3];
   double c[3];        // box centre
   double inv_pix[2];  // 1 / pixel size
+  float kf[3], exf[3], eyf[3], cf[3], inv_pixf[2];  // the same in f32
   int nx, ny;
 };
 
@@ -100,9 +101,9 @@ struct LaunchCfg {
 };
 
 // launch the persistent tracer over n_items items of total packages
-cudaError_t launch_trace(int precision, bool peel, const JobDev* jobs_dev, const ItemDev* items_dev,
-                         int n_items, unsigned long long* counter_dev, long long total,
-                         const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_trace(int precision, bool peel, int estimator, const JobDev* jobs_dev,
+                         const ItemDev* items_dev, int n_items, unsigned long long* counter_dev,
+                         long long total, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm);
 
 cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, const double* origins,

@@ -17,7 +17,11 @@
 //  * geometry runs in leaf-local coordinates (cell = 1 unit, Sect. 2.3) plus
 //    integer lattice coordinates at the leaf's level, so FP32 keeps its
 //    precision at deep levels; a face crossing moves to the sibling in the
-//    same octet with one load, otherwise re-descends from the root;
+//    same octet (or the root-level neighbour) with one load, otherwise
+//    re-descends from the root;
+//  * every pass of the loop loads exactly one node word per lane: a refined
+//    node advances the descent by one level, a leaf gets one segment, so a
+//    lane re-descending several levels never holds up the rest of its warp;
 //  * one 32-bit node word per visit (density or child index), absorbed
 //    energy by FP64 atomics (RED) into [bin][cell].
 #include <math_constants.h>
@@ -38,15 +42,28 @@ struct Num<float> {
   }
   static __device__ __forceinline__ float log_(float x) { return logf(x); }
   static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
+  // 1 - exp(-x) for x >= 0: Taylor series through x^6 below 1/8 (relative
+  // remainder < 1e-9), 1 - expf(-x) above (where it is >= 0.117)
+  // q = 1 - exp(-x) and e = exp(-x) for x >= 0, both without cancellation:
+  // Taylor series of q through x^6 below 1/8 (relative remainder < 1e-9)
+  // with e = 1 - q; expf above, where q = 1 - e >= 0.117
+  static __device__ __forceinline__ void absorb_pair(float x, float& q, float& e) {
+    const float p = x * (1.0f - x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x * (1.0f / 720.0f))))));
+    const float ex = expf(-x);
+    const bool small = x < 0.125f;
+    q = small ? p : 1.0f - ex;
+    e = small ? 1.0f - p : ex;
+  }
   static __device__ __forceinline__ float exp_(float x) { return expf(x); }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
   static __device__ __forceinline__ float ldexp_(float x, int e) { return ldexpf(x, e); }
   static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
   static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
-  static __device__ __forceinline__ float leaf_rho(const JobDev& J, uint32_t w, uint32_t) {
-    return __uint_as_float(w);
-  }
+  // 2^-l for 0 <= l <= 126, exact
+  static __device__ __forceinline__ float pow2m(int l) { return __int_as_float((127 - l) << 23); }
+  static __device__ __forceinline__ float leaf_rho(uint32_t w, double) { return __uint_as_float(w); }
+  static __device__ __forceinline__ double load_rho64(const double*, uint32_t) { return 0.0; }
   static __device__ __forceinline__ float kext(const BinDev& b) { return b.kext_f; }
   static __device__ __forceinline__ float alb(const BinDev& b) { return b.albedo; }
   static __device__ __forceinline__ float gg(const BinDev& b) { return b.g; }
@@ -57,22 +74,32 @@ struct Num<double> {
   static __device__ __forceinline__ double uni(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
   static __device__ __forceinline__ double log_(double x) { return log(x); }
   static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
+  static __device__ __forceinline__ void absorb_pair(double x, double& q, double& e) {
+    if (x < 0.125) {
+      q = -expm1(-x);
+      e = 1.0 - q;
+    } else {
+      e = exp(-x);
+      q = 1.0 - e;
+    }
+  }
   static __device__ __forceinline__ double exp_(double x) { return exp(x); }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double floor_(double x) { return floor(x); }
   static __device__ __forceinline__ double ldexp_(double x, int e) { return ldexp(x, e); }
   static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
   static __device__ __forceinline__ double inf() { return CUDART_INF; }
-  static __device__ __forceinline__ double leaf_rho(const JobDev& J, uint32_t, uint32_t idx) {
-    return __ldg(J.rho64 + idx);
-  }
+  static __device__ __forceinline__ double pow2m(int l) { return __longlong_as_double((long long)(1023 - l) << 52); }
+  static __device__ __forceinline__ double leaf_rho(uint32_t, double r64) { return r64; }
+  static __device__ __forceinline__ double load_rho64(const double* p, uint32_t i) { return __ldg(p + i); }
   static __device__ __forceinline__ double kext(const BinDev& b) { return b.kext_d; }
   static __device__ __forceinline__ double alb(const BinDev& b) { return b.albedo_d; }
   static __device__ __forceinline__ double gg(const BinDev& b) { return b.g_d; }
 };
 
-// position of a package: leaf at level `lev` with lattice coordinates c and
-// in-leaf offsets f in [0,1]; idx is the leaf's array index
+
+// Position of a package: a leaf at level `lev` with lattice coordinates c at
+// that level and in-leaf offsets f in [0,1] (cell = 1 unit, Sect. 2.3).
 template <typename R>
 struct Geo {
   uint32_t cx, cy, cz;
@@ -82,19 +109,38 @@ struct Geo {
   R rho;
 };
 
-__device__ __forceinline__ uint32_t load_node(const uint32_t* node, uint32_t i) { return __ldg(node + i); }
+// The next node to visit: `pending` is an array index whose node sits at
+// level k on the path to the package's leaf.  Every loop iteration loads
+// exactly one node word; a refined node advances one level, a leaf ends the
+// search.  Lanes therefore never wait on another lane's multi-level descent.
+struct Cursor {
+  uint32_t pending;
+  int k;
+};
 
-// point on a face belongs to the child the direction points into
+// grid geometry needed on the hot path, held in registers
+struct GridRegs {
+  const uint32_t* node;
+  const double* rho64;
+  uint32_t rx, ry, rz;
+};
+
+// a point on a face belongs to the child the direction points into
 template <typename R>
 __device__ __forceinline__ uint32_t upper_half(R f, R d) {
   return (f > R(0.5)) | ((f == R(0.5)) & (d >= R(0)));
 }
 
-// descend from a refined node word w at the current (c, lev) using offsets
+// one level of descent below a refined node word w at cursor level k
 template <typename R>
-__device__ __forceinline__ void descend(const JobDev& J, Geo<R>& g, uint32_t w, R dx, R dy, R dz) {
-  while (w & RT_INTERIOR) {
-    const uint32_t bx = upper_half(g.fx, dx), by = upper_half(g.fy, dy), bz = upper_half(g.fz, dz);
+__device__ __forceinline__ void descend_step(Geo<R>& g, Cursor& cur, uint32_t w, R dx, R dy, R dz) {
+  // above the lattice level: follow the lattice bits; at or below it: split
+  // the leaf-local offsets
+  const bool by_lattice = cur.k < g.lev;
+  const int sh = by_lattice ? g.lev - cur.k - 1 : 0;
+  const uint32_t ol = ((g.cx >> sh) & 1u) | (((g.cy >> sh) & 1u) << 1) | (((g.cz >> sh) & 1u) << 2);
+  const uint32_t bx = upper_half(g.fx, dx), by = upper_half(g.fy, dy), bz = upper_half(g.fz, dz);
+  if (!by_lattice) {
     g.fx = R(2) * g.fx - R(bx);
     g.fy = R(2) * g.fy - R(by);
     g.fz = R(2) * g.fz - R(bz);
@@ -102,54 +148,38 @@ __device__ __forceinline__ void descend(const JobDev& J, Geo<R>& g, uint32_t w, 
     g.cy = 2u * g.cy + by;
     g.cz = 2u * g.cz + bz;
     g.lev += 1;
-    g.idx = (w & RT_CHILD_MASK) + (bx | (by << 1) | (bz << 2));
-    w = load_node(J.node, g.idx);
   }
-  g.rho = Num<R>::leaf_rho(J, w, g.idx);
+  const uint32_t o = by_lattice ? ol : (bx | (by << 1) | (bz << 2));
+  cur.pending = (w & RT_CHILD_MASK) + o;
+  cur.k += 1;
 }
 
-// find the leaf holding (c, f) at level lev by descending from the root;
-// returns false if the point is outside the root grid
+// the node at the cursor is a leaf: if it is coarser than the lattice level,
+// re-express the offsets in its units
 template <typename R>
-__device__ __forceinline__ bool locate_root(const JobDev& J, Geo<R>& g, R dx, R dy, R dz) {
-  const uint32_t rx = g.cx >> g.lev, ry = g.cy >> g.lev, rz = g.cz >> g.lev;
-  if (rx >= J.root[0] || ry >= J.root[1] || rz >= J.root[2]) return false;
-  uint32_t idx = rx + J.root[0] * (ry + J.root[1] * rz);
-  uint32_t w = load_node(J.node, idx);
-  int l = 0;
-  while (l < g.lev && (w & RT_INTERIOR)) {
-    ++l;
-    const int sh = g.lev - l;
-    const uint32_t o = ((g.cx >> sh) & 1u) | (((g.cy >> sh) & 1u) << 1) | (((g.cz >> sh) & 1u) << 2);
-    idx = (w & RT_CHILD_MASK) + o;
-    w = load_node(J.node, idx);
-  }
-  g.idx = idx;
-  if (l < g.lev) {  // the leaf is coarser than the lattice level: re-express offsets
-    const int k = g.lev - l;
-    const uint32_t m = (1u << k) - 1u;
-    const R s = Num<R>::ldexp_(R(1), -k);
+__device__ __forceinline__ void settle_leaf(Geo<R>& g, const Cursor& cur, uint32_t w, double r64) {
+  if (cur.k < g.lev) {
+    const int kk = g.lev - cur.k;
+    const uint32_t m = (1u << kk) - 1u;
+    const R s = Num<R>::pow2m(kk);
     g.fx = (R(g.cx & m) + g.fx) * s;
     g.fy = (R(g.cy & m) + g.fy) * s;
     g.fz = (R(g.cz & m) + g.fz) * s;
-    g.cx >>= k;
-    g.cy >>= k;
-    g.cz >>= k;
-    g.lev = l;
-    g.rho = Num<R>::leaf_rho(J, w, idx);
-  } else {
-    descend(J, g, w, dx, dy, dz);
+    g.cx >>= kk;
+    g.cy >>= kk;
+    g.cz >>= kk;
+    g.lev = cur.k;
   }
-  return true;
+  g.idx = cur.pending;
+  g.rho = Num<R>::leaf_rho(w, r64);
 }
 
-// place a point given in root-cell units (root level), faces belong to the
-// cell the direction points into
+// start at a point given in root-cell units (faces belong to the cell the
+// direction points into); false if outside the root grid
 template <typename R>
-__device__ __forceinline__ bool place_root_units(const JobDev& J, Geo<R>& g, R px, R py, R pz, R dx, R dy,
-                                                 R dz) {
-  if (!(px >= R(0) && py >= R(0) && pz >= R(0) && px <= (R)J.root[0] && py <= (R)J.root[1] &&
-        pz <= (R)J.root[2]))
+__device__ __forceinline__ bool place_root(const GridRegs& G, Geo<R>& g, Cursor& cur, R px, R py, R pz, R dx,
+                                           R dy, R dz) {
+  if (!(px >= R(0) && py >= R(0) && pz >= R(0) && px <= (R)G.rx && py <= (R)G.ry && pz <= (R)G.rz))
     return false;
   R fl = Num<R>::floor_(px);
   g.cx = (uint32_t)fl;
@@ -164,7 +194,10 @@ __device__ __forceinline__ bool place_root_units(const JobDev& J, Geo<R>& g, R p
   g.fz = pz - fl;
   if (g.fz == R(0) && dz < R(0)) { g.cz -= 1u; g.fz = R(1); }
   g.lev = 0;
-  return locate_root(J, g, dx, dy, dz);
+  if (g.cx >= G.rx || g.cy >= G.ry || g.cz >= G.rz) return false;
+  cur.pending = g.cx + G.rx * (g.cy + G.ry * g.cz);
+  cur.k = 0;
+  return true;
 }
 
 // exit distance (leaf-local units) and axis; ties -> lowest axis.  Axes with
@@ -188,51 +221,33 @@ __device__ __forceinline__ R clamp01(R v) {
   return v < R(0) ? R(0) : (v > R(1) ? R(1) : v);
 }
 
-// Cross the exit face on axis a and find the next leaf.  Returns false when
-// the package leaves the root grid.
+// Cross the exit face on axis a; aim the cursor at the neighbour (the
+// sibling in the same octet or the root-level neighbour with one load,
+// otherwise a descent from the root).  False when the package leaves the
+// root grid.  Written with selects only: lanes crossing different axes do
+// not diverge.
 template <typename R>
-__device__ __forceinline__ bool cross_face(const JobDev& J, Geo<R>& g, int a, R t, R dx, R dy, R dz) {
-  uint32_t cold, cnew;
-  bool plus;
-  if (a == 0) {
-    plus = dx > R(0);
-    g.fy = clamp01(g.fy + t * dy);
-    g.fz = clamp01(g.fz + t * dz);
-    cold = g.cx;
-    g.cx = plus ? g.cx + 1u : g.cx - 1u;
-    g.fx = plus ? R(0) : R(1);
-    cnew = g.cx;
-  } else if (a == 1) {
-    plus = dy > R(0);
-    g.fx = clamp01(g.fx + t * dx);
-    g.fz = clamp01(g.fz + t * dz);
-    cold = g.cy;
-    g.cy = plus ? g.cy + 1u : g.cy - 1u;
-    g.fy = plus ? R(0) : R(1);
-    cnew = g.cy;
-  } else {
-    plus = dz > R(0);
-    g.fx = clamp01(g.fx + t * dx);
-    g.fy = clamp01(g.fy + t * dy);
-    cold = g.cz;
-    g.cz = plus ? g.cz + 1u : g.cz - 1u;
-    g.fz = plus ? R(0) : R(1);
-    cnew = g.cz;
-  }
-  uint32_t step;
-  if (g.lev == 0) {
-    if (cnew >= J.root[a]) return false;
-    step = (a == 0) ? 1u : (a == 1 ? J.root[0] : J.root[0] * J.root[1]);
-  } else if ((cold >> 1) == (cnew >> 1)) {
-    step = 1u << a;  // sibling in the same octet
-  } else {
-    return locate_root(J, g, dx, dy, dz);
-  }
-  g.idx = plus ? g.idx + step : g.idx - step;
-  const uint32_t w = load_node(J.node, g.idx);
-  if (w & RT_INTERIOR) descend(J, g, w, dx, dy, dz);
-  else g.rho = Num<R>::leaf_rho(J, w, g.idx);
-  return true;
+__device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, R t, R dx, R dy, R dz) {
+  const bool a0 = a == 0, a1 = a == 1, a2 = a == 2;
+  const bool px = dx > R(0), py = dy > R(0), pz = dz > R(0);
+  const R nfx = clamp01(g.fx + t * dx), nfy = clamp01(g.fy + t * dy), nfz = clamp01(g.fz + t * dz);
+  g.fx = a0 ? (px ? R(0) : R(1)) : nfx;
+  g.fy = a1 ? (py ? R(0) : R(1)) : nfy;
+  g.fz = a2 ? (pz ? R(0) : R(1)) : nfz;
+  const bool plus = a0 ? px : (a1 ? py : pz);
+  const uint32_t cold = a0 ? g.cx : (a1 ? g.cy : g.cz);
+  const uint32_t cnew = plus ? cold + 1u : cold - 1u;
+  g.cx = a0 ? cnew : g.cx;
+  g.cy = a1 ? cnew : g.cy;
+  g.cz = a2 ? cnew : g.cz;
+  const bool root_level = g.lev == 0;
+  const bool near = root_level || ((cold >> 1) == (cnew >> 1));  // root-level neighbour or sibling
+  const uint32_t step = root_level ? (a0 ? 1u : (a1 ? G.rx : G.rx * G.ry)) : (1u << a);
+  const uint32_t rx = g.cx >> g.lev, ry = g.cy >> g.lev, rz = g.cz >> g.lev;
+  const bool inside = rx < G.rx && ry < G.ry && rz < G.rz;
+  cur.pending = near ? (plus ? g.idx + step : g.idx - step) : rx + G.rx * (ry + G.ry * rz);
+  cur.k = near ? g.lev : 0;
+  return inside;
 }
 
 template <typename R>
@@ -293,29 +308,103 @@ __device__ __forceinline__ R inv_abs(R d) {
   return R(1) / fabs(d);
 }
 
-struct LaneLedger {
-  double emitted, absorbed, escaped, rr_gain, rr_loss, killed, peeled;
-  unsigned long long n_packets, n_cross, n_scatter, n_peel_cross, n_killed, n_peel_out;
-  __device__ void zero() {
-    emitted = absorbed = escaped = rr_gain = rr_loss = killed = peeled = 0.0;
-    n_packets = n_cross = n_scatter = n_peel_cross = n_killed = n_peel_out = 0ull;
+// ------------------------------------------------------------------------
+// shared-memory state of the tracer
+// ------------------------------------------------------------------------
+enum { L_EMIT = 0, L_ABS, L_ESC, L_RRG, L_RRL, L_KILL, L_PEEL, L_ND };
+enum { U_PK = 0, U_CROSS, U_SCAT, U_PCROSS, U_KILL, U_POUT, U_NU };
+
+// Energy ledger per warp, updated with shared-memory atomics at package
+// events (a few per package).  `tag` is the job it belongs to; a lane
+// working on another job (at job boundaries of a batched launch) books
+// directly to global memory.  Kept per warp rather than per thread: shared
+// memory taken here is L1 cache lost to the node loads.
+struct WarpLedger {
+  double d[L_ND][8];
+  unsigned long long u[U_NU][8];
+  int tag[8];
+};
+
+// Cold per-lane state: touched at emission, scattering and peel-off
+// events only, so it lives in shared memory instead of registers.
+template <typename R>
+struct ColdState {
+  uint32_t k0[256], k1[256], c0[256], c1[256], c3[256], next[256];
+  long long log_index[256], pix[256];
+  R W0[256], pw[256], gpar[256];
+  int bin[256], nscat[256], obs_i[256], job[256];
+  // scattering point and incoming direction, saved during the peel-off
+  uint32_t scx[256], scy[256], scz[256], sidx[256];
+  int slev[256];
+  R sfx[256], sfy[256], sfz[256], sdx[256], sdy[256], sdz[256];
+};
+
+template <typename R>
+__device__ __forceinline__ uint32_t draw_u32(ColdState<R>& C, int t) {
+  const uint32_t j = C.next[t];
+  C.next[t] = j + 1u;
+  const uint4 b = philox4x32_10(make_uint4(C.c0[t], C.c1[t], j >> 2, C.c3[t]), C.k0[t], C.k1[t]);
+  const uint32_t w = j & 3u;
+  return w == 0u ? b.x : (w == 1u ? b.y : (w == 2u ? b.z : b.w));
+}
+
+template <typename R>
+__device__ __forceinline__ R draw(ColdState<R>& C, int t) {
+  return Num<R>::uni(draw_u32(C, t));
+}
+
+__device__ __forceinline__ void book_d(WarpLedger& SL, const JobDev* jobs, int job, int wid, int i, double v) {
+  if (v == 0.0) return;
+  if (SL.tag[wid] == job) {
+    atomicAdd(&SL.d[i][wid], v);
+  } else {
+    LedgerDev* L = jobs[job].ledger;
+    double* dst[L_ND] = {&L->emitted, &L->absorbed, &L->escaped, &L->rr_gain, &L->rr_loss, &L->killed, &L->peeled};
+    atomicAdd(dst[i], v);
   }
-  __device__ void flush(LedgerDev* L) {
-    if (emitted != 0.0) atomicAdd(&L->emitted, emitted);
-    if (absorbed != 0.0) atomicAdd(&L->absorbed, absorbed);
-    if (escaped != 0.0) atomicAdd(&L->escaped, escaped);
-    if (rr_gain != 0.0) atomicAdd(&L->rr_gain, rr_gain);
-    if (rr_loss != 0.0) atomicAdd(&L->rr_loss, rr_loss);
-    if (killed != 0.0) atomicAdd(&L->killed, killed);
-    if (peeled != 0.0) atomicAdd(&L->peeled, peeled);
-    if (n_packets) atomicAdd(&L->n_packets, n_packets);
-    if (n_cross) atomicAdd(&L->n_cross, n_cross);
-    if (n_scatter) atomicAdd(&L->n_scatter, n_scatter);
-    if (n_peel_cross) atomicAdd(&L->n_peel_cross, n_peel_cross);
-    if (n_killed) atomicAdd(&L->n_killed, n_killed);
-    if (n_peel_out) atomicAdd(&L->n_peel_out, n_peel_out);
-    zero();
+}
+
+__device__ __forceinline__ void book_u(WarpLedger& SL, const JobDev* jobs, int job, int wid, int i,
+                                       unsigned long long v) {
+  if (v == 0ull) return;
+  if (SL.tag[wid] == job) {
+    atomicAdd(&SL.u[i][wid], v);
+  } else {
+    LedgerDev* L = jobs[job].ledger;
+    unsigned long long* dst[U_NU] = {&L->n_packets, &L->n_cross, &L->n_scatter, &L->n_peel_cross, &L->n_killed,
+                                     &L->n_peel_out};
+    atomicAdd(dst[i], v);
   }
+}
+
+// f32 -> f64 on the integer pipe (GB300's FP64 pipe is narrow); positive
+// normal values only, denormals map to 0
+__device__ __forceinline__ double widen(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t e = b >> 23;
+  const uint32_t hi = e ? (((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)) : 0u;
+  const uint32_t lo = e ? (b << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double v) { return v; }
+
+template <typename R>
+struct ObsGeom;
+template <>
+struct ObsGeom<float> {
+  static __device__ __forceinline__ float k(const ObsDev& O, int a) { return O.kf[a]; }
+  static __device__ __forceinline__ float ex(const ObsDev& O, int a) { return O.exf[a]; }
+  static __device__ __forceinline__ float ey(const ObsDev& O, int a) { return O.eyf[a]; }
+  static __device__ __forceinline__ float c(const ObsDev& O, int a) { return O.cf[a]; }
+  static __device__ __forceinline__ float ip(const ObsDev& O, int a) { return O.inv_pixf[a]; }
+};
+template <>
+struct ObsGeom<double> {
+  static __device__ __forceinline__ double k(const ObsDev& O, int a) { return O.k[a]; }
+  static __device__ __forceinline__ double ex(const ObsDev& O, int a) { return O.ex[a]; }
+  static __device__ __forceinline__ double ey(const ObsDev& O, int a) { return O.ey[a]; }
+  static __device__ __forceinline__ double c(const ObsDev& O, int a) { return O.c[a]; }
+  static __device__ __forceinline__ double ip(const ObsDev& O, int a) { return O.inv_pix[a]; }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -323,71 +412,77 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   return v;
 }
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  return v;
-}
 
 enum { ST_DEAD = 0, ST_TRACE = 1, ST_PEEL = 2, ST_DONE = 3 };
+enum { EV_NONE = 0, EV_IDLE, EV_INTERACT, EV_ESCAPE, EV_CUT, EV_KILL, EV_DEGEN };
 
-template <typename R, bool PEEL>
-__global__ void __launch_bounds__(256) trace_kernel(const JobDev* __restrict__ jobs,
-                                                    const ItemDev* __restrict__ items, int n_items,
-                                                    unsigned long long* __restrict__ counter,
-                                                    long long total, int refill_thr) {
+#ifndef RT_FP32_MIN_BLOCKS
+#define RT_FP32_MIN_BLOCKS 4
+#endif
+// resident 256-thread blocks per SM the register allocation is sized for
+template <typename R>
+struct MinBlocks {
+  static constexpr int value = sizeof(R) == 4 ? RT_FP32_MIN_BLOCKS : 2;
+};
+
+template <typename R, bool PEEL, int EST>
+__global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const JobDev* __restrict__ jobs,
+                                                                         const ItemDev* __restrict__ items,
+                                                                         int n_items,
+                                                                         unsigned long long* __restrict__ counter,
+                                                                         long long total, int refill_thr) {
   const unsigned FULL = 0xFFFFFFFFu;
-  const int lane = threadIdx.x & 31;
+  __shared__ WarpLedger SL;
+  __shared__ ColdState<R> C;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (lane < L_ND) SL.d[lane][wid] = 0.0;
+  if (lane < U_NU) SL.u[lane][wid] = 0ull;
+  if (lane == 0) SL.tag[wid] = -1;
+  C.job[t] = -1;
+  __syncwarp();
 
+  // hot per-lane state
   int st = ST_DEAD;
-  int job = -1, acc_job = -1;
-  LaneLedger acc;
-  acc.zero();
-
   Geo<R> g;
   g.cx = g.cy = g.cz = 0u;
   g.lev = 0;
   g.idx = 0u;
   g.fx = g.fy = g.fz = R(0);
   g.rho = R(0);
+  Cursor cur;
+  cur.pending = 0u;
+  cur.k = 0;
+  GridRegs G;
+  G.node = nullptr;
+  G.rho64 = nullptr;
+  G.rx = G.ry = G.rz = 1u;
   R dx = R(0), dy = R(0), dz = R(1), ix = R(0), iy = R(0), iz = R(0);
-  R W = R(0), W0 = R(0), tau = R(0), pkt_abs = R(0);
-  R kext = R(0), alb = R(0), gpar = R(0);
+  R W = R(0), tau = R(0), taup = R(0), pkt_abs = R(0), kext = R(0), alb = R(0), tau_cut = R(0);
   double* absb = nullptr;
-  const JobDev* Jp = jobs;
-  PhiloxStream rng;
-  rng.init(0ull, 0u, 0u, 0u, 0ull);
-  long long steps = 0, log_index = -1;
-  uint32_t nscat = 0u, ncross = 0u;
-  int bin = 0;
-  // peel-off state (observer march)
-  int obs_i = 0;
-  R taup = R(0), pw = R(0);
-  long long pix = -1;
-  Geo<R> sg = g;
-  R sdx = R(0), sdy = R(0), sdz = R(0);
+  uint32_t step_limit = 0u, ncross = 0u, npeel = 0u;
 
   // after a scattering (and its peel-off): new direction from the phase
   // function, Russian roulette when the weight is low, next free path.
   // Returns a fate (1 = roulette kill) or -1.
-  auto finish_scatter = [&](const JobDev& J) -> int {
-    const R mu = hg_mu(gpar, Num<R>::uni(rng.u32()));
-    scatter_dir(dx, dy, dz, mu, Num<R>::uni(rng.u32()));
+  auto finish_scatter = [&]() -> int {
+    const JobDev& J = jobs[C.job[t]];
+    const R mu = hg_mu(C.gpar[t], draw(C, t));
+    scatter_dir(dx, dy, dz, mu, draw(C, t));
     ix = inv_abs(dx);
     iy = inv_abs(dy);
     iz = inv_abs(dz);
-    if (J.rr_wmin > 0.0 && W < (R)J.rr_wmin * W0) {
-      const R ur = Num<R>::uni(rng.u32());
+    if (J.rr_wmin > 0.0 && W < (R)J.rr_wmin * C.W0[t]) {
+      const R ur = draw(C, t);
       if (ur < (R)J.rr_p) {
-        acc.rr_loss += (double)W;
+        book_d(SL, jobs, C.job[t], wid, L_RRL, (double)W);
         W = R(0);
         return 1;
       }
       const R Wn = W / (R(1) - (R)J.rr_p);
-      acc.rr_gain += (double)(Wn - W);
+      book_d(SL, jobs, C.job[t], wid, L_RRG, (double)(Wn - W));
       W = Wn;
     }
-    tau = -Num<R>::log_(Num<R>::uni(rng.u32()));
+    tau = -Num<R>::log_(draw(C, t));
     return -1;
   };
 
@@ -413,13 +508,17 @@ __global__ void __launch_bounds__(256) trace_kernel(const JobDev* __restrict__ j
             else hi = mid - 1;
           }
           const ItemDev& I = items[lo];
-          job = I.job;
-          if (job != acc_job) {
-            if (acc_job >= 0) acc.flush(jobs[acc_job].ledger);
-            acc_job = job;
-          }
-          Jp = jobs + job;
-          const JobDev& J = *Jp;
+          const int job = I.job;
+          const JobDev& J = jobs[job];
+          C.job[t] = job;
+          if (SL.tag[wid] < 0) atomicCAS(&SL.tag[wid], -1, job);
+          G.node = J.node;
+          G.rho64 = J.rho64;
+          G.rx = J.root[0];
+          G.ry = J.root[1];
+          G.rz = J.root[2];
+          step_limit = (uint32_t)min(J.step_limit, (long long)0xFFFFFFFFll);
+          tau_cut = J.peel_tau_max > 0.0 ? (R)J.peel_tau_max : Num<R>::inf();
           const long long p = gi - I.pkt_begin;
           int blo = 0, bhi = J.n_lambda - 1;
           while (blo < bhi) {
@@ -427,78 +526,82 @@ __global__ void __launch_bounds__(256) trace_kernel(const JobDev* __restrict__ j
             if (I.bin_prefix[mid] <= p) blo = mid;
             else bhi = mid - 1;
           }
-          bin = blo;
-          const long long k = p - I.bin_prefix[bin];
-          log_index = J.packet_log ? I.log_offset + p : -1;
-          rng.init(J.seed, J.job_id, J.iter, (I.src_index << 16) | (uint32_t)bin, (unsigned long long)k);
+          const int bin = blo;
+          const unsigned long long k = (unsigned long long)(p - I.bin_prefix[bin]);
+          C.bin[t] = bin;
+          C.log_index[t] = J.packet_log ? I.log_offset + p : -1;
+          C.k0[t] = (uint32_t)J.seed ^ J.job_id;
+          C.k1[t] = (uint32_t)(J.seed >> 32) ^ J.iter;
+          C.c0[t] = (uint32_t)k;
+          C.c1[t] = (uint32_t)(k >> 32);
+          C.c3[t] = (I.src_index << 16) | (uint32_t)bin;
+          C.next[t] = 0u;
           const BinDev& B = J.bins[bin];
           kext = Num<R>::kext(B);
           alb = Num<R>::alb(B);
-          gpar = Num<R>::gg(B);
+          C.gpar[t] = Num<R>::gg(B);
           absb = J.absorbed ? J.absorbed + (long long)(J.abs_bins > 1 ? bin : 0) * J.n_cells : nullptr;
-          W0 = (R)I.W0[bin];
+          const R W0 = (R)I.W0[bin];
+          C.W0[t] = W0;
           W = W0;
           pkt_abs = R(0);
-          steps = 0;
-          nscat = ncross = 0u;
-          acc.emitted += (double)W0;
-          acc.n_packets += 1ull;
+          ncross = npeel = 0u;
+          C.nscat[t] = 0;
+          book_d(SL, jobs, job, wid, L_EMIT, (double)W0);
+          book_u(SL, jobs, job, wid, U_PK, 1ull);
           bool inside;
           if (I.kind == RT_SRC_POINT || I.kind == RT_SRC_BEAM) {
             if (I.kind == RT_SRC_POINT) {
-              const R u1 = Num<R>::uni(rng.u32()), u2 = Num<R>::uni(rng.u32());
+              const R u1 = draw(C, t), u2 = draw(C, t);
               iso_dir(u1, u2, dx, dy, dz);
             } else {
               dx = (R)I.dir[0];
               dy = (R)I.dir[1];
               dz = (R)I.dir[2];
             }
-            inside = place_root_units(J, g, (R)I.pos[0], (R)I.pos[1], (R)I.pos[2], dx, dy, dz);
+            inside = place_root(G, g, cur, (R)I.pos[0], (R)I.pos[1], (R)I.pos[2], dx, dy, dz);
           } else if (I.kind == RT_SRC_EXTERNAL) {
             // face by area, uniform point on it, cosine-weighted inward direction
-            const double ax = (double)J.root[1] * J.root[2], ay = (double)J.root[0] * J.root[2],
-                         az = (double)J.root[0] * J.root[1];
-            const R u0 = Num<R>::uni(rng.u32());
-            const R tot = R(2) * (R)(ax + ay + az);
-            const R v = u0 * tot;
+            const R ax = (R)G.ry * (R)G.rz, ay = (R)G.rx * (R)G.rz, az = (R)G.rx * (R)G.ry;
+            const R v = draw(C, t) * (R(2) * (ax + ay + az));
             int face = 5;
             R cum = R(0);
-            const R ar[3] = {(R)ax, (R)ay, (R)az};
+            const R ar[3] = {ax, ay, az};
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
               cum += ar[f >> 1];
               if (face == 5 && v < cum) face = f;
             }
             const int a = face >> 1;
-            const R u1 = Num<R>::uni(rng.u32()), u2 = Num<R>::uni(rng.u32());
-            const R u3 = Num<R>::uni(rng.u32()), u4 = Num<R>::uni(rng.u32());
+            const R u1 = draw(C, t), u2 = draw(C, t);
+            const R u3 = draw(C, t), u4 = draw(C, t);
             const R mu = Num<R>::sqrt_(u3), st_ = Num<R>::sqrt_(fmax(R(0), R(1) - mu * mu));
             R sp, cp;
             Num<R>::sincos2pi(u4, &sp, &cp);
             const R dn = (face & 1) ? -mu : mu;
             R px, py, pz;
             if (a == 0) {
-              px = (face & 1) ? (R)J.root[0] : R(0);
-              py = u1 * (R)J.root[1];
-              pz = u2 * (R)J.root[2];
+              px = (face & 1) ? (R)G.rx : R(0);
+              py = u1 * (R)G.ry;
+              pz = u2 * (R)G.rz;
               dx = dn; dy = st_ * cp; dz = st_ * sp;
             } else if (a == 1) {
-              py = (face & 1) ? (R)J.root[1] : R(0);
-              px = u1 * (R)J.root[0];
-              pz = u2 * (R)J.root[2];
+              py = (face & 1) ? (R)G.ry : R(0);
+              px = u1 * (R)G.rx;
+              pz = u2 * (R)G.rz;
               dy = dn; dx = st_ * cp; dz = st_ * sp;
             } else {
-              pz = (face & 1) ? (R)J.root[2] : R(0);
-              px = u1 * (R)J.root[0];
-              py = u2 * (R)J.root[1];
+              pz = (face & 1) ? (R)G.rz : R(0);
+              px = u1 * (R)G.rx;
+              py = u2 * (R)G.ry;
               dz = dn; dx = st_ * cp; dy = st_ * sp;
             }
-            inside = place_root_units(J, g, px, py, pz, dx, dy, dz);
+            inside = place_root(G, g, cur, px, py, pz, dx, dy, dz);
           } else {
             // dust emission: cell from this bin's cumulative emission
             const double* cdf = I.cdf + (long long)bin * J.n_cells;
             const double totE = cdf[J.n_cells - 1];
-            const double target = (double)Num<R>::uni(rng.u32()) * totE;
+            const double target = (double)draw(C, t) * totE;
             long long clo = 0, chi = J.n_cells - 1;
             while (clo < chi) {
               const long long mid = clo + ((chi - clo) >> 1);
@@ -510,25 +613,26 @@ __global__ void __launch_bounds__(256) trace_kernel(const JobDev* __restrict__ j
             g.cy = (uint32_t)((cw >> RT_COORD_BITS) & RT_COORD_MASK);
             g.cz = (uint32_t)((cw >> (2 * RT_COORD_BITS)) & RT_COORD_MASK);
             g.lev = J.level[clo];
-            g.idx = (uint32_t)clo;
-            g.fx = Num<R>::uni(rng.u32());
-            g.fy = Num<R>::uni(rng.u32());
-            g.fz = Num<R>::uni(rng.u32());
-            g.rho = Num<R>::leaf_rho(J, load_node(J.node, g.idx), g.idx);
-            const R u4 = Num<R>::uni(rng.u32()), u5 = Num<R>::uni(rng.u32());
+            g.fx = draw(C, t);
+            g.fy = draw(C, t);
+            g.fz = draw(C, t);
+            cur.pending = (uint32_t)clo;
+            cur.k = g.lev;
+            const R u4 = draw(C, t), u5 = draw(C, t);
             iso_dir(u4, u5, dx, dy, dz);
             inside = true;
           }
           ix = inv_abs(dx);
           iy = inv_abs(dy);
           iz = inv_abs(dz);
-          tau = -Num<R>::log_(Num<R>::uni(rng.u32()));
+          tau = -Num<R>::log_(draw(C, t));
           if (inside) {
             st = ST_TRACE;
           } else {
-            acc.escaped += (double)W;
-            if (log_index >= 0) {
-              double* r = J.packet_log + log_index * 10;
+            book_d(SL, jobs, job, wid, L_ESC, (double)W);
+            const long long li = C.log_index[t];
+            if (li >= 0) {
+              double* r = J.packet_log + li * 10;
               r[0] = (double)W; r[1] = 0.0; r[2] = 0.0; r[3] = 0.0;
               r[4] = r[5] = r[6] = 0.0;
               r[7] = (double)dx; r[8] = (double)dy; r[9] = (double)dz;
@@ -538,175 +642,205 @@ __global__ void __launch_bounds__(256) trace_kernel(const JobDev* __restrict__ j
         }
       }
     }
-    {
-      const unsigned still = __ballot_sync(FULL, st != ST_DONE);
-      if (still == 0u) break;
+    if (__ballot_sync(FULL, st == ST_TRACE || st == ST_PEEL) == 0u) {
+      // nothing to step: finished, or packages that left at emission
+      if (__ballot_sync(FULL, st == ST_DEAD) == 0u) break;
+      continue;
     }
-    if (st != ST_TRACE && st != ST_PEEL) continue;
 
-    // ------------------------------------------------------------------ step
-    const JobDev& J = *Jp;
-    int fate = -1;  // >= 0: the package ends with this fate
-    if (st == ST_TRACE && steps >= J.step_limit) {
-      acc.killed += (double)W;
-      acc.n_killed += 1ull;
-      atomicOr(&J.ledger->status, 1);
-      fate = 2;
-    } else {
-      int a;
-      const R t = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
-      if (a < 0) {  // degenerate direction: cannot happen for |d| = 1
-        if (st == ST_TRACE) {
-          acc.killed += (double)W;
-          acc.n_killed += 1ull;
-          atomicOr(&J.ledger->status, 2);
-          fate = 2;
+    // ------------------------------------------------------------- fast path
+    // Step cells until some lane of the warp meets an event.  One node word
+    // is loaded per lane per pass: a refined node advances the descent by a
+    // level, a leaf gets one segment (Sect. 2.3) and a face crossing.
+    int ev = (st == ST_TRACE || st == ST_PEEL) ? EV_NONE : EV_IDLE;
+    do {
+      if (ev == EV_NONE) {
+        const uint32_t w = __ldg(G.node + cur.pending);
+        const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
+        if (w & RT_INTERIOR) {
+          descend_step(g, cur, w, dx, dy, dz);
         } else {
-          pix = -1;  // abandon this observer
-        }
-      } else {
-        const R kl = kext * g.rho * Num<R>::ldexp_(R(1), -g.lev);  // extinction per local unit
-        bool inside_event = false;
-        R tseg = t;
-        if (st == ST_TRACE) {
-          ++steps;
-          if (J.estimator == RT_EST_CONTINUOUS) {
-            const R ksca = alb * kl;
-            const R tsc = ksca * t;
-            if (ksca > R(0) && tsc >= tau) {
-              inside_event = true;
-              tseg = tau / ksca;
-            } else {
-              tau -= tsc;
-            }
-            const R q = -Num<R>::expm1_(-(kl - ksca) * tseg);
-            const R dep = W * q;
-            W -= dep;
-            if (dep > R(0)) {
-              pkt_abs += dep;
-              if (absb) atomicAdd(absb + g.idx, (double)dep);
-            }
+          settle_leaf(g, cur, w, r64);
+          const bool tr = st == ST_TRACE;
+          int a;
+          const R tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
+          if (tr && ncross >= step_limit) {
+            ev = EV_KILL;
+          } else if (a < 0) {
+            ev = EV_DEGEN;  // cannot happen for |d| = 1
           } else {
-            const R te = kl * t;
-            if (kl > R(0) && te >= tau) {
-              inside_event = true;
-              tseg = tau / kl;
-            } else {
-              tau -= te;
-            }
-          }
-          if (tseg > R(0)) ++ncross;
-        } else {
-          taup += kl * t;
-          if (t > R(0)) acc.n_peel_cross += 1ull;
-        }
-
-        if (inside_event) {
-          // ------------------------------------------- interaction in this cell
-          g.fx = clamp01(g.fx + tseg * dx);
-          g.fy = clamp01(g.fy + tseg * dy);
-          g.fz = clamp01(g.fz + tseg * dz);
-          bool scatter = true;
-          if (J.estimator == RT_EST_ANALOG) {
-            const R ua = Num<R>::uni(rng.u32());
-            if (ua >= alb) {
-              scatter = false;
-              if (absb) atomicAdd(absb + g.idx, (double)W);
-              pkt_abs += W;
-              W = R(0);
-              fate = 3;
-            }
-          }
-          if (scatter) {
-            ++nscat;
-            acc.n_scatter += 1ull;
-            if (PEEL && J.n_obs > 0) {
-              // save the scattering point and march towards each observer in
-              // turn (observer selection below); the new direction is drawn
-              // after the last observer
-              sg = g;
-              sdx = dx; sdy = dy; sdz = dz;
-              obs_i = -1;
-              pix = -1;
-              st = ST_PEEL;
-            } else {
-              fate = finish_scatter(J);
-            }
-          }
-        } else if (st == ST_PEEL && J.peel_tau_max > 0.0 && taup > (R)J.peel_tau_max) {
-          pix = -1;  // cut: this observer gets nothing; select the next one below
-        } else {
-          const bool in = cross_face(J, g, a, t, dx, dy, dz);
-          if (!in) {
-            if (st == ST_TRACE) {
-              acc.escaped += (double)W;
-              fate = 0;
-            } else {
-              // peel-off contribution reaches the observer
-              if (pix >= 0) {
-                const double c = (double)pw * (double)Num<R>::exp_(-taup);
-                atomicAdd(J.images + pix, c);
-                acc.peeled += c;
+            const R kl = kext * g.rho * Num<R>::pow2m(g.lev);  // extinction per local unit
+            bool inside_event = false;
+            R tseg = tx;
+            if (EST == RT_EST_CONTINUOUS) {
+              // free path drawn in scattering optical depth; the weight
+              // decays by the absorbed fraction along the segment
+              const R ksca = alb * kl;
+              const R tsc = ksca * tx;
+              inside_event = tr && ksca > R(0) && tsc >= tau;
+              if (inside_event) tseg = tau / ksca;
+              if (tr) {
+                R q, e;
+                Num<R>::absorb_pair((kl - ksca) * tseg, q, e);
+                tau = inside_event ? R(0) : tau - tsc;
+                const R dep = W * q;
+                W = W * e;
+                if (dep > R(0)) {
+                  pkt_abs += dep;
+                  if (absb) atomicAdd(absb + g.idx, widen(dep));
+                }
               }
-              pix = -1;
+            } else {
+              // analog: free path drawn in extinction optical depth
+              const R te = kl * tx;
+              inside_event = tr && kl > R(0) && te >= tau;
+              if (inside_event) tseg = tau / kl;
+              if (tr) tau = inside_event ? R(0) : tau - te;
+            }
+            if (tr) {
+              ncross += tseg > R(0) ? 1u : 0u;
+            } else {
+              taup += kl * tx;
+              npeel += tx > R(0) ? 1u : 0u;
+            }
+            if (inside_event) {
+              g.fx = clamp01(g.fx + tseg * dx);
+              g.fy = clamp01(g.fy + tseg * dy);
+              g.fz = clamp01(g.fz + tseg * dz);
+              cur.pending = g.idx;
+              cur.k = g.lev;
+              ev = EV_INTERACT;
+            } else if (!tr && taup > tau_cut) {
+              ev = EV_CUT;
+            } else if (!advance(G, g, cur, a, tx, dx, dy, dz)) {
+              ev = EV_ESCAPE;
             }
           }
+        }
+      }
+    } while (__all_sync(FULL, ev == EV_NONE || ev == EV_IDLE));
+
+    // ------------------------------------------------------------- slow path
+    if (ev == EV_NONE || ev == EV_IDLE) continue;
+    int fate = -1;  // >= 0: the package ends with this fate
+    bool pick_observer = false;
+    const int job = C.job[t];
+    if (ev == EV_KILL || (ev == EV_DEGEN && st == ST_TRACE)) {
+      book_d(SL, jobs, job, wid, L_KILL, (double)W);
+      book_u(SL, jobs, job, wid, U_KILL, 1ull);
+      atomicOr(&jobs[job].ledger->status, ev == EV_KILL ? 1 : 2);
+      fate = 2;
+    } else if (ev == EV_DEGEN || ev == EV_CUT) {
+      pick_observer = true;  // abandon this observer
+    } else if (ev == EV_ESCAPE) {
+      if (st == ST_TRACE) {
+        book_d(SL, jobs, job, wid, L_ESC, (double)W);
+        fate = 0;
+      } else {
+        // the peel-off contribution reaches the observer (Sect. 2.4)
+        const double c = (double)C.pw[t] * (double)Num<R>::exp_(-taup);
+        atomicAdd(jobs[job].images + C.pix[t], c);
+        book_d(SL, jobs, job, wid, L_PEEL, c);
+        pick_observer = true;
+      }
+    } else {  // EV_INTERACT: absorption (analog) or scattering in this cell
+      bool scatter = true;
+      if (EST == RT_EST_ANALOG) {
+        const R ua = draw(C, t);
+        if (ua >= alb) {
+          scatter = false;
+          if (absb) atomicAdd(absb + g.idx, widen(W));
+          pkt_abs += W;
+          W = R(0);
+          fate = 3;
+        }
+      }
+      if (scatter) {
+        C.nscat[t] += 1;
+        if (PEEL && jobs[job].n_obs > 0) {
+          // save the scattering point and march towards each observer in
+          // turn; the new direction is drawn after the last observer
+          C.scx[t] = g.cx; C.scy[t] = g.cy; C.scz[t] = g.cz;
+          C.sidx[t] = g.idx; C.slev[t] = g.lev;
+          C.sfx[t] = g.fx; C.sfy[t] = g.fy; C.sfz[t] = g.fz;
+          C.sdx[t] = dx; C.sdy[t] = dy; C.sdz[t] = dz;
+          C.obs_i[t] = -1;
+          st = ST_PEEL;
+          pick_observer = true;
+        } else {
+          fate = finish_scatter();
         }
       }
     }
 
     // -------------------------------------------- peel-off observer selection
-    if (PEEL && st == ST_PEEL && pix < 0) {
-      // choose the next observer whose pixel is inside the image
+    if (PEEL && pick_observer) {
+      const JobDev& J = jobs[C.job[t]];
+      // back to the scattering point
+      g.cx = C.scx[t]; g.cy = C.scy[t]; g.cz = C.scz[t];
+      g.idx = C.sidx[t]; g.lev = C.slev[t];
+      g.fx = C.sfx[t]; g.fy = C.sfy[t]; g.fz = C.sfz[t];
+      cur.pending = g.idx;
+      cur.k = g.lev;
+      const R sdx = C.sdx[t], sdy = C.sdy[t], sdz = C.sdz[t];
+      int o = C.obs_i[t];
       bool started = false;
       while (!started) {
-        ++obs_i;
-        if (obs_i >= J.n_obs) break;
-        const ObsDev& O = J.obs[obs_i];
-        // scattering point in root-cell units
-        const R s = Num<R>::ldexp_(R(1), -sg.lev);
-        const R Px = ((R)sg.cx + sg.fx) * s - (R)O.c[0];
-        const R Py = ((R)sg.cy + sg.fy) * s - (R)O.c[1];
-        const R Pz = ((R)sg.cz + sg.fz) * s - (R)O.c[2];
-        const R u = (Px * (R)O.ex[0] + Py * (R)O.ex[1] + Pz * (R)O.ex[2]) * (R)O.inv_pix[0] + R(0.5) * (R)O.nx;
-        const R v = (Px * (R)O.ey[0] + Py * (R)O.ey[1] + Pz * (R)O.ey[2]) * (R)O.inv_pix[1] + R(0.5) * (R)O.ny;
+        ++o;
+        if (o >= J.n_obs) break;
+        const ObsDev& O = J.obs[o];
+        // scattering point in root-cell units, projected on the image plane
+        const R s = Num<R>::pow2m(g.lev);
+        const R Px = ((R)g.cx + g.fx) * s - ObsGeom<R>::c(O, 0);
+        const R Py = ((R)g.cy + g.fy) * s - ObsGeom<R>::c(O, 1);
+        const R Pz = ((R)g.cz + g.fz) * s - ObsGeom<R>::c(O, 2);
+        const R u = (Px * ObsGeom<R>::ex(O, 0) + Py * ObsGeom<R>::ex(O, 1) + Pz * ObsGeom<R>::ex(O, 2)) *
+                        ObsGeom<R>::ip(O, 0) + R(0.5) * (R)O.nx;
+        const R v = (Px * ObsGeom<R>::ey(O, 0) + Py * ObsGeom<R>::ey(O, 1) + Pz * ObsGeom<R>::ey(O, 2)) *
+                        ObsGeom<R>::ip(O, 1) + R(0.5) * (R)O.ny;
         const R fu = Num<R>::floor_(u), fv = Num<R>::floor_(v);
         if (!(fu >= R(0) && fv >= R(0) && fu < (R)O.nx && fv < (R)O.ny)) {
-          acc.n_peel_out += 1ull;
+          book_u(SL, jobs, C.job[t], wid, U_POUT, 1ull);
           continue;
         }
-        const R kx = (R)O.k[0], ky = (R)O.k[1], kz = (R)O.k[2];
-        pw = W * hg_phase(gpar, sdx * kx + sdy * ky + sdz * kz);
-        pix = (((long long)obs_i * J.img_bins + (J.img_bins > 1 ? bin : 0)) * O.ny + (long long)fv) * O.nx +
-              (long long)fu;
-        g = sg;
+        const R kx = ObsGeom<R>::k(O, 0), ky = ObsGeom<R>::k(O, 1), kz = ObsGeom<R>::k(O, 2);
+        C.pw[t] = W * hg_phase(C.gpar[t], sdx * kx + sdy * ky + sdz * kz);
+        const int bin = C.bin[t];
+        C.pix[t] = (((long long)o * J.img_bins + (J.img_bins > 1 ? bin : 0)) * O.ny + (long long)fv) * O.nx +
+                   (long long)fu;
         dx = kx; dy = ky; dz = kz;
         ix = inv_abs(dx); iy = inv_abs(dy); iz = inv_abs(dz);
         taup = R(0);
         started = true;
       }
+      C.obs_i[t] = o;
       if (!started) {
-        // all observers done: restore the package and finish the scattering
-        g = sg;
+        // all observers done: continue the package from the scattering point
         dx = sdx; dy = sdy; dz = sdz;
         st = ST_TRACE;
-        fate = finish_scatter(J);
+        fate = finish_scatter();
       }
     }
 
     if (fate >= 0) {
-      acc.absorbed += (double)pkt_abs;
-      acc.n_cross += ncross;
-      if (log_index >= 0) {
-        double* r = J.packet_log + log_index * 10;
-        const R s = Num<R>::ldexp_(R(1), -g.lev);
+      const int job = C.job[t];
+      book_d(SL, jobs, job, wid, L_ABS, (double)pkt_abs);
+      book_u(SL, jobs, job, wid, U_CROSS, ncross);
+      book_u(SL, jobs, job, wid, U_SCAT, (unsigned long long)C.nscat[t]);
+      book_u(SL, jobs, job, wid, U_PCROSS, npeel);
+      const long long li = C.log_index[t];
+      if (li >= 0) {
+        double* r = jobs[job].packet_log + li * 10;
+        const double s = (double)Num<R>::pow2m(g.lev) * jobs[job].h0;
         r[0] = fate == 0 ? (double)W : 0.0;
-        r[1] = (double)nscat;
+        r[1] = (double)C.nscat[t];
         r[2] = (double)ncross;
         r[3] = (double)fate;
-        r[4] = ((double)g.cx + (double)g.fx) * (double)s * J.h0;
-        r[5] = ((double)g.cy + (double)g.fy) * (double)s * J.h0;
-        r[6] = ((double)g.cz + (double)g.fz) * (double)s * J.h0;
+        // signed lattice coordinates: a package that left through a lower
+        // face sits at index -1 with offset 1
+        r[4] = ((double)(int)g.cx + (double)g.fx) * s;
+        r[5] = ((double)(int)g.cy + (double)g.fy) * s;
+        r[6] = ((double)(int)g.cz + (double)g.fz) * s;
         r[7] = (double)dx; r[8] = (double)dy; r[9] = (double)dz;
       }
       st = ST_DEAD;
@@ -714,31 +848,25 @@ __global__ void __launch_bounds__(256) trace_kernel(const JobDev* __restrict__ j
   }
 
   // ------------------------------------------------------------ final ledger
-  const int j0 = __shfl_sync(FULL, acc_job, 0);
-  if (__all_sync(FULL, acc_job == j0)) {
-    if (j0 >= 0) {
-      double v[7] = {acc.emitted, acc.absorbed, acc.escaped, acc.rr_gain, acc.rr_loss, acc.killed, acc.peeled};
-      unsigned long long u[6] = {acc.n_packets, acc.n_cross, acc.n_scatter, acc.n_peel_cross, acc.n_killed,
-                                 acc.n_peel_out};
+  __syncwarp();
+  const int tag = SL.tag[wid];
+  if (tag >= 0 && lane == 0) {
+    LedgerDev* L = jobs[tag].ledger;
+    double* dd[L_ND] = {&L->emitted, &L->absorbed, &L->escaped, &L->rr_gain, &L->rr_loss, &L->killed, &L->peeled};
+    unsigned long long* du[U_NU] = {&L->n_packets, &L->n_cross, &L->n_scatter, &L->n_peel_cross, &L->n_killed,
+                                    &L->n_peel_out};
 #pragma unroll
-      for (int i = 0; i < 7; ++i) v[i] = warp_sum(v[i]);
+    for (int i = 0; i < L_ND; ++i)
+      if (SL.d[i][wid] != 0.0) atomicAdd(dd[i], SL.d[i][wid]);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) u[i] = warp_sum(u[i]);
-      if (lane == 0) {
-        acc.emitted = v[0]; acc.absorbed = v[1]; acc.escaped = v[2]; acc.rr_gain = v[3];
-        acc.rr_loss = v[4]; acc.killed = v[5]; acc.peeled = v[6];
-        acc.n_packets = u[0]; acc.n_cross = u[1]; acc.n_scatter = u[2]; acc.n_peel_cross = u[3];
-        acc.n_killed = u[4]; acc.n_peel_out = u[5];
-        acc.flush(jobs[j0].ledger);
-      }
-    }
-  } else if (acc_job >= 0) {
-    acc.flush(jobs[acc_job].ledger);
+    for (int i = 0; i < U_NU; ++i)
+      if (SL.u[i][wid]) atomicAdd(du[i], SL.u[i][wid]);
   }
 }
 
 // ------------------------------------------------------------------------
-// deterministic walk (diagnostic): the tracer's own stepping, no physics
+// deterministic walk (diagnostic): the tracer's own node visits and face
+// crossings, no physics
 // ------------------------------------------------------------------------
 template <typename R>
 __global__ void walk_kernel(const JobDev* __restrict__ job, long long n_rays, const double* __restrict__ origins,
@@ -747,27 +875,43 @@ __global__ void walk_kernel(const JobDev* __restrict__ job, long long n_rays, co
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rays) return;
   const JobDev& J = *job;
+  GridRegs G;
+  G.node = J.node;
+  G.rho64 = J.rho64;
+  G.rx = J.root[0];
+  G.ry = J.root[1];
+  G.rz = J.root[2];
   const R dx = (R)dirs[3 * r], dy = (R)dirs[3 * r + 1], dz = (R)dirs[3 * r + 2];
   Geo<R> g;
-  if (!place_root_units(J, g, (R)(origins[3 * r] / J.h0), (R)(origins[3 * r + 1] / J.h0),
-                        (R)(origins[3 * r + 2] / J.h0), dx, dy, dz)) {
+  Cursor cur;
+  g.rho = R(0);
+  g.idx = 0u;
+  if (!place_root(G, g, cur, (R)(origins[3 * r] / J.h0), (R)(origins[3 * r + 1] / J.h0),
+                  (R)(origins[3 * r + 2] / J.h0), dx, dy, dz)) {
     counts[r] = -1;
     return;
   }
   const R ix = inv_abs(dx), iy = inv_abs(dy), iz = inv_abs(dz);
   long long k = 0;
   for (long long guard = 0; guard < 64ll * (1ll << 22); ++guard) {
+    const uint32_t w = __ldg(G.node + cur.pending);
+    const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
+    if (w & RT_INTERIOR) {
+      descend_step(g, cur, w, dx, dy, dz);
+      continue;
+    }
+    settle_leaf(g, cur, w, r64);
     int a;
     const R t = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
     if (a < 0) break;
     if (t > R(0)) {
       if (k < max_seg) {
         cells[r * max_seg + k] = g.idx;
-        lengths[r * max_seg + k] = (double)t * ldexp(1.0, -g.lev) * J.h0;
+        lengths[r * max_seg + k] = (double)t * (double)Num<R>::pow2m(g.lev) * J.h0;
       }
       ++k;
     }
-    if (!cross_face(J, g, a, t, dx, dy, dz)) break;
+    if (!advance(G, g, cur, a, t, dx, dy, dz)) break;
   }
   counts[r] = k;
 }
@@ -787,30 +931,39 @@ __global__ void philox_kernel(long long n, const uint32_t* __restrict__ ctr, con
 // ------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------
-template <typename R, bool PEEL>
+template <typename R, bool PEEL, int EST>
 static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_items, unsigned long long* counter,
                             long long total, const LaunchCfg& cfg, cudaStream_t s) {
-  trace_kernel<R, PEEL><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill);
+  trace_kernel<R, PEEL, EST><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill);
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace(int precision, bool peel, const JobDev* jobs_dev, const ItemDev* items_dev, int n_items,
-                         unsigned long long* counter_dev, long long total, const LaunchCfg& cfg, cudaStream_t s) {
-  if (precision == 64) {
-    return peel ? launch_t<double, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
-                : launch_t<double, false>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
-  }
-  return peel ? launch_t<float, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
-              : launch_t<float, false>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
+template <typename R, int EST>
+static cudaError_t launch_pe(bool peel, const JobDev* jobs, const ItemDev* items, int n_items,
+                             unsigned long long* counter, long long total, const LaunchCfg& cfg, cudaStream_t s) {
+  return peel ? launch_t<R, true, EST>(jobs, items, n_items, counter, total, cfg, s)
+              : launch_t<R, false, EST>(jobs, items, n_items, counter, total, cfg, s);
+}
+
+cudaError_t launch_trace(int precision, bool peel, int estimator, const JobDev* jobs_dev, const ItemDev* items_dev,
+                         int n_items, unsigned long long* counter_dev, long long total, const LaunchCfg& cfg,
+                         cudaStream_t s) {
+  const bool an = estimator == RT_EST_ANALOG;
+  if (precision == 64)
+    return an ? launch_pe<double, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
+              : launch_pe<double, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
+  return an ? launch_pe<float, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
+            : launch_pe<float, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
+}
+
+template <typename R, bool PEEL>
+static cudaError_t occ_t(int block, int* n) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS>, block, 0);
 }
 
 cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm) {
-  if (precision == 64) {
-    return peel ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double, true>, block, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double, false>, block, 0);
-  }
-  return peel ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<float, true>, block, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<float, false>, block, 0);
+  if (precision == 64) return peel ? occ_t<double, true>(block, blocks_per_sm) : occ_t<double, false>(block, blocks_per_sm);
+  return peel ? occ_t<float, true>(block, blocks_per_sm) : occ_t<float, false>(block, blocks_per_sm);
 }
 
 cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, const double* origins,
