@@ -233,6 +233,29 @@ int rt_walk(rt_ctx* ctx, const rt_grid* grid, int64_t n_rays, const double* orig
 int rt_philox(rt_ctx* ctx, int64_t n, const uint32_t* ctr_dev, const uint32_t* key_dev,
               uint32_t* out_dev, void* cuda_stream);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free tracing (no counterpart in the paper)                     */
+/* ------------------------------------------------------------------------ */
+/* rt_trace without a context and without any device allocation, for callers
+ * that cannot let a library call cudaMalloc: applications whose device memory
+ * is owned by their own pool or caching allocator, and latency-critical code
+ * that cannot take the device synchronisation of cudaMalloc/cudaFree.  The
+ * tracer's scratch (job table, ledger, package counter) lives in a 64 KiB
+ * file-scope __device__ array that every GPU loading the library holds until
+ * the process exits.  The caller passes the grid (built beforehand with
+ * rt_build_grid), sources, optics, params and the output array exactly as for
+ * rt_trace; the result is the same.  Limits (RT_ERR_INVALID beyond them):
+ * 1..4 sources, 1..256 wavelength bins, point/external/beam sources only (a
+ * dust source needs a cumulative-emission table larger than the scratch),
+ * no observers.  The first call on a device looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  The scratch is cleared at the start of every call and shared by
+ * all calls: calls whose work overlaps on the GPU race on it and must be
+ * serialised by the caller.  ledger->kernel_ms is 0 (no timing events). */
+int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source* src, const rt_optics* optics,
+                     const rt_trace_params* params, double* absorbed_dev, rt_ledger* ledger,
+                     void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

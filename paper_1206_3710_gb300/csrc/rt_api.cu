@@ -39,6 +39,11 @@ static int fail(int code, const char* fmt, ...) {
   } while (0)
 
 extern "C" const char* rt_last_error(void) { return g_err.c_str(); }
+
+// lets other translation units of the library report through rt_last_error
+namespace rtk {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace rtk
 extern "C" const char* rt_version(void) { return "librt 0.1 (sm_103a)"; }
 
 // ------------------------------------------------------------------------

@@ -130,6 +130,9 @@ cudaError_t reduce_max_leaf(const double* rho64, const uint32_t* child, long lon
 cudaError_t validate_leaf_density(const double* rho64, const uint32_t* child, long long n, int* bad,
                                   cudaStream_t s);
 
+// record an error message for rt_last_error and return code
+int set_error(int code, const char* msg);
+
 // dust kernels
 cudaError_t dust_table(const double* lam_um, const double* kabs, const double* dnu, int nl, double Tmin,
                        double Tmax, int n_table, double* table, cudaStream_t s);

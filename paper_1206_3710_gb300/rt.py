@@ -23,7 +23,7 @@ SOURCE_KINDS = {"point": RT_SRC_POINT, "external": RT_SRC_EXTERNAL, "dust": RT_S
 
 EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "rt_build_grid", "rt_grid_get_info",
             "rt_grid_free", "rt_trace", "rt_peel", "rt_dust_temperature", "rt_dust_emission", "rt_walk",
-            "rt_philox"]
+            "rt_philox", "rt_trace_noalloc"]
 
 
 class RtError(RuntimeError):
@@ -118,6 +118,8 @@ def lib():
     L.rt_dust_emission.argtypes = [vp, vp, vp, C.POINTER(rt_dust), vp, vp, vp]
     L.rt_walk.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int, C.c_int64, vp, vp, vp, vp]
     L.rt_philox.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
+    L.rt_trace_noalloc.argtypes = [vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics),
+                                   C.POINTER(rt_trace_params), vp, C.POINTER(rt_ledger), vp]
     for name in EXPORTED:
         if name not in ("rt_ctx_destroy", "rt_grid_free", "rt_last_error", "rt_version"):
             getattr(L, name).restype = C.c_int
@@ -287,6 +289,19 @@ def rt_trace(ctx: Context, grid: Grid, sources, optics, absorbed, stream=None, *
     led = rt_ledger()
     rc = lib().rt_trace(ctx.handle, grid.handle, len(sources), src, C.byref(op), C.byref(prm), _ptr(absorbed),
                         C.byref(led), _stream(stream))
+    _check(rc, allow_step_limit=True)
+    return led.as_dict()
+
+
+def rt_trace_noalloc(grid: Grid, sources, optics, absorbed, stream=None, **params) -> dict:
+    """Allocation-free variant of rt_trace (scratch in a static device array)."""
+    keep = _Keep()
+    src = make_sources(sources, len(optics.kappa_ext), keep)
+    op = make_optics(optics, keep)
+    prm = make_params(keep, **params)
+    led = rt_ledger()
+    rc = lib().rt_trace_noalloc(grid.handle, len(sources), src, C.byref(op), C.byref(prm), _ptr(absorbed),
+                                C.byref(led), _stream(stream))
     _check(rc, allow_step_limit=True)
     return led.as_dict()
 
