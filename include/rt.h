@@ -163,6 +163,8 @@ typedef struct {
   int block_size;           /* 0: tuned default */
   int refill_threshold;     /* 0: tuned default; dead lanes per warp before a refill */
   int blocks_per_sm;        /* 0: occupancy-derived */
+  uint32_t* hits_dev;       /* optional device [n_cells]: deposits per cell are ADDED here
+                               (continuous estimator, rt_trace only); NULL: not counted */
 } rt_trace_params;
 
 typedef struct {
@@ -209,6 +211,42 @@ int rt_peel(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
  * cells get 0.  FP64 safeguarded Newton on a tabulated bracket. */
 int rt_dust_temperature(rt_ctx* ctx, const rt_grid* grid, const double* absorbed_dev, int n_bins,
                         const rt_dust* dust, double* T_dev, void* cuda_stream);
+
+/* Lambda iteration (Eq. 2): J_{n+1} = Lambda S_n + J_0, S_{n+1} = f(J_{n+1}).
+ * The field of the constant sources (`src`, e.g. a star) is traced once and
+ * stored (Sect. 3.2); each iteration re-emits the dust with the current
+ * temperatures (packages per bin in proportion to the bin emission, Sect. 4.2,
+ * or an equal count), traces them and solves the new temperatures from the
+ * sum of both fields.  The dust packages reuse the same random streams in
+ * every iteration (key iter = params.iter + 1), so the change in T measures
+ * convergence rather than Monte Carlo noise.  Stops when max |dT|/T over
+ * leaves with at least min_hits deposits (counted during the constant-source
+ * trace and the first dust trace) falls below tol, or after max_iter
+ * iterations (the disc test of Sect. 4.2 stops at 30). */
+typedef struct {
+  int max_iter;                  /* 1..64 */
+  double tol;                    /* stop threshold on max |dT|/T; 0: run max_iter */
+  double min_hits;               /* cells with fewer deposits are left out of the stop rule */
+  int64_t dust_packets_total;    /* packages per dust trace, spread over bins by emission */
+  int64_t dust_packets_per_bin;  /* > 0: this many per bin instead */
+} rt_lambda_params;
+
+typedef struct {
+  int n_iter;                    /* iterations taken */
+  double history[64];            /* max |dT|/T after iteration i+1 */
+  rt_ledger source_ledger;       /* the constant-source trace */
+  rt_ledger dust_ledger;         /* the last dust trace */
+  double ms;                     /* wall time of the whole iteration */
+} rt_lambda_result;
+
+/* src/params: the constant sources and their trace parameters (precision,
+ * roulette, packages); dust: the dust model (same bins as optics); T_dev
+ * (device [n_cells]) receives the final temperatures.  Library scratch:
+ * three f64 and one u32 array of n_cells. */
+int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
+                      const rt_optics* optics, const rt_dust* dust, const rt_trace_params* params,
+                      const rt_lambda_params* lp, double* T_dev, rt_lambda_result* result,
+                      void* cuda_stream);
 
 /* Dust emission per leaf and bin, 4 pi rho V kappa_abs,i B_nu_i(T) dnu_i,
  * into emission_dev (device [n_lambda][n_cells]); bin totals to

@@ -378,7 +378,8 @@ class _DustSource:
 
 
 def lambda_iterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed: int, T_min=2.7,
-                   T_max=3000.0, max_iter=30, tol=1e-3, min_hits=1000.0, n_threads=1):
+                   T_max=3000.0, max_iter=30, tol=1e-3, min_hits=1000.0, n_threads=1, dust_per_bin=False,
+                   **trace_kw):
     """Lambda iteration (Eq. 2): the field of the constant sources is computed
     once and stored (Sect. 3.2); each iteration re-emits the dust with the
     current temperatures, traces the dust photons, and solves the new
@@ -386,21 +387,26 @@ def lambda_iterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed
     same random streams every iteration (iteration index kept out of the
     key), so that the change in T between iterations measures convergence
     rather than Monte Carlo noise.  Stops when max dT/T over cells with at
-    least ``min_hits`` packet hits is below ``tol`` or after ``max_iter``."""
+    least ``min_hits`` packet hits is below ``tol`` or after ``max_iter``.
+    ``dust_per_bin``: ``packets_dust`` packages in every emitting bin instead
+    of a total spread in proportion to the bin emission."""
     kabs = (1 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
     lam = np.asarray(optics.lambda_um)
     dnu = np.asarray(optics.dnu)
     r = trace(tree, [star], optics, packets_star, seed=seed, iter_=0, per_lambda=False,
-              n_threads=n_threads, validation=True)
+              n_threads=n_threads, validation=True, **trace_kw)
     A_star = r["absorbed"][0]
     hits = r["hits"][0]
     T = dust_temperature(tree, A_star, lam, kabs, dnu, T_min, T_max, n_threads)
     history = []
     for it in range(1, max_iter + 1):
         em = dust_emission(tree, T, lam, kabs, dnu)
-        npk = packets_by_energy(em.sum(axis=1), packets_dust)
+        if dust_per_bin:
+            npk = np.where(em.sum(axis=1) > 0, packets_dust, 0).astype(np.int64)
+        else:
+            npk = packets_by_energy(em.sum(axis=1), packets_dust)
         rd = trace(tree, [_DustSource(em)], optics, npk, seed=seed, iter_=1, per_lambda=False,
-                   n_threads=n_threads, validation=True)
+                   n_threads=n_threads, validation=True, **trace_kw)
         A = A_star + rd["absorbed"][0]
         Tn = dust_temperature(tree, A, lam, kabs, dnu, T_min, T_max, n_threads)
         mask = (hits + rd["hits"][0]) >= min_hits

@@ -81,6 +81,7 @@ struct rt_ctx {
   DevBuf small;        // ledgers + counter
   DevBuf scan_tmp;
   DevBuf dust_arrays;  // lambda, kappa_abs, dnu, temperature table
+  DevBuf lam;          // Lambda iteration: stored fields, previous T, hits
   std::vector<DevBuf> cdf;  // per dust source
   void* pinned = nullptr;
   size_t pinned_n = 0;
@@ -159,6 +160,7 @@ extern "C" void rt_ctx_destroy(rt_ctx* c) {
   c->small.release();
   c->scan_tmp.release();
   c->dust_arrays.release();
+  c->lam.release();
   for (auto& b : c->cdf) b.release();
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
@@ -557,6 +559,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.images = T.images;
     J.n_obs = T.obs ? T.obs->n_obs : 0;
     J.packet_log = p->packet_log_dev;
+    J.hits = p->hits_dev;
     J.ledger = led_dev + j;
     J.seed = p->seed;
     J.job_id = p->job;
@@ -709,9 +712,13 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   cfg.blocks = c->sm_count * occ;
   cfg.refill = launch_prm->refill_threshold > 0 ? launch_prm->refill_threshold : default_refill(precision, peel);
   if (cfg.refill > 32) cfg.refill = 32;
+  bool hits = false;
+  for (int j = 0; j < n_jobs; ++j) hits = hits || jobs[j].prm->hits_dev != nullptr;
+  if (hits && (peel || estimator != RT_EST_CONTINUOUS))
+    return fail(RT_ERR_INVALID, "hit counting needs rt_trace with the continuous estimator");
   CK(cudaEventRecord(c->ev_a, s));
   if (total > 0 && n_items > 0)
-    CK(launch_trace(precision, peel, estimator, reinterpret_cast<const JobDev*>(base + job_off[0]),
+    CK(launch_trace(precision, peel, estimator, hits, reinterpret_cast<const JobDev*>(base + job_off[0]),
                     reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, s));
   CK(cudaEventRecord(c->ev_b, s));
   std::vector<LedgerDev> hl(n_jobs);
@@ -862,4 +869,96 @@ extern "C" int rt_philox(rt_ctx* ctx, int64_t n, const uint32_t* ctr_dev, const 
   CK(launch_philox(n, ctr_dev, key_dev, out_dev, s));
   CK(cudaEventRecord(ctx->ev_b, s));
   return wait_event(ctx->ev_b, 3600.0);
+}
+
+// ------------------------------------------------------------------------
+// Lambda iteration (Eq. 2, Sect. 3.2)
+// ------------------------------------------------------------------------
+extern "C" int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* g, int n_src, const rt_source* src, const rt_optics* op,
+                                 const rt_dust* du, const rt_trace_params* prm, const rt_lambda_params* lp,
+                                 double* T_dev, rt_lambda_result* res, void* cuda_stream) {
+  if (!ctx || !g || !src || !op || !du || !prm || !lp || !T_dev || !res)
+    return fail(RT_ERR_INVALID, "rt_lambda_iterate: NULL argument");
+  if (lp->max_iter < 1 || lp->max_iter > 64) return fail(RT_ERR_INVALID, "rt_lambda_iterate: max_iter must be 1..64");
+  if (lp->dust_packets_per_bin <= 0 && lp->dust_packets_total <= 0)
+    return fail(RT_ERR_INVALID, "rt_lambda_iterate: set dust_packets_total or dust_packets_per_bin");
+  int rc = check_optics(op);
+  if (rc) return rc;
+  rc = check_dust(du, op->n_lambda);
+  if (rc) return rc;
+  memset(res, 0, sizeof *res);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  const long long nc = g->n_cells;
+  const size_t fb = sizeof(double) * (size_t)nc;
+  rc = ctx->lam.ensure(3 * fb + sizeof(unsigned int) * (size_t)nc + 1024);
+  if (rc) return rc;
+  char* base = reinterpret_cast<char*>(ctx->lam.p);
+  double* A_star = reinterpret_cast<double*>(base);
+  double* A = reinterpret_cast<double*>(base + fb);
+  double* T_prev = reinterpret_cast<double*>(base + 2 * fb);
+  unsigned int* hits = reinterpret_cast<unsigned int*>(base + 3 * fb);
+  double* scal = reinterpret_cast<double*>(base + 3 * fb + ((sizeof(unsigned int) * (size_t)nc + 255) / 256) * 256);
+  CK(cudaMemsetAsync(A_star, 0, fb, s));
+  CK(cudaMemsetAsync(hits, 0, sizeof(unsigned int) * (size_t)nc, s));
+  const double to = prm->timeout_s > 0 ? prm->timeout_s : 3600.0;
+
+  // constant sources, traced once and stored (Sect. 3.2)
+  rt_trace_params sp = *prm;
+  sp.per_lambda = 0;
+  sp.hits_dev = hits;
+  sp.packet_log_dev = nullptr;
+  TraceArgs TS{g, n_src, src, op, &sp, nullptr, nullptr, A_star};
+  rc = run_jobs(ctx, 1, &TS, &res->source_ledger, s, &sp);
+  if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
+
+  const int n_table = 1024;
+  auto solve = [&](const double* absorbed) -> int {
+    double *lam, *kab, *dnu, *tab;
+    int r = upload_dust(ctx, du, n_table, &lam, &kab, &dnu, &tab, s);
+    if (r) return r;
+    CK(dust_table(lam, kab, dnu, du->n_lambda, du->T_min, du->T_max, n_table, tab, s));
+    CK(dust_temperature(absorbed, 1, nc, g->child, g->rho64, g->level, g->h0, lam, kab, dnu, du->n_lambda, du->T_min,
+                        du->T_max, tab, n_table, T_dev, s));
+    return RT_OK;
+  };
+  rc = solve(A_star);
+  if (rc) return rc;
+
+  // dust re-emission: same streams every iteration (key iter = params.iter + 1)
+  rt_source ds;
+  memset(&ds, 0, sizeof ds);
+  ds.kind = RT_SRC_DUST;
+  ds.T_dev = T_prev;
+  ds.dust = du;
+  rt_trace_params dp = *prm;
+  dp.per_lambda = 0;
+  dp.iter = prm->iter + 1;
+  dp.packets = nullptr;
+  dp.packet_log_dev = nullptr;
+  dp.packets_per_bin = lp->dust_packets_per_bin > 0 ? lp->dust_packets_per_bin : 0;
+  dp.packets_total = lp->dust_packets_per_bin > 0 ? 0 : lp->dust_packets_total;
+  for (int it = 1; it <= lp->max_iter; ++it) {
+    CK(cudaMemcpyAsync(T_prev, T_dev, fb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A, A_star, fb, cudaMemcpyDeviceToDevice, s));
+    dp.hits_dev = it == 1 ? hits : nullptr;
+    TraceArgs TD{g, 1, &ds, op, &dp, nullptr, nullptr, A};
+    rc = run_jobs(ctx, 1, &TD, &res->dust_ledger, s, &dp);
+    if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
+    rc = solve(A);
+    if (rc) return rc;
+    CK(max_rel_change(T_dev, T_prev, hits, g->child, nc, lp->min_hits, scal, s));
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, scal, sizeof v, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev_c, s));
+    rc = wait_event(ctx->ev_c, to);
+    if (rc) return rc;
+    res->history[it - 1] = v;
+    res->n_iter = it;
+    if (v < lp->tol) break;
+  }
+  res->ms = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return RT_OK;
 }

@@ -162,6 +162,30 @@ cudaError_t dust_emission(const double* T, long long n_cells, const uint32_t* ch
   return cudaGetLastError();
 }
 
+__global__ void max_rel_change_kernel(const double* __restrict__ T, const double* __restrict__ Tp,
+                                      const unsigned int* __restrict__ hits, const uint32_t* __restrict__ child,
+                                      long long n, double min_hits, double* out) {
+  double m = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (child[i] || (hits && (double)hits[i] < min_hits)) continue;
+    const double tp = Tp[i];
+    if (tp > 0.0) m = fmax(m, fabs(T[i] - tp) / tp);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  // non-negative doubles order like their bit patterns
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t max_rel_change(const double* T, const double* T_prev, const unsigned int* hits, const uint32_t* child,
+                           long long n, double min_hits, double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  max_rel_change_kernel<<<1024, 256, 0, s>>>(T, T_prev, hits, child, n, min_hits, out);
+  return cudaGetLastError();
+}
+
 __global__ void row_sum_kernel(const double* __restrict__ data, long long n, double* __restrict__ out) {
   const long long row = blockIdx.y;
   double v = 0.0;

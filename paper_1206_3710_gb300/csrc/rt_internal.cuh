@@ -72,6 +72,7 @@ struct JobDev {
   double rr_wmin, rr_p;
   long long step_limit;
   double peel_tau_max;
+  unsigned int* hits;  // optional deposits per cell
 };
 
 // one (job, source) work item: a contiguous range of the global package counter
@@ -101,7 +102,7 @@ struct LaunchCfg {
 };
 
 // launch the persistent tracer over n_items items of total packages
-cudaError_t launch_trace(int precision, bool peel, int estimator, const JobDev* jobs_dev,
+cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev,
                          long long total, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm);
@@ -143,6 +144,9 @@ cudaError_t dust_temperature(const double* absorbed, int n_bins, long long n_cel
 cudaError_t dust_emission(const double* T, long long n_cells, const uint32_t* child, const double* rho64,
                           const uint8_t* level, double h0, const double* lam_um, const double* kabs,
                           const double* dnu, int nl, double* emission, cudaStream_t s);
+// max over leaves with hits >= min_hits of |T - T_prev| / T_prev into *out
+cudaError_t max_rel_change(const double* T, const double* T_prev, const unsigned int* hits, const uint32_t* child,
+                           long long n, double min_hits, double* out, cudaStream_t s);
 // per-row sums of rows x n (f64) into out[rows] (device)
 cudaError_t row_sums_f64(const double* data, int n_rows, long long n, double* out, cudaStream_t s);
 // inclusive prefix sums of n_rows rows of length n (f64), in place

@@ -220,7 +220,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     cfg.block = block;
     cfg.blocks = sms * occ;
     cfg.refill = p->refill_threshold > 0 ? (p->refill_threshold > 32 ? 32 : p->refill_threshold) : 8;
-    if (launch_trace(p->precision, false, p->estimator, reinterpret_cast<const JobDev*>(dev + o_job),
+    if (launch_trace(p->precision, false, p->estimator, false, reinterpret_cast<const JobDev*>(dev + o_job),
                      reinterpret_cast<const ItemDev*>(dev + o_item), n_items,
                      reinterpret_cast<unsigned long long*>(dev + o_cnt), total, cfg, st) != cudaSuccess)
       return restore(set_error(RT_ERR_CUDA, "rt_trace_noalloc: kernel launch failed"));

@@ -425,7 +425,7 @@ struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? RT_FP32_MIN_BLOCKS : 2;
 };
 
-template <typename R, bool PEEL, int EST>
+template <typename R, bool PEEL, int EST, bool HITS>
 __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const JobDev* __restrict__ jobs,
                                                                          const ItemDev* __restrict__ items,
                                                                          int n_items,
@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   R dx = R(0), dy = R(0), dz = R(1), ix = R(0), iy = R(0), iz = R(0);
   R W = R(0), tau = R(0), taup = R(0), pkt_abs = R(0), kext = R(0), alb = R(0), tau_cut = R(0);
   double* absb = nullptr;
+  unsigned int* hitp = nullptr;
   uint32_t step_limit = 0u, ncross = 0u, npeel = 0u;
 
   // after a scattering (and its peel-off): new direction from the phase
@@ -541,6 +542,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           alb = Num<R>::alb(B);
           C.gpar[t] = Num<R>::gg(B);
           absb = J.absorbed ? J.absorbed + (long long)(J.abs_bins > 1 ? bin : 0) * J.n_cells : nullptr;
+          if (HITS) hitp = J.hits;
           const R W0 = (R)I.W0[bin];
           C.W0[t] = W0;
           W = W0;
@@ -688,6 +690,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
                 if (dep > R(0)) {
                   pkt_abs += dep;
                   if (absb) atomicAdd(absb + g.idx, widen(dep));
+                  if (HITS && hitp) atomicAdd(hitp + g.idx, 1u);
                 }
               }
             } else {
@@ -931,24 +934,32 @@ __global__ void philox_kernel(long long n, const uint32_t* __restrict__ ctr, con
 // ------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------
-template <typename R, bool PEEL, int EST>
+template <typename R, bool PEEL, int EST, bool HITS>
 static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_items, unsigned long long* counter,
                             long long total, const LaunchCfg& cfg, cudaStream_t s) {
-  trace_kernel<R, PEEL, EST><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill);
+  trace_kernel<R, PEEL, EST, HITS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill);
   return cudaGetLastError();
 }
 
 template <typename R, int EST>
 static cudaError_t launch_pe(bool peel, const JobDev* jobs, const ItemDev* items, int n_items,
                              unsigned long long* counter, long long total, const LaunchCfg& cfg, cudaStream_t s) {
-  return peel ? launch_t<R, true, EST>(jobs, items, n_items, counter, total, cfg, s)
-              : launch_t<R, false, EST>(jobs, items, n_items, counter, total, cfg, s);
+  return peel ? launch_t<R, true, EST, false>(jobs, items, n_items, counter, total, cfg, s)
+              : launch_t<R, false, EST, false>(jobs, items, n_items, counter, total, cfg, s);
 }
 
-cudaError_t launch_trace(int precision, bool peel, int estimator, const JobDev* jobs_dev, const ItemDev* items_dev,
-                         int n_items, unsigned long long* counter_dev, long long total, const LaunchCfg& cfg,
-                         cudaStream_t s) {
+// hit counting exists for the continuous estimator without peel-off (the
+// Lambda iteration's noise mask)
+cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
+                         const ItemDev* items_dev, int n_items, unsigned long long* counter_dev, long long total,
+                         const LaunchCfg& cfg, cudaStream_t s) {
   const bool an = estimator == RT_EST_ANALOG;
+  if (hits) {
+    if (peel || an) return cudaErrorInvalidValue;
+    return precision == 64
+               ? launch_t<double, false, RT_EST_CONTINUOUS, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
+               : launch_t<float, false, RT_EST_CONTINUOUS, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
+  }
   if (precision == 64)
     return an ? launch_pe<double, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
               : launch_pe<double, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
@@ -958,7 +969,7 @@ cudaError_t launch_trace(int precision, bool peel, int estimator, const JobDev* 
 
 template <typename R, bool PEEL>
 static cudaError_t occ_t(int block, int* n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false>, block, 0);
 }
 
 cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm) {

@@ -23,7 +23,7 @@ SOURCE_KINDS = {"point": RT_SRC_POINT, "external": RT_SRC_EXTERNAL, "dust": RT_S
 
 EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "rt_build_grid", "rt_grid_get_info",
             "rt_grid_free", "rt_trace", "rt_peel", "rt_dust_temperature", "rt_dust_emission", "rt_walk",
-            "rt_philox", "rt_trace_noalloc"]
+            "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate"]
 
 
 class RtError(RuntimeError):
@@ -66,7 +66,7 @@ class rt_trace_params(C.Structure):
                 ("peel_tau_max", C.c_double), ("per_lambda", C.c_int), ("packets_per_bin", C.c_int64),
                 ("packets", C.POINTER(C.c_int64)), ("packets_total", C.c_int64), ("packet_log_dev", C.c_void_p),
                 ("timeout_s", C.c_double), ("block_size", C.c_int), ("refill_threshold", C.c_int),
-                ("blocks_per_sm", C.c_int)]
+                ("blocks_per_sm", C.c_int), ("hits_dev", C.c_void_p)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
@@ -82,6 +82,16 @@ class rt_ledger(C.Structure):
 
     def as_dict(self):
         return {n: getattr(self, n) for n in LEDGER_FIELDS}
+
+
+class rt_lambda_params(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("tol", C.c_double), ("min_hits", C.c_double),
+                ("dust_packets_total", C.c_int64), ("dust_packets_per_bin", C.c_int64)]
+
+
+class rt_lambda_result(C.Structure):
+    _fields_ = [("n_iter", C.c_int), ("history", C.c_double * 64), ("source_ledger", rt_ledger),
+                ("dust_ledger", rt_ledger), ("ms", C.c_double)]
 
 
 class rt_observers(C.Structure):
@@ -120,6 +130,9 @@ def lib():
     L.rt_philox.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
     L.rt_trace_noalloc.argtypes = [vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics),
                                    C.POINTER(rt_trace_params), vp, C.POINTER(rt_ledger), vp]
+    L.rt_lambda_iterate.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics), C.POINTER(rt_dust),
+                                    C.POINTER(rt_trace_params), C.POINTER(rt_lambda_params), vp,
+                                    C.POINTER(rt_lambda_result), vp]
     for name in EXPORTED:
         if name not in ("rt_ctx_destroy", "rt_grid_free", "rt_last_error", "rt_version"):
             getattr(L, name).restype = C.c_int
@@ -256,7 +269,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
                 estimator: int = RT_EST_CONTINUOUS, rr_wmin: float = 0.0, rr_p: float = 0.9, step_limit: int = 0,
                 peel_tau_max: float = 0.0, per_lambda: bool = True, packets_per_bin: int = 0, packets=None,
                 packets_total: int = 0, packet_log=None, timeout_s: float = 0.0, block_size: int = 0,
-                refill_threshold: int = 0, blocks_per_sm: int = 0) -> rt_trace_params:
+                refill_threshold: int = 0, blocks_per_sm: int = 0, hits=None) -> rt_trace_params:
     p = rt_trace_params()
     p.seed, p.job, p.iter = int(seed), int(job), int(iter_)
     p.precision, p.estimator = int(precision), int(estimator)
@@ -268,6 +281,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
     p.packet_log_dev = _ptr(packet_log)
     p.timeout_s = float(timeout_s)
     p.block_size, p.refill_threshold, p.blocks_per_sm = int(block_size), int(refill_threshold), int(blocks_per_sm)
+    p.hits_dev = _ptr(hits)
     return p
 
 
@@ -335,6 +349,25 @@ def rt_dust_emission(ctx: Context, grid: Grid, T, lambda_um, kappa_abs, dnu, emi
     _check(lib().rt_dust_emission(ctx.handle, grid.handle, _ptr(T), C.byref(d), _ptr(emission),
                                   tot.ctypes.data_as(C.c_void_p), _stream(stream)))
     return tot
+
+
+def rt_lambda_iterate(ctx: Context, grid: Grid, sources, optics, T_out, *, max_iter: int = 30, tol: float = 1e-3,
+                      min_hits: float = 1000.0, dust_packets_total: int = 0, dust_packets_per_bin: int = 0,
+                      T_min: float = 2.7, T_max: float = 3000.0, stream=None, **params) -> dict:
+    """Lambda iteration (Eq. 2) on the device; returns iterations, history and ledgers."""
+    keep = _Keep()
+    src = make_sources(sources, len(optics.kappa_ext), keep)
+    op = make_optics(optics, keep)
+    kabs = (1.0 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
+    du = make_dust(optics.lambda_um, kabs, optics.dnu, T_min, T_max, keep)
+    prm = make_params(keep, **params)
+    lp = rt_lambda_params(max_iter=int(max_iter), tol=float(tol), min_hits=float(min_hits),
+                          dust_packets_total=int(dust_packets_total), dust_packets_per_bin=int(dust_packets_per_bin))
+    res = rt_lambda_result()
+    _check(lib().rt_lambda_iterate(ctx.handle, grid.handle, len(sources), src, C.byref(op), C.byref(du), C.byref(prm),
+                                   C.byref(lp), _ptr(T_out), C.byref(res), _stream(stream)))
+    return dict(n_iter=res.n_iter, history=[res.history[i] for i in range(res.n_iter)],
+                source_ledger=res.source_ledger.as_dict(), dust_ledger=res.dust_ledger.as_dict(), ms=res.ms)
 
 
 def rt_walk(ctx: Context, grid: Grid, origins, dirs, precision: int, max_seg: int, cells, lengths, counts,

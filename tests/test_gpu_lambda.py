@@ -1,0 +1,92 @@
+"""GPU parity for the Lambda iteration (Eq. 2, Sect. 3.2) and the hit counter
+that drives its stop rule."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1206_3710_gb300 import synth  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def rt():
+    from paper_1206_3710_gb300 import build
+    build.build()
+    from paper_1206_3710_gb300 import rt as _rt
+    return _rt
+
+
+@pytest.fixture(scope="module")
+def ctx(rt):
+    return rt.Context(0)
+
+
+def _star_model(tau_scale, n=8, n_lambda=12):
+    L = 20 * synth.AU_CM
+    rho = 1e-18
+    desc = synth.random_refined_tree((n,) * 3, (L,) * 3, 1, 0.2, 3, rho_fn=lambda l, x, y, z: np.full(x.size, rho))
+    lam = synth.log_lambda_grid(n_lambda)
+    optics = synth.powerlaw_dust(lam, tau_scale / (rho * L), 1.0)
+    star = synth.Source("point", bin_energy=synth.blackbody_star_bins(lam, 4000.0, 2 * synth.RSUN_CM),
+                        pos=(0.5 * L,) * 3)
+    return desc, optics, star
+
+
+def test_lambda_iteration_matches_oracle_fp64(rt, ctx, orc):
+    desc, optics, star = _star_model(1.0)
+    g = rt.Grid(ctx, desc)
+    T = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
+    npk = 3000
+    res = rt.rt_lambda_iterate(ctx, g, [star], optics, T, max_iter=3, tol=0.0, min_hits=0.0,
+                               dust_packets_per_bin=npk, seed=31, precision=64, packets_per_bin=npk)
+    tree = orc.Tree(desc)
+    T_o, hist_o = orc.lambda_iterate(tree, star, optics, npk, npk, seed=31, max_iter=3, tol=0.0, min_hits=0.0,
+                                     dust_per_bin=True)
+    assert res["n_iter"] == 3 and len(hist_o) == 3
+    _, leaf = tree.cells()
+    Tg = T.cpu().numpy()
+    np.testing.assert_allclose(Tg[leaf], T_o[leaf], rtol=1e-7)
+    assert np.all(Tg[~leaf] == 0)
+    np.testing.assert_allclose(res["history"], hist_o, rtol=1e-4)
+    # dust self-heating raised the temperatures above the star-only ones
+    assert res["dust_ledger"]["emitted"] > 0
+
+
+def test_hits_count_deposits(rt, ctx):
+    m = synth.tiny_clump()
+    g = rt.Grid(ctx, m.tree)
+    ab = torch.zeros((1, g.n_cells), dtype=torch.float64, device=DEV)
+    hits = torch.zeros(g.n_cells, dtype=torch.int32, device=DEV)
+    led = rt.rt_trace(ctx, g, m.sources, m.optics, ab, seed=3, precision=64, packets_per_bin=20000, hits=hits)
+    h = hits.cpu().numpy()
+    a = ab.cpu().numpy()[0]
+    np.testing.assert_array_equal(h > 0, a > 0)
+    # every positive-length segment with absorption is one deposit
+    assert h.sum() <= led["n_cross"] and h.sum() > 0.9 * led["n_cross"]
+    with pytest.raises(rt.RtError):  # not available with peel-off
+        im = torch.zeros((1, 1, 64, 64), dtype=torch.float64, device=DEV)
+        rt.rt_peel(ctx, g, m.sources, m.optics, m.observers, im, ab, seed=3, packets_per_bin=10, hits=hits)
+
+
+def test_lambda_iteration_small_disc_fp32(rt, ctx):
+    """The disc geometry of Sect. 4.2 at reduced size: the iteration runs to
+    its stop rule or cap, temperatures stay in range and the changes shrink."""
+    m = synth.disc(n_root=16, max_level=6, n_lambda=12, packets=0, target_cells=3e4, max_cells=200000)
+    g = rt.Grid(ctx, m.tree)
+    T = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
+    res = rt.rt_lambda_iterate(ctx, g, m.sources, m.optics, T, max_iter=30, tol=1e-3, min_hits=1000,
+                               dust_packets_total=400000, seed=5, precision=32, packets_total=400000,
+                               rr_wmin=1e-4, rr_p=0.9)
+    Tn = T.cpu().numpy()
+    leaf = m.tree.refine_flags == 0
+    assert np.all((Tn[leaf] >= 2.7) & (Tn[leaf] <= 3000.0))
+    hist = res["history"]
+    assert 1 <= res["n_iter"] <= 30
+    assert res["n_iter"] == 30 or hist[-1] < 1e-3
+    assert hist[-1] <= hist[0]
+    L = res["source_ledger"]
+    assert abs(L["emitted"] - L["absorbed"] - L["escaped"] - L["rr_loss"] + L["rr_gain"]) < 1e-4 * L["emitted"]
