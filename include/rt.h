@@ -203,6 +203,52 @@ int rt_peel(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
             double* images_dev, double* absorbed_dev, rt_ledger* ledger, void* cuda_stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batches: many models in one persistent launch                            */
+/* ------------------------------------------------------------------------ */
+/* One job = one model traced (and optionally peeled off) exactly as rt_trace
+ * / rt_peel would; a batch runs all jobs in one persistent launch that
+ * shares the package counter, so short and long jobs keep every SM busy.
+ * All jobs must use the same precision and estimator; the launch settings
+ * (block size, refill threshold) are taken from the first job's params. */
+typedef struct {
+  const rt_grid* grid;
+  int n_src;
+  const rt_source* src;
+  const rt_optics* optics;
+  const rt_trace_params* params;
+  const rt_observers* obs;  /* NULL: no images */
+  double* images_dev;       /* device, as rt_peel (added to) */
+  double* absorbed_dev;     /* device, as rt_trace (added to); may be NULL */
+} rt_job;
+
+/* One-shot batched launch; ledgers: host [n_jobs] (may be NULL). */
+int rt_trace_batch(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_ledger* ledgers, void* cuda_stream);
+
+/* A batch prepared once and replayed: the job table (and any dust emission
+ * tables, from the temperatures at creation) is uploaded into memory owned
+ * by the batch, and one CUDA graph holds the zeroing of every job's outputs,
+ * the ledger reset, the persistent tracer launch and the ledger read-back.
+ * rt_batch_run replays it on `cuda_stream` and waits (bounded). */
+typedef struct rt_batch rt_batch;
+int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_batch** out);
+int rt_batch_run(rt_batch* batch, rt_ledger* ledgers, double timeout_s, void* cuda_stream);
+void rt_batch_destroy(rt_batch* batch);
+
+/* Autotuner: runs the jobs with their package counts scaled by
+ * sample_fraction under every block size {128, 256} x refill threshold
+ * {2, 4, 8, 12, 16}, keeps the fastest (cell crossings per ms) as the
+ * context's default for this precision and peel-off mode, and zeroes the
+ * jobs' outputs afterwards.  rt_tune_save / rt_tune_load persist the choices
+ * per GPU architecture in a text file. */
+typedef struct {
+  int block_size, refill_threshold, blocks_per_sm;
+  double crossings_per_ms;
+} rt_tune_result;
+int rt_autotune(rt_ctx* ctx, int n_jobs, const rt_job* jobs, double sample_fraction, rt_tune_result* best);
+int rt_tune_save(const rt_ctx* ctx, const char* path);
+int rt_tune_load(rt_ctx* ctx, const char* path);
+
+/* ------------------------------------------------------------------------ */
 /* Dust (Sects. 3.2, 4)                                                      */
 /* ------------------------------------------------------------------------ */
 /* Per leaf: solve rho V 4 pi sum_i kappa_abs,i B_nu_i(T) dnu_i = A for T in

@@ -86,6 +86,12 @@ struct rt_ctx {
   void* pinned = nullptr;
   size_t pinned_n = 0;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr;
+  // launch defaults chosen by rt_autotune, per [FP64][peel-off]
+  struct Tuned {
+    bool set = false;
+    int block = 256, refill = 8, blocks_per_sm = 0;
+  } tuned[2][2];
+  int cc_major = 0, cc_minor = 0;
 };
 
 struct rt_grid {
@@ -142,6 +148,8 @@ extern "C" int rt_ctx_create(int device, rt_ctx** out) {
   rt_ctx* c = new rt_ctx();
   c->device = device;
   cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_a);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_b);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_c);
@@ -427,7 +435,12 @@ static void cross3(const double* a, const double* b, double* o) {
 // build the device job table for a list of jobs; returns total packages
 static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev* led_dev, cudaStream_t s,
                         Arena& A, std::vector<size_t>& job_off, size_t& items_off, int& n_items, long long& total,
-                        bool& any_peel, int& precision, int& estimator) {
+                        bool& any_peel, int& precision, int& estimator, DevBuf* table_buf = nullptr,
+                        std::vector<DevBuf>* cdf_bufs = nullptr) {
+  // device buffers for the table and the dust emission tables: the
+  // context's (one-shot calls) or a batch object's (replayed graphs)
+  DevBuf& table = table_buf ? *table_buf : c->table;
+  std::vector<DevBuf>& cdfv = cdf_bufs ? *cdf_bufs : c->cdf;
   // per job: validate, resolve packages per (source, bin), dust CDFs
   struct Pending {
     size_t ptr_field;  // offset of a pointer field to patch
@@ -437,6 +450,9 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
   std::vector<ItemDev> items;
   std::vector<std::vector<size_t>> item_patch;  // (bin_prefix, W0) arena offsets per item
   job_off.assign(n_jobs, 0);
+  // the kernel indexes the job records as one contiguous array: reserve it
+  // first, per-job data (bins, observers, items) follows
+  const size_t jobs_base = A.put(nullptr, sizeof(JobDev) * (size_t)n_jobs);
   total = 0;
   any_peel = false;
   precision = 0;
@@ -479,8 +495,8 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
         if (!S.T_dev) return fail(RT_ERR_INVALID, "job %d source %d: dust source needs T_dev", j, si);
         rc = check_dust(S.dust, nl);
         if (rc) return rc;
-        if ((int)c->cdf.size() <= dust_used) c->cdf.resize(dust_used + 1);
-        DevBuf& cb = c->cdf[dust_used++];
+        if ((int)cdfv.size() <= dust_used) cdfv.resize(dust_used + 1);
+        DevBuf& cb = cdfv[dust_used++];
         rc = cb.ensure(sizeof(double) * (size_t)nl * nc);
         if (rc) return rc;
         double *lam, *kab, *dnu, *tab;
@@ -568,7 +584,8 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.rr_p = p->rr_p;
     J.step_limit = p->step_limit > 0 ? p->step_limit : 100000000ll;
     J.peel_tau_max = p->peel_tau_max;
-    const size_t jo = A.put(&J, sizeof J);
+    const size_t jo = jobs_base + (size_t)j * sizeof(JobDev);
+    memcpy(A.h.data() + jo, &J, sizeof J);
     job_off[j] = jo;
     // bins
     std::vector<BinDev> bins(nl);
@@ -664,9 +681,9 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     patches.push_back({items_off + i * sizeof(ItemDev) + offsetof(ItemDev, W0), item_patch[i][1]});
   }
   // device copy, pointer fix-ups
-  int rc = c->table.ensure(A.h.size() + 256);
+  int rc = table.ensure(A.h.size() + 256);
   if (rc) return rc;
-  char* base = reinterpret_cast<char*>(c->table.p);
+  char* base = reinterpret_cast<char*>(table.p);
   for (const Pending& pp : patches) {
     void* v = base + pp.target;
     memcpy(A.h.data() + pp.ptr_field, &v, sizeof(void*));
@@ -682,6 +699,23 @@ static int default_refill(int precision, bool peel) {
   (void)precision;
   (void)peel;
   return 8;
+}
+
+// launch configuration: explicit params, else the autotuned default, else 256/8
+static int make_cfg(rt_ctx* c, int precision, bool peel, const rt_trace_params* lp, LaunchCfg* cfg) {
+  const rt_ctx::Tuned& t = c->tuned[precision == 64][peel ? 1 : 0];
+  cfg->block = lp->block_size > 0 ? lp->block_size : (t.set ? t.block : 256);
+  if (cfg->block % 32 || cfg->block > 256 || cfg->block < 32)
+    return fail(RT_ERR_INVALID, "block_size must be a multiple of 32 in 32..256");
+  int occ = 0;
+  CK(trace_occupancy(precision, peel, cfg->block, &occ));
+  if (occ < 1) occ = 1;
+  const int bps = lp->blocks_per_sm > 0 ? lp->blocks_per_sm : (t.set ? t.blocks_per_sm : 0);
+  if (bps > 0) occ = std::min(occ, bps);
+  cfg->blocks = c->sm_count * occ;
+  cfg->refill = lp->refill_threshold > 0 ? lp->refill_threshold : (t.set ? t.refill : default_refill(precision, peel));
+  if (cfg->refill > 32) cfg->refill = 32;
+  return RT_OK;
 }
 
 static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* ledgers, cudaStream_t s,
@@ -701,17 +735,9 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(c->table.p);
   CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + sizeof(unsigned long long), s));
-  // launch configuration
   LaunchCfg cfg;
-  cfg.block = launch_prm->block_size > 0 ? launch_prm->block_size : 256;
-  if (cfg.block % 32 || cfg.block > 256) return fail(RT_ERR_INVALID, "block_size must be a multiple of 32 and <= 256");
-  int occ = 0;
-  CK(trace_occupancy(precision, peel, cfg.block, &occ));
-  if (occ < 1) occ = 1;
-  if (launch_prm->blocks_per_sm > 0) occ = std::min(occ, launch_prm->blocks_per_sm);
-  cfg.blocks = c->sm_count * occ;
-  cfg.refill = launch_prm->refill_threshold > 0 ? launch_prm->refill_threshold : default_refill(precision, peel);
-  if (cfg.refill > 32) cfg.refill = 32;
+  rc = make_cfg(c, precision, peel, launch_prm, &cfg);
+  if (rc) return rc;
   bool hits = false;
   for (int j = 0; j < n_jobs; ++j) hits = hits || jobs[j].prm->hits_dev != nullptr;
   if (hits && (peel || estimator != RT_EST_CONTINUOUS))
@@ -961,4 +987,269 @@ extern "C" int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* g, int n_src, const
   }
   res->ms = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return RT_OK;
+}
+
+// ------------------------------------------------------------------------
+// batches: many models in one persistent launch
+// ------------------------------------------------------------------------
+static int jobs_to_args(int n_jobs, const rt_job* jobs, std::vector<TraceArgs>& out) {
+  if (n_jobs < 1 || !jobs) return fail(RT_ERR_INVALID, "batch: need at least one job");
+  out.resize(n_jobs);
+  for (int j = 0; j < n_jobs; ++j) {
+    const rt_job& J = jobs[j];
+    if (!J.grid || !J.params) return fail(RT_ERR_INVALID, "batch job %d: NULL grid or params", j);
+    out[j] = TraceArgs{J.grid, J.n_src, J.src, J.optics, J.params, J.obs, J.images_dev, J.absorbed_dev};
+  }
+  return RT_OK;
+}
+
+extern "C" int rt_trace_batch(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_ledger* ledgers, void* cuda_stream) {
+  if (!ctx) return fail(RT_ERR_INVALID, "rt_trace_batch: NULL context");
+  std::vector<TraceArgs> args;
+  int rc = jobs_to_args(n_jobs, jobs, args);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  if (ledgers) memset(ledgers, 0, sizeof(rt_ledger) * n_jobs);
+  return run_jobs(ctx, n_jobs, args.data(), ledgers, (cudaStream_t)cuda_stream, jobs[0].params);
+}
+
+struct rt_batch {
+  rt_ctx* ctx = nullptr;
+  int n_jobs = 0;
+  DevBuf table, small;
+  std::vector<DevBuf> cdf;
+  LedgerDev* host_led = nullptr;  // pinned, written by the graph
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+extern "C" void rt_batch_destroy(rt_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->ctx->device);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->host_led) cudaFreeHost(b->host_led);
+  b->table.release();
+  b->small.release();
+  for (auto& d : b->cdf) d.release();
+  delete b;
+}
+
+extern "C" int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_batch** out) {
+  if (!ctx || !out) return fail(RT_ERR_INVALID, "rt_batch_create: NULL argument");
+  *out = nullptr;
+  std::vector<TraceArgs> args;
+  int rc = jobs_to_args(n_jobs, jobs, args);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  rt_batch* b = new rt_batch();
+  b->ctx = ctx;
+  b->n_jobs = n_jobs;
+  auto bail = [&](int code) -> int {
+    rt_batch_destroy(b);
+    return code;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->host_led, sizeof(LedgerDev) * n_jobs);
+  if (e != cudaSuccess) return bail(fail(RT_ERR_CUDA, "rt_batch_create: %s", cudaGetErrorString(e)));
+  rc = b->small.ensure(sizeof(LedgerDev) * n_jobs + 256);
+  if (rc) return bail(rc);
+  LedgerDev* led = reinterpret_cast<LedgerDev*>(b->small.p);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(led + n_jobs);
+  Arena A;
+  std::vector<size_t> job_off;
+  size_t items_off = 0;
+  int n_items = 0, precision = 32, estimator = RT_EST_CONTINUOUS;
+  long long total = 0;
+  bool peel = false;
+  rc = build_tables(ctx, n_jobs, args.data(), led, b->cap, A, job_off, items_off, n_items, total, peel, precision,
+                    estimator, &b->table, &b->cdf);
+  if (rc) return bail(rc);
+  for (int j = 0; j < n_jobs; ++j)
+    if (args[j].prm->hits_dev) return bail(fail(RT_ERR_INVALID, "rt_batch_create: hit counting is not batched"));
+  e = cudaStreamSynchronize(b->cap);
+  if (e != cudaSuccess) return bail(fail(RT_ERR_CUDA, "rt_batch_create: %s", cudaGetErrorString(e)));
+  LaunchCfg cfg;
+  rc = make_cfg(ctx, precision, peel, jobs[0].params, &cfg);
+  if (rc) return bail(rc);
+  // capture: zero every job's outputs and the ledgers, run the tracer, read back
+  char* base = reinterpret_cast<char*>(b->table.p);
+  e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  for (int j = 0; j < n_jobs && e == cudaSuccess; ++j) {
+    const TraceArgs& T = args[j];
+    const int bins = T.prm->per_lambda ? T.optics->n_lambda : 1;
+    if (T.absorbed) e = cudaMemsetAsync(T.absorbed, 0, sizeof(double) * (size_t)bins * T.grid->n_cells, b->cap);
+    if (e == cudaSuccess && T.obs && T.images)
+      e = cudaMemsetAsync(T.images, 0, sizeof(double) * (size_t)T.obs->n_obs * bins * T.obs->nx * T.obs->ny, b->cap);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(led, 0, sizeof(LedgerDev) * n_jobs + sizeof(unsigned long long), b->cap);
+  if (e == cudaSuccess && total > 0 && n_items > 0)
+    e = launch_trace(precision, peel, estimator, false, reinterpret_cast<const JobDev*>(base + job_off[0]),
+                     reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, b->cap);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->host_led, led, sizeof(LedgerDev) * n_jobs, cudaMemcpyDeviceToHost, b->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+  b->graph = g;
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return bail(fail(RT_ERR_CUDA, "rt_batch_create: capture failed: %s",
+                     cudaGetErrorString(e != cudaSuccess ? e : e2)));
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) return bail(fail(RT_ERR_CUDA, "rt_batch_create: instantiate: %s", cudaGetErrorString(e)));
+  *out = b;
+  return RT_OK;
+}
+
+extern "C" int rt_batch_run(rt_batch* b, rt_ledger* ledgers, double timeout_s, void* cuda_stream) {
+  if (!b) return fail(RT_ERR_INVALID, "rt_batch_run: NULL batch");
+  std::lock_guard<std::mutex> lk(b->ctx->mu);
+  DeviceGuard dg(b->ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CK(cudaEventRecord(b->ev0, s));
+  CK(cudaGraphLaunch(b->exec, s));
+  CK(cudaEventRecord(b->ev1, s));
+  int rc = wait_event(b->ev1, timeout_s > 0 ? timeout_s : 3600.0);
+  if (rc) return rc;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+  int status = RT_OK;
+  for (int j = 0; j < b->n_jobs; ++j) {
+    const LedgerDev& L = b->host_led[j];
+    if (ledgers) {
+      rt_ledger& o = ledgers[j];
+      o.emitted = L.emitted; o.absorbed = L.absorbed; o.escaped = L.escaped; o.rr_gain = L.rr_gain;
+      o.rr_loss = L.rr_loss; o.killed = L.killed; o.peeled = L.peeled; o.n_packets = L.n_packets;
+      o.n_cross = L.n_cross; o.n_scatter = L.n_scatter; o.n_peel_cross = L.n_peel_cross; o.n_killed = L.n_killed;
+      o.n_peel_out = L.n_peel_out; o.status = L.status ? RT_ERR_STEP_LIMIT : RT_OK; o.kernel_ms = ms;
+    }
+    if (L.status) status = RT_ERR_STEP_LIMIT;
+  }
+  if (status != RT_OK) return fail(status, "rt_batch_run: some packages hit the step limit");
+  return RT_OK;
+}
+
+// ------------------------------------------------------------------------
+// autotuner: block size and refill threshold from short trial launches
+// ------------------------------------------------------------------------
+extern "C" int rt_autotune(rt_ctx* ctx, int n_jobs, const rt_job* jobs, double sample_fraction, rt_tune_result* best) {
+  if (!ctx || !best) return fail(RT_ERR_INVALID, "rt_autotune: NULL argument");
+  if (!(sample_fraction > 0.0 && sample_fraction <= 1.0)) return fail(RT_ERR_INVALID, "rt_autotune: fraction in (0,1]");
+  std::vector<TraceArgs> args;
+  int rc = jobs_to_args(n_jobs, jobs, args);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  // trial copies of the jobs with scaled package counts and private outputs
+  std::vector<rt_trace_params> prm(n_jobs);
+  std::vector<std::vector<int64_t>> pk(n_jobs);
+  bool peel = false;
+  for (int j = 0; j < n_jobs; ++j) {
+    prm[j] = *args[j].prm;
+    prm[j].packet_log_dev = nullptr;
+    prm[j].hits_dev = nullptr;
+    if (prm[j].packets_per_bin > 0) prm[j].packets_per_bin = std::max<int64_t>(1, (int64_t)(prm[j].packets_per_bin * sample_fraction));
+    else if (prm[j].packets_total > 0) prm[j].packets_total = std::max<int64_t>(1, (int64_t)(prm[j].packets_total * sample_fraction));
+    else if (prm[j].packets) {
+      const int nl = args[j].optics ? args[j].optics->n_lambda : 0;
+      pk[j].resize((size_t)args[j].n_src * nl);
+      for (size_t i = 0; i < pk[j].size(); ++i) pk[j][i] = (int64_t)(prm[j].packets[i] * sample_fraction);
+      prm[j].packets = pk[j].data();
+    }
+    args[j].prm = &prm[j];
+    peel = peel || args[j].obs != nullptr;
+  }
+  const int precision = prm[0].precision;
+  const int blocks[2] = {128, 256};
+  const int refills[5] = {2, 4, 8, 12, 16};
+  rt_tune_result res;
+  res.crossings_per_ms = -1.0;
+  res.block_size = 256;
+  res.refill_threshold = 8;
+  res.blocks_per_sm = 0;
+  std::vector<rt_ledger> led(n_jobs);
+  for (int bi = 0; bi < 2; ++bi)
+    for (int ri = 0; ri < 5; ++ri) {
+      for (int j = 0; j < n_jobs; ++j) {
+        prm[j].block_size = blocks[bi];
+        prm[j].refill_threshold = refills[ri];
+        prm[j].blocks_per_sm = 0;
+      }
+      // outputs are accumulated into the real buffers: zero them after tuning
+      rc = run_jobs(ctx, n_jobs, args.data(), led.data(), nullptr, &prm[0]);
+      if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
+      double cross = 0.0;
+      for (auto& L : led) cross += (double)L.n_cross + (double)L.n_peel_cross;
+      const double rate = led[0].kernel_ms > 0 ? cross / led[0].kernel_ms : 0.0;
+      if (rate > res.crossings_per_ms) {
+        res.crossings_per_ms = rate;
+        res.block_size = blocks[bi];
+        res.refill_threshold = refills[ri];
+      }
+    }
+  // clear what the trials accumulated
+  for (int j = 0; j < n_jobs; ++j) {
+    const TraceArgs& T = args[j];
+    const int bins = T.prm->per_lambda ? T.optics->n_lambda : 1;
+    if (T.absorbed) CK(cudaMemset(T.absorbed, 0, sizeof(double) * (size_t)bins * T.grid->n_cells));
+    if (T.obs && T.images)
+      CK(cudaMemset(T.images, 0, sizeof(double) * (size_t)T.obs->n_obs * bins * T.obs->nx * T.obs->ny));
+  }
+  rt_ctx::Tuned& t = ctx->tuned[precision == 64][peel ? 1 : 0];
+  t.set = true;
+  t.block = res.block_size;
+  t.refill = res.refill_threshold;
+  t.blocks_per_sm = 0;
+  *best = res;
+  return RT_OK;
+}
+
+extern "C" int rt_tune_save(const rt_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(RT_ERR_INVALID, "rt_tune_save: NULL argument");
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(RT_ERR_INVALID, "rt_tune_save: cannot open %s", path);
+  fprintf(f, "# arch precision peel block refill blocks_per_sm\n");
+  for (int p = 0; p < 2; ++p)
+    for (int q = 0; q < 2; ++q) {
+      const rt_ctx::Tuned& t = ctx->tuned[p][q];
+      if (t.set)
+        fprintf(f, "sm_%d%d %d %d %d %d %d\n", ctx->cc_major, ctx->cc_minor, p ? 64 : 32, q, t.block, t.refill,
+                t.blocks_per_sm);
+    }
+  fclose(f);
+  return RT_OK;
+}
+
+extern "C" int rt_tune_load(rt_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(RT_ERR_INVALID, "rt_tune_load: NULL argument");
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(RT_ERR_INVALID, "rt_tune_load: cannot open %s", path);
+  char line[256];
+  char arch[32];
+  char mine[32];
+  snprintf(mine, sizeof mine, "sm_%d%d", ctx->cc_major, ctx->cc_minor);
+  int loaded = 0;
+  while (fgets(line, sizeof line, f)) {
+    if (line[0] == '#') continue;
+    int prec, peel, block, refill, bps;
+    if (sscanf(line, "%31s %d %d %d %d %d", arch, &prec, &peel, &block, &refill, &bps) != 6) continue;
+    if (strcmp(arch, mine) != 0 || (prec != 32 && prec != 64) || (peel != 0 && peel != 1)) continue;
+    if (block < 32 || block > 256 || block % 32 || refill < 1 || refill > 32 || bps < 0) continue;
+    rt_ctx::Tuned& t = ctx->tuned[prec == 64][peel];
+    t.set = true;
+    t.block = block;
+    t.refill = refill;
+    t.blocks_per_sm = bps;
+    ++loaded;
+  }
+  fclose(f);
+  return loaded > 0 ? RT_OK : fail(RT_ERR_INVALID, "rt_tune_load: no entry for %s in %s", mine, path);
 }

@@ -23,7 +23,8 @@ SOURCE_KINDS = {"point": RT_SRC_POINT, "external": RT_SRC_EXTERNAL, "dust": RT_S
 
 EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "rt_build_grid", "rt_grid_get_info",
             "rt_grid_free", "rt_trace", "rt_peel", "rt_dust_temperature", "rt_dust_emission", "rt_walk",
-            "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate"]
+            "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate", "rt_trace_batch", "rt_batch_create",
+            "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load"]
 
 
 class RtError(RuntimeError):
@@ -99,6 +100,17 @@ class rt_observers(C.Structure):
                 ("nx", C.c_int), ("ny", C.c_int), ("fov", C.c_double * 2)]
 
 
+class rt_job(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("n_src", C.c_int), ("src", C.POINTER(rt_source)),
+                ("optics", C.POINTER(rt_optics)), ("params", C.POINTER(rt_trace_params)),
+                ("obs", C.POINTER(rt_observers)), ("images_dev", C.c_void_p), ("absorbed_dev", C.c_void_p)]
+
+
+class rt_tune_result(C.Structure):
+    _fields_ = [("block_size", C.c_int), ("refill_threshold", C.c_int), ("blocks_per_sm", C.c_int),
+                ("crossings_per_ms", C.c_double)]
+
+
 _lib = None
 
 
@@ -133,8 +145,16 @@ def lib():
     L.rt_lambda_iterate.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics), C.POINTER(rt_dust),
                                     C.POINTER(rt_trace_params), C.POINTER(rt_lambda_params), vp,
                                     C.POINTER(rt_lambda_result), vp]
+    L.rt_trace_batch.argtypes = [vp, C.c_int, C.POINTER(rt_job), C.POINTER(rt_ledger), vp]
+    L.rt_batch_create.argtypes = [vp, C.c_int, C.POINTER(rt_job), C.POINTER(vp)]
+    L.rt_batch_run.argtypes = [vp, C.POINTER(rt_ledger), C.c_double, vp]
+    L.rt_batch_destroy.argtypes = [vp]
+    L.rt_batch_destroy.restype = None
+    L.rt_autotune.argtypes = [vp, C.c_int, C.POINTER(rt_job), C.c_double, C.POINTER(rt_tune_result)]
+    L.rt_tune_save.argtypes = [vp, C.c_char_p]
+    L.rt_tune_load.argtypes = [vp, C.c_char_p]
     for name in EXPORTED:
-        if name not in ("rt_ctx_destroy", "rt_grid_free", "rt_last_error", "rt_version"):
+        if name not in ("rt_ctx_destroy", "rt_grid_free", "rt_last_error", "rt_version", "rt_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -390,3 +410,84 @@ class DustSource:
         self.T_dev, self.lambda_um, self.kappa_abs, self.dnu = T_dev, lambda_um, kappa_abs, dnu
         self.T_min, self.T_max = T_min, T_max
         self.bin_energy = None
+
+
+class Job:
+    """One model of a batched launch (the arguments of rt_trace / rt_peel)."""
+
+    def __init__(self, grid: Grid, sources, optics, absorbed=None, observers=None, images=None, **params):
+        self.grid, self.sources, self.optics, self.absorbed = grid, sources, optics, absorbed
+        self.observers, self.images, self.params = observers, images, params
+
+
+def _jobs_array(jobs, keep: _Keep):
+    arr = (rt_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        J = arr[i]
+        J.grid = j.grid.handle
+        J.n_src = len(j.sources)
+        src = make_sources(j.sources, len(j.optics.kappa_ext), keep)
+        op = make_optics(j.optics, keep)
+        prm = make_params(keep, **j.params)
+        keep.items += [src, op, prm]
+        J.src = C.cast(src, C.POINTER(rt_source))
+        J.optics = C.pointer(op)
+        J.params = C.pointer(prm)
+        if j.observers is not None:
+            ob = make_observers(j.observers, keep)
+            keep.items.append(ob)
+            J.obs = C.pointer(ob)
+        J.images_dev = _ptr(j.images)
+        J.absorbed_dev = _ptr(j.absorbed)
+    return arr
+
+
+def rt_trace_batch(ctx: Context, jobs, stream=None):
+    """All jobs in one persistent launch; returns one ledger per job."""
+    keep = _Keep()
+    arr = _jobs_array(jobs, keep)
+    leds = (rt_ledger * len(jobs))()
+    rc = lib().rt_trace_batch(ctx.handle, len(jobs), arr, leds, _stream(stream))
+    _check(rc, allow_step_limit=True)
+    return [leds[i].as_dict() for i in range(len(jobs))]
+
+
+class Batch:
+    """A batch whose launch is captured once in a CUDA graph and replayed."""
+
+    def __init__(self, ctx: Context, jobs):
+        keep = _Keep()
+        arr = _jobs_array(jobs, keep)
+        h = C.c_void_p()
+        _check(lib().rt_batch_create(ctx.handle, len(jobs), arr, C.byref(h)))
+        self.handle, self.n, self.ctx, self.jobs = h, len(jobs), ctx, jobs
+
+    def run(self, timeout_s: float = 0.0, stream=None):
+        leds = (rt_ledger * self.n)()
+        _check(lib().rt_batch_run(self.handle, leds, float(timeout_s), _stream(stream)), allow_step_limit=True)
+        return [leds[i].as_dict() for i in range(self.n)]
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.rt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def rt_autotune(ctx: Context, jobs, sample_fraction: float = 0.05) -> dict:
+    keep = _Keep()
+    arr = _jobs_array(jobs, keep)
+    res = rt_tune_result()
+    _check(lib().rt_autotune(ctx.handle, len(jobs), arr, float(sample_fraction), C.byref(res)))
+    return dict(block_size=res.block_size, refill_threshold=res.refill_threshold, blocks_per_sm=res.blocks_per_sm,
+                crossings_per_ms=res.crossings_per_ms)
+
+
+def rt_tune_save(ctx: Context, path: str) -> None:
+    _check(lib().rt_tune_save(ctx.handle, path.encode()))
+
+
+def rt_tune_load(ctx: Context, path: str) -> None:
+    _check(lib().rt_tune_load(ctx.handle, path.encode()))
