@@ -249,6 +249,48 @@ int rt_tune_save(const rt_ctx* ctx, const char* path);
 int rt_tune_load(rt_ctx* ctx, const char* path);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: continuous batching with admission by device-memory footprint    */
+/* ------------------------------------------------------------------------ */
+/* Models (density trees) are registered once by id; their grids are built on
+ * first use and stay resident on the device until memory is needed (least
+ * recently used first, never while a running job uses them).  A request is
+ * admitted, in arrival order, when its footprint -- its grid unless resident
+ * plus its accumulators -- fits the free part of hbm_budget.  max_slots
+ * dispatcher threads, each with its own context and stream, run every
+ * admitted request (up to max_batch_jobs, after waiting batch_window_ms for
+ * company) as one batched persistent launch; requests arriving meanwhile
+ * join the next launch of whichever slot frees first.  Results stay on the
+ * device (counted in the budget) until rt_server_fetch. */
+typedef struct {
+  size_t hbm_budget;
+  int max_slots;          /* 1..16 */
+  int max_batch_jobs;
+  double batch_window_ms;
+} rt_server_config;
+
+typedef struct {
+  uint64_t model_id;
+  int n_src;
+  const rt_source* src;   /* point, external or beam */
+  const rt_optics* optics;
+  const rt_trace_params* params;
+  const rt_observers* obs; /* NULL: no images */
+} rt_serve_job;
+
+int rt_server_create(rt_ctx* ctx, const rt_server_config* cfg, rt_server** out);
+/* Host tree copied; RT_ERR_INVALID if the id exists. */
+int rt_server_add_model(rt_server* srv, uint64_t model_id, const rt_tree_desc* tree);
+/* Queues a request (host data copied); RT_ERR_BUSY if it can never fit. */
+int rt_server_submit(rt_server* srv, const rt_serve_job* job, uint64_t* ticket);
+/* done = 1 once finished; latency_ms = submit to completion of its launch. */
+int rt_server_poll(rt_server* srv, uint64_t ticket, int* done, rt_ledger* ledger, double* latency_ms);
+int rt_server_wait(rt_server* srv, uint64_t ticket, double timeout_s);
+/* Copies results to host arrays (either may be NULL) and releases the job. */
+int rt_server_fetch(rt_server* srv, uint64_t ticket, double* absorbed_host, double* images_host);
+int rt_server_stats(rt_server* srv, size_t* used_bytes, int* queued, int* running);
+void rt_server_destroy(rt_server* srv);
+
+/* ------------------------------------------------------------------------ */
 /* Dust (Sects. 3.2, 4)                                                      */
 /* ------------------------------------------------------------------------ */
 /* Per leaf: solve rho V 4 pi sum_i kappa_abs,i B_nu_i(T) dnu_i = A for T in

@@ -191,6 +191,10 @@ static int wait_event(cudaEvent_t ev, double timeout_s) {
   }
 }
 
+namespace rtk {
+int ctx_device(const rt_ctx* c) { return c->device; }
+}  // namespace rtk
+
 // ------------------------------------------------------------------------
 // grid
 // ------------------------------------------------------------------------

@@ -133,6 +133,8 @@ cudaError_t validate_leaf_density(const double* rho64, const uint32_t* child, lo
 
 // record an error message for rt_last_error and return code
 int set_error(int code, const char* msg);
+// device of a context
+int ctx_device(const rt_ctx* c);
 
 // dust kernels
 cudaError_t dust_table(const double* lam_um, const double* kabs, const double* dnu, int nl, double Tmin,

@@ -24,7 +24,9 @@ SOURCE_KINDS = {"point": RT_SRC_POINT, "external": RT_SRC_EXTERNAL, "dust": RT_S
 EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "rt_build_grid", "rt_grid_get_info",
             "rt_grid_free", "rt_trace", "rt_peel", "rt_dust_temperature", "rt_dust_emission", "rt_walk",
             "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate", "rt_trace_batch", "rt_batch_create",
-            "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load"]
+            "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load", "rt_server_create",
+            "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
+            "rt_server_stats", "rt_server_destroy"]
 
 
 class RtError(RuntimeError):
@@ -106,6 +108,17 @@ class rt_job(C.Structure):
                 ("obs", C.POINTER(rt_observers)), ("images_dev", C.c_void_p), ("absorbed_dev", C.c_void_p)]
 
 
+class rt_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("max_batch_jobs", C.c_int),
+                ("batch_window_ms", C.c_double)]
+
+
+class rt_serve_job(C.Structure):
+    _fields_ = [("model_id", C.c_uint64), ("n_src", C.c_int), ("src", C.POINTER(rt_source)),
+                ("optics", C.POINTER(rt_optics)), ("params", C.POINTER(rt_trace_params)),
+                ("obs", C.POINTER(rt_observers))]
+
+
 class rt_tune_result(C.Structure):
     _fields_ = [("block_size", C.c_int), ("refill_threshold", C.c_int), ("blocks_per_sm", C.c_int),
                 ("crossings_per_ms", C.c_double)]
@@ -153,8 +166,18 @@ def lib():
     L.rt_autotune.argtypes = [vp, C.c_int, C.POINTER(rt_job), C.c_double, C.POINTER(rt_tune_result)]
     L.rt_tune_save.argtypes = [vp, C.c_char_p]
     L.rt_tune_load.argtypes = [vp, C.c_char_p]
+    L.rt_server_create.argtypes = [vp, C.POINTER(rt_server_config), C.POINTER(vp)]
+    L.rt_server_add_model.argtypes = [vp, C.c_uint64, C.POINTER(rt_tree_desc)]
+    L.rt_server_submit.argtypes = [vp, C.POINTER(rt_serve_job), C.POINTER(C.c_uint64)]
+    L.rt_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(rt_ledger), C.POINTER(C.c_double)]
+    L.rt_server_wait.argtypes = [vp, C.c_uint64, C.c_double]
+    L.rt_server_fetch.argtypes = [vp, C.c_uint64, vp, vp]
+    L.rt_server_stats.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rt_server_destroy.argtypes = [vp]
+    L.rt_server_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("rt_ctx_destroy", "rt_grid_free", "rt_last_error", "rt_version", "rt_batch_destroy"):
+        if name not in ("rt_ctx_destroy", "rt_grid_free", "rt_last_error", "rt_version", "rt_batch_destroy",
+                        "rt_server_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -491,3 +514,89 @@ def rt_tune_save(ctx: Context, path: str) -> None:
 
 def rt_tune_load(ctx: Context, path: str) -> None:
     _check(lib().rt_tune_load(ctx.handle, path.encode()))
+
+
+def _tree_struct(desc, keep: _Keep) -> rt_tree_desc:
+    d = rt_tree_desc()
+    d.root = (C.c_int * 3)(*desc.root)
+    d.box = (C.c_double * 3)(*desc.box)
+    d.n_levels = len(desc.n_refined)
+    d.n_refined = keep.dp(desc.n_refined, np.int64, C.c_int64)
+    d.refine_flags = keep.dp(desc.refine_flags, np.uint8, C.c_uint8)
+    d.density = keep.dp(desc.density, np.float64, C.c_double)
+    return d
+
+
+class Server:
+    """Job server: resident grids, admission by device-memory footprint,
+    continuous batching over `slots` streams (rt_server_* in librt)."""
+
+    def __init__(self, ctx: Context, hbm_budget: int, slots: int = 2, max_batch_jobs: int = 64,
+                 batch_window_ms: float = 1.0):
+        cfg = rt_server_config(hbm_budget=int(hbm_budget), max_slots=int(slots), max_batch_jobs=int(max_batch_jobs),
+                               batch_window_ms=float(batch_window_ms))
+        h = C.c_void_p()
+        _check(lib().rt_server_create(ctx.handle, C.byref(cfg), C.byref(h)))
+        self.handle, self.ctx = h, ctx
+        self.shapes = {}
+        self.cells = {}
+
+    def add_model(self, model_id: int, desc) -> None:
+        keep = _Keep()
+        d = _tree_struct(desc, keep)
+        _check(lib().rt_server_add_model(self.handle, int(model_id), C.byref(d)))
+        self.cells[int(model_id)] = int(desc.n_cells)
+
+    def submit(self, model_id: int, sources, optics, observers=None, **params) -> int:
+        keep = _Keep()
+        src = make_sources(sources, len(optics.kappa_ext), keep)
+        op = make_optics(optics, keep)
+        prm = make_params(keep, **params)
+        j = rt_serve_job(model_id=int(model_id), n_src=len(sources))
+        j.src = C.cast(src, C.POINTER(rt_source))
+        j.optics = C.pointer(op)
+        j.params = C.pointer(prm)
+        if observers is not None:
+            ob = make_observers(observers, keep)
+            keep.items.append(ob)
+            j.obs = C.pointer(ob)
+        t = C.c_uint64()
+        _check(lib().rt_server_submit(self.handle, C.byref(j), C.byref(t)))
+        bins = len(optics.kappa_ext) if params.get("per_lambda", True) else 1
+        img = None if observers is None else (observers.n_obs, bins, observers.ny, observers.nx)
+        self.shapes[t.value] = ((bins, self.cells[int(model_id)]), img)
+        return t.value
+
+    def poll(self, ticket: int):
+        done = C.c_int()
+        led = rt_ledger()
+        lat = C.c_double()
+        _check(lib().rt_server_poll(self.handle, ticket, C.byref(done), C.byref(led), C.byref(lat)),
+               allow_step_limit=True)
+        return bool(done.value), (led.as_dict() if done.value else None), lat.value
+
+    def wait(self, ticket: int, timeout_s: float = 600.0) -> None:
+        _check(lib().rt_server_wait(self.handle, ticket, float(timeout_s)), allow_step_limit=True)
+
+    def fetch(self, ticket: int):
+        ab_shape, img_shape = self.shapes.pop(ticket)
+        ab = np.zeros(ab_shape)
+        img = np.zeros(img_shape) if img_shape else None
+        _check(lib().rt_server_fetch(self.handle, ticket, ab.ctypes.data_as(C.c_void_p),
+                                     img.ctypes.data_as(C.c_void_p) if img is not None else None))
+        return ab, img
+
+    def stats(self):
+        used = C.c_size_t()
+        q = C.c_int()
+        r = C.c_int()
+        _check(lib().rt_server_stats(self.handle, C.byref(used), C.byref(q), C.byref(r)))
+        return dict(used_bytes=used.value, queued=q.value, running=r.value)
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.rt_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

@@ -53,10 +53,11 @@ def test_binding_struct_sizes_match_header(built_lib):
 #include <stddef.h>
 #include "rt.h"
 int main(void){
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rt_tree_desc), sizeof(rt_grid_info),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rt_tree_desc), sizeof(rt_grid_info),
          sizeof(rt_optics), sizeof(rt_dust), sizeof(rt_source), sizeof(rt_trace_params), sizeof(rt_ledger),
          sizeof(rt_observers), offsetof(rt_trace_params, packet_log_dev), offsetof(rt_trace_params, hits_dev),
-         sizeof(rt_lambda_params), sizeof(rt_lambda_result), sizeof(rt_job), sizeof(rt_tune_result));
+         sizeof(rt_lambda_params), sizeof(rt_lambda_result), sizeof(rt_job), sizeof(rt_tune_result),
+         sizeof(rt_server_config), sizeof(rt_serve_job));
   return 0;
 }
 """
@@ -70,7 +71,8 @@ int main(void){
             ctypes.sizeof(rt.rt_dust), ctypes.sizeof(rt.rt_source), ctypes.sizeof(rt.rt_trace_params),
             ctypes.sizeof(rt.rt_ledger), ctypes.sizeof(rt.rt_observers), rt.rt_trace_params.packet_log_dev.offset,
             rt.rt_trace_params.hits_dev.offset, ctypes.sizeof(rt.rt_lambda_params), ctypes.sizeof(rt.rt_lambda_result),
-            ctypes.sizeof(rt.rt_job), ctypes.sizeof(rt.rt_tune_result)]
+            ctypes.sizeof(rt.rt_job), ctypes.sizeof(rt.rt_tune_result), ctypes.sizeof(rt.rt_server_config),
+            ctypes.sizeof(rt.rt_serve_job)]
     assert vals == mine
 
 
