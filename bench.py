@@ -47,6 +47,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cloud", choices=["cloud", "disc", "batch", "serve"],
+                    help="cloud: the headline workload; disc/batch/serve: the other model families")
+    ap.add_argument("--iters", type=int, default=30, help="disc: Lambda-iteration cap")
+    ap.add_argument("--disc-packets", type=int, default=100_000_000)
+    ap.add_argument("--models", type=int, default=64, help="batch: models per launch")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-max-packets", type=float, default=1e7)
     ap.add_argument("--n-root", type=int, default=256)
     ap.add_argument("--levels", type=int, default=3)
     ap.add_argument("--n-lambda", type=int, default=20)
@@ -210,6 +218,10 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.workload != "cloud":
+        import bench_families
+        bench_families.run(a)
         return
     import torch
     import torch.distributed as dist

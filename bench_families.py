@@ -1,0 +1,224 @@
+"""Measurements of the other model families (bench.py --workload disc|batch|serve).
+
+* disc  -- circumstellar disc (64^3 root, <=10 levels, ~9e6 cells), 30
+           wavelengths, 1e8 packages per trace, Lambda iteration of the dust
+           temperature until max dT/T < 1e-3 (cells with >= 1e3 deposits) or
+           30 iterations (Sect. 4.2, Eq. 2).
+* batch -- 64 models (roots 32^3/64^3/128^3, 0-4 levels, clump or lognormal,
+           16 wavelengths, 1e5-1e7 packages) in one autotuned, graph-captured
+           FP32 launch, against one plain FP64 launch per model.
+* serve -- Poisson arrivals of jobs drawn from the model families; the job
+           server admits by device-memory footprint and batches continuously;
+           p50/p99 latency and packages/s against running the same jobs one
+           at a time.
+Each prints one JSON line.
+"""
+from __future__ import annotations
+
+import json
+import math
+import threading
+import time
+
+import numpy as np
+
+
+def _clock_start(local=0):
+    from bench import ClockSampler
+    c = ClockSampler(local)
+    c.start()
+    return c
+
+
+def run(a):
+    import torch
+    from paper_1206_3710_gb300 import rt, synth
+    torch.cuda.set_device(0)
+    ctx = rt.Context(0)
+    {"disc": run_disc, "batch": run_batch, "serve": run_serve}[a.workload](a, rt, synth, ctx, torch)
+
+
+def run_disc(a, rt, synth, ctx, torch):
+    t0 = time.perf_counter()
+    m = synth.disc(packets=a.disc_packets)
+    t_gen = time.perf_counter() - t0
+    g = rt.Grid(ctx, m.tree)
+    T = torch.zeros(g.n_cells, dtype=torch.float64, device="cuda")
+    kw = dict(seed=1003, precision=32, packets_total=a.disc_packets, rr_wmin=1e-4, rr_p=0.9)
+    clk = _clock_start()
+    res = rt.rt_lambda_iterate(ctx, g, m.sources, m.optics, T, max_iter=a.iters, tol=1e-3, min_hits=1000,
+                               dust_packets_total=a.disc_packets, **kw)
+    clocks = clk.stop()
+    src, dust = res["source_ledger"], res["dust_ledger"]
+    Tn = T.cpu().numpy()
+    leaf = m.tree.refine_flags == 0
+    line = {"metric": "Lambda iteration: cell crossings/s and iterations to max dT/T < 1e-3",
+            "workload": "disc", "n_cells": int(m.tree.n_cells), "n_levels": int(m.tree.n_levels),
+            "tau_cell_threshold": m.tau_cell_thr, "iterations": res["n_iter"], "history": res["history"],
+            "total_ms": res["ms"], "ms_per_iteration": res["ms"] / max(1, res["n_iter"] + 1),
+            "source_trace": {k: src[k] for k in ("n_packets", "n_cross", "n_scatter", "kernel_ms")},
+            "dust_trace_last": {k: dust[k] for k in ("n_packets", "n_cross", "n_scatter", "kernel_ms")},
+            "dust_cross_per_s": dust["n_cross"] / (dust["kernel_ms"] * 1e-3) if dust["kernel_ms"] else None,
+            "T_leaf_min_median_max": [float(Tn[leaf].min()), float(np.median(Tn[leaf])), float(Tn[leaf].max())],
+            "model_generation_s": t_gen, "clocks": clocks, "dtype": "f32 trace, f64 accumulators and solve"}
+    print(json.dumps(line))
+
+
+def _batch_jobs(rt, ctx, torch, models, precision):
+    grids, jobs = [], []
+    for i, m in enumerate(models):
+        g = rt.Grid(ctx, m.tree)
+        grids.append(g)
+        ab = torch.zeros((m.optics.n_lambda, g.n_cells), dtype=torch.float64, device="cuda")
+        jobs.append(rt.Job(g, m.sources, m.optics, ab, seed=m.seed, job=i, precision=precision,
+                           packets_per_bin=m.packets_per_bin, rr_wmin=1e-4, rr_p=0.9))
+    return grids, jobs
+
+
+def run_batch(a, rt, synth, ctx, torch):
+    t0 = time.perf_counter()
+    models = synth.batch_models(n_models=a.models, seed=1004)
+    t_gen = time.perf_counter() - t0
+    grids, jobs32 = _batch_jobs(rt, ctx, torch, models, 32)
+    tune = rt.rt_autotune(ctx, jobs32, sample_fraction=0.05)
+    batch = rt.Batch(ctx, jobs32)
+    for _ in range(max(1, a.warmup)):
+        batch.run()
+    torch.cuda.synchronize()
+    clk = _clock_start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    leds = None
+    for _ in range(a.steps):
+        leds = batch.run()
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms_batch = ev0.elapsed_time(ev1) / a.steps
+    pk = sum(x["n_packets"] for x in leds)
+    cross = sum(x["n_cross"] for x in leds)
+    res32 = [j.absorbed.sum().item() for j in jobs32]
+    # plain FP64 launches, one per model
+    _, jobs64 = _batch_jobs(rt, ctx, torch, models, 64)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    leds64 = []
+    for j in jobs64:
+        leds64.append(rt.rt_trace(ctx, j.grid, j.sources, j.optics, j.absorbed, **j.params))
+    torch.cuda.synchronize()
+    ms_plain = (time.perf_counter() - t1) * 1e3
+    res64 = [j.absorbed.sum().item() for j in jobs64]
+    rel = [abs(x / y - 1) for x, y in zip(res32, res64) if y > 0]
+    line = {"metric": "batched FP32 packets/s vs one plain FP64 launch per model",
+            "workload": "batch", "models": len(models), "packets_per_run": int(pk), "crossings_per_run": int(cross),
+            "batched_fp32": {"ms": ms_batch, "packets_per_s": pk / (ms_batch * 1e-3),
+                             "cross_per_s": cross / (ms_batch * 1e-3), "autotune": tune},
+            "plain_fp64_per_model": {"ms": ms_plain, "packets_per_s": pk / (ms_plain * 1e-3)},
+            "speedup": ms_plain / ms_batch,
+            "accuracy": {"max_rel_diff_total_absorbed": max(rel), "median": float(np.median(rel))},
+            "model_generation_s": t_gen, "clocks": clocks}
+    print(json.dumps(line))
+
+
+def _serve_library(synth):
+    lib = [synth.tiny_clump(),
+           synth.cloud(n_root=64, levels=3, n_lambda=30, seed=2101, packets_per_bin=0, n_pix=64),
+           synth.cloud(n_root=128, levels=3, n_lambda=30, seed=2102, packets_per_bin=0, n_pix=64),
+           synth.disc(n_root=32, max_level=7, n_lambda=30, packets=0, target_cells=3e5, max_cells=2_000_000)]
+    lib += synth.batch_models(n_models=4, seed=2103, n_lambda=30, roots=(32, 64), max_levels=3)
+    return lib
+
+
+def _optics_subset(synth, m, nl, rng):
+    """A job's wavelengths: nl bins of the model's grid (its dust law)."""
+    idx = np.sort(rng.choice(m.optics.n_lambda, size=nl, replace=False))
+    o = m.optics
+    opt = synth.Optics(o.lambda_um[idx], o.kappa_ext[idx], o.albedo[idx], o.g_hg[idx], o.dnu[idx])
+    src = []
+    for s in m.sources:
+        be = s.bin_energy[idx] if s.bin_energy is not None and len(s.bin_energy) == o.n_lambda else np.full(nl, 1.0 / nl)
+        src.append(synth.Source(s.kind, bin_energy=be, pos=s.pos))
+    return opt, src
+
+
+def run_serve(a, rt, synth, ctx, torch):
+    rng = np.random.default_rng(1005)
+    t0 = time.perf_counter()
+    library = _serve_library(synth)
+    t_gen = time.perf_counter() - t0
+    n_jobs = max(1, int(a.serve_seconds * a.serve_rate))
+    arrivals = np.cumsum(rng.exponential(1.0 / a.serve_rate, n_jobs))
+    jobs = []
+    for i in range(n_jobs):
+        mid = int(rng.integers(len(library)))
+        m = library[mid]
+        nl = int(rng.integers(1, min(30, m.optics.n_lambda) + 1))
+        opt, src = _optics_subset(synth, m, nl, rng)
+        total = math.exp(rng.uniform(math.log(1e5), math.log(a.serve_max_packets)))
+        ppb = max(1, int(total / nl))
+        jobs.append((arrivals[i], mid, src, opt, dict(seed=5000 + i, job=i, precision=32, packets_per_bin=ppb,
+                                                      rr_wmin=1e-4, rr_p=0.9, per_lambda=False)))
+    free = torch.cuda.mem_get_info()[0]
+    srv = rt.Server(ctx, hbm_budget=int(0.5 * free), slots=2, max_batch_jobs=64, batch_window_ms=2.0)
+    for mid, m in enumerate(library):
+        srv.add_model(mid, m.tree)
+    tickets = [None] * n_jobs
+    done_lat = [None] * n_jobs
+    leds = [None] * n_jobs
+
+    def collector():
+        for i in range(n_jobs):
+            while tickets[i] is None:
+                time.sleep(0.001)
+            srv.wait(tickets[i], 3600)
+            _, led, lat = srv.poll(tickets[i])
+            srv.fetch(tickets[i])
+            done_lat[i], leds[i] = lat, led
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    clk = _clock_start()
+    start = time.perf_counter()
+    for i, (t_arr, mid, src, opt, prm) in enumerate(jobs):
+        dt = start + t_arr - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets[i] = srv.submit(mid, src, opt, **prm)
+    th.join()
+    wall = time.perf_counter() - start
+    clocks = clk.stop()
+    srv.close()
+    lat = np.array(done_lat)
+    pk = sum(x["n_packets"] for x in leds)
+    # the same jobs one at a time, each with its own launch (no overlap, no batching)
+    grids = [rt.Grid(ctx, m.tree) for m in library]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for (t_arr, mid, src, opt, prm) in jobs:
+        ab = torch.zeros((1, grids[mid].n_cells), dtype=torch.float64, device="cuda")
+        rt.rt_trace(ctx, grids[mid], src, opt, ab, **prm)
+    torch.cuda.synchronize()
+    serial = time.perf_counter() - t1
+    offered = pk / float(arrivals[-1])
+    # capacity: the same jobs submitted at once (served back to back, batched)
+    srv = rt.Server(ctx, hbm_budget=int(0.5 * free), slots=2, max_batch_jobs=64, batch_window_ms=2.0)
+    for mid, m in enumerate(library):
+        srv.add_model(mid, m.tree)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ts = [srv.submit(mid, src, opt, **prm) for (t_arr, mid, src, opt, prm) in jobs]
+    for t in ts:
+        srv.wait(t, 3600)
+        srv.fetch(t)
+    burst = time.perf_counter() - t2
+    srv.close()
+    line = {"metric": "serving: p50/p99 job latency and packages/s under Poisson arrivals",
+            "workload": "serve", "jobs": n_jobs, "rate_per_s": a.serve_rate, "arrival_window_s": float(arrivals[-1]),
+            "packets_total": int(pk), "offered_packets_per_s": offered,
+            "served": {"wall_s": wall, "packets_per_s": pk / wall, "p50_ms": float(np.percentile(lat, 50)),
+                       "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())},
+            "one_at_a_time": {"busy_s": serial, "packets_per_s": pk / serial},
+            "burst_capacity": {"wall_s": burst, "packets_per_s": pk / burst},
+            "library": [m.name for m in library], "model_generation_s": t_gen, "clocks": clocks,
+            "packets_per_job": f"log-uniform 1e5..{a.serve_max_packets:.0e}", "wavelengths_per_job": "uniform 1..30"}
+    print(json.dumps(line))

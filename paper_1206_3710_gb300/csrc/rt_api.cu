@@ -401,7 +401,7 @@ static int check_dust(const rt_dust* du, int nl) {
 static int upload_dust(rt_ctx* c, const rt_dust* du, int n_table, double** lam, double** kab, double** dnu,
                        double** table, cudaStream_t s) {
   const int nl = du->n_lambda;
-  const size_t bytes = sizeof(double) * (3 * (size_t)nl + (size_t)n_table) + 256;
+  const size_t bytes = sizeof(double) * (3 * (size_t)nl + 3 * (size_t)n_table) + 256;
   int rc = c->dust_arrays.ensure(bytes);
   if (rc) return rc;
   rc = ensure_pinned(c, bytes);
@@ -820,7 +820,7 @@ extern "C" int rt_dust_temperature(rt_ctx* ctx, const rt_grid* g, const double* 
   std::lock_guard<std::mutex> lk(ctx->mu);
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  const int n_table = 1024;
+  const int n_table = 8192;
   double *lam, *kab, *dnu, *tab;
   rc = upload_dust(ctx, dust, n_table, &lam, &kab, &dnu, &tab, s);
   if (rc) return rc;
@@ -944,7 +944,7 @@ extern "C" int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* g, int n_src, const
   rc = run_jobs(ctx, 1, &TS, &res->source_ledger, s, &sp);
   if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
 
-  const int n_table = 1024;
+  const int n_table = 8192;
   auto solve = [&](const double* absorbed) -> int {
     double *lam, *kab, *dnu, *tab;
     int r = upload_dust(ctx, du, n_table, &lam, &kab, &dnu, &tab, s);

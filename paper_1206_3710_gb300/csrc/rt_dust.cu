@@ -5,9 +5,11 @@
 //
 // Per leaf the solve finds T with rho V E(T) = A, where
 //   E(T) = 4 pi sum_i kappa_abs,i B_nu(nu_i, T) dnu_i     (erg/s/g)
-// is the same for every cell.  A tabulated E on a log-T grid gives the
-// bracket; a safeguarded Newton iteration in FP64 on the exact sum
-// finishes to 1e-13 relative.
+// is the same for every cell.  It is tabulated once per call (log E and its
+// slope on a uniform log-T grid, FP64) and each leaf inverts the cubic
+// Hermite interpolant, so no leaf evaluates the Planck sum (GB300's FP64
+// pipe is narrow); where E underflows at the cold end the exact sum is
+// solved by safeguarded Newton instead.
 #include "rt_internal.cuh"
 
 namespace rtk {
@@ -45,13 +47,22 @@ __device__ __forceinline__ double emission_per_mass(const double* lam, const dou
   return FOUR_PI * s;
 }
 
+// Table of the emission per unit mass on a uniform grid in log T:
+// tab[3i] = log T_i, tab[3i+1] = log E(T_i), tab[3i+2] = d log E / d log T.
+// log E(log T) is smooth, so cubic Hermite interpolation between nodes
+// (spacing ~1e-3 in log T for 8192 nodes) inverts it to ~1e-13 in T.
 __global__ void table_kernel(const double* __restrict__ lam, const double* __restrict__ kabs,
                              const double* __restrict__ dnu, int nl, double Tmin, double Tmax, int n,
                              double* __restrict__ table) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double T = Tmin * exp(log(Tmax / Tmin) * (double)i / (double)(n - 1));
-  table[i] = emission_per_mass(lam, kabs, dnu, nl, T, nullptr);
+  const double x = log(Tmin) + log(Tmax / Tmin) * (double)i / (double)(n - 1);
+  const double T = exp(x);
+  double dE;
+  const double E = emission_per_mass(lam, kabs, dnu, nl, T, &dE);
+  table[3 * i] = x;
+  table[3 * i + 1] = E > 0.0 ? log(E) : -HUGE_VAL;
+  table[3 * i + 2] = E > 0.0 ? T * dE / E : 0.0;
 }
 
 cudaError_t dust_table(const double* lam, const double* kabs, const double* dnu, int nl, double Tmin, double Tmax,
@@ -59,6 +70,26 @@ cudaError_t dust_table(const double* lam, const double* kabs, const double* dnu,
   const int B = 128;
   table_kernel<<<(n_table + B - 1) / B, B, 0, s>>>(lam, kabs, dnu, nl, Tmin, Tmax, n_table, table);
   return cudaGetLastError();
+}
+
+// exact safeguarded Newton on E(T) = target inside [Tl, Th] (used where the
+// table has no finite logarithm, i.e. E underflows to 0 at the cold end)
+__device__ double solve_exact(const double* lam, const double* kabs, const double* dnu, int nl, double target,
+                              double Tl, double Th) {
+  double T = 0.5 * (Tl + Th);
+  for (int it = 0; it < 200; ++it) {
+    double dE;
+    const double E = emission_per_mass(lam, kabs, dnu, nl, T, &dE);
+    const double f = E - target;
+    if (f < 0.0) Tl = T;
+    else Th = T;
+    double Tn = dE > 0.0 ? T - f / dE : 0.5 * (Tl + Th);
+    if (!(Tn > Tl && Tn < Th)) Tn = 0.5 * (Tl + Th);
+    const double step = fabs(Tn - T);
+    T = Tn;
+    if (step <= 1e-14 * T || (Th - Tl) <= 1e-14 * Tl) break;
+  }
+  return T;
 }
 
 __global__ void temperature_kernel(const double* __restrict__ absorbed, int n_bins, long long n,
@@ -81,42 +112,43 @@ __global__ void temperature_kernel(const double* __restrict__ absorbed, int n_bi
     Tout[c] = Tmin;
     return;
   }
-  const double target = A / mass;
-  if (target <= table[0]) {
+  const double Y = log(A / mass);
+  if (!(Y > table[1])) {
     Tout[c] = Tmin;
     return;
   }
-  if (target >= table[n_table - 1]) {
+  if (Y >= table[3 * (n_table - 1) + 1]) {
     Tout[c] = Tmax;
     return;
   }
-  // bracket from the table (E is increasing in T)
+  // bracket: y_lo <= Y < y_hi (log E is increasing in log T)
   int lo = 0, hi = n_table - 1;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (table[mid] <= target) lo = mid;
+    if (table[3 * mid + 1] <= Y) lo = mid;
     else hi = mid;
   }
-  const double lr = log(Tmax / Tmin) / (double)(n_table - 1);
-  double Tl = Tmin * exp(lr * lo), Th = Tmin * exp(lr * hi);
-  if (lo == 0) Tl = Tmin;
-  if (hi == n_table - 1) Th = Tmax;
-  // start by log-log interpolation inside the bracket
-  double T = Tl * exp(log(Th / Tl) * log(target / table[lo]) / log(table[hi] / table[lo]));
-  if (!(T > Tl && T < Th)) T = 0.5 * (Tl + Th);
-  for (int it = 0; it < 100; ++it) {
-    double dE;
-    const double E = emission_per_mass(lam, kabs, dnu, nl, T, &dE);
-    const double f = E - target;
-    if (f < 0.0) Tl = T;
-    else Th = T;
-    double Tn = T - f / dE;
-    if (!(Tn > Tl && Tn < Th)) Tn = 0.5 * (Tl + Th);
-    const double step = fabs(Tn - T);
-    T = Tn;
-    if (step <= 1e-13 * T || (Th - Tl) <= 1e-13 * Tl) break;
+  const double x0 = table[3 * lo], y0 = table[3 * lo + 1], s0 = table[3 * lo + 2];
+  const double x1 = table[3 * hi], y1 = table[3 * hi + 1], s1 = table[3 * hi + 2];
+  if (!(y0 > -HUGE_VAL)) {
+    Tout[c] = solve_exact(lam, kabs, dnu, nl, A / mass, exp(x0), exp(x1));
+    return;
   }
-  Tout[c] = T;
+  // invert the cubic Hermite interpolant p(t), t in [0,1], by Newton
+  const double hx = x1 - x0;
+  const double m0 = s0 * hx, m1 = s1 * hx;
+  double t = (Y - y0) / (y1 - y0);
+  for (int it = 0; it < 6; ++it) {
+    const double t2 = t * t, t3 = t2 * t;
+    const double p = (2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + t) * m0 + (-2 * t3 + 3 * t2) * y1 + (t3 - t2) * m1;
+    const double dp = (6 * t2 - 6 * t) * y0 + (3 * t2 - 4 * t + 1) * m0 + (-6 * t2 + 6 * t) * y1 + (3 * t2 - 2 * t) * m1;
+    double tn = dp > 0.0 ? t - (p - Y) / dp : t;
+    tn = tn < 0.0 ? 0.0 : (tn > 1.0 ? 1.0 : tn);
+    const bool done = fabs(tn - t) < 1e-15;
+    t = tn;
+    if (done) break;
+  }
+  Tout[c] = exp(x0 + t * hx);
 }
 
 cudaError_t dust_temperature(const double* absorbed, int n_bins, long long n_cells, const uint32_t* child,

@@ -315,14 +315,18 @@ enum { L_EMIT = 0, L_ABS, L_ESC, L_RRG, L_RRL, L_KILL, L_PEEL, L_ND };
 enum { U_PK = 0, U_CROSS, U_SCAT, U_PCROSS, U_KILL, U_POUT, U_NU };
 
 // Energy ledger per warp, updated with shared-memory atomics at package
-// events (a few per package).  `tag` is the job it belongs to; a lane
-// working on another job (at job boundaries of a batched launch) books
-// directly to global memory.  Kept per warp rather than per thread: shared
-// memory taken here is L1 cache lost to the node loads.
+// events (a few per package).  Two slots per warp, each tagged with the job
+// it belongs to: in a batched launch a warp moves from job to job, and at
+// each refill a slot that no live lane still books to is flushed to the
+// job's global ledger and re-tagged to the job being emitted, so the old
+// job's packages finish in one slot while the new job's start in the other.
+// A lane whose job has no slot (a third job inside one warp) books directly
+// to global memory.  Kept per warp rather than per thread: shared memory
+// taken here is L1 cache lost to the node loads.
 struct WarpLedger {
-  double d[L_ND][8];
-  unsigned long long u[U_NU][8];
-  int tag[8];
+  double d[2][L_ND][8];
+  unsigned long long u[2][U_NU][8];
+  int tag[2][8];
 };
 
 // Cold per-lane state: touched at emission, scattering and peel-off
@@ -353,27 +357,32 @@ __device__ __forceinline__ R draw(ColdState<R>& C, int t) {
   return Num<R>::uni(draw_u32(C, t));
 }
 
+// the ledger's sums and counts are contiguous, in the order of L_* and U_*
+static_assert(offsetof(LedgerDev, peeled) == offsetof(LedgerDev, emitted) + 8 * L_PEEL, "ledger layout");
+static_assert(offsetof(LedgerDev, n_peel_out) == offsetof(LedgerDev, n_packets) + 8 * U_POUT, "ledger layout");
+__device__ __forceinline__ double* ledger_d(LedgerDev* L, int i) { return &L->emitted + i; }
+__device__ __forceinline__ unsigned long long* ledger_u(LedgerDev* L, int i) { return &L->n_packets + i; }
+
 __device__ __forceinline__ void book_d(WarpLedger& SL, const JobDev* jobs, int job, int wid, int i, double v) {
   if (v == 0.0) return;
-  if (SL.tag[wid] == job) {
-    atomicAdd(&SL.d[i][wid], v);
+  if (SL.tag[0][wid] == job) {
+    atomicAdd(&SL.d[0][i][wid], v);
+  } else if (SL.tag[1][wid] == job) {
+    atomicAdd(&SL.d[1][i][wid], v);
   } else {
-    LedgerDev* L = jobs[job].ledger;
-    double* dst[L_ND] = {&L->emitted, &L->absorbed, &L->escaped, &L->rr_gain, &L->rr_loss, &L->killed, &L->peeled};
-    atomicAdd(dst[i], v);
+    atomicAdd(ledger_d(jobs[job].ledger, i), v);
   }
 }
 
 __device__ __forceinline__ void book_u(WarpLedger& SL, const JobDev* jobs, int job, int wid, int i,
                                        unsigned long long v) {
   if (v == 0ull) return;
-  if (SL.tag[wid] == job) {
-    atomicAdd(&SL.u[i][wid], v);
+  if (SL.tag[0][wid] == job) {
+    atomicAdd(&SL.u[0][i][wid], v);
+  } else if (SL.tag[1][wid] == job) {
+    atomicAdd(&SL.u[1][i][wid], v);
   } else {
-    LedgerDev* L = jobs[job].ledger;
-    unsigned long long* dst[U_NU] = {&L->n_packets, &L->n_cross, &L->n_scatter, &L->n_peel_cross, &L->n_killed,
-                                     &L->n_peel_out};
-    atomicAdd(dst[i], v);
+    atomicAdd(ledger_u(jobs[job].ledger, i), v);
   }
 }
 
@@ -435,9 +444,9 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   __shared__ WarpLedger SL;
   __shared__ ColdState<R> C;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  if (lane < L_ND) SL.d[lane][wid] = 0.0;
-  if (lane < U_NU) SL.u[lane][wid] = 0ull;
-  if (lane == 0) SL.tag[wid] = -1;
+  if (lane < L_ND) SL.d[0][lane][wid] = SL.d[1][lane][wid] = 0.0;
+  if (lane < U_NU) SL.u[0][lane][wid] = SL.u[1][lane][wid] = 0ull;
+  if (lane < 2) SL.tag[lane][wid] = -1;
   C.job[t] = -1;
   __syncwarp();
 
@@ -496,23 +505,53 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       unsigned long long base = 0ull;
       if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(dead));
       base = __shfl_sync(FULL, base, leader);
+      const long long gi = (long long)base + __popc(dead & ((1u << lane) - 1u));
+      int lo = -1;
+      if (st == ST_DEAD && gi < total) {
+        lo = 0;
+        int hi = n_items - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (items[mid].pkt_begin <= gi) lo = mid;
+          else hi = mid - 1;
+        }
+      }
+      // the leader's package is the first one handed out: give its job a slot
+      const int nj = __shfl_sync(FULL, lo >= 0 ? items[lo].job : -1, leader);
+      if (nj >= 0 && SL.tag[0][wid] != nj && SL.tag[1][wid] != nj) {
+        const bool live = st == ST_TRACE || st == ST_PEEL;
+        const bool use0 = __any_sync(FULL, live && C.job[t] == SL.tag[0][wid]);
+        const bool use1 = __any_sync(FULL, live && C.job[t] == SL.tag[1][wid]);
+        const int sl = !use0 ? 0 : (!use1 ? 1 : -1);
+        if (sl >= 0) {
+          __syncwarp();
+          const int old = SL.tag[sl][wid];
+          if (old >= 0) {
+            LedgerDev* L = jobs[old].ledger;
+            if (lane < L_ND) {
+              const double v = SL.d[sl][lane][wid];
+              if (v != 0.0) atomicAdd(ledger_d(L, lane), v);
+              SL.d[sl][lane][wid] = 0.0;
+            } else if (lane < L_ND + U_NU) {
+              const unsigned long long v = SL.u[sl][lane - L_ND][wid];
+              if (v) atomicAdd(ledger_u(L, lane - L_ND), v);
+              SL.u[sl][lane - L_ND][wid] = 0ull;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) SL.tag[sl][wid] = nj;
+          __syncwarp();
+        }
+      }
       if (st == ST_DEAD) {
-        const long long gi = (long long)base + __popc(dead & ((1u << lane) - 1u));
-        if (gi >= total) {
+        if (lo < 0) {
           st = ST_DONE;
         } else {
           // ------------------------------------------------ emission (Sect. 2.3)
-          int lo = 0, hi = n_items - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (items[mid].pkt_begin <= gi) lo = mid;
-            else hi = mid - 1;
-          }
           const ItemDev& I = items[lo];
           const int job = I.job;
           const JobDev& J = jobs[job];
           C.job[t] = job;
-          if (SL.tag[wid] < 0) atomicCAS(&SL.tag[wid], -1, job);
           G.node = J.node;
           G.rho64 = J.rho64;
           G.rx = J.root[0];
@@ -852,18 +891,17 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
 
   // ------------------------------------------------------------ final ledger
   __syncwarp();
-  const int tag = SL.tag[wid];
-  if (tag >= 0 && lane == 0) {
-    LedgerDev* L = jobs[tag].ledger;
-    double* dd[L_ND] = {&L->emitted, &L->absorbed, &L->escaped, &L->rr_gain, &L->rr_loss, &L->killed, &L->peeled};
-    unsigned long long* du[U_NU] = {&L->n_packets, &L->n_cross, &L->n_scatter, &L->n_peel_cross, &L->n_killed,
-                                    &L->n_peel_out};
+  if (lane < 2) {
+    const int tag = SL.tag[lane][wid];
+    if (tag >= 0) {
+      LedgerDev* L = jobs[tag].ledger;
 #pragma unroll
-    for (int i = 0; i < L_ND; ++i)
-      if (SL.d[i][wid] != 0.0) atomicAdd(dd[i], SL.d[i][wid]);
+      for (int i = 0; i < L_ND; ++i)
+        if (SL.d[lane][i][wid] != 0.0) atomicAdd(ledger_d(L, i), SL.d[lane][i][wid]);
 #pragma unroll
-    for (int i = 0; i < U_NU; ++i)
-      if (SL.u[i][wid]) atomicAdd(du[i], SL.u[i][wid]);
+      for (int i = 0; i < U_NU; ++i)
+        if (SL.u[lane][i][wid]) atomicAdd(ledger_u(L, i), SL.u[lane][i][wid]);
+    }
   }
 }
 

@@ -449,6 +449,36 @@ def test_dust_temperature_parity(rt, ctx, orc):
     np.testing.assert_allclose(tot, eo.sum(axis=1), rtol=1e-10)   # summation order
 
 
+@pytest.mark.parametrize("n_lambda,T_min,T_max", [(3, 2.7, 3000.0), (5, 10.0, 2000.0), (64, 2.7, 3000.0)])
+def test_dust_temperature_parity_ranges(rt, ctx, orc, n_lambda, T_min, T_max):
+    """The temperature solve over the whole [T_min, T_max] range, with few
+    wavelength bins (where one bin's Wien tail dominates E(T) at the cold
+    end) and many: absorbed energies are set from temperatures drawn
+    log-uniformly, plus values beyond both ends."""
+    desc = synth.random_refined_tree((8, 8, 8), (4e16,) * 3, 1, 0.2, 9,
+                                     rho_fn=lambda l, x, y, z: np.full(x.size, 1e-20))
+    g = rt.Grid(ctx, desc)
+    tree = orc.Tree(desc)
+    lam = synth.log_lambda_grid(n_lambda)
+    kabs = 300.0 * (lam / 0.55) ** -1.8
+    dnu = synth.bin_dnu(lam)
+    _, leaf = tree.cells()
+    rng = np.random.default_rng(n_lambda)
+    T_true = np.exp(rng.uniform(np.log(T_min) - 0.3, np.log(T_max) + 0.3, desc.n_cells))
+    T_true[:4] = [T_min, T_max, T_min * (1 + 1e-9), T_max * (1 - 1e-9)]
+    # A from the oracle's own emission at T_true: rho V E(T) summed over bins
+    em = orc.dust_emission(tree, np.where(leaf, T_true, 0.0), lam, kabs, dnu)
+    A = em.sum(axis=0)
+    A[~leaf] = 0.0
+    T = _zeros(desc.n_cells)
+    rt.rt_dust_temperature(ctx, g, torch.from_numpy(A[None, :]).to(DEV), 1, lam, kabs, dnu, T, T_min=T_min,
+                           T_max=T_max)
+    To = orc.dust_temperature(tree, A, lam, kabs, dnu, T_min=T_min, T_max=T_max)
+    np.testing.assert_allclose(T.cpu().numpy(), To, rtol=1e-10)
+    inside = leaf & (T_true > T_min) & (T_true < T_max) & (A > 0)
+    np.testing.assert_allclose(To[inside], T_true[inside], rtol=1e-9)
+
+
 def test_fp64_dust_source_per_packet(rt, ctx, orc):
     L = 20 * synth.AU_CM
     desc = synth.random_refined_tree((6, 6, 6), (L,) * 3, 2, 0.3, 4,
