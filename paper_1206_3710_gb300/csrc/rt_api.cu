@@ -452,7 +452,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
   };
   std::vector<Pending> patches;
   std::vector<ItemDev> items;
-  std::vector<std::vector<size_t>> item_patch;  // (bin_prefix, W0) arena offsets per item
+  std::vector<std::vector<size_t>> item_patch;  // (bin_prefix, W0, W0f) arena offsets per item
   job_off.assign(n_jobs, 0);
   // the kernel indexes the job records as one contiguous array: reserve it
   // first, per-job data (bins, observers, items) follows
@@ -588,6 +588,13 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.rr_p = p->rr_p;
     J.step_limit = p->step_limit > 0 ? p->step_limit : 100000000ll;
     J.peel_tau_max = p->peel_tau_max;
+    J.rr_wmin_f = (float)p->rr_wmin;
+    J.rr_p_f = (float)p->rr_p;
+    J.peel_tau_max_f = (float)p->peel_tau_max;
+    double w0_max = 0.0;
+    for (size_t i = 0; i < pk.size(); ++i)
+      if (pk[i] > 0) w0_max = std::max(w0_max, energy[i] / (double)pk[i]);
+    J.led_shift = ledger_shift(w0_max, p->rr_wmin, p->rr_p);
     const size_t jo = jobs_base + (size_t)j * sizeof(JobDev);
     memcpy(A.h.data() + jo, &J, sizeof J);
     job_off[j] = jo;
@@ -657,12 +664,18 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
         const double n2 = std::sqrt(S.dir[0] * S.dir[0] + S.dir[1] * S.dir[1] + S.dir[2] * S.dir[2]);
         for (int a = 0; a < 3; ++a) I.dir[a] = S.dir[a] / n2;
       }
+      for (int a = 0; a < 3; ++a) {
+        I.posf[a] = (float)I.pos[a];
+        I.dirf[a] = (float)I.dir[a];
+      }
       std::vector<long long> pref(nl + 1, 0);
       std::vector<double> w0(nl, 0.0);
+      std::vector<float> w0f(nl, 0.0f);
       for (int b = 0; b < nl; ++b) {
         const long long np_ = pk[(size_t)si * nl + b];
         pref[b + 1] = pref[b] + np_;
         w0[b] = np_ > 0 ? energy[(size_t)si * nl + b] / (double)np_ : 0.0;
+        w0f[b] = (float)w0[b];
       }
       I.pkt_begin = total;
       I.pkt_end = total + pref[nl];
@@ -672,9 +685,10 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
       log_off += pref[nl];
       const size_t po = A.put(pref.data(), sizeof(long long) * (nl + 1));
       const size_t wo = A.put(w0.data(), sizeof(double) * nl);
+      const size_t wfo = A.put(w0f.data(), sizeof(float) * nl);
       if (pref[nl] == 0) continue;  // nothing to emit
       items.push_back(I);
-      item_patch.push_back({po, wo});
+      item_patch.push_back({po, wo, wfo});
     }
   }
   // items array
@@ -683,6 +697,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
   for (int i = 0; i < n_items; ++i) {
     patches.push_back({items_off + i * sizeof(ItemDev) + offsetof(ItemDev, bin_prefix), item_patch[i][0]});
     patches.push_back({items_off + i * sizeof(ItemDev) + offsetof(ItemDev, W0), item_patch[i][1]});
+    patches.push_back({items_off + i * sizeof(ItemDev) + offsetof(ItemDev, W0f), item_patch[i][2]});
   }
   // device copy, pointer fix-ups
   int rc = table.ensure(A.h.size() + 256);

@@ -11,6 +11,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include "rt.h"
 
 #define RT_MAX_OBS 16
@@ -73,6 +76,10 @@ struct JobDev {
   long long step_limit;
   double peel_tau_max;
   unsigned int* hits;  // optional deposits per cell
+  // f32 copies for the f32 tracer (GB300's FP64 pipe is narrow)
+  float rr_wmin_f, rr_p_f, peel_tau_max_f;
+  // the f32 tracer books ledger energies in 64-bit fixed point: value * 2^led_shift
+  int led_shift;
 };
 
 // one (job, source) work item: a contiguous range of the global package counter
@@ -88,7 +95,21 @@ struct ItemDev {
   const long long* bin_prefix;  // [n_lambda + 1] package prefix within the item
   const double* W0;             // [n_lambda]
   const double* cdf;            // dust: [n_lambda][n_cells] inclusive cumulative emission
+  const float* W0f;             // [n_lambda] f32 copy of W0
+  float posf[3], dirf[3];       // f32 copies of pos, dir
+  int pad2;
 };
+
+// Fixed-point scale of a job's ledger in the f32 tracer: the largest value a
+// single booking can carry is bounded by the largest package weight, times
+// the roulette survival gain; 40 fractional bits below that bound leave 24
+// bits of headroom for the sum of a warp's bookings.
+inline int ledger_shift(double w0_max, double rr_wmin, double rr_p) {
+  double bound = w0_max;
+  if (rr_wmin > 0.0 && rr_p < 1.0) bound *= std::max(1.0, rr_wmin / (1.0 - rr_p));
+  if (!(bound > 0.0) || !std::isfinite(bound)) return 0;
+  return 40 - (std::ilogb(bound) + 2);
+}
 
 // ------------------------------------------------------------------------
 // host-side helpers implemented in rt_trace.cu / rt_dust.cu / rt_grid.cu

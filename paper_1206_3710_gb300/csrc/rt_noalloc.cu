@@ -116,14 +116,15 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
       pk[s][b] = v;
     }
 
-  // scratch layout: ledger | counter | job | bins | items | prefixes | weights
+  // scratch layout: ledger | counter | job | bins | items | prefixes | weights (f64, f32)
   const size_t o_led = 0, o_cnt = sizeof(LedgerDev);
   const size_t o_job = align_up(o_cnt + sizeof(unsigned long long), 256);
   const size_t o_bin = align_up(o_job + sizeof(JobDev), 16);
   const size_t o_item = align_up(o_bin + sizeof(BinDev) * nl, 16);
   const size_t o_pref = align_up(o_item + sizeof(ItemDev) * n_src, 16);
   const size_t o_w0 = align_up(o_pref + sizeof(long long) * (nl + 1) * n_src, 16);
-  const size_t bytes = align_up(o_w0 + sizeof(double) * nl * n_src, 16);
+  const size_t o_w0f = align_up(o_w0 + sizeof(double) * nl * n_src, 16);
+  const size_t bytes = align_up(o_w0f + sizeof(float) * nl * n_src, 16);
   if (bytes > RT_NOALLOC_SCRATCH_BYTES)
     return set_error(RT_ERR_INVALID, "rt_trace_noalloc: job table exceeds the 64 KiB scratch");
 
@@ -157,6 +158,9 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
   J.rr_p = p->rr_p;
   J.step_limit = p->step_limit > 0 ? p->step_limit : 100000000ll;
   J.peel_tau_max = p->peel_tau_max;
+  J.rr_wmin_f = (float)p->rr_wmin;
+  J.rr_p_f = (float)p->rr_p;
+  J.peel_tau_max_f = (float)p->peel_tau_max;
   BinDev* B = reinterpret_cast<BinDev*>(host + o_bin);
   for (int b = 0; b < nl; ++b) {
     B[b].kext_d = op->kappa_ext[b] * J.h0;
@@ -169,15 +173,20 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
   ItemDev* I = reinterpret_cast<ItemDev*>(host + o_item);
   long long* pref = reinterpret_cast<long long*>(host + o_pref);
   double* w0 = reinterpret_cast<double*>(host + o_w0);
+  float* w0f = reinterpret_cast<float*>(host + o_w0f);
+  double w0_max = 0.0;
   long long total = 0;
   int n_items = 0;
   for (int s = 0; s < n_src; ++s) {
     long long* pr = pref + (size_t)s * (nl + 1);
     double* w = w0 + (size_t)s * nl;
+    float* wf = w0f + (size_t)s * nl;
     pr[0] = 0;
     for (int b = 0; b < nl; ++b) {
       pr[b + 1] = pr[b] + pk[s][b];
       w[b] = pk[s][b] > 0 ? src[s].bin_energy[b] / (double)pk[s][b] : 0.0;
+      wf[b] = (float)w[b];
+      w0_max = std::max(w0_max, w[b]);
     }
     if (pr[nl] == 0) continue;
     ItemDev& it = I[n_items++];
@@ -195,9 +204,15 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     }
     it.bin_prefix = reinterpret_cast<const long long*>(dev + o_pref) + (size_t)s * (nl + 1);
     it.W0 = reinterpret_cast<const double*>(dev + o_w0) + (size_t)s * nl;
+    it.W0f = reinterpret_cast<const float*>(dev + o_w0f) + (size_t)s * nl;
+    for (int a = 0; a < 3; ++a) {
+      it.posf[a] = (float)it.pos[a];
+      it.dirf[a] = (float)it.dir[a];
+    }
     it.cdf = nullptr;
     total += pr[nl];
   }
+  J.led_shift = ledger_shift(w0_max, p->rr_wmin, p->rr_p);
 
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int prev = -1;

@@ -65,6 +65,12 @@ struct Num<float> {
   static __device__ __forceinline__ float leaf_rho(uint32_t w, double) { return __uint_as_float(w); }
   static __device__ __forceinline__ double load_rho64(const double*, uint32_t) { return 0.0; }
   static __device__ __forceinline__ float kext(const BinDev& b) { return b.kext_f; }
+  static __device__ __forceinline__ float w0(const ItemDev& I, int bin) { return I.W0f[bin]; }
+  static __device__ __forceinline__ float pos(const ItemDev& I, int a) { return I.posf[a]; }
+  static __device__ __forceinline__ float dir(const ItemDev& I, int a) { return I.dirf[a]; }
+  static __device__ __forceinline__ float rr_wmin(const JobDev& J) { return J.rr_wmin_f; }
+  static __device__ __forceinline__ float rr_p(const JobDev& J) { return J.rr_p_f; }
+  static __device__ __forceinline__ float tau_max(const JobDev& J) { return J.peel_tau_max_f; }
   static __device__ __forceinline__ float alb(const BinDev& b) { return b.albedo; }
   static __device__ __forceinline__ float gg(const BinDev& b) { return b.g; }
 };
@@ -93,6 +99,12 @@ struct Num<double> {
   static __device__ __forceinline__ double leaf_rho(uint32_t, double r64) { return r64; }
   static __device__ __forceinline__ double load_rho64(const double* p, uint32_t i) { return __ldg(p + i); }
   static __device__ __forceinline__ double kext(const BinDev& b) { return b.kext_d; }
+  static __device__ __forceinline__ double w0(const ItemDev& I, int bin) { return I.W0[bin]; }
+  static __device__ __forceinline__ double pos(const ItemDev& I, int a) { return I.pos[a]; }
+  static __device__ __forceinline__ double dir(const ItemDev& I, int a) { return I.dir[a]; }
+  static __device__ __forceinline__ double rr_wmin(const JobDev& J) { return J.rr_wmin; }
+  static __device__ __forceinline__ double rr_p(const JobDev& J) { return J.rr_p; }
+  static __device__ __forceinline__ double tau_max(const JobDev& J) { return J.peel_tau_max; }
   static __device__ __forceinline__ double alb(const BinDev& b) { return b.albedo_d; }
   static __device__ __forceinline__ double gg(const BinDev& b) { return b.g_d; }
 };
@@ -323,10 +335,14 @@ enum { U_PK = 0, U_CROSS, U_SCAT, U_PCROSS, U_KILL, U_POUT, U_NU };
 // A lane whose job has no slot (a third job inside one warp) books directly
 // to global memory.  Kept per warp rather than per thread: shared memory
 // taken here is L1 cache lost to the node loads.
+// Energies are kept as the bits of an FP64 sum (FP64 tracer) or as 64-bit
+// fixed point, value * 2^shift of the slot's job (FP32 tracer: integer adds
+// are exact, order-independent and stay off the narrow FP64 pipe).
 struct WarpLedger {
-  double d[2][L_ND][8];
+  unsigned long long d[2][L_ND][8];
   unsigned long long u[2][U_NU][8];
   int tag[2][8];
+  int shift[2][8];
 };
 
 // Cold per-lane state: touched at emission, scattering and peel-off
@@ -341,13 +357,24 @@ struct ColdState {
   uint32_t scx[256], scy[256], scz[256], sidx[256];
   int slev[256];
   R sfx[256], sfy[256], sfz[256], sdx[256], sdy[256], sdz[256];
+  // the last Philox block (four words) drawn by the lane and its index: the
+  // draws of an event come from consecutive words of one block
+  uint4 rblk[256];
+  uint32_t rtag[256];
 };
 
 template <typename R>
 __device__ __forceinline__ uint32_t draw_u32(ColdState<R>& C, int t) {
   const uint32_t j = C.next[t];
   C.next[t] = j + 1u;
-  const uint4 b = philox4x32_10(make_uint4(C.c0[t], C.c1[t], j >> 2, C.c3[t]), C.k0[t], C.k1[t]);
+  uint4 b;
+  if (C.rtag[t] == (j >> 2)) {
+    b = C.rblk[t];
+  } else {
+    b = philox4x32_10(make_uint4(C.c0[t], C.c1[t], j >> 2, C.c3[t]), C.k0[t], C.k1[t]);
+    C.rblk[t] = b;
+    C.rtag[t] = j >> 2;
+  }
   const uint32_t w = j & 3u;
   return w == 0u ? b.x : (w == 1u ? b.y : (w == 2u ? b.z : b.w));
 }
@@ -363,14 +390,44 @@ static_assert(offsetof(LedgerDev, n_peel_out) == offsetof(LedgerDev, n_packets) 
 __device__ __forceinline__ double* ledger_d(LedgerDev* L, int i) { return &L->emitted + i; }
 __device__ __forceinline__ unsigned long long* ledger_u(LedgerDev* L, int i) { return &L->n_packets + i; }
 
-__device__ __forceinline__ void book_d(WarpLedger& SL, const JobDev* jobs, int job, int wid, int i, double v) {
-  if (v == 0.0) return;
+// floor(v * 2^shift) for v >= 0 from the bits of v, on the integer pipe
+// (saturates at 2^63; zero and denormals give 0)
+__device__ __forceinline__ unsigned long long to_fixed(float v, int shift) {
+  const uint32_t b = __float_as_uint(v);
+  const int e = (int)(b >> 23);
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = e - 150 + shift;  // v = m * 2^(e - 150)
+  const unsigned long long q =
+      sh >= 0 ? (sh > 39 ? (1ull << 63) : (m << sh)) : (sh <= -24 ? 0ull : (m >> (-sh)));
+  return e == 0 ? 0ull : q;
+}
+
+template <typename R>
+struct SlotNum;
+template <>
+struct SlotNum<float> {
+  static __device__ __forceinline__ void add(unsigned long long* slot, float v, int shift) {
+    atomicAdd(slot, to_fixed(v, shift));
+  }
+  static __device__ __forceinline__ double value(unsigned long long q, int shift) { return ldexp((double)q, -shift); }
+};
+template <>
+struct SlotNum<double> {
+  static __device__ __forceinline__ void add(unsigned long long* slot, double v, int) {
+    atomicAdd(reinterpret_cast<double*>(slot), v);
+  }
+  static __device__ __forceinline__ double value(unsigned long long q, int) { return __longlong_as_double((long long)q); }
+};
+
+template <typename R>
+__device__ __forceinline__ void book_d(WarpLedger& SL, const JobDev* jobs, int job, int wid, int i, R v) {
+  if (v == R(0)) return;
   if (SL.tag[0][wid] == job) {
-    atomicAdd(&SL.d[0][i][wid], v);
+    SlotNum<R>::add(&SL.d[0][i][wid], v, SL.shift[0][wid]);
   } else if (SL.tag[1][wid] == job) {
-    atomicAdd(&SL.d[1][i][wid], v);
+    SlotNum<R>::add(&SL.d[1][i][wid], v, SL.shift[1][wid]);
   } else {
-    atomicAdd(ledger_d(jobs[job].ledger, i), v);
+    atomicAdd(ledger_d(jobs[job].ledger, i), (double)v);
   }
 }
 
@@ -384,6 +441,30 @@ __device__ __forceinline__ void book_u(WarpLedger& SL, const JobDev* jobs, int j
   } else {
     atomicAdd(ledger_u(jobs[job].ledger, i), v);
   }
+}
+
+#ifndef RT_RED_HINT
+#define RT_RED_HINT 1
+#endif
+// L2 residency hints: the node words of the grid are read at every crossing
+// and should stay in L2 (evict_last); accumulator lines are touched by a few
+// consecutive deposits and then not again for a long time (evict_first), so
+// they should not push the node words out.
+__device__ __forceinline__ uint32_t ld_node(const uint32_t* p) {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  uint32_t w;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(w) : "l"(p), "l"(pol));
+  return w;
+}
+__device__ __forceinline__ void red_acc(double* p, double v) {
+#if RT_RED_HINT
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+#else
+  atomicAdd(p, v);
+#endif
 }
 
 // f32 -> f64 on the integer pipe (GB300's FP64 pipe is narrow); positive
@@ -444,7 +525,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   __shared__ WarpLedger SL;
   __shared__ ColdState<R> C;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  if (lane < L_ND) SL.d[0][lane][wid] = SL.d[1][lane][wid] = 0.0;
+  if (lane < L_ND) SL.d[0][lane][wid] = SL.d[1][lane][wid] = 0ull;
   if (lane < U_NU) SL.u[0][lane][wid] = SL.u[1][lane][wid] = 0ull;
   if (lane < 2) SL.tag[lane][wid] = -1;
   C.job[t] = -1;
@@ -481,15 +562,17 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
     ix = inv_abs(dx);
     iy = inv_abs(dy);
     iz = inv_abs(dz);
-    if (J.rr_wmin > 0.0 && W < (R)J.rr_wmin * C.W0[t]) {
+    const R wmin = Num<R>::rr_wmin(J);
+    if (wmin > R(0) && W < wmin * C.W0[t]) {
       const R ur = draw(C, t);
-      if (ur < (R)J.rr_p) {
-        book_d(SL, jobs, C.job[t], wid, L_RRL, (double)W);
+      const R rp = Num<R>::rr_p(J);
+      if (ur < rp) {
+        book_d(SL, jobs, C.job[t], wid, L_RRL, W);
         W = R(0);
         return 1;
       }
-      const R Wn = W / (R(1) - (R)J.rr_p);
-      book_d(SL, jobs, C.job[t], wid, L_RRG, (double)(Wn - W));
+      const R Wn = W / (R(1) - rp);
+      book_d(SL, jobs, C.job[t], wid, L_RRG, Wn - W);
       W = Wn;
     }
     tau = -Num<R>::log_(draw(C, t));
@@ -529,9 +612,9 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           if (old >= 0) {
             LedgerDev* L = jobs[old].ledger;
             if (lane < L_ND) {
-              const double v = SL.d[sl][lane][wid];
-              if (v != 0.0) atomicAdd(ledger_d(L, lane), v);
-              SL.d[sl][lane][wid] = 0.0;
+              const unsigned long long q = SL.d[sl][lane][wid];
+              if (q) atomicAdd(ledger_d(L, lane), SlotNum<R>::value(q, SL.shift[sl][wid]));
+              SL.d[sl][lane][wid] = 0ull;
             } else if (lane < L_ND + U_NU) {
               const unsigned long long v = SL.u[sl][lane - L_ND][wid];
               if (v) atomicAdd(ledger_u(L, lane - L_ND), v);
@@ -539,7 +622,10 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
             }
           }
           __syncwarp();
-          if (lane == 0) SL.tag[sl][wid] = nj;
+          if (lane == 0) {
+            SL.tag[sl][wid] = nj;
+            SL.shift[sl][wid] = jobs[nj].led_shift;
+          }
           __syncwarp();
         }
       }
@@ -558,7 +644,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           G.ry = J.root[1];
           G.rz = J.root[2];
           step_limit = (uint32_t)min(J.step_limit, (long long)0xFFFFFFFFll);
-          tau_cut = J.peel_tau_max > 0.0 ? (R)J.peel_tau_max : Num<R>::inf();
+          tau_cut = Num<R>::tau_max(J) > R(0) ? Num<R>::tau_max(J) : Num<R>::inf();
           const long long p = gi - I.pkt_begin;
           int blo = 0, bhi = J.n_lambda - 1;
           while (blo < bhi) {
@@ -576,19 +662,20 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           C.c1[t] = (uint32_t)(k >> 32);
           C.c3[t] = (I.src_index << 16) | (uint32_t)bin;
           C.next[t] = 0u;
+          C.rtag[t] = 0xFFFFFFFFu;
           const BinDev& B = J.bins[bin];
           kext = Num<R>::kext(B);
           alb = Num<R>::alb(B);
           C.gpar[t] = Num<R>::gg(B);
           absb = J.absorbed ? J.absorbed + (long long)(J.abs_bins > 1 ? bin : 0) * J.n_cells : nullptr;
           if (HITS) hitp = J.hits;
-          const R W0 = (R)I.W0[bin];
+          const R W0 = Num<R>::w0(I, bin);
           C.W0[t] = W0;
           W = W0;
           pkt_abs = R(0);
           ncross = npeel = 0u;
           C.nscat[t] = 0;
-          book_d(SL, jobs, job, wid, L_EMIT, (double)W0);
+          book_d(SL, jobs, job, wid, L_EMIT, W0);
           book_u(SL, jobs, job, wid, U_PK, 1ull);
           bool inside;
           if (I.kind == RT_SRC_POINT || I.kind == RT_SRC_BEAM) {
@@ -596,11 +683,11 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
               const R u1 = draw(C, t), u2 = draw(C, t);
               iso_dir(u1, u2, dx, dy, dz);
             } else {
-              dx = (R)I.dir[0];
-              dy = (R)I.dir[1];
-              dz = (R)I.dir[2];
+              dx = Num<R>::dir(I, 0);
+              dy = Num<R>::dir(I, 1);
+              dz = Num<R>::dir(I, 2);
             }
-            inside = place_root(G, g, cur, (R)I.pos[0], (R)I.pos[1], (R)I.pos[2], dx, dy, dz);
+            inside = place_root(G, g, cur, Num<R>::pos(I, 0), Num<R>::pos(I, 1), Num<R>::pos(I, 2), dx, dy, dz);
           } else if (I.kind == RT_SRC_EXTERNAL) {
             // face by area, uniform point on it, cosine-weighted inward direction
             const R ax = (R)G.ry * (R)G.rz, ay = (R)G.rx * (R)G.rz, az = (R)G.rx * (R)G.ry;
@@ -643,10 +730,13 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
             const double* cdf = I.cdf + (long long)bin * J.n_cells;
             const double totE = cdf[J.n_cells - 1];
             const double target = (double)draw(C, t) * totE;
+            // non-negative doubles order as their bit patterns: the search
+            // compares integers
+            const long long tb = __double_as_longlong(target);
             long long clo = 0, chi = J.n_cells - 1;
             while (clo < chi) {
               const long long mid = clo + ((chi - clo) >> 1);
-              if (cdf[mid] > target) chi = mid;
+              if (__double_as_longlong(cdf[mid]) > tb) chi = mid;
               else clo = mid + 1;
             }
             const uint64_t cw = J.coord[clo];
@@ -670,7 +760,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           if (inside) {
             st = ST_TRACE;
           } else {
-            book_d(SL, jobs, job, wid, L_ESC, (double)W);
+            book_d(SL, jobs, job, wid, L_ESC, W);
             const long long li = C.log_index[t];
             if (li >= 0) {
               double* r = J.packet_log + li * 10;
@@ -696,7 +786,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
     int ev = (st == ST_TRACE || st == ST_PEEL) ? EV_NONE : EV_IDLE;
     do {
       if (ev == EV_NONE) {
-        const uint32_t w = __ldg(G.node + cur.pending);
+        const uint32_t w = ld_node(G.node + cur.pending);
         const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
         if (w & RT_INTERIOR) {
           descend_step(g, cur, w, dx, dy, dz);
@@ -728,7 +818,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
                 W = W * e;
                 if (dep > R(0)) {
                   pkt_abs += dep;
-                  if (absb) atomicAdd(absb + g.idx, widen(dep));
+                  if (absb) red_acc(absb + g.idx, widen(dep));
                   if (HITS && hitp) atomicAdd(hitp + g.idx, 1u);
                 }
               }
@@ -768,7 +858,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
     bool pick_observer = false;
     const int job = C.job[t];
     if (ev == EV_KILL || (ev == EV_DEGEN && st == ST_TRACE)) {
-      book_d(SL, jobs, job, wid, L_KILL, (double)W);
+      book_d(SL, jobs, job, wid, L_KILL, W);
       book_u(SL, jobs, job, wid, U_KILL, 1ull);
       atomicOr(&jobs[job].ledger->status, ev == EV_KILL ? 1 : 2);
       fate = 2;
@@ -776,12 +866,12 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       pick_observer = true;  // abandon this observer
     } else if (ev == EV_ESCAPE) {
       if (st == ST_TRACE) {
-        book_d(SL, jobs, job, wid, L_ESC, (double)W);
+        book_d(SL, jobs, job, wid, L_ESC, W);
         fate = 0;
       } else {
         // the peel-off contribution reaches the observer (Sect. 2.4)
-        const double c = (double)C.pw[t] * (double)Num<R>::exp_(-taup);
-        atomicAdd(jobs[job].images + C.pix[t], c);
+        const R c = C.pw[t] * Num<R>::exp_(-taup);
+        if (c > R(0)) atomicAdd(jobs[job].images + C.pix[t], widen(c));
         book_d(SL, jobs, job, wid, L_PEEL, c);
         pick_observer = true;
       }
@@ -866,7 +956,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
 
     if (fate >= 0) {
       const int job = C.job[t];
-      book_d(SL, jobs, job, wid, L_ABS, (double)pkt_abs);
+      book_d(SL, jobs, job, wid, L_ABS, pkt_abs);
       book_u(SL, jobs, job, wid, U_CROSS, ncross);
       book_u(SL, jobs, job, wid, U_SCAT, (unsigned long long)C.nscat[t]);
       book_u(SL, jobs, job, wid, U_PCROSS, npeel);
@@ -897,7 +987,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       LedgerDev* L = jobs[tag].ledger;
 #pragma unroll
       for (int i = 0; i < L_ND; ++i)
-        if (SL.d[lane][i][wid] != 0.0) atomicAdd(ledger_d(L, i), SL.d[lane][i][wid]);
+        if (SL.d[lane][i][wid]) atomicAdd(ledger_d(L, i), SlotNum<R>::value(SL.d[lane][i][wid], SL.shift[lane][wid]));
 #pragma unroll
       for (int i = 0; i < U_NU; ++i)
         if (SL.u[lane][i][wid]) atomicAdd(ledger_u(L, i), SL.u[lane][i][wid]);
