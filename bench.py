@@ -39,6 +39,7 @@ BYTES_IMAGE_DEPOSIT = 16        # FP64 pixel read-modify-write
 # DRAM traffic of the tracer kernel per launch measured by ncu (bytes per
 # trace-equivalent unit); None until a capture of the current kernel exists
 NCU_TRAFFIC_PER_LAUNCH = None
+NCU_PEEL_TRAFFIC_PER_LAUNCH = None
 
 
 def parse():
@@ -290,18 +291,30 @@ def main():
         cross, pk = float(ct[0]), float(ct[1])
     value = cross / (t_ms * 1e-3)
 
-    # roofline of the tracer kernel (device time of each launch from the library's events)
+    # rooflines of the tracer and of the deferred peel-off kernel (device time
+    # of each launch from the library's events on the launching stream)
     L0 = leds[-1]
     kern_ms = statistics.mean(L["kernel_ms"] for L in leds)
+    peel_ms = statistics.mean(L["peel_ms"] for L in leds)
     deposits = L0["n_scatter"] * obs.n_obs - L0["n_peel_out"]
-    alg_bytes = BYTES_TRACE_CROSS * L0["n_cross"] + BYTES_PEEL_CROSS * L0["n_peel_cross"] + BYTES_IMAGE_DEPOSIT * deposits
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    trace_bytes = BYTES_TRACE_CROSS * L0["n_cross"]
+    peel_bytes = BYTES_PEEL_CROSS * L0["n_peel_cross"] + BYTES_IMAGE_DEPOSIT * deposits
+    if L0["n_peel_deferred"] < L0["n_scatter"]:  # some peel-offs ran inline in the tracer
+        trace_bytes, peel_bytes = trace_bytes + peel_bytes, 0
+    achieved = trace_bytes / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": NCU_TRAFFIC_PER_LAUNCH, "peak_kind": peak_kind, "kernel": "trace_kernel<float,true>",
-            "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes,
+            "traffic": NCU_TRAFFIC_PER_LAUNCH, "peak_kind": peak_kind, "kernel": "trace_kernel<float,1,0,0>",
+            "kernel_ms": kern_ms, "alg_bytes_per_launch": trace_bytes,
             "bytes_per_unit": {"trace_crossing": BYTES_TRACE_CROSS, "peel_crossing": BYTES_PEEL_CROSS,
                                "image_deposit": BYTES_IMAGE_DEPOSIT}}
+    peel_roof = None
+    if peel_ms > 0:
+        pa = peel_bytes / (peel_ms * 1e-3) / 1e9
+        peel_roof = {"kernel": "peel_kernel<float>", "bound": "hbm", "achieved": pa, "peak": peak, "unit": "GB/s",
+                     "frac": pa / peak, "kernel_ms": peel_ms, "alg_bytes_per_launch": peel_bytes,
+                     "traffic": NCU_PEEL_TRAFFIC_PER_LAUNCH,
+                     "crossings_per_s": L0["n_peel_cross"] / (peel_ms * 1e-3)}
 
     out = None
     if rank == 0:
@@ -317,8 +330,9 @@ def main():
                "data": "synthetic (seeded lognormal cloud, random-field density)",
                "config": workload_config(a, m), "packets_per_s": pk / (t_ms * 1e-3),
                "crossings_per_step": {"trace": L0["n_cross"], "peel": L0["n_peel_cross"]},
-               "scatterings_per_step": L0["n_scatter"], "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-               "clocks": clk, "gpu_launches": 3 * a.steps,
+               "scatterings_per_step": L0["n_scatter"], "roofline": roof, "roofline_peel_kernel": peel_roof,
+               "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "gpu_launches": (3 + (1 if peel_ms > 0 else 0)) * a.steps,
                "energy_balance": (L0["emitted"] - L0["absorbed"] - L0["escaped"]) / L0["emitted"],
                "model_generation_s": t_gen}
         print(json.dumps(out))

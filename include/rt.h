@@ -55,6 +55,14 @@ typedef struct rt_server rt_server;
  * time (calls lock it). */
 int rt_ctx_create(int device, rt_ctx** out);
 void rt_ctx_destroy(rt_ctx* ctx);
+/* Peel-off (Sect. 2.4) is deferred: each scattering appends one record
+ * (48 B in FP32, 80 B in FP64) to a context-owned device queue, and a second
+ * kernel marches every (record, observer) pair after the tracer.  The queue
+ * holds min(max_records, packages of the launch / 4) records (at least 65536);
+ * scatterings beyond it peel off inline in the tracer, with the same
+ * results.  max_records = 0 disables deferral, < 0 restores the default
+ * (2^27).  Takes effect at the next launch (and at rt_batch_create). */
+int rt_ctx_set_peel_queue(rt_ctx* ctx, int64_t max_records);
 /* Message of the last failing call on this thread (static storage, valid
  * until the next call on the same thread). */
 const char* rt_last_error(void);
@@ -170,8 +178,10 @@ typedef struct {
 typedef struct {
   double emitted, absorbed, escaped, rr_gain, rr_loss, killed, peeled;
   uint64_t n_packets, n_cross, n_scatter, n_peel_cross, n_killed, n_peel_out;
+  uint64_t n_peel_deferred; /* scatterings whose peel-off ran in the deferred peel-off kernel */
   int status;               /* RT_OK or RT_ERR_STEP_LIMIT */
   double kernel_ms;         /* device time of the tracer launch */
+  double peel_ms;           /* device time of the deferred peel-off launch (0: none) */
 } rt_ledger;
 
 /* Trace every package of every source and accumulate the absorbed energy

@@ -85,7 +85,9 @@ struct rt_ctx {
   std::vector<DevBuf> cdf;  // per dust source
   void* pinned = nullptr;
   size_t pinned_n = 0;
-  cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr, ev_m = nullptr;
+  DevBuf peel_q;                          // deferred peel-off records
+  long long peel_q_max = 1ll << 27;       // records; 0: peel-off inline
   // launch defaults chosen by rt_autotune, per [FP64][peel-off]
   struct Tuned {
     bool set = false;
@@ -153,6 +155,7 @@ extern "C" int rt_ctx_create(int device, rt_ctx** out) {
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_a);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_b);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_c);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev_m);
   if (e != cudaSuccess) {
     delete c;
     return fail(RT_ERR_CUDA, "rt_ctx_create: %s", cudaGetErrorString(e));
@@ -174,8 +177,38 @@ extern "C" void rt_ctx_destroy(rt_ctx* c) {
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->ev_b) cudaEventDestroy(c->ev_b);
   if (c->ev_c) cudaEventDestroy(c->ev_c);
+  if (c->ev_m) cudaEventDestroy(c->ev_m);
+  c->peel_q.release();
   delete c;
 }
+
+extern "C" int rt_ctx_set_peel_queue(rt_ctx* c, int64_t max_records) {
+  if (!c) return fail(RT_ERR_INVALID, "rt_ctx_set_peel_queue: NULL context");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->peel_q_max = max_records < 0 ? (1ll << 27) : (long long)max_records;
+  return RT_OK;
+}
+
+// Queue for the deferred peel-off of one launch: min(max_records, total / 4)
+// records, at least 65536.  When the device has no room for it the launch
+// peels off inline (same results), so an allocation failure is not an error.
+static PeelQueue make_queue(DevBuf& buf, long long max_records, bool peel, int n_jobs, long long total,
+                            int precision, unsigned long long* count_dev) {
+  PeelQueue q;
+  q.rec = nullptr;
+  q.count = count_dev;
+  q.cap = 0;
+  if (!peel || max_records <= 0 || n_jobs > RT_PEEL_MAX_JOBS) return q;
+  const long long cap = std::min<long long>(max_records, std::max<long long>(total / 4, 65536));
+  if (buf.ensure(peel_record_bytes(precision) * (size_t)cap) != RT_OK) {
+    cudaGetLastError();  // allocation failures are not sticky
+    return q;
+  }
+  q.rec = buf.p;
+  q.cap = cap;
+  return q;
+}
+
 
 // wait for an event with a deadline; the device keeps running on timeout
 static int wait_event(cudaEvent_t ev, double timeout_s) {
@@ -429,6 +462,13 @@ struct TraceArgs {
   double* images;
   double* absorbed;
 };
+
+static int max_observers(int n_jobs, const TraceArgs* jobs) {
+  int m = 0;
+  for (int j = 0; j < n_jobs; ++j)
+    if (jobs[j].obs) m = std::max(m, jobs[j].obs->n_obs);
+  return m;
+}
 
 static void cross3(const double* a, const double* b, double* o) {
   o[0] = a[1] * b[2] - a[2] * b[1];
@@ -743,6 +783,7 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   int rc = c->small.ensure(sizeof(LedgerDev) * n_jobs + 256);
   if (rc) return rc;
   LedgerDev* led = reinterpret_cast<LedgerDev*>(c->small.p);
+  // package counter, peel-off queue length, peel-off work counter
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(led + n_jobs);
   Arena A;
   std::vector<size_t> job_off;
@@ -753,7 +794,8 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   rc = build_tables(c, n_jobs, jobs, led, s, A, job_off, items_off, n_items, total, peel, precision, estimator);
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(c->table.p);
-  CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + 3 * sizeof(unsigned long long), s));
+  const PeelQueue q = make_queue(c->peel_q, c->peel_q_max, peel, n_jobs, total, precision, counter + 1);
   LaunchCfg cfg;
   rc = make_cfg(c, precision, peel, launch_prm, &cfg);
   if (rc) return rc;
@@ -764,7 +806,11 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   CK(cudaEventRecord(c->ev_a, s));
   if (total > 0 && n_items > 0)
     CK(launch_trace(precision, peel, estimator, hits, reinterpret_cast<const JobDev*>(base + job_off[0]),
-                    reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, s));
+                    reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, q, s));
+  CK(cudaEventRecord(c->ev_m, s));
+  if (total > 0 && n_items > 0 && q.cap > 0)
+    CK(launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
+                   max_observers(n_jobs, jobs), cfg.refill, s));
   CK(cudaEventRecord(c->ev_b, s));
   std::vector<LedgerDev> hl(n_jobs);
   CK(cudaMemcpyAsync(hl.data(), led, sizeof(LedgerDev) * n_jobs, cudaMemcpyDeviceToHost, s));
@@ -772,8 +818,9 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   const double to = launch_prm->timeout_s > 0 ? launch_prm->timeout_s : 3600.0;
   rc = wait_event(c->ev_c, to);
   if (rc) return rc;
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
+  float ms = 0.f, ms_peel = 0.f;
+  cudaEventElapsedTime(&ms, c->ev_a, c->ev_m);
+  cudaEventElapsedTime(&ms_peel, c->ev_m, c->ev_b);
   int status = RT_OK;
   for (int j = 0; j < n_jobs; ++j) {
     const LedgerDev& L = hl[j];
@@ -792,8 +839,10 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
       o.n_peel_cross = L.n_peel_cross;
       o.n_killed = L.n_killed;
       o.n_peel_out = L.n_peel_out;
+      o.n_peel_deferred = L.n_peel_deferred;
       o.status = L.status ? RT_ERR_STEP_LIMIT : RT_OK;
       o.kernel_ms = ms;
+      o.peel_ms = q.cap > 0 ? ms_peel : 0.0;
     }
     if (L.status) status = RT_ERR_STEP_LIMIT;
   }
@@ -1036,7 +1085,7 @@ extern "C" int rt_trace_batch(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_le
 struct rt_batch {
   rt_ctx* ctx = nullptr;
   int n_jobs = 0;
-  DevBuf table, small;
+  DevBuf table, small, peel_q;
   std::vector<DevBuf> cdf;
   LedgerDev* host_led = nullptr;  // pinned, written by the graph
   cudaStream_t cap = nullptr;
@@ -1056,6 +1105,7 @@ extern "C" void rt_batch_destroy(rt_batch* b) {
   if (b->host_led) cudaFreeHost(b->host_led);
   b->table.release();
   b->small.release();
+  b->peel_q.release();
   for (auto& d : b->cdf) d.release();
   delete b;
 }
@@ -1100,7 +1150,9 @@ extern "C" int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_b
   LaunchCfg cfg;
   rc = make_cfg(ctx, precision, peel, jobs[0].params, &cfg);
   if (rc) return bail(rc);
-  // capture: zero every job's outputs and the ledgers, run the tracer, read back
+  const PeelQueue q = make_queue(b->peel_q, ctx->peel_q_max, peel, n_jobs, total, precision, counter + 1);
+  // capture: zero every job's outputs and the ledgers, run the tracer and
+  // the deferred peel-off, read back
   char* base = reinterpret_cast<char*>(b->table.p);
   e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   for (int j = 0; j < n_jobs && e == cudaSuccess; ++j) {
@@ -1110,10 +1162,13 @@ extern "C" int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_b
     if (e == cudaSuccess && T.obs && T.images)
       e = cudaMemsetAsync(T.images, 0, sizeof(double) * (size_t)T.obs->n_obs * bins * T.obs->nx * T.obs->ny, b->cap);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(led, 0, sizeof(LedgerDev) * n_jobs + sizeof(unsigned long long), b->cap);
+  if (e == cudaSuccess) e = cudaMemsetAsync(led, 0, sizeof(LedgerDev) * n_jobs + 3 * sizeof(unsigned long long), b->cap);
   if (e == cudaSuccess && total > 0 && n_items > 0)
     e = launch_trace(precision, peel, estimator, false, reinterpret_cast<const JobDev*>(base + job_off[0]),
-                     reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, b->cap);
+                     reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, q, b->cap);
+  if (e == cudaSuccess && total > 0 && n_items > 0 && q.cap > 0)
+    e = launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
+                    max_observers(n_jobs, args.data()), cfg.refill, b->cap);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->host_led, led, sizeof(LedgerDev) * n_jobs, cudaMemcpyDeviceToHost, b->cap);
   cudaGraph_t g = nullptr;
@@ -1148,7 +1203,8 @@ extern "C" int rt_batch_run(rt_batch* b, rt_ledger* ledgers, double timeout_s, v
       o.emitted = L.emitted; o.absorbed = L.absorbed; o.escaped = L.escaped; o.rr_gain = L.rr_gain;
       o.rr_loss = L.rr_loss; o.killed = L.killed; o.peeled = L.peeled; o.n_packets = L.n_packets;
       o.n_cross = L.n_cross; o.n_scatter = L.n_scatter; o.n_peel_cross = L.n_peel_cross; o.n_killed = L.n_killed;
-      o.n_peel_out = L.n_peel_out; o.status = L.status ? RT_ERR_STEP_LIMIT : RT_OK; o.kernel_ms = ms;
+      o.n_peel_out = L.n_peel_out; o.n_peel_deferred = L.n_peel_deferred;
+      o.status = L.status ? RT_ERR_STEP_LIMIT : RT_OK; o.kernel_ms = ms; o.peel_ms = 0.0;
     }
     if (L.status) status = RT_ERR_STEP_LIMIT;
   }
@@ -1207,7 +1263,8 @@ extern "C" int rt_autotune(rt_ctx* ctx, int n_jobs, const rt_job* jobs, double s
       if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
       double cross = 0.0;
       for (auto& L : led) cross += (double)L.n_cross + (double)L.n_peel_cross;
-      const double rate = led[0].kernel_ms > 0 ? cross / led[0].kernel_ms : 0.0;
+      const double ms = led[0].kernel_ms + led[0].peel_ms;  // tracer + deferred peel-off
+      const double rate = ms > 0 ? cross / ms : 0.0;
       if (rate > res.crossings_per_ms) {
         res.crossings_per_ms = rate;
         res.block_size = blocks[bi];

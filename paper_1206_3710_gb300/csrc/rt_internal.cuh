@@ -44,9 +44,33 @@ struct ObsDev {
 
 struct LedgerDev {
   double emitted, absorbed, escaped, rr_gain, rr_loss, killed, peeled;
-  unsigned long long n_packets, n_cross, n_scatter, n_peel_cross, n_killed, n_peel_out;
+  unsigned long long n_packets, n_cross, n_scatter, n_peel_cross, n_killed, n_peel_out, n_peel_deferred;
   int status;
   int pad;
+};
+
+// Deferred peel-off (Sect. 2.4): at a scattering the tracer appends the
+// scattering point, incoming direction and weight to a queue; a second
+// kernel marches every (record, observer) pair to the grid edge.  The
+// tracer's lanes then all trace, and the marches run in a kernel of their
+// own.  meta = level | bin << 5 | job << 13.
+struct PeelRec32 {
+  uint32_t cx, cy, cz, idx;
+  float fx, fy, fz, W;
+  float dx, dy, dz;
+  uint32_t meta;
+};
+struct PeelRec64 {
+  uint32_t cx, cy, cz, idx;
+  double fx, fy, fz, W;
+  double dx, dy, dz;
+  uint32_t meta, pad;
+};
+#define RT_PEEL_MAX_JOBS (1 << 19)
+struct PeelQueue {
+  void* rec;                    // PeelRec32 or PeelRec64 [cap]
+  unsigned long long* count;    // records requested (may exceed cap: the rest peel inline)
+  long long cap;                // 0: no queue, every peel-off inline
 };
 
 struct JobDev {
@@ -125,8 +149,13 @@ struct LaunchCfg {
 // launch the persistent tracer over n_items items of total packages
 cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev,
-                         long long total, const LaunchCfg& cfg, cudaStream_t s);
+                         long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s);
 cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm);
+// march the queued peel-off records (n_obs_max observers each); work_dev is a
+// zeroed counter
+cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
+                        int n_obs_max, int refill, cudaStream_t s);
+size_t peel_record_bytes(int precision);
 
 cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, const double* origins,
                         const double* dirs, long long max_seg, long long* cells, double* lengths,

@@ -235,9 +235,13 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     cfg.block = block;
     cfg.blocks = sms * occ;
     cfg.refill = p->refill_threshold > 0 ? (p->refill_threshold > 32 ? 32 : p->refill_threshold) : 8;
+    PeelQueue q;  // no observers: no peel-off queue
+    q.rec = nullptr;
+    q.count = nullptr;
+    q.cap = 0;
     if (launch_trace(p->precision, false, p->estimator, false, reinterpret_cast<const JobDev*>(dev + o_job),
                      reinterpret_cast<const ItemDev*>(dev + o_item), n_items,
-                     reinterpret_cast<unsigned long long*>(dev + o_cnt), total, cfg, st) != cudaSuccess)
+                     reinterpret_cast<unsigned long long*>(dev + o_cnt), total, cfg, q, st) != cudaSuccess)
       return restore(set_error(RT_ERR_CUDA, "rt_trace_noalloc: kernel launch failed"));
   }
   LedgerDev hl;
@@ -268,6 +272,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     ledger->n_peel_cross = hl.n_peel_cross;
     ledger->n_killed = hl.n_killed;
     ledger->n_peel_out = hl.n_peel_out;
+    ledger->n_peel_deferred = hl.n_peel_deferred;
     ledger->status = hl.status ? RT_ERR_STEP_LIMIT : RT_OK;
     ledger->kernel_ms = 0.0;
   }

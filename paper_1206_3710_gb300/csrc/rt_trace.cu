@@ -324,7 +324,7 @@ __device__ __forceinline__ R inv_abs(R d) {
 // shared-memory state of the tracer
 // ------------------------------------------------------------------------
 enum { L_EMIT = 0, L_ABS, L_ESC, L_RRG, L_RRL, L_KILL, L_PEEL, L_ND };
-enum { U_PK = 0, U_CROSS, U_SCAT, U_PCROSS, U_KILL, U_POUT, U_NU };
+enum { U_PK = 0, U_CROSS, U_SCAT, U_PCROSS, U_KILL, U_POUT, U_DEFER, U_NU };
 
 // Energy ledger per warp, updated with shared-memory atomics at package
 // events (a few per package).  Two slots per warp, each tagged with the job
@@ -386,7 +386,7 @@ __device__ __forceinline__ R draw(ColdState<R>& C, int t) {
 
 // the ledger's sums and counts are contiguous, in the order of L_* and U_*
 static_assert(offsetof(LedgerDev, peeled) == offsetof(LedgerDev, emitted) + 8 * L_PEEL, "ledger layout");
-static_assert(offsetof(LedgerDev, n_peel_out) == offsetof(LedgerDev, n_packets) + 8 * U_POUT, "ledger layout");
+static_assert(offsetof(LedgerDev, n_peel_deferred) == offsetof(LedgerDev, n_packets) + 8 * U_DEFER, "ledger layout");
 __device__ __forceinline__ double* ledger_d(LedgerDev* L, int i) { return &L->emitted + i; }
 __device__ __forceinline__ unsigned long long* ledger_u(LedgerDev* L, int i) { return &L->n_packets + i; }
 
@@ -440,6 +440,64 @@ __device__ __forceinline__ void book_u(WarpLedger& SL, const JobDev* jobs, int j
     atomicAdd(&SL.u[1][i][wid], v);
   } else {
     atomicAdd(ledger_u(jobs[job].ledger, i), v);
+  }
+}
+
+// Warp-uniform: give job nj a ledger slot if it has none, flushing a slot
+// that no live lane (lane_job: the lane's job, -1 if not live) books to.
+template <typename R>
+__device__ __forceinline__ void ledger_retag(WarpLedger& SL, const JobDev* jobs, int wid, int lane, int nj,
+                                             int lane_job) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  if (nj < 0 || SL.tag[0][wid] == nj || SL.tag[1][wid] == nj) return;
+  const bool use0 = __any_sync(FULL, lane_job >= 0 && lane_job == SL.tag[0][wid]);
+  const bool use1 = __any_sync(FULL, lane_job >= 0 && lane_job == SL.tag[1][wid]);
+  const int sl = !use0 ? 0 : (!use1 ? 1 : -1);
+  if (sl < 0) return;
+  __syncwarp();
+  const int old = SL.tag[sl][wid];
+  if (old >= 0) {
+    LedgerDev* L = jobs[old].ledger;
+    if (lane < L_ND) {
+      const unsigned long long q = SL.d[sl][lane][wid];
+      if (q) atomicAdd(ledger_d(L, lane), SlotNum<R>::value(q, SL.shift[sl][wid]));
+      SL.d[sl][lane][wid] = 0ull;
+    } else if (lane < L_ND + U_NU) {
+      const unsigned long long v = SL.u[sl][lane - L_ND][wid];
+      if (v) atomicAdd(ledger_u(L, lane - L_ND), v);
+      SL.u[sl][lane - L_ND][wid] = 0ull;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    SL.tag[sl][wid] = nj;
+    SL.shift[sl][wid] = jobs[nj].led_shift;
+  }
+  __syncwarp();
+}
+
+template <typename R>
+__device__ __forceinline__ void ledger_init(WarpLedger& SL, int wid, int lane) {
+  if (lane < L_ND) SL.d[0][lane][wid] = SL.d[1][lane][wid] = 0ull;
+  if (lane < U_NU) SL.u[0][lane][wid] = SL.u[1][lane][wid] = 0ull;
+  if (lane < 2) SL.tag[lane][wid] = -1;
+  __syncwarp();
+}
+
+template <typename R>
+__device__ __forceinline__ void ledger_flush(WarpLedger& SL, const JobDev* jobs, int wid, int lane) {
+  __syncwarp();
+  if (lane < 2) {
+    const int tag = SL.tag[lane][wid];
+    if (tag >= 0) {
+      LedgerDev* L = jobs[tag].ledger;
+#pragma unroll
+      for (int i = 0; i < L_ND; ++i)
+        if (SL.d[lane][i][wid]) atomicAdd(ledger_d(L, i), SlotNum<R>::value(SL.d[lane][i][wid], SL.shift[lane][wid]));
+#pragma unroll
+      for (int i = 0; i < U_NU; ++i)
+        if (SL.u[lane][i][wid]) atomicAdd(ledger_u(L, i), SL.u[lane][i][wid]);
+    }
   }
 }
 
@@ -506,6 +564,88 @@ __device__ __forceinline__ double warp_sum(double v) {
 enum { ST_DEAD = 0, ST_TRACE = 1, ST_PEEL = 2, ST_DONE = 3 };
 enum { EV_NONE = 0, EV_IDLE, EV_INTERACT, EV_ESCAPE, EV_CUT, EV_KILL, EV_DEGEN };
 
+// ------------------------------------------------------------------------
+// deferred peel-off records
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t peel_meta(int lev, int bin, int job) {
+  return (uint32_t)lev | ((uint32_t)bin << 5) | ((uint32_t)job << 13);
+}
+
+template <typename R>
+struct PeelIO;
+template <>
+struct PeelIO<float> {
+  static __device__ __forceinline__ void put(void* base, unsigned long long i, const Geo<float>& g, float dx,
+                                             float dy, float dz, float W, uint32_t meta) {
+    uint4* p = reinterpret_cast<uint4*>(static_cast<PeelRec32*>(base) + i);
+    p[0] = make_uint4(g.cx, g.cy, g.cz, g.idx);
+    p[1] = make_uint4(__float_as_uint(g.fx), __float_as_uint(g.fy), __float_as_uint(g.fz), __float_as_uint(W));
+    p[2] = make_uint4(__float_as_uint(dx), __float_as_uint(dy), __float_as_uint(dz), meta);
+  }
+  static __device__ __forceinline__ void get(const void* base, long long i, Geo<float>& g, float& dx, float& dy,
+                                             float& dz, float& W, uint32_t& meta) {
+    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const PeelRec32*>(base) + i);
+    const uint4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    g.cx = a.x; g.cy = a.y; g.cz = a.z; g.idx = a.w;
+    g.fx = __uint_as_float(b.x); g.fy = __uint_as_float(b.y); g.fz = __uint_as_float(b.z);
+    W = __uint_as_float(b.w);
+    dx = __uint_as_float(c.x); dy = __uint_as_float(c.y); dz = __uint_as_float(c.z);
+    meta = c.w;
+  }
+};
+template <>
+struct PeelIO<double> {
+  static __device__ __forceinline__ void put(void* base, unsigned long long i, const Geo<double>& g, double dx,
+                                             double dy, double dz, double W, uint32_t meta) {
+    PeelRec64* r = static_cast<PeelRec64*>(base) + i;
+    *reinterpret_cast<uint4*>(&r->cx) = make_uint4(g.cx, g.cy, g.cz, g.idx);
+    *reinterpret_cast<double2*>(&r->fx) = make_double2(g.fx, g.fy);
+    *reinterpret_cast<double2*>(&r->fz) = make_double2(g.fz, W);
+    *reinterpret_cast<double2*>(&r->dx) = make_double2(dx, dy);
+    r->dz = dz;
+    r->meta = meta;
+  }
+  static __device__ __forceinline__ void get(const void* base, long long i, Geo<double>& g, double& dx,
+                                             double& dy, double& dz, double& W, uint32_t& meta) {
+    const PeelRec64* r = static_cast<const PeelRec64*>(base) + i;
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(&r->cx));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(&r->fx));
+    const double2 c = __ldg(reinterpret_cast<const double2*>(&r->fz));
+    const double2 d = __ldg(reinterpret_cast<const double2*>(&r->dx));
+    g.cx = a.x; g.cy = a.y; g.cz = a.z; g.idx = a.w;
+    g.fx = b.x; g.fy = b.y; g.fz = c.x;
+    W = c.y;
+    dx = d.x; dy = d.y;
+    dz = __ldg(&r->dz);
+    meta = __ldg(&r->meta);
+  }
+};
+static_assert(sizeof(PeelRec32) == 48 && sizeof(PeelRec64) == 80, "peel record layout");
+
+// Peel-off towards observer o from the scattering point g (incoming
+// direction sd, weight W): the pixel the point projects to and the weight
+// W p_HG(k . d_in) that reaches it before extinction (Sect. 2.4).  False
+// when the point projects outside the image.
+template <typename R>
+__device__ __forceinline__ bool peel_setup(const JobDev& J, int o, const Geo<R>& g, R sdx, R sdy, R sdz, R W,
+                                           R gpar, int bin, R& pw, long long& pix) {
+  const ObsDev& O = J.obs[o];
+  const R s = Num<R>::pow2m(g.lev);
+  const R Px = ((R)g.cx + g.fx) * s - ObsGeom<R>::c(O, 0);
+  const R Py = ((R)g.cy + g.fy) * s - ObsGeom<R>::c(O, 1);
+  const R Pz = ((R)g.cz + g.fz) * s - ObsGeom<R>::c(O, 2);
+  const R u = (Px * ObsGeom<R>::ex(O, 0) + Py * ObsGeom<R>::ex(O, 1) + Pz * ObsGeom<R>::ex(O, 2)) *
+                  ObsGeom<R>::ip(O, 0) + R(0.5) * (R)O.nx;
+  const R v = (Px * ObsGeom<R>::ey(O, 0) + Py * ObsGeom<R>::ey(O, 1) + Pz * ObsGeom<R>::ey(O, 2)) *
+                  ObsGeom<R>::ip(O, 1) + R(0.5) * (R)O.ny;
+  const R fu = Num<R>::floor_(u), fv = Num<R>::floor_(v);
+  if (!(fu >= R(0) && fv >= R(0) && fu < (R)O.nx && fv < (R)O.ny)) return false;
+  const R kx = ObsGeom<R>::k(O, 0), ky = ObsGeom<R>::k(O, 1), kz = ObsGeom<R>::k(O, 2);
+  pw = W * hg_phase(gpar, sdx * kx + sdy * ky + sdz * kz);
+  pix = (((long long)o * J.img_bins + (J.img_bins > 1 ? bin : 0)) * O.ny + (long long)fv) * O.nx + (long long)fu;
+  return true;
+}
+
 #ifndef RT_FP32_MIN_BLOCKS
 #define RT_FP32_MIN_BLOCKS 4
 #endif
@@ -520,14 +660,13 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
                                                                          const ItemDev* __restrict__ items,
                                                                          int n_items,
                                                                          unsigned long long* __restrict__ counter,
-                                                                         long long total, int refill_thr) {
+                                                                         long long total, int refill_thr,
+                                                                         PeelQueue Q) {
   const unsigned FULL = 0xFFFFFFFFu;
   __shared__ WarpLedger SL;
   __shared__ ColdState<R> C;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  if (lane < L_ND) SL.d[0][lane][wid] = SL.d[1][lane][wid] = 0ull;
-  if (lane < U_NU) SL.u[0][lane][wid] = SL.u[1][lane][wid] = 0ull;
-  if (lane < 2) SL.tag[lane][wid] = -1;
+  ledger_init<R>(SL, wid, lane);
   C.job[t] = -1;
   __syncwarp();
 
@@ -601,34 +740,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       }
       // the leader's package is the first one handed out: give its job a slot
       const int nj = __shfl_sync(FULL, lo >= 0 ? items[lo].job : -1, leader);
-      if (nj >= 0 && SL.tag[0][wid] != nj && SL.tag[1][wid] != nj) {
-        const bool live = st == ST_TRACE || st == ST_PEEL;
-        const bool use0 = __any_sync(FULL, live && C.job[t] == SL.tag[0][wid]);
-        const bool use1 = __any_sync(FULL, live && C.job[t] == SL.tag[1][wid]);
-        const int sl = !use0 ? 0 : (!use1 ? 1 : -1);
-        if (sl >= 0) {
-          __syncwarp();
-          const int old = SL.tag[sl][wid];
-          if (old >= 0) {
-            LedgerDev* L = jobs[old].ledger;
-            if (lane < L_ND) {
-              const unsigned long long q = SL.d[sl][lane][wid];
-              if (q) atomicAdd(ledger_d(L, lane), SlotNum<R>::value(q, SL.shift[sl][wid]));
-              SL.d[sl][lane][wid] = 0ull;
-            } else if (lane < L_ND + U_NU) {
-              const unsigned long long v = SL.u[sl][lane - L_ND][wid];
-              if (v) atomicAdd(ledger_u(L, lane - L_ND), v);
-              SL.u[sl][lane - L_ND][wid] = 0ull;
-            }
-          }
-          __syncwarp();
-          if (lane == 0) {
-            SL.tag[sl][wid] = nj;
-            SL.shift[sl][wid] = jobs[nj].led_shift;
-          }
-          __syncwarp();
-        }
-      }
+      ledger_retag<R>(SL, jobs, wid, lane, nj, (st == ST_TRACE || st == ST_PEEL) ? C.job[t] : -1);
       if (st == ST_DEAD) {
         if (lo < 0) {
           st = ST_DONE;
@@ -889,9 +1001,20 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       }
       if (scatter) {
         C.nscat[t] += 1;
-        if (PEEL && jobs[job].n_obs > 0) {
-          // save the scattering point and march towards each observer in
-          // turn; the new direction is drawn after the last observer
+        bool inline_peel = PEEL && jobs[job].n_obs > 0;
+        if (inline_peel && Q.cap > 0) {
+          // defer: the peel-off kernel marches this record to every observer
+          const unsigned long long slot = atomicAdd(Q.count, 1ull);
+          if (slot < (unsigned long long)Q.cap) {
+            PeelIO<R>::put(Q.rec, slot, g, dx, dy, dz, W, peel_meta(g.lev, C.bin[t], job));
+            book_u(SL, jobs, job, wid, U_DEFER, 1ull);
+            inline_peel = false;
+          }
+        }
+        if (inline_peel) {
+          // queue full (or none): save the scattering point and march
+          // towards each observer in turn; the new direction is drawn after
+          // the last observer
           C.scx[t] = g.cx; C.scy[t] = g.cy; C.scz[t] = g.cz;
           C.sidx[t] = g.idx; C.slev[t] = g.lev;
           C.sfx[t] = g.fx; C.sfy[t] = g.fy; C.sfz[t] = g.fz;
@@ -920,27 +1043,16 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       while (!started) {
         ++o;
         if (o >= J.n_obs) break;
-        const ObsDev& O = J.obs[o];
-        // scattering point in root-cell units, projected on the image plane
-        const R s = Num<R>::pow2m(g.lev);
-        const R Px = ((R)g.cx + g.fx) * s - ObsGeom<R>::c(O, 0);
-        const R Py = ((R)g.cy + g.fy) * s - ObsGeom<R>::c(O, 1);
-        const R Pz = ((R)g.cz + g.fz) * s - ObsGeom<R>::c(O, 2);
-        const R u = (Px * ObsGeom<R>::ex(O, 0) + Py * ObsGeom<R>::ex(O, 1) + Pz * ObsGeom<R>::ex(O, 2)) *
-                        ObsGeom<R>::ip(O, 0) + R(0.5) * (R)O.nx;
-        const R v = (Px * ObsGeom<R>::ey(O, 0) + Py * ObsGeom<R>::ey(O, 1) + Pz * ObsGeom<R>::ey(O, 2)) *
-                        ObsGeom<R>::ip(O, 1) + R(0.5) * (R)O.ny;
-        const R fu = Num<R>::floor_(u), fv = Num<R>::floor_(v);
-        if (!(fu >= R(0) && fv >= R(0) && fu < (R)O.nx && fv < (R)O.ny)) {
+        R pw;
+        long long pix;
+        if (!peel_setup<R>(J, o, g, sdx, sdy, sdz, W, C.gpar[t], C.bin[t], pw, pix)) {
           book_u(SL, jobs, C.job[t], wid, U_POUT, 1ull);
           continue;
         }
-        const R kx = ObsGeom<R>::k(O, 0), ky = ObsGeom<R>::k(O, 1), kz = ObsGeom<R>::k(O, 2);
-        C.pw[t] = W * hg_phase(C.gpar[t], sdx * kx + sdy * ky + sdz * kz);
-        const int bin = C.bin[t];
-        C.pix[t] = (((long long)o * J.img_bins + (J.img_bins > 1 ? bin : 0)) * O.ny + (long long)fv) * O.nx +
-                   (long long)fu;
-        dx = kx; dy = ky; dz = kz;
+        C.pw[t] = pw;
+        C.pix[t] = pix;
+        const ObsDev& O = J.obs[o];
+        dx = ObsGeom<R>::k(O, 0); dy = ObsGeom<R>::k(O, 1); dz = ObsGeom<R>::k(O, 2);
         ix = inv_abs(dx); iy = inv_abs(dy); iz = inv_abs(dz);
         taup = R(0);
         started = true;
@@ -980,19 +1092,149 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   }
 
   // ------------------------------------------------------------ final ledger
-  __syncwarp();
-  if (lane < 2) {
-    const int tag = SL.tag[lane][wid];
-    if (tag >= 0) {
-      LedgerDev* L = jobs[tag].ledger;
-#pragma unroll
-      for (int i = 0; i < L_ND; ++i)
-        if (SL.d[lane][i][wid]) atomicAdd(ledger_d(L, i), SlotNum<R>::value(SL.d[lane][i][wid], SL.shift[lane][wid]));
-#pragma unroll
-      for (int i = 0; i < U_NU; ++i)
-        if (SL.u[lane][i][wid]) atomicAdd(ledger_u(L, i), SL.u[lane][i][wid]);
+  ledger_flush<R>(SL, jobs, wid, lane);
+}
+
+// ------------------------------------------------------------------------
+// deferred peel-off (Sect. 2.4): one work item per (record, observer); each
+// lane marches from the scattering point to the grid edge along k_o, summing
+// the extinction optical depth, and adds W p_HG e^{-tau} to its pixel.
+// Persistent warps refill finished lanes from a global counter.
+// ------------------------------------------------------------------------
+#ifndef RT_PEEL_MIN_BLOCKS
+#define RT_PEEL_MIN_BLOCKS 4
+#endif
+template <typename R>
+struct PeelMinBlocks {
+  static constexpr int value = sizeof(R) == 4 ? RT_PEEL_MIN_BLOCKS : 2;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(const JobDev* __restrict__ jobs,
+                                                                           PeelQueue Q,
+                                                                           unsigned long long* __restrict__ work,
+                                                                           int n_obs_max, int refill_thr) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  enum { P_DEAD = 0, P_LIVE = 1, P_DONE = 2 };
+  __shared__ WarpLedger SL;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  ledger_init<R>(SL, wid, lane);
+  const long long n_rec = min((long long)*Q.count, Q.cap);
+  const long long total = n_rec * (long long)n_obs_max;
+
+  int st = P_DEAD, job = -1;
+  Geo<R> g;
+  Cursor cur;
+  GridRegs G;
+  R dx = R(0), dy = R(0), dz = R(1), ix = R(0), iy = R(0), iz = R(1);
+  R kext = R(0), taup = R(0), tau_cut = R(0), pw = R(0);
+  long long pix = 0;
+  uint32_t npeel = 0u;
+  g.lev = 0;
+  cur.pending = 0u;
+  cur.k = 0;
+  G.node = nullptr;
+  G.rho64 = nullptr;
+  G.rx = G.ry = G.rz = 1u;
+
+  for (;;) {
+    // ---------------------------------------------------------------- refill
+    const unsigned dead = __ballot_sync(FULL, st == P_DEAD);
+    const unsigned live = __ballot_sync(FULL, st == P_LIVE);
+    if (dead != 0u && (__popc(dead) >= refill_thr || live == 0u)) {
+      const int leader = __ffs(dead) - 1;
+      unsigned long long base = 0ull;
+      if (lane == leader) base = atomicAdd(work, (unsigned long long)__popc(dead));
+      base = __shfl_sync(FULL, base, leader);
+      const long long gi = (long long)base + __popc(dead & ((1u << lane) - 1u));
+      const bool have = st == P_DEAD && gi < total;
+      if (st == P_DEAD && !have) st = P_DONE;
+      Geo<R> rg;
+      R sdx = R(0), sdy = R(0), sdz = R(0), W = R(0);
+      uint32_t meta = 0u;
+      int o = 0, rjob = -1;
+      if (have) {
+        const long long rec = gi / n_obs_max;
+        o = (int)(gi - rec * n_obs_max);
+        PeelIO<R>::get(Q.rec, rec, rg, sdx, sdy, sdz, W, meta);
+        rjob = (int)(meta >> 13);
+      }
+      const int nj = __shfl_sync(FULL, rjob, leader);
+      ledger_retag<R>(SL, jobs, wid, lane, nj, st == P_LIVE ? job : -1);
+      if (have) {
+        const JobDev& J = jobs[rjob];
+        if (o < J.n_obs) {
+          rg.lev = (int)(meta & 31u);
+          const int bin = (int)((meta >> 5) & 255u);
+          const BinDev& B = J.bins[bin];
+          if (peel_setup<R>(J, o, rg, sdx, sdy, sdz, W, Num<R>::gg(B), bin, pw, pix)) {
+            const ObsDev& O = J.obs[o];
+            dx = ObsGeom<R>::k(O, 0);
+            dy = ObsGeom<R>::k(O, 1);
+            dz = ObsGeom<R>::k(O, 2);
+            ix = inv_abs(dx);
+            iy = inv_abs(dy);
+            iz = inv_abs(dz);
+            g = rg;
+            cur.pending = g.idx;
+            cur.k = g.lev;
+            G.node = J.node;
+            G.rho64 = J.rho64;
+            G.rx = J.root[0];
+            G.ry = J.root[1];
+            G.rz = J.root[2];
+            kext = Num<R>::kext(B);
+            tau_cut = Num<R>::tau_max(J) > R(0) ? Num<R>::tau_max(J) : Num<R>::inf();
+            taup = R(0);
+            npeel = 0u;
+            job = rjob;
+            st = P_LIVE;
+          } else {
+            book_u(SL, jobs, rjob, wid, U_POUT, 1ull);
+          }
+        }
+      }
+    }
+    if (__ballot_sync(FULL, st == P_LIVE) == 0u) {
+      if (__ballot_sync(FULL, st == P_DEAD) == 0u) break;
+      continue;
+    }
+
+    // ----------------------------------------------------------------- march
+    int ev = st == P_LIVE ? EV_NONE : EV_IDLE;
+    do {
+      if (ev == EV_NONE) {
+        const uint32_t w = ld_node(G.node + cur.pending);
+        const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
+        if (w & RT_INTERIOR) {
+          descend_step(g, cur, w, dx, dy, dz);
+        } else {
+          settle_leaf(g, cur, w, r64);
+          int a;
+          const R tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
+          if (a < 0) {
+            ev = EV_CUT;  // cannot happen for |k| = 1
+          } else {
+            taup += kext * g.rho * Num<R>::pow2m(g.lev) * tx;
+            npeel += tx > R(0) ? 1u : 0u;
+            if (taup > tau_cut) ev = EV_CUT;
+            else if (!advance(G, g, cur, a, tx, dx, dy, dz)) ev = EV_ESCAPE;
+          }
+        }
+      }
+    } while (__all_sync(FULL, ev == EV_NONE || ev == EV_IDLE));
+
+    if (ev == EV_ESCAPE) {
+      const R c = pw * Num<R>::exp_(-taup);
+      if (c > R(0)) atomicAdd(jobs[job].images + pix, widen(c));
+      book_d(SL, jobs, job, wid, L_PEEL, c);
+    }
+    if (ev == EV_ESCAPE || ev == EV_CUT) {
+      book_u(SL, jobs, job, wid, U_PCROSS, (unsigned long long)npeel);
+      st = P_DEAD;
     }
   }
+  ledger_flush<R>(SL, jobs, wid, lane);
 }
 
 // ------------------------------------------------------------------------
@@ -1064,35 +1306,59 @@ __global__ void philox_kernel(long long n, const uint32_t* __restrict__ ctr, con
 // ------------------------------------------------------------------------
 template <typename R, bool PEEL, int EST, bool HITS>
 static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_items, unsigned long long* counter,
-                            long long total, const LaunchCfg& cfg, cudaStream_t s) {
-  trace_kernel<R, PEEL, EST, HITS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill);
+                            long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s) {
+  trace_kernel<R, PEEL, EST, HITS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill,
+                                                                    q);
   return cudaGetLastError();
 }
 
 template <typename R, int EST>
 static cudaError_t launch_pe(bool peel, const JobDev* jobs, const ItemDev* items, int n_items,
-                             unsigned long long* counter, long long total, const LaunchCfg& cfg, cudaStream_t s) {
-  return peel ? launch_t<R, true, EST, false>(jobs, items, n_items, counter, total, cfg, s)
-              : launch_t<R, false, EST, false>(jobs, items, n_items, counter, total, cfg, s);
+                             unsigned long long* counter, long long total, const LaunchCfg& cfg,
+                             const PeelQueue& q, cudaStream_t s) {
+  return peel ? launch_t<R, true, EST, false>(jobs, items, n_items, counter, total, cfg, q, s)
+              : launch_t<R, false, EST, false>(jobs, items, n_items, counter, total, cfg, q, s);
 }
 
 // hit counting exists for the continuous estimator without peel-off (the
 // Lambda iteration's noise mask)
 cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev, long long total,
-                         const LaunchCfg& cfg, cudaStream_t s) {
+                         const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s) {
   const bool an = estimator == RT_EST_ANALOG;
   if (hits) {
     if (peel || an) return cudaErrorInvalidValue;
     return precision == 64
-               ? launch_t<double, false, RT_EST_CONTINUOUS, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
-               : launch_t<float, false, RT_EST_CONTINUOUS, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
+               ? launch_t<double, false, RT_EST_CONTINUOUS, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg,
+                                                                  q, s)
+               : launch_t<float, false, RT_EST_CONTINUOUS, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg,
+                                                                 q, s);
   }
   if (precision == 64)
-    return an ? launch_pe<double, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
-              : launch_pe<double, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
-  return an ? launch_pe<float, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s)
-            : launch_pe<float, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, s);
+    return an ? launch_pe<double, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s)
+              : launch_pe<double, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s);
+  return an ? launch_pe<float, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s)
+            : launch_pe<float, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s);
+}
+
+size_t peel_record_bytes(int precision) { return precision == 64 ? sizeof(PeelRec64) : sizeof(PeelRec32); }
+
+template <typename R>
+static cudaError_t launch_peel_t(const JobDev* jobs, const PeelQueue& q, unsigned long long* work, int n_obs_max,
+                                 int refill, cudaStream_t s) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, peel_kernel<R>, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+  peel_kernel<R><<<sms * occ, 256, 0, s>>>(jobs, q, work, n_obs_max, refill);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
+                        int n_obs_max, int refill, cudaStream_t s) {
+  if (q.cap <= 0 || n_obs_max <= 0) return cudaSuccess;
+  return precision == 64 ? launch_peel_t<double>(jobs_dev, q, work_dev, n_obs_max, refill, s)
+                         : launch_peel_t<float>(jobs_dev, q, work_dev, n_obs_max, refill, s);
 }
 
 template <typename R, bool PEEL>

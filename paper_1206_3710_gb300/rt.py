@@ -26,7 +26,7 @@ EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "r
             "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate", "rt_trace_batch", "rt_batch_create",
             "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load", "rt_server_create",
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
-            "rt_server_stats", "rt_server_destroy"]
+            "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue"]
 
 
 class RtError(RuntimeError):
@@ -73,7 +73,8 @@ class rt_trace_params(C.Structure):
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
-                 "n_scatter", "n_peel_cross", "n_killed", "n_peel_out", "status", "kernel_ms"]
+                 "n_scatter", "n_peel_cross", "n_killed", "n_peel_out", "n_peel_deferred", "status", "kernel_ms",
+                 "peel_ms"]
 
 
 class rt_ledger(C.Structure):
@@ -81,7 +82,8 @@ class rt_ledger(C.Structure):
                 ("rr_gain", C.c_double), ("rr_loss", C.c_double), ("killed", C.c_double), ("peeled", C.c_double),
                 ("n_packets", C.c_uint64), ("n_cross", C.c_uint64), ("n_scatter", C.c_uint64),
                 ("n_peel_cross", C.c_uint64), ("n_killed", C.c_uint64), ("n_peel_out", C.c_uint64),
-                ("status", C.c_int), ("kernel_ms", C.c_double)]
+                ("n_peel_deferred", C.c_uint64), ("status", C.c_int), ("kernel_ms", C.c_double),
+                ("peel_ms", C.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n in LEDGER_FIELDS}
@@ -227,6 +229,11 @@ class Context:
         _check(lib().rt_ctx_create(device, C.byref(h)))
         self.handle = h
         self.device = device
+
+    def set_peel_queue(self, max_records: int) -> None:
+        """Capacity of the deferred peel-off queue in records (0: peel off
+        inline in the tracer; < 0: the default)."""
+        _check(lib().rt_ctx_set_peel_queue(self.handle, C.c_int64(int(max_records))))
 
     def close(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -350,6 +350,40 @@ def test_fp64_cloud_external_peel(rt, ctx, orc):
     assert out["led"]["n_peel_cross"] == out["ref"]["ledger"]["n_peel_cross"]
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_deferred_peel_equals_inline(rt, precision):
+    """Peel-off deferred to the peel-off kernel, done inline in the tracer,
+    and split between the two by a queue that overflows give the same images,
+    absorbed energy and counters (only the order of the FP64 additions
+    differs)."""
+    m = _small_cloud()
+    res = {}
+    for name, cap in (("deferred", -1), ("inline", 0), ("mixed", 100)):
+        c = rt.Context(0)
+        c.set_peel_queue(cap)
+        g = rt.Grid(c, m.tree)
+        nl = m.optics.n_lambda
+        ab = _zeros(nl, g.n_cells)
+        im = _zeros(m.observers.n_obs, nl, m.observers.ny, m.observers.nx)
+        led = rt.rt_peel(c, g, m.sources, m.optics, m.observers, im, ab, seed=31, precision=precision,
+                         packets_per_bin=3000, rr_wmin=1e-3, rr_p=0.5)
+        res[name] = (ab.cpu().numpy(), im.cpu().numpy(), led)
+        c.close()
+    ab0, im0, l0 = res["inline"]
+    assert l0["n_peel_deferred"] == 0 and l0["n_scatter"] > 1000
+    assert res["deferred"][2]["n_peel_deferred"] == l0["n_scatter"]
+    assert res["mixed"][2]["n_peel_deferred"] == 100
+    for name in ("deferred", "mixed"):
+        ab, im, led = res[name]
+        np.testing.assert_allclose(ab, ab0, rtol=1e-12, atol=1e-14 * np.abs(ab0).max())
+        np.testing.assert_allclose(im, im0, rtol=1e-12, atol=1e-14 * np.abs(im0).max())
+        for k in ("n_packets", "n_cross", "n_scatter", "n_peel_cross", "n_peel_out"):
+            assert led[k] == l0[k], (name, k)
+        for k in ("emitted", "absorbed", "escaped", "peeled", "rr_gain", "rr_loss"):
+            assert led[k] == pytest.approx(l0[k], rel=1e-12), (name, k)
+        assert led["peel_ms"] > 0
+
+
 def test_fp64_roulette_and_summed_bins(rt, ctx, orc):
     m = _small_cloud(n_root=16, levels=2, n_lambda=4)
     out = _run_pair(rt, ctx, orc, m, 3000, 64, seed=22, rr_wmin=0.3, rr_p=0.6, per_lambda=False)
