@@ -36,10 +36,12 @@ UNIT = "cell crossings/s"
 BYTES_TRACE_CROSS = 4 + 16      # node word + FP64 accumulator read-modify-write
 BYTES_PEEL_CROSS = 4            # node word
 BYTES_IMAGE_DEPOSIT = 16        # FP64 pixel read-modify-write
-# DRAM traffic of the tracer kernel per launch measured by ncu (bytes per
-# trace-equivalent unit); None until a capture of the current kernel exists
-NCU_TRAFFIC_PER_LAUNCH = None
-NCU_PEEL_TRAFFIC_PER_LAUNCH = None
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# of the tracer and of the deferred peel-off kernel on the default molecular
+# cloud workload, from a single-pass ncu capture of the current kernels (set
+# to None whenever a kernel changes until it is captured again)
+NCU_TRAFFIC_PER_LAUNCH = 3991218162688 + 1116500421120       # dram read + write, one launch
+NCU_PEEL_TRAFFIC_PER_LAUNCH = 466647693312 + 5282686208       # of this exact workload
 
 
 def parse():

@@ -501,27 +501,43 @@ __device__ __forceinline__ void ledger_flush(WarpLedger& SL, const JobDev* jobs,
   }
 }
 
-#ifndef RT_RED_HINT
-#define RT_RED_HINT 1
+// L2 residency hints (createpolicy + .L2::cache_hint): 0 none, 1 evict_last,
+// 2 evict_first.  The node words of the grid are read at every crossing; the
+// accumulator lines take a few consecutive deposits and are then not touched
+// for a long time, so they are marked evict_first and do not push the node
+// words out.
+#ifndef RT_NODE_HINT
+#define RT_NODE_HINT 1
 #endif
-// L2 residency hints: the node words of the grid are read at every crossing
-// and should stay in L2 (evict_last); accumulator lines are touched by a few
-// consecutive deposits and then not again for a long time (evict_first), so
-// they should not push the node words out.
+#ifndef RT_RED_HINT
+#define RT_RED_HINT 2
+#endif
 __device__ __forceinline__ uint32_t ld_node(const uint32_t* p) {
+#if RT_NODE_HINT == 0
+  return __ldg(p);
+#else
   uint64_t pol;
+#if RT_NODE_HINT == 1
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+#else
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+#endif
   uint32_t w;
   asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(w) : "l"(p), "l"(pol));
   return w;
+#endif
 }
 __device__ __forceinline__ void red_acc(double* p, double v) {
-#if RT_RED_HINT
-  uint64_t pol;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
-#else
+#if RT_RED_HINT == 0
   atomicAdd(p, v);
+#else
+  uint64_t pol;
+#if RT_RED_HINT == 1
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+#else
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+#endif
+  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
 #endif
 }
 
