@@ -63,6 +63,18 @@ void rt_ctx_destroy(rt_ctx* ctx);
  * results.  max_records = 0 disables deferral, < 0 restores the default
  * (2^27).  Takes effect at the next launch (and at rt_batch_create). */
 int rt_ctx_set_peel_queue(rt_ctx* ctx, int64_t max_records);
+/* Tiled tracing (the GPU form of the grid-by-grid processing of Sect. 2.2 and
+ * App. A): for single-job rt_trace / rt_peel / rt_lambda_iterate launches the
+ * root grid is cut into cubic tiles of tile_edge root cells (a power of
+ * two); packages are traced in rounds, each round one (wavelength bin, tile)
+ * after another, and a package that enters another tile continues in the
+ * next round.  Results are those of the untiled tracer (the same package
+ * histories; only the order of the FP64 additions differs).  tile_edge < 0:
+ * automatic (tiles whose node words plus one bin's accumulators take at most
+ * 48 MB, only when the whole grid's take more); 0: off.  Uses two record
+ * buffers of up to 2^25 (FP32, 80 B each) or 2^24 (FP64, 128 B each)
+ * records.  Returns RT_ERR_INVALID if tile_edge is not a power of two. */
+int rt_ctx_set_tiles(rt_ctx* ctx, int tile_edge);
 /* Message of the last failing call on this thread (static storage, valid
  * until the next call on the same thread). */
 const char* rt_last_error(void);

@@ -88,6 +88,9 @@ struct rt_ctx {
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr, ev_m = nullptr;
   DevBuf peel_q;                          // deferred peel-off records
   long long peel_q_max = 1ll << 27;       // records; 0: peel-off inline
+  int tile_edge = -1;                     // tiled tracing: -1 auto, 0 off, > 0 tile edge in root cells
+  DevBuf tile_a, tile_b, tile_key, tile_hist;
+  unsigned long long* pin_count = nullptr;  // pinned: record count read back per round
   // launch defaults chosen by rt_autotune, per [FP64][peel-off]
   struct Tuned {
     bool set = false;
@@ -156,6 +159,7 @@ extern "C" int rt_ctx_create(int device, rt_ctx** out) {
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_b);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_c);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_m);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pin_count, 64);
   if (e != cudaSuccess) {
     delete c;
     return fail(RT_ERR_CUDA, "rt_ctx_create: %s", cudaGetErrorString(e));
@@ -178,8 +182,22 @@ extern "C" void rt_ctx_destroy(rt_ctx* c) {
   if (c->ev_b) cudaEventDestroy(c->ev_b);
   if (c->ev_c) cudaEventDestroy(c->ev_c);
   if (c->ev_m) cudaEventDestroy(c->ev_m);
+  if (c->pin_count) cudaFreeHost(c->pin_count);
   c->peel_q.release();
+  c->tile_a.release();
+  c->tile_b.release();
+  c->tile_key.release();
+  c->tile_hist.release();
   delete c;
+}
+
+extern "C" int rt_ctx_set_tiles(rt_ctx* c, int tile_edge) {
+  if (!c) return fail(RT_ERR_INVALID, "rt_ctx_set_tiles: NULL context");
+  if (tile_edge > 0 && (tile_edge & (tile_edge - 1)))
+    return fail(RT_ERR_INVALID, "rt_ctx_set_tiles: tile edge must be a power of two");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->tile_edge = tile_edge < 0 ? -1 : tile_edge;
+  return RT_OK;
 }
 
 extern "C" int rt_ctx_set_peel_queue(rt_ctx* c, int64_t max_records) {
@@ -777,6 +795,85 @@ static int make_cfg(rt_ctx* c, int precision, bool peel, const rt_trace_params* 
   return RT_OK;
 }
 
+// Tiled tracing pays off when one wavelength's working set (4-byte node word
+// and 8-byte accumulator per cell) is well above the L2 (129 MB on GB300):
+// the root grid is cut into tiles of edge 2^tsh root cells whose working set
+// is at most 48 MB.  Single-job launches only.
+static bool choose_tiles(const rt_ctx* c, const rt_grid* G, int n_jobs, TileRun* T) {
+  if (n_jobs != 1 || c->tile_edge == 0) return false;
+  const int* R = G->root;
+  auto count = [&](int edge) {
+    return (long long)((R[0] + edge - 1) / edge) * ((R[1] + edge - 1) / edge) * ((R[2] + edge - 1) / edge);
+  };
+  int edge = c->tile_edge;
+  if (edge < 0) {
+    const double ws = 12.0 * (double)G->n_cells, cap = 48.0 * 1024 * 1024;
+    if (ws <= cap) return false;
+    const double need = ws / cap;
+    edge = 1;
+    while (edge * 2 <= std::max(R[0], std::max(R[1], R[2]))) edge *= 2;
+    while (edge > 1 && count(edge) < need) edge /= 2;
+  }
+  while (count(edge) > 512) edge *= 2;  // key space: bins x tiles
+  if (count(edge) < 2) return false;
+  int tsh = 0;
+  while ((1 << tsh) < edge) ++tsh;
+  memset(T, 0, sizeof *T);
+  T->tsh = tsh;
+  T->ntx = (R[0] + edge - 1) / edge;
+  T->nty = (R[1] + edge - 1) / edge;
+  T->n_tiles = (int)count(edge);
+  return true;
+}
+
+// Tiled run of one job: emit the packages chunk by chunk into records, then
+// sort by (bin, tile) and trace round after round until no package is left.
+static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool peel, int estimator, bool hits,
+                     const JobDev* jobs_dev, const ItemDev* items_dev, int n_items, long long total,
+                     const LaunchCfg& cfg, const PeelQueue& q, unsigned long long* counter,
+                     unsigned long long* n_out, int* status, double timeout_s, cudaStream_t s) {
+  const long long chunk = std::min<long long>(total, precision == 64 ? (1ll << 24) : (1ll << 25));
+  const size_t rb = tile_record_bytes(precision);
+  const int n_keys = n_lambda * T.n_tiles;
+  int rc = c->tile_a.ensure(rb * (size_t)chunk);
+  if (!rc) rc = c->tile_b.ensure(rb * (size_t)chunk);
+  if (!rc) rc = c->tile_key.ensure(sizeof(uint32_t) * (size_t)chunk);
+  if (!rc) rc = c->tile_hist.ensure(sizeof(unsigned long long) * ((size_t)n_keys + 1));
+  if (rc) return rc;
+  T.out_key = reinterpret_cast<uint32_t*>(c->tile_key.p);
+  T.n_out = n_out;
+  T.cap_out = chunk;
+  T.status = status;
+  for (long long c0 = 0; c0 < total; c0 += chunk) {
+    const long long c1 = std::min(total, c0 + chunk);
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(n_out, 0, sizeof(unsigned long long), s));
+    T.in = nullptr;
+    T.out = c->tile_a.p;
+    T.first = c0;
+    CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, c1, cfg, q, s, 1, &T));
+    for (long long round = 0;; ++round) {
+      if (round > 10000000) return fail(RT_ERR_CUDA, "tiled tracing did not finish");
+      CK(cudaMemcpyAsync(c->pin_count, n_out, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(c->ev_c, s));
+      rc = wait_event(c->ev_c, timeout_s);
+      if (rc) return rc;
+      const long long n = (long long)c->pin_count[0];
+      if (n == 0) break;
+      if (n > chunk) return fail(RT_ERR_CUDA, "tile record buffer overflow (%lld > %lld)", n, chunk);
+      CK(tile_sort(c->tile_a.p, T.out_key, n, (int)rb, n_keys, reinterpret_cast<unsigned long long*>(c->tile_hist.p),
+                   c->tile_b.p, s));
+      CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+      CK(cudaMemsetAsync(n_out, 0, sizeof(unsigned long long), s));
+      T.in = c->tile_b.p;
+      T.out = c->tile_a.p;
+      T.first = 0;
+      CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, n, cfg, q, s, 2, &T));
+    }
+  }
+  return RT_OK;
+}
+
 static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* ledgers, cudaStream_t s,
                     const rt_trace_params* launch_prm) {
   // ledgers + package counter
@@ -794,7 +891,9 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   rc = build_tables(c, n_jobs, jobs, led, s, A, job_off, items_off, n_items, total, peel, precision, estimator);
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(c->table.p);
-  CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + 3 * sizeof(unsigned long long), s));
+  // counter[0] packages, [1] peel-off queue length, [2] peel-off work,
+  // [3] tile records written, [4] tile status
+  CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + 5 * sizeof(unsigned long long), s));
   const PeelQueue q = make_queue(c->peel_q, c->peel_q_max, peel, n_jobs, total, precision, counter + 1);
   LaunchCfg cfg;
   rc = make_cfg(c, precision, peel, launch_prm, &cfg);
@@ -803,10 +902,20 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   for (int j = 0; j < n_jobs; ++j) hits = hits || jobs[j].prm->hits_dev != nullptr;
   if (hits && (peel || estimator != RT_EST_CONTINUOUS))
     return fail(RT_ERR_INVALID, "hit counting needs rt_trace with the continuous estimator");
+  const double to = launch_prm->timeout_s > 0 ? launch_prm->timeout_s : 3600.0;
+  TileRun tiles;
+  const bool tiled = total > 0 && n_items > 0 && choose_tiles(c, jobs[0].grid, n_jobs, &tiles);
+  int* tile_status = reinterpret_cast<int*>(counter + 4);
   CK(cudaEventRecord(c->ev_a, s));
-  if (total > 0 && n_items > 0)
+  if (tiled) {
+    rc = run_tiled(c, tiles, jobs[0].optics->n_lambda, precision, peel, estimator, hits,
+                   reinterpret_cast<const JobDev*>(base + job_off[0]), reinterpret_cast<const ItemDev*>(base + items_off),
+                   n_items, total, cfg, q, counter, counter + 3, tile_status, to, s);
+    if (rc) return rc;
+  } else if (total > 0 && n_items > 0) {
     CK(launch_trace(precision, peel, estimator, hits, reinterpret_cast<const JobDev*>(base + job_off[0]),
                     reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, q, s));
+  }
   CK(cudaEventRecord(c->ev_m, s));
   if (total > 0 && n_items > 0 && q.cap > 0)
     CK(launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
@@ -814,10 +923,12 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   CK(cudaEventRecord(c->ev_b, s));
   std::vector<LedgerDev> hl(n_jobs);
   CK(cudaMemcpyAsync(hl.data(), led, sizeof(LedgerDev) * n_jobs, cudaMemcpyDeviceToHost, s));
+  int tstat = 0;
+  if (tiled) CK(cudaMemcpyAsync(&tstat, tile_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(c->ev_c, s));
-  const double to = launch_prm->timeout_s > 0 ? launch_prm->timeout_s : 3600.0;
   rc = wait_event(c->ev_c, to);
   if (rc) return rc;
+  if (tstat) return fail(RT_ERR_CUDA, "tile record buffer overflow");
   float ms = 0.f, ms_peel = 0.f;
   cudaEventElapsedTime(&ms, c->ev_a, c->ev_m);
   cudaEventElapsedTime(&ms_peel, c->ev_m, c->ev_b);

@@ -67,6 +67,40 @@ struct PeelRec64 {
   uint32_t meta, pad;
 };
 #define RT_PEEL_MAX_JOBS (1 << 19)
+
+// Tiled tracing, the GPU form of the grid-by-grid processing of Sect. 2.2
+// (App. A): the root grid is cut into tiles of 2^tsh root cells per axis.
+// Packages are emitted into records, sorted by (bin, tile), and traced in
+// rounds; a package that crosses into another tile is written back to a
+// record for the next round, so the cells touched at any time belong to a
+// few (bin, tile) pairs whose node words and accumulators stay in L2.
+struct TRec32 {
+  uint32_t cx, cy, cz, meta;  // lattice coordinates at level; meta = lev | bin << 5 | job << 13
+  float fx, fy, fz, W;
+  float dx, dy, dz, tau;
+  float pkt_abs;
+  uint32_t next, nscat, ncross;
+  unsigned long long gi;      // package index in the launch's package counter
+  uint32_t npeel, pad;
+};
+struct TRec64 {
+  uint32_t cx, cy, cz, meta;
+  double fx, fy, fz, W;
+  double dx, dy, dz, tau;
+  double pkt_abs;
+  uint32_t next, nscat, ncross, npeel;
+  unsigned long long gi, pad0, pad1;
+};
+struct TileRun {
+  const void* in;               // run: records sorted by key
+  void* out;                    // emit/run: records written for the next round
+  uint32_t* out_key;            // their keys: bin * n_tiles + tile
+  unsigned long long* n_out;    // records written
+  long long cap_out;
+  long long first;              // emit: index of the first package of the chunk
+  int tsh, ntx, nty, n_tiles;
+  int* status;                  // bit 0: record buffer overflow
+};
 struct PeelQueue {
   void* rec;                    // PeelRec32 or PeelRec64 [cap]
   unsigned long long* count;    // records requested (may exceed cap: the rest peel inline)
@@ -146,10 +180,18 @@ struct LaunchCfg {
   int refill;
 };
 
-// launch the persistent tracer over n_items items of total packages
+// launch the persistent tracer over n_items items of total packages;
+// mode 0 plain, 1 emit into tile records (packages [T.first, total)),
+// 2 trace the records T.in[0, total) within their tiles
 cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev,
-                         long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s);
+                         long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s,
+                         int mode = 0, const TileRun* tiles = nullptr);
+size_t tile_record_bytes(int precision);
+// counting sort of n records (rec_bytes each) by key (< n_keys) from in/key
+// into out; hist_dev holds n_keys + 1 counters
+cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_bytes, int n_keys,
+                      unsigned long long* hist_dev, void* out, cudaStream_t s);
 cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm);
 // march the queued peel-off records (n_obs_max observers each); work_dev is a
 // zeroed counter

@@ -26,6 +26,9 @@
 //    energy by FP64 atomics (RED) into [bin][cell].
 #include <math_constants.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "philox.cuh"
 #include "rt_internal.cuh"
 
@@ -350,7 +353,7 @@ struct WarpLedger {
 template <typename R>
 struct ColdState {
   uint32_t k0[256], k1[256], c0[256], c1[256], c3[256], next[256];
-  long long log_index[256], pix[256];
+  long long log_index[256], pix[256], gi[256];
   R W0[256], pw[256], gpar[256];
   int bin[256], nscat[256], obs_i[256], job[256];
   // scattering point and incoming direction, saved during the peel-off
@@ -578,7 +581,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 enum { ST_DEAD = 0, ST_TRACE = 1, ST_PEEL = 2, ST_DONE = 3 };
-enum { EV_NONE = 0, EV_IDLE, EV_INTERACT, EV_ESCAPE, EV_CUT, EV_KILL, EV_DEGEN };
+enum { EV_NONE = 0, EV_IDLE, EV_INTERACT, EV_ESCAPE, EV_CUT, EV_KILL, EV_DEGEN, EV_TILE };
 
 // ------------------------------------------------------------------------
 // deferred peel-off records
@@ -662,6 +665,27 @@ __device__ __forceinline__ bool peel_setup(const JobDev& J, int o, const Geo<R>&
   return true;
 }
 
+// ------------------------------------------------------------------------
+// tiled tracing: package records between rounds
+// ------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ uint32_t tile_of(const Geo<R>& g, const TileRun& T) {
+  const int s = g.lev + T.tsh;
+  return (g.cx >> s) + (uint32_t)T.ntx * ((g.cy >> s) + (uint32_t)T.nty * (g.cz >> s));
+}
+
+template <typename R>
+struct TileIO;
+template <>
+struct TileIO<float> {
+  typedef TRec32 Rec;
+};
+template <>
+struct TileIO<double> {
+  typedef TRec64 Rec;
+};
+static_assert(sizeof(TRec32) == 80 && sizeof(TRec64) == 128, "tile record layout");
+
 #ifndef RT_FP32_MIN_BLOCKS
 #define RT_FP32_MIN_BLOCKS 4
 #endif
@@ -671,13 +695,14 @@ struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? RT_FP32_MIN_BLOCKS : 2;
 };
 
-template <typename R, bool PEEL, int EST, bool HITS>
+template <typename R, bool PEEL, int EST, bool HITS, int MODE>
 __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const JobDev* __restrict__ jobs,
                                                                          const ItemDev* __restrict__ items,
                                                                          int n_items,
                                                                          unsigned long long* __restrict__ counter,
                                                                          long long total, int refill_thr,
-                                                                         PeelQueue Q) {
+                                                                         PeelQueue Q, TileRun T) {
+  typedef typename TileIO<R>::Rec TRec;
   const unsigned FULL = 0xFFFFFFFFu;
   __shared__ WarpLedger SL;
   __shared__ ColdState<R> C;
@@ -706,6 +731,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   double* absb = nullptr;
   unsigned int* hitp = nullptr;
   uint32_t step_limit = 0u, ncross = 0u, npeel = 0u;
+  uint32_t tile_cur = 0u;  // tiled rounds: the tile this lane traces in
 
   // after a scattering (and its peel-off): new direction from the phase
   // function, Russian roulette when the weight is low, next free path.
@@ -734,6 +760,28 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
     return -1;
   };
 
+  // tiled tracing: hand the package to the next round as a record (its
+  // current position, direction, weight, optical depth to the next
+  // interaction, random-number position and counters)
+  auto tile_push = [&]() {
+    const unsigned long long slot = atomicAdd(T.n_out, 1ull);
+    if (slot < (unsigned long long)T.cap_out) {
+      TRec r;
+      r.cx = g.cx; r.cy = g.cy; r.cz = g.cz;
+      r.meta = peel_meta(g.lev, C.bin[t], C.job[t]);
+      r.fx = g.fx; r.fy = g.fy; r.fz = g.fz; r.W = W;
+      r.dx = dx; r.dy = dy; r.dz = dz; r.tau = tau;
+      r.pkt_abs = pkt_abs;
+      r.next = C.next[t]; r.nscat = (uint32_t)C.nscat[t]; r.ncross = ncross; r.npeel = npeel;
+      r.gi = (unsigned long long)C.gi[t];
+      static_cast<TRec*>(T.out)[slot] = r;
+      T.out_key[slot] = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
+    } else {
+      atomicOr(T.status, 1);
+    }
+    st = ST_DEAD;
+  };
+
   for (;;) {
     // ---------------------------------------------------------------- refill
     const unsigned dead = __ballot_sync(FULL, st == ST_DEAD);
@@ -743,9 +791,15 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       unsigned long long base = 0ull;
       if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(dead));
       base = __shfl_sync(FULL, base, leader);
-      const long long gi = (long long)base + __popc(dead & ((1u << lane) - 1u));
+      const long long slot = (long long)base + __popc(dead & ((1u << lane) - 1u));
+      long long gi = MODE == 1 ? T.first + slot : slot;  // package index
+      const TRec* rec = nullptr;
+      if (MODE == 2 && st == ST_DEAD && slot < total) {
+        rec = static_cast<const TRec*>(T.in) + slot;
+        gi = (long long)rec->gi;
+      }
       int lo = -1;
-      if (st == ST_DEAD && gi < total) {
+      if (st == ST_DEAD && (MODE == 2 ? rec != nullptr : gi < total)) {
         lo = 0;
         int hi = n_items - 1;
         while (lo < hi) {
@@ -760,12 +814,68 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       if (st == ST_DEAD) {
         if (lo < 0) {
           st = ST_DONE;
+        } else if (MODE == 2) {
+          // ---------------------------------- resume a package from its record
+          const TRec r = *rec;
+          const ItemDev& I = items[lo];
+          const int job = I.job;
+          const JobDev& J = jobs[job];
+          C.job[t] = job;
+          C.gi[t] = gi;
+          G.node = J.node;
+          G.rho64 = J.rho64;
+          G.rx = J.root[0];
+          G.ry = J.root[1];
+          G.rz = J.root[2];
+          step_limit = (uint32_t)min(J.step_limit, (long long)0xFFFFFFFFll);
+          tau_cut = Num<R>::tau_max(J) > R(0) ? Num<R>::tau_max(J) : Num<R>::inf();
+          const long long p = gi - I.pkt_begin;
+          const int bin = (int)((r.meta >> 5) & 255u);
+          const unsigned long long k = (unsigned long long)(p - I.bin_prefix[bin]);
+          C.bin[t] = bin;
+          C.log_index[t] = J.packet_log ? I.log_offset + p : -1;
+          C.k0[t] = (uint32_t)J.seed ^ J.job_id;
+          C.k1[t] = (uint32_t)(J.seed >> 32) ^ J.iter;
+          C.c0[t] = (uint32_t)k;
+          C.c1[t] = (uint32_t)(k >> 32);
+          C.c3[t] = (I.src_index << 16) | (uint32_t)bin;
+          C.next[t] = r.next;
+          C.rtag[t] = 0xFFFFFFFFu;
+          const BinDev& B = J.bins[bin];
+          kext = Num<R>::kext(B);
+          alb = Num<R>::alb(B);
+          C.gpar[t] = Num<R>::gg(B);
+          absb = J.absorbed ? J.absorbed + (long long)(J.abs_bins > 1 ? bin : 0) * J.n_cells : nullptr;
+          if (HITS) hitp = J.hits;
+          C.W0[t] = Num<R>::w0(I, bin);
+          C.nscat[t] = (int)r.nscat;
+          W = r.W;
+          tau = r.tau;
+          pkt_abs = r.pkt_abs;
+          ncross = r.ncross;
+          npeel = r.npeel;
+          g.cx = r.cx; g.cy = r.cy; g.cz = r.cz;
+          g.lev = (int)(r.meta & 31u);
+          g.fx = r.fx; g.fy = r.fy; g.fz = r.fz;
+          g.idx = 0u;
+          g.rho = R(0);
+          dx = r.dx; dy = r.dy; dz = r.dz;
+          ix = inv_abs(dx);
+          iy = inv_abs(dy);
+          iz = inv_abs(dz);
+          // the package sits on the face of a root cell of this tile:
+          // descend from that root cell
+          cur.pending = (g.cx >> g.lev) + G.rx * ((g.cy >> g.lev) + G.ry * (g.cz >> g.lev));
+          cur.k = 0;
+          tile_cur = tile_of(g, T);
+          st = ST_TRACE;
         } else {
           // ------------------------------------------------ emission (Sect. 2.3)
           const ItemDev& I = items[lo];
           const int job = I.job;
           const JobDev& J = jobs[job];
           C.job[t] = job;
+          C.gi[t] = gi;
           G.node = J.node;
           G.rho64 = J.rho64;
           G.rx = J.root[0];
@@ -901,6 +1011,13 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
         }
       }
     }
+    if (MODE == 1) {
+      // emission round of tiled tracing: every emitted package becomes a
+      // record keyed by its (bin, tile)
+      if (st == ST_TRACE) tile_push();
+      if (__ballot_sync(FULL, st == ST_DEAD) == 0u) break;
+      continue;
+    }
     if (__ballot_sync(FULL, st == ST_TRACE || st == ST_PEEL) == 0u) {
       // nothing to step: finished, or packages that left at emission
       if (__ballot_sync(FULL, st == ST_DEAD) == 0u) break;
@@ -974,6 +1091,8 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
               ev = EV_CUT;
             } else if (!advance(G, g, cur, a, tx, dx, dy, dz)) {
               ev = EV_ESCAPE;
+            } else if (MODE == 2 && tr && cur.k == 0 && tile_of(g, T) != tile_cur) {
+              ev = EV_TILE;  // entered another tile: next round
             }
           }
         }
@@ -1003,6 +1122,8 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
         book_d(SL, jobs, job, wid, L_PEEL, c);
         pick_observer = true;
       }
+    } else if (MODE == 2 && ev == EV_TILE) {
+      tile_push();
     } else {  // EV_INTERACT: absorption (analog) or scattering in this cell
       bool scatter = true;
       if (EST == RT_EST_ANALOG) {
@@ -1322,39 +1443,146 @@ __global__ void philox_kernel(long long n, const uint32_t* __restrict__ ctr, con
 // ------------------------------------------------------------------------
 template <typename R, bool PEEL, int EST, bool HITS>
 static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_items, unsigned long long* counter,
-                            long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s) {
-  trace_kernel<R, PEEL, EST, HITS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill,
-                                                                    q);
+                            long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode,
+                            const TileRun* tr) {
+  TileRun T;
+  memset(&T, 0, sizeof T);
+  if (tr) T = *tr;
+  if (mode == 1)
+    trace_kernel<R, PEEL, EST, HITS, 1><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total,
+                                                                        cfg.refill, q, T);
+  else if (mode == 2)
+    trace_kernel<R, PEEL, EST, HITS, 2><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total,
+                                                                        cfg.refill, q, T);
+  else
+    trace_kernel<R, PEEL, EST, HITS, 0><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total,
+                                                                        cfg.refill, q, T);
   return cudaGetLastError();
 }
 
 template <typename R, int EST>
 static cudaError_t launch_pe(bool peel, const JobDev* jobs, const ItemDev* items, int n_items,
                              unsigned long long* counter, long long total, const LaunchCfg& cfg,
-                             const PeelQueue& q, cudaStream_t s) {
-  return peel ? launch_t<R, true, EST, false>(jobs, items, n_items, counter, total, cfg, q, s)
-              : launch_t<R, false, EST, false>(jobs, items, n_items, counter, total, cfg, q, s);
+                             const PeelQueue& q, cudaStream_t s, int mode, const TileRun* tr) {
+  return peel ? launch_t<R, true, EST, false>(jobs, items, n_items, counter, total, cfg, q, s, mode, tr)
+              : launch_t<R, false, EST, false>(jobs, items, n_items, counter, total, cfg, q, s, mode, tr);
 }
 
 // hit counting exists for the continuous estimator without peel-off (the
 // Lambda iteration's noise mask)
 cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev, long long total,
-                         const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s) {
+                         const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode, const TileRun* tr) {
   const bool an = estimator == RT_EST_ANALOG;
+  if ((mode == 1 || mode == 2) && !tr) return cudaErrorInvalidValue;
   if (hits) {
     if (peel || an) return cudaErrorInvalidValue;
     return precision == 64
                ? launch_t<double, false, RT_EST_CONTINUOUS, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg,
-                                                                  q, s)
+                                                                  q, s, mode, tr)
                : launch_t<float, false, RT_EST_CONTINUOUS, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg,
-                                                                 q, s);
+                                                                 q, s, mode, tr);
   }
   if (precision == 64)
-    return an ? launch_pe<double, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s)
-              : launch_pe<double, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s);
-  return an ? launch_pe<float, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s)
-            : launch_pe<float, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s);
+    return an ? launch_pe<double, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s,
+                                                 mode, tr)
+              : launch_pe<double, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q,
+                                                     s, mode, tr);
+  return an ? launch_pe<float, RT_EST_ANALOG>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s, mode,
+                                              tr)
+            : launch_pe<float, RT_EST_CONTINUOUS>(peel, jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s,
+                                                  mode, tr);
+}
+
+size_t tile_record_bytes(int precision) { return precision == 64 ? sizeof(TRec64) : sizeof(TRec32); }
+
+// ------------------------------------------------------------------------
+// counting sort of tile records by key
+// ------------------------------------------------------------------------
+__global__ void tile_hist_kernel(const uint32_t* __restrict__ key, long long n, int n_keys,
+                                 unsigned long long* __restrict__ hist) {
+  extern __shared__ unsigned int sh[];
+  const bool use_sh = n_keys <= 8192;
+  if (use_sh)
+    for (int k = threadIdx.x; k < n_keys; k += blockDim.x) sh[k] = 0u;
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t k = key[i];
+    if (use_sh) atomicAdd(&sh[k], 1u);
+    else atomicAdd(&hist[k], 1ull);
+  }
+  __syncthreads();
+  if (use_sh)
+    for (int k = threadIdx.x; k < n_keys; k += blockDim.x)
+      if (sh[k]) atomicAdd(&hist[k], (unsigned long long)sh[k]);
+}
+
+// exclusive prefix sum of hist[0, n) in place, one block
+__global__ void tile_scan_kernel(unsigned long long* hist, int n) {
+  __shared__ unsigned long long part[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int per = (n + nt - 1) / nt;
+  const int b = t * per, e = min(n, b + per);
+  unsigned long long sum = 0ull;
+  for (int i = b; i < e; ++i) sum += hist[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    const unsigned long long v = t >= off ? part[t - off] : 0ull;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  unsigned long long run = part[t] - sum;
+  for (int i = b; i < e; ++i) {
+    const unsigned long long v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+// scatter records to their key's range; lanes of a warp with equal keys
+// take consecutive places with one atomic
+__global__ void tile_scatter_kernel(const uint4* __restrict__ in, const uint32_t* __restrict__ key, long long n,
+                                    int rec_u4, unsigned long long* __restrict__ offs, uint4* __restrict__ out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long n_up = (n + 31) / 32 * 32;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
+    const bool have = i < n;
+    const uint32_t k = have ? key[i] : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    unsigned long long base = 0ull;
+    if (have && lane == leader) base = atomicAdd(&offs[k], (unsigned long long)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (have) {
+      const unsigned long long pos = base + __popc(peers & ((1u << lane) - 1u));
+      const uint4* src = in + i * rec_u4;
+      uint4* dst = out + pos * rec_u4;
+      for (int w = 0; w < rec_u4; ++w) dst[w] = src[w];
+    }
+  }
+}
+
+cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_bytes, int n_keys,
+                      unsigned long long* hist_dev, void* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (rec_bytes % 16) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(hist_dev, 0, sizeof(unsigned long long) * (size_t)n_keys, s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int B = 512;
+  const long long want = (n + B - 1) / B;
+  const int G = (int)std::min<long long>(want, (long long)sms * 4);
+  const size_t shb = n_keys <= 8192 ? sizeof(unsigned int) * (size_t)n_keys : 0;
+  tile_hist_kernel<<<G, B, shb, s>>>(key, n, n_keys, hist_dev);
+  tile_scan_kernel<<<1, 1024, 0, s>>>(hist_dev, n_keys);
+  tile_scatter_kernel<<<G, B, 0, s>>>(static_cast<const uint4*>(in), key, n, rec_bytes / 16, hist_dev,
+                                      static_cast<uint4*>(out));
+  return cudaGetLastError();
 }
 
 size_t peel_record_bytes(int precision) { return precision == 64 ? sizeof(PeelRec64) : sizeof(PeelRec32); }
@@ -1379,7 +1607,7 @@ cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& 
 
 template <typename R, bool PEEL>
 static cudaError_t occ_t(int block, int* n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 0>, block, 0);
 }
 
 cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm) {

@@ -26,7 +26,7 @@ EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "r
             "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate", "rt_trace_batch", "rt_batch_create",
             "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load", "rt_server_create",
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
-            "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue"]
+            "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles"]
 
 
 class RtError(RuntimeError):
@@ -234,6 +234,11 @@ class Context:
         """Capacity of the deferred peel-off queue in records (0: peel off
         inline in the tracer; < 0: the default)."""
         _check(lib().rt_ctx_set_peel_queue(self.handle, C.c_int64(int(max_records))))
+
+    def set_tiles(self, tile_edge: int) -> None:
+        """Tiled tracing: tile edge in root cells (a power of two), 0 off,
+        < 0 automatic."""
+        _check(lib().rt_ctx_set_tiles(self.handle, int(tile_edge)))
 
     def close(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -384,6 +384,53 @@ def test_deferred_peel_equals_inline(rt, precision):
         assert led["peel_ms"] > 0
 
 
+@pytest.mark.parametrize("case", ["cloud64_peel", "cloud32_peel", "cloud32_trace", "clump64_analog", "clump32"])
+def test_tiled_equals_untiled(rt, case):
+    """Tiled tracing (rounds over (bin, tile) record queues) gives every
+    package the history it has untiled: identical per-package logs and
+    counters, absorbed energy and images up to the order of the FP64
+    additions."""
+    precision = 64 if "64" in case else 32
+    peel = case.endswith("peel")
+    if case.startswith("cloud"):
+        m, edge, kw = _small_cloud(n_root=32, levels=2, n_lambda=4), 8, dict(rr_wmin=1e-3, rr_p=0.5)
+    else:
+        m, edge, kw = synth.tiny_clump(), 4, {}
+        if case.endswith("analog"):
+            kw["estimator"] = 1
+    npk = 3000
+    nl = m.optics.n_lambda
+    res = {}
+    for e in (0, edge):
+        c = rt.Context(0)
+        c.set_tiles(e)
+        g = rt.Grid(c, m.tree)
+        ab = _zeros(nl, g.n_cells)
+        log = _zeros(npk * nl * len(m.sources), 10)
+        im = None
+        if peel:
+            obs = m.observers
+            im = _zeros(obs.n_obs, nl, obs.ny, obs.nx)
+            led = rt.rt_peel(c, g, m.sources, m.optics, obs, im, ab, seed=41, precision=precision,
+                             packets_per_bin=npk, packet_log=log, **kw)
+        else:
+            led = rt.rt_trace(c, g, m.sources, m.optics, ab, seed=41, precision=precision, packets_per_bin=npk,
+                              packet_log=log, **kw)
+        res[e] = (ab.cpu().numpy(), None if im is None else im.cpu().numpy(), log.cpu().numpy(), led)
+        c.close()
+    a0, i0, l0, led0 = res[0]
+    a1, i1, l1, led1 = res[edge]
+    assert led0["n_cross"] > 10000
+    np.testing.assert_array_equal(l1, l0)
+    np.testing.assert_allclose(a1, a0, rtol=1e-12, atol=1e-14 * np.abs(a0).max())
+    if peel:
+        np.testing.assert_allclose(i1, i0, rtol=1e-12, atol=1e-14 * np.abs(i0).max())
+    for k in ("n_packets", "n_cross", "n_scatter", "n_peel_cross", "n_peel_out", "n_killed"):
+        assert led1[k] == led0[k], k
+    for k in ("emitted", "absorbed", "escaped", "peeled", "rr_gain", "rr_loss"):
+        assert led1[k] == pytest.approx(led0[k], rel=1e-12), k
+
+
 def test_fp64_roulette_and_summed_bins(rt, ctx, orc):
     m = _small_cloud(n_root=16, levels=2, n_lambda=4)
     out = _run_pair(rt, ctx, orc, m, 3000, 64, seed=22, rr_wmin=0.3, rr_p=0.6, per_lambda=False)
