@@ -36,12 +36,13 @@ UNIT = "cell crossings/s"
 BYTES_TRACE_CROSS = 4 + 16      # node word + FP64 accumulator read-modify-write
 BYTES_PEEL_CROSS = 4            # node word
 BYTES_IMAGE_DEPOSIT = 16        # FP64 pixel read-modify-write
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
-# of the tracer and of the deferred peel-off kernel on the default molecular
-# cloud workload, from a single-pass ncu capture of the current kernels (set
-# to None whenever a kernel changes until it is captured again)
-NCU_TRAFFIC_PER_LAUNCH = 3991218162688 + 1116500421120       # dram read + write, one launch
-NCU_PEEL_TRAFFIC_PER_LAUNCH = 466647693312 + 5282686208       # of this exact workload
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per step of the
+# tracer (all its launches: the emission round and the tiled rounds) and of
+# the deferred peel-off kernel on the default molecular cloud workload, from
+# a single-pass ncu capture of the current kernels (set to None whenever a
+# kernel changes until it is captured again)
+NCU_TRAFFIC_PER_LAUNCH = (201.0e9 + 143.3e9 + 13.9e9 + 34.0e9) / 2
+NCU_PEEL_TRAFFIC_PER_LAUNCH = (113.3e9 + 1.3e9) / 2
 
 
 def parse():
@@ -72,6 +73,10 @@ def parse():
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--tiles", type=int, default=-1,
+                    help="tiled tracing: tile edge in root cells (power of two), 0 off, -1 automatic")
+    ap.add_argument("--peel-queue", type=int, default=-1,
+                    help="deferred peel-off queue in records, 0 inline, -1 default")
     return ap.parse_args()
 
 
@@ -243,6 +248,8 @@ def main():
     m = make_model(a)
     t_gen = time.perf_counter() - t_gen
     ctx = rt.Context(local)
+    ctx.set_tiles(a.tiles)
+    ctx.set_peel_queue(a.peel_queue)
     grid = rt.Grid(ctx, m.tree)
     nl = m.optics.n_lambda
     nc = grid.n_cells
@@ -334,7 +341,8 @@ def main():
                "crossings_per_step": {"trace": L0["n_cross"], "peel": L0["n_peel_cross"]},
                "scatterings_per_step": L0["n_scatter"], "roofline": roof, "roofline_peel_kernel": peel_roof,
                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-               "gpu_launches": (3 + (1 if peel_ms > 0 else 0)) * a.steps,
+               "gpu_launches": sum(int(L["n_launches"]) + 2 for L in leds),  # + dust table and temperature
+               "tiling": {"tiles": L0["n_tiles"], "rounds_per_step": L0["n_rounds"]},
                "energy_balance": (L0["emitted"] - L0["absorbed"] - L0["escaped"]) / L0["emitted"],
                "model_generation_s": t_gen}
         print(json.dumps(out))

@@ -72,7 +72,7 @@ int rt_ctx_set_peel_queue(rt_ctx* ctx, int64_t max_records);
  * histories; only the order of the FP64 additions differs).  tile_edge < 0:
  * automatic (tiles whose node words plus one bin's accumulators take at most
  * 48 MB, only when the whole grid's take more); 0: off.  Uses two record
- * buffers of up to 2^25 (FP32, 80 B each) or 2^24 (FP64, 128 B each)
+ * buffers of up to 2^26 (FP32, 80 B each) or 2^25 (FP64, 128 B each)
  * records.  Returns RT_ERR_INVALID if tile_edge is not a power of two. */
 int rt_ctx_set_tiles(rt_ctx* ctx, int tile_edge);
 /* Message of the last failing call on this thread (static storage, valid
@@ -194,6 +194,9 @@ typedef struct {
   int status;               /* RT_OK or RT_ERR_STEP_LIMIT */
   double kernel_ms;         /* device time of the tracer launch */
   double peel_ms;           /* device time of the deferred peel-off launch (0: none) */
+  int64_t n_launches;       /* kernel launches of the call (tracer rounds, record sorts, peel-off) */
+  int32_t n_tiles;          /* tiled tracing: tiles (0: untiled) */
+  int32_t n_rounds;         /* tiled tracing: rounds after the emission round */
 } rt_ledger;
 
 /* Trace every package of every source and accumulate the absorbed energy

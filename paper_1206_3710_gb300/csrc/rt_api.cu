@@ -831,8 +831,9 @@ static bool choose_tiles(const rt_ctx* c, const rt_grid* G, int n_jobs, TileRun*
 static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool peel, int estimator, bool hits,
                      const JobDev* jobs_dev, const ItemDev* items_dev, int n_items, long long total,
                      const LaunchCfg& cfg, const PeelQueue& q, unsigned long long* counter,
-                     unsigned long long* n_out, int* status, double timeout_s, cudaStream_t s) {
-  const long long chunk = std::min<long long>(total, precision == 64 ? (1ll << 24) : (1ll << 25));
+                     unsigned long long* n_out, int* status, double timeout_s, cudaStream_t s,
+                     long long* launches, int* rounds) {
+  const long long chunk = std::min<long long>(total, precision == 64 ? (1ll << 25) : (1ll << 26));
   const size_t rb = tile_record_bytes(precision);
   const int n_keys = n_lambda * T.n_tiles;
   int rc = c->tile_a.ensure(rb * (size_t)chunk);
@@ -852,6 +853,7 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
     T.out = c->tile_a.p;
     T.first = c0;
     CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, c1, cfg, q, s, 1, &T));
+    *launches += 1;
     for (long long round = 0;; ++round) {
       if (round > 10000000) return fail(RT_ERR_CUDA, "tiled tracing did not finish");
       CK(cudaMemcpyAsync(c->pin_count, n_out, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -869,6 +871,8 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
       T.out = c->tile_a.p;
       T.first = 0;
       CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, n, cfg, q, s, 2, &T));
+      *launches += 4;  // histogram, scan, scatter, tracer
+      *rounds += 1;
     }
   }
   return RT_OK;
@@ -906,16 +910,20 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   TileRun tiles;
   const bool tiled = total > 0 && n_items > 0 && choose_tiles(c, jobs[0].grid, n_jobs, &tiles);
   int* tile_status = reinterpret_cast<int*>(counter + 4);
+  long long n_launch = 0;
+  int n_rounds = 0;
   CK(cudaEventRecord(c->ev_a, s));
   if (tiled) {
     rc = run_tiled(c, tiles, jobs[0].optics->n_lambda, precision, peel, estimator, hits,
                    reinterpret_cast<const JobDev*>(base + job_off[0]), reinterpret_cast<const ItemDev*>(base + items_off),
-                   n_items, total, cfg, q, counter, counter + 3, tile_status, to, s);
+                   n_items, total, cfg, q, counter, counter + 3, tile_status, to, s, &n_launch, &n_rounds);
     if (rc) return rc;
   } else if (total > 0 && n_items > 0) {
     CK(launch_trace(precision, peel, estimator, hits, reinterpret_cast<const JobDev*>(base + job_off[0]),
                     reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, q, s));
+    n_launch = 1;
   }
+  if (total > 0 && n_items > 0 && q.cap > 0) n_launch += 1;  // the deferred peel-off
   CK(cudaEventRecord(c->ev_m, s));
   if (total > 0 && n_items > 0 && q.cap > 0)
     CK(launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
@@ -954,6 +962,9 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
       o.status = L.status ? RT_ERR_STEP_LIMIT : RT_OK;
       o.kernel_ms = ms;
       o.peel_ms = q.cap > 0 ? ms_peel : 0.0;
+      o.n_launches = n_launch;
+      o.n_tiles = tiled ? tiles.n_tiles : 0;
+      o.n_rounds = n_rounds;
     }
     if (L.status) status = RT_ERR_STEP_LIMIT;
   }
@@ -1203,6 +1214,7 @@ struct rt_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  long long launches = 0;  // kernels per replay (tracer, peel-off)
 };
 
 extern "C" void rt_batch_destroy(rt_batch* b) {
@@ -1280,6 +1292,7 @@ extern "C" int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_b
   if (e == cudaSuccess && total > 0 && n_items > 0 && q.cap > 0)
     e = launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
                     max_observers(n_jobs, args.data()), cfg.refill, b->cap);
+  b->launches = (total > 0 && n_items > 0) ? 1 + (q.cap > 0 ? 1 : 0) : 0;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->host_led, led, sizeof(LedgerDev) * n_jobs, cudaMemcpyDeviceToHost, b->cap);
   cudaGraph_t g = nullptr;
@@ -1316,6 +1329,7 @@ extern "C" int rt_batch_run(rt_batch* b, rt_ledger* ledgers, double timeout_s, v
       o.n_cross = L.n_cross; o.n_scatter = L.n_scatter; o.n_peel_cross = L.n_peel_cross; o.n_killed = L.n_killed;
       o.n_peel_out = L.n_peel_out; o.n_peel_deferred = L.n_peel_deferred;
       o.status = L.status ? RT_ERR_STEP_LIMIT : RT_OK; o.kernel_ms = ms; o.peel_ms = 0.0;
+      o.n_launches = b->launches; o.n_tiles = 0; o.n_rounds = 0;
     }
     if (L.status) status = RT_ERR_STEP_LIMIT;
   }

@@ -275,6 +275,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     ledger->n_peel_deferred = hl.n_peel_deferred;
     ledger->status = hl.status ? RT_ERR_STEP_LIMIT : RT_OK;
     ledger->kernel_ms = 0.0;
+    ledger->n_launches = total > 0 ? 1 : 0;
   }
   if (hl.status) return restore(set_error(RT_ERR_STEP_LIMIT, "rt_trace_noalloc: some packages hit the step limit"));
   return restore(RT_OK);

@@ -74,7 +74,7 @@ class rt_trace_params(C.Structure):
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
                  "n_scatter", "n_peel_cross", "n_killed", "n_peel_out", "n_peel_deferred", "status", "kernel_ms",
-                 "peel_ms"]
+                 "peel_ms", "n_launches", "n_tiles", "n_rounds"]
 
 
 class rt_ledger(C.Structure):
@@ -83,7 +83,7 @@ class rt_ledger(C.Structure):
                 ("n_packets", C.c_uint64), ("n_cross", C.c_uint64), ("n_scatter", C.c_uint64),
                 ("n_peel_cross", C.c_uint64), ("n_killed", C.c_uint64), ("n_peel_out", C.c_uint64),
                 ("n_peel_deferred", C.c_uint64), ("status", C.c_int), ("kernel_ms", C.c_double),
-                ("peel_ms", C.c_double)]
+                ("peel_ms", C.c_double), ("n_launches", C.c_int64), ("n_tiles", C.c_int32), ("n_rounds", C.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n in LEDGER_FIELDS}
