@@ -222,6 +222,24 @@ def run_reference(a):
     print(json.dumps(line))
 
 
+def shard_params(rank: int, packets_per_bin: int) -> dict:
+    """Rank r traces packages [r*n, (r+1)*n) of every (source, bin): one Philox
+    key for all ranks and disjoint package indices, so the ranks together are
+    one run of world*n packages per bin (each rank's weights carry the full
+    source energy: their mean is that run's result)."""
+    return dict(job=0, packet_offset=rank * packets_per_bin)
+
+
+def reduce_over_ranks(dist, t_ms: float, counts, device):
+    """Max of the ranks' timed spans and sums of their work counters."""
+    import torch
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ct = torch.tensor([float(c) for c in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(ct)
+    return float(tt.item()), [float(v) for v in ct.tolist()]
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -259,9 +277,10 @@ def main():
     T = torch.zeros(nc, dtype=torch.float64, device=dev)
     lam, kabs, dnu = dust_arrays(m)
     stream = torch.cuda.current_stream(dev)
-    kw = dict(seed=1002, job=rank, precision=a.precision, packets_per_bin=a.packets_per_bin,
+    kw = dict(seed=1002, precision=a.precision, packets_per_bin=a.packets_per_bin,
               rr_wmin=a.rr_wmin, rr_p=a.rr_p,
-              block_size=a.block_size, refill_threshold=a.refill, blocks_per_sm=a.blocks_per_sm)
+              block_size=a.block_size, refill_threshold=a.refill, blocks_per_sm=a.blocks_per_sm,
+              **shard_params(rank, a.packets_per_bin))
 
     def step():
         absorbed.zero_()
@@ -288,16 +307,10 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
     cross = sum(L["n_cross"] + L["n_peel_cross"] for L in leds)
     pk = sum(L["n_packets"] for L in leds)
     if world > 1:
-        ct = torch.tensor([float(cross), float(pk)], dtype=torch.float64, device=dev)
-        dist.all_reduce(ct)
-        cross, pk = float(ct[0]), float(ct[1])
+        t_ms, (cross, pk) = reduce_over_ranks(dist, t_ms, [cross, pk], dev)
     value = cross / (t_ms * 1e-3)
 
     # rooflines of the tracer and of the deferred peel-off kernel (device time

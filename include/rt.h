@@ -185,6 +185,9 @@ typedef struct {
   int blocks_per_sm;        /* 0: occupancy-derived */
   uint32_t* hits_dev;       /* optional device [n_cells]: deposits per cell are ADDED here
                                (continuous estimator, rt_trace only); NULL: not counted */
+  int64_t packet_offset;    /* package k of a (source, bin) draws the random stream of package
+                               k + packet_offset: launches with offsets 0, n, 2n, ... of n packages
+                               each are shards of one run of their total (weights aside) */
 } rt_trace_params;
 
 typedef struct {

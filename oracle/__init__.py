@@ -69,7 +69,7 @@ class _Params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("job", C.c_uint32), ("iter", C.c_uint32),
                 ("estimator", C.c_int), ("rr_wmin", C.c_double), ("rr_p", C.c_double),
                 ("step_limit", C.c_int64), ("peel_tau_max", C.c_double), ("per_lambda", C.c_int),
-                ("n_threads", C.c_int)]
+                ("n_threads", C.c_int), ("packet_offset", C.c_int64)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled",
@@ -250,7 +250,7 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
           estimator: int = EST_CONTINUOUS, rr_wmin: float = 0.0, rr_p: float = 0.9,
           step_limit: int = 0, peel_tau_max: float = 0.0, per_lambda: bool = True,
           observers=None, n_threads: int = 1, validation: bool = False, record: bool = False,
-          emission: Optional[np.ndarray] = None):
+          emission: Optional[np.ndarray] = None, packet_offset: int = 0):
     """Run the oracle tracer.
 
     ``sources`` are ``synth.Source``-like objects (kind "point", "external",
@@ -284,7 +284,7 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
     o = _optics(optics, keep)
     prm = _Params(seed=seed, job=job, iter=iter_, estimator=estimator, rr_wmin=rr_wmin, rr_p=rr_p,
                   step_limit=step_limit, peel_tau_max=peel_tau_max, per_lambda=int(per_lambda),
-                  n_threads=n_threads)
+                  n_threads=n_threads, packet_offset=packet_offset)
     ob = _observers(observers, keep)
     bins = nl if per_lambda else 1
     nc = tree.n_cells

@@ -488,7 +488,8 @@ static void trace_one(trace_worker* w, int64_t p) {
   int64_t k = p - J->seg_begin[seg];
   int64_t npk = J->seg_begin[seg + 1] - J->seg_begin[seg];
   const orc_source* S = &J->src[si];
-  rstream rs = {prm->seed, (uint64_t)k, 0, prm->job, prm->iter, ((uint32_t)si << 16) | (uint32_t)bin};
+  rstream rs = {prm->seed, (uint64_t)(k + prm->packet_offset), 0, prm->job, prm->iter,
+                ((uint32_t)si << 16) | (uint32_t)bin};
   int ob = J->bins > 1 ? bin : 0;
   int64_t nc = t->n_cells;
 

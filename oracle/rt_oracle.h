@@ -94,6 +94,7 @@ typedef struct {
   double peel_tau_max;         /* <= 0: march to the boundary always */
   int per_lambda;              /* 1: outputs per bin; 0: summed */
   int n_threads;
+  int64_t packet_offset;       /* package k of a (source, bin) draws the stream of index k + offset */
 } orc_params;
 
 typedef struct {

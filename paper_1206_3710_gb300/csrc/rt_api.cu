@@ -533,6 +533,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     precision = p->precision;
     if (p->estimator != RT_EST_CONTINUOUS && p->estimator != RT_EST_ANALOG)
       return fail(RT_ERR_INVALID, "job %d: unknown estimator", j);
+    if (p->packet_offset < 0) return fail(RT_ERR_INVALID, "job %d: packet_offset must be >= 0", j);
     if (j > 0 && p->estimator != estimator) return fail(RT_ERR_INVALID, "jobs of one launch must share the estimator");
     estimator = p->estimator;
     if (p->rr_wmin > 0.0 && !(p->rr_p >= 0.0 && p->rr_p < 1.0)) return fail(RT_ERR_INVALID, "job %d: rr_p must be in [0,1)", j);
@@ -649,6 +650,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.rr_wmin_f = (float)p->rr_wmin;
     J.rr_p_f = (float)p->rr_p;
     J.peel_tau_max_f = (float)p->peel_tau_max;
+    J.pkt_offset = p->packet_offset;
     double w0_max = 0.0;
     for (size_t i = 0; i < pk.size(); ++i)
       if (pk[i] > 0) w0_max = std::max(w0_max, energy[i] / (double)pk[i]);

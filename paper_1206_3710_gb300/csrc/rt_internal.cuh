@@ -138,6 +138,8 @@ struct JobDev {
   float rr_wmin_f, rr_p_f, peel_tau_max_f;
   // the f32 tracer books ledger energies in 64-bit fixed point: value * 2^led_shift
   int led_shift;
+  int pad1;
+  long long pkt_offset;  // added to the package index of the random streams
 };
 
 // one (job, source) work item: a contiguous range of the global package counter

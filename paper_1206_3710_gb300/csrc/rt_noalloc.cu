@@ -73,6 +73,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
   if (p->precision != 32 && p->precision != 64) return set_error(RT_ERR_INVALID, "rt_trace_noalloc: precision must be 32 or 64");
   if (p->estimator != RT_EST_CONTINUOUS && p->estimator != RT_EST_ANALOG)
     return set_error(RT_ERR_INVALID, "rt_trace_noalloc: unknown estimator");
+  if (p->packet_offset < 0) return set_error(RT_ERR_INVALID, "rt_trace_noalloc: packet_offset must be >= 0");
   if (p->rr_wmin > 0.0 && (p->estimator != RT_EST_CONTINUOUS || !(p->rr_p >= 0.0 && p->rr_p < 1.0)))
     return set_error(RT_ERR_INVALID, "rt_trace_noalloc: roulette needs the continuous estimator and rr_p in [0,1)");
   for (int s = 0; s < n_src; ++s) {
@@ -158,6 +159,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
   J.rr_p = p->rr_p;
   J.step_limit = p->step_limit > 0 ? p->step_limit : 100000000ll;
   J.peel_tau_max = p->peel_tau_max;
+  J.pkt_offset = p->packet_offset;
   J.rr_wmin_f = (float)p->rr_wmin;
   J.rr_p_f = (float)p->rr_p;
   J.peel_tau_max_f = (float)p->peel_tau_max;

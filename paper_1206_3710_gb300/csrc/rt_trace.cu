@@ -831,7 +831,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           tau_cut = Num<R>::tau_max(J) > R(0) ? Num<R>::tau_max(J) : Num<R>::inf();
           const long long p = gi - I.pkt_begin;
           const int bin = (int)((r.meta >> 5) & 255u);
-          const unsigned long long k = (unsigned long long)(p - I.bin_prefix[bin]);
+          const unsigned long long k = (unsigned long long)(p - I.bin_prefix[bin] + J.pkt_offset);
           C.bin[t] = bin;
           C.log_index[t] = J.packet_log ? I.log_offset + p : -1;
           C.k0[t] = (uint32_t)J.seed ^ J.job_id;
@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
             else bhi = mid - 1;
           }
           const int bin = blo;
-          const unsigned long long k = (unsigned long long)(p - I.bin_prefix[bin]);
+          const unsigned long long k = (unsigned long long)(p - I.bin_prefix[bin] + J.pkt_offset);
           C.bin[t] = bin;
           C.log_index[t] = J.packet_log ? I.log_offset + p : -1;
           C.k0[t] = (uint32_t)J.seed ^ J.job_id;

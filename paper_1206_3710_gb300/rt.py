@@ -69,7 +69,7 @@ class rt_trace_params(C.Structure):
                 ("peel_tau_max", C.c_double), ("per_lambda", C.c_int), ("packets_per_bin", C.c_int64),
                 ("packets", C.POINTER(C.c_int64)), ("packets_total", C.c_int64), ("packet_log_dev", C.c_void_p),
                 ("timeout_s", C.c_double), ("block_size", C.c_int), ("refill_threshold", C.c_int),
-                ("blocks_per_sm", C.c_int), ("hits_dev", C.c_void_p)]
+                ("blocks_per_sm", C.c_int), ("hits_dev", C.c_void_p), ("packet_offset", C.c_int64)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
@@ -324,7 +324,8 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
                 estimator: int = RT_EST_CONTINUOUS, rr_wmin: float = 0.0, rr_p: float = 0.9, step_limit: int = 0,
                 peel_tau_max: float = 0.0, per_lambda: bool = True, packets_per_bin: int = 0, packets=None,
                 packets_total: int = 0, packet_log=None, timeout_s: float = 0.0, block_size: int = 0,
-                refill_threshold: int = 0, blocks_per_sm: int = 0, hits=None) -> rt_trace_params:
+                refill_threshold: int = 0, blocks_per_sm: int = 0, hits=None,
+                packet_offset: int = 0) -> rt_trace_params:
     p = rt_trace_params()
     p.seed, p.job, p.iter = int(seed), int(job), int(iter_)
     p.precision, p.estimator = int(precision), int(estimator)
@@ -337,6 +338,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
     p.timeout_s = float(timeout_s)
     p.block_size, p.refill_threshold, p.blocks_per_sm = int(block_size), int(refill_threshold), int(blocks_per_sm)
     p.hits_dev = _ptr(hits)
+    p.packet_offset = int(packet_offset)
     return p
 
 

@@ -431,6 +431,34 @@ def test_tiled_equals_untiled(rt, case):
         assert led1[k] == pytest.approx(led0[k], rel=1e-12), k
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_shards_are_one_run(rt, ctx, precision):
+    """Launches with package offsets 0 and n are, package by package, the two
+    halves of one launch of 2n packages per bin (the multi-GPU sharding):
+    identical histories, weights doubled exactly, mean of the shards equal to
+    the single run."""
+    m = _small_cloud(n_root=32, levels=2, n_lambda=3)
+    g = rt.Grid(ctx, m.tree)
+    nl, n = m.optics.n_lambda, 4000
+
+    def run(npk, off):
+        ab = _zeros(nl, g.n_cells)
+        log = _zeros(npk * nl, 10)
+        rt.rt_trace(ctx, g, m.sources, m.optics, ab, seed=12, precision=precision, packets_per_bin=npk,
+                    packet_offset=off, packet_log=log, rr_wmin=1e-3, rr_p=0.5)
+        return ab.cpu().numpy(), log.cpu().numpy()
+
+    one, l1 = run(2 * n, 0)
+    a, la = run(n, 0)
+    b, lb = run(n, n)
+    np.testing.assert_allclose(0.5 * (a + b), one, rtol=1e-12, atol=1e-14 * one.max())
+    for k in range(nl):
+        half = np.concatenate([la[k * n:(k + 1) * n], lb[k * n:(k + 1) * n]])
+        ref = l1[k * 2 * n:(k + 1) * 2 * n]
+        np.testing.assert_array_equal(half[:, 1:], ref[:, 1:])
+        np.testing.assert_array_equal(half[:, 0], 2.0 * ref[:, 0])
+
+
 def test_fp64_roulette_and_summed_bins(rt, ctx, orc):
     m = _small_cloud(n_root=16, levels=2, n_lambda=4)
     out = _run_pair(rt, ctx, orc, m, 3000, 64, seed=22, rr_wmin=0.3, rr_p=0.6, per_lambda=False)

@@ -326,3 +326,28 @@ def test_p9_peel_matches_escape_binning(orc):
         peel = r["images"][o].sum()
         assert abs(peel - est) < 4 * sd + 0.02 * est, (o, peel, est, sd)
     assert r["ledger"]["n_peel_out"] == 0
+
+
+# Sharding ------------------------------------------------------------------
+
+def test_shards_are_one_run(orc):
+    """Packages are independent (Sect. 5.2): two shards of n packages per bin
+    with package offsets 0 and n are, package by package, the first and
+    second half of one run of 2n (each shard's weights carry the full source
+    energy, i.e. twice the single run's), so their mean is that run."""
+    m = synth.tiny_clump()
+    tree = orc.Tree(m.tree)
+    n = 1500
+    kw = dict(seed=9, record=True, rr_wmin=0.3, rr_p=0.6)
+    one = orc.trace(tree, m.sources, m.optics, 2 * n, **kw)
+    a = orc.trace(tree, m.sources, m.optics, n, packet_offset=0, **kw)
+    b = orc.trace(tree, m.sources, m.optics, n, packet_offset=n, **kw)
+    rec = np.concatenate([a["rec"], b["rec"]])
+    np.testing.assert_array_equal(rec[:, 1:], one["rec"][:, 1:])      # scatterings, crossings, fate, exit
+    np.testing.assert_array_equal(rec[:, 0], 2.0 * one["rec"][:, 0])  # escaped weight, W0 doubled exactly
+    np.testing.assert_allclose(0.5 * (a["absorbed"] + b["absorbed"]), one["absorbed"], rtol=1e-12,
+                               atol=1e-15 * one["absorbed"].max())
+    assert one["ledger"]["rr_loss"] > 0
+    # a different offset is a different set of packages
+    c = orc.trace(tree, m.sources, m.optics, n, packet_offset=7, **kw)
+    assert not np.array_equal(c["rec"][:, 2], a["rec"][:, 2])
