@@ -58,7 +58,7 @@ void rt_ctx_destroy(rt_ctx* ctx);
 /* Peel-off (Sect. 2.4) is deferred: each scattering appends one record
  * (48 B in FP32, 80 B in FP64) to a context-owned device queue, and a second
  * kernel marches every (record, observer) pair after the tracer.  The queue
- * holds min(max_records, packages of the launch / 4) records (at least 65536);
+ * holds min(max_records, 2 x packages of the launch) records (at least 2^20);
  * scatterings beyond it peel off inline in the tracer, with the same
  * results.  max_records = 0 disables deferral, < 0 restores the default
  * (2^27).  Takes effect at the next launch (and at rt_batch_create). */
@@ -229,6 +229,38 @@ typedef struct {
 int rt_peel(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
             const rt_optics* optics, const rt_trace_params* params, const rt_observers* obs,
             double* images_dev, double* absorbed_dev, rt_ledger* ledger, void* cuda_stream);
+
+/* Accelerated peel-off (Sect. 2.4): before the simulation, the faces of
+ * blocks of block_edge^3 root cells are cut into tiles_per_edge^2 tiles, and
+ * for each observer the column density (sum of density x path length) from
+ * every tile centre (of the part of the tile inside the model) along the
+ * observer direction to the border of the model is stored, for the block
+ * faces a ray along that direction can leave through.  A peel-off march then
+ * follows the optical depth exactly only until it leaves the block of the
+ * scattering point and adds kappa_ext times the entry of the tile it leaves
+ * through: an approximation (the tile centre stands in for the exit point)
+ * that is exact for observers along an axis on grids whose cells are not
+ * refined below the tile size.  block_edge and tiles_per_edge are powers of
+ * two, at most 1024 blocks per axis; the tables (FP64, device memory owned
+ * by the returned object) take 8 bytes x observers x blocks x exit axes x
+ * tiles_per_edge^2 and are built on `cuda_stream` (FP64 marches).  The
+ * object refers to `grid`, which must outlive it. */
+typedef struct rt_peel_tables rt_peel_tables;
+int rt_peel_tables_create(rt_ctx* ctx, const rt_grid* grid, const rt_observers* obs, int block_edge,
+                          int tiles_per_edge, rt_peel_tables** out, void* cuda_stream);
+void rt_peel_tables_destroy(rt_peel_tables* tables);
+/* Number of table entries; rt_peel_tables_read copies them to host memory
+ * (n >= that number) in the layout: observers in order, then
+ * [blocks x-fastest][exit axes in x, y, z order][v along axis (a+2)%3][u along (a+1)%3]. */
+int64_t rt_peel_tables_size(const rt_peel_tables* tables);
+int rt_peel_tables_read(const rt_peel_tables* tables, double* host, int64_t n);
+/* rt_peel with the tables (same grid, same observer directions as at
+ * creation, else RT_ERR_INVALID).  Scatterings that do not fit the deferred
+ * peel-off queue are peeled off inline with exact marches. */
+int rt_peel_tabulated(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
+                      const rt_optics* optics, const rt_trace_params* params, const rt_observers* obs,
+                      const rt_peel_tables* tables, double* images_dev, double* absorbed_dev,
+                      rt_ledger* ledger, void* cuda_stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batches: many models in one persistent launch                            */

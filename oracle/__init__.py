@@ -69,7 +69,8 @@ class _Params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("job", C.c_uint32), ("iter", C.c_uint32),
                 ("estimator", C.c_int), ("rr_wmin", C.c_double), ("rr_p", C.c_double),
                 ("step_limit", C.c_int64), ("peel_tau_max", C.c_double), ("per_lambda", C.c_int),
-                ("n_threads", C.c_int), ("packet_offset", C.c_int64)]
+                ("n_threads", C.c_int), ("packet_offset", C.c_int64), ("peel_block", C.c_int),
+                ("peel_tiles", C.c_int)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled",
@@ -108,6 +109,8 @@ def lib():
         L.orc_trace.argtypes = [C.c_void_p, C.c_int, C.POINTER(_Source), C.POINTER(_Optics),
                                 C.POINTER(_Params), C.POINTER(_Observers), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Ledger)]
+        L.orc_peel_table.restype = C.c_int64
+        L.orc_peel_table.argtypes = [C.c_void_p, C.POINTER(_Observers), C.c_int, C.c_int, C.c_void_p]
         L.orc_peel_point.restype = C.c_int
         L.orc_peel_point.argtypes = [C.c_void_p, C.POINTER(_Optics), C.POINTER(_Observers), C.c_int,
                                      C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
@@ -250,7 +253,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
           estimator: int = EST_CONTINUOUS, rr_wmin: float = 0.0, rr_p: float = 0.9,
           step_limit: int = 0, peel_tau_max: float = 0.0, per_lambda: bool = True,
           observers=None, n_threads: int = 1, validation: bool = False, record: bool = False,
-          emission: Optional[np.ndarray] = None, packet_offset: int = 0):
+          emission: Optional[np.ndarray] = None, packet_offset: int = 0, peel_block: int = 0,
+          peel_tiles: int = 0):
     """Run the oracle tracer.
 
     ``sources`` are ``synth.Source``-like objects (kind "point", "external",
@@ -284,7 +288,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
     o = _optics(optics, keep)
     prm = _Params(seed=seed, job=job, iter=iter_, estimator=estimator, rr_wmin=rr_wmin, rr_p=rr_p,
                   step_limit=step_limit, peel_tau_max=peel_tau_max, per_lambda=int(per_lambda),
-                  n_threads=n_threads, packet_offset=packet_offset)
+                  n_threads=n_threads, packet_offset=packet_offset, peel_block=peel_block,
+                  peel_tiles=peel_tiles)
     ob = _observers(observers, keep)
     bins = nl if per_lambda else 1
     nc = tree.n_cells
@@ -306,6 +311,20 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
         raise RuntimeError(f"orc_trace failed: {rc}")
     return dict(absorbed=absorbed, images=images, sumsq=sumsq, hits=hits, rec=rec,
                 ledger={n: getattr(led, n) for n in LEDGER_FIELDS})
+
+
+def peel_table(tree: Tree, observers, block: int, tiles: int) -> np.ndarray:
+    """Extinction tables of the accelerated peel-off (Sect. 2.4): column
+    densities from block-face tile centres to the model border per observer
+    (layout in rt_oracle.h)."""
+    keep = _Keep()
+    ob = _observers(observers, keep)
+    n = lib().orc_peel_table(tree.handle, C.byref(ob), int(block), int(tiles), None)
+    if n < 0:
+        raise ValueError("orc_peel_table: bad arguments")
+    out = np.zeros(max(n, 1))
+    lib().orc_peel_table(tree.handle, C.byref(ob), int(block), int(tiles), _p(out))
+    return out[:n]
 
 
 def peel_point(tree: Tree, optics, observers, bin_: int, x_cm, d_in, W, per_lambda=True):

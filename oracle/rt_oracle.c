@@ -12,7 +12,11 @@
  *     (Sect. 2.3, Lucy 1999) and are removed only at the outer boundary of
  *     the root grid or by Russian roulette (Sect. 2.3);
  *   - scattered light is peeled off towards observers after every scattering
- *     (Sect. 2.4, Yusef-Zadeh et al. 1984);
+ *     (Sect. 2.4, Yusef-Zadeh et al. 1984); optionally with Sect. 2.4's
+ *     accelerated variant: the optical depth is followed exactly only to the
+ *     boundary of the scattering point's block of root cells, and the rest
+ *     is a column density tabulated from the centre of the face tile the ray
+ *     leaves through to the model border;
  *   - dust temperatures follow from the equilibrium between absorbed and
  *     emitted energy (Sects. 3.2 and 4: a single dust component in
  *     equilibrium with the local radiation field).
@@ -347,6 +351,7 @@ typedef struct {
   int shared_atomic;
   double* absorbed_shared;
   double* images_shared;
+  double* peel_tab;        /* accelerated peel-off: orc_peel_table of the observers, or NULL */
 } trace_job;
 
 typedef struct {
@@ -422,6 +427,120 @@ static double peel_march(trace_worker* w, const double x0[3], const double k[3],
   return tau;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Accelerated peel-off (Sect. 2.4): extinction tables on block faces          */
+/* ------------------------------------------------------------------------ */
+static int blocks_along(const orc_tree* t, int a, int block) { return (t->root[a] + block - 1) / block; }
+
+static int n_axes(const double k[3]) { return (k[0] != 0.0) + (k[1] != 0.0) + (k[2] != 0.0); }
+
+static int axis_slot(const double k[3], int a) {
+  int s = 0;
+  for (int b = 0; b < a; ++b) s += k[b] != 0.0;
+  return s;
+}
+
+/* column density (g/cm^3 x root-cell units) from x along k to the border */
+static double column_march(const orc_tree* t, const double x0[3], const double k[3]) {
+  double x[3] = {x0[0], x0[1], x0[2]};
+  double col = 0.0;
+  const orc_node* n = locate(t, x, k);
+  while (n) {
+    int a;
+    double s = exit_dist(n, x, k, &a);
+    col += n->rho * s;
+    move_to_face(n, x, k, s, a);
+    n = locate(t, x, k);
+  }
+  return col;
+}
+
+int64_t orc_peel_table(const orc_tree* t, const orc_observers* obs, int block, int tiles, double* out) {
+  if (!t || !obs || block < 1 || tiles < 1) return -1;
+  const int nb[3] = {blocks_along(t, 0, block), blocks_along(t, 1, block), blocks_along(t, 2, block)};
+  const int64_t n_blocks = (int64_t)nb[0] * nb[1] * nb[2];
+  int64_t idx = 0;
+  for (int o = 0; o < obs->n_obs; ++o) {
+    const double* k = &obs->dir[3 * o];
+    const int na = n_axes(k);
+    for (int64_t blk = 0; blk < n_blocks; ++blk) {
+      const int b[3] = {(int)(blk % nb[0]), (int)((blk / nb[0]) % nb[1]), (int)(blk / ((int64_t)nb[0] * nb[1]))};
+      for (int a = 0; a < 3; ++a) {
+        if (k[a] == 0.0) continue;
+        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        for (int iv = 0; iv < tiles; ++iv)
+          for (int iu = 0; iu < tiles; ++iu, ++idx) {
+            if (!out) continue;
+            double c[3];
+            c[a] = k[a] > 0 ? fmin((double)(b[a] + 1) * block, (double)t->root[a]) : (double)b[a] * block;
+            const double w = (double)block / tiles;
+            const double u0 = (double)b[a1] * block + iu * w, v0 = (double)b[a2] * block + iv * w;
+            if (u0 >= t->root[a1] || v0 >= t->root[a2]) {
+              out[idx] = 0.0;
+              continue;
+            }
+            c[a1] = 0.5 * (u0 + fmin(u0 + w, (double)t->root[a1]));
+            c[a2] = 0.5 * (v0 + fmin(v0 + w, (double)t->root[a2]));
+            out[idx] = column_march(t, c, k);
+          }
+      }
+    }
+    (void)na;
+  }
+  return idx;
+}
+
+/* offset of observer o's entries in the table */
+static int64_t table_offset(const orc_tree* t, const orc_observers* obs, int block, int tiles, int o) {
+  const int64_t n_blocks = (int64_t)blocks_along(t, 0, block) * blocks_along(t, 1, block) * blocks_along(t, 2, block);
+  int64_t off = 0;
+  for (int p = 0; p < o; ++p) off += n_blocks * n_axes(&obs->dir[3 * p]) * (int64_t)tiles * tiles;
+  return off;
+}
+
+/* Peel-off march with the tables: exact optical depth until the ray leaves
+ * the block of the scattering point, then the tabulated column of the tile
+ * it leaves through. */
+static double peel_march_tab(trace_worker* w, const double x0[3], int o, int bin, double tau_max, int* cut) {
+  const orc_tree* t = w->job->t;
+  const orc_observers* obs = w->job->obs;
+  const int B = w->job->prm->peel_block, S = w->job->prm->peel_tiles;
+  const double* k = &obs->dir[3 * o];
+  double x[3] = {x0[0], x0[1], x0[2]};
+  double kext = w->job->op->kappa_ext[bin] * t->h0;
+  double tau = 0.0;
+  *cut = 0;
+  const orc_node* n = locate(t, x, k);
+  if (!n) return 0.0;
+  int b0[3];
+  for (int a = 0; a < 3; ++a) b0[a] = (int)floor(n->lo[a]) / B;
+  while (n) {
+    int a;
+    double s = exit_dist(n, x, k, &a);
+    tau += kext * n->rho * s;
+    if (s > 0) w->led.n_peel_cross += 1;
+    if (tau_max > 0 && tau > tau_max) { *cut = 1; return tau; }
+    move_to_face(n, x, k, s, a);
+    n = locate(t, x, k);
+    if (n && ((int)floor(n->lo[0]) / B != b0[0] || (int)floor(n->lo[1]) / B != b0[1] ||
+              (int)floor(n->lo[2]) / B != b0[2])) {
+      const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+      int iu = (int)floor((x[a1] - (double)b0[a1] * B) * S / B);
+      int iv = (int)floor((x[a2] - (double)b0[a2] * B) * S / B);
+      iu = iu < 0 ? 0 : (iu >= S ? S - 1 : iu);
+      iv = iv < 0 ? 0 : (iv >= S ? S - 1 : iv);
+      const int nb0 = blocks_along(t, 0, B), nb1 = blocks_along(t, 1, B);
+      const int64_t blk = b0[0] + (int64_t)nb0 * (b0[1] + (int64_t)nb1 * b0[2]);
+      const int64_t i = table_offset(t, obs, B, S, o) +
+                        ((blk * n_axes(k) + axis_slot(k, a)) * S + iv) * (int64_t)S + iu;
+      tau += kext * w->job->peel_tab[i];
+      if (tau_max > 0 && tau > tau_max) *cut = 1;
+      return tau;
+    }
+  }
+  return tau;
+}
+
 static void peel(trace_worker* w, const double x[3], const double din[3], double W, int bin) {
   const orc_observers* obs = w->job->obs;
   const orc_tree* t = w->job->t;
@@ -431,7 +550,8 @@ static void peel(trace_worker* w, const double x[3], const double din[3], double
     const double* k = &obs->dir[3 * o];
     double mu = din[0] * k[0] + din[1] * k[1] + din[2] * k[2];
     int cut;
-    double tau = peel_march(w, x, k, bin, w->job->prm->peel_tau_max, &cut);
+    double tau = w->job->peel_tab ? peel_march_tab(w, x, o, bin, w->job->prm->peel_tau_max, &cut)
+                                  : peel_march(w, x, k, bin, w->job->prm->peel_tau_max, &cut);
     if (cut) continue;
     double c = W * orc_hg_phase(g, mu) * exp(-tau);
     /* image basis: ex = normalise(up x k), ey = k x ex; centred on the box centre */
@@ -686,6 +806,12 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
       }
     }
   J.n_packets = J.seg_begin[(int64_t)n_src * nl];
+  if (obs && obs->n_obs > 0 && prm->peel_block > 0) {
+    const int64_t ne = orc_peel_table(t, obs, prm->peel_block, prm->peel_tiles, NULL);
+    if (ne < 0) return -1;
+    J.peel_tab = (double*)calloc((size_t)(ne > 0 ? ne : 1), sizeof(double));
+    orc_peel_table(t, obs, prm->peel_block, prm->peel_tiles, J.peel_tab);
+  }
   int T = prm->n_threads > 0 ? prm->n_threads : 1;
   if (J.n_packets < T) T = J.n_packets > 0 ? (int)J.n_packets : 1;
   int64_t n_img = obs && obs->n_obs > 0 ? (int64_t)obs->n_obs * bins * obs->ny * obs->nx : 0;
@@ -743,7 +869,7 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
   }
   if (ledger) *ledger = L;
   for (int64_t i = 0; i < (int64_t)n_src * nl; ++i) free(J.cdf[i]);
-  free(J.cdf); free(J.seg_begin); free(ws); free(th);
+  free(J.cdf); free(J.seg_begin); free(ws); free(th); free(J.peel_tab);
   return 0;
 }
 

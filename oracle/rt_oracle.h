@@ -95,6 +95,8 @@ typedef struct {
   int per_lambda;              /* 1: outputs per bin; 0: summed */
   int n_threads;
   int64_t packet_offset;       /* package k of a (source, bin) draws the stream of index k + offset */
+  int peel_block;              /* > 0: accelerated peel-off (Sect. 2.4) with blocks of this many root cells */
+  int peel_tiles;              /*      and peel_tiles x peel_tiles tiles on each block face */
 } orc_params;
 
 typedef struct {
@@ -110,6 +112,21 @@ typedef struct {
 int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_optics* op,
               const orc_params* prm, const orc_observers* obs, double* absorbed,
               double* images, double* sumsq, double* hits, double* rec, orc_ledger* ledger);
+
+/* Extinction tables of the accelerated peel-off (Sect. 2.4).  The root grid
+ * is cut into blocks of `block` root cells per axis; each block face is cut
+ * into tiles x tiles tiles.  For observer o and each face of each block
+ * through which a ray along dir[o] can leave it (axes a with dir[o][a] != 0;
+ * the face on the side the direction points to), the entry is the column
+ * density (sum of density x path length, g/cm^3 x root-cell units) from the
+ * tile centre along dir[o] to the border of the model; the tile centre is
+ * taken on the part of the tile inside the model.  Layout: for o in order,
+ * [n_blocks][n_axes(o)][tiles][tiles] (v along axis (a+2)%3, u along
+ * (a+1)%3), blocks x-fastest.  A peel-off march then stops where it leaves
+ * the block of the scattering point and adds kappa_ext h0 times the entry
+ * of the tile it leaves through.  Returns the number of entries (out may be
+ * NULL to query it) or a negative error. */
+int64_t orc_peel_table(const orc_tree* t, const orc_observers* obs, int block, int tiles, double* out);
 
 /* Single peel-off contribution of a scattering at x (cm) with incoming
  * direction din and weight W, into images [n_obs][bins][ny][nx]. */

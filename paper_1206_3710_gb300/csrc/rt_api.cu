@@ -207,8 +207,8 @@ extern "C" int rt_ctx_set_peel_queue(rt_ctx* c, int64_t max_records) {
   return RT_OK;
 }
 
-// Queue for the deferred peel-off of one launch: min(max_records, total / 4)
-// records, at least 65536.  When the device has no room for it the launch
+// Queue for the deferred peel-off of one launch: min(max_records, 2 x total)
+// records, at least 2^20.  When the device has no room for it the launch
 // peels off inline (same results), so an allocation failure is not an error.
 static PeelQueue make_queue(DevBuf& buf, long long max_records, bool peel, int n_jobs, long long total,
                             int precision, unsigned long long* count_dev) {
@@ -217,7 +217,7 @@ static PeelQueue make_queue(DevBuf& buf, long long max_records, bool peel, int n
   q.count = count_dev;
   q.cap = 0;
   if (!peel || max_records <= 0 || n_jobs > RT_PEEL_MAX_JOBS) return q;
-  const long long cap = std::min<long long>(max_records, std::max<long long>(total / 4, 65536));
+  const long long cap = std::min<long long>(max_records, std::max<long long>(2 * total, 1ll << 20));
   if (buf.ensure(peel_record_bytes(precision) * (size_t)cap) != RT_OK) {
     cudaGetLastError();  // allocation failures are not sticky
     return q;
@@ -479,7 +479,28 @@ struct TraceArgs {
   const rt_observers* obs;
   double* images;
   double* absorbed;
+  const rt_peel_tables* tab = nullptr;  // accelerated peel-off tables, or NULL
 };
+
+// accelerated peel-off tables (Sect. 2.4)
+struct rt_peel_tables {
+  rt_ctx* ctx = nullptr;
+  const rt_grid* grid = nullptr;
+  DevBuf buf;                 // [job record | table]
+  const double* table = nullptr;
+  long long n = 0;
+  PeelTabSpec spec;
+  std::vector<double> dirs;   // the observers' directions as given
+  int bsh = 0, ssh = 0;
+};
+
+// unit observer direction as the job tables compute it
+static bool unit_dir(const double* d, double k[3]) {
+  const double kn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (!(kn > 0) || !std::isfinite(kn)) return false;
+  for (int a = 0; a < 3; ++a) k[a] = d[a] / kn;
+  return true;
+}
 
 static int max_observers(int n_jobs, const TraceArgs* jobs) {
   int m = 0;
@@ -651,6 +672,19 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.rr_p_f = (float)p->rr_p;
     J.peel_tau_max_f = (float)p->peel_tau_max;
     J.pkt_offset = p->packet_offset;
+    if (T.tab) {
+      if (T.tab->grid != G || !T.obs || T.obs->n_obs != T.tab->spec.n_obs)
+        return fail(RT_ERR_INVALID, "job %d: peel-off tables were built for another grid or observer set", j);
+      for (int o = 0; o < T.obs->n_obs; ++o)
+        for (int a = 0; a < 3; ++a)
+          if (T.obs->dir[3 * o + a] != T.tab->dirs[3 * o + a])
+            return fail(RT_ERR_INVALID, "job %d: observer %d differs from the tables' observer", j, o);
+      J.ptab = T.tab->table;
+      J.ptab_bsh = T.tab->bsh;
+      J.ptab_ssh = T.tab->ssh;
+      J.ptab_nbx = T.tab->spec.nb[0];
+      J.ptab_nby = T.tab->spec.nb[1];
+    }
     double w0_max = 0.0;
     for (size_t i = 0; i < pk.size(); ++i)
       if (pk[i] > 0) w0_max = std::max(w0_max, energy[i] / (double)pk[i]);
@@ -678,10 +712,14 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
       for (int o = 0; o < T.obs->n_obs; ++o) {
         ObsDev& O = ob[o];
         memset(&O, 0, sizeof O);
-        double k[3] = {T.obs->dir[3 * o], T.obs->dir[3 * o + 1], T.obs->dir[3 * o + 2]};
-        const double kn = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
-        if (!(kn > 0)) return fail(RT_ERR_INVALID, "job %d observer %d: zero direction", j, o);
-        for (double& v : k) v /= kn;
+        double k[3];
+        if (!unit_dir(&T.obs->dir[3 * o], k)) return fail(RT_ERR_INVALID, "job %d observer %d: zero direction", j, o);
+        if (T.tab) {
+          O.tab_off = T.tab->spec.off[o];
+          O.tab_naxes = T.tab->spec.n_axes[o];
+          for (int a = 0; a < 3; ++a) O.tab_slot[a] = 0;
+          for (int s2 = 0; s2 < T.tab->spec.n_axes[o]; ++s2) O.tab_slot[T.tab->spec.axes[o][s2]] = s2;
+        }
         double ex[3], ey[3];
         cross3(&T.obs->up[3 * o], k, ex);
         const double en = std::sqrt(ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2]);
@@ -927,9 +965,14 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   }
   if (total > 0 && n_items > 0 && q.cap > 0) n_launch += 1;  // the deferred peel-off
   CK(cudaEventRecord(c->ev_m, s));
-  if (total > 0 && n_items > 0 && q.cap > 0)
-    CK(launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
-                   max_observers(n_jobs, jobs), cfg.refill, s));
+  if (total > 0 && n_items > 0 && q.cap > 0) {
+    if (n_jobs == 1 && jobs[0].tab)
+      CK(launch_peel_tab(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
+                         max_observers(n_jobs, jobs), cfg.refill, s));
+    else
+      CK(launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
+                     max_observers(n_jobs, jobs), cfg.refill, s));
+  }
   CK(cudaEventRecord(c->ev_b, s));
   std::vector<LedgerDev> hl(n_jobs);
   CK(cudaMemcpyAsync(hl.data(), led, sizeof(LedgerDev) * n_jobs, cudaMemcpyDeviceToHost, s));
@@ -991,6 +1034,106 @@ extern "C" int rt_peel(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_sou
   std::lock_guard<std::mutex> lk(ctx->mu);
   DeviceGuard dg(ctx->device);
   TraceArgs T{grid, n_src, src, optics, params, obs, images_dev, absorbed_dev};
+  if (ledger) memset(ledger, 0, sizeof *ledger);
+  return run_jobs(ctx, 1, &T, ledger, (cudaStream_t)cuda_stream, params);
+}
+
+extern "C" int rt_peel_tables_create(rt_ctx* ctx, const rt_grid* grid, const rt_observers* obs, int block_edge,
+                                     int tiles_per_edge, rt_peel_tables** out, void* cuda_stream) {
+  if (!ctx || !grid || !obs || !out) return fail(RT_ERR_INVALID, "rt_peel_tables_create: NULL argument");
+  *out = nullptr;
+  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+  if (!pow2(block_edge) || !pow2(tiles_per_edge) || tiles_per_edge > 4096)
+    return fail(RT_ERR_INVALID, "rt_peel_tables_create: block_edge and tiles_per_edge must be powers of two");
+  if (obs->n_obs < 1 || obs->n_obs > RT_MAX_OBS || !obs->dir)
+    return fail(RT_ERR_INVALID, "rt_peel_tables_create: 1..%d observers", RT_MAX_OBS);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  if (grid->device != ctx->device) return fail(RT_ERR_INVALID, "rt_peel_tables_create: grid on another device");
+  rt_peel_tables* t = new rt_peel_tables();
+  t->ctx = ctx;
+  t->grid = grid;
+  PeelTabSpec& S = t->spec;
+  memset(&S, 0, sizeof S);
+  S.n_obs = obs->n_obs;
+  S.block = block_edge;
+  S.tiles = tiles_per_edge;
+  for (int a = 0; a < 3; ++a) S.nb[a] = (grid->root[a] + block_edge - 1) / block_edge;
+  if (S.nb[0] > 1024 || S.nb[1] > 1024 || S.nb[2] > 1024) {
+    delete t;
+    return fail(RT_ERR_INVALID, "rt_peel_tables_create: at most 1024 blocks per axis");
+  }
+  while ((1 << t->bsh) < block_edge) ++t->bsh;
+  while ((1 << t->ssh) < tiles_per_edge) ++t->ssh;
+  const long long nblk = (long long)S.nb[0] * S.nb[1] * S.nb[2];
+  t->dirs.assign(obs->dir, obs->dir + 3 * obs->n_obs);
+  S.off[0] = 0;
+  for (int o = 0; o < obs->n_obs; ++o) {
+    if (!unit_dir(&obs->dir[3 * o], S.k[o])) {
+      delete t;
+      return fail(RT_ERR_INVALID, "rt_peel_tables_create: observer %d has a zero direction", o);
+    }
+    S.n_axes[o] = 0;
+    for (int a = 0; a < 3; ++a)
+      if (S.k[o][a] != 0.0) S.axes[o][S.n_axes[o]++] = a;
+    S.off[o + 1] = S.off[o] + nblk * S.n_axes[o] * (long long)tiles_per_edge * tiles_per_edge;
+  }
+  t->n = S.off[obs->n_obs];
+  JobDev J;
+  memset(&J, 0, sizeof J);
+  J.node = grid->node;
+  J.rho64 = grid->rho64;
+  for (int a = 0; a < 3; ++a) J.root[a] = (uint32_t)grid->root[a];
+  int rc = t->buf.ensure(256 + sizeof(double) * (size_t)std::max<long long>(t->n, 1));
+  if (rc) {
+    delete t;
+    return rc;
+  }
+  t->table = reinterpret_cast<const double*>(reinterpret_cast<char*>(t->buf.p) + 256);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  rc = ensure_pinned(ctx, sizeof J);
+  if (!rc) {
+    memcpy(ctx->pinned, &J, sizeof J);
+    cudaError_t e = cudaMemcpyAsync(t->buf.p, ctx->pinned, sizeof J, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = build_peel_table(reinterpret_cast<const JobDev*>(t->buf.p), S, const_cast<double*>(t->table), s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_c, s);
+    if (e != cudaSuccess) rc = fail(RT_ERR_CUDA, "rt_peel_tables_create: %s", cudaGetErrorString(e));
+  }
+  if (!rc) rc = wait_event(ctx->ev_c, 3600.0);
+  if (rc) {
+    t->buf.release();
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return RT_OK;
+}
+
+extern "C" void rt_peel_tables_destroy(rt_peel_tables* t) {
+  if (!t) return;
+  DeviceGuard dg(t->ctx->device);
+  t->buf.release();
+  delete t;
+}
+
+extern "C" int64_t rt_peel_tables_size(const rt_peel_tables* t) { return t ? (int64_t)t->n : -1; }
+
+extern "C" int rt_peel_tables_read(const rt_peel_tables* t, double* host, int64_t n) {
+  if (!t || !host || n < t->n) return fail(RT_ERR_INVALID, "rt_peel_tables_read: NULL argument or short buffer");
+  DeviceGuard dg(t->ctx->device);
+  CK(cudaMemcpy(host, t->table, sizeof(double) * (size_t)t->n, cudaMemcpyDeviceToHost));
+  return RT_OK;
+}
+
+extern "C" int rt_peel_tabulated(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
+                                 const rt_optics* optics, const rt_trace_params* params, const rt_observers* obs,
+                                 const rt_peel_tables* tables, double* images_dev, double* absorbed_dev,
+                                 rt_ledger* ledger, void* cuda_stream) {
+  if (!ctx || !grid || !params || !obs || !tables) return fail(RT_ERR_INVALID, "rt_peel_tabulated: NULL argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  TraceArgs T{grid, n_src, src, optics, params, obs, images_dev, absorbed_dev, tables};
   if (ledger) memset(ledger, 0, sizeof *ledger);
   return run_jobs(ctx, 1, &T, ledger, (cudaStream_t)cuda_stream, params);
 }

@@ -40,6 +40,11 @@ struct ObsDev {
   double inv_pix[2];  // 1 / pixel size
   float kf[3], exf[3], eyf[3], cf[3], inv_pixf[2];  // the same in f32
   int nx, ny;
+  // accelerated peel-off tables (Sect. 2.4): this observer's entries start
+  // at tab_off; tab_slot[a] is the slot of axis a among its exit axes
+  long long tab_off;
+  int tab_slot[3];
+  int tab_naxes;
 };
 
 struct LedgerDev {
@@ -140,6 +145,10 @@ struct JobDev {
   int led_shift;
   int pad1;
   long long pkt_offset;  // added to the package index of the random streams
+  // accelerated peel-off: column densities on block faces (NULL: exact
+  // marches); blocks of 2^ptab_bsh root cells, 2^ptab_ssh tiles per face edge
+  const double* ptab;
+  int ptab_bsh, ptab_ssh, ptab_nbx, ptab_nby;
 };
 
 // one (job, source) work item: a contiguous range of the global package counter
@@ -200,6 +209,20 @@ cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per
 cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
                         int n_obs_max, int refill, cudaStream_t s);
 size_t peel_record_bytes(int precision);
+// peel-off kernel with the extinction tables of JobDev::ptab
+cudaError_t launch_peel_tab(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
+                            int n_obs_max, int refill, cudaStream_t s);
+// the extinction tables: column density from each block-face tile centre
+// along each observer direction to the border of the model (FP64 marches)
+struct PeelTabSpec {
+  int n_obs;
+  double k[RT_MAX_OBS][3];
+  long long off[RT_MAX_OBS + 1];
+  int axes[RT_MAX_OBS][3];  // exit axes of observer o, n_axes[o] of them
+  int n_axes[RT_MAX_OBS];
+  int block, tiles, nb[3];
+};
+cudaError_t build_peel_table(const JobDev* job_dev, const PeelTabSpec& spec, double* table, cudaStream_t s);
 
 cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, const double* origins,
                         const double* dirs, long long max_seg, long long* cells, double* lengths,

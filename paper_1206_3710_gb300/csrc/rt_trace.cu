@@ -1246,7 +1246,7 @@ struct PeelMinBlocks {
   static constexpr int value = sizeof(R) == 4 ? RT_PEEL_MIN_BLOCKS : 2;
 };
 
-template <typename R>
+template <typename R, bool TAB>
 __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(const JobDev* __restrict__ jobs,
                                                                            PeelQueue Q,
                                                                            unsigned long long* __restrict__ work,
@@ -1267,6 +1267,11 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
   R kext = R(0), taup = R(0), tau_cut = R(0), pw = R(0);
   long long pix = 0;
   uint32_t npeel = 0u;
+  // accelerated peel-off: block of the scattering point (x | y << 10 | z << 20),
+  // the observer, kappa_ext h0 of the bin
+  uint32_t tab_blk = 0u;
+  int tab_o = 0;
+  R ktab = R(0);
   g.lev = 0;
   cur.pending = 0u;
   cur.k = 0;
@@ -1325,6 +1330,12 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
             taup = R(0);
             npeel = 0u;
             job = rjob;
+            if (TAB) {
+              const int sh = g.lev + J.ptab_bsh;
+              tab_blk = (g.cx >> sh) | ((g.cy >> sh) << 10) | ((g.cz >> sh) << 20);
+              tab_o = o;
+              ktab = (R)B.kext_d;
+            }
             st = P_LIVE;
           } else {
             book_u(SL, jobs, rjob, wid, U_POUT, 1ull);
@@ -1354,8 +1365,36 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
           } else {
             taup += kext * g.rho * Num<R>::pow2m(g.lev) * tx;
             npeel += tx > R(0) ? 1u : 0u;
-            if (taup > tau_cut) ev = EV_CUT;
-            else if (!advance(G, g, cur, a, tx, dx, dy, dz)) ev = EV_ESCAPE;
+            if (taup > tau_cut) {
+              ev = EV_CUT;
+            } else if (!advance(G, g, cur, a, tx, dx, dy, dz)) {
+              ev = EV_ESCAPE;
+            } else if (TAB && cur.k == 0) {
+              const JobDev& J = jobs[job];
+              const int sh = g.lev + J.ptab_bsh;
+              const uint32_t bx = g.cx >> sh, by = g.cy >> sh, bz = g.cz >> sh;
+              if ((bx | (by << 10) | (bz << 20)) != tab_blk) {
+                // left the scattering point's block through the face on
+                // axis a: add the tabulated column of the tile it crossed
+                const uint32_t cu = a == 0 ? g.cy : (a == 1 ? g.cz : g.cx);
+                const uint32_t cv = a == 0 ? g.cz : (a == 1 ? g.cx : g.cy);
+                const R fu = a == 0 ? g.fy : (a == 1 ? g.fz : g.fx);
+                const R fv = a == 0 ? g.fz : (a == 1 ? g.fx : g.fy);
+                const uint32_t mask = (1u << sh) - 1u;
+                const R scale = Num<R>::pow2m(g.lev) * (R)(1 << J.ptab_ssh) / (R)(1 << J.ptab_bsh);
+                const int S = 1 << J.ptab_ssh;
+                int iu = (int)Num<R>::floor_(((R)(cu & mask) + fu) * scale);
+                int iv = (int)Num<R>::floor_(((R)(cv & mask) + fv) * scale);
+                iu = iu < 0 ? 0 : (iu >= S ? S - 1 : iu);
+                iv = iv < 0 ? 0 : (iv >= S ? S - 1 : iv);
+                const ObsDev& O = J.obs[tab_o];
+                const uint32_t b0x = tab_blk & 1023u, b0y = (tab_blk >> 10) & 1023u, b0z = tab_blk >> 20;
+                const long long blk = (long long)b0x + (long long)J.ptab_nbx * ((long long)b0y + (long long)J.ptab_nby * b0z);
+                const long long i = O.tab_off + ((blk * O.tab_naxes + O.tab_slot[a]) * S + iv) * (long long)S + iu;
+                taup += ktab * (R)__ldg(J.ptab + i);
+                ev = taup > tau_cut ? EV_CUT : EV_ESCAPE;
+              }
+            }
           }
         }
       }
@@ -1587,22 +1626,100 @@ cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_
 
 size_t peel_record_bytes(int precision) { return precision == 64 ? sizeof(PeelRec64) : sizeof(PeelRec32); }
 
-template <typename R>
+template <typename R, bool TAB>
 static cudaError_t launch_peel_t(const JobDev* jobs, const PeelQueue& q, unsigned long long* work, int n_obs_max,
                                  int refill, cudaStream_t s) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, peel_kernel<R>, 256, 0) != cudaSuccess || occ < 1) occ = 1;
-  peel_kernel<R><<<sms * occ, 256, 0, s>>>(jobs, q, work, n_obs_max, refill);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, peel_kernel<R, TAB>, 256, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  peel_kernel<R, TAB><<<sms * occ, 256, 0, s>>>(jobs, q, work, n_obs_max, refill);
   return cudaGetLastError();
 }
 
 cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
                         int n_obs_max, int refill, cudaStream_t s) {
   if (q.cap <= 0 || n_obs_max <= 0) return cudaSuccess;
-  return precision == 64 ? launch_peel_t<double>(jobs_dev, q, work_dev, n_obs_max, refill, s)
-                         : launch_peel_t<float>(jobs_dev, q, work_dev, n_obs_max, refill, s);
+  return precision == 64 ? launch_peel_t<double, false>(jobs_dev, q, work_dev, n_obs_max, refill, s)
+                         : launch_peel_t<float, false>(jobs_dev, q, work_dev, n_obs_max, refill, s);
+}
+
+cudaError_t launch_peel_tab(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
+                            int n_obs_max, int refill, cudaStream_t s) {
+  if (q.cap <= 0 || n_obs_max <= 0) return cudaSuccess;
+  return precision == 64 ? launch_peel_t<double, true>(jobs_dev, q, work_dev, n_obs_max, refill, s)
+                         : launch_peel_t<float, true>(jobs_dev, q, work_dev, n_obs_max, refill, s);
+}
+
+// ------------------------------------------------------------------------
+// accelerated peel-off tables (Sect. 2.4): one thread per entry marches in
+// FP64 from the tile centre to the model border and sums density x length
+// ------------------------------------------------------------------------
+__global__ void peel_table_kernel(const JobDev* __restrict__ job, PeelTabSpec S, long long n,
+                                  double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int o = 0;
+  while (o + 1 < S.n_obs && S.off[o + 1] <= i) ++o;
+  long long r = i - S.off[o];
+  const int T = S.tiles;
+  const int iu = (int)(r % T);
+  r /= T;
+  const int iv = (int)(r % T);
+  r /= T;
+  const int ai = (int)(r % S.n_axes[o]);
+  const long long blk = r / S.n_axes[o];
+  const int a = S.axes[o][ai], a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+  const JobDev& J = *job;
+  const int Rr[3] = {(int)J.root[0], (int)J.root[1], (int)J.root[2]};
+  const int b[3] = {(int)(blk % S.nb[0]), (int)((blk / S.nb[0]) % S.nb[1]), (int)(blk / ((long long)S.nb[0] * S.nb[1]))};
+  const double* k = S.k[o];
+  double c[3];
+  c[a] = k[a] > 0 ? fmin((double)(b[a] + 1) * S.block, (double)Rr[a]) : (double)b[a] * S.block;
+  const double w = (double)S.block / T;
+  const double u0 = (double)b[a1] * S.block + iu * w, v0 = (double)b[a2] * S.block + iv * w;
+  if (u0 >= Rr[a1] || v0 >= Rr[a2]) {
+    out[i] = 0.0;
+    return;
+  }
+  c[a1] = 0.5 * (u0 + fmin(u0 + w, (double)Rr[a1]));
+  c[a2] = 0.5 * (v0 + fmin(v0 + w, (double)Rr[a2]));
+  GridRegs G;
+  G.node = J.node;
+  G.rho64 = J.rho64;
+  G.rx = J.root[0];
+  G.ry = J.root[1];
+  G.rz = J.root[2];
+  Geo<double> g;
+  Cursor cur;
+  double col = 0.0;
+  if (place_root(G, g, cur, c[0], c[1], c[2], k[0], k[1], k[2])) {
+    const double ix = inv_abs(k[0]), iy = inv_abs(k[1]), iz = inv_abs(k[2]);
+    for (int pass = 0; pass < (1 << 26); ++pass) {
+      const uint32_t wd = G.node[cur.pending];
+      const double r64 = G.rho64[cur.pending];
+      if (wd & RT_INTERIOR) {
+        descend_step(g, cur, wd, k[0], k[1], k[2]);
+        continue;
+      }
+      settle_leaf(g, cur, wd, r64);
+      int ax;
+      const double t = exit_dist(g, k[0], k[1], k[2], ix, iy, iz, ax);
+      if (ax < 0) break;
+      col += g.rho * Num<double>::pow2m(g.lev) * t;
+      if (!advance(G, g, cur, ax, t, k[0], k[1], k[2])) break;
+    }
+  }
+  out[i] = col;
+}
+
+cudaError_t build_peel_table(const JobDev* job_dev, const PeelTabSpec& spec, double* table, cudaStream_t s) {
+  const long long n = spec.off[spec.n_obs];
+  if (n <= 0) return cudaSuccess;
+  const int B = 128;
+  peel_table_kernel<<<(unsigned)((n + B - 1) / B), B, 0, s>>>(job_dev, spec, n, table);
+  return cudaGetLastError();
 }
 
 template <typename R, bool PEEL>

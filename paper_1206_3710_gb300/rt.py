@@ -26,7 +26,9 @@ EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "r
             "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate", "rt_trace_batch", "rt_batch_create",
             "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load", "rt_server_create",
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
-            "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles"]
+            "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles",
+            "rt_peel_tables_create", "rt_peel_tables_destroy", "rt_peel_tables_size", "rt_peel_tables_read",
+            "rt_peel_tabulated"]
 
 
 class RtError(RuntimeError):
@@ -152,6 +154,15 @@ def lib():
     L.rt_peel.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics), C.POINTER(rt_trace_params),
                           C.POINTER(rt_observers), vp, vp, C.POINTER(rt_ledger), vp]
     L.rt_dust_temperature.argtypes = [vp, vp, vp, C.c_int, C.POINTER(rt_dust), vp, vp]
+    L.rt_peel_tables_create.argtypes = [vp, vp, C.POINTER(rt_observers), C.c_int, C.c_int, C.POINTER(vp), vp]
+    L.rt_peel_tables_destroy.argtypes = [vp]
+    L.rt_peel_tables_destroy.restype = None
+    L.rt_peel_tables_size.argtypes = [vp]
+    L.rt_peel_tables_size.restype = C.c_int64
+    L.rt_peel_tables_read.argtypes = [vp, vp, C.c_int64]
+    L.rt_peel_tabulated.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics),
+                                    C.POINTER(rt_trace_params), C.POINTER(rt_observers), vp, vp, vp,
+                                    C.POINTER(rt_ledger), vp]
     L.rt_dust_emission.argtypes = [vp, vp, vp, C.POINTER(rt_dust), vp, vp, vp]
     L.rt_walk.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int, C.c_int64, vp, vp, vp, vp]
     L.rt_philox.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
@@ -179,7 +190,7 @@ def lib():
     L.rt_server_destroy.restype = None
     for name in EXPORTED:
         if name not in ("rt_ctx_destroy", "rt_grid_free", "rt_last_error", "rt_version", "rt_batch_destroy",
-                        "rt_server_destroy"):
+                        "rt_server_destroy", "rt_peel_tables_destroy", "rt_peel_tables_size"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -387,6 +398,50 @@ def rt_peel(ctx: Context, grid: Grid, sources, optics, observers, images, absorb
     led = rt_ledger()
     rc = lib().rt_peel(ctx.handle, grid.handle, len(sources), src, C.byref(op), C.byref(prm), C.byref(ob),
                        _ptr(images), _ptr(absorbed), C.byref(led), _stream(stream))
+    _check(rc, allow_step_limit=True)
+    return led.as_dict()
+
+
+class PeelTables:
+    """Extinction tables of the accelerated peel-off (Sect. 2.4) for one grid
+    and observer set (device memory owned by the library)."""
+
+    def __init__(self, ctx: Context, grid: Grid, observers, block_edge: int, tiles_per_edge: int, stream=None):
+        keep = _Keep()
+        ob = make_observers(observers, keep)
+        h = C.c_void_p()
+        _check(lib().rt_peel_tables_create(ctx.handle, grid.handle, C.byref(ob), int(block_edge),
+                                           int(tiles_per_edge), C.byref(h), _stream(stream)))
+        self.handle, self.grid, self.observers = h, grid, observers
+
+    @property
+    def size(self) -> int:
+        return int(lib().rt_peel_tables_size(self.handle))
+
+    def read(self) -> np.ndarray:
+        out = np.zeros(max(self.size, 1))
+        _check(lib().rt_peel_tables_read(self.handle, out.ctypes.data_as(C.c_void_p), C.c_int64(out.size)))
+        return out[:self.size]
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.rt_peel_tables_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def rt_peel_tabulated(ctx: Context, grid: Grid, sources, optics, observers, tables: PeelTables, images,
+                      absorbed=None, stream=None, **params) -> dict:
+    keep = _Keep()
+    src = make_sources(sources, len(optics.kappa_ext), keep)
+    op = make_optics(optics, keep)
+    prm = make_params(keep, **params)
+    ob = make_observers(observers, keep)
+    led = rt_ledger()
+    rc = lib().rt_peel_tabulated(ctx.handle, grid.handle, len(sources), src, C.byref(op), C.byref(prm), C.byref(ob),
+                                 tables.handle, _ptr(images), _ptr(absorbed), C.byref(led), _stream(stream))
     _check(rc, allow_step_limit=True)
     return led.as_dict()
 

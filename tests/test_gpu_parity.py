@@ -615,3 +615,77 @@ def test_fp64_dust_source_per_packet(rt, ctx, orc):
     out = dict(log=log.cpu().numpy(), ref=ref)
     _per_packet(out, per_bin=npk)
     np.testing.assert_allclose(ab.cpu().numpy().sum(), ref["absorbed"].sum(), rtol=1e-6)
+
+
+# ----------------------------------------------------------------- accelerated peel-off (Sect. 2.4)
+
+_PEEL_DIRS = np.array([[0.6, 0.8, 0.0], [0.0, 0.6, -0.8], [-0.48, 0.6, 0.64], [0.0, 0.0, 1.0]])
+
+
+def _peel_model(seed=8):
+    root = (20, 12, 9)
+    L = 20 * synth.AU_CM
+    h = L / root[0]
+    desc = synth.random_refined_tree(root, tuple(r * h for r in root), 2, 0.3, seed,
+                                     rho_fn=lambda l, x, y, z: np.random.default_rng(l + seed).uniform(1e-19, 1e-18,
+                                                                                                      x.size))
+    ups = np.array([(0.0, 0.0, 1.0) if abs(d[2]) < 0.9 else (1.0, 0.0, 0.0) for d in _PEEL_DIRS])
+    # the field of view holds the projected box in every direction: no
+    # scattering projects outside the image
+    obs = synth.Observers(dirs=_PEEL_DIRS, ups=ups, nx=24, ny=24, fov=(2 * root[0] * h, 2 * root[0] * h))
+    lam = synth.log_lambda_grid(3)
+    optics = synth.powerlaw_dust(lam, 2.0 / (1e-18 * L), 1.0)
+    src = synth.Source("point", bin_energy=np.ones(3), pos=(7.3 * h, 5.1 * h, 4.4 * h))
+    return desc, obs, optics, src
+
+
+def test_peel_tables_match_oracle(rt, ctx, orc):
+    """The device's extinction tables (FP64 marches from the tile centres)
+    equal the oracle's, entry by entry, with partial blocks and oblique
+    directions."""
+    desc, obs, _, _ = _peel_model()
+    g = rt.Grid(ctx, desc)
+    for block, tiles in ((8, 4), (4, 8)):
+        t = rt.PeelTables(ctx, g, obs, block, tiles)
+        ref = orc.peel_table(orc.Tree(desc), obs, block, tiles)
+        got = t.read()
+        assert got.size == ref.size and np.count_nonzero(ref) > ref.size // 5
+        np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-12 * ref.max())
+        t.close()
+
+
+def test_peel_tabulated_fp64_matches_oracle(rt, ctx, orc):
+    """rt_peel_tabulated in FP64 against the oracle's accelerated peel-off:
+    the same images, absorbed energy and peel-off crossings."""
+    desc, obs, optics, src = _peel_model()
+    g = rt.Grid(ctx, desc)
+    tree = orc.Tree(desc)
+    nl, npk = optics.n_lambda, 3000
+    t = rt.PeelTables(ctx, g, obs, 4, 4)
+    ab = _zeros(nl, g.n_cells)
+    im = _zeros(obs.n_obs, nl, obs.ny, obs.nx)
+    led = rt.rt_peel_tabulated(ctx, g, [src], optics, obs, t, im, ab, seed=44, precision=64, packets_per_bin=npk)
+    ref = orc.trace(tree, [src], optics, npk, seed=44, observers=obs, peel_block=4, peel_tiles=4)
+    exact = orc.trace(tree, [src], optics, npk, seed=44, observers=obs)
+    assert led["n_peel_deferred"] == led["n_scatter"] > 0  # every scattering went through the tables
+    _close(ab.cpu().numpy(), ref["absorbed"])
+    _close(im.cpu().numpy(), ref["images"])
+    assert led["n_peel_out"] == 0
+    # segments of zero length at edge and corner crossings are not counted:
+    # the two coordinate systems round a handful of them differently
+    assert led["n_peel_cross"] == pytest.approx(ref["ledger"]["n_peel_cross"], rel=1e-4)
+    assert led["n_peel_cross"] < 0.5 * exact["ledger"]["n_peel_cross"]
+    # the approximation stays close to the exact peel-off on this model
+    assert abs(im.cpu().numpy().sum() / exact["images"].sum() - 1) < 0.05
+
+
+def test_peel_tabulated_rejects_other_observers(rt, ctx):
+    desc, obs, optics, src = _peel_model()
+    g = rt.Grid(ctx, desc)
+    t = rt.PeelTables(ctx, g, obs, 4, 4)
+    other = synth.Observers(dirs=obs.dirs[::-1].copy(), ups=obs.ups[::-1].copy(), nx=obs.nx, ny=obs.ny, fov=obs.fov)
+    im = _zeros(obs.n_obs, optics.n_lambda, obs.ny, obs.nx)
+    with pytest.raises(rt.RtError):
+        rt.rt_peel_tabulated(ctx, g, [src], optics, other, t, im, None, seed=1, packets_per_bin=10)
+    with pytest.raises(rt.RtError):
+        rt.PeelTables(ctx, g, obs, 3, 4)

@@ -351,3 +351,76 @@ def test_shards_are_one_run(orc):
     # a different offset is a different set of packages
     c = orc.trace(tree, m.sources, m.optics, n, packet_offset=7, **kw)
     assert not np.array_equal(c["rec"][:, 2], a["rec"][:, 2])
+
+
+# Accelerated peel-off (Sect. 2.4) ---------------------------------------------
+
+_OBLIQUE = np.array([[0.6, 0.8, 0.0], [0.0, 0.6, -0.8], [-0.48, 0.6, 0.64], [-1.0, 0.0, 0.0]])
+
+
+def _obs(dirs, n=16, fov=1.0):
+    ups = np.array([(0.0, 0.0, 1.0) if abs(d[2]) < 0.9 else (1.0, 0.0, 0.0) for d in dirs])
+    return synth.Observers(dirs=np.asarray(dirs, float), ups=ups, nx=n, ny=n, fov=(fov, fov))
+
+
+def test_peel_table_uniform_closed_form(orc):
+    """In a uniform medium the tabulated column is the density times the
+    distance from the tile centre to the border along the direction; checked
+    for oblique and axis directions, with blocks that do not divide the root
+    grid (partial blocks and tiles)."""
+    root, B, S, rho = (10, 7, 12), 4, 2, 3.0
+    desc = synth.random_refined_tree(root, tuple(float(r) for r in root), 2, 0.3, 5,
+                                     rho_fn=lambda l, x, y, z: np.full(x.size, rho))
+    tree = orc.Tree(desc)
+    obs = _obs(_OBLIQUE)
+    tab = orc.peel_table(tree, obs, B, S)
+    nb = [(r + B - 1) // B for r in root]
+    i = 0
+    for k in obs.dirs:
+        for bz in range(nb[2]):
+            for by in range(nb[1]):
+                for bx in range(nb[0]):
+                    b = (bx, by, bz)
+                    for a in range(3):
+                        if k[a] == 0:
+                            continue
+                        a1, a2 = (a + 1) % 3, (a + 2) % 3
+                        for iv in range(S):
+                            for iu in range(S):
+                                w = B / S
+                                u0, v0 = b[a1] * B + iu * w, b[a2] * B + iv * w
+                                if u0 >= root[a1] or v0 >= root[a2]:
+                                    expect = 0.0
+                                else:
+                                    c = np.zeros(3)
+                                    c[a] = min((b[a] + 1) * B, root[a]) if k[a] > 0 else b[a] * B
+                                    c[a1] = 0.5 * (u0 + min(u0 + w, root[a1]))
+                                    c[a2] = 0.5 * (v0 + min(v0 + w, root[a2]))
+                                    dist = min(((root[d] if k[d] > 0 else 0.0) - c[d]) / k[d]
+                                               for d in range(3) if k[d] != 0)
+                                    expect = rho * max(dist, 0.0)
+                                assert tab[i] == pytest.approx(expect, rel=1e-12, abs=1e-12), (i, expect)
+                                i += 1
+    assert i == tab.size
+
+
+def test_peel_tabulated_exact_along_axes(orc):
+    """Observers along the axes, tiles the size of a root-cell face, no
+    refinement: every point of a tile sees the same row of cells to the
+    border, so the accelerated peel-off equals the exact one."""
+    root = (12, 10, 8)
+    rng = np.random.default_rng(3)
+    desc = synth.grow_tree(root, tuple(float(r) for r in root), 0,
+                           lambda l, x, y, z: rng.uniform(0.2, 2.0, x.size),
+                           lambda l, x, y, z, r: np.zeros(x.size, bool))
+    tree = orc.Tree(desc)
+    lam = np.array([0.55])
+    optics = synth.Optics(lambda_um=lam, kappa_ext=np.array([0.3]), albedo=np.array([0.7]),
+                          g_hg=np.array([0.3]), dnu=np.ones(1))
+    src = synth.Source("point", bin_energy=np.array([1.0]), pos=(6.1, 5.3, 3.7))
+    obs = _obs([[1, 0, 0], [0, -1, 0], [0, 0, 1]], n=24, fov=16.0)
+    exact = orc.trace(tree, [src], optics, 4000, seed=3, observers=obs)
+    tab = orc.trace(tree, [src], optics, 4000, seed=3, observers=obs, peel_block=4, peel_tiles=4)
+    assert exact["images"].sum() > 0
+    np.testing.assert_allclose(tab["images"], exact["images"], rtol=1e-11, atol=1e-14 * exact["images"].max())
+    assert tab["ledger"]["n_peel_cross"] < exact["ledger"]["n_peel_cross"]
