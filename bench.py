@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="cloud", choices=["cloud", "disc", "batch", "serve"],
-                    help="cloud: the headline workload; disc/batch/serve: the other model families")
+    ap.add_argument("--workload", default="cloud", choices=["cloud", "disc", "batch", "serve", "peeltab"],
+                    help="cloud: the headline workload; disc/batch/serve: the other model families; "
+                         "peeltab: accelerated against exact peel-off")
     ap.add_argument("--iters", type=int, default=30, help="disc: Lambda-iteration cap")
     ap.add_argument("--disc-packets", type=int, default=100_000_000)
     ap.add_argument("--models", type=int, default=64, help="batch: models per launch")

@@ -1079,6 +1079,10 @@ extern "C" int rt_peel_tables_create(rt_ctx* ctx, const rt_grid* grid, const rt_
     S.off[o + 1] = S.off[o] + nblk * S.n_axes[o] * (long long)tiles_per_edge * tiles_per_edge;
   }
   t->n = S.off[obs->n_obs];
+  if (t->n > (1ll << 32)) {
+    delete t;
+    return fail(RT_ERR_INVALID, "rt_peel_tables_create: %lld entries (more than 2^32)", (long long)S.off[obs->n_obs]);
+  }
   JobDev J;
   memset(&J, 0, sizeof J);
   J.node = grid->node;
