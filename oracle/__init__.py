@@ -70,7 +70,7 @@ class _Params(C.Structure):
                 ("estimator", C.c_int), ("rr_wmin", C.c_double), ("rr_p", C.c_double),
                 ("step_limit", C.c_int64), ("peel_tau_max", C.c_double), ("per_lambda", C.c_int),
                 ("n_threads", C.c_int), ("packet_offset", C.c_int64), ("peel_block", C.c_int),
-                ("peel_tiles", C.c_int)]
+                ("peel_tiles", C.c_int), ("per_level", C.c_int), ("confine_level", C.c_int)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled",
@@ -254,7 +254,7 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
           step_limit: int = 0, peel_tau_max: float = 0.0, per_lambda: bool = True,
           observers=None, n_threads: int = 1, validation: bool = False, record: bool = False,
           emission: Optional[np.ndarray] = None, packet_offset: int = 0, peel_block: int = 0,
-          peel_tiles: int = 0):
+          peel_tiles: int = 0, per_level: bool = False, confine_level: int = -1):
     """Run the oracle tracer.
 
     ``sources`` are ``synth.Source``-like objects (kind "point", "external",
@@ -289,9 +289,9 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
     prm = _Params(seed=seed, job=job, iter=iter_, estimator=estimator, rr_wmin=rr_wmin, rr_p=rr_p,
                   step_limit=step_limit, peel_tau_max=peel_tau_max, per_lambda=int(per_lambda),
                   n_threads=n_threads, packet_offset=packet_offset, peel_block=peel_block,
-                  peel_tiles=peel_tiles)
+                  peel_tiles=peel_tiles, per_level=int(per_level), confine_level=confine_level)
     ob = _observers(observers, keep)
-    bins = nl if per_lambda else 1
+    bins = tree.desc.n_levels if per_level else (nl if per_lambda else 1)
     nc = tree.n_cells
     absorbed = np.zeros((bins, nc))
     images = None
@@ -436,3 +436,54 @@ def lambda_iterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed
         if dmax < tol:
             break
     return T, history
+
+
+def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed: int, schedule,
+                      sub_level: int, T_min=2.7, T_max=3000.0, min_hits=1000.0, n_threads=1,
+                      dust_per_bin=False, **trace_kw):
+    """Lambda iteration with subiterations (Sect. 3.2, App. B).  The field of
+    the constant sources is computed once.  The dust field is kept in one
+    array per grid level i (Eq. 9): I_i holds what packages deposited after
+    reaching, as their shallowest grid, one of level i.  A step is either
+    "full" (dust emitted from every cell, all I_i replaced) or "sub", a
+    subiteration of every subtree below a refined cell of level
+    ``sub_level`` = L: dust emitted only from cells of level > L, packages
+    leave the run where they reach a grid of level <= L, and only I_i for
+    i > L are replaced.  After each step T follows from I_stars + sum_i I_i.
+    Returns T and the per-step max dT/T over cells with >= ``min_hits`` hits."""
+    kabs = (1 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
+    lam = np.asarray(optics.lambda_um)
+    dnu = np.asarray(optics.dnu)
+    r = trace(tree, [star], optics, packets_star, seed=seed, iter_=0, per_lambda=False,
+              n_threads=n_threads, validation=True, **trace_kw)
+    A_star = r["absorbed"][0]
+    hits = r["hits"][0]
+    T = dust_temperature(tree, A_star, lam, kabs, dnu, T_min, T_max, n_threads)
+    level, _ = tree.cells()
+    L = int(sub_level)
+    I = np.zeros((tree.desc.n_levels, tree.n_cells))
+    history = []
+    for step in schedule:
+        em = dust_emission(tree, T, lam, kabs, dnu)
+        if step == "sub":
+            em = em * (level > L)[None, :]
+        elif step != "full":
+            raise ValueError("schedule entries are 'full' or 'sub'")
+        if dust_per_bin:
+            npk = np.where(em.sum(axis=1) > 0, packets_dust, 0).astype(np.int64)
+        else:
+            npk = packets_by_energy(em.sum(axis=1), packets_dust)
+        rd = trace(tree, [_DustSource(em)], optics, npk, seed=seed, iter_=1, per_lambda=False,
+                   n_threads=n_threads, validation=True, per_level=True,
+                   confine_level=L if step == "sub" else -1, **trace_kw)
+        if step == "full":
+            I[:] = rd["absorbed"]
+        else:
+            I[L + 1:] = rd["absorbed"][L + 1:]
+        A = A_star + I.sum(axis=0)
+        Tn = dust_temperature(tree, A, lam, kabs, dnu, T_min, T_max, n_threads)
+        mask = (hits + rd["hits"].sum(axis=0)) >= min_hits
+        rel = np.abs(Tn - T)[mask] / np.maximum(T[mask], 1e-300)
+        history.append(float(rel.max()) if rel.size else 0.0)
+        T = Tn
+    return T, history, I

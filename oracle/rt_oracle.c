@@ -577,6 +577,19 @@ static void peel(trace_worker* w, const double x[3], const double din[3], double
   }
 }
 
+/* level of the shallowest grid between two cells: one below their deepest
+ * common ancestor (0 if they lie in different root cells) */
+static int visited_level(const orc_node* a, const orc_node* b) {
+  const int top = a->level < b->level ? a->level : b->level;
+  for (int l = top - 1; l >= 0; --l) {  /* ancestors at level l, deepest first */
+    const double s = ldexp(1.0, l);
+    int same = 1;
+    for (int k = 0; k < 3; ++k) same &= floor(a->lo[k] * s) == floor(b->lo[k] * s);
+    if (same) return l + 1;
+  }
+  return 0;
+}
+
 static int64_t search_cdf(const double* cdf, int64_t n, double target) {
   /* first index with cdf[i] > target */
   int64_t lo = 0, hi = n - 1;
@@ -668,6 +681,8 @@ static void trace_one(trace_worker* w, int64_t p) {
   double nscat = 0, ncross = 0;
   int fate = 0;
   int64_t steps = 0;
+  const orc_node* prev = NULL;
+  int mlev = 0;  /* shallowest grid level visited (subiterations) */
   for (;;) {
     const orc_node* n = locate(t, x, d);
     if (!n) {  /* left through the outer boundary of the root grid */
@@ -675,6 +690,17 @@ static void trace_one(trace_worker* w, int64_t p) {
       fate = 0;
       break;
     }
+    if (n != prev) {
+      const int v = prev ? visited_level(prev, n) : n->level;
+      if (prev && prm->confine_level >= 0 && v <= prm->confine_level) {
+        w->led.escaped += W;  /* left the subtree of the subiteration */
+        fate = 0;
+        break;
+      }
+      if (!prev || v < mlev) mlev = v;
+      prev = n;
+    }
+    if (prm->per_level) ob = mlev;
     if (prm->step_limit > 0 && steps >= prm->step_limit) {
       w->led.killed += W;
       w->led.n_killed += 1;
@@ -786,8 +812,9 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
               const orc_params* prm, const orc_observers* obs, double* absorbed, double* images,
               double* sumsq, double* hits, double* rec, orc_ledger* ledger) {
   if (!t || n_src <= 0 || !src || !op || !prm || op->n_lambda <= 0) return -1;
+  if (prm->per_level && obs && obs->n_obs > 0) return -1;  /* levels take the place of bins */
   int nl = op->n_lambda;
-  int bins = prm->per_lambda ? nl : 1;
+  int bins = prm->per_level ? t->n_levels : (prm->per_lambda ? nl : 1);
   int64_t nc = t->n_cells;
   trace_job J;
   memset(&J, 0, sizeof J);

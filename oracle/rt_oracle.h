@@ -97,6 +97,16 @@ typedef struct {
   int64_t packet_offset;       /* package k of a (source, bin) draws the stream of index k + offset */
   int peel_block;              /* > 0: accelerated peel-off (Sect. 2.4) with blocks of this many root cells */
   int peel_tiles;              /*      and peel_tiles x peel_tiles tiles on each block face */
+  /* Subiterations (Sect. 3.2, App. B): the grid of a cell at level l is the
+   * set of 8 children of its parent (the root grid for l = 0).  A package
+   * remembers the shallowest grid level it has been in: the level of its
+   * emission cell at first, then, at each crossing, the level of the
+   * shallowest grid on the way (one below the deepest common ancestor of the
+   * two cells; 0 between root cells). */
+  int per_level;               /* 1: absorbed is [n_levels][n_cells]: deposits by that level */
+  int confine_level;           /* >= 0: a package that reaches a grid of this level or shallower
+                                  (it left the subtree of its level-L ancestor) leaves the run,
+                                  booked as escaped; < 0: no confinement */
 } orc_params;
 
 typedef struct {

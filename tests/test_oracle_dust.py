@@ -102,3 +102,77 @@ def test_p12_lambda_iteration_self_heating(orc):
     assert np.median(T / T0) > 1.01
     assert hist[-1] < hist[0]
     assert len(hist) >= 2
+
+
+# P13: subiterations (Sect. 3.2, App. B) --------------------------------------
+
+def _sub_model(tau=2.0):
+    L = 20 * synth.AU_CM
+    desc = synth.random_refined_tree((6, 6, 6), (L,) * 3, 3, 0.35, 21,
+                                     rho_fn=lambda l, x, y, z: np.random.default_rng(l + 3).uniform(0.5e-18, 2e-18,
+                                                                                                    x.size))
+    lam = synth.log_lambda_grid(8)
+    optics = synth.powerlaw_dust(lam, tau / (1e-18 * L), 1.0)
+    star = synth.Source("point", bin_energy=synth.blackbody_star_bins(lam, 4000.0, 2 * synth.RSUN_CM),
+                        pos=(0.43 * L, 0.52 * L, 0.47 * L))
+    return desc, optics, star
+
+
+def _dust_source(orc, tree, optics, T):
+    kabs = (1 - optics.albedo) * optics.kappa_ext
+    return orc.dust_emission(tree, T, optics.lambda_um, kabs, optics.dnu)
+
+
+def test_p13_levels_partition_the_field(orc):
+    """Splitting the dust field by the shallowest grid level a package reached
+    changes where deposits are summed, not what is deposited: the level
+    arrays add up to the plain field, and a cell holds nothing above its own
+    level (a package in a cell has been in that cell's grid)."""
+    desc, optics, _ = _sub_model()
+    tree = orc.Tree(desc)
+    level, leaf = tree.cells()
+    T = np.where(leaf, 300.0 * np.random.default_rng(2).uniform(0.5, 1.5, tree.n_cells), 0.0)
+    em = _dust_source(orc, tree, optics, T)
+    src = orc._DustSource(em)
+    plain = orc.trace(tree, [src], optics, 3000, seed=8, iter_=1, per_lambda=False)
+    lev = orc.trace(tree, [src], optics, 3000, seed=8, iter_=1, per_lambda=False, per_level=True)
+    A = lev["absorbed"]
+    assert A.shape == (desc.n_levels, tree.n_cells)
+    np.testing.assert_allclose(A.sum(axis=0), plain["absorbed"][0], rtol=1e-12, atol=1e-14 * plain["absorbed"].max())
+    for i in range(desc.n_levels):
+        assert np.all(A[i][level < i] == 0)
+    assert all(A[i].sum() > 0 for i in range(desc.n_levels))
+    assert lev["ledger"]["n_cross"] == plain["ledger"]["n_cross"]
+
+
+def test_p13_confinement(orc):
+    """Confined to the subtrees below level L, packages emitted there deposit
+    only into levels > L, and whatever leaves a subtree is booked as escaped
+    (the energy balance still closes)."""
+    desc, optics, _ = _sub_model()
+    tree = orc.Tree(desc)
+    level, leaf = tree.cells()
+    L = 0
+    T = np.where(leaf & (level > L), 250.0, 0.0)
+    em = _dust_source(orc, tree, optics, T)
+    r = orc.trace(tree, [orc._DustSource(em)], optics, 3000, seed=8, iter_=1, per_lambda=False, per_level=True,
+                  confine_level=L)
+    A = r["absorbed"]
+    assert np.all(A[:L + 1] == 0) and A[L + 1:].sum() > 0
+    assert np.all(A.sum(axis=0)[level <= L] == 0)
+    led = r["ledger"]
+    assert abs(led["emitted"] - led["absorbed"] - led["escaped"]) <= 1e-12 * led["emitted"]
+    free = orc.trace(tree, [orc._DustSource(em)], optics, 3000, seed=8, iter_=1, per_lambda=False)
+    assert led["escaped"] > free["ledger"]["escaped"]
+
+
+def test_p13_full_schedule_is_the_lambda_iteration(orc):
+    """With full steps only, the subiteration driver is the Lambda iteration
+    of Eq. 2: the same temperatures and changes step by step."""
+    desc, optics, star = _sub_model()
+    tree = orc.Tree(desc)
+    T1, h1 = orc.lambda_iterate(tree, star, optics, 2000, 2000, seed=6, tol=0.0, max_iter=3, min_hits=10)
+    T2, h2, _ = orc.lambda_subiterate(tree, star, optics, 2000, 2000, seed=6, schedule=["full"] * 3, sub_level=1,
+                                      min_hits=10)
+    np.testing.assert_allclose(T2, T1, rtol=1e-12)
+    np.testing.assert_allclose(h2, h1, rtol=1e-9)
