@@ -396,6 +396,48 @@ int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_sour
                       const rt_lambda_params* lp, double* T_dev, rt_lambda_result* result,
                       void* cuda_stream);
 
+/* Lambda iteration with subiterations (Sect. 3.2, App. B).  The grid of a
+ * cell at level l is the set of 8 children of its parent (the root grid for
+ * l = 0); a package remembers the shallowest grid level it has reached (the
+ * level of its emission cell at first; one below the deepest common
+ * ancestor at every crossing out of a parent octet).  The dust field is kept
+ * in one array per level (Eq. 9: a cell's field is the constant sources' plus
+ * all its level arrays).  A step is
+ *   full (0): dust emitted by every cell, all level arrays replaced;
+ *   sub  (1): a subiteration of every subtree below the refined cells of level
+ *             sub_level = L: dust emitted by the cells of level > L, packages
+ *             leave the run where they reach a grid of level <= L (booked as
+ *             escaped), the level arrays > L replaced.
+ * After each step T follows from the summed field.  The dust packages reuse
+ * the same random streams every step (key iter = params.iter + 1).  With an
+ * explicit schedule the steps run as given (the run stops early when max
+ * dT/T over cells with >= lp->min_hits hits drops below lp->tol); with
+ * n_steps = 0, lp->max_iter steps are chosen automatically from the energy
+ * balance (Sect. 3.3): the first step is full; then a full step whenever the
+ * mass-weighted mean |absorbed - emitted| of the leaves at level <= L
+ * (measured at the last full step) is at least select_frac times the larger
+ * of it and that of the leaves below L (measured every step), else a
+ * subiteration.  Library scratch: 4 f64 + 2 u32 arrays of n_cells and 2 f64
+ * arrays of n_levels x n_cells. */
+typedef struct {
+  int sub_level;           /* L: subiterations cover the subtrees below the refined cells of level L */
+  int n_steps;             /* > 0: explicit schedule of this length (<= 64); 0: automatic */
+  const int* schedule;     /* host [n_steps]: 0 full step, 1 subiteration */
+  double select_frac;      /* automatic choice threshold (0.25 in Sect. 4.2) */
+} rt_subiter_params;
+
+typedef struct {
+  rt_lambda_result lambda;       /* steps taken, max dT/T per step, ledgers, wall time */
+  int step_kind[64];             /* 0 full, 1 subiteration */
+  double imbalance[64][2];       /* after each step: mean |absorbed - emitted| per unit mass, levels <= L and > L */
+  double step_ms[64];            /* wall time of each step */
+} rt_subiter_result;
+
+int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src,
+                         const rt_optics* optics, const rt_dust* dust, const rt_trace_params* params,
+                         const rt_lambda_params* lp, const rt_subiter_params* sp, double* T_dev,
+                         rt_subiter_result* result, void* cuda_stream);
+
 /* Dust emission per leaf and bin, 4 pi rho V kappa_abs,i B_nu_i(T) dnu_i,
  * into emission_dev (device [n_lambda][n_cells]); bin totals to
  * bin_total_host (host [n_lambda], may be NULL; waits for the stream). */

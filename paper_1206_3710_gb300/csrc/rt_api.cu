@@ -480,6 +480,8 @@ struct TraceArgs {
   double* images;
   double* absorbed;
   const rt_peel_tables* tab = nullptr;  // accelerated peel-off tables, or NULL
+  int levels = 0;                       // subiterations: absorbed is [n_levels][n_cells] by grid level
+  int confine = -1;                     // subiterations: packages leave at grids of level <= confine
 };
 
 // accelerated peel-off tables (Sect. 2.4)
@@ -672,6 +674,8 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.rr_p_f = (float)p->rr_p;
     J.peel_tau_max_f = (float)p->peel_tau_max;
     J.pkt_offset = p->packet_offset;
+    J.sub_conf = T.confine;
+    if (T.levels && (T.obs || nl < 1)) return fail(RT_ERR_INVALID, "job %d: level arrays exclude peel-off", j);
     if (T.tab) {
       if (T.tab->grid != G || !T.obs || T.obs->n_obs != T.tab->spec.n_obs)
         return fail(RT_ERR_INVALID, "job %d: peel-off tables were built for another grid or observer set", j);
@@ -872,7 +876,7 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
                      const JobDev* jobs_dev, const ItemDev* items_dev, int n_items, long long total,
                      const LaunchCfg& cfg, const PeelQueue& q, unsigned long long* counter,
                      unsigned long long* n_out, int* status, double timeout_s, cudaStream_t s,
-                     long long* launches, int* rounds) {
+                     long long* launches, int* rounds, bool levels) {
   const long long chunk = std::min<long long>(total, precision == 64 ? (1ll << 25) : (1ll << 26));
   const size_t rb = tile_record_bytes(precision);
   const int n_keys = n_lambda * T.n_tiles;
@@ -892,7 +896,8 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
     T.in = nullptr;
     T.out = c->tile_a.p;
     T.first = c0;
-    CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, c1, cfg, q, s, 1, &T));
+    CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, c1, cfg, q, s, 1, &T,
+                    levels));
     *launches += 1;
     for (long long round = 0;; ++round) {
       if (round > 10000000) return fail(RT_ERR_CUDA, "tiled tracing did not finish");
@@ -910,7 +915,8 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
       T.in = c->tile_b.p;
       T.out = c->tile_a.p;
       T.first = 0;
-      CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, n, cfg, q, s, 2, &T));
+      CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, n, cfg, q, s, 2, &T,
+                      levels));
       *launches += 4;  // histogram, scan, scatter, tracer
       *rounds += 1;
     }
@@ -956,11 +962,13 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   if (tiled) {
     rc = run_tiled(c, tiles, jobs[0].optics->n_lambda, precision, peel, estimator, hits,
                    reinterpret_cast<const JobDev*>(base + job_off[0]), reinterpret_cast<const ItemDev*>(base + items_off),
-                   n_items, total, cfg, q, counter, counter + 3, tile_status, to, s, &n_launch, &n_rounds);
+                   n_items, total, cfg, q, counter, counter + 3, tile_status, to, s, &n_launch, &n_rounds,
+                   jobs[0].levels != 0);
     if (rc) return rc;
   } else if (total > 0 && n_items > 0) {
     CK(launch_trace(precision, peel, estimator, hits, reinterpret_cast<const JobDev*>(base + job_off[0]),
-                    reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, q, s));
+                    reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, q, s, 0,
+                    nullptr, n_jobs == 1 && jobs[0].levels != 0));
     n_launch = 1;
   }
   if (total > 0 && n_items > 0 && q.cap > 0) n_launch += 1;  // the deferred peel-off
@@ -1325,6 +1333,146 @@ extern "C" int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* g, int n_src, const
     if (v < lp->tol) break;
   }
   res->ms = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return RT_OK;
+}
+
+// ------------------------------------------------------------------------
+// Lambda iteration with subiterations (Sect. 3.2, App. B)
+// ------------------------------------------------------------------------
+extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, const rt_source* src,
+                                    const rt_optics* op, const rt_dust* du, const rt_trace_params* prm,
+                                    const rt_lambda_params* lp, const rt_subiter_params* sp, double* T_dev,
+                                    rt_subiter_result* res, void* cuda_stream) {
+  if (!ctx || !g || !src || !op || !du || !prm || !lp || !sp || !T_dev || !res)
+    return fail(RT_ERR_INVALID, "rt_lambda_subiterate: NULL argument");
+  const int n_steps = sp->n_steps > 0 ? sp->n_steps : lp->max_iter;
+  if (n_steps < 1 || n_steps > 64) return fail(RT_ERR_INVALID, "rt_lambda_subiterate: 1..64 steps");
+  if (sp->n_steps > 0 && !sp->schedule) return fail(RT_ERR_INVALID, "rt_lambda_subiterate: schedule is NULL");
+  if (sp->sub_level < 0 || sp->sub_level >= g->n_levels - 1)
+    return fail(RT_ERR_INVALID, "rt_lambda_subiterate: sub_level must be 0..%d", g->n_levels - 2);
+  if (lp->dust_packets_per_bin <= 0 && lp->dust_packets_total <= 0)
+    return fail(RT_ERR_INVALID, "rt_lambda_subiterate: set dust_packets_total or dust_packets_per_bin");
+  int rc = check_optics(op);
+  if (rc) return rc;
+  rc = check_dust(du, op->n_lambda);
+  if (rc) return rc;
+  memset(res, 0, sizeof *res);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  const long long nc = g->n_cells;
+  const int nlev = g->n_levels, L = sp->sub_level;
+  const size_t fb = sizeof(double) * (size_t)nc, hb = sizeof(unsigned int) * (size_t)nc;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  // A_star, A, T_prev, T_emit | I (levels) | I_step (levels) | hits_star, hits_step | scalars
+  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
+  if (rc) return rc;
+  char* base = reinterpret_cast<char*>(ctx->lam.p);
+  double* A_star = reinterpret_cast<double*>(base);
+  double* A = reinterpret_cast<double*>(base + al(fb));
+  double* T_prev = reinterpret_cast<double*>(base + 2 * al(fb));
+  double* T_emit = reinterpret_cast<double*>(base + 3 * al(fb));
+  double* I = reinterpret_cast<double*>(base + 4 * al(fb));
+  double* I_step = reinterpret_cast<double*>(base + 4 * al(fb) + al(fb * nlev));
+  unsigned int* hits_star = reinterpret_cast<unsigned int*>(base + 4 * al(fb) + 2 * al(fb * nlev));
+  unsigned int* hits_step = reinterpret_cast<unsigned int*>(base + 4 * al(fb) + 2 * al(fb * nlev) + al(hb));
+  double* scal = reinterpret_cast<double*>(base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb));
+  CK(cudaMemsetAsync(A_star, 0, fb, s));
+  CK(cudaMemsetAsync(hits_star, 0, hb, s));
+  CK(cudaMemsetAsync(I, 0, fb * nlev, s));
+  const double to = prm->timeout_s > 0 ? prm->timeout_s : 3600.0;
+
+  // constant sources, traced once and stored (Sect. 3.2)
+  rt_trace_params stp = *prm;
+  stp.per_lambda = 0;
+  stp.hits_dev = hits_star;
+  stp.packet_log_dev = nullptr;
+  TraceArgs TS{g, n_src, src, op, &stp, nullptr, nullptr, A_star};
+  rc = run_jobs(ctx, 1, &TS, &res->lambda.source_ledger, s, &stp);
+  if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
+
+  const int n_table = 8192;
+  double *lam, *kab, *dnu, *tab;
+  auto upload = [&]() -> int {
+    int r = upload_dust(ctx, du, n_table, &lam, &kab, &dnu, &tab, s);
+    if (r) return r;
+    CK(dust_table(lam, kab, dnu, du->n_lambda, du->T_min, du->T_max, n_table, tab, s));
+    return RT_OK;
+  };
+  auto solve = [&](const double* absorbed) -> int {
+    int r = upload();
+    if (r) return r;
+    CK(dust_temperature(absorbed, 1, nc, g->child, g->rho64, g->level, g->h0, lam, kab, dnu, du->n_lambda, du->T_min,
+                        du->T_max, tab, n_table, T_dev, s));
+    return RT_OK;
+  };
+  auto read_scalars = [&](double* out, int n) -> int {
+    CK(cudaMemcpyAsync(ctx->pin_count, scal, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev_c, s));
+    int r = wait_event(ctx->ev_c, to);
+    if (r) return r;
+    memcpy(out, ctx->pin_count, sizeof(double) * n);
+    return RT_OK;
+  };
+  rc = solve(A_star);
+  if (rc) return rc;
+
+  rt_source ds;
+  memset(&ds, 0, sizeof ds);
+  ds.kind = RT_SRC_DUST;
+  ds.T_dev = T_emit;
+  ds.dust = du;
+  rt_trace_params dp = *prm;
+  dp.per_lambda = 0;
+  dp.iter = prm->iter + 1;  // the same streams every step
+  dp.packets = nullptr;
+  dp.packet_log_dev = nullptr;
+  dp.hits_dev = hits_step;
+  dp.packets_per_bin = lp->dust_packets_per_bin > 0 ? lp->dust_packets_per_bin : 0;
+  dp.packets_total = lp->dust_packets_per_bin > 0 ? 0 : lp->dust_packets_total;
+  double imb_low = 0.0, imb_deep = 0.0;  // mass-weighted mean imbalance at levels <= L and > L
+  for (int it = 1; it <= n_steps; ++it) {
+    const auto ts = std::chrono::steady_clock::now();
+    int kind;
+    if (sp->n_steps > 0) kind = sp->schedule[it - 1] ? 1 : 0;
+    else kind = it == 1 || imb_low >= sp->select_frac * std::max(imb_low, imb_deep) ? 0 : 1;
+    CK(cudaMemcpyAsync(T_prev, T_dev, fb, cudaMemcpyDeviceToDevice, s));
+    if (kind == 1) CK(mask_levels(T_dev, g->level, nc, L, T_emit, s));
+    else CK(cudaMemcpyAsync(T_emit, T_dev, fb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(hits_step, hits_star, hb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(I_step, 0, fb * nlev, s));
+    TraceArgs TD{g, 1, &ds, op, &dp, nullptr, nullptr, I_step};
+    TD.levels = 1;
+    TD.confine = kind == 1 ? L : -1;
+    rc = run_jobs(ctx, 1, &TD, &res->lambda.dust_ledger, s, &dp);
+    if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
+    // a full step replaces every level array, a subiteration those below L
+    const int first = kind == 1 ? L + 1 : 0;
+    CK(cudaMemcpyAsync(I + (size_t)first * nc, I_step + (size_t)first * nc, fb * (size_t)(nlev - first),
+                       cudaMemcpyDeviceToDevice, s));
+    CK(sum_levels(I, nlev, nc, A_star, A, s));
+    // imbalance of the new field against the emission that produced it
+    rc = upload();
+    if (rc) return rc;
+    CK(level_imbalance(A, T_prev, g->child, g->rho64, g->level, g->h0, tab, n_table, nc, L, scal + 1, s));
+    rc = solve(A);
+    if (rc) return rc;
+    CK(max_rel_change(T_dev, T_prev, hits_step, g->child, nc, lp->min_hits, scal, s));
+    double v[5];
+    rc = read_scalars(v, 5);
+    if (rc) return rc;
+    if (kind == 0) imb_low = v[2] > 0 ? v[1] / v[2] : 0.0;
+    imb_deep = v[4] > 0 ? v[3] / v[4] : 0.0;
+    res->lambda.history[it - 1] = v[0];
+    res->lambda.n_iter = it;
+    res->step_kind[it - 1] = kind;
+    res->imbalance[it - 1][0] = imb_low;
+    res->imbalance[it - 1][1] = imb_deep;
+    res->step_ms[it - 1] = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - ts).count();
+    if (v[0] < lp->tol) break;
+  }
+  res->lambda.ms = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return RT_OK;
 }
 

@@ -238,4 +238,81 @@ cudaError_t row_sums_f64(const double* data, int n_rows, long long n, double* ou
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------
+// subiterations (Sect. 3.2, App. B)
+// ------------------------------------------------------------------------
+// temperatures that emit in a subiteration: the cells below level L
+__global__ void mask_levels_kernel(const double* __restrict__ T, const uint8_t* __restrict__ level, long long n,
+                                   int L, double* __restrict__ out) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) out[c] = (int)level[c] > L ? T[c] : 0.0;
+}
+
+cudaError_t mask_levels(const double* T, const uint8_t* level, long long n, int L, double* out, cudaStream_t s) {
+  mask_levels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(T, level, n, L, out);
+  return cudaGetLastError();
+}
+
+// Eq. 9: the field of a cell, constant sources plus the dust field of every
+// level array (a cell holds nothing above its own level)
+__global__ void sum_levels_kernel(const double* __restrict__ I, int n_levels, long long n,
+                                  const double* __restrict__ A_star, double* __restrict__ A) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double v = A_star[c];
+  for (int i = 0; i < n_levels; ++i) v += I[(long long)i * n + c];
+  A[c] = v;
+}
+
+cudaError_t sum_levels(const double* I, int n_levels, long long n, const double* A_star, double* A, cudaStream_t s) {
+  sum_levels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(I, n_levels, n, A_star, A);
+  return cudaGetLastError();
+}
+
+// Energy imbalance |absorbed - emitted| and mass, summed over the leaves at
+// level <= L (out[0], out[1]) and below L (out[2], out[3]).  The emission is
+// rho V E(T) with E from the tabulated log E(log T) (cubic Hermite).
+__global__ void imbalance_kernel(const double* __restrict__ A, const double* __restrict__ T,
+                                 const uint32_t* __restrict__ child, const double* __restrict__ rho64,
+                                 const uint8_t* __restrict__ level, double h0, const double* __restrict__ table,
+                                 int n_table, long long n, int L, double* __restrict__ out) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const double x0 = table[0], hx = table[3] - table[0];
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    if (child[c]) continue;
+    const double h = ldexp(h0, -(int)level[c]);
+    const double mass = rho64[c] * h * h * h;
+    double E = 0.0;
+    if (T[c] > 0.0) {
+      const double x = log(T[c]);
+      int i = (int)floor((x - x0) / hx);
+      i = i < 0 ? 0 : (i > n_table - 2 ? n_table - 2 : i);
+      const double y0 = table[3 * i + 1], y1 = table[3 * i + 4];
+      if (y0 > -HUGE_VAL) {
+        const double tt = (x - table[3 * i]) / hx, m0 = table[3 * i + 2] * hx, m1 = table[3 * i + 5] * hx;
+        const double t2 = tt * tt, t3 = t2 * tt;
+        E = exp((2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + tt) * m0 + (-2 * t3 + 3 * t2) * y1 + (t3 - t2) * m1);
+      }
+    }
+    const int gi = (int)level[c] > L ? 2 : 0;
+    v[gi] += fabs(A[c] - mass * E);
+    v[gi + 1] += mass;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    if ((threadIdx.x & 31) == 0 && x != 0.0) atomicAdd(out + k, x);
+  }
+}
+
+cudaError_t level_imbalance(const double* A, const double* T, const uint32_t* child, const double* rho64,
+                            const uint8_t* level, double h0, const double* table, int n_table, long long n, int L,
+                            double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  imbalance_kernel<<<1024, 256, 0, s>>>(A, T, child, rho64, level, h0, table, n_table, n, L, out);
+  return cudaGetLastError();
+}
+
 }  // namespace rtk

@@ -149,6 +149,11 @@ struct JobDev {
   // marches); blocks of 2^ptab_bsh root cells, 2^ptab_ssh tiles per face edge
   const double* ptab;
   int ptab_bsh, ptab_ssh, ptab_nbx, ptab_nby;
+  // subiterations (Sect. 3.2, App. B): absorbed is [n_levels][n_cells] and a
+  // deposit goes to the shallowest grid level the package has reached; a
+  // package that reaches a grid of level <= sub_conf leaves the run
+  int sub_conf;
+  int pad2;
 };
 
 // one (job, source) work item: a contiguous range of the global package counter
@@ -197,7 +202,7 @@ struct LaunchCfg {
 cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev,
                          long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s,
-                         int mode = 0, const TileRun* tiles = nullptr);
+                         int mode = 0, const TileRun* tiles = nullptr, bool levels = false);
 size_t tile_record_bytes(int precision);
 // counting sort of n records (rec_bytes each) by key (< n_keys) from in/key
 // into out; hist_dev holds n_keys + 1 counters
@@ -266,6 +271,14 @@ cudaError_t dust_emission(const double* T, long long n_cells, const uint32_t* ch
 // max over leaves with hits >= min_hits of |T - T_prev| / T_prev into *out
 cudaError_t max_rel_change(const double* T, const double* T_prev, const unsigned int* hits, const uint32_t* child,
                            long long n, double min_hits, double* out, cudaStream_t s);
+// subiterations: T of the cells below level L (0 elsewhere); A = A_star +
+// sum of the level arrays; imbalance |A - rho V E(T)| and mass over the
+// leaves at level <= L and below L (out[4])
+cudaError_t mask_levels(const double* T, const uint8_t* level, long long n, int L, double* out, cudaStream_t s);
+cudaError_t sum_levels(const double* I, int n_levels, long long n, const double* A_star, double* A, cudaStream_t s);
+cudaError_t level_imbalance(const double* A, const double* T, const uint32_t* child, const double* rho64,
+                            const uint8_t* level, double h0, const double* table, int n_table, long long n, int L,
+                            double* out, cudaStream_t s);
 // per-row sums of rows x n (f64) into out[rows] (device)
 cudaError_t row_sums_f64(const double* data, int n_rows, long long n, double* out, cudaStream_t s);
 // inclusive prefix sums of n_rows rows of length n (f64), in place

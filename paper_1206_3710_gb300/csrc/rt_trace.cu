@@ -685,6 +685,24 @@ struct TileIO<double> {
   typedef TRec64 Rec;
 };
 static_assert(sizeof(TRec32) == 80 && sizeof(TRec64) == 128, "tile record layout");
+__device__ __forceinline__ void tile_set_mlev(TRec32& r, int m) { r.pad = (uint32_t)m; }
+__device__ __forceinline__ void tile_set_mlev(TRec64& r, int m) { r.pad0 = (unsigned long long)m; }
+__device__ __forceinline__ int tile_mlev(const TRec32& r) { return (int)r.pad; }
+__device__ __forceinline__ int tile_mlev(const TRec64& r) { return (int)r.pad0; }
+
+// Subiterations: after a crossing that restarted the cursor at the root (a
+// move out of the parent octet, or between root cells), the shallowest grid
+// the package passed is one level below the deepest common ancestor of the
+// two cells: the level of the highest lattice bit that changed on the
+// crossing axis, counted from the lattice level (0 between root cells).
+template <typename R>
+__device__ __forceinline__ int crossed_grid_level(const Geo<R>& g, int a, R dx, R dy, R dz) {
+  const uint32_t cn = a == 0 ? g.cx : (a == 1 ? g.cy : g.cz);
+  const bool plus = (a == 0 ? dx : (a == 1 ? dy : dz)) > R(0);
+  const uint32_t co = plus ? cn - 1u : cn + 1u;
+  const int b = 31 - __clz((int)(co ^ cn));
+  return g.lev > b ? g.lev - b : 0;
+}
 
 #ifndef RT_FP32_MIN_BLOCKS
 #define RT_FP32_MIN_BLOCKS 4
@@ -695,7 +713,7 @@ struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? RT_FP32_MIN_BLOCKS : 2;
 };
 
-template <typename R, bool PEEL, int EST, bool HITS, int MODE>
+template <typename R, bool PEEL, int EST, bool HITS, int MODE, bool LEVELS = false>
 __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const JobDev* __restrict__ jobs,
                                                                          const ItemDev* __restrict__ items,
                                                                          int n_items,
@@ -732,6 +750,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   unsigned int* hitp = nullptr;
   uint32_t step_limit = 0u, ncross = 0u, npeel = 0u;
   uint32_t tile_cur = 0u;  // tiled rounds: the tile this lane traces in
+  int mlev = 0;            // subiterations: shallowest grid level reached
 
   // after a scattering (and its peel-off): new direction from the phase
   // function, Russian roulette when the weight is low, next free path.
@@ -774,6 +793,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       r.pkt_abs = pkt_abs;
       r.next = C.next[t]; r.nscat = (uint32_t)C.nscat[t]; r.ncross = ncross; r.npeel = npeel;
       r.gi = (unsigned long long)C.gi[t];
+      tile_set_mlev(r, mlev);
       static_cast<TRec*>(T.out)[slot] = r;
       T.out_key[slot] = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
     } else {
@@ -845,7 +865,9 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           kext = Num<R>::kext(B);
           alb = Num<R>::alb(B);
           C.gpar[t] = Num<R>::gg(B);
-          absb = J.absorbed ? J.absorbed + (long long)(J.abs_bins > 1 ? bin : 0) * J.n_cells : nullptr;
+          if (LEVELS) mlev = tile_mlev(r);
+          absb = J.absorbed ? J.absorbed + (long long)(LEVELS ? mlev : (J.abs_bins > 1 ? bin : 0)) * J.n_cells
+                            : nullptr;
           if (HITS) hitp = J.hits;
           C.W0[t] = Num<R>::w0(I, bin);
           C.nscat[t] = (int)r.nscat;
@@ -995,6 +1017,11 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           iy = inv_abs(dy);
           iz = inv_abs(dz);
           tau = -Num<R>::log_(draw(C, t));
+          if (LEVELS) {
+            // a package starts in the grid of its emission cell
+            mlev = g.lev;
+            absb = J.absorbed ? J.absorbed + (long long)mlev * J.n_cells : nullptr;
+          }
           if (inside) {
             st = ST_TRACE;
           } else {
@@ -1091,6 +1118,16 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
               ev = EV_CUT;
             } else if (!advance(G, g, cur, a, tx, dx, dy, dz)) {
               ev = EV_ESCAPE;
+            } else if (LEVELS && tr && cur.k == 0 && crossed_grid_level(g, a, dx, dy, dz) < mlev) {
+              const JobDev& J = jobs[C.job[t]];
+              const int v = crossed_grid_level(g, a, dx, dy, dz);
+              if (v <= J.sub_conf) {
+                ev = EV_ESCAPE;  // left the subtree of this subiteration
+              } else {
+                mlev = v;
+                absb = J.absorbed ? J.absorbed + (long long)mlev * J.n_cells : nullptr;
+                if (MODE == 2 && tile_of(g, T) != tile_cur) ev = EV_TILE;
+              }
             } else if (MODE == 2 && tr && cur.k == 0 && tile_of(g, T) != tile_cur) {
               ev = EV_TILE;  // entered another tile: next round
             }
@@ -1480,7 +1517,7 @@ __global__ void philox_kernel(long long n, const uint32_t* __restrict__ ctr, con
 // ------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------
-template <typename R, bool PEEL, int EST, bool HITS>
+template <typename R, bool PEEL, int EST, bool HITS, bool LEVELS = false>
 static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_items, unsigned long long* counter,
                             long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode,
                             const TileRun* tr) {
@@ -1488,14 +1525,14 @@ static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_item
   memset(&T, 0, sizeof T);
   if (tr) T = *tr;
   if (mode == 1)
-    trace_kernel<R, PEEL, EST, HITS, 1><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total,
-                                                                        cfg.refill, q, T);
+    trace_kernel<R, PEEL, EST, HITS, 1, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
+                                                                                total, cfg.refill, q, T);
   else if (mode == 2)
-    trace_kernel<R, PEEL, EST, HITS, 2><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total,
-                                                                        cfg.refill, q, T);
+    trace_kernel<R, PEEL, EST, HITS, 2, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
+                                                                                total, cfg.refill, q, T);
   else
-    trace_kernel<R, PEEL, EST, HITS, 0><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total,
-                                                                        cfg.refill, q, T);
+    trace_kernel<R, PEEL, EST, HITS, 0, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
+                                                                                total, cfg.refill, q, T);
   return cudaGetLastError();
 }
 
@@ -1511,9 +1548,23 @@ static cudaError_t launch_pe(bool peel, const JobDev* jobs, const ItemDev* items
 // Lambda iteration's noise mask)
 cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev, long long total,
-                         const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode, const TileRun* tr) {
+                         const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode, const TileRun* tr,
+                         bool levels) {
   const bool an = estimator == RT_EST_ANALOG;
   if ((mode == 1 || mode == 2) && !tr) return cudaErrorInvalidValue;
+  if (levels) {
+    // subiterations: dust traces with the continuous estimator, no peel-off
+    if (peel || an) return cudaErrorInvalidValue;
+    if (precision == 64)
+      return hits ? launch_t<double, false, RT_EST_CONTINUOUS, true, true>(jobs_dev, items_dev, n_items, counter_dev,
+                                                                           total, cfg, q, s, mode, tr)
+                  : launch_t<double, false, RT_EST_CONTINUOUS, false, true>(jobs_dev, items_dev, n_items, counter_dev,
+                                                                            total, cfg, q, s, mode, tr);
+    return hits ? launch_t<float, false, RT_EST_CONTINUOUS, true, true>(jobs_dev, items_dev, n_items, counter_dev,
+                                                                        total, cfg, q, s, mode, tr)
+                : launch_t<float, false, RT_EST_CONTINUOUS, false, true>(jobs_dev, items_dev, n_items, counter_dev,
+                                                                         total, cfg, q, s, mode, tr);
+  }
   if (hits) {
     if (peel || an) return cudaErrorInvalidValue;
     return precision == 64

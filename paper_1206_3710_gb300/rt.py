@@ -28,7 +28,7 @@ EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "r
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
             "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles",
             "rt_peel_tables_create", "rt_peel_tables_destroy", "rt_peel_tables_size", "rt_peel_tables_read",
-            "rt_peel_tabulated"]
+            "rt_peel_tabulated", "rt_lambda_subiterate"]
 
 
 class RtError(RuntimeError):
@@ -99,6 +99,16 @@ class rt_lambda_params(C.Structure):
 class rt_lambda_result(C.Structure):
     _fields_ = [("n_iter", C.c_int), ("history", C.c_double * 64), ("source_ledger", rt_ledger),
                 ("dust_ledger", rt_ledger), ("ms", C.c_double)]
+
+
+class rt_subiter_params(C.Structure):
+    _fields_ = [("sub_level", C.c_int), ("n_steps", C.c_int), ("schedule", C.POINTER(C.c_int)),
+                ("select_frac", C.c_double)]
+
+
+class rt_subiter_result(C.Structure):
+    _fields_ = [("lambda_", rt_lambda_result), ("step_kind", C.c_int * 64), ("imbalance", (C.c_double * 2) * 64),
+                ("step_ms", C.c_double * 64)]
 
 
 class rt_observers(C.Structure):
@@ -172,6 +182,9 @@ def lib():
                                     C.POINTER(rt_trace_params), C.POINTER(rt_lambda_params), vp,
                                     C.POINTER(rt_lambda_result), vp]
     L.rt_trace_batch.argtypes = [vp, C.c_int, C.POINTER(rt_job), C.POINTER(rt_ledger), vp]
+    L.rt_lambda_subiterate.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics),
+                                       C.POINTER(rt_dust), C.POINTER(rt_trace_params), C.POINTER(rt_lambda_params),
+                                       C.POINTER(rt_subiter_params), vp, C.POINTER(rt_subiter_result), vp]
     L.rt_batch_create.argtypes = [vp, C.c_int, C.POINTER(rt_job), C.POINTER(vp)]
     L.rt_batch_run.argtypes = [vp, C.POINTER(rt_ledger), C.c_double, vp]
     L.rt_batch_destroy.argtypes = [vp]
@@ -480,6 +493,38 @@ def rt_lambda_iterate(ctx: Context, grid: Grid, sources, optics, T_out, *, max_i
                                    C.byref(lp), _ptr(T_out), C.byref(res), _stream(stream)))
     return dict(n_iter=res.n_iter, history=[res.history[i] for i in range(res.n_iter)],
                 source_ledger=res.source_ledger.as_dict(), dust_ledger=res.dust_ledger.as_dict(), ms=res.ms)
+
+
+def rt_lambda_subiterate(ctx: Context, grid: Grid, sources, optics, T_out, *, sub_level: int, schedule=None,
+                         max_iter: int = 30, select_frac: float = 0.25, tol: float = 0.0, min_hits: float = 1000.0,
+                         dust_packets_total: int = 0, dust_packets_per_bin: int = 0, T_min: float = 2.7,
+                         T_max: float = 3000.0, stream=None, **params) -> dict:
+    """Lambda iteration with subiterations (Sect. 3.2, App. B).  ``schedule``:
+    a list of "full" / "sub" steps, or None for the automatic choice over
+    ``max_iter`` steps."""
+    keep = _Keep()
+    src = make_sources(sources, len(optics.kappa_ext), keep)
+    op = make_optics(optics, keep)
+    kabs = (1.0 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
+    du = make_dust(optics.lambda_um, kabs, optics.dnu, T_min, T_max, keep)
+    prm = make_params(keep, **params)
+    lp = rt_lambda_params(max_iter=int(max_iter), tol=float(tol), min_hits=float(min_hits),
+                          dust_packets_total=int(dust_packets_total), dust_packets_per_bin=int(dust_packets_per_bin))
+    sp = rt_subiter_params(sub_level=int(sub_level), n_steps=0, select_frac=float(select_frac))
+    if schedule is not None:
+        kinds = np.array([{"full": 0, "sub": 1}[k] for k in schedule], dtype=np.int32)
+        sp.n_steps = len(kinds)
+        sp.schedule = keep.dp(kinds, np.int32, C.c_int)
+    res = rt_subiter_result()
+    _check(lib().rt_lambda_subiterate(ctx.handle, grid.handle, len(sources), src, C.byref(op), C.byref(du),
+                                      C.byref(prm), C.byref(lp), C.byref(sp), _ptr(T_out), C.byref(res),
+                                      _stream(stream)))
+    n = res.lambda_.n_iter
+    return dict(n_iter=n, history=[res.lambda_.history[i] for i in range(n)],
+                steps=["sub" if res.step_kind[i] else "full" for i in range(n)],
+                imbalance=[(res.imbalance[i][0], res.imbalance[i][1]) for i in range(n)],
+                step_ms=[res.step_ms[i] for i in range(n)], source_ledger=res.lambda_.source_ledger.as_dict(),
+                dust_ledger=res.lambda_.dust_ledger.as_dict(), ms=res.lambda_.ms)
 
 
 def rt_walk(ctx: Context, grid: Grid, origins, dirs, precision: int, max_seg: int, cells, lengths, counts,

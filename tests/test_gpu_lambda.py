@@ -90,3 +90,68 @@ def test_lambda_iteration_small_disc_fp32(rt, ctx):
     assert hist[-1] <= hist[0]
     L = res["source_ledger"]
     assert abs(L["emitted"] - L["absorbed"] - L["escaped"] - L["rr_loss"] + L["rr_gain"]) < 1e-4 * L["emitted"]
+
+
+# ----------------------------------------------------------------- subiterations (Sect. 3.2, App. B)
+
+def _sub_model(tau=2.0):
+    L = 20 * synth.AU_CM
+    desc = synth.random_refined_tree((6, 6, 6), (L,) * 3, 3, 0.35, 21,
+                                     rho_fn=lambda l, x, y, z: np.random.default_rng(l + 3).uniform(0.5e-18, 2e-18,
+                                                                                                    x.size))
+    lam = synth.log_lambda_grid(8)
+    optics = synth.powerlaw_dust(lam, tau / (1e-18 * L), 1.0)
+    star = synth.Source("point", bin_energy=synth.blackbody_star_bins(lam, 4000.0, 2 * synth.RSUN_CM),
+                        pos=(0.43 * L, 0.52 * L, 0.47 * L))
+    return desc, optics, star
+
+
+def test_subiterations_match_oracle_fp64(rt, ctx, orc):
+    """A schedule of full steps and subiterations below level 1, against the
+    oracle's: the same temperatures after every step sequence."""
+    desc, optics, star = _sub_model()
+    g = rt.Grid(ctx, desc)
+    T = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
+    sched = ["full", "sub", "sub", "full", "sub"]
+    npk = 2000
+    res = rt.rt_lambda_subiterate(ctx, g, [star], optics, T, sub_level=1, schedule=sched, min_hits=0.0,
+                                  dust_packets_per_bin=npk, seed=33, precision=64, packets_per_bin=npk)
+    tree = orc.Tree(desc)
+    T_o, hist_o, _ = orc.lambda_subiterate(tree, star, optics, npk, npk, seed=33, schedule=sched, sub_level=1,
+                                           min_hits=0.0, dust_per_bin=True)
+    assert res["steps"] == sched and res["n_iter"] == len(sched)
+    _, leaf = tree.cells()
+    Tg = T.cpu().numpy()
+    np.testing.assert_allclose(Tg[leaf], T_o[leaf], rtol=1e-7)
+    np.testing.assert_allclose(res["history"], hist_o, rtol=1e-4)
+    assert res["dust_ledger"]["escaped"] > 0
+
+
+def test_full_steps_are_the_lambda_iteration(rt, ctx):
+    """Full steps only: the subiteration driver gives the temperatures of the
+    plain Lambda iteration (the level arrays only split the same field)."""
+    desc, optics, star = _sub_model()
+    g = rt.Grid(ctx, desc)
+    kw = dict(dust_packets_per_bin=3000, seed=5, precision=64, packets_per_bin=3000, min_hits=0.0)
+    T1 = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
+    rt.rt_lambda_iterate(ctx, g, [star], optics, T1, max_iter=3, tol=0.0, **kw)
+    T2 = torch.zeros_like(T1)
+    rt.rt_lambda_subiterate(ctx, g, [star], optics, T2, sub_level=1, schedule=["full"] * 3, **kw)
+    np.testing.assert_allclose(T2.cpu().numpy(), T1.cpu().numpy(), rtol=1e-10)
+
+
+def test_subiterations_automatic_small_disc(rt, ctx):
+    """The automatic choice (Sect. 3.3 energy balance) on a small disc: starts
+    with a full step, subiterates the deep levels, returns to full steps, and
+    keeps temperatures in range."""
+    m = synth.disc(n_root=16, max_level=6, n_lambda=12, packets=0, target_cells=3e4, max_cells=200000)
+    g = rt.Grid(ctx, m.tree)
+    T = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
+    res = rt.rt_lambda_subiterate(ctx, g, m.sources, m.optics, T, sub_level=2, max_iter=12, select_frac=0.25,
+                                  min_hits=1000, dust_packets_total=400000, seed=5, precision=32,
+                                  packets_total=400000, rr_wmin=1e-4, rr_p=0.9)
+    assert res["steps"][0] == "full" and "sub" in res["steps"]
+    Tn = T.cpu().numpy()
+    leaf = m.tree.refine_flags == 0
+    assert np.all((Tn[leaf] >= 2.7) & (Tn[leaf] <= 3000.0))
+    assert all(a >= 0 and b >= 0 for a, b in res["imbalance"])
