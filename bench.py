@@ -56,6 +56,10 @@ def parse():
                          "peeltab: accelerated against exact peel-off")
     ap.add_argument("--iters", type=int, default=30, help="disc: Lambda-iteration cap")
     ap.add_argument("--disc-packets", type=int, default=100_000_000)
+    ap.add_argument("--sub-level", type=int, default=-1,
+                    help="disc: compare full Lambda iterations with subiterations below this level")
+    ap.add_argument("--flux-frac", type=float, default=0.05,
+                    help="disc subiterations: full step once the emission below the level changed by this fraction")
     ap.add_argument("--models", type=int, default=64, help="batch: models per launch")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=20.0)

@@ -43,7 +43,55 @@ def run(a):
                                                                                                    torch)
 
 
+def run_disc_subiter(a, rt, synth, ctx, torch):
+    """Sect. 4.2's comparison: the same number of steps of full Lambda
+    iterations and of automatically chosen subiterations (App. B) on the disc;
+    wall time, step kinds and the temperature difference between the two."""
+    m = synth.disc(packets=a.disc_packets)
+    g = rt.Grid(ctx, m.tree)
+    kw = dict(seed=1003, precision=32, packets_total=a.disc_packets, rr_wmin=1e-4, rr_p=0.9,
+              dust_packets_total=a.disc_packets, min_hits=1000, tol=0.0)
+    leaf = m.tree.refine_flags == 0
+    h = m.tree.box[0] / m.tree.root[0] * 0.5 ** synth_levels(m.tree)
+    mass = m.tree.density * h ** 3
+    T_full = torch.zeros(g.n_cells, dtype=torch.float64, device="cuda")
+    clk = _clock_start()
+    rf = rt.rt_lambda_subiterate(ctx, g, m.sources, m.optics, T_full, sub_level=a.sub_level,
+                                 schedule=["full"] * a.iters, **kw)
+    T_sub = torch.zeros_like(T_full)
+    rs = rt.rt_lambda_subiterate(ctx, g, m.sources, m.optics, T_sub, sub_level=a.sub_level, max_iter=a.iters,
+                                 select_frac=0.25, flux_frac=a.flux_frac, **kw)
+    clocks = clk.stop()
+    tf, ts = T_full.cpu().numpy()[leaf], T_sub.cpu().numpy()[leaf]
+    w = mass[leaf]
+    d = ts - tf
+    line = {"metric": "Lambda iteration: full steps against subiterations (App. B), same number of steps",
+            "workload": "disc_subiter", "n_cells": int(m.tree.n_cells), "sub_level": a.sub_level,
+            "flux_frac": a.flux_frac,
+            "steps": a.iters, "full_ms": rf["ms"], "subiter_ms": rs["ms"], "speedup": rf["ms"] / rs["ms"],
+            "subiter_steps": rs["steps"], "subiter_step_ms": rs["step_ms"], "full_step_ms": rf["step_ms"],
+            "imbalance": rs["imbalance"],
+            "rms_dT_K": float(np.sqrt(np.mean(d * d))), "mass_weighted_rms_dT_K": float(np.sqrt(np.sum(w * d * d) / w.sum())),
+            "rms_T_K": float(np.sqrt(np.mean(tf * tf))), "mean_dT_K": float(d.mean()),
+            "history_full": rf["history"], "history_subiter": rs["history"], "clocks": clocks}
+    print(json.dumps(line))
+
+
+def synth_levels(tree):
+    """Level of every cell of a level-ordered tree description."""
+    n0 = int(np.prod(tree.root))
+    lev = np.zeros(tree.n_cells, np.int64)
+    off, cnt = n0, n0
+    for l in range(len(tree.n_refined) - 1):
+        nxt = 8 * int(tree.n_refined[l])
+        lev[off:off + nxt] = l + 1
+        off += nxt
+    return lev
+
+
 def run_disc(a, rt, synth, ctx, torch):
+    if a.sub_level >= 0:
+        return run_disc_subiter(a, rt, synth, ctx, torch)
     t0 = time.perf_counter()
     m = synth.disc(packets=a.disc_packets)
     t_gen = time.perf_counter() - t0

@@ -408,6 +408,9 @@ int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_sour
  *             sub_level = L: dust emitted by the cells of level > L, packages
  *             leave the run where they reach a grid of level <= L (booked as
  *             escaped), the level arrays > L replaced.
+ * A subiteration sends from each cell the packages a full step would: with
+ * lp->dust_packets_total its total is scaled by the fraction of the dust
+ * emission that comes from below L (per-bin counts stay as given).
  * After each step T follows from the summed field.  The dust packages reuse
  * the same random streams every step (key iter = params.iter + 1).  With an
  * explicit schedule the steps run as given (the run stops early when max
@@ -416,14 +419,19 @@ int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_sour
  * balance (Sect. 3.3): the first step is full; then a full step whenever the
  * mass-weighted mean |absorbed - emitted| of the leaves at level <= L
  * (measured at the last full step) is at least select_frac times the larger
- * of it and that of the leaves below L (measured every step), else a
- * subiteration.  Library scratch: 4 f64 + 2 u32 arrays of n_cells and 2 f64
+ * of it and that of the leaves below L (measured every step), or when the
+ * dust emission below L has changed by flux_frac since the last full step
+ * (Sect. 3.3: the flux a grid receives from its children has changed), else
+ * a subiteration.  Library scratch: 4 f64 + 2 u32 arrays of n_cells and 2 f64
  * arrays of n_levels x n_cells. */
 typedef struct {
   int sub_level;           /* L: subiterations cover the subtrees below the refined cells of level L */
   int n_steps;             /* > 0: explicit schedule of this length (<= 64); 0: automatic */
   const int* schedule;     /* host [n_steps]: 0 full step, 1 subiteration */
   double select_frac;      /* automatic choice threshold (0.25 in Sect. 4.2) */
+  double flux_frac;        /* automatic: also a full step once the emission below L has changed by this
+                              fraction since the last full step (the upper levels' field from below
+                              is stale); <= 0: off */
 } rt_subiter_params;
 
 typedef struct {

@@ -465,14 +465,18 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
     history = []
     for step in schedule:
         em = dust_emission(tree, T, lam, kabs, dnu)
+        total = packets_dust
         if step == "sub":
+            e_all = em.sum()
             em = em * (level > L)[None, :]
+            # each cell sends the packages a full step would (App. B)
+            total = max(1, int(np.rint(packets_dust * (em.sum() / e_all if e_all > 0 else 1.0))))
         elif step != "full":
             raise ValueError("schedule entries are 'full' or 'sub'")
         if dust_per_bin:
             npk = np.where(em.sum(axis=1) > 0, packets_dust, 0).astype(np.int64)
         else:
-            npk = packets_by_energy(em.sum(axis=1), packets_dust)
+            npk = packets_by_energy(em.sum(axis=1), total)
         rd = trace(tree, [_DustSource(em)], optics, npk, seed=seed, iter_=1, per_lambda=False,
                    n_threads=n_threads, validation=True, per_level=True,
                    confine_level=L if step == "sub" else -1, **trace_kw)

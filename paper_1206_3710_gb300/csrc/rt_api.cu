@@ -1366,6 +1366,7 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   const size_t fb = sizeof(double) * (size_t)nc, hb = sizeof(unsigned int) * (size_t)nc;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   // A_star, A, T_prev, T_emit | I (levels) | I_step (levels) | hits_star, hits_step | scalars
+  // (scal[0] max dT/T, scal[1..6] level_imbalance sums)
   rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(ctx->lam.p);
@@ -1391,6 +1392,7 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   TraceArgs TS{g, n_src, src, op, &stp, nullptr, nullptr, A_star};
   rc = run_jobs(ctx, 1, &TS, &res->lambda.source_ledger, s, &stp);
   if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
+  CK(cudaMemcpyAsync(A, A_star, fb, cudaMemcpyDeviceToDevice, s));
 
   const int n_table = 8192;
   double *lam, *kab, *dnu, *tab;
@@ -1432,16 +1434,47 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   dp.packets_per_bin = lp->dust_packets_per_bin > 0 ? lp->dust_packets_per_bin : 0;
   dp.packets_total = lp->dust_packets_per_bin > 0 ? 0 : lp->dust_packets_total;
   double imb_low = 0.0, imb_deep = 0.0;  // mass-weighted mean imbalance at levels <= L and > L
+  double e_ref = -1.0;                   // emission below L after the last full step
+  int last_kind = 0;
   for (int it = 1; it <= n_steps; ++it) {
     const auto ts = std::chrono::steady_clock::now();
+    // emission at levels <= L and below L with the current temperatures
+    double e[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (it > 1) {
+      rc = upload();
+      if (rc) return rc;
+      CK(level_imbalance(A, T_dev, g->child, g->rho64, g->level, g->h0, tab, n_table, nc, L, scal + 1, s));
+      rc = read_scalars(e, 7);
+      if (rc) return rc;
+      if (last_kind == 0) e_ref = e[6];
+    }
     int kind;
-    if (sp->n_steps > 0) kind = sp->schedule[it - 1] ? 1 : 0;
-    else kind = it == 1 || imb_low >= sp->select_frac * std::max(imb_low, imb_deep) ? 0 : 1;
+    if (sp->n_steps > 0) {
+      kind = sp->schedule[it - 1] ? 1 : 0;
+    } else if (it == 1) {
+      kind = 0;
+    } else {
+      // Sect. 3.3: iterate the upper levels when their imbalance is a
+      // sizeable fraction of the largest, or when the radiation they receive
+      // from below (tracked by the emission below L) has changed
+      // appreciably since they were last included
+      const bool tagged = sp->flux_frac > 0 && e_ref > 0 && std::fabs(e[6] - e_ref) >= sp->flux_frac * e_ref;
+      kind = tagged || imb_low >= sp->select_frac * std::max(imb_low, imb_deep) ? 0 : 1;
+    }
+    last_kind = kind;
     CK(cudaMemcpyAsync(T_prev, T_dev, fb, cudaMemcpyDeviceToDevice, s));
     if (kind == 1) CK(mask_levels(T_dev, g->level, nc, L, T_emit, s));
     else CK(cudaMemcpyAsync(T_emit, T_dev, fb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(hits_step, hits_star, hb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(I_step, 0, fb * nlev, s));
+    // a subiteration sends from each cell the packages a full step would
+    // (App. B): with a package total, the total scales with the emission of
+    // the subtrees
+    dp.packets_total = lp->dust_packets_per_bin > 0 ? 0 : lp->dust_packets_total;
+    if (kind == 1 && dp.packets_total > 0) {
+      const double f = e[5] + e[6] > 0 ? e[6] / (e[5] + e[6]) : 1.0;
+      dp.packets_total = std::max<int64_t>(1, (int64_t)std::llround((double)lp->dust_packets_total * f));
+    }
     TraceArgs TD{g, 1, &ds, op, &dp, nullptr, nullptr, I_step};
     TD.levels = 1;
     TD.confine = kind == 1 ? L : -1;
@@ -1459,8 +1492,8 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
     rc = solve(A);
     if (rc) return rc;
     CK(max_rel_change(T_dev, T_prev, hits_step, g->child, nc, lp->min_hits, scal, s));
-    double v[5];
-    rc = read_scalars(v, 5);
+    double v[7];
+    rc = read_scalars(v, 7);
     if (rc) return rc;
     if (kind == 0) imb_low = v[2] > 0 ? v[1] / v[2] : 0.0;
     imb_deep = v[4] > 0 ? v[3] / v[4] : 0.0;

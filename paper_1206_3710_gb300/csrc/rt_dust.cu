@@ -269,14 +269,15 @@ cudaError_t sum_levels(const double* I, int n_levels, long long n, const double*
   return cudaGetLastError();
 }
 
-// Energy imbalance |absorbed - emitted| and mass, summed over the leaves at
-// level <= L (out[0], out[1]) and below L (out[2], out[3]).  The emission is
-// rho V E(T) with E from the tabulated log E(log T) (cubic Hermite).
+// Energy imbalance |absorbed - emitted|, mass and emission, summed over the
+// leaves at level <= L (out[0], out[1], out[4]) and below L (out[2], out[3],
+// out[5]).  The emission is rho V E(T) with E from the tabulated
+// log E(log T) (cubic Hermite).
 __global__ void imbalance_kernel(const double* __restrict__ A, const double* __restrict__ T,
                                  const uint32_t* __restrict__ child, const double* __restrict__ rho64,
                                  const uint8_t* __restrict__ level, double h0, const double* __restrict__ table,
                                  int n_table, long long n, int L, double* __restrict__ out) {
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const double x0 = table[0], hx = table[3] - table[0];
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     if (child[c]) continue;
@@ -297,9 +298,10 @@ __global__ void imbalance_kernel(const double* __restrict__ A, const double* __r
     const int gi = (int)level[c] > L ? 2 : 0;
     v[gi] += fabs(A[c] - mass * E);
     v[gi + 1] += mass;
+    v[4 + gi / 2] += mass * E;
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 6; ++k) {
     double x = v[k];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
     if ((threadIdx.x & 31) == 0 && x != 0.0) atomicAdd(out + k, x);
@@ -309,7 +311,7 @@ __global__ void imbalance_kernel(const double* __restrict__ A, const double* __r
 cudaError_t level_imbalance(const double* A, const double* T, const uint32_t* child, const double* rho64,
                             const uint8_t* level, double h0, const double* table, int n_table, long long n, int L,
                             double* out, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(double), s);
+  cudaError_t e = cudaMemsetAsync(out, 0, 6 * sizeof(double), s);
   if (e != cudaSuccess) return e;
   imbalance_kernel<<<1024, 256, 0, s>>>(A, T, child, rho64, level, h0, table, n_table, n, L, out);
   return cudaGetLastError();

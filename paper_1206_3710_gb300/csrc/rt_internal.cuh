@@ -272,8 +272,9 @@ cudaError_t dust_emission(const double* T, long long n_cells, const uint32_t* ch
 cudaError_t max_rel_change(const double* T, const double* T_prev, const unsigned int* hits, const uint32_t* child,
                            long long n, double min_hits, double* out, cudaStream_t s);
 // subiterations: T of the cells below level L (0 elsewhere); A = A_star +
-// sum of the level arrays; imbalance |A - rho V E(T)| and mass over the
-// leaves at level <= L and below L (out[4])
+// sum of the level arrays; imbalance |A - rho V E(T)|, mass and emission
+// rho V E(T) over the leaves at level <= L and below L (out[6]: imbalance,
+// mass at <= L, imbalance, mass below L, emission at <= L, below L)
 cudaError_t mask_levels(const double* T, const uint8_t* level, long long n, int L, double* out, cudaStream_t s);
 cudaError_t sum_levels(const double* I, int n_levels, long long n, const double* A_star, double* A, cudaStream_t s);
 cudaError_t level_imbalance(const double* A, const double* T, const uint32_t* child, const double* rho64,

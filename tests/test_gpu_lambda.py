@@ -106,19 +106,23 @@ def _sub_model(tau=2.0):
     return desc, optics, star
 
 
-def test_subiterations_match_oracle_fp64(rt, ctx, orc):
+@pytest.mark.parametrize("per_bin", [True, False])
+def test_subiterations_match_oracle_fp64(rt, ctx, orc, per_bin):
     """A schedule of full steps and subiterations below level 1, against the
-    oracle's: the same temperatures after every step sequence."""
+    oracle's: the same temperatures after every step sequence (dust packages
+    per bin, or a total that subiterations scale by the subtrees' share of
+    the emission)."""
     desc, optics, star = _sub_model()
     g = rt.Grid(ctx, desc)
     T = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
     sched = ["full", "sub", "sub", "full", "sub"]
     npk = 2000
+    dkw = dict(dust_packets_per_bin=npk) if per_bin else dict(dust_packets_total=npk * 8)
     res = rt.rt_lambda_subiterate(ctx, g, [star], optics, T, sub_level=1, schedule=sched, min_hits=0.0,
-                                  dust_packets_per_bin=npk, seed=33, precision=64, packets_per_bin=npk)
+                                  seed=33, precision=64, packets_per_bin=npk, **dkw)
     tree = orc.Tree(desc)
-    T_o, hist_o, _ = orc.lambda_subiterate(tree, star, optics, npk, npk, seed=33, schedule=sched, sub_level=1,
-                                           min_hits=0.0, dust_per_bin=True)
+    T_o, hist_o, _ = orc.lambda_subiterate(tree, star, optics, npk, npk if per_bin else npk * 8, seed=33,
+                                           schedule=sched, sub_level=1, min_hits=0.0, dust_per_bin=per_bin)
     assert res["steps"] == sched and res["n_iter"] == len(sched)
     _, leaf = tree.cells()
     Tg = T.cpu().numpy()
