@@ -70,7 +70,8 @@ class _Params(C.Structure):
                 ("estimator", C.c_int), ("rr_wmin", C.c_double), ("rr_p", C.c_double),
                 ("step_limit", C.c_int64), ("peel_tau_max", C.c_double), ("per_lambda", C.c_int),
                 ("n_threads", C.c_int), ("packet_offset", C.c_int64), ("peel_block", C.c_int),
-                ("peel_tiles", C.c_int), ("per_level", C.c_int), ("confine_level", C.c_int)]
+                ("peel_tiles", C.c_int), ("per_level", C.c_int), ("confine_level", C.c_int),
+                ("self_absorbed", C.c_void_p)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled",
@@ -254,7 +255,7 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
           step_limit: int = 0, peel_tau_max: float = 0.0, per_lambda: bool = True,
           observers=None, n_threads: int = 1, validation: bool = False, record: bool = False,
           emission: Optional[np.ndarray] = None, packet_offset: int = 0, peel_block: int = 0,
-          peel_tiles: int = 0, per_level: bool = False, confine_level: int = -1):
+          peel_tiles: int = 0, per_level: bool = False, confine_level: int = -1, self_absorbed=None):
     """Run the oracle tracer.
 
     ``sources`` are ``synth.Source``-like objects (kind "point", "external",
@@ -289,7 +290,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
     prm = _Params(seed=seed, job=job, iter=iter_, estimator=estimator, rr_wmin=rr_wmin, rr_p=rr_p,
                   step_limit=step_limit, peel_tau_max=peel_tau_max, per_lambda=int(per_lambda),
                   n_threads=n_threads, packet_offset=packet_offset, peel_block=peel_block,
-                  peel_tiles=peel_tiles, per_level=int(per_level), confine_level=confine_level)
+                  peel_tiles=peel_tiles, per_level=int(per_level), confine_level=confine_level,
+                  self_absorbed=None if self_absorbed is None else self_absorbed.ctypes.data)
     ob = _observers(observers, keep)
     bins = tree.desc.n_levels if per_level else (nl if per_lambda else 1)
     nc = tree.n_cells
@@ -440,7 +442,7 @@ def lambda_iterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed
 
 def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed: int, schedule,
                       sub_level: int, T_min=2.7, T_max=3000.0, min_hits=1000.0, n_threads=1,
-                      dust_per_bin=False, **trace_kw):
+                      dust_per_bin=False, ali=False, **trace_kw):
     """Lambda iteration with subiterations (Sect. 3.2, App. B).  The field of
     the constant sources is computed once.  The dust field is kept in one
     array per grid level i (Eq. 9): I_i holds what packages deposited after
@@ -450,6 +452,10 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
     ``sub_level`` = L: dust emitted only from cells of level > L, packages
     leave the run where they reach a grid of level <= L, and only I_i for
     i > L are replaced.  After each step T follows from I_stars + sum_i I_i.
+    ``ali``: the accelerated Lambda iteration with the diagonal operator of
+    Eq. 3: each step also sums the energy a package leaves in its own
+    emission cell (Lambda_cc E_c, the diagonal part), and T solves
+    E(T) (1 - Lambda_cc) = A - Lambda_cc E(T_old), with Lambda_cc = self / E(T_old).
     Returns T and the per-step max dT/T over cells with >= ``min_hits`` hits."""
     kabs = (1 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
     lam = np.asarray(optics.lambda_um)
@@ -477,14 +483,19 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
             npk = np.where(em.sum(axis=1) > 0, packets_dust, 0).astype(np.int64)
         else:
             npk = packets_by_energy(em.sum(axis=1), total)
+        self_abs = np.zeros(tree.n_cells) if ali else None
         rd = trace(tree, [_DustSource(em)], optics, npk, seed=seed, iter_=1, per_lambda=False,
                    n_threads=n_threads, validation=True, per_level=True,
-                   confine_level=L if step == "sub" else -1, **trace_kw)
+                   confine_level=L if step == "sub" else -1, self_absorbed=self_abs, **trace_kw)
         if step == "full":
             I[:] = rd["absorbed"]
         else:
             I[L + 1:] = rd["absorbed"][L + 1:]
         A = A_star + I.sum(axis=0)
+        if ali:
+            e_old = em.sum(axis=0)
+            lam_cc = np.minimum(np.where(e_old > 0, self_abs / np.where(e_old > 0, e_old, 1.0), 0.0), 0.999)
+            A = (A - self_abs) / (1.0 - lam_cc)
         Tn = dust_temperature(tree, A, lam, kabs, dnu, T_min, T_max, n_threads)
         mask = (hits + rd["hits"].sum(axis=0)) >= min_hits
         rel = np.abs(Tn - T)[mask] / np.maximum(T[mask], 1e-300)

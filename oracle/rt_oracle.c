@@ -627,6 +627,7 @@ static void trace_one(trace_worker* w, int64_t p) {
   int64_t nc = t->n_cells;
 
   double x[3], d[3], E;
+  int64_t origin = -1;  /* emission cell of a dust package */
   if (S->kind == ORC_SRC_DUST) E = J->cdf[seg][nc - 1];
   else E = S->bin_energy[bin];
   double W0 = E / (double)npk, W = W0;
@@ -663,6 +664,7 @@ static void trace_one(trace_worker* w, int64_t p) {
     const double* cdf = J->cdf[seg];
     double u0 = uni(&rs);
     int64_t c = search_cdf(cdf, nc, u0 * cdf[nc - 1]);
+    origin = c;
     const orc_node* n = &t->nodes[c];
     double u1 = uni(&rs), u2 = uni(&rs), u3 = uni(&rs);
     x[0] = n->lo[0] + u1 * n->size;
@@ -720,6 +722,7 @@ static void trace_one(trace_worker* w, int64_t p) {
         double ts = tau / ksca;
         double dep = -W * expm1(-kabs * ts);   /* W (1 - e^-dtau) without cancellation */
         deposit(w, slot, p, dep);
+        if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], dep);
         w->led.absorbed += dep;
         W *= exp(-kabs * ts);
         for (int b = 0; b < 3; ++b) x[b] += ts * d[b];
@@ -749,6 +752,7 @@ static void trace_one(trace_worker* w, int64_t p) {
         tau -= ksca * s;
         double dep = -W * expm1(-kabs * s);
         deposit(w, slot, p, dep);
+        if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], dep);
         w->led.absorbed += dep;
         W *= exp(-kabs * s);
         if (s > 0) { ncross += 1; w->led.n_cross += 1; }

@@ -107,6 +107,8 @@ typedef struct {
   int confine_level;           /* >= 0: a package that reaches a grid of this level or shallower
                                   (it left the subtree of its level-L ancestor) leaves the run,
                                   booked as escaped; < 0: no confinement */
+  double* self_absorbed;       /* optional [n_cells]: energy a dust package deposits in its own
+                                  emission cell, summed per cell (the diagonal of Lambda, Eq. 3) */
 } orc_params;
 
 typedef struct {

@@ -3,6 +3,8 @@
 Sect. 4)."""
 import math
 
+import pytest
+
 import numpy as np
 
 from paper_1206_3710_gb300 import synth
@@ -176,3 +178,45 @@ def test_p13_full_schedule_is_the_lambda_iteration(orc):
                                       min_hits=10)
     np.testing.assert_allclose(T2, T1, rtol=1e-12)
     np.testing.assert_allclose(h2, h1, rtol=1e-9)
+
+
+def test_p13_self_absorption_and_ali(orc):
+    """The diagonal of Lambda (Eq. 3): in a one-cell model every dust deposit
+    lands in the package's own emission cell, so the self-absorption tally
+    equals the absorbed dust energy; and the ALI step, which solves for the
+    cell's own re-absorption, converges where the plain Lambda iteration
+    (Eq. 2) still creeps upwards."""
+    L = 5 * synth.AU_CM
+    rho = 1e-18
+    desc = synth.uniform_tree((1, 1, 1), (L,) * 3, rho)
+    tree = orc.Tree(desc)
+    lam = synth.log_lambda_grid(10)
+    o = synth.powerlaw_dust(lam, 2000.0 / (rho * L), 1.0)   # thick to its own emission, a pure absorber
+    optics = synth.Optics(o.lambda_um, o.kappa_ext, np.zeros(lam.size), np.zeros(lam.size), o.dnu)
+    star = synth.Source("point", bin_energy=synth.blackbody_star_bins(lam, 4000.0, 2 * synth.RSUN_CM),
+                        pos=(0.5 * L, 0.51 * L, 0.49 * L))
+    kabs = (1 - optics.albedo) * optics.kappa_ext
+    T0 = np.array([100.0])
+    em = orc.dust_emission(tree, T0, optics.lambda_um, kabs, optics.dnu)
+    self_abs = np.zeros(1)
+    r = orc.trace(tree, [orc._DustSource(em)], optics, 4000, seed=2, iter_=1, per_lambda=False,
+                  self_absorbed=self_abs)
+    assert self_abs[0] == pytest.approx(r["absorbed"][0][0], rel=1e-12) and self_abs[0] > 0
+    kw = dict(seed=3, schedule=["full"] * 5, sub_level=0, min_hits=0.0, dust_per_bin=True)
+    T_plain, h_plain, _ = orc.lambda_subiterate(tree, star, optics, 2000, 2000, **kw)
+    T_ali, h_ali, _ = orc.lambda_subiterate(tree, star, optics, 2000, 2000, ali=True, **kw)
+    assert h_plain[3] > 0.02 and h_ali[3] < 0.25 * h_plain[3]
+    assert T_ali[0] > T_plain[0]   # the plain iteration is still climbing towards it
+
+
+def test_p13_self_absorption_bounded(orc):
+    desc, optics, _ = _sub_model()
+    tree = orc.Tree(desc)
+    level, leaf = tree.cells()
+    T = np.where(leaf, 200.0, 0.0)
+    em = _dust_source(orc, tree, optics, T)
+    self_abs = np.zeros(tree.n_cells)
+    r = orc.trace(tree, [orc._DustSource(em)], optics, 3000, seed=8, iter_=1, per_lambda=False, self_absorbed=self_abs)
+    A = r["absorbed"][0]
+    assert np.all(self_abs <= A * (1 + 1e-12)) and self_abs.sum() > 0
+    assert np.all(self_abs <= em.sum(axis=0) * (1 + 1e-12))
