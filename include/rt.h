@@ -422,7 +422,7 @@ int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_sour
  * of it and that of the leaves below L (measured every step), or when the
  * dust emission below L has changed by flux_frac since the last full step
  * (Sect. 3.3: the flux a grid receives from its children has changed), else
- * a subiteration.  Library scratch: 4 f64 + 2 u32 arrays of n_cells and 2 f64
+ * a subiteration.  Library scratch: 6 f64 + 2 u32 arrays of n_cells and 2 f64
  * arrays of n_levels x n_cells. */
 typedef struct {
   int sub_level;           /* L: subiterations cover the subtrees below the refined cells of level L */
@@ -432,6 +432,10 @@ typedef struct {
   double flux_frac;        /* automatic: also a full step once the emission below L has changed by this
                               fraction since the last full step (the upper levels' field from below
                               is stale); <= 0: off */
+  int ali;                 /* 1: accelerated Lambda iteration with the diagonal operator (Eq. 3): each
+                              step tallies the energy dust packages leave in their own emission cell,
+                              Lambda_cc = self / E(T_emit), and T solves
+                              E(T) = (A - self) / (1 - Lambda_cc) (Lambda_cc capped at 0.999) */
 } rt_subiter_params;
 
 typedef struct {

@@ -482,6 +482,7 @@ struct TraceArgs {
   const rt_peel_tables* tab = nullptr;  // accelerated peel-off tables, or NULL
   int levels = 0;                       // subiterations: absorbed is [n_levels][n_cells] by grid level
   int confine = -1;                     // subiterations: packages leave at grids of level <= confine
+  double* self_abs = nullptr;           // ALI: self-absorption tally per cell (levels only)
 };
 
 // accelerated peel-off tables (Sect. 2.4)
@@ -675,6 +676,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.peel_tau_max_f = (float)p->peel_tau_max;
     J.pkt_offset = p->packet_offset;
     J.sub_conf = T.confine;
+    J.self_abs = T.levels ? T.self_abs : nullptr;
     if (T.levels && (T.obs || nl < 1)) return fail(RT_ERR_INVALID, "job %d: level arrays exclude peel-off", j);
     if (T.tab) {
       if (T.tab->grid != G || !T.obs || T.obs->n_obs != T.tab->spec.n_obs)
@@ -1366,8 +1368,8 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   const size_t fb = sizeof(double) * (size_t)nc, hb = sizeof(unsigned int) * (size_t)nc;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   // A_star, A, T_prev, T_emit | I (levels) | I_step (levels) | hits_star, hits_step | scalars
-  // (scal[0] max dT/T, scal[1..6] level_imbalance sums)
-  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
+  // (scal[0] max dT/T, scal[1..6] level_imbalance sums) | self, A_ali (ALI)
+  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024 + 2 * al(fb));
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(ctx->lam.p);
   double* A_star = reinterpret_cast<double*>(base);
@@ -1379,6 +1381,8 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   unsigned int* hits_star = reinterpret_cast<unsigned int*>(base + 4 * al(fb) + 2 * al(fb * nlev));
   unsigned int* hits_step = reinterpret_cast<unsigned int*>(base + 4 * al(fb) + 2 * al(fb * nlev) + al(hb));
   double* scal = reinterpret_cast<double*>(base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb));
+  double* self_abs = reinterpret_cast<double*>(base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
+  double* A_ali = reinterpret_cast<double*>(base + 5 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
   CK(cudaMemsetAsync(A_star, 0, fb, s));
   CK(cudaMemsetAsync(hits_star, 0, hb, s));
   CK(cudaMemsetAsync(I, 0, fb * nlev, s));
@@ -1478,6 +1482,10 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
     TraceArgs TD{g, 1, &ds, op, &dp, nullptr, nullptr, I_step};
     TD.levels = 1;
     TD.confine = kind == 1 ? L : -1;
+    if (sp->ali) {
+      CK(cudaMemsetAsync(self_abs, 0, fb, s));
+      TD.self_abs = self_abs;
+    }
     rc = run_jobs(ctx, 1, &TD, &res->lambda.dust_ledger, s, &dp);
     if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
     // a full step replaces every level array, a subiteration those below L
@@ -1489,7 +1497,13 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
     rc = upload();
     if (rc) return rc;
     CK(level_imbalance(A, T_prev, g->child, g->rho64, g->level, g->h0, tab, n_table, nc, L, scal + 1, s));
-    rc = solve(A);
+    if (sp->ali) {
+      // Eq. 3: the cell's own re-absorption solved with the new temperature
+      CK(ali_field(A, self_abs, T_emit, g->child, g->rho64, g->level, g->h0, tab, n_table, nc, A_ali, s));
+      rc = solve(A_ali);
+    } else {
+      rc = solve(A);
+    }
     if (rc) return rc;
     CK(max_rel_change(T_dev, T_prev, hits_step, g->child, nc, lp->min_hits, scal, s));
     double v[7];

@@ -269,6 +269,46 @@ cudaError_t sum_levels(const double* I, int n_levels, long long n, const double*
   return cudaGetLastError();
 }
 
+// emission per unit mass E(T) from the table of log E(log T) (cubic Hermite)
+__device__ __forceinline__ double table_emission(double T, const double* __restrict__ table, int n_table) {
+  if (!(T > 0.0)) return 0.0;
+  const double x0 = table[0], hx = table[3] - table[0];
+  const double x = log(T);
+  int i = (int)floor((x - x0) / hx);
+  i = i < 0 ? 0 : (i > n_table - 2 ? n_table - 2 : i);
+  const double y0 = table[3 * i + 1], y1 = table[3 * i + 4];
+  if (!(y0 > -HUGE_VAL)) return 0.0;
+  const double tt = (x - table[3 * i]) / hx, m0 = table[3 * i + 2] * hx, m1 = table[3 * i + 5] * hx;
+  const double t2 = tt * tt, t3 = t2 * tt;
+  return exp((2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + tt) * m0 + (-2 * t3 + 3 * t2) * y1 + (t3 - t2) * m1);
+}
+
+__global__ void ali_field_kernel(const double* __restrict__ A, const double* __restrict__ self,
+                                 const double* __restrict__ T_emit, const uint32_t* __restrict__ child,
+                                 const double* __restrict__ rho64, const uint8_t* __restrict__ level, double h0,
+                                 const double* __restrict__ table, int n_table, long long n, double* __restrict__ out) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double a = A[c];
+  if (!child[c] && self[c] > 0.0) {
+    const double h = ldexp(h0, -(int)level[c]);
+    const double E = rho64[c] * h * h * h * table_emission(T_emit[c], table, n_table);
+    if (E > 0.0) {
+      const double lam = fmin(self[c] / E, 0.999);
+      a = (a - self[c]) / (1.0 - lam);
+    }
+  }
+  out[c] = a;
+}
+
+cudaError_t ali_field(const double* A, const double* self, const double* T_emit, const uint32_t* child,
+                      const double* rho64, const uint8_t* level, double h0, const double* table, int n_table,
+                      long long n, double* out, cudaStream_t s) {
+  ali_field_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, T_emit, child, rho64, level, h0, table,
+                                                                n_table, n, out);
+  return cudaGetLastError();
+}
+
 // Energy imbalance |absorbed - emitted|, mass and emission, summed over the
 // leaves at level <= L (out[0], out[1], out[4]) and below L (out[2], out[3],
 // out[5]).  The emission is rho V E(T) with E from the tabulated
@@ -278,23 +318,11 @@ __global__ void imbalance_kernel(const double* __restrict__ A, const double* __r
                                  const uint8_t* __restrict__ level, double h0, const double* __restrict__ table,
                                  int n_table, long long n, int L, double* __restrict__ out) {
   double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  const double x0 = table[0], hx = table[3] - table[0];
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     if (child[c]) continue;
     const double h = ldexp(h0, -(int)level[c]);
     const double mass = rho64[c] * h * h * h;
-    double E = 0.0;
-    if (T[c] > 0.0) {
-      const double x = log(T[c]);
-      int i = (int)floor((x - x0) / hx);
-      i = i < 0 ? 0 : (i > n_table - 2 ? n_table - 2 : i);
-      const double y0 = table[3 * i + 1], y1 = table[3 * i + 4];
-      if (y0 > -HUGE_VAL) {
-        const double tt = (x - table[3 * i]) / hx, m0 = table[3 * i + 2] * hx, m1 = table[3 * i + 5] * hx;
-        const double t2 = tt * tt, t3 = t2 * tt;
-        E = exp((2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + tt) * m0 + (-2 * t3 + 3 * t2) * y1 + (t3 - t2) * m1);
-      }
-    }
+    const double E = table_emission(T[c], table, n_table);
     const int gi = (int)level[c] > L ? 2 : 0;
     v[gi] += fabs(A[c] - mass * E);
     v[gi + 1] += mass;

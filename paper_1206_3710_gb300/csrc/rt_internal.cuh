@@ -86,7 +86,8 @@ struct TRec32 {
   float pkt_abs;
   uint32_t next, nscat, ncross;
   unsigned long long gi;      // package index in the launch's package counter
-  uint32_t npeel, pad;
+  uint32_t npeel, pad;        // pad: subiterations' shallowest grid level
+  uint32_t orig, pad1, pad2, pad3;  // orig: ALI, the emission cell of a dust package
 };
 struct TRec64 {
   uint32_t cx, cy, cz, meta;
@@ -94,7 +95,7 @@ struct TRec64 {
   double dx, dy, dz, tau;
   double pkt_abs;
   uint32_t next, nscat, ncross, npeel;
-  unsigned long long gi, pad0, pad1;
+  unsigned long long gi, pad0, pad1;  // pad0: shallowest grid level, pad1: ALI emission cell
 };
 struct TileRun {
   const void* in;               // run: records sorted by key
@@ -154,6 +155,9 @@ struct JobDev {
   // package that reaches a grid of level <= sub_conf leaves the run
   int sub_conf;
   int pad2;
+  // ALI (Eq. 3): energy a dust package leaves in its own emission cell, per
+  // cell (the diagonal of Lambda); NULL: not tallied
+  double* self_abs;
 };
 
 // one (job, source) work item: a contiguous range of the global package counter
@@ -277,6 +281,12 @@ cudaError_t max_rel_change(const double* T, const double* T_prev, const unsigned
 // mass at <= L, imbalance, mass below L, emission at <= L, below L)
 cudaError_t mask_levels(const double* T, const uint8_t* level, long long n, int L, double* out, cudaStream_t s);
 cudaError_t sum_levels(const double* I, int n_levels, long long n, const double* A_star, double* A, cudaStream_t s);
+// ALI temperature input: A' = (A - self) / (1 - self / (rho V E(T_emit))) per
+// leaf (A elsewhere), the field a cell would absorb once its own emission is
+// in equilibrium with it (Eq. 3 with a diagonal Lambda_0)
+cudaError_t ali_field(const double* A, const double* self, const double* T_emit, const uint32_t* child,
+                      const double* rho64, const uint8_t* level, double h0, const double* table, int n_table,
+                      long long n, double* out, cudaStream_t s);
 cudaError_t level_imbalance(const double* A, const double* T, const uint32_t* child, const double* rho64,
                             const uint8_t* level, double h0, const double* table, int n_table, long long n, int L,
                             double* out, cudaStream_t s);

@@ -354,6 +354,7 @@ template <typename R>
 struct ColdState {
   uint32_t k0[256], k1[256], c0[256], c1[256], c3[256], next[256];
   long long log_index[256], pix[256], gi[256];
+  uint32_t orig[256];  // ALI: emission cell of a dust package (~0u: none)
   R W0[256], pw[256], gpar[256];
   int bin[256], nscat[256], obs_i[256], job[256];
   // scattering point and incoming direction, saved during the peel-off
@@ -684,7 +685,11 @@ template <>
 struct TileIO<double> {
   typedef TRec64 Rec;
 };
-static_assert(sizeof(TRec32) == 80 && sizeof(TRec64) == 128, "tile record layout");
+static_assert(sizeof(TRec32) == 96 && sizeof(TRec64) == 128, "tile record layout");
+__device__ __forceinline__ void tile_set_orig(TRec32& r, uint32_t o) { r.orig = o; }
+__device__ __forceinline__ void tile_set_orig(TRec64& r, uint32_t o) { r.pad1 = o; }
+__device__ __forceinline__ uint32_t tile_orig(const TRec32& r) { return r.orig; }
+__device__ __forceinline__ uint32_t tile_orig(const TRec64& r) { return (uint32_t)r.pad1; }
 __device__ __forceinline__ void tile_set_mlev(TRec32& r, int m) { r.pad = (uint32_t)m; }
 __device__ __forceinline__ void tile_set_mlev(TRec64& r, int m) { r.pad0 = (unsigned long long)m; }
 __device__ __forceinline__ int tile_mlev(const TRec32& r) { return (int)r.pad; }
@@ -727,6 +732,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   ledger_init<R>(SL, wid, lane);
   C.job[t] = -1;
+  C.orig[t] = 0xFFFFFFFFu;
   __syncwarp();
 
   // hot per-lane state
@@ -751,6 +757,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   uint32_t step_limit = 0u, ncross = 0u, npeel = 0u;
   uint32_t tile_cur = 0u;  // tiled rounds: the tile this lane traces in
   int mlev = 0;            // subiterations: shallowest grid level reached
+  double* selfb = nullptr; // ALI: self-absorption tally (LEVELS kernels)
 
   // after a scattering (and its peel-off): new direction from the phase
   // function, Russian roulette when the weight is low, next free path.
@@ -794,6 +801,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       r.next = C.next[t]; r.nscat = (uint32_t)C.nscat[t]; r.ncross = ncross; r.npeel = npeel;
       r.gi = (unsigned long long)C.gi[t];
       tile_set_mlev(r, mlev);
+      tile_set_orig(r, C.orig[t]);
       static_cast<TRec*>(T.out)[slot] = r;
       T.out_key[slot] = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
     } else {
@@ -865,7 +873,11 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           kext = Num<R>::kext(B);
           alb = Num<R>::alb(B);
           C.gpar[t] = Num<R>::gg(B);
-          if (LEVELS) mlev = tile_mlev(r);
+          if (LEVELS) {
+            mlev = tile_mlev(r);
+            C.orig[t] = tile_orig(r);
+            selfb = J.self_abs;
+          }
           absb = J.absorbed ? J.absorbed + (long long)(LEVELS ? mlev : (J.abs_bins > 1 ? bin : 0)) * J.n_cells
                             : nullptr;
           if (HITS) hitp = J.hits;
@@ -1021,6 +1033,8 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
             // a package starts in the grid of its emission cell
             mlev = g.lev;
             absb = J.absorbed ? J.absorbed + (long long)mlev * J.n_cells : nullptr;
+            C.orig[t] = I.kind == RT_SRC_DUST ? cur.pending : 0xFFFFFFFFu;
+            selfb = J.self_abs;
           }
           if (inside) {
             st = ST_TRACE;
@@ -1092,6 +1106,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
                   pkt_abs += dep;
                   if (absb) red_acc(absb + g.idx, widen(dep));
                   if (HITS && hitp) atomicAdd(hitp + g.idx, 1u);
+                  if (LEVELS && selfb && g.idx == C.orig[t]) atomicAdd(selfb + g.idx, widen(dep));
                 }
               }
             } else {

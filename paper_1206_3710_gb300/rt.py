@@ -103,7 +103,7 @@ class rt_lambda_result(C.Structure):
 
 class rt_subiter_params(C.Structure):
     _fields_ = [("sub_level", C.c_int), ("n_steps", C.c_int), ("schedule", C.POINTER(C.c_int)),
-                ("select_frac", C.c_double), ("flux_frac", C.c_double)]
+                ("select_frac", C.c_double), ("flux_frac", C.c_double), ("ali", C.c_int)]
 
 
 class rt_subiter_result(C.Structure):
@@ -497,7 +497,7 @@ def rt_lambda_iterate(ctx: Context, grid: Grid, sources, optics, T_out, *, max_i
 
 def rt_lambda_subiterate(ctx: Context, grid: Grid, sources, optics, T_out, *, sub_level: int, schedule=None,
                          max_iter: int = 30, select_frac: float = 0.25, flux_frac: float = 0.05,
-                         tol: float = 0.0, min_hits: float = 1000.0,
+                         ali: bool = False, tol: float = 0.0, min_hits: float = 1000.0,
                          dust_packets_total: int = 0, dust_packets_per_bin: int = 0, T_min: float = 2.7,
                          T_max: float = 3000.0, stream=None, **params) -> dict:
     """Lambda iteration with subiterations (Sect. 3.2, App. B).  ``schedule``:
@@ -512,7 +512,7 @@ def rt_lambda_subiterate(ctx: Context, grid: Grid, sources, optics, T_out, *, su
     lp = rt_lambda_params(max_iter=int(max_iter), tol=float(tol), min_hits=float(min_hits),
                           dust_packets_total=int(dust_packets_total), dust_packets_per_bin=int(dust_packets_per_bin))
     sp = rt_subiter_params(sub_level=int(sub_level), n_steps=0, select_frac=float(select_frac),
-                           flux_frac=float(flux_frac))
+                           flux_frac=float(flux_frac), ali=int(bool(ali)))
     if schedule is not None:
         kinds = np.array([{"full": 0, "sub": 1}[k] for k in schedule], dtype=np.int32)
         sp.n_steps = len(kinds)

@@ -159,3 +159,21 @@ def test_subiterations_automatic_small_disc(rt, ctx):
     leaf = m.tree.refine_flags == 0
     assert np.all((Tn[leaf] >= 2.7) & (Tn[leaf] <= 3000.0))
     assert all(a >= 0 and b >= 0 for a, b in res["imbalance"])
+
+
+def test_ali_matches_oracle_fp64(rt, ctx, orc):
+    """The accelerated Lambda iteration (diagonal operator, Eq. 3) with full
+    steps and subiterations, against the oracle's."""
+    desc, optics, star = _sub_model(tau=4.0)
+    g = rt.Grid(ctx, desc)
+    T = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
+    sched = ["full", "sub", "full"]
+    npk = 2000
+    res = rt.rt_lambda_subiterate(ctx, g, [star], optics, T, sub_level=1, schedule=sched, ali=True, min_hits=0.0,
+                                  dust_packets_per_bin=npk, seed=34, precision=64, packets_per_bin=npk)
+    tree = orc.Tree(desc)
+    T_o, hist_o, _ = orc.lambda_subiterate(tree, star, optics, npk, npk, seed=34, schedule=sched, sub_level=1,
+                                           min_hits=0.0, dust_per_bin=True, ali=True)
+    _, leaf = tree.cells()
+    np.testing.assert_allclose(T.cpu().numpy()[leaf], T_o[leaf], rtol=1e-7)
+    np.testing.assert_allclose(res["history"], hist_o, rtol=1e-4)
