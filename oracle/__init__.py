@@ -71,11 +71,12 @@ class _Params(C.Structure):
                 ("step_limit", C.c_int64), ("peel_tau_max", C.c_double), ("per_lambda", C.c_int),
                 ("n_threads", C.c_int), ("packet_offset", C.c_int64), ("peel_block", C.c_int),
                 ("peel_tiles", C.c_int), ("per_level", C.c_int), ("confine_level", C.c_int),
-                ("self_absorbed", C.c_void_p)]
+                ("self_absorbed", C.c_void_p), ("self_emitted", C.c_void_p), ("self_count", C.c_void_p),
+                ("split_factor", C.c_int), ("split_max_level", C.c_int)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled",
-                 "n_packets", "n_cross", "n_scatter", "n_peel_cross", "n_killed", "n_peel_out"]
+                 "n_packets", "n_cross", "n_scatter", "n_peel_cross", "n_killed", "n_peel_out", "n_split"]
 
 
 class _Ledger(C.Structure):
@@ -255,7 +256,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
           step_limit: int = 0, peel_tau_max: float = 0.0, per_lambda: bool = True,
           observers=None, n_threads: int = 1, validation: bool = False, record: bool = False,
           emission: Optional[np.ndarray] = None, packet_offset: int = 0, peel_block: int = 0,
-          peel_tiles: int = 0, per_level: bool = False, confine_level: int = -1, self_absorbed=None):
+          peel_tiles: int = 0, per_level: bool = False, confine_level: int = -1, self_absorbed=None,
+          self_emitted=None, self_count=None, split_factor: int = 1, split_max_level: int = 255):
     """Run the oracle tracer.
 
     ``sources`` are ``synth.Source``-like objects (kind "point", "external",
@@ -291,7 +293,10 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
                   step_limit=step_limit, peel_tau_max=peel_tau_max, per_lambda=int(per_lambda),
                   n_threads=n_threads, packet_offset=packet_offset, peel_block=peel_block,
                   peel_tiles=peel_tiles, per_level=int(per_level), confine_level=confine_level,
-                  self_absorbed=None if self_absorbed is None else self_absorbed.ctypes.data)
+                  self_absorbed=None if self_absorbed is None else self_absorbed.ctypes.data,
+                  self_emitted=None if self_emitted is None else self_emitted.ctypes.data,
+                  self_count=None if self_count is None else self_count.ctypes.data,
+                  split_factor=int(split_factor), split_max_level=int(split_max_level))
     ob = _observers(observers, keep)
     bins = tree.desc.n_levels if per_level else (nl if per_lambda else 1)
     nc = tree.n_cells
@@ -442,7 +447,7 @@ def lambda_iterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed
 
 def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed: int, schedule,
                       sub_level: int, T_min=2.7, T_max=3000.0, min_hits=1000.0, n_threads=1,
-                      dust_per_bin=False, ali=False, **trace_kw):
+                      dust_per_bin=False, ali=False, ali_min_packages=100, **trace_kw):
     """Lambda iteration with subiterations (Sect. 3.2, App. B).  The field of
     the constant sources is computed once.  The dust field is kept in one
     array per grid level i (Eq. 9): I_i holds what packages deposited after
@@ -453,9 +458,14 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
     leave the run where they reach a grid of level <= L, and only I_i for
     i > L are replaced.  After each step T follows from I_stars + sum_i I_i.
     ``ali``: the accelerated Lambda iteration with the diagonal operator of
-    Eq. 3: each step also sums the energy a package leaves in its own
-    emission cell (Lambda_cc E_c, the diagonal part), and T solves
-    E(T) (1 - Lambda_cc) = A - Lambda_cc E(T_old), with Lambda_cc = self / E(T_old).
+    Eq. 3: each step also sums, per cell, the energy its own packages leave
+    in it (self), the energy they carried (emitted) and their number;
+    Lambda_cc = self / emitted is the fraction of a cell's emission it
+    re-absorbs, capped at 0.999, and T solves E(T) (1 - Lambda_cc) =
+    A - Lambda_cc emitted (= A - self below the cap).  The diagonal operator
+    is used in the cells that sent at least ``ali_min_packages`` packages;
+    the others take the plain step (Lambda_cc = 0), whose expectation
+    includes their rare self-absorbed packages.
     Returns T and the per-step max dT/T over cells with >= ``min_hits`` hits."""
     kabs = (1 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
     lam = np.asarray(optics.lambda_um)
@@ -484,18 +494,22 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
         else:
             npk = packets_by_energy(em.sum(axis=1), total)
         self_abs = np.zeros(tree.n_cells) if ali else None
+        self_emit = np.zeros(tree.n_cells) if ali else None
+        self_n = np.zeros(tree.n_cells) if ali else None
         rd = trace(tree, [_DustSource(em)], optics, npk, seed=seed, iter_=1, per_lambda=False,
                    n_threads=n_threads, validation=True, per_level=True,
-                   confine_level=L if step == "sub" else -1, self_absorbed=self_abs, **trace_kw)
+                   confine_level=L if step == "sub" else -1, self_absorbed=self_abs, self_emitted=self_emit,
+                   self_count=self_n,
+                   **trace_kw)
         if step == "full":
             I[:] = rd["absorbed"]
         else:
             I[L + 1:] = rd["absorbed"][L + 1:]
         A = A_star + I.sum(axis=0)
         if ali:
-            e_old = em.sum(axis=0)
-            lam_cc = np.minimum(np.where(e_old > 0, self_abs / np.where(e_old > 0, e_old, 1.0), 0.0), 0.999)
-            A = (A - self_abs) / (1.0 - lam_cc)
+            use = (self_n >= max(ali_min_packages, 1)) & (self_emit > 0)
+            lam_cc = np.minimum(np.where(use, self_abs / np.where(use, self_emit, 1.0), 0.0), 0.999)
+            A = (A - lam_cc * self_emit) / (1.0 - lam_cc)
         Tn = dust_temperature(tree, A, lam, kabs, dnu, T_min, T_max, n_threads)
         mask = (hits + rd["hits"].sum(axis=0)) >= min_hits
         rel = np.abs(Tn - T)[mask] / np.maximum(T[mask], 1e-300)

@@ -354,6 +354,16 @@ typedef struct {
   double* peel_tab;        /* accelerated peel-off: orc_peel_table of the observers, or NULL */
 } trace_job;
 
+/* One photon-package path: the primary package, or a copy made where a
+ * package entered a deeper grid (package splitting, Sect. 2.3). */
+typedef struct {
+  double x[3], d[3], W, W0, tau;
+  rstream rs;
+  const orc_node* prev;
+  int mlev;  /* shallowest grid level visited (subiterations) */
+  int plev;  /* resampling: grid level of the last cell, capped at split_max_level (-1: none yet) */
+} orc_path;
+
 typedef struct {
   trace_job* job;
   int64_t p0, p1;
@@ -365,6 +375,8 @@ typedef struct {
   int64_t* stamp;
   int64_t* touched;
   int64_t n_touched, cap_touched;
+  orc_path* stack;               /* copies waiting to be followed (package splitting) */
+  int64_t n_stack, cap_stack;
   orc_ledger led;
 } trace_worker;
 
@@ -601,6 +613,197 @@ static int64_t search_cdf(const double* cdf, int64_t n, double target) {
   return lo;
 }
 
+static uint32_t raw_word(rstream* s) {
+  return orc_draw_u32(s->seed, s->job, s->iter, s->stream, s->pkt, s->next++);
+}
+
+static int ipow(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+/* Resampling at a change of grid level (Sect. 2.3): entering a grid dl
+ * levels deeper, the package becomes M = N^dl packages of weight W/M at the
+ * same point and direction, the copies with their own random streams (three
+ * words drawn by the package name them) and free paths; leaving for a grid
+ * dl levels shallower, it survives with probability 1/M (an integer test on
+ * one drawn word) and then carries M W.  W0, the reference of the ordinary
+ * roulette, follows the weight.  Returns 1 when the package is killed. */
+static int resample(trace_worker* w, orc_path* P, const orc_node* n) {
+  const orc_params* prm = w->job->prm;
+  const int lv = n->level < prm->split_max_level ? n->level : prm->split_max_level;
+  const int last = P->plev;
+  P->plev = lv;
+  if (last < 0 || lv == last) return 0;
+  if (lv > last) {
+    const int M = ipow(prm->split_factor, lv - last);
+    const uint32_t w0 = raw_word(&P->rs), w1 = raw_word(&P->rs), w2 = raw_word(&P->rs);
+    P->W /= M;
+    P->W0 /= M;
+    for (int k = 1; k < M; ++k) {
+      if (w->n_stack == w->cap_stack) {
+        w->cap_stack = w->cap_stack ? 2 * w->cap_stack : 64;
+        w->stack = (orc_path*)realloc(w->stack, (size_t)w->cap_stack * sizeof(orc_path));
+      }
+      orc_path* c = &w->stack[w->n_stack++];
+      *c = *P;
+      c->rs.pkt = (uint64_t)w0 | ((uint64_t)w1 << 32);
+      c->rs.next = 0;
+      c->rs.stream = 0x80000000u | (w2 & 0x7FFFFF00u) | (uint32_t)k;
+      c->tau = -log(uni(&c->rs));
+    }
+    w->led.n_split += M - 1;
+    return 0;
+  }
+  const uint32_t M = (uint32_t)ipow(prm->split_factor, last - lv);
+  const uint32_t u = raw_word(&P->rs);
+  if ((uint64_t)u * M < ((uint64_t)1 << 32)) {
+    const double Wn = P->W * M;
+    w->led.rr_gain += Wn - P->W;
+    P->W = Wn;
+    P->W0 *= M;
+    return 0;
+  }
+  w->led.rr_loss += P->W;
+  P->W = 0;
+  return 1;
+}
+
+/* Follows one path until it escapes, is killed or absorbed; returns its
+ * fate (0 escaped, 1 roulette, 2 step limit, 3 analog absorption). */
+static int follow(trace_worker* w, orc_path* P, int64_t p, int bin, double kext_b, int64_t origin,
+                  double* nscat_out, double* ncross_out) {
+  trace_job* J = w->job;
+  const orc_tree* t = J->t;
+  const orc_params* prm = J->prm;
+  int64_t nc = t->n_cells;
+  int ob = J->bins > 1 ? bin : 0;
+  double alb = J->op->albedo[bin], g = J->op->g_hg[bin];
+  int analog = prm->estimator == ORC_EST_ANALOG;
+  double* x = P->x;
+  double* d = P->d;
+  double W = P->W, tau = P->tau;
+  double nscat = 0, ncross = 0;
+  int fate = 0;
+  int64_t steps = 0;
+  for (;;) {
+    const orc_node* n = locate(t, x, d);
+    if (!n) {  /* left through the outer boundary of the root grid */
+      w->led.escaped += W;
+      fate = 0;
+      break;
+    }
+    if (n != P->prev) {
+      const int v = P->prev ? visited_level(P->prev, n) : n->level;
+      if (P->prev && prm->confine_level >= 0 && v <= prm->confine_level) {
+        w->led.escaped += W;  /* left the subtree of the subiteration */
+        fate = 0;
+        break;
+      }
+      if (!P->prev || v < P->mlev) P->mlev = v;
+      P->prev = n;
+      if (prm->split_factor > 1) {
+        P->W = W;
+        P->tau = tau;
+        if (resample(w, P, n)) { W = 0; fate = 1; break; }
+        W = P->W;
+      }
+    }
+    if (prm->per_level) ob = P->mlev;
+    if (prm->step_limit > 0 && steps >= prm->step_limit) {
+      w->led.killed += W;
+      w->led.n_killed += 1;
+      fate = 2;
+      W = 0;
+      break;
+    }
+    ++steps;
+    int a;
+    double s = exit_dist(n, x, d, &a);
+    double kext = kext_b * n->rho;
+    int64_t slot = (int64_t)ob * nc + n->id;
+    if (!analog) {
+      double ksca = alb * kext, kabs = (1.0 - alb) * kext;
+      if (ksca > 0 && ksca * s >= tau) {
+        /* scattering inside this cell */
+        double ts = tau / ksca;
+        double dep = -W * expm1(-kabs * ts);   /* W (1 - e^-dtau) without cancellation */
+        deposit(w, slot, p, dep);
+        if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], dep);
+        w->led.absorbed += dep;
+        W *= exp(-kabs * ts);
+        for (int b = 0; b < 3; ++b) x[b] += ts * d[b];
+        if (ts > 0) { ncross += 1; w->led.n_cross += 1; }
+        nscat += 1;
+        w->led.n_scatter += 1;
+        if (J->obs && J->obs->n_obs > 0) peel(w, x, d, W, bin);
+        double mu = orc_hg_mu(g, uni(&P->rs));
+        double phi = 2.0 * ORC_PI * uni(&P->rs);
+        double nd[3];
+        orc_scatter_dir(d, mu, phi, nd);
+        d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
+        if (prm->rr_wmin > 0 && W < prm->rr_wmin * P->W0) {
+          double ur = uni(&P->rs);
+          if (ur < prm->rr_p) {
+            w->led.rr_loss += W;
+            W = 0;
+            fate = 1;
+            break;
+          }
+          double Wn = W / (1.0 - prm->rr_p);
+          w->led.rr_gain += Wn - W;
+          W = Wn;
+        }
+        tau = -log(uni(&P->rs));
+      } else {
+        tau -= ksca * s;
+        double dep = -W * expm1(-kabs * s);
+        deposit(w, slot, p, dep);
+        if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], dep);
+        w->led.absorbed += dep;
+        W *= exp(-kabs * s);
+        if (s > 0) { ncross += 1; w->led.n_cross += 1; }
+        move_to_face(n, x, d, s, a);
+      }
+    } else {
+      if (kext > 0 && kext * s >= tau) {
+        double ts = tau / kext;
+        for (int b = 0; b < 3; ++b) x[b] += ts * d[b];
+        if (ts > 0) { ncross += 1; w->led.n_cross += 1; }
+        double ua = uni(&P->rs);
+        if (ua < alb) {
+          nscat += 1;
+          w->led.n_scatter += 1;
+          if (J->obs && J->obs->n_obs > 0) peel(w, x, d, W, bin);
+          double mu = orc_hg_mu(g, uni(&P->rs));
+          double phi = 2.0 * ORC_PI * uni(&P->rs);
+          double nd[3];
+          orc_scatter_dir(d, mu, phi, nd);
+          d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
+        } else {
+          deposit(w, slot, p, W);
+          if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], W);
+          w->led.absorbed += W;
+          W = 0;
+          fate = 3;
+          break;
+        }
+        tau = -log(uni(&P->rs));
+      } else {
+        tau -= kext * s;
+        if (s > 0) { ncross += 1; w->led.n_cross += 1; }
+        move_to_face(n, x, d, s, a);
+      }
+    }
+  }
+  P->W = W;
+  P->tau = tau;
+  *nscat_out = nscat;
+  *ncross_out = ncross;
+  return fate;
+}
+
 static void trace_one(trace_worker* w, int64_t p) {
   trace_job* J = w->job;
   const orc_tree* t = J->t;
@@ -665,6 +868,8 @@ static void trace_one(trace_worker* w, int64_t p) {
     double u0 = uni(&rs);
     int64_t c = search_cdf(cdf, nc, u0 * cdf[nc - 1]);
     origin = c;
+    if (prm->self_emitted) atomic_add_double(&prm->self_emitted[c], W0);
+    if (prm->self_count) atomic_add_double(&prm->self_count[c], 1.0);
     const orc_node* n = &t->nodes[c];
     double u1 = uni(&rs), u2 = uni(&rs), u3 = uni(&rs);
     x[0] = n->lo[0] + u1 * n->size;
@@ -677,126 +882,33 @@ static void trace_one(trace_worker* w, int64_t p) {
   w->led.n_packets += 1;
 
   double kext_b = J->op->kappa_ext[bin] * t->h0;   /* per unit density, per root-cell unit */
-  double alb = J->op->albedo[bin], g = J->op->g_hg[bin];
-  int analog = prm->estimator == ORC_EST_ANALOG;
-  double tau = -log(uni(&rs));
-  double nscat = 0, ncross = 0;
-  int fate = 0;
-  int64_t steps = 0;
-  const orc_node* prev = NULL;
-  int mlev = 0;  /* shallowest grid level visited (subiterations) */
+  orc_path P;
+  for (int k2 = 0; k2 < 3; ++k2) { P.x[k2] = x[k2]; P.d[k2] = d[k2]; }
+  P.W = W;
+  P.W0 = W0;
+  P.rs = rs;
+  P.tau = -log(uni(&P.rs));
+  P.prev = NULL;
+  P.mlev = 0;
+  /* resampling (Sect. 2.3): the external field enters through the root grid */
+  P.plev = S->kind == ORC_SRC_EXTERNAL ? 0 : -1;
+  int primary = 1;
   for (;;) {
-    const orc_node* n = locate(t, x, d);
-    if (!n) {  /* left through the outer boundary of the root grid */
-      w->led.escaped += W;
-      fate = 0;
-      break;
+    double nscat = 0, ncross = 0;
+    int fate = follow(w, &P, p, bin, kext_b, origin, &nscat, &ncross);
+    if (primary && J->rec) {
+      double* r = &J->rec[p * 10];
+      r[0] = fate == 0 ? P.W : 0.0;
+      r[1] = nscat;
+      r[2] = ncross;
+      r[3] = fate;
+      for (int a = 0; a < 3; ++a) { r[4 + a] = P.x[a] * t->h0; r[7 + a] = P.d[a]; }
     }
-    if (n != prev) {
-      const int v = prev ? visited_level(prev, n) : n->level;
-      if (prev && prm->confine_level >= 0 && v <= prm->confine_level) {
-        w->led.escaped += W;  /* left the subtree of the subiteration */
-        fate = 0;
-        break;
-      }
-      if (!prev || v < mlev) mlev = v;
-      prev = n;
-    }
-    if (prm->per_level) ob = mlev;
-    if (prm->step_limit > 0 && steps >= prm->step_limit) {
-      w->led.killed += W;
-      w->led.n_killed += 1;
-      fate = 2;
-      W = 0;
-      break;
-    }
-    ++steps;
-    int a;
-    double s = exit_dist(n, x, d, &a);
-    double kext = kext_b * n->rho;
-    int64_t slot = (int64_t)ob * nc + n->id;
-    if (!analog) {
-      double ksca = alb * kext, kabs = (1.0 - alb) * kext;
-      if (ksca > 0 && ksca * s >= tau) {
-        /* scattering inside this cell */
-        double ts = tau / ksca;
-        double dep = -W * expm1(-kabs * ts);   /* W (1 - e^-dtau) without cancellation */
-        deposit(w, slot, p, dep);
-        if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], dep);
-        w->led.absorbed += dep;
-        W *= exp(-kabs * ts);
-        for (int b = 0; b < 3; ++b) x[b] += ts * d[b];
-        if (ts > 0) { ncross += 1; w->led.n_cross += 1; }
-        nscat += 1;
-        w->led.n_scatter += 1;
-        if (J->obs && J->obs->n_obs > 0) peel(w, x, d, W, bin);
-        double mu = orc_hg_mu(g, uni(&rs));
-        double phi = 2.0 * ORC_PI * uni(&rs);
-        double nd[3];
-        orc_scatter_dir(d, mu, phi, nd);
-        d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
-        if (prm->rr_wmin > 0 && W < prm->rr_wmin * W0) {
-          double ur = uni(&rs);
-          if (ur < prm->rr_p) {
-            w->led.rr_loss += W;
-            W = 0;
-            fate = 1;
-            break;
-          }
-          double Wn = W / (1.0 - prm->rr_p);
-          w->led.rr_gain += Wn - W;
-          W = Wn;
-        }
-        tau = -log(uni(&rs));
-      } else {
-        tau -= ksca * s;
-        double dep = -W * expm1(-kabs * s);
-        deposit(w, slot, p, dep);
-        if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], dep);
-        w->led.absorbed += dep;
-        W *= exp(-kabs * s);
-        if (s > 0) { ncross += 1; w->led.n_cross += 1; }
-        move_to_face(n, x, d, s, a);
-      }
-    } else {
-      if (kext > 0 && kext * s >= tau) {
-        double ts = tau / kext;
-        for (int b = 0; b < 3; ++b) x[b] += ts * d[b];
-        if (ts > 0) { ncross += 1; w->led.n_cross += 1; }
-        double ua = uni(&rs);
-        if (ua < alb) {
-          nscat += 1;
-          w->led.n_scatter += 1;
-          if (J->obs && J->obs->n_obs > 0) peel(w, x, d, W, bin);
-          double mu = orc_hg_mu(g, uni(&rs));
-          double phi = 2.0 * ORC_PI * uni(&rs);
-          double nd[3];
-          orc_scatter_dir(d, mu, phi, nd);
-          d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
-        } else {
-          deposit(w, slot, p, W);
-          w->led.absorbed += W;
-          W = 0;
-          fate = 3;
-          break;
-        }
-        tau = -log(uni(&rs));
-      } else {
-        tau -= kext * s;
-        if (s > 0) { ncross += 1; w->led.n_cross += 1; }
-        move_to_face(n, x, d, s, a);
-      }
-    }
+    primary = 0;
+    if (w->n_stack == 0) break;
+    P = w->stack[--w->n_stack];
   }
   if (w->pkt_acc) flush_packet(w);
-  if (J->rec) {
-    double* r = &J->rec[p * 10];
-    r[0] = fate == 0 ? W : 0.0;
-    r[1] = nscat;
-    r[2] = ncross;
-    r[3] = fate;
-    for (int a = 0; a < 3; ++a) { r[4 + a] = x[a] * t->h0; r[7 + a] = d[a]; }
-  }
 }
 
 static void* trace_thread(void* arg) {
@@ -810,6 +922,7 @@ static void ledger_add(orc_ledger* a, const orc_ledger* b) {
   a->rr_gain += b->rr_gain; a->rr_loss += b->rr_loss; a->killed += b->killed; a->peeled += b->peeled;
   a->n_packets += b->n_packets; a->n_cross += b->n_cross; a->n_scatter += b->n_scatter;
   a->n_peel_cross += b->n_peel_cross; a->n_killed += b->n_killed; a->n_peel_out += b->n_peel_out;
+  a->n_split += b->n_split;
 }
 
 int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_optics* op,
@@ -817,6 +930,13 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
               double* sumsq, double* hits, double* rec, orc_ledger* ledger) {
   if (!t || n_src <= 0 || !src || !op || !prm || op->n_lambda <= 0) return -1;
   if (prm->per_level && obs && obs->n_obs > 0) return -1;  /* levels take the place of bins */
+  if (prm->split_factor > 1) {  /* a split makes at most 256 packages */
+    const int lm = prm->split_max_level < t->n_levels - 1 ? prm->split_max_level : t->n_levels - 1;
+    if (lm < 0) return -1;
+    int64_t m = 1;
+    for (int l = 0; l < lm; ++l) m *= prm->split_factor;
+    if (m > 256) return -1;
+  }
   int nl = op->n_lambda;
   int bins = prm->per_level ? t->n_levels : (prm->per_lambda ? nl : 1);
   int64_t nc = t->n_cells;
@@ -896,7 +1016,7 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
         for (int64_t k = 0; k < (int64_t)bins * nc; ++k) { sumsq[k] += w->sumsq[k]; hits[k] += w->hits[k]; }
       free(w->absorbed); free(w->images); free(w->sumsq); free(w->hits);
     }
-    free(w->pkt_acc); free(w->stamp); free(w->touched);
+    free(w->pkt_acc); free(w->stamp); free(w->touched); free(w->stack);
   }
   if (ledger) *ledger = L;
   for (int64_t i = 0; i < (int64_t)n_src * nl; ++i) free(J.cdf[i]);

@@ -109,11 +109,20 @@ typedef struct {
                                   booked as escaped; < 0: no confinement */
   double* self_absorbed;       /* optional [n_cells]: energy a dust package deposits in its own
                                   emission cell, summed per cell (the diagonal of Lambda, Eq. 3) */
+  double* self_emitted;        /* with self_absorbed: energy of the dust packages emitted per cell */
+  double* self_count;          /* with self_absorbed: number of dust packages emitted per cell */
+  /* Resampling at grid boundaries (Sect. 2.3): a package entering a cell dl
+   * grid levels deeper than its last cell is split into split_factor^dl
+   * packages; one leaving for a cell dl levels shallower survives with
+   * probability split_factor^-dl.  Levels are capped at split_max_level. */
+  int split_factor;            /* <= 1: off */
+  int split_max_level;
 } orc_params;
 
 typedef struct {
   double emitted, absorbed, escaped, rr_gain, rr_loss, killed, peeled;
   double n_packets, n_cross, n_scatter, n_peel_cross, n_killed, n_peel_out;
+  double n_split;              /* copies made by package splitting */
 } orc_ledger;
 
 /* Trace all packets of all sources.  absorbed [bins][n_cells] and images

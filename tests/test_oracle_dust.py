@@ -210,13 +210,27 @@ def test_p13_self_absorption_and_ali(orc):
 
 
 def test_p13_self_absorption_bounded(orc):
+    """The two tallies behind Lambda_cc: what a cell's own packages leave in
+    it is part of what it absorbed and of what they carried; the carried
+    energies add up to the whole dust emission (every package is booked at
+    its emission cell once), and per cell they follow the emission."""
     desc, optics, _ = _sub_model()
     tree = orc.Tree(desc)
     level, leaf = tree.cells()
     T = np.where(leaf, 200.0, 0.0)
     em = _dust_source(orc, tree, optics, T)
     self_abs = np.zeros(tree.n_cells)
-    r = orc.trace(tree, [orc._DustSource(em)], optics, 3000, seed=8, iter_=1, per_lambda=False, self_absorbed=self_abs)
+    self_emit = np.zeros(tree.n_cells)
+    r = orc.trace(tree, [orc._DustSource(em)], optics, 3000, seed=8, iter_=1, per_lambda=False, self_absorbed=self_abs,
+                  self_emitted=self_emit)
     A = r["absorbed"][0]
     assert np.all(self_abs <= A * (1 + 1e-12)) and self_abs.sum() > 0
-    assert np.all(self_abs <= em.sum(axis=0) * (1 + 1e-12))
+    assert np.all(self_abs <= self_emit * (1 + 1e-12))
+    assert self_emit.sum() == pytest.approx(em.sum(), rel=1e-12)
+    assert np.all(self_emit[~leaf] == 0.0)
+    # the emitted tally is a multinomial draw around the emission: summed
+    # over the leaves of a level it follows the level's share
+    e = em.sum(axis=0)
+    for lv in range(2):
+        s = (level == lv) & leaf
+        assert self_emit[s].sum() == pytest.approx(e[s].sum(), rel=0.1)
