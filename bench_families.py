@@ -15,6 +15,11 @@
            marches on the molecular cloud (6 axis observers) and the disc
            (5 observers 2 degrees above the plane): table build time, peel-off
            kernel time, crossings, image relative RMS difference.
+* split -- resampling at grid boundaries (Sect. 2.3, Table 1): the 4 um
+           radiation field of the molecular cloud from the external field and
+           from embedded point sources, R runs with and without splitting
+           (factor 4) from the same number of initial packages; RMS deviation
+           per hierarchy level from the mean of all runs, and trace time.
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -39,8 +44,8 @@ def run(a):
     from paper_1206_3710_gb300 import rt, synth
     torch.cuda.set_device(0)
     ctx = rt.Context(0)
-    {"disc": run_disc, "batch": run_batch, "serve": run_serve, "peeltab": run_peeltab}[a.workload](a, rt, synth, ctx,
-                                                                                                   torch)
+    {"disc": run_disc, "batch": run_batch, "serve": run_serve, "peeltab": run_peeltab,
+     "split": run_split}[a.workload](a, rt, synth, ctx, torch)
 
 
 def run_disc_subiter(a, rt, synth, ctx, torch):
@@ -61,6 +66,22 @@ def run_disc_subiter(a, rt, synth, ctx, torch):
     T_sub = torch.zeros_like(T_full)
     rs = rt.rt_lambda_subiterate(ctx, g, m.sources, m.optics, T_sub, sub_level=a.sub_level, max_iter=a.iters,
                                  select_frac=0.25, flux_frac=a.flux_frac, **kw)
+    ali = None
+    if a.ali:
+        T_ali = torch.zeros_like(T_full)
+        ra = rt.rt_lambda_subiterate(ctx, g, m.sources, m.optics, T_ali, sub_level=a.sub_level,
+                                     schedule=["full"] * a.iters, ali=True, **kw)
+        ta = T_ali.cpu().numpy()[leaf]
+        tfa = T_full.cpu().numpy()[leaf]
+        lv = synth_levels(m.tree)[leaf]
+        per_level = [[int(l), int((lv == l).sum()), round(float(tfa[lv == l].mean()), 2),
+                      round(float(ta[lv == l].mean()), 2)] for l in range(int(lv.max()) + 1) if (lv == l).any()]
+        ali = {"ms": ra["ms"], "history": ra["history"], "mean_T_K": float(ta.mean()),
+               "mean_T_full_K": float(tfa.mean()),
+               "mass_weighted_mean_dT_vs_full_K": float(np.sum(mass[leaf] * (ta - tfa)) / mass[leaf].sum()),
+               "per_level_leaves_meanT_full_ali": per_level,
+               # mass-weighted mean |absorbed - emitted| per unit mass after the last step
+               "imbalance_last_ali": ra["imbalance"][-1], "imbalance_last_full": rf["imbalance"][-1]}
     clocks = clk.stop()
     tf, ts = T_full.cpu().numpy()[leaf], T_sub.cpu().numpy()[leaf]
     w = mass[leaf]
@@ -73,7 +94,8 @@ def run_disc_subiter(a, rt, synth, ctx, torch):
             "imbalance": rs["imbalance"],
             "rms_dT_K": float(np.sqrt(np.mean(d * d))), "mass_weighted_rms_dT_K": float(np.sqrt(np.sum(w * d * d) / w.sum())),
             "rms_T_K": float(np.sqrt(np.mean(tf * tf))), "mean_dT_K": float(d.mean()),
-            "history_full": rf["history"], "history_subiter": rs["history"], "clocks": clocks}
+            "history_full": rf["history"], "history_subiter": rs["history"], "ali_full_steps": ali,
+            "clocks": clocks}
     print(json.dumps(line))
 
 
@@ -332,3 +354,81 @@ def run_peeltab(a, rt, synth, ctx, torch):
                           [(8, 8), (8, 64), (4, 64), (2, 32)], max(1, a.steps))
     print(json.dumps({"metric": "accelerated peel-off (extinction tables) vs exact peel-off marches",
                       "workload": "peeltab", "cloud": res_c, "disc": res_d, "dtype": "f32"}))
+
+
+def run_split(a, rt, synth, ctx, torch):
+    """Table 1: noise of the 4 um field per hierarchy level with and without
+    resampling, R runs each from the same initial packages (seeds differ),
+    deviations taken from the mean of all 2R runs of a source type."""
+    cloud = synth.cloud(n_root=a.n_root, levels=a.levels, n_lambda=1, packets_per_bin=0, n_pix=16)
+    desc = cloud.tree
+    L = desc.box[0]
+    rho_unit = 70.0 * 2.8 * synth.MH_G
+    kV = 0.4 / (rho_unit * L)
+    lam = np.array([4.0])
+    optics = synth.Optics(lambda_um=lam, kappa_ext=kV * (lam / 0.55) ** -1.8, albedo=synth.albedo_law(lam),
+                          g_hg=np.array([0.5]), dnu=np.ones(1))
+    # embedded sources: point sources at the centres of the four densest root cells
+    n0 = int(np.prod(desc.root))
+    h = L / desc.root[0]
+    top = np.argsort(desc.density[:n0])[-4:]
+    stars = [synth.Source("point", bin_energy=np.array([0.25]),
+                          pos=((i % desc.root[0] + 0.5) * h, ((i // desc.root[0]) % desc.root[1] + 0.5) * h,
+                               (i // (desc.root[0] * desc.root[1]) + 0.5) * h)) for i in top]
+    ext = [synth.Source("external", bin_energy=np.array([1.0]))]
+    g = rt.Grid(ctx, desc)
+    lev = synth_levels(desc)
+    leaf = desc.refine_flags == 0
+    vol = (h * 0.5 ** lev) ** 3
+    mass = torch.as_tensor(desc.density * vol, device="cuda:0")
+    runs = max(2, a.split_runs)
+    npk = a.split_packets
+    clk = _clock_start()
+    out = {}
+    for name, src in (("external", ext), ("internal", stars)):
+        res = {}
+        J = {}
+        for N in (1, 4):
+            s1 = torch.zeros(g.n_cells, dtype=torch.float64, device="cuda:0")
+            s2 = torch.zeros_like(s1)
+            ab = torch.zeros((1, g.n_cells), dtype=torch.float64, device="cuda:0")
+            ms, nsplit, ncross = [], 0, 0
+            for r in range(runs + 1):
+                ab.zero_()
+                led = rt.rt_trace(ctx, g, src, optics, ab, seed=3000 + r, precision=32, packets_per_bin=npk,
+                                  rr_wmin=1e-4, rr_p=0.9, split_factor=N)
+                if r == 0:
+                    continue  # warm-up
+                ms.append(led["kernel_ms"])
+                nsplit += led["n_split"]
+                ncross += led["n_cross"]
+                assert led["n_split_skipped"] == 0
+                j = ab[0] / mass
+                s1 += j
+                s2 += j * j
+            res[N] = dict(trace_ms=float(np.median(ms)), n_split=nsplit // runs, n_cross=ncross // runs)
+            J[N] = (s1, s2)
+        ref = (J[1][0] + J[4][0]) / (2 * runs)
+        noise = {}
+        for N in (1, 4):
+            s1, s2 = J[N]
+            # mean over runs of (J - J_ref)^2 per cell
+            msd = (s2 - 2 * ref * s1 + runs * ref * ref) / runs
+            msd = msd.cpu().numpy()
+            noise[N] = [float(np.sqrt(np.mean(msd[leaf & (lev == l)]))) if np.any(leaf & (lev == l)) else None
+                        for l in range(int(lev.max()) + 1)]
+        top_n = max(v for N in (1, 4) for v in noise[N] if v is not None)
+        worst1 = max(v for v in noise[1] if v is not None)
+        worst4 = max(v for v in noise[4] if v is not None)
+        out[name] = {"levels": list(range(int(lev.max()) + 1)),
+                     "rms_with_resampling": [None if v is None else round(v / top_n, 4) for v in noise[4]],
+                     "rms_no_resampling": [None if v is None else round(v / top_n, 4) for v in noise[1]],
+                     "trace_ms_with": res[4]["trace_ms"], "trace_ms_without": res[1]["trace_ms"],
+                     "copies_per_run": res[4]["n_split"],
+                     "crossings_per_run_with": res[4]["n_cross"], "crossings_per_run_without": res[1]["n_cross"],
+                     # packages needed without resampling for the worst level's noise with it, in time
+                     "equal_noise_speedup": float((worst1 / worst4) ** 2 * res[1]["trace_ms"] / res[4]["trace_ms"])}
+    clocks = clk.stop()
+    print(json.dumps({"metric": "resampling at grid boundaries (Table 1): RMS noise per level, 4 um field",
+                      "workload": "split", "cells": int(g.n_cells), "runs": runs, "packages_per_run": npk,
+                      "split_factor": 4, **out, "dtype": "f32", "clocks": clocks}))

@@ -188,6 +188,22 @@ typedef struct {
   int64_t packet_offset;    /* package k of a (source, bin) draws the random stream of package
                                k + packet_offset: launches with offsets 0, n, 2n, ... of n packages
                                each are shards of one run of their total (weights aside) */
+  /* Resampling at grid boundaries (Sect. 2.3, Table 1).  The grid of a cell
+   * of level l is the octet of its parent (the root grid for l = 0); grid
+   * levels are capped at split_max_level.  A package that enters a cell dl
+   * levels deeper than its last cell is split into M = split_factor^dl
+   * packages of weight W/M at that point and direction (each copy with its
+   * own random stream, named by three words the package draws, and a fresh
+   * free path); one that enters a cell dl levels shallower survives with
+   * probability 1/M and carries M W (booked as roulette gain and loss).
+   * The roulette reference W0 follows the weight.  External-field packages
+   * start in the root grid, the others in the grid of their first cell.
+   * rt_trace / rt_peel of one job only, continuous estimator, no hit counts
+   * or level arrays; split_factor^min(split_max_level, depth) <= 256.  Copies
+   * are traced in the rounds of the tiled tracer; a split that finds no room
+   * in its record buffer is skipped (counted in n_split_skipped). */
+  int split_factor;         /* <= 1: off */
+  int split_max_level;      /* < 0: the grid's depth */
 } rt_trace_params;
 
 typedef struct {
@@ -200,6 +216,8 @@ typedef struct {
   int64_t n_launches;       /* kernel launches of the call (tracer rounds, record sorts, peel-off) */
   int32_t n_tiles;          /* tiled tracing: tiles (0: untiled) */
   int32_t n_rounds;         /* tiled tracing: rounds after the emission round */
+  uint64_t n_split;         /* resampling: copies made */
+  uint64_t n_split_skipped; /* resampling: splits skipped for lack of record space */
 } rt_ledger;
 
 /* Trace every package of every source and accumulate the absorbed energy
@@ -422,7 +440,7 @@ int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_sour
  * of it and that of the leaves below L (measured every step), or when the
  * dust emission below L has changed by flux_frac since the last full step
  * (Sect. 3.3: the flux a grid receives from its children has changed), else
- * a subiteration.  Library scratch: 6 f64 + 2 u32 arrays of n_cells and 2 f64
+ * a subiteration.  Library scratch: 7 f64 + 3 u32 arrays of n_cells and 2 f64
  * arrays of n_levels x n_cells. */
 typedef struct {
   int sub_level;           /* L: subiterations cover the subtrees below the refined cells of level L */
@@ -433,9 +451,12 @@ typedef struct {
                               fraction since the last full step (the upper levels' field from below
                               is stale); <= 0: off */
   int ali;                 /* 1: accelerated Lambda iteration with the diagonal operator (Eq. 3): each
-                              step tallies the energy dust packages leave in their own emission cell,
-                              Lambda_cc = self / E(T_emit), and T solves
-                              E(T) = (A - self) / (1 - Lambda_cc) (Lambda_cc capped at 0.999) */
+                              step tallies per cell the energy its dust packages leave in it (self),
+                              the energy they carried (emitted) and their number; Lambda_cc =
+                              self / emitted (capped at 0.999) and T solves
+                              E(T) (1 - Lambda_cc) = A - Lambda_cc emitted in the cells that sent at
+                              least ali_min_packages packages; the others take the plain step */
+  int ali_min_packages;    /* <= 1: every cell that sent a package */
 } rt_subiter_params;
 
 typedef struct {

@@ -366,7 +366,10 @@ extern "C" int rt_build_grid(rt_ctx* ctx, const rt_tree_desc* d, rt_grid** out) 
   CKG(cudaMemcpyAsync(&hmax, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   CKG(cudaStreamSynchronize(s));
   if (hbad) return finish(fail(RT_ERR_INVALID, "rt_build_grid: negative, NaN or infinite leaf density"));
-  g->rho_scale = hmax > 0.0 ? hmax : 1.0;
+  // f32 node densities span 2^64 down to 2^-126 times rho_scale: the densest
+  // leaf sits at 2^64, so leaves down to ~1e-57 of it keep a normal f32
+  // density (a near-vacuum cell keeps its absorbed energy per unit mass)
+  g->rho_scale = hmax > 0.0 ? std::ldexp(hmax, -64) : 1.0;
   CKG(build_nodes(g->rho64, g->child, n, 1.0 / g->rho_scale, g->density, g->node, s));
   CKG(cudaStreamSynchronize(s));
 #undef CKG
@@ -483,6 +486,8 @@ struct TraceArgs {
   int levels = 0;                       // subiterations: absorbed is [n_levels][n_cells] by grid level
   int confine = -1;                     // subiterations: packages leave at grids of level <= confine
   double* self_abs = nullptr;           // ALI: self-absorption tally per cell (levels only)
+  double* self_emit = nullptr;          // ALI: energy of the dust packages each cell emitted
+  unsigned int* self_cnt = nullptr;     // ALI: their number
 };
 
 // accelerated peel-off tables (Sect. 2.4)
@@ -563,6 +568,16 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     if (p->rr_wmin > 0.0 && !(p->rr_p >= 0.0 && p->rr_p < 1.0)) return fail(RT_ERR_INVALID, "job %d: rr_p must be in [0,1)", j);
     if (p->estimator == RT_EST_ANALOG && p->rr_wmin > 0.0)
       return fail(RT_ERR_INVALID, "job %d: roulette applies to the continuous-absorption estimator only", j);
+    if (p->split_factor > 1) {
+      if (n_jobs != 1) return fail(RT_ERR_INVALID, "resampling runs one job per call");
+      if (p->estimator != RT_EST_CONTINUOUS || p->hits_dev || T.levels)
+        return fail(RT_ERR_INVALID, "job %d: resampling needs the continuous estimator, no hits or level arrays", j);
+      const int depth = T.grid->n_levels - 1;
+      const int lm = p->split_max_level < 0 ? depth : std::min(p->split_max_level, depth);
+      long long m = 1;
+      for (int l = 0; l < lm && m <= 256; ++l) m *= p->split_factor;
+      if (m > 256) return fail(RT_ERR_INVALID, "job %d: split_factor^%d exceeds 256 packages per split", j, lm);
+    }
     if (T.obs) {
       const rt_observers* o = T.obs;
       if (o->n_obs < 1 || o->n_obs > RT_MAX_OBS || !o->dir || !o->up || o->nx < 1 || o->ny < 1 || !(o->fov[0] > 0) ||
@@ -676,7 +691,11 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.peel_tau_max_f = (float)p->peel_tau_max;
     J.pkt_offset = p->packet_offset;
     J.sub_conf = T.confine;
+    J.split_n = p->split_factor > 1 ? p->split_factor : 1;
+    J.split_lmax = p->split_max_level < 0 ? G->n_levels - 1 : std::min(p->split_max_level, G->n_levels - 1);
     J.self_abs = T.levels ? T.self_abs : nullptr;
+    J.self_emit = T.levels ? T.self_emit : nullptr;
+    J.self_cnt = T.levels ? T.self_cnt : nullptr;
     if (T.levels && (T.obs || nl < 1)) return fail(RT_ERR_INVALID, "job %d: level arrays exclude peel-off", j);
     if (T.tab) {
       if (T.tab->grid != G || !T.obs || T.obs->n_obs != T.tab->spec.n_obs)
@@ -874,23 +893,30 @@ static bool choose_tiles(const rt_ctx* c, const rt_grid* G, int n_jobs, TileRun*
 
 // Tiled run of one job: emit the packages chunk by chunk into records, then
 // sort by (bin, tile) and trace round after round until no package is left.
+// With resampling the record buffers also take the copies of split
+// packages: the emission chunks are a quarter of the buffer, and each
+// round may add as many copies as the buffer has room for beyond its input.
 static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool peel, int estimator, bool hits,
                      const JobDev* jobs_dev, const ItemDev* items_dev, int n_items, long long total,
                      const LaunchCfg& cfg, const PeelQueue& q, unsigned long long* counter,
                      unsigned long long* n_out, int* status, double timeout_s, cudaStream_t s,
-                     long long* launches, int* rounds, bool levels) {
-  const long long chunk = std::min<long long>(total, precision == 64 ? (1ll << 25) : (1ll << 26));
-  const size_t rb = tile_record_bytes(precision);
+                     long long* launches, int* rounds, bool levels, bool split, unsigned long long* n_split) {
+  const long long cap = precision == 64 ? (1ll << 25) : (1ll << 26);
+  const long long chunk = std::min<long long>(total, split ? cap / 4 : cap);
+  const long long rec_cap = split ? std::min(cap, std::max(16 * chunk, 1ll << 20)) : chunk;
+  const size_t rb = tile_record_bytes(precision, levels || split);
   const int n_keys = n_lambda * T.n_tiles;
-  int rc = c->tile_a.ensure(rb * (size_t)chunk);
-  if (!rc) rc = c->tile_b.ensure(rb * (size_t)chunk);
-  if (!rc) rc = c->tile_key.ensure(sizeof(uint32_t) * (size_t)chunk);
+  int rc = c->tile_a.ensure(rb * (size_t)rec_cap);
+  if (!rc) rc = c->tile_b.ensure(rb * (size_t)rec_cap);
+  if (!rc) rc = c->tile_key.ensure(sizeof(uint32_t) * (size_t)rec_cap);
   if (!rc) rc = c->tile_hist.ensure(sizeof(unsigned long long) * ((size_t)n_keys + 1));
   if (rc) return rc;
   T.out_key = reinterpret_cast<uint32_t*>(c->tile_key.p);
   T.n_out = n_out;
-  T.cap_out = chunk;
+  T.cap_out = rec_cap;
   T.status = status;
+  T.n_split = n_split;
+  T.split_cap = 0;
   for (long long c0 = 0; c0 < total; c0 += chunk) {
     const long long c1 = std::min(total, c0 + chunk);
     CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
@@ -898,8 +924,9 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
     T.in = nullptr;
     T.out = c->tile_a.p;
     T.first = c0;
+    T.split_cap = 0;
     CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, c1, cfg, q, s, 1, &T,
-                    levels));
+                    levels, split));
     *launches += 1;
     for (long long round = 0;; ++round) {
       if (round > 10000000) return fail(RT_ERR_CUDA, "tiled tracing did not finish");
@@ -909,7 +936,7 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
       if (rc) return rc;
       const long long n = (long long)c->pin_count[0];
       if (n == 0) break;
-      if (n > chunk) return fail(RT_ERR_CUDA, "tile record buffer overflow (%lld > %lld)", n, chunk);
+      if (n > rec_cap) return fail(RT_ERR_CUDA, "tile record buffer overflow (%lld > %lld)", n, rec_cap);
       CK(tile_sort(c->tile_a.p, T.out_key, n, (int)rb, n_keys, reinterpret_cast<unsigned long long*>(c->tile_hist.p),
                    c->tile_b.p, s));
       CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
@@ -917,8 +944,10 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
       T.in = c->tile_b.p;
       T.out = c->tile_a.p;
       T.first = 0;
+      T.split_cap = rec_cap - n;
+      if (split) CK(cudaMemsetAsync(n_split, 0, sizeof(unsigned long long), s));
       CK(launch_trace(precision, peel, estimator, hits, jobs_dev, items_dev, n_items, counter, n, cfg, q, s, 2, &T,
-                      levels));
+                      levels, split));
       *launches += 4;  // histogram, scan, scatter, tracer
       *rounds += 1;
     }
@@ -944,8 +973,8 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(c->table.p);
   // counter[0] packages, [1] peel-off queue length, [2] peel-off work,
-  // [3] tile records written, [4] tile status
-  CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + 5 * sizeof(unsigned long long), s));
+  // [3] tile records written, [4] tile status, [5] split copies this round
+  CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + 6 * sizeof(unsigned long long), s));
   const PeelQueue q = make_queue(c->peel_q, c->peel_q_max, peel, n_jobs, total, precision, counter + 1);
   LaunchCfg cfg;
   rc = make_cfg(c, precision, peel, launch_prm, &cfg);
@@ -956,7 +985,19 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
     return fail(RT_ERR_INVALID, "hit counting needs rt_trace with the continuous estimator");
   const double to = launch_prm->timeout_s > 0 ? launch_prm->timeout_s : 3600.0;
   TileRun tiles;
-  const bool tiled = total > 0 && n_items > 0 && choose_tiles(c, jobs[0].grid, n_jobs, &tiles);
+  bool tiled = total > 0 && n_items > 0 && choose_tiles(c, jobs[0].grid, n_jobs, &tiles);
+  const bool split = n_jobs == 1 && jobs[0].prm->split_factor > 1;
+  if (split && total > 0 && n_items > 0 && !tiled) {
+    // resampling runs in the rounds of the tiled tracer: one tile
+    const int* R = jobs[0].grid->root;
+    int tsh = 0;
+    while ((1 << tsh) < std::max(R[0], std::max(R[1], R[2]))) ++tsh;
+    memset(&tiles, 0, sizeof tiles);
+    tiles.tsh = tsh;
+    tiles.ntx = tiles.nty = 1;
+    tiles.n_tiles = 1;
+    tiled = true;
+  }
   int* tile_status = reinterpret_cast<int*>(counter + 4);
   long long n_launch = 0;
   int n_rounds = 0;
@@ -965,7 +1006,7 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
     rc = run_tiled(c, tiles, jobs[0].optics->n_lambda, precision, peel, estimator, hits,
                    reinterpret_cast<const JobDev*>(base + job_off[0]), reinterpret_cast<const ItemDev*>(base + items_off),
                    n_items, total, cfg, q, counter, counter + 3, tile_status, to, s, &n_launch, &n_rounds,
-                   jobs[0].levels != 0);
+                   jobs[0].levels != 0, split, counter + 5);
     if (rc) return rc;
   } else if (total > 0 && n_items > 0) {
     CK(launch_trace(precision, peel, estimator, hits, reinterpret_cast<const JobDev*>(base + job_off[0]),
@@ -1020,6 +1061,8 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
       o.n_launches = n_launch;
       o.n_tiles = tiled ? tiles.n_tiles : 0;
       o.n_rounds = n_rounds;
+      o.n_split = L.n_split;
+      o.n_split_skipped = L.n_split_skipped;
     }
     if (L.status) status = RT_ERR_STEP_LIMIT;
   }
@@ -1368,8 +1411,8 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   const size_t fb = sizeof(double) * (size_t)nc, hb = sizeof(unsigned int) * (size_t)nc;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   // A_star, A, T_prev, T_emit | I (levels) | I_step (levels) | hits_star, hits_step | scalars
-  // (scal[0] max dT/T, scal[1..6] level_imbalance sums) | self, A_ali (ALI)
-  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024 + 2 * al(fb));
+  // (scal[0] max dT/T, scal[1..6] level_imbalance sums) | self, A_ali, emitted, count (ALI)
+  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024 + 3 * al(fb) + al(hb));
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(ctx->lam.p);
   double* A_star = reinterpret_cast<double*>(base);
@@ -1383,6 +1426,9 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   double* scal = reinterpret_cast<double*>(base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb));
   double* self_abs = reinterpret_cast<double*>(base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
   double* A_ali = reinterpret_cast<double*>(base + 5 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
+  double* self_emit = reinterpret_cast<double*>(base + 6 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
+  unsigned int* self_cnt =
+      reinterpret_cast<unsigned int*>(base + 7 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
   CK(cudaMemsetAsync(A_star, 0, fb, s));
   CK(cudaMemsetAsync(hits_star, 0, hb, s));
   CK(cudaMemsetAsync(I, 0, fb * nlev, s));
@@ -1484,7 +1530,11 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
     TD.confine = kind == 1 ? L : -1;
     if (sp->ali) {
       CK(cudaMemsetAsync(self_abs, 0, fb, s));
+      CK(cudaMemsetAsync(self_emit, 0, fb, s));
+      CK(cudaMemsetAsync(self_cnt, 0, hb, s));
       TD.self_abs = self_abs;
+      TD.self_emit = self_emit;
+      TD.self_cnt = self_cnt;
     }
     rc = run_jobs(ctx, 1, &TD, &res->lambda.dust_ledger, s, &dp);
     if (rc && rc != RT_ERR_STEP_LIMIT) return rc;
@@ -1499,7 +1549,7 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
     CK(level_imbalance(A, T_prev, g->child, g->rho64, g->level, g->h0, tab, n_table, nc, L, scal + 1, s));
     if (sp->ali) {
       // Eq. 3: the cell's own re-absorption solved with the new temperature
-      CK(ali_field(A, self_abs, T_emit, g->child, g->rho64, g->level, g->h0, tab, n_table, nc, A_ali, s));
+      CK(ali_field(A, self_abs, self_emit, self_cnt, (unsigned)std::max(1, sp->ali_min_packages), nc, A_ali, s));
       rc = solve(A_ali);
     } else {
       rc = solve(A);
@@ -1611,7 +1661,8 @@ extern "C" int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_b
                     estimator, &b->table, &b->cdf);
   if (rc) return bail(rc);
   for (int j = 0; j < n_jobs; ++j)
-    if (args[j].prm->hits_dev) return bail(fail(RT_ERR_INVALID, "rt_batch_create: hit counting is not batched"));
+    if (args[j].prm->hits_dev || args[j].prm->split_factor > 1)
+      return bail(fail(RT_ERR_INVALID, "rt_batch_create: hit counting and resampling are not batched"));
   e = cudaStreamSynchronize(b->cap);
   if (e != cudaSuccess) return bail(fail(RT_ERR_CUDA, "rt_batch_create: %s", cudaGetErrorString(e)));
   LaunchCfg cfg;

@@ -283,29 +283,31 @@ __device__ __forceinline__ double table_emission(double T, const double* __restr
   return exp((2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + tt) * m0 + (-2 * t3 + 3 * t2) * y1 + (t3 - t2) * m1);
 }
 
+// Eq. 3 with the diagonal operator: Lambda_cc is the fraction of the energy a
+// cell's own packages carried that they left in it (self / emitted, a ratio
+// of two tallies of the same packages, so the package-count noise cancels),
+// capped at 0.999, and the field solved for is (A - Lambda_cc emitted) /
+// (1 - Lambda_cc): the same operator on both sides, = (A - self) / (1 -
+// Lambda_cc) below the cap.  Only cells that sent at least min_count
+// packages use it; the others keep A, the plain step, whose expectation
+// includes the rare packages a weakly emitting cell sends to itself.
 __global__ void ali_field_kernel(const double* __restrict__ A, const double* __restrict__ self,
-                                 const double* __restrict__ T_emit, const uint32_t* __restrict__ child,
-                                 const double* __restrict__ rho64, const uint8_t* __restrict__ level, double h0,
-                                 const double* __restrict__ table, int n_table, long long n, double* __restrict__ out) {
+                                 const double* __restrict__ emitted, const unsigned int* __restrict__ count,
+                                 unsigned int min_count, long long n, double* __restrict__ out) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   double a = A[c];
-  if (!child[c] && self[c] > 0.0) {
-    const double h = ldexp(h0, -(int)level[c]);
-    const double E = rho64[c] * h * h * h * table_emission(T_emit[c], table, n_table);
-    if (E > 0.0) {
-      const double lam = fmin(self[c] / E, 0.999);
-      a = (a - self[c]) / (1.0 - lam);
-    }
+  const double e = emitted[c];
+  if (e > 0.0 && count[c] >= min_count) {
+    const double lam = fmin(self[c] / e, 0.999);
+    a = (a - lam * e) / (1.0 - lam);
   }
   out[c] = a;
 }
 
-cudaError_t ali_field(const double* A, const double* self, const double* T_emit, const uint32_t* child,
-                      const double* rho64, const uint8_t* level, double h0, const double* table, int n_table,
-                      long long n, double* out, cudaStream_t s) {
-  ali_field_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, T_emit, child, rho64, level, h0, table,
-                                                                n_table, n, out);
+cudaError_t ali_field(const double* A, const double* self, const double* emitted, const unsigned int* count,
+                      unsigned int min_count, long long n, double* out, cudaStream_t s) {
+  ali_field_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, emitted, count, min_count, n, out);
   return cudaGetLastError();
 }
 

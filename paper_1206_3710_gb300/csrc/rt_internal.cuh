@@ -50,6 +50,7 @@ struct ObsDev {
 struct LedgerDev {
   double emitted, absorbed, escaped, rr_gain, rr_loss, killed, peeled;
   unsigned long long n_packets, n_cross, n_scatter, n_peel_cross, n_killed, n_peel_out, n_peel_deferred;
+  unsigned long long n_split, n_split_skipped;
   int status;
   int pad;
 };
@@ -79,6 +80,14 @@ struct PeelRec64 {
 // rounds; a package that crosses into another tile is written back to a
 // record for the next round, so the cells touched at any time belong to a
 // few (bin, tile) pairs whose node words and accumulators stay in L2.
+//
+// aux = mlev | (plev + 1) << 8 | (sexp + 128) << 16: the subiterations'
+// shallowest grid level, the resampling's grid level of the last cell (-1:
+// none yet) and its split exponent (the weight reference W0 is the
+// package's emitted W0 times split_factor^-sexp).  The wide records, used
+// by the subiteration and resampling tracers, add the ALI emission cell and
+// the random stream of a split copy (s3 bit 31 set; else the stream follows
+// from gi).
 struct TRec32 {
   uint32_t cx, cy, cz, meta;  // lattice coordinates at level; meta = lev | bin << 5 | job << 13
   float fx, fy, fz, W;
@@ -86,8 +95,11 @@ struct TRec32 {
   float pkt_abs;
   uint32_t next, nscat, ncross;
   unsigned long long gi;      // package index in the launch's package counter
-  uint32_t npeel, pad;        // pad: subiterations' shallowest grid level
-  uint32_t orig, pad1, pad2, pad3;  // orig: ALI, the emission cell of a dust package
+  uint32_t npeel, aux;
+};
+struct TRec32W {
+  TRec32 b;
+  uint32_t orig, s0, s1, s3;
 };
 struct TRec64 {
   uint32_t cx, cy, cz, meta;
@@ -95,7 +107,9 @@ struct TRec64 {
   double dx, dy, dz, tau;
   double pkt_abs;
   uint32_t next, nscat, ncross, npeel;
-  unsigned long long gi, pad0, pad1;  // pad0: shallowest grid level, pad1: ALI emission cell
+  unsigned long long gi;
+  uint32_t aux, orig, s0, s1, s3, pad0;
+  unsigned long long pad1;
 };
 struct TileRun {
   const void* in;               // run: records sorted by key
@@ -106,6 +120,8 @@ struct TileRun {
   long long first;              // emit: index of the first package of the chunk
   int tsh, ntx, nty, n_tiles;
   int* status;                  // bit 0: record buffer overflow
+  unsigned long long* n_split;  // resampling: copies written this round
+  long long split_cap;          // resampling: copies the record buffer has room for this round
 };
 struct PeelQueue {
   void* rec;                    // PeelRec32 or PeelRec64 [cap]
@@ -155,9 +171,16 @@ struct JobDev {
   // package that reaches a grid of level <= sub_conf leaves the run
   int sub_conf;
   int pad2;
+  // resampling at grid boundaries (Sect. 2.3): split factor (<= 1: off) and
+  // the level at which grid levels are capped
+  int split_n;
+  int split_lmax;
   // ALI (Eq. 3): energy a dust package leaves in its own emission cell, per
-  // cell (the diagonal of Lambda); NULL: not tallied
+  // cell (the diagonal of Lambda), and the energy of the dust packages each
+  // cell emitted; NULL: not tallied
   double* self_abs;
+  double* self_emit;
+  unsigned int* self_cnt;  // dust packages emitted per cell
 };
 
 // one (job, source) work item: a contiguous range of the global package counter
@@ -206,8 +229,8 @@ struct LaunchCfg {
 cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev,
                          long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s,
-                         int mode = 0, const TileRun* tiles = nullptr, bool levels = false);
-size_t tile_record_bytes(int precision);
+                         int mode = 0, const TileRun* tiles = nullptr, bool levels = false, bool split = false);
+size_t tile_record_bytes(int precision, bool wide);
 // counting sort of n records (rec_bytes each) by key (< n_keys) from in/key
 // into out; hist_dev holds n_keys + 1 counters
 cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_bytes, int n_keys,
@@ -284,9 +307,8 @@ cudaError_t sum_levels(const double* I, int n_levels, long long n, const double*
 // ALI temperature input: A' = (A - self) / (1 - self / (rho V E(T_emit))) per
 // leaf (A elsewhere), the field a cell would absorb once its own emission is
 // in equilibrium with it (Eq. 3 with a diagonal Lambda_0)
-cudaError_t ali_field(const double* A, const double* self, const double* T_emit, const uint32_t* child,
-                      const double* rho64, const uint8_t* level, double h0, const double* table, int n_table,
-                      long long n, double* out, cudaStream_t s);
+cudaError_t ali_field(const double* A, const double* self, const double* emitted, const unsigned int* count,
+                      unsigned int min_count, long long n, double* out, cudaStream_t s);
 cudaError_t level_imbalance(const double* A, const double* T, const uint32_t* child, const double* rho64,
                             const uint8_t* level, double h0, const double* table, int n_table, long long n, int L,
                             double* out, cudaStream_t s);

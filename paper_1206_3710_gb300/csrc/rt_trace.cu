@@ -327,7 +327,7 @@ __device__ __forceinline__ R inv_abs(R d) {
 // shared-memory state of the tracer
 // ------------------------------------------------------------------------
 enum { L_EMIT = 0, L_ABS, L_ESC, L_RRG, L_RRL, L_KILL, L_PEEL, L_ND };
-enum { U_PK = 0, U_CROSS, U_SCAT, U_PCROSS, U_KILL, U_POUT, U_DEFER, U_NU };
+enum { U_PK = 0, U_CROSS, U_SCAT, U_PCROSS, U_KILL, U_POUT, U_DEFER, U_SPLIT, U_SPLIT_SKIP, U_NU };
 
 // Energy ledger per warp, updated with shared-memory atomics at package
 // events (a few per package).  Two slots per warp, each tagged with the job
@@ -355,6 +355,7 @@ struct ColdState {
   uint32_t k0[256], k1[256], c0[256], c1[256], c3[256], next[256];
   long long log_index[256], pix[256], gi[256];
   uint32_t orig[256];  // ALI: emission cell of a dust package (~0u: none)
+  int sexp[256];       // resampling: split exponent of the package (W0 = emitted W0 / N^sexp)
   R W0[256], pw[256], gpar[256];
   int bin[256], nscat[256], obs_i[256], job[256];
   // scattering point and incoming direction, saved during the peel-off
@@ -391,6 +392,8 @@ __device__ __forceinline__ R draw(ColdState<R>& C, int t) {
 // the ledger's sums and counts are contiguous, in the order of L_* and U_*
 static_assert(offsetof(LedgerDev, peeled) == offsetof(LedgerDev, emitted) + 8 * L_PEEL, "ledger layout");
 static_assert(offsetof(LedgerDev, n_peel_deferred) == offsetof(LedgerDev, n_packets) + 8 * U_DEFER, "ledger layout");
+static_assert(offsetof(LedgerDev, n_split_skipped) == offsetof(LedgerDev, n_packets) + 8 * U_SPLIT_SKIP,
+              "ledger layout");
 __device__ __forceinline__ double* ledger_d(LedgerDev* L, int i) { return &L->emitted + i; }
 __device__ __forceinline__ unsigned long long* ledger_u(LedgerDev* L, int i) { return &L->n_packets + i; }
 
@@ -582,7 +585,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 enum { ST_DEAD = 0, ST_TRACE = 1, ST_PEEL = 2, ST_DONE = 3 };
-enum { EV_NONE = 0, EV_IDLE, EV_INTERACT, EV_ESCAPE, EV_CUT, EV_KILL, EV_DEGEN, EV_TILE };
+enum { EV_NONE = 0, EV_IDLE, EV_INTERACT, EV_ESCAPE, EV_CUT, EV_KILL, EV_DEGEN, EV_TILE, EV_SPLIT };
 
 // ------------------------------------------------------------------------
 // deferred peel-off records
@@ -675,25 +678,63 @@ __device__ __forceinline__ uint32_t tile_of(const Geo<R>& g, const TileRun& T) {
   return (g.cx >> s) + (uint32_t)T.ntx * ((g.cy >> s) + (uint32_t)T.nty * (g.cz >> s));
 }
 
-template <typename R>
+// The FP32 tracer writes the narrow record unless it tracks levels or
+// resamples; the FP64 record always has room for everything.
+template <typename R, bool WIDE>
 struct TileIO;
 template <>
-struct TileIO<float> {
+struct TileIO<float, false> {
   typedef TRec32 Rec;
+  static __device__ __forceinline__ TRec32& b(Rec& r) { return r; }
+  static __device__ __forceinline__ const TRec32& b(const Rec& r) { return r; }
+  static __device__ __forceinline__ void set_ext(Rec&, uint32_t, uint32_t, uint32_t, uint32_t) {}
+  static __device__ __forceinline__ void ext(const Rec&, uint32_t& o, uint32_t& s0, uint32_t& s1, uint32_t& s3) {
+    o = 0xFFFFFFFFu; s0 = s1 = s3 = 0u;
+  }
 };
 template <>
-struct TileIO<double> {
-  typedef TRec64 Rec;
+struct TileIO<float, true> {
+  typedef TRec32W Rec;
+  static __device__ __forceinline__ TRec32& b(Rec& r) { return r.b; }
+  static __device__ __forceinline__ const TRec32& b(const Rec& r) { return r.b; }
+  static __device__ __forceinline__ void set_ext(Rec& r, uint32_t o, uint32_t s0, uint32_t s1, uint32_t s3) {
+    r.orig = o; r.s0 = s0; r.s1 = s1; r.s3 = s3;
+  }
+  static __device__ __forceinline__ void ext(const Rec& r, uint32_t& o, uint32_t& s0, uint32_t& s1, uint32_t& s3) {
+    o = r.orig; s0 = r.s0; s1 = r.s1; s3 = r.s3;
+  }
 };
-static_assert(sizeof(TRec32) == 96 && sizeof(TRec64) == 128, "tile record layout");
-__device__ __forceinline__ void tile_set_orig(TRec32& r, uint32_t o) { r.orig = o; }
-__device__ __forceinline__ void tile_set_orig(TRec64& r, uint32_t o) { r.pad1 = o; }
-__device__ __forceinline__ uint32_t tile_orig(const TRec32& r) { return r.orig; }
-__device__ __forceinline__ uint32_t tile_orig(const TRec64& r) { return (uint32_t)r.pad1; }
-__device__ __forceinline__ void tile_set_mlev(TRec32& r, int m) { r.pad = (uint32_t)m; }
-__device__ __forceinline__ void tile_set_mlev(TRec64& r, int m) { r.pad0 = (unsigned long long)m; }
-__device__ __forceinline__ int tile_mlev(const TRec32& r) { return (int)r.pad; }
-__device__ __forceinline__ int tile_mlev(const TRec64& r) { return (int)r.pad0; }
+template <bool WIDE>
+struct TileIO<double, WIDE> {
+  typedef TRec64 Rec;
+  static __device__ __forceinline__ TRec64& b(Rec& r) { return r; }
+  static __device__ __forceinline__ const TRec64& b(const Rec& r) { return r; }
+  static __device__ __forceinline__ void set_ext(Rec& r, uint32_t o, uint32_t s0, uint32_t s1, uint32_t s3) {
+    r.orig = o; r.s0 = s0; r.s1 = s1; r.s3 = s3;
+  }
+  static __device__ __forceinline__ void ext(const Rec& r, uint32_t& o, uint32_t& s0, uint32_t& s1, uint32_t& s3) {
+    o = r.orig; s0 = r.s0; s1 = r.s1; s3 = r.s3;
+  }
+};
+static_assert(sizeof(TRec32) == 80 && sizeof(TRec32W) == 96 && sizeof(TRec64) == 144, "tile record layout");
+__device__ __forceinline__ uint32_t pack_aux(int mlev, int plev, int sexp) {
+  return (uint32_t)mlev | ((uint32_t)(plev + 1) << 8) | ((uint32_t)(sexp + 128) << 16);
+}
+__device__ __forceinline__ int aux_mlev(uint32_t a) { return (int)(a & 255u); }
+__device__ __forceinline__ int aux_plev(uint32_t a) { return (int)((a >> 8) & 255u) - 1; }
+__device__ __forceinline__ int aux_sexp(uint32_t a) { return (int)((a >> 16) & 255u) - 128; }
+
+// N^e for the resampling factor (N^e <= 256 is checked on the host)
+__device__ __forceinline__ uint32_t ipow_u(uint32_t n, int e) {
+  uint32_t r = 1u;
+  for (int i = 0; i < e; ++i) r *= n;
+  return r;
+}
+// w N^-e for either sign of e
+template <typename R>
+__device__ __forceinline__ R scale_pow(R w, uint32_t n, int e) {
+  return e >= 0 ? w / (R)ipow_u(n, e) : w * (R)ipow_u(n, -e);
+}
 
 // Subiterations: after a crossing that restarted the cursor at the root (a
 // move out of the parent octet, or between root cells), the shallowest grid
@@ -718,14 +759,15 @@ struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? RT_FP32_MIN_BLOCKS : 2;
 };
 
-template <typename R, bool PEEL, int EST, bool HITS, int MODE, bool LEVELS = false>
+template <typename R, bool PEEL, int EST, bool HITS, int MODE, bool LEVELS = false, bool SPLIT = false>
 __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const JobDev* __restrict__ jobs,
                                                                          const ItemDev* __restrict__ items,
                                                                          int n_items,
                                                                          unsigned long long* __restrict__ counter,
                                                                          long long total, int refill_thr,
                                                                          PeelQueue Q, TileRun T) {
-  typedef typename TileIO<R>::Rec TRec;
+  typedef TileIO<R, LEVELS || SPLIT> IO;
+  typedef typename IO::Rec TRec;
   const unsigned FULL = 0xFFFFFFFFu;
   __shared__ WarpLedger SL;
   __shared__ ColdState<R> C;
@@ -758,6 +800,8 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   uint32_t tile_cur = 0u;  // tiled rounds: the tile this lane traces in
   int mlev = 0;            // subiterations: shallowest grid level reached
   double* selfb = nullptr; // ALI: self-absorption tally (LEVELS kernels)
+  int plev = -1;           // resampling: grid level of the last cell (capped), -1: none yet
+  int splt_lmax = 0;       // resampling: the cap of the grid levels
 
   // after a scattering (and its peel-off): new direction from the phase
   // function, Russian roulette when the weight is low, next free path.
@@ -792,7 +836,8 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   auto tile_push = [&]() {
     const unsigned long long slot = atomicAdd(T.n_out, 1ull);
     if (slot < (unsigned long long)T.cap_out) {
-      TRec r;
+      TRec rr;
+      auto& r = IO::b(rr);
       r.cx = g.cx; r.cy = g.cy; r.cz = g.cz;
       r.meta = peel_meta(g.lev, C.bin[t], C.job[t]);
       r.fx = g.fx; r.fy = g.fy; r.fz = g.fz; r.W = W;
@@ -800,9 +845,10 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       r.pkt_abs = pkt_abs;
       r.next = C.next[t]; r.nscat = (uint32_t)C.nscat[t]; r.ncross = ncross; r.npeel = npeel;
       r.gi = (unsigned long long)C.gi[t];
-      tile_set_mlev(r, mlev);
-      tile_set_orig(r, C.orig[t]);
-      static_cast<TRec*>(T.out)[slot] = r;
+      r.aux = pack_aux(mlev, plev, SPLIT ? C.sexp[t] : 0);
+      const bool copy = SPLIT && (C.c3[t] & 0x80000000u);
+      IO::set_ext(rr, C.orig[t], C.c0[t], C.c1[t], copy ? C.c3[t] : 0u);
+      static_cast<TRec*>(T.out)[slot] = rr;
       T.out_key[slot] = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
     } else {
       atomicOr(T.status, 1);
@@ -824,7 +870,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       const TRec* rec = nullptr;
       if (MODE == 2 && st == ST_DEAD && slot < total) {
         rec = static_cast<const TRec*>(T.in) + slot;
-        gi = (long long)rec->gi;
+        gi = (long long)IO::b(*rec).gi;
       }
       int lo = -1;
       if (st == ST_DEAD && (MODE == 2 ? rec != nullptr : gi < total)) {
@@ -844,7 +890,10 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           st = ST_DONE;
         } else if (MODE == 2) {
           // ---------------------------------- resume a package from its record
-          const TRec r = *rec;
+          const TRec rr = *rec;
+          const auto& r = IO::b(rr);
+          uint32_t x_orig, s0, s1, s3;
+          IO::ext(rr, x_orig, s0, s1, s3);
           const ItemDev& I = items[lo];
           const int job = I.job;
           const JobDev& J = jobs[job];
@@ -867,6 +916,13 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           C.c0[t] = (uint32_t)k;
           C.c1[t] = (uint32_t)(k >> 32);
           C.c3[t] = (I.src_index << 16) | (uint32_t)bin;
+          if (SPLIT && (s3 & 0x80000000u)) {
+            // a copy from a split: its own stream, no package log
+            C.c0[t] = s0;
+            C.c1[t] = s1;
+            C.c3[t] = s3;
+            C.log_index[t] = -1;
+          }
           C.next[t] = r.next;
           C.rtag[t] = 0xFFFFFFFFu;
           const BinDev& B = J.bins[bin];
@@ -874,14 +930,20 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           alb = Num<R>::alb(B);
           C.gpar[t] = Num<R>::gg(B);
           if (LEVELS) {
-            mlev = tile_mlev(r);
-            C.orig[t] = tile_orig(r);
+            mlev = aux_mlev(r.aux);
+            C.orig[t] = x_orig;
             selfb = J.self_abs;
           }
           absb = J.absorbed ? J.absorbed + (long long)(LEVELS ? mlev : (J.abs_bins > 1 ? bin : 0)) * J.n_cells
                             : nullptr;
           if (HITS) hitp = J.hits;
           C.W0[t] = Num<R>::w0(I, bin);
+          if (SPLIT) {
+            plev = aux_plev(r.aux);
+            C.sexp[t] = aux_sexp(r.aux);
+            splt_lmax = J.split_lmax;
+            C.W0[t] = scale_pow(C.W0[t], (uint32_t)J.split_n, C.sexp[t]);
+          }
           C.nscat[t] = (int)r.nscat;
           W = r.W;
           tau = r.tau;
@@ -944,6 +1006,12 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           const R W0 = Num<R>::w0(I, bin);
           C.W0[t] = W0;
           W = W0;
+          if (SPLIT) {
+            // the external field enters through the root grid (Sect. 2.2)
+            plev = I.kind == RT_SRC_EXTERNAL ? 0 : -1;
+            C.sexp[t] = 0;
+            splt_lmax = J.split_lmax;
+          }
           pkt_abs = R(0);
           ncross = npeel = 0u;
           C.nscat[t] = 0;
@@ -1035,6 +1103,10 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
             absb = J.absorbed ? J.absorbed + (long long)mlev * J.n_cells : nullptr;
             C.orig[t] = I.kind == RT_SRC_DUST ? cur.pending : 0xFFFFFFFFu;
             selfb = J.self_abs;
+            if (selfb && J.self_emit && I.kind == RT_SRC_DUST) {
+              atomicAdd(J.self_emit + cur.pending, widen(W));
+              atomicAdd(J.self_cnt + cur.pending, 1u);
+            }
           }
           if (inside) {
             st = ST_TRACE;
@@ -1081,10 +1153,17 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           const bool tr = st == ST_TRACE;
           int a;
           const R tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
+          int lvs = 0;
+          if (SPLIT && tr) {
+            lvs = min(g.lev, splt_lmax);
+            if (plev < 0) plev = lvs;
+          }
           if (tr && ncross >= step_limit) {
             ev = EV_KILL;
           } else if (a < 0) {
             ev = EV_DEGEN;  // cannot happen for |d| = 1
+          } else if (SPLIT && tr && lvs != plev) {
+            ev = EV_SPLIT;  // entered a grid of another level: resample first
           } else {
             const R kl = kext * g.rho * Num<R>::pow2m(g.lev);  // extinction per local unit
             bool inside_event = false;
@@ -1176,6 +1255,71 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       }
     } else if (MODE == 2 && ev == EV_TILE) {
       tile_push();
+    } else if (SPLIT && ev == EV_SPLIT) {
+      // Resampling at a grid boundary (Sect. 2.3).  Entering a grid dl
+      // levels deeper: M = N^dl packages of weight W/M at this point and
+      // direction; the copies are written as records for the next round,
+      // each with the stream named by three words drawn here and the copy
+      // index, and a free path from that stream.  Leaving for a grid dl
+      // levels shallower: survive with probability 1/M (integer test on one
+      // word), carrying M W.  W0 follows the weight.
+      const JobDev& J = jobs[job];
+      const int lv = min(g.lev, splt_lmax);
+      const int dl = lv - plev;
+      plev = lv;
+      if (dl > 0) {
+        const uint32_t M = ipow_u((uint32_t)J.split_n, dl);
+        const uint32_t w0 = draw_u32(C, t), w1 = draw_u32(C, t), w2 = draw_u32(C, t);
+        const unsigned long long need = (unsigned long long)(M - 1u);
+        const unsigned long long base = atomicAdd(T.n_split, need);
+        if (base + need <= (unsigned long long)T.split_cap) {
+          W = W / (R)M;
+          C.W0[t] = C.W0[t] / (R)M;
+          C.sexp[t] += dl;
+          const unsigned long long slot0 = atomicAdd(T.n_out, need);
+          const uint32_t key = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
+          for (uint32_t kk = 1u; kk < M; ++kk) {
+            const unsigned long long slot = slot0 + kk - 1u;
+            if (slot >= (unsigned long long)T.cap_out) {
+              atomicOr(T.status, 1);
+              break;
+            }
+            const uint32_t s3 = 0x80000000u | (w2 & 0x7FFFFF00u) | kk;
+            const uint4 blk = philox4x32_10(make_uint4(w0, w1, 0u, s3), C.k0[t], C.k1[t]);
+            TRec rr;
+            auto& r = IO::b(rr);
+            r.cx = g.cx; r.cy = g.cy; r.cz = g.cz;
+            r.meta = peel_meta(g.lev, C.bin[t], job);
+            r.fx = g.fx; r.fy = g.fy; r.fz = g.fz; r.W = W;
+            r.dx = dx; r.dy = dy; r.dz = dz;
+            r.tau = -Num<R>::log_(Num<R>::uni(blk.x));
+            r.pkt_abs = R(0);
+            r.next = 1u; r.nscat = 0u; r.ncross = 0u; r.npeel = 0u;
+            r.gi = (unsigned long long)C.gi[t];
+            r.aux = pack_aux(mlev, lv, C.sexp[t]);
+            IO::set_ext(rr, C.orig[t], w0, w1, s3);
+            static_cast<TRec*>(T.out)[slot] = rr;
+            T.out_key[slot] = key;
+          }
+          book_u(SL, jobs, job, wid, U_SPLIT, need);
+        } else {
+          book_u(SL, jobs, job, wid, U_SPLIT_SKIP, 1ull);  // no room: the package goes on whole
+        }
+      } else {
+        const uint32_t M = ipow_u((uint32_t)J.split_n, -dl);
+        const uint32_t u = draw_u32(C, t);
+        if ((unsigned long long)u * M < (1ull << 32)) {
+          const R Wn = W * (R)M;
+          book_d(SL, jobs, job, wid, L_RRG, Wn - W);
+          W = Wn;
+          C.W0[t] = C.W0[t] * (R)M;
+          C.sexp[t] += dl;
+        } else {
+          book_d(SL, jobs, job, wid, L_RRL, W);
+          W = R(0);
+          fate = 1;
+        }
+      }
     } else {  // EV_INTERACT: absorption (analog) or scattering in this cell
       bool scatter = true;
       if (EST == RT_EST_ANALOG) {
@@ -1551,6 +1695,20 @@ static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_item
   return cudaGetLastError();
 }
 
+// resampling tracers: tiled modes only, continuous estimator, no hit counts
+template <typename R, bool PEEL>
+static cudaError_t launch_split(const JobDev* jobs, const ItemDev* items, int n_items, unsigned long long* counter,
+                                long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode,
+                                const TileRun* tr) {
+  if (mode == 1)
+    trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 1, false, true>
+        <<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill, q, *tr);
+  else
+    trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2, false, true>
+        <<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill, q, *tr);
+  return cudaGetLastError();
+}
+
 template <typename R, int EST>
 static cudaError_t launch_pe(bool peel, const JobDev* jobs, const ItemDev* items, int n_items,
                              unsigned long long* counter, long long total, const LaunchCfg& cfg,
@@ -1564,9 +1722,17 @@ static cudaError_t launch_pe(bool peel, const JobDev* jobs, const ItemDev* items
 cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, const JobDev* jobs_dev,
                          const ItemDev* items_dev, int n_items, unsigned long long* counter_dev, long long total,
                          const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode, const TileRun* tr,
-                         bool levels) {
+                         bool levels, bool split) {
   const bool an = estimator == RT_EST_ANALOG;
   if ((mode == 1 || mode == 2) && !tr) return cudaErrorInvalidValue;
+  if (split) {
+    if (levels || hits || an || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
+    if (precision == 64)
+      return peel ? launch_split<double, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s, mode, tr)
+                  : launch_split<double, false>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s, mode, tr);
+    return peel ? launch_split<float, true>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s, mode, tr)
+                : launch_split<float, false>(jobs_dev, items_dev, n_items, counter_dev, total, cfg, q, s, mode, tr);
+  }
   if (levels) {
     // subiterations: dust traces with the continuous estimator, no peel-off
     if (peel || an) return cudaErrorInvalidValue;
@@ -1599,7 +1765,9 @@ cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, con
                                                   mode, tr);
 }
 
-size_t tile_record_bytes(int precision) { return precision == 64 ? sizeof(TRec64) : sizeof(TRec32); }
+size_t tile_record_bytes(int precision, bool wide) {
+  return precision == 64 ? sizeof(TRec64) : (wide ? sizeof(TRec32W) : sizeof(TRec32));
+}
 
 // ------------------------------------------------------------------------
 // counting sort of tile records by key

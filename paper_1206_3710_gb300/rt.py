@@ -71,12 +71,13 @@ class rt_trace_params(C.Structure):
                 ("peel_tau_max", C.c_double), ("per_lambda", C.c_int), ("packets_per_bin", C.c_int64),
                 ("packets", C.POINTER(C.c_int64)), ("packets_total", C.c_int64), ("packet_log_dev", C.c_void_p),
                 ("timeout_s", C.c_double), ("block_size", C.c_int), ("refill_threshold", C.c_int),
-                ("blocks_per_sm", C.c_int), ("hits_dev", C.c_void_p), ("packet_offset", C.c_int64)]
+                ("blocks_per_sm", C.c_int), ("hits_dev", C.c_void_p), ("packet_offset", C.c_int64),
+                ("split_factor", C.c_int), ("split_max_level", C.c_int)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
                  "n_scatter", "n_peel_cross", "n_killed", "n_peel_out", "n_peel_deferred", "status", "kernel_ms",
-                 "peel_ms", "n_launches", "n_tiles", "n_rounds"]
+                 "peel_ms", "n_launches", "n_tiles", "n_rounds", "n_split", "n_split_skipped"]
 
 
 class rt_ledger(C.Structure):
@@ -85,7 +86,8 @@ class rt_ledger(C.Structure):
                 ("n_packets", C.c_uint64), ("n_cross", C.c_uint64), ("n_scatter", C.c_uint64),
                 ("n_peel_cross", C.c_uint64), ("n_killed", C.c_uint64), ("n_peel_out", C.c_uint64),
                 ("n_peel_deferred", C.c_uint64), ("status", C.c_int), ("kernel_ms", C.c_double),
-                ("peel_ms", C.c_double), ("n_launches", C.c_int64), ("n_tiles", C.c_int32), ("n_rounds", C.c_int32)]
+                ("peel_ms", C.c_double), ("n_launches", C.c_int64), ("n_tiles", C.c_int32), ("n_rounds", C.c_int32),
+                ("n_split", C.c_uint64), ("n_split_skipped", C.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n in LEDGER_FIELDS}
@@ -103,7 +105,8 @@ class rt_lambda_result(C.Structure):
 
 class rt_subiter_params(C.Structure):
     _fields_ = [("sub_level", C.c_int), ("n_steps", C.c_int), ("schedule", C.POINTER(C.c_int)),
-                ("select_frac", C.c_double), ("flux_frac", C.c_double), ("ali", C.c_int)]
+                ("select_frac", C.c_double), ("flux_frac", C.c_double), ("ali", C.c_int),
+                ("ali_min_packages", C.c_int)]
 
 
 class rt_subiter_result(C.Structure):
@@ -349,7 +352,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
                 peel_tau_max: float = 0.0, per_lambda: bool = True, packets_per_bin: int = 0, packets=None,
                 packets_total: int = 0, packet_log=None, timeout_s: float = 0.0, block_size: int = 0,
                 refill_threshold: int = 0, blocks_per_sm: int = 0, hits=None,
-                packet_offset: int = 0) -> rt_trace_params:
+                packet_offset: int = 0, split_factor: int = 1, split_max_level: int = -1) -> rt_trace_params:
     p = rt_trace_params()
     p.seed, p.job, p.iter = int(seed), int(job), int(iter_)
     p.precision, p.estimator = int(precision), int(estimator)
@@ -363,6 +366,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
     p.block_size, p.refill_threshold, p.blocks_per_sm = int(block_size), int(refill_threshold), int(blocks_per_sm)
     p.hits_dev = _ptr(hits)
     p.packet_offset = int(packet_offset)
+    p.split_factor, p.split_max_level = int(split_factor), int(split_max_level)
     return p
 
 
@@ -497,7 +501,8 @@ def rt_lambda_iterate(ctx: Context, grid: Grid, sources, optics, T_out, *, max_i
 
 def rt_lambda_subiterate(ctx: Context, grid: Grid, sources, optics, T_out, *, sub_level: int, schedule=None,
                          max_iter: int = 30, select_frac: float = 0.25, flux_frac: float = 0.05,
-                         ali: bool = False, tol: float = 0.0, min_hits: float = 1000.0,
+                         ali: bool = False, ali_min_packages: int = 100, tol: float = 0.0,
+                         min_hits: float = 1000.0,
                          dust_packets_total: int = 0, dust_packets_per_bin: int = 0, T_min: float = 2.7,
                          T_max: float = 3000.0, stream=None, **params) -> dict:
     """Lambda iteration with subiterations (Sect. 3.2, App. B).  ``schedule``:
@@ -512,7 +517,8 @@ def rt_lambda_subiterate(ctx: Context, grid: Grid, sources, optics, T_out, *, su
     lp = rt_lambda_params(max_iter=int(max_iter), tol=float(tol), min_hits=float(min_hits),
                           dust_packets_total=int(dust_packets_total), dust_packets_per_bin=int(dust_packets_per_bin))
     sp = rt_subiter_params(sub_level=int(sub_level), n_steps=0, select_frac=float(select_frac),
-                           flux_frac=float(flux_frac), ali=int(bool(ali)))
+                           flux_frac=float(flux_frac), ali=int(bool(ali)),
+                           ali_min_packages=int(ali_min_packages))
     if schedule is not None:
         kinds = np.array([{"full": 0, "sub": 1}[k] for k in schedule], dtype=np.int32)
         sp.n_steps = len(kinds)
