@@ -72,7 +72,7 @@ class _Params(C.Structure):
                 ("n_threads", C.c_int), ("packet_offset", C.c_int64), ("peel_block", C.c_int),
                 ("peel_tiles", C.c_int), ("per_level", C.c_int), ("confine_level", C.c_int),
                 ("self_absorbed", C.c_void_p), ("self_emitted", C.c_void_p), ("self_count", C.c_void_p),
-                ("split_factor", C.c_int), ("split_max_level", C.c_int)]
+                ("split_factor", C.c_int), ("split_max_level", C.c_int), ("poly_group", C.c_int)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled",
@@ -257,7 +257,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
           observers=None, n_threads: int = 1, validation: bool = False, record: bool = False,
           emission: Optional[np.ndarray] = None, packet_offset: int = 0, peel_block: int = 0,
           peel_tiles: int = 0, per_level: bool = False, confine_level: int = -1, self_absorbed=None,
-          self_emitted=None, self_count=None, split_factor: int = 1, split_max_level: int = 255):
+          self_emitted=None, self_count=None, split_factor: int = 1, split_max_level: int = 255,
+          poly_group: int = 1):
     """Run the oracle tracer.
 
     ``sources`` are ``synth.Source``-like objects (kind "point", "external",
@@ -275,6 +276,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
         pk = np.full((ns, nl), int(pk), np.int64)
     elif pk.ndim == 1:
         pk = np.tile(pk, (ns, 1))
+    if poly_group > 1:  # packages are counted per group, at its first bin
+        pk = np.where((np.arange(nl) % poly_group == 0)[None, :], pk, 0)
     kinds = {"point": SRC_POINT, "external": SRC_EXTERNAL, "dust": SRC_DUST, "beam": SRC_BEAM}
     src_arr = (_Source * ns)()
     for i, s in enumerate(sources):
@@ -296,7 +299,7 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
                   self_absorbed=None if self_absorbed is None else self_absorbed.ctypes.data,
                   self_emitted=None if self_emitted is None else self_emitted.ctypes.data,
                   self_count=None if self_count is None else self_count.ctypes.data,
-                  split_factor=int(split_factor), split_max_level=int(split_max_level))
+                  split_factor=int(split_factor), split_max_level=int(split_max_level), poly_group=int(poly_group))
     ob = _observers(observers, keep)
     bins = tree.desc.n_levels if per_level else (nl if per_lambda else 1)
     nc = tree.n_cells

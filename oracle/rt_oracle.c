@@ -804,6 +804,208 @@ static int follow(trace_worker* w, orc_path* P, int64_t p, int bin, double kext_
   return fate;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Polychromatic packages (Sect. 2.3, after Jonsson 2006)                     */
+/* ------------------------------------------------------------------------ */
+/* A package carries weights W_j for the bins j of its group; free paths and
+ * scattering directions are drawn for the reference bin r.  Each W_j
+ * carries the likelihood ratio of that path for its own bin: along a
+ * segment of length s with no scattering the ratio of the no-scattering
+ * probabilities, e^{-(ks_j - ks_r) rho s}; at a scattering the ratio of the
+ * scattering coefficients ks_j / ks_r and of the phase functions
+ * p_j(mu) / p_r(mu).  Absorption stays continuous: over a segment the bin-j
+ * deposit is the integral of W_j(t) ka_j rho dt with
+ * W_j(t) = W_j e^{-(ka_j + ks_j - ks_r) rho t}, i.e.
+ *     W_j ta_j (1 - e^{-x_j}) / x_j,   x_j = (ka_j + ks_j - ks_r) rho s,
+ * and W_j <- W_j e^{-x_j}.  For j = r this is the monochromatic package. */
+static double phi1(double x) { return x != 0.0 ? -expm1(-x) / x : 1.0; }
+
+#define ORC_POLY_MAX 8
+
+static void peel_poly(trace_worker* w, const double x[3], const double din[3], const double* W, int first,
+                      int size) {
+  const orc_observers* obs = w->job->obs;
+  const orc_tree* t = w->job->t;
+  const orc_optics* op = w->job->op;
+  for (int o = 0; o < obs->n_obs; ++o) {
+    const double* k = &obs->dir[3 * o];
+    double mu = din[0] * k[0] + din[1] * k[1] + din[2] * k[2];
+    const double* up = &obs->up[3 * o];
+    double ex[3] = {up[1] * k[2] - up[2] * k[1], up[2] * k[0] - up[0] * k[2], up[0] * k[1] - up[1] * k[0]};
+    double nn = sqrt(ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2]);
+    ex[0] /= nn; ex[1] /= nn; ex[2] /= nn;
+    double ey[3] = {k[1] * ex[2] - k[2] * ex[1], k[2] * ex[0] - k[0] * ex[2], k[0] * ex[1] - k[1] * ex[0]};
+    double r[3];
+    for (int a = 0; a < 3; ++a) r[a] = x[a] * t->h0 - 0.5 * t->box[a];
+    double u = r[0] * ex[0] + r[1] * ex[1] + r[2] * ex[2];
+    double v = r[0] * ey[0] + r[1] * ey[1] + r[2] * ey[2];
+    double fx = floor(u / (obs->fov[0] / obs->nx) + 0.5 * obs->nx);
+    double fy = floor(v / (obs->fov[1] / obs->ny) + 0.5 * obs->ny);
+    if (fx < 0 || fy < 0 || fx >= obs->nx || fy >= obs->ny) {
+      w->led.n_peel_out += 1;
+      continue;
+    }
+    /* column density to the border (density x root-cell units): one march for all bins */
+    double xx[3] = {x[0], x[1], x[2]};
+    double col = 0.0;
+    const orc_node* n = locate(t, xx, k);
+    while (n) {
+      int a;
+      double s = exit_dist(n, xx, k, &a);
+      col += n->rho * s;
+      if (s > 0) w->led.n_peel_cross += 1;
+      move_to_face(n, xx, k, s, a);
+      n = locate(t, xx, k);
+    }
+    for (int j = 0; j < size; ++j) {
+      const int b = first + j;
+      double c = W[j] * orc_hg_phase(op->g_hg[b], mu) * exp(-op->kappa_ext[b] * t->h0 * col);
+      int ob = w->job->bins > 1 ? b : 0;
+      int64_t slot = (((int64_t)o * w->job->bins + ob) * obs->ny + (int64_t)fy) * obs->nx + (int64_t)fx;
+      if (w->job->shared_atomic) atomic_add_double(&w->job->images_shared[slot], c);
+      else w->images[slot] += c;
+      w->led.peeled += c;
+    }
+  }
+}
+
+/* One polychromatic package of the group that starts at bin `first`. */
+static void trace_poly(trace_worker* w, int64_t p, int si, int first, int64_t k, int64_t npk) {
+  trace_job* J = w->job;
+  const orc_tree* t = J->t;
+  const orc_params* prm = J->prm;
+  const orc_optics* op = J->op;
+  const int nl = op->n_lambda;
+  const int size = prm->poly_group < nl - first ? prm->poly_group : nl - first;
+  const int rb = first + (size - 1) / 2;
+  const orc_source* S = &J->src[si];
+  rstream rs = {prm->seed, (uint64_t)(k + prm->packet_offset), 0, prm->job, prm->iter,
+                ((uint32_t)si << 16) | (uint32_t)first};
+  const int64_t nc = t->n_cells;
+  double W[ORC_POLY_MAX], W0[ORC_POLY_MAX], ka[ORC_POLY_MAX], ks[ORC_POLY_MAX];
+  double W0sum = 0.0;
+  for (int j = 0; j < size; ++j) {
+    const int b = first + j;
+    W0[j] = S->bin_energy[b] / (double)npk;
+    W[j] = W0[j];
+    W0sum += W0[j];
+    ka[j] = (1.0 - op->albedo[b]) * op->kappa_ext[b] * t->h0;
+    ks[j] = op->albedo[b] * op->kappa_ext[b] * t->h0;
+  }
+  const double ksr = op->albedo[rb] * op->kappa_ext[rb] * t->h0, gr = op->g_hg[rb];
+  double x[3], d[3];
+  if (S->kind == ORC_SRC_POINT) {
+    for (int a = 0; a < 3; ++a) x[a] = S->pos[a] / t->h0;
+    double u1 = uni(&rs), u2 = uni(&rs);
+    iso_dir(u1, u2, d);
+  } else if (S->kind == ORC_SRC_BEAM) {
+    double nn = sqrt(S->dir[0] * S->dir[0] + S->dir[1] * S->dir[1] + S->dir[2] * S->dir[2]);
+    for (int a = 0; a < 3; ++a) { x[a] = S->pos[a] / t->h0; d[a] = S->dir[a] / nn; }
+  } else {
+    double area[3] = {t->box[1] * t->box[2], t->box[0] * t->box[2], t->box[0] * t->box[1]};
+    double tot = 2.0 * (area[0] + area[1] + area[2]);
+    double u0 = uni(&rs) * tot, cum = 0.0;
+    int face = 5;
+    for (int f = 0; f < 6; ++f) {
+      cum += area[f / 2];
+      if (u0 < cum) { face = f; break; }
+    }
+    int a = face / 2, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    if (a1 > a2) { int tmp = a1; a1 = a2; a2 = tmp; }
+    double u1 = uni(&rs), u2 = uni(&rs), u3 = uni(&rs), u4 = uni(&rs);
+    x[a] = (face & 1) ? (double)t->root[a] : 0.0;
+    x[a1] = u1 * t->root[a1];
+    x[a2] = u2 * t->root[a2];
+    double mu = sqrt(u3), st = sqrt(fmax(0.0, 1.0 - mu * mu)), phi = 2.0 * ORC_PI * u4;
+    d[a] = (face & 1) ? -mu : mu;
+    d[a1] = st * cos(phi);
+    d[a2] = st * sin(phi);
+  }
+  w->led.emitted += W0sum;
+  w->led.n_packets += 1;
+  double tau = -log(uni(&rs));
+  double nscat = 0, ncross = 0;
+  int fate = 0;
+  int64_t steps = 0;
+  for (;;) {
+    const orc_node* n = locate(t, x, d);
+    if (!n) {
+      for (int j = 0; j < size; ++j) w->led.escaped += W[j];
+      fate = 0;
+      break;
+    }
+    if (prm->step_limit > 0 && steps >= prm->step_limit) {
+      for (int j = 0; j < size; ++j) { w->led.killed += W[j]; W[j] = 0; }
+      w->led.n_killed += 1;
+      fate = 2;
+      break;
+    }
+    ++steps;
+    int a;
+    double s = exit_dist(n, x, d, &a);
+    const double ksr_c = ksr * n->rho;
+    const int scat = ksr_c > 0 && ksr_c * s >= tau;
+    const double seg = scat ? tau / ksr_c : s;
+    for (int j = 0; j < size; ++j) {
+      const double xj = (ka[j] + ks[j] - ksr) * n->rho * seg;
+      const double dep = W[j] * ka[j] * n->rho * seg * phi1(xj);
+      int ob = J->bins > 1 ? first + j : 0;
+      deposit(w, (int64_t)ob * nc + n->id, p, dep);
+      w->led.absorbed += dep;
+      W[j] *= exp(-xj);
+    }
+    if (seg > 0) { ncross += 1; w->led.n_cross += 1; }
+    if (scat) {
+      for (int b = 0; b < 3; ++b) x[b] += seg * d[b];
+      nscat += 1;
+      w->led.n_scatter += 1;
+      /* the event: each bin scatters here with ks_j / ks_r of the reference's rate */
+      for (int j = 0; j < size; ++j) W[j] *= ks[j] / ksr;
+      if (J->obs && J->obs->n_obs > 0) peel_poly(w, x, d, W, first, size);
+      double mu = orc_hg_mu(gr, uni(&rs));
+      double phi = 2.0 * ORC_PI * uni(&rs);
+      double nd[3];
+      orc_scatter_dir(d, mu, phi, nd);
+      d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
+      const double pr = orc_hg_phase(gr, mu);
+      double rmax = 0.0;
+      for (int j = 0; j < size; ++j) {
+        W[j] *= orc_hg_phase(op->g_hg[first + j], mu) / pr;
+        const double q = W[j] / W0[j];
+        if (q > rmax) rmax = q;
+      }
+      if (prm->rr_wmin > 0 && rmax < prm->rr_wmin) {
+        double ur = uni(&rs);
+        if (ur < prm->rr_p) {
+          for (int j = 0; j < size; ++j) { w->led.rr_loss += W[j]; W[j] = 0; }
+          fate = 1;
+          break;
+        }
+        for (int j = 0; j < size; ++j) {
+          double Wn = W[j] / (1.0 - prm->rr_p);
+          w->led.rr_gain += Wn - W[j];
+          W[j] = Wn;
+        }
+      }
+      tau = -log(uni(&rs));
+    } else {
+      tau -= ksr_c * s;
+      move_to_face(n, x, d, s, a);
+    }
+  }
+  if (w->pkt_acc) flush_packet(w);
+  if (J->rec) {
+    double* r = &J->rec[p * 10];
+    double we = 0.0;
+    for (int j = 0; j < size; ++j) we += W[j];
+    r[0] = fate == 0 ? we : 0.0;
+    r[1] = nscat;
+    r[2] = ncross;
+    r[3] = fate;
+    for (int b = 0; b < 3; ++b) { r[4 + b] = x[b] * t->h0; r[7 + b] = d[b]; }
+  }
+}
+
 static void trace_one(trace_worker* w, int64_t p) {
   trace_job* J = w->job;
   const orc_tree* t = J->t;
@@ -823,6 +1025,10 @@ static void trace_one(trace_worker* w, int64_t p) {
   int si = (int)(seg / nl), bin = (int)(seg % nl);
   int64_t k = p - J->seg_begin[seg];
   int64_t npk = J->seg_begin[seg + 1] - J->seg_begin[seg];
+  if (prm->poly_group > 1) {
+    trace_poly(w, p, si, bin, k, npk);
+    return;
+  }
   const orc_source* S = &J->src[si];
   rstream rs = {prm->seed, (uint64_t)(k + prm->packet_offset), 0, prm->job, prm->iter,
                 ((uint32_t)si << 16) | (uint32_t)bin};
@@ -930,6 +1136,20 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
               double* sumsq, double* hits, double* rec, orc_ledger* ledger) {
   if (!t || n_src <= 0 || !src || !op || !prm || op->n_lambda <= 0) return -1;
   if (prm->per_level && obs && obs->n_obs > 0) return -1;  /* levels take the place of bins */
+  if (prm->poly_group > 1) {  /* polychromatic: plain continuous estimator, no dust sources */
+    if (prm->poly_group > ORC_POLY_MAX || prm->estimator != ORC_EST_CONTINUOUS || prm->split_factor > 1 ||
+        prm->per_level || prm->self_absorbed || prm->peel_block > 0)
+      return -1;
+    for (int s = 0; s < n_src; ++s)
+      if (src[s].kind == ORC_SRC_DUST) return -1;
+    for (int f = 0; f < op->n_lambda; f += prm->poly_group) {  /* the reference bin must scatter */
+      const int size = prm->poly_group < op->n_lambda - f ? prm->poly_group : op->n_lambda - f;
+      const int r = f + (size - 1) / 2;
+      int any = 0;
+      for (int j = 0; j < size; ++j) any |= op->albedo[f + j] * op->kappa_ext[f + j] > 0;
+      if (any && !(op->albedo[r] * op->kappa_ext[r] > 0)) return -1;
+    }
+  }
   if (prm->split_factor > 1) {  /* a split makes at most 256 packages */
     const int lm = prm->split_max_level < t->n_levels - 1 ? prm->split_max_level : t->n_levels - 1;
     if (lm < 0) return -1;

@@ -117,6 +117,13 @@ typedef struct {
    * probability split_factor^-dl.  Levels are capped at split_max_level. */
   int split_factor;            /* <= 1: off */
   int split_max_level;
+  /* Polychromatic packages (Sect. 2.3): > 1: the wavelength bins form
+   * consecutive groups of poly_group bins (the last may be shorter) and a
+   * package carries one weight per bin of its group; its path is drawn at
+   * the group's reference bin (the middle one) and each bin's weight carries
+   * the likelihood ratio of that path.  Packages are counted per group, at
+   * the group's first bin of `packets`. */
+  int poly_group;
 } orc_params;
 
 typedef struct {
