@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="cloud", choices=["cloud", "disc", "batch", "serve", "peeltab", "split"],
+    ap.add_argument("--workload", default="cloud",
+                    choices=["cloud", "disc", "batch", "serve", "peeltab", "split", "merge", "poly"],
                     help="cloud: the headline workload; disc/batch/serve: the other model families; "
                          "peeltab: accelerated against exact peel-off")
     ap.add_argument("--iters", type=int, default=30, help="disc: Lambda-iteration cap")
@@ -61,6 +62,9 @@ def parse():
     ap.add_argument("--ali", action="store_true", help="disc subiterations: also 30 full ALI steps")
     ap.add_argument("--split-runs", type=int, default=20, help="split: runs with and without resampling")
     ap.add_argument("--split-packets", type=int, default=2_000_000, help="split: initial packages per run")
+    ap.add_argument("--merge-packets", type=int, default=20_000_000, help="merge: packages per wavelength")
+    ap.add_argument("--poly-group", type=int, default=4, help="poly: bins per polychromatic package")
+    ap.add_argument("--poly-packets", type=int, default=1_000_000, help="poly: packages per bin / per group")
     ap.add_argument("--flux-frac", type=float, default=0.05,
                     help="disc subiterations: full step once the emission below the level changed by this fraction")
     ap.add_argument("--models", type=int, default=64, help="batch: models per launch")

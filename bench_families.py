@@ -15,6 +15,16 @@
            marches on the molecular cloud (6 axis observers) and the disc
            (5 observers 2 degrees above the plane): table build time, peel-off
            kernel time, crossings, image relative RMS difference.
+* merge -- Sect. 4.1: a full-resolution lognormal cloud cube (256^3) against
+           the hierarchical model built from it (32^3 root, 3 levels, cells
+           combined while tau_V <= 0.05 and contrast < 30): cells, trace and
+           peel-off time, and the relative mean and RMS differences of the
+           scattered-light maps (Eqs. 6-7).
+* poly -- polychromatic packages (groups of 4 bins) against monochromatic
+           ones on a 128^3 molecular cloud (20 wavelengths, external field,
+           6 observers): time per run, per-bin noise of the absorbed energy
+           and of the images (two seeds), and the efficiency ratio
+           t_mono noise_mono^2 / (t_poly noise_poly^2).
 * split -- resampling at grid boundaries (Sect. 2.3, Table 1): the 4 um
            radiation field of the molecular cloud from the external field and
            from embedded point sources, R runs with and without splitting
@@ -45,7 +55,7 @@ def run(a):
     torch.cuda.set_device(0)
     ctx = rt.Context(0)
     {"disc": run_disc, "batch": run_batch, "serve": run_serve, "peeltab": run_peeltab,
-     "split": run_split}[a.workload](a, rt, synth, ctx, torch)
+     "split": run_split, "merge": run_merge, "poly": run_poly}[a.workload](a, rt, synth, ctx, torch)
 
 
 def run_disc_subiter(a, rt, synth, ctx, torch):
@@ -432,3 +442,130 @@ def run_split(a, rt, synth, ctx, torch):
     print(json.dumps({"metric": "resampling at grid boundaries (Table 1): RMS noise per level, 4 um field",
                       "workload": "split", "cells": int(g.n_cells), "runs": runs, "packages_per_run": npk,
                       "split_factor": 4, **out, "dtype": "f32", "clocks": clocks}))
+
+
+def run_merge(a, rt, synth, ctx, torch):
+    """Sect. 4.1: full resolution against the hierarchical model built from
+    it, traced with the same packages (same seed), scattered-light maps
+    compared by Eqs. 6-7."""
+    n_full, root_n = 256, 32
+    box_pc = 2.0
+    L = box_pc * synth.PC_CM
+    rho_unit = 70.0 * 2.8 * synth.MH_G
+    g = synth.gaussian_random_field(n_full, 1002)
+    rho = rho_unit * np.exp(1.5 * g - 1.125)          # [z][y][x], mean rho_unit
+    lam = np.array([0.3, 0.55, 1.0, 2.2])[: max(1, min(4, a.n_lambda))]  # scattered light: UV to near-IR
+    kV = 0.4 / (rho_unit * L)                          # mean tau_V across the box = 0.4
+    optics = synth.powerlaw_dust(lam, kV, 0.55, g=0.5)
+    src = [synth.Source("external", bin_energy=np.full(lam.size, 1.0 / lam.size))]
+    obs = synth.axis_observers(n_full, L, "all6")
+    full = synth.TreeDesc(root=(n_full,) * 3, box=(L,) * 3, n_refined=np.zeros(1, np.int64),
+                          refine_flags=np.zeros(n_full ** 3, np.uint8), density=rho.ravel().copy())
+    rho_dev = torch.from_numpy(rho).to("cuda:0")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    amr = rt.rt_merge_uniform(ctx, rho_dev, (root_n,) * 3, (L,) * 3, kV, 0.05, 30.0)
+    merge_s = time.perf_counter() - t0
+    del rho_dev
+    npk = a.merge_packets
+    clk = _clock_start()
+    res = {}
+    # the full model twice (other seed: the Monte Carlo noise floor of the
+    # comparison), then the hierarchical model with the first seed
+    for name, desc, seed in (("full", full, 1001), ("full_seed2", full, 2002), ("hierarchical", amr, 1001)):
+        gr = rt.Grid(ctx, desc)
+        im = torch.zeros((obs.n_obs, lam.size, obs.ny, obs.nx), dtype=torch.float64, device="cuda:0")
+        ms = []
+        for r in range(max(1, a.steps) + 1):
+            im.zero_()
+            led = rt.rt_peel(ctx, gr, src, optics, obs, im, None, seed=seed, precision=32, packets_per_bin=npk,
+                             rr_wmin=1e-4, rr_p=0.9)
+            if r:
+                ms.append(led["kernel_ms"] + led["peel_ms"])
+        res[name] = dict(cells=int(gr.n_cells), ms=float(np.median(ms)), n_cross=int(led["n_cross"]),
+                         n_peel_cross=int(led["n_peel_cross"]), images=im.cpu().numpy())
+        del gr
+    clocks = clk.stop()
+    f, h, f2 = res["full"]["images"], res["hierarchical"]["images"], res["full_seed2"]["images"]
+    per_lambda = []
+    def binned(x, k=8):  # k x k pixel blocks: less Monte Carlo noise per map element
+        o, ny, nx = x.shape
+        return x.reshape(o, ny // k, k, nx // k, k).sum(axis=(2, 4))
+
+    for b in range(lam.size):
+        d = h[:, b] - f[:, b]
+        n = f2[:, b] - f[:, b]
+        fb, db, nb = binned(f[:, b]), binned(d), binned(n)
+        per_lambda.append({"lambda_um": float(lam[b]),
+                           "delta_mean": float(d.sum() / f[:, b].sum()),
+                           "delta_rms": float(np.sqrt((d * d).sum() / (f[:, b] ** 2).sum())),
+                           "noise_floor_delta_mean": float(n.sum() / f[:, b].sum()),
+                           "noise_floor_delta_rms": float(np.sqrt((n * n).sum() / (f[:, b] ** 2).sum())),
+                           "delta_rms_8x8": float(np.sqrt((db * db).sum() / (fb * fb).sum())),
+                           "noise_floor_delta_rms_8x8": float(np.sqrt((nb * nb).sum() / (fb * fb).sum()))})
+    print(json.dumps({"metric": "hierarchical model built from the full-resolution cube (Sect. 4.1)",
+                      "workload": "merge", "full_cells": res["full"]["cells"],
+                      "hierarchical_cells": res["hierarchical"]["cells"],
+                      "cell_ratio": res["full"]["cells"] / res["hierarchical"]["cells"],
+                      "levels": int(amr.n_levels), "cells_per_level_refined": [int(v) for v in amr.n_refined],
+                      "merge_s": merge_s, "packages_per_bin": npk, "n_lambda": int(lam.size),
+                      "trace_peel_ms_full": res["full"]["ms"], "trace_peel_ms_hierarchical": res["hierarchical"]["ms"],
+                      "speedup": res["full"]["ms"] / res["hierarchical"]["ms"],
+                      "crossings_full": res["full"]["n_cross"], "crossings_hierarchical": res["hierarchical"]["n_cross"],
+                      "peel_crossings_full": res["full"]["n_peel_cross"],
+                      "peel_crossings_hierarchical": res["hierarchical"]["n_peel_cross"],
+                      "maps": per_lambda, "dtype": "f32", "clocks": clocks}))
+
+
+def run_poly(a, rt, synth, ctx, torch):
+    """Polychromatic against monochromatic packages at the same number of
+    packages per wavelength bin (monochromatic) or per group (polychromatic),
+    untiled, FP32.  Noise: relative RMS difference of two seeds per bin."""
+    m = synth.cloud(n_root=128, levels=3, n_lambda=20, packets_per_bin=0, n_pix=64)
+    ctx.set_tiles(0)
+    g = rt.Grid(ctx, m.tree)
+    nl = m.optics.n_lambda
+    obs = m.observers
+    leaf = torch.as_tensor(m.tree.refine_flags == 0, device="cuda:0")
+    npk = a.poly_packets
+    clk = _clock_start()
+    out = {}
+    for F in (1, a.poly_group):
+        runs = []
+        for seed in (11, 22, 33):
+            ab = torch.zeros((nl, g.n_cells), dtype=torch.float64, device="cuda:0")
+            im = torch.zeros((obs.n_obs, nl, obs.ny, obs.nx), dtype=torch.float64, device="cuda:0")
+            led = rt.rt_peel(ctx, g, m.sources, m.optics, obs, im, ab, seed=seed, precision=32, packets_per_bin=npk,
+                             rr_wmin=1e-4, rr_p=0.9, poly_group=F)
+            runs.append((ab[:, leaf], im, led))
+        ms = float(np.median([r[2]["kernel_ms"] + r[2]["peel_ms"] for r in runs[1:]]))
+        a1, a2 = runs[1][0], runs[2][0]
+        i1, i2 = runs[1][1], runs[2][1]
+        cell_noise = (torch.sqrt(((a1 - a2) ** 2).mean(dim=1) / 2) / a1.abs().mean(dim=1).clamp_min(1e-300)).cpu().numpy()
+        img_noise = (torch.sqrt(((i1 - i2) ** 2).sum(dim=(0, 2, 3)) / 2 / (i1 ** 2).sum(dim=(0, 2, 3)).clamp_min(1e-300))
+                     ).cpu().numpy()
+        out[F] = dict(ms=ms, packages=int(runs[1][2]["n_packets"]), crossings=int(runs[1][2]["n_cross"]),
+                      peel_crossings=int(runs[1][2]["n_peel_cross"]), cell_noise=cell_noise, img_noise=img_noise,
+                      absorbed_total=runs[1][0].sum(dim=1).cpu().numpy())
+    clocks = clk.stop()
+    P = a.poly_group
+    eff_cells = (out[1]["ms"] * out[1]["cell_noise"] ** 2) / (out[P]["ms"] * out[P]["cell_noise"] ** 2)
+    eff_img = (out[1]["ms"] * out[1]["img_noise"] ** 2) / (out[P]["ms"] * np.maximum(out[P]["img_noise"], 1e-300) ** 2)
+    print(json.dumps({
+        "metric": "polychromatic packages (Sect. 2.3) against monochromatic ones",
+        "workload": "poly", "cells": int(g.n_cells), "n_lambda": nl, "group": P,
+        "packages_per_bin_or_group": npk,
+        "ms_mono": out[1]["ms"], "ms_poly": out[P]["ms"],
+        "packages_mono": out[1]["packages"], "packages_poly": out[P]["packages"],
+        "crossings_mono": out[1]["crossings"], "crossings_poly": out[P]["crossings"],
+        "peel_crossings_mono": out[1]["peel_crossings"], "peel_crossings_poly": out[P]["peel_crossings"],
+        "lambda_um": [float(v) for v in m.optics.lambda_um],
+        "cell_noise_mono": [round(float(v), 5) for v in out[1]["cell_noise"]],
+        "cell_noise_poly": [round(float(v), 5) for v in out[P]["cell_noise"]],
+        "image_noise_mono": [round(float(v), 5) for v in out[1]["img_noise"]],
+        "image_noise_poly": [round(float(v), 5) for v in out[P]["img_noise"]],
+        "absorbed_ratio_poly_over_mono": [round(float(x / y), 5) if y > 0 else None
+                                          for x, y in zip(out[P]["absorbed_total"], out[1]["absorbed_total"])],
+        "efficiency_cells": [round(float(v), 3) for v in eff_cells],
+        "efficiency_images": [round(float(v), 3) for v in eff_img],
+        "dtype": "f32", "clocks": clocks}))

@@ -204,6 +204,25 @@ typedef struct {
    * in its record buffer is skipped (counted in n_split_skipped). */
   int split_factor;         /* <= 1: off */
   int split_max_level;      /* < 0: the grid's depth */
+  /* Polychromatic packages (Sect. 2.3, after Jonsson 2006): 2..8 groups the
+   * bins into consecutive groups of poly_group bins (the last may be
+   * shorter); a package carries one weight per bin of its group, its path is
+   * drawn for the group's reference bin r (bin first + (size - 1) / 2) and
+   * each weight carries the likelihood ratio of that path: e^{-(ks_j -
+   * ks_r) rho s} along a segment without scattering, ks_j / ks_r at a
+   * scattering, p_j(mu) / p_r(mu) for the new direction; a segment deposits
+   * W_j ta_j (1 - e^{-x_j}) / x_j with x_j = (ka_j + ks_j - ks_r) rho s and
+   * W_j <- W_j e^{-x_j}.  Packages are counted per group (packets_per_bin
+   * per group; packets_total in proportion to the group's energy; packets:
+   * the entry of the group's first bin); W0_j = E_j / N_group.  The random
+   * stream of a group is that of the monochromatic package of its first
+   * bin.  Roulette acts on all weights when max_j W_j / W0_j < rr_wmin.
+   * One job, point / external / beam sources, continuous estimator, no hit
+   * counts, levels, resampling or tabulated peel-off; the group's reference
+   * bin must scatter if any bin of the group does; untiled, peel-off inline.
+   * The ledger sums the bins; per package its energy balance holds in
+   * expectation only (the likelihood ratios change the weights).  <= 1: off. */
+  int poly_group;
 } rt_trace_params;
 
 typedef struct {
@@ -476,6 +495,30 @@ int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_s
  * bin_total_host (host [n_lambda], may be NULL; waits for the stream). */
 int rt_dust_emission(rt_ctx* ctx, const rt_grid* grid, const double* T_dev, const rt_dust* dust,
                      double* emission_dev, double* bin_total_host, void* cuda_stream);
+
+/* Hierarchical model built bottom-up from a full-resolution cube (Sect. 4.1:
+ * cells are combined while the combined cell's V-band optical thickness is
+ * <= 0.05 and the density contrast of the cells combined is < 30).
+ * rho_dev: device [nz][ny][nx] f64 densities (g/cm^3, x fastest) with
+ * n = root[i] * 2^n_fine_levels cells per axis; box: model size (cm, cubic
+ * cells).  Eight cells of level l+1 are combined into their parent when all
+ * eight are undivided, kappa * rho_mean * h_l <= tau_max (kappa: cm^2/g,
+ * h_l: the parent's size) and rho_max < contrast_max * rho_min over the
+ * full-resolution cells the parent covers (rho_min = 0: only if rho_max =
+ * 0); the parent's density is the mean of the eight, added in octant order
+ * o = ox + 2 oy + 4 oz.  Output (caller-owned host arrays): the level-ordered
+ * description rt_build_grid takes -- refine_flags / density [cap_cells]
+ * (root cells x-fastest, then the children of each divided cell in the
+ * order of their parents, in octant order), n_refined [n_fine_levels + 1]
+ * (divided cells per level), n_levels_out, n_cells_out.  If the
+ * description has more than cap_cells cells nothing past cap_cells is
+ * written, n_cells_out holds the size needed and the call returns
+ * RT_ERR_INVALID.  Device scratch is allocated and freed inside the call
+ * (~1.3 x the cube's bytes).  Synchronises the stream. */
+int rt_merge_uniform(rt_ctx* ctx, const int* root, const double* box, int n_fine_levels, const double* rho_dev,
+                     double kappa, double tau_max, double contrast_max, int64_t cap_cells,
+                     uint8_t* refine_flags_host, double* density_host, int64_t* n_refined_host, int* n_levels_out,
+                     int64_t* n_cells_out, void* cuda_stream);
 
 /* ------------------------------------------------------------------------ */
 /* Diagnostics used by the parity tests                                      */

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt.so")
-SOURCES = ["rt_api.cu", "rt_trace.cu", "rt_grid.cu", "rt_dust.cu", "rt_noalloc.cu", "rt_server.cu"]
+SOURCES = ["rt_api.cu", "rt_trace.cu", "rt_grid.cu", "rt_dust.cu", "rt_noalloc.cu", "rt_server.cu", "rt_merge.cu",
+           "rt_poly.cu"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -568,6 +568,22 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     if (p->rr_wmin > 0.0 && !(p->rr_p >= 0.0 && p->rr_p < 1.0)) return fail(RT_ERR_INVALID, "job %d: rr_p must be in [0,1)", j);
     if (p->estimator == RT_EST_ANALOG && p->rr_wmin > 0.0)
       return fail(RT_ERR_INVALID, "job %d: roulette applies to the continuous-absorption estimator only", j);
+    if (p->poly_group > 1) {
+      if (p->poly_group > 8) return fail(RT_ERR_INVALID, "job %d: poly_group must be 1..8", j);
+      if (n_jobs != 1) return fail(RT_ERR_INVALID, "polychromatic packages run one job per call");
+      if (p->estimator != RT_EST_CONTINUOUS || p->hits_dev || T.levels || T.tab || p->split_factor > 1)
+        return fail(RT_ERR_INVALID, "job %d: polychromatic packages need the continuous estimator, no hits, "
+                    "levels, resampling or tabulated peel-off", j);
+      for (int si = 0; si < T.n_src; ++si)
+        if (T.src[si].kind == RT_SRC_DUST) return fail(RT_ERR_INVALID, "job %d: no polychromatic dust sources", j);
+      for (int f = 0; f < nl; f += p->poly_group) {
+        const int size = std::min(p->poly_group, nl - f), r = f + (size - 1) / 2;
+        bool any = false;
+        for (int b = f; b < f + size; ++b) any = any || T.optics->albedo[b] * T.optics->kappa_ext[b] > 0.0;
+        if (any && !(T.optics->albedo[r] * T.optics->kappa_ext[r] > 0.0))
+          return fail(RT_ERR_INVALID, "job %d: the reference bin %d of a scattering group does not scatter", j, r);
+      }
+    }
     if (p->split_factor > 1) {
       if (n_jobs != 1) return fail(RT_ERR_INVALID, "resampling runs one job per call");
       if (p->estimator != RT_EST_CONTINUOUS || p->hits_dev || T.levels)
@@ -653,6 +669,20 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     } else {
       return fail(RT_ERR_INVALID, "job %d: set packets_per_bin, packets_total or packets", j);
     }
+    // polychromatic: packages per group, counted at the group's first bin
+    const int poly = p->poly_group > 1 ? p->poly_group : 1;
+    if (poly > 1)
+      for (int si = 0; si < T.n_src; ++si)
+        for (int f = 0; f < nl; f += poly) {
+          const int size = std::min(poly, nl - f);
+          long long n = 0;
+          if (p->packets_per_bin > 0 || p->packets) {
+            n = pk[(size_t)si * nl + f];
+          } else {
+            for (int b = f; b < f + size; ++b) n += pk[(size_t)si * nl + b];
+          }
+          for (int b = f; b < f + size; ++b) pk[(size_t)si * nl + b] = b == f ? n : 0;
+        }
     // a dust bin that emits nothing has no cell to sample from: no packages
     for (int si = 0; si < T.n_src; ++si)
       if (T.src[si].kind == RT_SRC_DUST)
@@ -692,6 +722,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.pkt_offset = p->packet_offset;
     J.sub_conf = T.confine;
     J.split_n = p->split_factor > 1 ? p->split_factor : 1;
+    J.poly_n = poly;
     J.split_lmax = p->split_max_level < 0 ? G->n_levels - 1 : std::min(p->split_max_level, G->n_levels - 1);
     J.self_abs = T.levels ? T.self_abs : nullptr;
     J.self_emit = T.levels ? T.self_emit : nullptr;
@@ -797,7 +828,9 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
       for (int b = 0; b < nl; ++b) {
         const long long np_ = pk[(size_t)si * nl + b];
         pref[b + 1] = pref[b] + np_;
-        w0[b] = np_ > 0 ? energy[(size_t)si * nl + b] / (double)np_ : 0.0;
+        // polychromatic: every bin of a group shares the group's packages
+        const long long ng = poly > 1 ? pk[(size_t)si * nl + (b / poly) * poly] : np_;
+        w0[b] = ng > 0 ? energy[(size_t)si * nl + b] / (double)ng : 0.0;
         w0f[b] = (float)w0[b];
       }
       I.pkt_begin = total;
@@ -975,7 +1008,9 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   // counter[0] packages, [1] peel-off queue length, [2] peel-off work,
   // [3] tile records written, [4] tile status, [5] split copies this round
   CK(cudaMemsetAsync(c->small.p, 0, sizeof(LedgerDev) * n_jobs + 6 * sizeof(unsigned long long), s));
-  const PeelQueue q = make_queue(c->peel_q, c->peel_q_max, peel, n_jobs, total, precision, counter + 1);
+  // polychromatic packages: their own tracer, peel-off inline
+  const bool poly = n_jobs == 1 && jobs[0].prm->poly_group > 1;
+  const PeelQueue q = make_queue(c->peel_q, c->peel_q_max, peel && !poly, n_jobs, total, precision, counter + 1);
   LaunchCfg cfg;
   rc = make_cfg(c, precision, peel, launch_prm, &cfg);
   if (rc) return rc;
@@ -985,7 +1020,7 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
     return fail(RT_ERR_INVALID, "hit counting needs rt_trace with the continuous estimator");
   const double to = launch_prm->timeout_s > 0 ? launch_prm->timeout_s : 3600.0;
   TileRun tiles;
-  bool tiled = total > 0 && n_items > 0 && choose_tiles(c, jobs[0].grid, n_jobs, &tiles);
+  bool tiled = !poly && total > 0 && n_items > 0 && choose_tiles(c, jobs[0].grid, n_jobs, &tiles);
   const bool split = n_jobs == 1 && jobs[0].prm->split_factor > 1;
   if (split && total > 0 && n_items > 0 && !tiled) {
     // resampling runs in the rounds of the tiled tracer: one tile
@@ -1008,6 +1043,10 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
                    n_items, total, cfg, q, counter, counter + 3, tile_status, to, s, &n_launch, &n_rounds,
                    jobs[0].levels != 0, split, counter + 5);
     if (rc) return rc;
+  } else if (poly && total > 0 && n_items > 0) {
+    CK(launch_poly(precision, jobs[0].prm->poly_group, peel, reinterpret_cast<const JobDev*>(base + job_off[0]),
+                   reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, c->sm_count, s));
+    n_launch = 1;
   } else if (total > 0 && n_items > 0) {
     CK(launch_trace(precision, peel, estimator, hits, reinterpret_cast<const JobDev*>(base + job_off[0]),
                     reinterpret_cast<const ItemDev*>(base + items_off), n_items, counter, total, cfg, q, s, 0,
@@ -1661,8 +1700,9 @@ extern "C" int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_b
                     estimator, &b->table, &b->cdf);
   if (rc) return bail(rc);
   for (int j = 0; j < n_jobs; ++j)
-    if (args[j].prm->hits_dev || args[j].prm->split_factor > 1)
-      return bail(fail(RT_ERR_INVALID, "rt_batch_create: hit counting and resampling are not batched"));
+    if (args[j].prm->hits_dev || args[j].prm->split_factor > 1 || args[j].prm->poly_group > 1)
+      return bail(fail(RT_ERR_INVALID, "rt_batch_create: hit counting, resampling and polychromatic packages are "
+                                       "not batched"));
   e = cudaStreamSynchronize(b->cap);
   if (e != cudaSuccess) return bail(fail(RT_ERR_CUDA, "rt_batch_create: %s", cudaGetErrorString(e)));
   LaunchCfg cfg;
@@ -1848,4 +1888,40 @@ extern "C" int rt_tune_load(rt_ctx* ctx, const char* path) {
   }
   fclose(f);
   return loaded > 0 ? RT_OK : fail(RT_ERR_INVALID, "rt_tune_load: no entry for %s in %s", mine, path);
+}
+
+// ------------------------------------------------------------------------
+// hierarchical model from a full-resolution cube (Sect. 4.1)
+// ------------------------------------------------------------------------
+extern "C" int rt_merge_uniform(rt_ctx* ctx, const int* root, const double* box, int n_fine_levels,
+                                const double* rho_dev, double kappa, double tau_max, double contrast_max,
+                                int64_t cap_cells, uint8_t* refine_flags_host, double* density_host,
+                                int64_t* n_refined_host, int* n_levels_out, int64_t* n_cells_out, void* cuda_stream) {
+  if (!ctx || !root || !box || !rho_dev || !n_refined_host || !n_levels_out || !n_cells_out)
+    return fail(RT_ERR_INVALID, "rt_merge_uniform: NULL argument");
+  if (cap_cells > 0 && (!refine_flags_host || !density_host))
+    return fail(RT_ERR_INVALID, "rt_merge_uniform: output arrays are NULL");
+  if (n_fine_levels < 0 || n_fine_levels > 20) return fail(RT_ERR_INVALID, "rt_merge_uniform: n_fine_levels must be 0..20");
+  for (int a = 0; a < 3; ++a) {
+    if (root[a] < 1 || ((long long)root[a] << n_fine_levels) > (1ll << RT_COORD_BITS))
+      return fail(RT_ERR_INVALID, "rt_merge_uniform: root dims must be >= 1 with root * 2^L <= 2^%d", RT_COORD_BITS);
+    if (!(box[a] > 0.0) || !std::isfinite(box[a])) return fail(RT_ERR_INVALID, "rt_merge_uniform: bad box size");
+  }
+  const double h0 = box[0] / root[0];
+  for (int a = 1; a < 3; ++a)
+    if (std::fabs(box[a] / root[a] - h0) > 1e-12 * h0) return fail(RT_ERR_INVALID, "rt_merge_uniform: cells are not cubic");
+  if (!(kappa >= 0.0) || !std::isfinite(kappa) || !(tau_max > 0.0) || !(contrast_max >= 1.0))
+    return fail(RT_ERR_INVALID, "rt_merge_uniform: need kappa >= 0, tau_max > 0, contrast_max >= 1");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard dg(ctx->device);
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  long long nref[24] = {0};
+  long long nc = 0;
+  int nlev = 0;
+  const int rc = rtk::merge_uniform(root, h0, n_fine_levels, rho_dev, kappa, tau_max, contrast_max, cap_cells,
+                                    refine_flags_host, density_host, nref, &nlev, &nc, s);
+  *n_cells_out = nc;
+  *n_levels_out = nlev;
+  for (int l = 0; l < nlev; ++l) n_refined_host[l] = nref[l];
+  return rc;
 }

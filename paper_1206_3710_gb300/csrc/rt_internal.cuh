@@ -175,6 +175,9 @@ struct JobDev {
   // the level at which grid levels are capped
   int split_n;
   int split_lmax;
+  // polychromatic packages: bins per group (1: monochromatic)
+  int poly_n;
+  int pad3;
   // ALI (Eq. 3): energy a dust package leaves in its own emission cell, per
   // cell (the diagonal of Lambda), and the energy of the dust packages each
   // cell emitted; NULL: not tallied
@@ -231,6 +234,9 @@ cudaError_t launch_trace(int precision, bool peel, int estimator, bool hits, con
                          long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s,
                          int mode = 0, const TileRun* tiles = nullptr, bool levels = false, bool split = false);
 size_t tile_record_bytes(int precision, bool wide);
+// polychromatic tracer (groups of 2..8 bins), one job
+cudaError_t launch_poly(int precision, int group, bool peel, const JobDev* jobs, const ItemDev* items, int n_items,
+                        unsigned long long* counter, long long total, int sm_count, cudaStream_t s);
 // counting sort of n records (rec_bytes each) by key (< n_keys) from in/key
 // into out; hist_dev holds n_keys + 1 counters
 cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_bytes, int n_keys,
@@ -282,6 +288,11 @@ cudaError_t validate_leaf_density(const double* rho64, const uint32_t* child, lo
 
 // record an error message for rt_last_error and return code
 int set_error(int code, const char* msg);
+// the hierarchical model built bottom-up from a full-resolution cube
+// (Sect. 4.1); see rt_merge_uniform in rt.h
+int merge_uniform(const int* root, double h0, int L, const double* rho, double kappa, double tau_max, double cmax,
+                  long long cap, uint8_t* flags_host, double* dens_host, long long* n_ref_host, int* n_levels,
+                  long long* n_cells, cudaStream_t s);
 // device of a context
 int ctx_device(const rt_ctx* c);
 

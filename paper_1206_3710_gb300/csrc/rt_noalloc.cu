@@ -61,7 +61,8 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
   using namespace rtk;
   if (ledger) memset(ledger, 0, sizeof *ledger);
   if (!grid || !src || !op || !p) return set_error(RT_ERR_INVALID, "rt_trace_noalloc: NULL argument");
-  if (p->split_factor > 1) return set_error(RT_ERR_INVALID, "rt_trace_noalloc: no resampling (records need scratch)");
+  if (p->split_factor > 1 || p->poly_group > 1)
+    return set_error(RT_ERR_INVALID, "rt_trace_noalloc: no resampling or polychromatic packages");
   if (n_src < 1 || n_src > RT_NOALLOC_MAX_SOURCES)
     return set_error(RT_ERR_INVALID, "rt_trace_noalloc: n_src must be 1..4 (scratch limit)");
   if (op->n_lambda < 1 || op->n_lambda > RT_MAX_LAMBDA || !op->kappa_ext || !op->albedo || !op->g_hg)

@@ -28,7 +28,7 @@ EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "r
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
             "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles",
             "rt_peel_tables_create", "rt_peel_tables_destroy", "rt_peel_tables_size", "rt_peel_tables_read",
-            "rt_peel_tabulated", "rt_lambda_subiterate"]
+            "rt_peel_tabulated", "rt_lambda_subiterate", "rt_merge_uniform"]
 
 
 class RtError(RuntimeError):
@@ -72,7 +72,7 @@ class rt_trace_params(C.Structure):
                 ("packets", C.POINTER(C.c_int64)), ("packets_total", C.c_int64), ("packet_log_dev", C.c_void_p),
                 ("timeout_s", C.c_double), ("block_size", C.c_int), ("refill_threshold", C.c_int),
                 ("blocks_per_sm", C.c_int), ("hits_dev", C.c_void_p), ("packet_offset", C.c_int64),
-                ("split_factor", C.c_int), ("split_max_level", C.c_int)]
+                ("split_factor", C.c_int), ("split_max_level", C.c_int), ("poly_group", C.c_int)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
@@ -178,6 +178,9 @@ def lib():
                                     C.POINTER(rt_ledger), vp]
     L.rt_dust_emission.argtypes = [vp, vp, vp, C.POINTER(rt_dust), vp, vp, vp]
     L.rt_walk.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int, C.c_int64, vp, vp, vp, vp]
+    L.rt_merge_uniform.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int, vp, C.c_double, C.c_double,
+                                   C.c_double, C.c_int64, vp, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int64), vp]
     L.rt_philox.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
     L.rt_trace_noalloc.argtypes = [vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics),
                                    C.POINTER(rt_trace_params), vp, C.POINTER(rt_ledger), vp]
@@ -352,7 +355,8 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
                 peel_tau_max: float = 0.0, per_lambda: bool = True, packets_per_bin: int = 0, packets=None,
                 packets_total: int = 0, packet_log=None, timeout_s: float = 0.0, block_size: int = 0,
                 refill_threshold: int = 0, blocks_per_sm: int = 0, hits=None,
-                packet_offset: int = 0, split_factor: int = 1, split_max_level: int = -1) -> rt_trace_params:
+                packet_offset: int = 0, split_factor: int = 1, split_max_level: int = -1,
+                poly_group: int = 1) -> rt_trace_params:
     p = rt_trace_params()
     p.seed, p.job, p.iter = int(seed), int(job), int(iter_)
     p.precision, p.estimator = int(precision), int(estimator)
@@ -367,6 +371,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
     p.hits_dev = _ptr(hits)
     p.packet_offset = int(packet_offset)
     p.split_factor, p.split_max_level = int(split_factor), int(split_max_level)
+    p.poly_group = int(poly_group)
     return p
 
 
@@ -540,6 +545,33 @@ def rt_walk(ctx: Context, grid: Grid, origins, dirs, precision: int, max_seg: in
     n = int(origins.shape[0])
     _check(lib().rt_walk(ctx.handle, grid.handle, n, _ptr(origins), _ptr(dirs), int(precision), int(max_seg),
                          _ptr(cells), _ptr(lengths), _ptr(counts), _stream(stream)))
+
+
+def rt_merge_uniform(ctx: Context, rho, root, box, kappa: float, tau_max: float = 0.05, contrast_max: float = 30.0,
+                     stream=None):
+    """Hierarchical model from a full-resolution cube (Sect. 4.1).  ``rho``:
+    device f64 tensor [nz][ny][nx] (x fastest) with root * 2^L cells per
+    axis.  Returns a tree description for ``Grid``."""
+    from . import synth
+    nz, ny, nx = (int(v) for v in rho.shape)
+    L = 0
+    while (int(root[0]) << L) < nx:
+        L += 1
+    cap = sum(int(np.prod(root)) << (3 * l) for l in range(L + 1))
+    flags = np.zeros(cap, dtype=np.uint8)
+    dens = np.zeros(cap, dtype=np.float64)
+    n_ref = np.zeros(L + 1, dtype=np.int64)
+    n_lev = C.c_int(0)
+    n_cells = C.c_int64(0)
+    r = (C.c_int * 3)(*[int(v) for v in root])
+    b = (C.c_double * 3)(*[float(v) for v in box])
+    _check(lib().rt_merge_uniform(ctx.handle, r, b, L, _ptr(rho), float(kappa), float(tau_max), float(contrast_max),
+                                  cap, flags.ctypes.data, dens.ctypes.data,
+                                  n_ref.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(n_lev), C.byref(n_cells),
+                                  _stream(stream)))
+    n = int(n_cells.value)
+    return synth.TreeDesc(root=tuple(int(v) for v in root), box=tuple(float(v) for v in box),
+                          n_refined=n_ref[: n_lev.value].copy(), refine_flags=flags[:n].copy(), density=dens[:n].copy())
 
 
 def rt_philox(ctx: Context, ctr, key, out, stream=None) -> None:
