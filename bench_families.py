@@ -530,6 +530,18 @@ def run_poly(a, rt, synth, ctx, torch):
     npk = a.poly_packets
     clk = _clock_start()
     out = {}
+    # the summed absorbed energy (what the temperature solve takes): one
+    # accumulator update per crossing and group instead of one per bin
+    summed = {}
+    for F in (1, a.poly_group):
+        ab = torch.zeros((1, g.n_cells), dtype=torch.float64, device="cuda:0")
+        t = []
+        for seed in (11, 22):
+            ab.zero_()
+            led = rt.rt_trace(ctx, g, m.sources, m.optics, ab, seed=seed, precision=32, packets_per_bin=npk,
+                              rr_wmin=1e-4, rr_p=0.9, poly_group=F, per_lambda=False)
+            t.append(led["kernel_ms"])
+        summed[F] = float(t[-1])
     for F in (1, a.poly_group):
         runs = []
         for seed in (11, 22, 33):
@@ -556,6 +568,7 @@ def run_poly(a, rt, synth, ctx, torch):
         "workload": "poly", "cells": int(g.n_cells), "n_lambda": nl, "group": P,
         "packages_per_bin_or_group": npk,
         "ms_mono": out[1]["ms"], "ms_poly": out[P]["ms"],
+        "trace_ms_summed_output_mono": summed[1], "trace_ms_summed_output_poly": summed[P],
         "packages_mono": out[1]["packages"], "packages_poly": out[P]["packages"],
         "crossings_mono": out[1]["crossings"], "crossings_poly": out[P]["crossings"],
         "peel_crossings_mono": out[1]["peel_crossings"], "peel_crossings_poly": out[P]["peel_crossings"],

@@ -888,6 +888,11 @@ static int make_cfg(rt_ctx* c, int precision, bool peel, const rt_trace_params* 
   const int bps = lp->blocks_per_sm > 0 ? lp->blocks_per_sm : (t.set ? t.blocks_per_sm : 0);
   if (bps > 0) occ = std::min(occ, bps);
   cfg->blocks = c->sm_count * occ;
+  int occ2 = 0;
+  CK(trace_occupancy(precision, peel, cfg->block, &occ2, 2));
+  if (occ2 < 1) occ2 = 1;
+  if (bps > 0) occ2 = std::min(occ2, bps);
+  cfg->blocks_tiled = c->sm_count * occ2;
   cfg->refill = lp->refill_threshold > 0 ? lp->refill_threshold : (t.set ? t.refill : default_refill(precision, peel));
   if (cfg->refill > 32) cfg->refill = 32;
   return RT_OK;

@@ -222,8 +222,9 @@ namespace rtk {
 
 struct LaunchCfg {
   int block;
-  int blocks;
+  int blocks;        // grid of the untiled and emission launches
   int refill;
+  int blocks_tiled;  // grid of the tiled rounds (their tracer is sized for fewer blocks per SM)
 };
 
 // launch the persistent tracer over n_items items of total packages;
@@ -241,7 +242,7 @@ cudaError_t launch_poly(int precision, int group, bool peel, const JobDev* jobs,
 // into out; hist_dev holds n_keys + 1 counters
 cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_bytes, int n_keys,
                       unsigned long long* hist_dev, void* out, cudaStream_t s);
-cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm);
+cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm, int mode = 0);
 // march the queued peel-off records (n_obs_max observers each); work_dev is a
 // zeroed counter
 cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,

@@ -238,6 +238,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     LaunchCfg cfg;
     cfg.block = block;
     cfg.blocks = sms * occ;
+    cfg.blocks_tiled = cfg.blocks;  // untiled only
     cfg.refill = p->refill_threshold > 0 ? (p->refill_threshold > 32 ? 32 : p->refill_threshold) : 8;
     PeelQueue q;  // no observers: no peel-off queue
     q.rec = nullptr;

@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(256) poly_kernel(const JobDev* __restrict__ jo
       const bool ev = kr > R(0) && tsc >= tau;
       const R tseg = ev ? tau / kr : tx;
       tau = ev ? R(0) : tau - tsc;
+      R dsum = R(0);  // summed output: one accumulator update for the group
 #pragma unroll
       for (int j = 0; j < F; ++j) {
         if (j < size) {
@@ -221,10 +222,15 @@ __global__ void __launch_bounds__(256) poly_kernel(const JobDev* __restrict__ jo
           W[j] *= e;
           if (dep > R(0)) {
             pkt_abs += dep;
-            if (absb) red_acc(absb + (long long)(per_bin ? first + j : 0) * J.n_cells + g.idx, widen(dep));
+            if (per_bin) {
+              if (absb) red_acc(absb + (long long)(first + j) * J.n_cells + g.idx, widen(dep));
+            } else {
+              dsum += dep;
+            }
           }
         }
       }
+      if (!per_bin && absb && dsum > R(0)) red_acc(absb + g.idx, widen(dsum));
       ncross += tseg > R(0) ? 1u : 0u;
       if (ev) {
         g.fx = clamp01(g.fx + tseg * dx);

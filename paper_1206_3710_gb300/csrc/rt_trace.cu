@@ -68,8 +68,6 @@ template <typename R>
 struct ColdState {
   uint32_t k0[256], k1[256], c0[256], c1[256], c3[256], next[256];
   long long log_index[256], pix[256], gi[256];
-  uint32_t orig[256];  // ALI: emission cell of a dust package (~0u: none)
-  int sexp[256];       // resampling: split exponent of the package (W0 = emitted W0 / N^sexp)
   R W0[256], pw[256], gpar[256];
   int bin[256], nscat[256], obs_i[256], job[256];
   // scattering point and incoming direction, saved during the peel-off
@@ -389,14 +387,21 @@ __device__ __forceinline__ int crossed_grid_level(const Geo<R>& g, int a, R dx, 
 #ifndef RT_FP32_MIN_BLOCKS
 #define RT_FP32_MIN_BLOCKS 4
 #endif
-// resident 256-thread blocks per SM the register allocation is sized for
-template <typename R>
+#ifndef RT_FP32_TILED_MIN_BLOCKS
+#define RT_FP32_TILED_MIN_BLOCKS 3
+#endif
+// Resident 256-thread blocks per SM the register allocation is sized for.
+// The tiled rounds (mode 2) run on L2-resident cells: there 3 blocks of
+// 80-register threads beat 4 blocks of 64 registers with spills (786 against
+// 861 ms for the cloud's rounds); the untiled tracer gathers from HBM and
+// keeps 4 blocks for latency hiding.
+template <typename R, int MODE>
 struct MinBlocks {
-  static constexpr int value = sizeof(R) == 4 ? RT_FP32_MIN_BLOCKS : 2;
+  static constexpr int value = sizeof(R) == 4 ? (MODE == 2 ? RT_FP32_TILED_MIN_BLOCKS : RT_FP32_MIN_BLOCKS) : 2;
 };
 
 template <typename R, bool PEEL, int EST, bool HITS, int MODE, bool LEVELS = false, bool SPLIT = false>
-__global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const JobDev* __restrict__ jobs,
+__global__ void __launch_bounds__(256, MinBlocks<R, MODE>::value) trace_kernel(const JobDev* __restrict__ jobs,
                                                                          const ItemDev* __restrict__ items,
                                                                          int n_items,
                                                                          unsigned long long* __restrict__ counter,
@@ -410,7 +415,14 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   ledger_init<R>(SL, wid, lane);
   C.job[t] = -1;
-  C.orig[t] = 0xFFFFFFFFu;
+  // per-lane state of the level-tracking and resampling tracers only: the ALI
+  // emission cell of a dust package (~0u: none) and the split exponent
+  // (W0 = emitted W0 / N^sexp); one element in the other tracers
+  __shared__ uint32_t s_orig[(LEVELS || SPLIT) ? 256 : 1];
+  __shared__ int s_sexp[SPLIT ? 256 : 1];
+  uint32_t& orig_t = s_orig[(LEVELS || SPLIT) ? t : 0];
+  int& sexp_t = s_sexp[SPLIT ? t : 0];
+  if (LEVELS || SPLIT) orig_t = 0xFFFFFFFFu;
   __syncwarp();
 
   // hot per-lane state
@@ -481,9 +493,9 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
       r.pkt_abs = pkt_abs;
       r.next = C.next[t]; r.nscat = (uint32_t)C.nscat[t]; r.ncross = ncross; r.npeel = npeel;
       r.gi = (unsigned long long)C.gi[t];
-      r.aux = pack_aux(mlev, plev, SPLIT ? C.sexp[t] : 0);
+      r.aux = pack_aux(mlev, plev, SPLIT ? sexp_t : 0);
       const bool copy = SPLIT && (C.c3[t] & 0x80000000u);
-      IO::set_ext(rr, C.orig[t], C.c0[t], C.c1[t], copy ? C.c3[t] : 0u);
+      IO::set_ext(rr, orig_t, C.c0[t], C.c1[t], copy ? C.c3[t] : 0u);
       static_cast<TRec*>(T.out)[slot] = rr;
       T.out_key[slot] = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
     } else {
@@ -567,7 +579,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           C.gpar[t] = Num<R>::gg(B);
           if (LEVELS) {
             mlev = aux_mlev(r.aux);
-            C.orig[t] = x_orig;
+            orig_t = x_orig;
             selfb = J.self_abs;
           }
           absb = J.absorbed ? J.absorbed + (long long)(LEVELS ? mlev : (J.abs_bins > 1 ? bin : 0)) * J.n_cells
@@ -576,9 +588,9 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           C.W0[t] = Num<R>::w0(I, bin);
           if (SPLIT) {
             plev = aux_plev(r.aux);
-            C.sexp[t] = aux_sexp(r.aux);
+            sexp_t = aux_sexp(r.aux);
             splt_lmax = J.split_lmax;
-            C.W0[t] = scale_pow(C.W0[t], (uint32_t)J.split_n, C.sexp[t]);
+            C.W0[t] = scale_pow(C.W0[t], (uint32_t)J.split_n, sexp_t);
           }
           C.nscat[t] = (int)r.nscat;
           W = r.W;
@@ -645,7 +657,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           if (SPLIT) {
             // the external field enters through the root grid (Sect. 2.2)
             plev = I.kind == RT_SRC_EXTERNAL ? 0 : -1;
-            C.sexp[t] = 0;
+            sexp_t = 0;
             splt_lmax = J.split_lmax;
           }
           pkt_abs = R(0);
@@ -737,7 +749,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
             // a package starts in the grid of its emission cell
             mlev = g.lev;
             absb = J.absorbed ? J.absorbed + (long long)mlev * J.n_cells : nullptr;
-            C.orig[t] = I.kind == RT_SRC_DUST ? cur.pending : 0xFFFFFFFFu;
+            orig_t = I.kind == RT_SRC_DUST ? cur.pending : 0xFFFFFFFFu;
             selfb = J.self_abs;
             if (selfb && J.self_emit && I.kind == RT_SRC_DUST) {
               atomicAdd(J.self_emit + cur.pending, widen(W));
@@ -821,7 +833,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
                   pkt_abs += dep;
                   if (absb) red_acc(absb + g.idx, widen(dep));
                   if (HITS && hitp) atomicAdd(hitp + g.idx, 1u);
-                  if (LEVELS && selfb && g.idx == C.orig[t]) atomicAdd(selfb + g.idx, widen(dep));
+                  if (LEVELS && selfb && g.idx == orig_t) atomicAdd(selfb + g.idx, widen(dep));
                 }
               }
             } else {
@@ -911,7 +923,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
         if (base + need <= (unsigned long long)T.split_cap) {
           W = W / (R)M;
           C.W0[t] = C.W0[t] / (R)M;
-          C.sexp[t] += dl;
+          sexp_t += dl;
           const unsigned long long slot0 = atomicAdd(T.n_out, need);
           const uint32_t key = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
           for (uint32_t kk = 1u; kk < M; ++kk) {
@@ -932,8 +944,8 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
             r.pkt_abs = R(0);
             r.next = 1u; r.nscat = 0u; r.ncross = 0u; r.npeel = 0u;
             r.gi = (unsigned long long)C.gi[t];
-            r.aux = pack_aux(mlev, lv, C.sexp[t]);
-            IO::set_ext(rr, C.orig[t], w0, w1, s3);
+            r.aux = pack_aux(mlev, lv, sexp_t);
+            IO::set_ext(rr, orig_t, w0, w1, s3);
             static_cast<TRec*>(T.out)[slot] = rr;
             T.out_key[slot] = key;
           }
@@ -949,7 +961,7 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) trace_kernel(const J
           book_d(SL, jobs, job, wid, L_RRG, Wn - W);
           W = Wn;
           C.W0[t] = C.W0[t] * (R)M;
-          C.sexp[t] += dl;
+          sexp_t += dl;
         } else {
           book_d(SL, jobs, job, wid, L_RRL, W);
           W = R(0);
@@ -1323,8 +1335,8 @@ static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_item
     trace_kernel<R, PEEL, EST, HITS, 1, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
                                                                                 total, cfg.refill, q, T);
   else if (mode == 2)
-    trace_kernel<R, PEEL, EST, HITS, 2, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
-                                                                                total, cfg.refill, q, T);
+    trace_kernel<R, PEEL, EST, HITS, 2, LEVELS><<<cfg.blocks_tiled, cfg.block, 0, s>>>(jobs, items, n_items, counter,
+                                                                                      total, cfg.refill, q, T);
   else
     trace_kernel<R, PEEL, EST, HITS, 0, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
                                                                                 total, cfg.refill, q, T);
@@ -1341,7 +1353,7 @@ static cudaError_t launch_split(const JobDev* jobs, const ItemDev* items, int n_
         <<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill, q, *tr);
   else
     trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2, false, true>
-        <<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill, q, *tr);
+        <<<cfg.blocks_tiled, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill, q, *tr);
   return cudaGetLastError();
 }
 
@@ -1593,13 +1605,18 @@ cudaError_t build_peel_table(const JobDev* job_dev, const PeelTabSpec& spec, dou
 }
 
 template <typename R, bool PEEL>
-static cudaError_t occ_t(int block, int* n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 0>, block, 0);
+static cudaError_t occ_t(int block, int* n, int mode) {
+  return mode == 2
+             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2>,
+                                                             block, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 0>,
+                                                             block, 0);
 }
 
-cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm) {
-  if (precision == 64) return peel ? occ_t<double, true>(block, blocks_per_sm) : occ_t<double, false>(block, blocks_per_sm);
-  return peel ? occ_t<float, true>(block, blocks_per_sm) : occ_t<float, false>(block, blocks_per_sm);
+cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm, int mode) {
+  if (precision == 64)
+    return peel ? occ_t<double, true>(block, blocks_per_sm, mode) : occ_t<double, false>(block, blocks_per_sm, mode);
+  return peel ? occ_t<float, true>(block, blocks_per_sm, mode) : occ_t<float, false>(block, blocks_per_sm, mode);
 }
 
 cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, const double* origins,
