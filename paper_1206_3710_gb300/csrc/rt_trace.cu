@@ -388,20 +388,30 @@ __device__ __forceinline__ int crossed_grid_level(const Geo<R>& g, int a, R dx, 
 #define RT_FP32_MIN_BLOCKS 4
 #endif
 #ifndef RT_FP32_TILED_MIN_BLOCKS
-#define RT_FP32_TILED_MIN_BLOCKS 3
+#define RT_FP32_TILED_MIN_BLOCKS 4
 #endif
-// Resident 256-thread blocks per SM the register allocation is sized for.
-// The tiled rounds (mode 2) run on L2-resident cells: there 3 blocks of
-// 80-register threads beat 4 blocks of 64 registers with spills (786 against
-// 861 ms for the cloud's rounds); the untiled tracer gathers from HBM and
-// keeps 4 blocks for latency hiding.
+// Resident blocks per SM the register allocation is sized for.  The tiled
+// rounds (mode 2) run on L2-resident cells and wait on their node loads: 4
+// blocks of 224 threads at 72 registers (28 warps, almost no spills) beat 3
+// blocks of 256 at 80 registers (24 warps; 788 against 798 ms for the
+// cloud's rounds), which beat 4 blocks of 256 at 64 registers with spills
+// (861 ms); the untiled tracer keeps 4 blocks of 256.
+#ifndef RT_FP32_TILED_BLOCK
+#define RT_FP32_TILED_BLOCK 224
+#endif
 template <typename R, int MODE>
 struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? (MODE == 2 ? RT_FP32_TILED_MIN_BLOCKS : RT_FP32_MIN_BLOCKS) : 2;
 };
+// threads per block the tracer is compiled for (the FP32 tiled rounds may
+// use fewer than 256 to fit one more block per SM)
+template <typename R, int MODE>
+struct MaxThreads {
+  static constexpr int value = (sizeof(R) == 4 && MODE == 2) ? RT_FP32_TILED_BLOCK : 256;
+};
 
 template <typename R, bool PEEL, int EST, bool HITS, int MODE, bool LEVELS = false, bool SPLIT = false>
-__global__ void __launch_bounds__(256, MinBlocks<R, MODE>::value) trace_kernel(const JobDev* __restrict__ jobs,
+__global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>::value) trace_kernel(const JobDev* __restrict__ jobs,
                                                                          const ItemDev* __restrict__ items,
                                                                          int n_items,
                                                                          unsigned long long* __restrict__ counter,
@@ -1335,8 +1345,8 @@ static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_item
     trace_kernel<R, PEEL, EST, HITS, 1, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
                                                                                 total, cfg.refill, q, T);
   else if (mode == 2)
-    trace_kernel<R, PEEL, EST, HITS, 2, LEVELS><<<cfg.blocks_tiled, cfg.block, 0, s>>>(jobs, items, n_items, counter,
-                                                                                      total, cfg.refill, q, T);
+    trace_kernel<R, PEEL, EST, HITS, 2, LEVELS><<<cfg.blocks_tiled, std::min(cfg.block, MaxThreads<R, 2>::value), 0, s>>>(
+        jobs, items, n_items, counter, total, cfg.refill, q, T);
   else
     trace_kernel<R, PEEL, EST, HITS, 0, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
                                                                                 total, cfg.refill, q, T);
@@ -1353,7 +1363,8 @@ static cudaError_t launch_split(const JobDev* jobs, const ItemDev* items, int n_
         <<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill, q, *tr);
   else
     trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2, false, true>
-        <<<cfg.blocks_tiled, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill, q, *tr);
+        <<<cfg.blocks_tiled, std::min(cfg.block, MaxThreads<R, 2>::value), 0, s>>>(jobs, items, n_items, counter,
+                                                                                  total, cfg.refill, q, *tr);
   return cudaGetLastError();
 }
 
@@ -1608,7 +1619,7 @@ template <typename R, bool PEEL>
 static cudaError_t occ_t(int block, int* n, int mode) {
   return mode == 2
              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2>,
-                                                             block, 0)
+                                                             std::min(block, MaxThreads<R, 2>::value), 0)
              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 0>,
                                                              block, 0);
 }
