@@ -41,8 +41,8 @@ BYTES_IMAGE_DEPOSIT = 16        # FP64 pixel read-modify-write
 # the deferred peel-off kernel on the default molecular cloud workload, from
 # a single-pass ncu capture of the current kernels (set to None whenever a
 # kernel changes until it is captured again)
-NCU_TRAFFIC_PER_LAUNCH = (201.0e9 + 143.3e9 + 13.9e9 + 34.0e9) / 2
-NCU_PEEL_TRAFFIC_PER_LAUNCH = (113.3e9 + 1.3e9) / 2
+NCU_TRAFFIC_PER_LAUNCH = (182.02e9 + 153.36e9 + 0.01e9 + 33.21e9) / 2
+NCU_PEEL_TRAFFIC_PER_LAUNCH = (102.59e9 + 1.17e9) / 2
 
 
 def parse():
@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--sub-level", type=int, default=-1,
                     help="disc: compare full Lambda iterations with subiterations below this level")
     ap.add_argument("--ali", action="store_true", help="disc subiterations: also 30 full ALI steps")
+    ap.add_argument("--ali-min", type=int, nargs="+", default=[100],
+                    help="disc ALI: minimum packages a cell sends for its diagonal operator (one run per value)")
     ap.add_argument("--split-runs", type=int, default=20, help="split: runs with and without resampling")
     ap.add_argument("--split-packets", type=int, default=2_000_000, help="split: initial packages per run")
     ap.add_argument("--merge-packets", type=int, default=20_000_000, help="merge: packages per wavelength")

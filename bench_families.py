@@ -78,20 +78,22 @@ def run_disc_subiter(a, rt, synth, ctx, torch):
                                  select_frac=0.25, flux_frac=a.flux_frac, **kw)
     ali = None
     if a.ali:
-        T_ali = torch.zeros_like(T_full)
-        ra = rt.rt_lambda_subiterate(ctx, g, m.sources, m.optics, T_ali, sub_level=a.sub_level,
-                                     schedule=["full"] * a.iters, ali=True, **kw)
-        ta = T_ali.cpu().numpy()[leaf]
-        tfa = T_full.cpu().numpy()[leaf]
-        lv = synth_levels(m.tree)[leaf]
-        per_level = [[int(l), int((lv == l).sum()), round(float(tfa[lv == l].mean()), 2),
-                      round(float(ta[lv == l].mean()), 2)] for l in range(int(lv.max()) + 1) if (lv == l).any()]
-        ali = {"ms": ra["ms"], "history": ra["history"], "mean_T_K": float(ta.mean()),
-               "mean_T_full_K": float(tfa.mean()),
-               "mass_weighted_mean_dT_vs_full_K": float(np.sum(mass[leaf] * (ta - tfa)) / mass[leaf].sum()),
-               "per_level_leaves_meanT_full_ali": per_level,
-               # mass-weighted mean |absorbed - emitted| per unit mass after the last step
-               "imbalance_last_ali": ra["imbalance"][-1], "imbalance_last_full": rf["imbalance"][-1]}
+        ali = []
+        for amin in a.ali_min:
+            T_ali = torch.zeros_like(T_full)
+            ra = rt.rt_lambda_subiterate(ctx, g, m.sources, m.optics, T_ali, sub_level=a.sub_level,
+                                         schedule=["full"] * a.iters, ali=True, ali_min_packages=amin, **kw)
+            ta = T_ali.cpu().numpy()[leaf]
+            tfa = T_full.cpu().numpy()[leaf]
+            lv = synth_levels(m.tree)[leaf]
+            per_level = [[int(l), int((lv == l).sum()), round(float(tfa[lv == l].mean()), 2),
+                          round(float(ta[lv == l].mean()), 2)] for l in range(int(lv.max()) + 1) if (lv == l).any()]
+            ali.append({"ali_min_packages": amin, "ms": ra["ms"], "history": ra["history"],
+                        "mean_T_K": float(ta.mean()), "mean_T_full_K": float(tfa.mean()),
+                        "mass_weighted_mean_dT_vs_full_K": float(np.sum(mass[leaf] * (ta - tfa)) / mass[leaf].sum()),
+                        "per_level_leaves_meanT_full_ali": per_level,
+                        # mass-weighted mean |absorbed - emitted| per unit mass after the last step
+                        "imbalance_last_ali": ra["imbalance"][-1], "imbalance_last_full": rf["imbalance"][-1]})
     clocks = clk.stop()
     tf, ts = T_full.cpu().numpy()[leaf], T_sub.cpu().numpy()[leaf]
     w = mass[leaf]

@@ -125,6 +125,9 @@ def lib():
         L.orc_emission_per_mass.argtypes = [C.POINTER(_Dust), C.c_double]
         L.orc_dust_temperature.restype = C.c_int
         L.orc_dust_temperature.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Dust), C.c_int, C.c_void_p]
+        L.orc_dust_temperature_weighted.restype = C.c_int
+        L.orc_dust_temperature_weighted.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Dust), C.c_int,
+                                                    C.c_void_p]
         L.orc_dust_emission.restype = C.c_int
         L.orc_dust_emission.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Dust), C.c_void_p]
         _lib = L
@@ -378,6 +381,20 @@ def dust_temperature(tree: Tree, absorbed_total, lambda_um, kappa_abs, dnu, T_mi
     return T
 
 
+def dust_temperature_weighted(tree: Tree, rhs, weights, lambda_um, kappa_abs, dnu, T_min=2.7, T_max=3000.0,
+                              n_threads=1) -> np.ndarray:
+    """Per leaf the T with sum_b weights[b][c] E_b(T) = rhs[c] (bisection)."""
+    keep = _Keep()
+    d = _dust(lambda_um, kappa_abs, dnu, T_min, T_max, keep)
+    r = keep.arr(rhs, np.float64)
+    w = keep.arr(weights, np.float64)
+    T = np.zeros(tree.n_cells)
+    rc = lib().orc_dust_temperature_weighted(tree.handle, _p(r), _p(w), C.byref(d), n_threads, _p(T))
+    if rc != 0:
+        raise RuntimeError("orc_dust_temperature_weighted failed")
+    return T
+
+
 def dust_emission(tree: Tree, T, lambda_um, kappa_abs, dnu) -> np.ndarray:
     keep = _Keep()
     d = _dust(lambda_um, kappa_abs, dnu, 2.7, 3000.0, keep)
@@ -461,14 +478,16 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
     leave the run where they reach a grid of level <= L, and only I_i for
     i > L are replaced.  After each step T follows from I_stars + sum_i I_i.
     ``ali``: the accelerated Lambda iteration with the diagonal operator of
-    Eq. 3: each step also sums, per cell, the energy its own packages leave
-    in it (self), the energy they carried (emitted) and their number;
-    Lambda_cc = self / emitted is the fraction of a cell's emission it
-    re-absorbs, capped at 0.999, and T solves E(T) (1 - Lambda_cc) =
-    A - Lambda_cc emitted (= A - self below the cap).  The diagonal operator
-    is used in the cells that sent at least ``ali_min_packages`` packages;
-    the others take the plain step (Lambda_cc = 0), whose expectation
-    includes their rare self-absorbed packages.
+    Eq. 3, per frequency (Sect. 3.1: the system decouples into one equation
+    per cell with N_freq unknowns): each step also sums, per bin and cell,
+    the energy the cell's own packages leave in it (self_b) and the energy
+    they carried (emitted_b), and per cell their number; Lambda_b =
+    self_b / emitted_b is the fraction of the cell's bin-b emission it
+    re-absorbs, capped at 0.999, and T solves
+    sum_b (1 - Lambda_b) E_b(T) = A - sum_b Lambda_b emitted_b.  The
+    diagonal operator is used in the cells that sent at least
+    ``ali_min_packages`` packages; the others take the plain step, whose
+    expectation includes their rare self-absorbed packages.
     Returns T and the per-step max dT/T over cells with >= ``min_hits`` hits."""
     kabs = (1 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
     lam = np.asarray(optics.lambda_um)
@@ -496,8 +515,9 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
             npk = np.where(em.sum(axis=1) > 0, packets_dust, 0).astype(np.int64)
         else:
             npk = packets_by_energy(em.sum(axis=1), total)
-        self_abs = np.zeros(tree.n_cells) if ali else None
-        self_emit = np.zeros(tree.n_cells) if ali else None
+        nlam = len(optics.kappa_ext)
+        self_abs = np.zeros((nlam, tree.n_cells)) if ali else None
+        self_emit = np.zeros((nlam, tree.n_cells)) if ali else None
         self_n = np.zeros(tree.n_cells) if ali else None
         rd = trace(tree, [_DustSource(em)], optics, npk, seed=seed, iter_=1, per_lambda=False,
                    n_threads=n_threads, validation=True, per_level=True,
@@ -510,10 +530,12 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
             I[L + 1:] = rd["absorbed"][L + 1:]
         A = A_star + I.sum(axis=0)
         if ali:
-            use = (self_n >= max(ali_min_packages, 1)) & (self_emit > 0)
-            lam_cc = np.minimum(np.where(use, self_abs / np.where(use, self_emit, 1.0), 0.0), 0.999)
-            A = (A - lam_cc * self_emit) / (1.0 - lam_cc)
-        Tn = dust_temperature(tree, A, lam, kabs, dnu, T_min, T_max, n_threads)
+            use = (self_n >= max(ali_min_packages, 1))[None, :] & (self_emit > 0)
+            lam_b = np.minimum(np.where(use, self_abs / np.where(use, self_emit, 1.0), 0.0), 0.999)
+            rhs = A - (lam_b * self_emit).sum(axis=0)
+            Tn = dust_temperature_weighted(tree, rhs, 1.0 - lam_b, lam, kabs, dnu, T_min, T_max, n_threads)
+        else:
+            Tn = dust_temperature(tree, A, lam, kabs, dnu, T_min, T_max, n_threads)
         mask = (hits + rd["hits"].sum(axis=0)) >= min_hits
         rel = np.abs(Tn - T)[mask] / np.maximum(T[mask], 1e-300)
         history.append(float(rel.max()) if rel.size else 0.0)

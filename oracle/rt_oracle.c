@@ -730,7 +730,8 @@ static int follow(trace_worker* w, orc_path* P, int64_t p, int bin, double kext_
         double ts = tau / ksca;
         double dep = -W * expm1(-kabs * ts);   /* W (1 - e^-dtau) without cancellation */
         deposit(w, slot, p, dep);
-        if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], dep);
+        if (prm->self_absorbed && n->id == origin)
+          atomic_add_double(&prm->self_absorbed[(int64_t)bin * nc + n->id], dep);
         w->led.absorbed += dep;
         W *= exp(-kabs * ts);
         for (int b = 0; b < 3; ++b) x[b] += ts * d[b];
@@ -760,7 +761,8 @@ static int follow(trace_worker* w, orc_path* P, int64_t p, int bin, double kext_
         tau -= ksca * s;
         double dep = -W * expm1(-kabs * s);
         deposit(w, slot, p, dep);
-        if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], dep);
+        if (prm->self_absorbed && n->id == origin)
+          atomic_add_double(&prm->self_absorbed[(int64_t)bin * nc + n->id], dep);
         w->led.absorbed += dep;
         W *= exp(-kabs * s);
         if (s > 0) { ncross += 1; w->led.n_cross += 1; }
@@ -783,7 +785,8 @@ static int follow(trace_worker* w, orc_path* P, int64_t p, int bin, double kext_
           d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
         } else {
           deposit(w, slot, p, W);
-          if (prm->self_absorbed && n->id == origin) atomic_add_double(&prm->self_absorbed[n->id], W);
+          if (prm->self_absorbed && n->id == origin)
+            atomic_add_double(&prm->self_absorbed[(int64_t)bin * nc + n->id], W);
           w->led.absorbed += W;
           W = 0;
           fate = 3;
@@ -1074,7 +1077,7 @@ static void trace_one(trace_worker* w, int64_t p) {
     double u0 = uni(&rs);
     int64_t c = search_cdf(cdf, nc, u0 * cdf[nc - 1]);
     origin = c;
-    if (prm->self_emitted) atomic_add_double(&prm->self_emitted[c], W0);
+    if (prm->self_emitted) atomic_add_double(&prm->self_emitted[(int64_t)bin * nc + c], W0);
     if (prm->self_count) atomic_add_double(&prm->self_count[c], 1.0);
     const orc_node* n = &t->nodes[c];
     double u1 = uni(&rs), u2 = uni(&rs), u3 = uni(&rs);
@@ -1327,6 +1330,74 @@ int orc_dust_temperature(const orc_tree* t, const double* absorbed_total, const 
   if (NT == 1) temp_thread(&ws[0]);
   else {
     for (int i = 0; i < NT; ++i) pthread_create(&th[i], NULL, temp_thread, &ws[i]);
+    for (int i = 0; i < NT; ++i) pthread_join(th[i], NULL);
+  }
+  free(ws); free(th);
+  return 0;
+}
+
+/* The temperature of the ALI step with a diagonal operator per frequency
+ * (Eq. 3; Sect. 3.1: the system decouples into one equation per cell):
+ * sum_b w_b E_b(T) = rhs per leaf, with E_b(T) = 4 pi rho V kappa_b B_b(T)
+ * dnu_b and weights w_b = 1 - Lambda_b ([n_lambda][n_cells]), by bisection
+ * in T to 1e-13 relative, clamped to [T_min, T_max]. */
+typedef struct {
+  const orc_tree* t;
+  const double* rhs;
+  const double* w;
+  const orc_dust* d;
+  double* T;
+  int64_t c0, c1;
+} wtemp_work;
+
+static double weighted_emission(const orc_dust* d, const double* w, int64_t nc, int64_t c, double T) {
+  double s = 0.0;
+  for (int b = 0; b < d->n_lambda; ++b) {
+    double nu = C_CGS / (d->lambda_um[b] * 1e-4);
+    s += w[(int64_t)b * nc + c] * d->kappa_abs[b] * planck_nu(nu, T) * d->dnu[b];
+  }
+  return 4.0 * ORC_PI * s;
+}
+
+static void* wtemp_thread(void* arg) {
+  wtemp_work* w = (wtemp_work*)arg;
+  const orc_tree* t = w->t;
+  const int64_t nc = t->n_cells;
+  for (int64_t c = w->c0; c < w->c1; ++c) {
+    const orc_node* n = &t->nodes[c];
+    if (n->child) { w->T[c] = 0.0; continue; }
+    double h = t->h0 * n->size;
+    double mass = n->rho * h * h * h;
+    if (!(mass > 0) || !(w->rhs[c] > 0)) { w->T[c] = w->d->T_min; continue; }
+    double target = w->rhs[c] / mass;
+    if (target <= weighted_emission(w->d, w->w, nc, c, w->d->T_min)) { w->T[c] = w->d->T_min; continue; }
+    if (target >= weighted_emission(w->d, w->w, nc, c, w->d->T_max)) { w->T[c] = w->d->T_max; continue; }
+    double lo = w->d->T_min, hi = w->d->T_max;
+    while (hi - lo > 1e-13 * lo) {
+      double mid = 0.5 * (lo + hi);
+      if (weighted_emission(w->d, w->w, nc, c, mid) < target) lo = mid;
+      else hi = mid;
+    }
+    w->T[c] = 0.5 * (lo + hi);
+  }
+  return NULL;
+}
+
+int orc_dust_temperature_weighted(const orc_tree* t, const double* rhs, const double* weights, const orc_dust* d,
+                                  int n_threads, double* T) {
+  if (!t || !rhs || !weights || !d || !T || d->n_lambda <= 0 || !(d->T_min > 0) || !(d->T_max > d->T_min))
+    return -1;
+  int NT = n_threads > 0 ? n_threads : 1;
+  wtemp_work* ws = (wtemp_work*)calloc((size_t)NT, sizeof(wtemp_work));
+  pthread_t* th = (pthread_t*)calloc((size_t)NT, sizeof(pthread_t));
+  for (int i = 0; i < NT; ++i) {
+    ws[i].t = t; ws[i].rhs = rhs; ws[i].w = weights; ws[i].d = d; ws[i].T = T;
+    ws[i].c0 = t->n_cells * i / NT;
+    ws[i].c1 = t->n_cells * (i + 1) / NT;
+  }
+  if (NT == 1) wtemp_thread(&ws[0]);
+  else {
+    for (int i = 0; i < NT; ++i) pthread_create(&th[i], NULL, wtemp_thread, &ws[i]);
     for (int i = 0; i < NT; ++i) pthread_join(th[i], NULL);
   }
   free(ws); free(th);

@@ -107,10 +107,11 @@ typedef struct {
   int confine_level;           /* >= 0: a package that reaches a grid of this level or shallower
                                   (it left the subtree of its level-L ancestor) leaves the run,
                                   booked as escaped; < 0: no confinement */
-  double* self_absorbed;       /* optional [n_cells]: energy a dust package deposits in its own
-                                  emission cell, summed per cell (the diagonal of Lambda, Eq. 3) */
-  double* self_emitted;        /* with self_absorbed: energy of the dust packages emitted per cell */
-  double* self_count;          /* with self_absorbed: number of dust packages emitted per cell */
+  double* self_absorbed;       /* optional [n_lambda][n_cells]: energy a dust package deposits in its
+                                  own emission cell, per bin and cell (the diagonal of Lambda, Eq. 3) */
+  double* self_emitted;        /* with self_absorbed: [n_lambda][n_cells] energy of the dust packages
+                                  emitted per bin and cell */
+  double* self_count;          /* with self_absorbed: [n_cells] number of dust packages emitted per cell */
   /* Resampling at grid boundaries (Sect. 2.3): a package entering a cell dl
    * grid levels deeper than its last cell is split into split_factor^dl
    * packages; one leaving for a cell dl levels shallower survives with
@@ -182,6 +183,11 @@ int orc_dust_temperature(const orc_tree* t, const double* absorbed_total, const 
                          int n_threads, double* T);
 /* Per leaf and bin: 4 pi rho V kappa_abs,i B_nu_i(T) dnu_i, [n_lambda][n_cells]. */
 int orc_dust_emission(const orc_tree* t, const double* T, const orc_dust* d, double* emission);
+/* ALI with a per-frequency diagonal operator: per leaf, the T in
+ * [T_min, T_max] with sum_b weights[b][c] E_b(T) = rhs[c] (E_b: the cell's
+ * emission in bin b; weights = 1 - Lambda_b). */
+int orc_dust_temperature_weighted(const orc_tree* t, const double* rhs, const double* weights, const orc_dust* d,
+                                  int n_threads, double* T);
 
 #ifdef __cplusplus
 }

@@ -1455,8 +1455,11 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   const size_t fb = sizeof(double) * (size_t)nc, hb = sizeof(unsigned int) * (size_t)nc;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   // A_star, A, T_prev, T_emit | I (levels) | I_step (levels) | hits_star, hits_step | scalars
-  // (scal[0] max dT/T, scal[1..6] level_imbalance sums) | self, A_ali, emitted, count (ALI)
-  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024 + 3 * al(fb) + al(hb));
+  // (scal[0] max dT/T, scal[1..6] level_imbalance sums) | ALI: self, emitted, weights (bins x
+  // cells each), right-hand side, package count, use flag
+  const int nlb = op->n_lambda;
+  const size_t ali_bytes = sp->ali ? 3 * al(fb * nlb) + al(fb) + al(hb) + al((size_t)nc) : 0;
+  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024 + ali_bytes);
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(ctx->lam.p);
   double* A_star = reinterpret_cast<double*>(base);
@@ -1468,11 +1471,13 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   unsigned int* hits_star = reinterpret_cast<unsigned int*>(base + 4 * al(fb) + 2 * al(fb * nlev));
   unsigned int* hits_step = reinterpret_cast<unsigned int*>(base + 4 * al(fb) + 2 * al(fb * nlev) + al(hb));
   double* scal = reinterpret_cast<double*>(base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb));
-  double* self_abs = reinterpret_cast<double*>(base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
-  double* A_ali = reinterpret_cast<double*>(base + 5 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
-  double* self_emit = reinterpret_cast<double*>(base + 6 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
-  unsigned int* self_cnt =
-      reinterpret_cast<unsigned int*>(base + 7 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024);
+  char* ali_base = base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024;
+  double* self_abs = reinterpret_cast<double*>(ali_base);
+  double* self_emit = reinterpret_cast<double*>(ali_base + al(fb * nlb));
+  double* ali_w = reinterpret_cast<double*>(ali_base + 2 * al(fb * nlb));
+  double* ali_rhs = reinterpret_cast<double*>(ali_base + 3 * al(fb * nlb));
+  unsigned int* self_cnt = reinterpret_cast<unsigned int*>(ali_base + 3 * al(fb * nlb) + al(fb));
+  uint8_t* ali_use = reinterpret_cast<uint8_t*>(ali_base + 3 * al(fb * nlb) + al(fb) + al(hb));
   CK(cudaMemsetAsync(A_star, 0, fb, s));
   CK(cudaMemsetAsync(hits_star, 0, hb, s));
   CK(cudaMemsetAsync(I, 0, fb * nlev, s));
@@ -1573,8 +1578,8 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
     TD.levels = 1;
     TD.confine = kind == 1 ? L : -1;
     if (sp->ali) {
-      CK(cudaMemsetAsync(self_abs, 0, fb, s));
-      CK(cudaMemsetAsync(self_emit, 0, fb, s));
+      CK(cudaMemsetAsync(self_abs, 0, fb * nlb, s));
+      CK(cudaMemsetAsync(self_emit, 0, fb * nlb, s));
       CK(cudaMemsetAsync(self_cnt, 0, hb, s));
       TD.self_abs = self_abs;
       TD.self_emit = self_emit;
@@ -1591,12 +1596,14 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
     rc = upload();
     if (rc) return rc;
     CK(level_imbalance(A, T_prev, g->child, g->rho64, g->level, g->h0, tab, n_table, nc, L, scal + 1, s));
-    if (sp->ali) {
-      // Eq. 3: the cell's own re-absorption solved with the new temperature
-      CK(ali_field(A, self_abs, self_emit, self_cnt, (unsigned)std::max(1, sp->ali_min_packages), nc, A_ali, s));
-      rc = solve(A_ali);
-    } else {
-      rc = solve(A);
+    rc = solve(A);
+    if (!rc && sp->ali) {
+      // Eq. 3 per frequency: the cells' own re-absorption solved with the
+      // new temperature, from the plain solve's T
+      CK(ali_weights(A, self_abs, self_emit, self_cnt, (unsigned)std::max(1, sp->ali_min_packages), nlb, nc, ali_rhs,
+                     ali_w, ali_use, s));
+      CK(dust_temperature_weighted(ali_rhs, ali_w, ali_use, nc, g->child, g->rho64, g->level, g->h0, lam, kab, dnu,
+                                   du->n_lambda, du->T_min, du->T_max, T_dev, s));
     }
     if (rc) return rc;
     CK(max_rel_change(T_dev, T_prev, hits_step, g->child, nc, lp->min_hits, scal, s));

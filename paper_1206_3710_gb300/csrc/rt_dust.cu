@@ -283,31 +283,106 @@ __device__ __forceinline__ double table_emission(double T, const double* __restr
   return exp((2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + tt) * m0 + (-2 * t3 + 3 * t2) * y1 + (t3 - t2) * m1);
 }
 
-// Eq. 3 with the diagonal operator: Lambda_cc is the fraction of the energy a
-// cell's own packages carried that they left in it (self / emitted, a ratio
-// of two tallies of the same packages, so the package-count noise cancels),
-// capped at 0.999, and the field solved for is (A - Lambda_cc emitted) /
-// (1 - Lambda_cc): the same operator on both sides, = (A - self) / (1 -
-// Lambda_cc) below the cap.  Only cells that sent at least min_count
-// packages use it; the others keep A, the plain step, whose expectation
-// includes the rare packages a weakly emitting cell sends to itself.
-__global__ void ali_field_kernel(const double* __restrict__ A, const double* __restrict__ self,
-                                 const double* __restrict__ emitted, const unsigned int* __restrict__ count,
-                                 unsigned int min_count, long long n, double* __restrict__ out) {
+// Eq. 3 with a diagonal operator per frequency (Sect. 3.1: the system
+// decouples into one equation per cell, with one unknown per frequency):
+// Lambda_b of a cell is the fraction of the energy its own bin-b packages
+// carried that they left in it (self_b / emitted_b, two tallies of the same
+// packages), capped at 0.999; the cell's temperature then solves
+//   sum_b (1 - Lambda_b) E_b(T) = A - sum_b Lambda_b emitted_b.
+// Only cells that sent at least min_count packages use it (flag 1); the
+// others keep the plain step E(T) = A.
+__global__ void ali_weights_kernel(const double* __restrict__ A, const double* __restrict__ self,
+                                   const double* __restrict__ emitted, const unsigned int* __restrict__ count,
+                                   unsigned int min_count, int nl, long long n, double* __restrict__ rhs,
+                                   double* __restrict__ w, uint8_t* __restrict__ use) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
-  double a = A[c];
-  const double e = emitted[c];
-  if (e > 0.0 && count[c] >= min_count) {
-    const double lam = fmin(self[c] / e, 0.999);
-    a = (a - lam * e) / (1.0 - lam);
+  const bool on = count[c] >= min_count;
+  double r = A[c];
+  for (int b = 0; b < nl; ++b) {
+    const double e = emitted[(long long)b * n + c];
+    const double lam = (on && e > 0.0) ? fmin(self[(long long)b * n + c] / e, 0.999) : 0.0;
+    r -= lam * e;
+    w[(long long)b * n + c] = 1.0 - lam;
   }
-  out[c] = a;
+  rhs[c] = r;
+  use[c] = on ? 1 : 0;
 }
 
-cudaError_t ali_field(const double* A, const double* self, const double* emitted, const unsigned int* count,
-                      unsigned int min_count, long long n, double* out, cudaStream_t s) {
-  ali_field_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, emitted, count, min_count, n, out);
+cudaError_t ali_weights(const double* A, const double* self, const double* emitted, const unsigned int* count,
+                        unsigned int min_count, int nl, long long n, double* rhs, double* w, uint8_t* use,
+                        cudaStream_t s) {
+  ali_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, emitted, count, min_count, nl, n, rhs, w,
+                                                                  use);
+  return cudaGetLastError();
+}
+
+// sum_b w_b E_b(T) per unit mass and its derivative
+__device__ __forceinline__ double weighted_emission(const double* lam, const double* kabs, const double* dnu,
+                                                    const double* __restrict__ w, long long n, long long c, int nl,
+                                                    double T, double* dEdT) {
+  double s = 0.0, ds = 0.0;
+  for (int b = 0; b < nl; ++b) {
+    double B, dB;
+    planck_and_deriv(C_CGS / (lam[b] * 1e-4), T, &B, &dB);
+    const double k = w[(long long)b * n + c] * kabs[b] * dnu[b];
+    s += k * B;
+    ds += k * dB;
+  }
+  *dEdT = FOUR_PI * ds;
+  return FOUR_PI * s;
+}
+
+// The ALI cells' temperatures: safeguarded Newton (bisection when a step
+// leaves the bracket) on sum_b w_b E_b(T) = rhs / (rho V), starting from the
+// plain solve's T; T_min / T_max where the target lies outside.
+__global__ void temperature_weighted_kernel(const double* __restrict__ rhs, const double* __restrict__ w,
+                                            const uint8_t* __restrict__ use, long long n,
+                                            const uint32_t* __restrict__ child, const double* __restrict__ rho64,
+                                            const uint8_t* __restrict__ level, double h0,
+                                            const double* __restrict__ lam, const double* __restrict__ kabs,
+                                            const double* __restrict__ dnu, int nl, double Tmin, double Tmax,
+                                            double* __restrict__ T) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n || !use[c] || child[c]) return;
+  const double h = ldexp(h0, -(int)level[c]);
+  const double mass = rho64[c] * h * h * h;
+  if (!(mass > 0.0) || !(rhs[c] > 0.0)) {
+    T[c] = Tmin;
+    return;
+  }
+  const double target = rhs[c] / mass;
+  double d;
+  if (target <= weighted_emission(lam, kabs, dnu, w, n, c, nl, Tmin, &d)) {
+    T[c] = Tmin;
+    return;
+  }
+  if (target >= weighted_emission(lam, kabs, dnu, w, n, c, nl, Tmax, &d)) {
+    T[c] = Tmax;
+    return;
+  }
+  double lo = Tmin, hi = Tmax;
+  double t = T[c] > Tmin && T[c] < Tmax ? T[c] : sqrt(Tmin * Tmax);
+  for (int it = 0; it < 200; ++it) {
+    double dE;
+    const double f = weighted_emission(lam, kabs, dnu, w, n, c, nl, t, &dE) - target;
+    if (f < 0.0) lo = t;
+    else hi = t;
+    double tn = dE > 0.0 ? t - f / dE : 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    const double step = fabs(tn - t);
+    t = tn;
+    if (step <= 1e-14 * t || (hi - lo) <= 1e-14 * lo) break;
+  }
+  T[c] = t;
+}
+
+cudaError_t dust_temperature_weighted(const double* rhs, const double* w, const uint8_t* use, long long n,
+                                      const uint32_t* child, const double* rho64, const uint8_t* level, double h0,
+                                      const double* lam, const double* kabs, const double* dnu, int nl, double Tmin,
+                                      double Tmax, double* T, cudaStream_t s) {
+  temperature_weighted_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(rhs, w, use, n, child, rho64, level, h0, lam,
+                                                                          kabs, dnu, nl, Tmin, Tmax, T);
   return cudaGetLastError();
 }
 

@@ -179,8 +179,9 @@ struct JobDev {
   int poly_n;
   int pad3;
   // ALI (Eq. 3): energy a dust package leaves in its own emission cell, per
-  // cell (the diagonal of Lambda), and the energy of the dust packages each
-  // cell emitted; NULL: not tallied
+  // bin and cell [n_lambda][n_cells] (the diagonal of Lambda per
+  // frequency), and the energy of the dust packages each cell emitted in
+  // each bin; NULL: not tallied
   double* self_abs;
   double* self_emit;
   unsigned int* self_cnt;  // dust packages emitted per cell
@@ -319,8 +320,16 @@ cudaError_t sum_levels(const double* I, int n_levels, long long n, const double*
 // ALI temperature input: A' = (A - self) / (1 - self / (rho V E(T_emit))) per
 // leaf (A elsewhere), the field a cell would absorb once its own emission is
 // in equilibrium with it (Eq. 3 with a diagonal Lambda_0)
-cudaError_t ali_field(const double* A, const double* self, const double* emitted, const unsigned int* count,
-                      unsigned int min_count, long long n, double* out, cudaStream_t s);
+// ALI per frequency (Eq. 3): weights w_b = 1 - Lambda_b [nl][n], the
+// right-hand side A - sum_b Lambda_b emitted_b and the cells that use it
+cudaError_t ali_weights(const double* A, const double* self, const double* emitted, const unsigned int* count,
+                        unsigned int min_count, int nl, long long n, double* rhs, double* w, uint8_t* use,
+                        cudaStream_t s);
+// the ALI cells' temperatures from sum_b w_b E_b(T) = rhs (starts from T)
+cudaError_t dust_temperature_weighted(const double* rhs, const double* w, const uint8_t* use, long long n,
+                                      const uint32_t* child, const double* rho64, const uint8_t* level, double h0,
+                                      const double* lam, const double* kabs, const double* dnu, int nl, double Tmin,
+                                      double Tmax, double* T, cudaStream_t s);
 cudaError_t level_imbalance(const double* A, const double* T, const uint32_t* child, const double* rho64,
                             const uint8_t* level, double h0, const double* table, int n_table, long long n, int L,
                             double* out, cudaStream_t s);

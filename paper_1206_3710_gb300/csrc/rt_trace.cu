@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           if (LEVELS) {
             mlev = aux_mlev(r.aux);
             orig_t = x_orig;
-            selfb = J.self_abs;
+            selfb = J.self_abs ? J.self_abs + (long long)bin * J.n_cells : nullptr;
           }
           absb = J.absorbed ? J.absorbed + (long long)(LEVELS ? mlev : (J.abs_bins > 1 ? bin : 0)) * J.n_cells
                             : nullptr;
@@ -760,9 +760,9 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
             mlev = g.lev;
             absb = J.absorbed ? J.absorbed + (long long)mlev * J.n_cells : nullptr;
             orig_t = I.kind == RT_SRC_DUST ? cur.pending : 0xFFFFFFFFu;
-            selfb = J.self_abs;
+            selfb = J.self_abs ? J.self_abs + (long long)bin * J.n_cells : nullptr;
             if (selfb && J.self_emit && I.kind == RT_SRC_DUST) {
-              atomicAdd(J.self_emit + cur.pending, widen(W));
+              atomicAdd(J.self_emit + (long long)bin * J.n_cells + cur.pending, widen(W));
               atomicAdd(J.self_cnt + cur.pending, 1u);
             }
           }

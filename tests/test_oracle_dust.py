@@ -198,10 +198,11 @@ def test_p13_self_absorption_and_ali(orc):
     kabs = (1 - optics.albedo) * optics.kappa_ext
     T0 = np.array([100.0])
     em = orc.dust_emission(tree, T0, optics.lambda_um, kabs, optics.dnu)
-    self_abs = np.zeros(1)
-    r = orc.trace(tree, [orc._DustSource(em)], optics, 4000, seed=2, iter_=1, per_lambda=False,
+    self_abs = np.zeros((lam.size, 1))
+    r = orc.trace(tree, [orc._DustSource(em)], optics, 4000, seed=2, iter_=1, per_lambda=True,
                   self_absorbed=self_abs)
-    assert self_abs[0] == pytest.approx(r["absorbed"][0][0], rel=1e-12) and self_abs[0] > 0
+    np.testing.assert_allclose(self_abs[:, 0], r["absorbed"][:, 0], rtol=1e-12)
+    assert self_abs.sum() > 0
     kw = dict(seed=3, schedule=["full"] * 5, sub_level=0, min_hits=0.0, dust_per_bin=True)
     T_plain, h_plain, _ = orc.lambda_subiterate(tree, star, optics, 2000, 2000, **kw)
     T_ali, h_ali, _ = orc.lambda_subiterate(tree, star, optics, 2000, 2000, ali=True, **kw)
@@ -219,18 +220,52 @@ def test_p13_self_absorption_bounded(orc):
     level, leaf = tree.cells()
     T = np.where(leaf, 200.0, 0.0)
     em = _dust_source(orc, tree, optics, T)
-    self_abs = np.zeros(tree.n_cells)
-    self_emit = np.zeros(tree.n_cells)
-    r = orc.trace(tree, [orc._DustSource(em)], optics, 3000, seed=8, iter_=1, per_lambda=False, self_absorbed=self_abs,
+    nl = len(optics.kappa_ext)
+    self_abs = np.zeros((nl, tree.n_cells))
+    self_emit = np.zeros((nl, tree.n_cells))
+    r = orc.trace(tree, [orc._DustSource(em)], optics, 3000, seed=8, iter_=1, per_lambda=True, self_absorbed=self_abs,
                   self_emitted=self_emit)
-    A = r["absorbed"][0]
+    A = r["absorbed"]
     assert np.all(self_abs <= A * (1 + 1e-12)) and self_abs.sum() > 0
     assert np.all(self_abs <= self_emit * (1 + 1e-12))
-    assert self_emit.sum() == pytest.approx(em.sum(), rel=1e-12)
-    assert np.all(self_emit[~leaf] == 0.0)
+    # every bin's packages carry that bin's emission between them
+    np.testing.assert_allclose(self_emit.sum(axis=1), em.sum(axis=1), rtol=1e-12)
+    assert np.all(self_emit[:, ~leaf] == 0.0)
     # the emitted tally is a multinomial draw around the emission: summed
     # over the leaves of a level it follows the level's share
     e = em.sum(axis=0)
     for lv in range(2):
         s = (level == lv) & leaf
-        assert self_emit[s].sum() == pytest.approx(e[s].sum(), rel=0.1)
+        assert self_emit[:, s].sum() == pytest.approx(e[s].sum(), rel=0.1)
+
+
+def test_p13_weighted_temperature_solve(orc):
+    """The ALI temperature solve, sum_b w_b E_b(T) = rhs: with a single
+    nonzero weight it inverts one bin's Planck term in closed form,
+    T = h nu / (k ln(1 + 2 h nu^3 w kappa dnu 4 pi m / (c^2 rhs))); with
+    uniform weights w it is the plain solve of rhs / w."""
+    desc, optics, _ = _sub_model()
+    tree = orc.Tree(desc)
+    level, leaf = tree.cells()
+    lam = np.asarray(optics.lambda_um)
+    kabs = (1 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
+    dnu = np.asarray(optics.dnu)
+    nl, nc = lam.size, tree.n_cells
+    h0 = desc.box[0] / desc.root[0]
+    mass = np.asarray(desc.density) * (h0 * 0.5 ** level) ** 3
+    T_true = np.where(leaf, np.random.default_rng(4).uniform(20.0, 800.0, nc), 0.0)
+    H, K, CL = 6.62607015e-27, 1.380649e-16, 2.99792458e10
+    b = 3
+    nu = CL / (lam[b] * 1e-4)
+    planck = 2 * H * nu ** 3 / CL ** 2 / np.expm1(H * nu / (K * np.where(leaf, T_true, 1e3)))
+    w = np.zeros((nl, nc))
+    w[b] = 0.37
+    rhs = np.where(leaf, w[b] * 4 * np.pi * mass * kabs[b] * planck * dnu[b], 0.0)
+    T = orc.dust_temperature_weighted(tree, rhs, w, lam, kabs, dnu, T_min=2.7, T_max=3000.0)
+    np.testing.assert_allclose(T[leaf], T_true[leaf], rtol=1e-11)
+    # uniform weights: the plain solve of rhs / w
+    A = np.where(leaf, np.random.default_rng(5).uniform(0.1, 10.0, nc) * mass, 0.0)
+    wu = np.full((nl, nc), 0.25)
+    Tw = orc.dust_temperature_weighted(tree, A, wu, lam, kabs, dnu)
+    Tp = orc.dust_temperature(tree, A / 0.25, lam, kabs, dnu)
+    np.testing.assert_allclose(Tw[leaf], Tp[leaf], rtol=1e-11)
