@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--sub-level", type=int, default=-1,
                     help="disc: compare full Lambda iterations with subiterations below this level")
     ap.add_argument("--ali", action="store_true", help="disc subiterations: also 30 full ALI steps")
+    ap.add_argument("--ali-max-lambda", type=float, nargs="+", default=[0.999],
+                    help="disc ALI: cap of Lambda_b (one run per value, with the first --ali-min)")
     ap.add_argument("--ali-min", type=int, nargs="+", default=[100],
                     help="disc ALI: minimum packages a cell sends for its diagonal operator (one run per value)")
     ap.add_argument("--split-runs", type=int, default=20, help="split: runs with and without resampling")

@@ -79,16 +79,19 @@ def run_disc_subiter(a, rt, synth, ctx, torch):
     ali = None
     if a.ali:
         ali = []
-        for amin in a.ali_min:
+        runs = [(amin, a.ali_max_lambda[0]) for amin in a.ali_min] + \
+            [(a.ali_min[0], cap) for cap in a.ali_max_lambda[1:]]
+        for amin, cap in runs:
             T_ali = torch.zeros_like(T_full)
             ra = rt.rt_lambda_subiterate(ctx, g, m.sources, m.optics, T_ali, sub_level=a.sub_level,
-                                         schedule=["full"] * a.iters, ali=True, ali_min_packages=amin, **kw)
+                                         schedule=["full"] * a.iters, ali=True, ali_min_packages=amin,
+                                         ali_max_lambda=cap, **kw)
             ta = T_ali.cpu().numpy()[leaf]
             tfa = T_full.cpu().numpy()[leaf]
             lv = synth_levels(m.tree)[leaf]
             per_level = [[int(l), int((lv == l).sum()), round(float(tfa[lv == l].mean()), 2),
                           round(float(ta[lv == l].mean()), 2)] for l in range(int(lv.max()) + 1) if (lv == l).any()]
-            ali.append({"ali_min_packages": amin, "ms": ra["ms"], "history": ra["history"],
+            ali.append({"ali_min_packages": amin, "ali_max_lambda": cap, "ms": ra["ms"], "history": ra["history"],
                         "mean_T_K": float(ta.mean()), "mean_T_full_K": float(tfa.mean()),
                         "mass_weighted_mean_dT_vs_full_K": float(np.sum(mass[leaf] * (ta - tfa)) / mass[leaf].sum()),
                         "per_level_leaves_meanT_full_ali": per_level,

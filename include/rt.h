@@ -472,10 +472,12 @@ typedef struct {
   int ali;                 /* 1: accelerated Lambda iteration with the diagonal operator (Eq. 3): each
                               step tallies per cell the energy its dust packages leave in it (self),
                               the energy they carried (emitted) and their number; Lambda_cc =
-                              self / emitted (capped at 0.999) and T solves
+                              self / emitted (capped at ali_max_lambda) and T solves
                               E(T) (1 - Lambda_cc) = A - Lambda_cc emitted in the cells that sent at
                               least ali_min_packages packages; the others take the plain step */
   int ali_min_packages;    /* <= 1: every cell that sent a package */
+  double ali_max_lambda;   /* cap of Lambda_b (it bounds the amplification 1 / (1 - Lambda_b) of the
+                              cell's incoming field); outside (0, 1): 0.999 */
 } rt_subiter_params;
 
 typedef struct {

@@ -467,7 +467,7 @@ def lambda_iterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed
 
 def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, seed: int, schedule,
                       sub_level: int, T_min=2.7, T_max=3000.0, min_hits=1000.0, n_threads=1,
-                      dust_per_bin=False, ali=False, ali_min_packages=100, **trace_kw):
+                      dust_per_bin=False, ali=False, ali_min_packages=100, ali_max_lambda=0.999, **trace_kw):
     """Lambda iteration with subiterations (Sect. 3.2, App. B).  The field of
     the constant sources is computed once.  The dust field is kept in one
     array per grid level i (Eq. 9): I_i holds what packages deposited after
@@ -483,7 +483,7 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
     the energy the cell's own packages leave in it (self_b) and the energy
     they carried (emitted_b), and per cell their number; Lambda_b =
     self_b / emitted_b is the fraction of the cell's bin-b emission it
-    re-absorbs, capped at 0.999, and T solves
+    re-absorbs, capped at ``ali_max_lambda``, and T solves
     sum_b (1 - Lambda_b) E_b(T) = A - sum_b Lambda_b emitted_b.  The
     diagonal operator is used in the cells that sent at least
     ``ali_min_packages`` packages; the others take the plain step, whose
@@ -531,7 +531,7 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
         A = A_star + I.sum(axis=0)
         if ali:
             use = (self_n >= max(ali_min_packages, 1))[None, :] & (self_emit > 0)
-            lam_b = np.minimum(np.where(use, self_abs / np.where(use, self_emit, 1.0), 0.0), 0.999)
+            lam_b = np.minimum(np.where(use, self_abs / np.where(use, self_emit, 1.0), 0.0), ali_max_lambda)
             rhs = A - (lam_b * self_emit).sum(axis=0)
             Tn = dust_temperature_weighted(tree, rhs, 1.0 - lam_b, lam, kabs, dnu, T_min, T_max, n_threads)
         else:

@@ -287,13 +287,13 @@ __device__ __forceinline__ double table_emission(double T, const double* __restr
 // decouples into one equation per cell, with one unknown per frequency):
 // Lambda_b of a cell is the fraction of the energy its own bin-b packages
 // carried that they left in it (self_b / emitted_b, two tallies of the same
-// packages), capped at 0.999; the cell's temperature then solves
+// packages), capped at lam_max; the cell's temperature then solves
 //   sum_b (1 - Lambda_b) E_b(T) = A - sum_b Lambda_b emitted_b.
 // Only cells that sent at least min_count packages use it (flag 1); the
 // others keep the plain step E(T) = A.
 __global__ void ali_weights_kernel(const double* __restrict__ A, const double* __restrict__ self,
                                    const double* __restrict__ emitted, const unsigned int* __restrict__ count,
-                                   unsigned int min_count, int nl, long long n, double* __restrict__ rhs,
+                                   unsigned int min_count, double lam_max, int nl, long long n, double* __restrict__ rhs,
                                    double* __restrict__ w, uint8_t* __restrict__ use) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -301,7 +301,7 @@ __global__ void ali_weights_kernel(const double* __restrict__ A, const double* _
   double r = A[c];
   for (int b = 0; b < nl; ++b) {
     const double e = emitted[(long long)b * n + c];
-    const double lam = (on && e > 0.0) ? fmin(self[(long long)b * n + c] / e, 0.999) : 0.0;
+    const double lam = (on && e > 0.0) ? fmin(self[(long long)b * n + c] / e, lam_max) : 0.0;
     r -= lam * e;
     w[(long long)b * n + c] = 1.0 - lam;
   }
@@ -310,10 +310,10 @@ __global__ void ali_weights_kernel(const double* __restrict__ A, const double* _
 }
 
 cudaError_t ali_weights(const double* A, const double* self, const double* emitted, const unsigned int* count,
-                        unsigned int min_count, int nl, long long n, double* rhs, double* w, uint8_t* use,
-                        cudaStream_t s) {
-  ali_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, emitted, count, min_count, nl, n, rhs, w,
-                                                                  use);
+                        unsigned int min_count, double lam_max, int nl, long long n, double* rhs, double* w,
+                        uint8_t* use, cudaStream_t s) {
+  ali_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, emitted, count, min_count, lam_max, nl, n,
+                                                                  rhs, w, use);
   return cudaGetLastError();
 }
 

@@ -323,8 +323,8 @@ cudaError_t sum_levels(const double* I, int n_levels, long long n, const double*
 // ALI per frequency (Eq. 3): weights w_b = 1 - Lambda_b [nl][n], the
 // right-hand side A - sum_b Lambda_b emitted_b and the cells that use it
 cudaError_t ali_weights(const double* A, const double* self, const double* emitted, const unsigned int* count,
-                        unsigned int min_count, int nl, long long n, double* rhs, double* w, uint8_t* use,
-                        cudaStream_t s);
+                        unsigned int min_count, double lam_max, int nl, long long n, double* rhs, double* w,
+                        uint8_t* use, cudaStream_t s);
 // the ALI cells' temperatures from sum_b w_b E_b(T) = rhs (starts from T)
 cudaError_t dust_temperature_weighted(const double* rhs, const double* w, const uint8_t* use, long long n,
                                       const uint32_t* child, const double* rho64, const uint8_t* level, double h0,

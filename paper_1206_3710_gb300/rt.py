@@ -106,7 +106,7 @@ class rt_lambda_result(C.Structure):
 class rt_subiter_params(C.Structure):
     _fields_ = [("sub_level", C.c_int), ("n_steps", C.c_int), ("schedule", C.POINTER(C.c_int)),
                 ("select_frac", C.c_double), ("flux_frac", C.c_double), ("ali", C.c_int),
-                ("ali_min_packages", C.c_int)]
+                ("ali_min_packages", C.c_int), ("ali_max_lambda", C.c_double)]
 
 
 class rt_subiter_result(C.Structure):
@@ -506,7 +506,8 @@ def rt_lambda_iterate(ctx: Context, grid: Grid, sources, optics, T_out, *, max_i
 
 def rt_lambda_subiterate(ctx: Context, grid: Grid, sources, optics, T_out, *, sub_level: int, schedule=None,
                          max_iter: int = 30, select_frac: float = 0.25, flux_frac: float = 0.05,
-                         ali: bool = False, ali_min_packages: int = 100, tol: float = 0.0,
+                         ali: bool = False, ali_min_packages: int = 100, ali_max_lambda: float = 0.999,
+                         tol: float = 0.0,
                          min_hits: float = 1000.0,
                          dust_packets_total: int = 0, dust_packets_per_bin: int = 0, T_min: float = 2.7,
                          T_max: float = 3000.0, stream=None, **params) -> dict:
@@ -523,7 +524,7 @@ def rt_lambda_subiterate(ctx: Context, grid: Grid, sources, optics, T_out, *, su
                           dust_packets_total=int(dust_packets_total), dust_packets_per_bin=int(dust_packets_per_bin))
     sp = rt_subiter_params(sub_level=int(sub_level), n_steps=0, select_frac=float(select_frac),
                            flux_frac=float(flux_frac), ali=int(bool(ali)),
-                           ali_min_packages=int(ali_min_packages))
+                           ali_min_packages=int(ali_min_packages), ali_max_lambda=float(ali_max_lambda))
     if schedule is not None:
         kinds = np.array([{"full": 0, "sub": 1}[k] for k in schedule], dtype=np.int32)
         sp.n_steps = len(kinds)
