@@ -177,3 +177,25 @@ def test_ali_matches_oracle_fp64(rt, ctx, orc):
     _, leaf = tree.cells()
     np.testing.assert_allclose(T.cpu().numpy()[leaf], T_o[leaf], rtol=1e-7)
     np.testing.assert_allclose(res["history"], hist_o, rtol=1e-4)
+
+
+@pytest.mark.parametrize("ali", [False, True])
+def test_subiterations_tiled_equal_untiled(rt, ali):
+    """The level-tracking tracer in tiled rounds (its records carry the
+    shallowest grid level and the ALI emission cell) gives the untiled
+    temperatures (FP64, same streams; only the order of the FP64 additions
+    differs)."""
+    desc, optics, star = _sub_model(tau=4.0)
+    res = {}
+    for edge in (0, 2):
+        c = rt.Context(0)
+        c.set_tiles(edge)
+        g = rt.Grid(c, desc)
+        T = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
+        r = rt.rt_lambda_subiterate(c, g, [star], optics, T, sub_level=1, schedule=["full", "sub", "full"], ali=ali,
+                                    min_hits=0.0, dust_packets_per_bin=2000, seed=35, precision=64,
+                                    packets_per_bin=2000)
+        res[edge] = (T.cpu().numpy(), r)
+        c.close()
+    assert res[2][1]["dust_ledger"]["n_tiles"] > 1
+    np.testing.assert_allclose(res[2][0], res[0][0], rtol=1e-10)
