@@ -943,7 +943,11 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
   const long long chunk = std::min<long long>(total, split ? cap / 4 : cap);
   const long long rec_cap = split ? std::min(cap, std::max(16 * chunk, 1ll << 20)) : chunk;
   const size_t rb = tile_record_bytes(precision, levels || split);
-  const int n_keys = n_lambda * T.n_tiles;
+#ifndef RT_TILE_SUB_BITS
+#define RT_TILE_SUB_BITS 0
+#endif
+  T.sbits = std::min(RT_TILE_SUB_BITS, T.tsh);
+  const int n_keys = (n_lambda * T.n_tiles) << (3 * T.sbits);
   int rc = c->tile_a.ensure(rb * (size_t)rec_cap);
   if (!rc) rc = c->tile_b.ensure(rb * (size_t)rec_cap);
   if (!rc) rc = c->tile_key.ensure(sizeof(uint32_t) * (size_t)rec_cap);

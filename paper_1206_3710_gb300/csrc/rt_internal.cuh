@@ -122,6 +122,8 @@ struct TileRun {
   int* status;                  // bit 0: record buffer overflow
   unsigned long long* n_split;  // resampling: copies written this round
   long long split_cap;          // resampling: copies the record buffer has room for this round
+  int sbits;                    // records are also sorted by 2^sbits-per-axis blocks within a tile
+  int pad;
 };
 struct PeelQueue {
   void* rec;                    // PeelRec32 or PeelRec64 [cap]

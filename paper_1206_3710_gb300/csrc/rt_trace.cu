@@ -311,6 +311,18 @@ __device__ __forceinline__ uint32_t tile_of(const Geo<R>& g, const TileRun& T) {
   const int s = g.lev + T.tsh;
   return (g.cx >> s) + (uint32_t)T.ntx * ((g.cy >> s) + (uint32_t)T.nty * (g.cz >> s));
 }
+// sort key of a record: (bin, tile), then the block of 2^-sbits tile edges
+// the package sits in, so that a warp takes up packages that start close
+// together
+template <typename R>
+__device__ __forceinline__ uint32_t tile_key(const Geo<R>& g, const TileRun& T, int bin) {
+  const uint32_t k = (uint32_t)bin * (uint32_t)T.n_tiles + tile_of(g, T);
+  if (T.sbits == 0) return k;
+  const int ss = g.lev + T.tsh - T.sbits;
+  const uint32_t m = (1u << T.sbits) - 1u;
+  const uint32_t sub = ((g.cx >> ss) & m) | (((g.cy >> ss) & m) << T.sbits) | (((g.cz >> ss) & m) << (2 * T.sbits));
+  return (k << (3 * T.sbits)) | sub;
+}
 
 // The FP32 tracer writes the narrow record unless it tracks levels or
 // resamples; the FP64 record always has room for everything.
@@ -507,7 +519,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
       const bool copy = SPLIT && (C.c3[t] & 0x80000000u);
       IO::set_ext(rr, orig_t, C.c0[t], C.c1[t], copy ? C.c3[t] : 0u);
       static_cast<TRec*>(T.out)[slot] = rr;
-      T.out_key[slot] = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
+      T.out_key[slot] = tile_key(g, T, C.bin[t]);
     } else {
       atomicOr(T.status, 1);
     }
@@ -935,7 +947,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           C.W0[t] = C.W0[t] / (R)M;
           sexp_t += dl;
           const unsigned long long slot0 = atomicAdd(T.n_out, need);
-          const uint32_t key = (uint32_t)C.bin[t] * (uint32_t)T.n_tiles + tile_of(g, T);
+          const uint32_t key = tile_key(g, T, C.bin[t]);
           for (uint32_t kk = 1u; kk < M; ++kk) {
             const unsigned long long slot = slot0 + kk - 1u;
             if (slot >= (unsigned long long)T.cap_out) {
