@@ -66,6 +66,7 @@ def parse():
                     help="disc ALI: minimum packages a cell sends for its diagonal operator (one run per value)")
     ap.add_argument("--split-runs", type=int, default=20, help="split: runs with and without resampling")
     ap.add_argument("--split-packets", type=int, default=2_000_000, help="split: initial packages per run")
+    ap.add_argument("--split-lambda", type=float, default=4.0, help="split: wavelength (um) of the field")
     ap.add_argument("--merge-packets", type=int, default=20_000_000, help="merge: packages per wavelength")
     ap.add_argument("--poly-group", type=int, default=4, help="poly: bins per polychromatic package")
     ap.add_argument("--poly-packets", type=int, default=1_000_000, help="poly: packages per bin / per group")

@@ -380,7 +380,7 @@ def run_split(a, rt, synth, ctx, torch):
     L = desc.box[0]
     rho_unit = 70.0 * 2.8 * synth.MH_G
     kV = 0.4 / (rho_unit * L)
-    lam = np.array([4.0])
+    lam = np.array([a.split_lambda])
     optics = synth.Optics(lambda_um=lam, kappa_ext=kV * (lam / 0.55) ** -1.8, albedo=synth.albedo_law(lam),
                           g_hg=np.array([0.5]), dnu=np.ones(1))
     # embedded sources: point sources at the centres of the four densest root cells
@@ -444,7 +444,7 @@ def run_split(a, rt, synth, ctx, torch):
                      # packages needed without resampling for the worst level's noise with it, in time
                      "equal_noise_speedup": float((worst1 / worst4) ** 2 * res[1]["trace_ms"] / res[4]["trace_ms"])}
     clocks = clk.stop()
-    print(json.dumps({"metric": "resampling at grid boundaries (Table 1): RMS noise per level, 4 um field",
+    print(json.dumps({"metric": f"resampling at grid boundaries (Table 1): RMS noise per level, {a.split_lambda:g} um field",
                       "workload": "split", "cells": int(g.n_cells), "runs": runs, "packages_per_run": npk,
                       "split_factor": 4, **out, "dtype": "f32", "clocks": clocks}))
 
