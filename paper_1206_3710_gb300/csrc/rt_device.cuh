@@ -243,6 +243,31 @@ __device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cu
   return inside;
 }
 
+// advance() for a direction along axis a (the other two components zero):
+// the offsets on the other axes do not move, so only axis a is updated
+// (the same results as advance() with that direction)
+template <typename R>
+__device__ __forceinline__ bool advance_axis(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, bool plus) {
+  const bool a0 = a == 0, a1 = a == 1, a2 = a == 2;
+  const R fnew = plus ? R(0) : R(1);
+  g.fx = a0 ? fnew : g.fx;
+  g.fy = a1 ? fnew : g.fy;
+  g.fz = a2 ? fnew : g.fz;
+  const uint32_t cold = a0 ? g.cx : (a1 ? g.cy : g.cz);
+  const uint32_t cnew = plus ? cold + 1u : cold - 1u;
+  g.cx = a0 ? cnew : g.cx;
+  g.cy = a1 ? cnew : g.cy;
+  g.cz = a2 ? cnew : g.cz;
+  const bool root_level = g.lev == 0;
+  const bool near = root_level || ((cold >> 1) == (cnew >> 1));
+  const uint32_t step = root_level ? (a0 ? 1u : (a1 ? G.rx : G.rx * G.ry)) : (1u << a);
+  const uint32_t rx = g.cx >> g.lev, ry = g.cy >> g.lev, rz = g.cz >> g.lev;
+  const bool inside = rx < G.rx && ry < G.ry && rz < G.rz;
+  cur.pending = near ? (plus ? g.idx + step : g.idx - step) : rx + G.rx * (ry + G.ry * rz);
+  cur.k = near ? g.lev : 0;
+  return inside;
+}
+
 template <typename R>
 __device__ __forceinline__ R hg_mu(R g, R u) {
   R mu;

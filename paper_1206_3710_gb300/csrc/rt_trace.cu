@@ -1138,6 +1138,10 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
   uint32_t tab_blk = 0u;
   int tab_o = 0;
   R ktab = R(0);
+  // an observer along a coordinate axis (the paper's maps, Sect. 4.1): the
+  // march moves on that axis only (pax, pplus); -1 otherwise
+  int pax = -1;
+  bool pplus = false;
   g.lev = 0;
   cur.pending = 0u;
   cur.k = 0;
@@ -1183,6 +1187,10 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
             ix = inv_abs(dx);
             iy = inv_abs(dy);
             iz = inv_abs(dz);
+            pax = TAB ? -1
+                      : ((dy == R(0) && dz == R(0)) ? 0
+                                                     : ((dx == R(0) && dz == R(0)) ? 1 : ((dx == R(0) && dy == R(0)) ? 2 : -1)));
+            pplus = (pax == 0 ? dx : (pax == 1 ? dy : dz)) > R(0);
             g = rg;
             cur.pending = g.idx;
             cur.k = g.lev;
@@ -1225,7 +1233,15 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
         } else {
           settle_leaf(g, cur, w, r64);
           int a;
-          const R tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
+          R tx;
+          if (pax >= 0) {
+            // along an axis: the exit distance is the offset to the face ahead
+            const R f = pax == 0 ? g.fx : (pax == 1 ? g.fy : g.fz);
+            tx = pplus ? R(1) - f : f;
+            a = pax;
+          } else {
+            tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
+          }
           if (a < 0) {
             ev = EV_CUT;  // cannot happen for |k| = 1
           } else {
@@ -1233,7 +1249,7 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
             npeel += tx > R(0) ? 1u : 0u;
             if (taup > tau_cut) {
               ev = EV_CUT;
-            } else if (!advance(G, g, cur, a, tx, dx, dy, dz)) {
+            } else if (!(pax >= 0 ? advance_axis(G, g, cur, a, pplus) : advance(G, g, cur, a, tx, dx, dy, dz))) {
               ev = EV_ESCAPE;
             } else if (TAB && cur.k == 0) {
               const JobDev& J = jobs[job];
