@@ -41,8 +41,8 @@ BYTES_IMAGE_DEPOSIT = 16        # FP64 pixel read-modify-write
 # the deferred peel-off kernel on the default molecular cloud workload, from
 # a single-pass ncu capture of the current kernels (set to None whenever a
 # kernel changes until it is captured again)
-NCU_TRAFFIC_PER_LAUNCH = (182.02e9 + 153.36e9 + 0.01e9 + 33.21e9) / 2
-NCU_PEEL_TRAFFIC_PER_LAUNCH = None  # peel-off kernel changed since the last capture
+NCU_TRAFFIC_PER_LAUNCH = (181.41e9 + 153.30e9 + 0.00e9 + 33.21e9) / 2
+NCU_PEEL_TRAFFIC_PER_LAUNCH = (102.73e9 + 1.17e9) / 2
 
 
 def parse():
