@@ -82,3 +82,35 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(rt, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(ImportError):
         rt.lib()
+
+
+STRUCTS = ["rt_tree_desc", "rt_grid_info", "rt_optics", "rt_dust", "rt_source", "rt_trace_params", "rt_ledger",
+           "rt_observers", "rt_job", "rt_tune_result", "rt_server_config", "rt_serve_job", "rt_lambda_params",
+           "rt_lambda_result", "rt_subiter_params", "rt_subiter_result"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors in the binding have the sizes and field offsets of
+    the C structs in include/rt.h (compiled with the host C compiler)."""
+    from paper_1206_3710_gb300 import rt
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rt.h"', 'int main(void) {']
+    checks = []
+    for s in STRUCTS:
+        cls = getattr(rt, s)
+        lines.append(f'  printf("%zu\\n", sizeof({s}));')
+        checks.append((s, None, ctypes.sizeof(cls)))
+        for name, _ in cls._fields_:
+            cname = "lambda" if (s == "rt_subiter_result" and name == "lambda_") else name
+            lines.append(f'  printf("%zu\\n", offsetof({s}, {cname}));')
+            checks.append((s, name, getattr(cls, name).offset))
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert len(out) == len(checks)
+    bad = [(s, f, int(v), want) for (s, f, want), v in zip(checks, out) if int(v) != want]
+    assert not bad, bad
