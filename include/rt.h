@@ -469,12 +469,15 @@ typedef struct {
   double flux_frac;        /* automatic: also a full step once the emission below L has changed by this
                               fraction since the last full step (the upper levels' field from below
                               is stale); <= 0: off */
-  int ali;                 /* 1: accelerated Lambda iteration with the diagonal operator (Eq. 3): each
-                              step tallies per cell the energy its dust packages leave in it (self),
-                              the energy they carried (emitted) and their number; Lambda_cc =
-                              self / emitted (capped at ali_max_lambda) and T solves
-                              E(T) (1 - Lambda_cc) = A - Lambda_cc emitted in the cells that sent at
-                              least ali_min_packages packages; the others take the plain step */
+  int ali;                 /* 1: accelerated Lambda iteration with the diagonal operator (Eq. 3), per
+                              frequency bin b: each step tallies per cell and bin the energy its dust
+                              packages leave in it (self_b) and the energy they carried (emitted_b),
+                              and per cell their number; Lambda_b = self_b / emitted_b (capped at
+                              ali_max_lambda) and T solves sum_b (1 - Lambda_b) E_b(T) =
+                              A - sum_b Lambda_b emitted_b in the cells that sent at least
+                              ali_min_packages packages; a bin such a cell did not sample takes the
+                              largest Lambda_j of its sampled bins with kappa_abs,j <= kappa_abs,b
+                              (0 if none); the other cells take the plain step */
   int ali_min_packages;    /* <= 1: every cell that sent a package */
   double ali_max_lambda;   /* cap of Lambda_b (it bounds the amplification 1 / (1 - Lambda_b) of the
                               cell's incoming field); outside (0, 1): 0.999 */

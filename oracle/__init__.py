@@ -487,7 +487,12 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
     sum_b (1 - Lambda_b) E_b(T) = A - sum_b Lambda_b emitted_b.  The
     diagonal operator is used in the cells that sent at least
     ``ali_min_packages`` packages; the others take the plain step, whose
-    expectation includes their rare self-absorbed packages.
+    expectation includes their rare self-absorbed packages.  A bin in which
+    such a cell sent no package has no estimate of its own; since a cell
+    re-absorbs more of its emission the more opaque it is, the bin takes
+    the largest Lambda_j of the cell's sampled bins j with kappa_abs,j <=
+    kappa_abs,b (0 if there is none) rather than 0, which would count that
+    bin's emission at T as escaping in full.
     Returns T and the per-step max dT/T over cells with >= ``min_hits`` hits."""
     kabs = (1 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
     lam = np.asarray(optics.lambda_um)
@@ -530,8 +535,14 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
             I[L + 1:] = rd["absorbed"][L + 1:]
         A = A_star + I.sum(axis=0)
         if ali:
-            use = (self_n >= max(ali_min_packages, 1))[None, :] & (self_emit > 0)
-            lam_b = np.minimum(np.where(use, self_abs / np.where(use, self_emit, 1.0), 0.0), ali_max_lambda)
+            on = self_n >= max(ali_min_packages, 1)
+            use = on[None, :] & (self_emit > 0)
+            lam_s = np.minimum(np.where(use, self_abs / np.where(use, self_emit, 1.0), 0.0), ali_max_lambda)
+            lam_b = lam_s.copy()
+            for b in range(nlam):
+                below = kabs <= kabs[b]
+                env = np.where(use[below], lam_s[below], 0.0).max(axis=0)
+                lam_b[b] = np.where(on & ~use[b], env, lam_s[b])
             rhs = A - (lam_b * self_emit).sum(axis=0)
             Tn = dust_temperature_weighted(tree, rhs, 1.0 - lam_b, lam, kabs, dnu, T_min, T_max, n_threads)
         else:

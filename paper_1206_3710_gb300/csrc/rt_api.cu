@@ -1605,8 +1605,8 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
       // Eq. 3 per frequency: the cells' own re-absorption solved with the
       // new temperature, from the plain solve's T
       const double lam_max = sp->ali_max_lambda > 0.0 && sp->ali_max_lambda < 1.0 ? sp->ali_max_lambda : 0.999;
-      CK(ali_weights(A, self_abs, self_emit, self_cnt, (unsigned)std::max(1, sp->ali_min_packages), lam_max, nlb, nc,
-                     ali_rhs, ali_w, ali_use, s));
+      CK(ali_weights(A, self_abs, self_emit, self_cnt, kab, (unsigned)std::max(1, sp->ali_min_packages), lam_max,
+                     nlb, nc, ali_rhs, ali_w, ali_use, s));
       CK(dust_temperature_weighted(ali_rhs, ali_w, ali_use, nc, g->child, g->rho64, g->level, g->h0, lam, kab, dnu,
                                    du->n_lambda, du->T_min, du->T_max, T_dev, s));
     }

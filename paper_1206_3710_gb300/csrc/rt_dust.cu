@@ -290,19 +290,34 @@ __device__ __forceinline__ double table_emission(double T, const double* __restr
 // packages), capped at lam_max; the cell's temperature then solves
 //   sum_b (1 - Lambda_b) E_b(T) = A - sum_b Lambda_b emitted_b.
 // Only cells that sent at least min_count packages use it (flag 1); the
-// others keep the plain step E(T) = A.
+// others keep the plain step E(T) = A.  A bin in which such a cell sent no
+// package takes the largest Lambda_j of the cell's sampled bins with
+// kabs_j <= kabs_b (0 if none): self-absorption grows with opacity, and a
+// weight of 1 would count that bin's emission at the new T as escaping.
+__device__ __forceinline__ double ali_lambda(const double* __restrict__ self, const double* __restrict__ emitted,
+                                             double lam_max, long long n, long long c, int b) {
+  const double e = emitted[(long long)b * n + c];
+  return e > 0.0 ? fmin(self[(long long)b * n + c] / e, lam_max) : -1.0;
+}
+
 __global__ void ali_weights_kernel(const double* __restrict__ A, const double* __restrict__ self,
                                    const double* __restrict__ emitted, const unsigned int* __restrict__ count,
-                                   unsigned int min_count, double lam_max, int nl, long long n, double* __restrict__ rhs,
-                                   double* __restrict__ w, uint8_t* __restrict__ use) {
+                                   const double* __restrict__ kabs, unsigned int min_count, double lam_max, int nl,
+                                   long long n, double* __restrict__ rhs, double* __restrict__ w,
+                                   uint8_t* __restrict__ use) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const bool on = count[c] >= min_count;
   double r = A[c];
   for (int b = 0; b < nl; ++b) {
-    const double e = emitted[(long long)b * n + c];
-    const double lam = (on && e > 0.0) ? fmin(self[(long long)b * n + c] / e, lam_max) : 0.0;
-    r -= lam * e;
+    double lam = on ? ali_lambda(self, emitted, lam_max, n, c, b) : 0.0;
+    if (lam >= 0.0) {
+      r -= lam * emitted[(long long)b * n + c];
+    } else {
+      lam = 0.0;
+      for (int j = 0; j < nl; ++j)
+        if (kabs[j] <= kabs[b]) lam = fmax(lam, ali_lambda(self, emitted, lam_max, n, c, j));
+    }
     w[(long long)b * n + c] = 1.0 - lam;
   }
   rhs[c] = r;
@@ -310,10 +325,10 @@ __global__ void ali_weights_kernel(const double* __restrict__ A, const double* _
 }
 
 cudaError_t ali_weights(const double* A, const double* self, const double* emitted, const unsigned int* count,
-                        unsigned int min_count, double lam_max, int nl, long long n, double* rhs, double* w,
-                        uint8_t* use, cudaStream_t s) {
-  ali_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, emitted, count, min_count, lam_max, nl, n,
-                                                                  rhs, w, use);
+                        const double* kabs, unsigned int min_count, double lam_max, int nl, long long n, double* rhs,
+                        double* w, uint8_t* use, cudaStream_t s) {
+  ali_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, self, emitted, count, kabs, min_count, lam_max, nl,
+                                                                  n, rhs, w, use);
   return cudaGetLastError();
 }
 

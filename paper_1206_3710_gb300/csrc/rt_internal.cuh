@@ -319,14 +319,12 @@ cudaError_t max_rel_change(const double* T, const double* T_prev, const unsigned
 // mass at <= L, imbalance, mass below L, emission at <= L, below L)
 cudaError_t mask_levels(const double* T, const uint8_t* level, long long n, int L, double* out, cudaStream_t s);
 cudaError_t sum_levels(const double* I, int n_levels, long long n, const double* A_star, double* A, cudaStream_t s);
-// ALI temperature input: A' = (A - self) / (1 - self / (rho V E(T_emit))) per
-// leaf (A elsewhere), the field a cell would absorb once its own emission is
-// in equilibrium with it (Eq. 3 with a diagonal Lambda_0)
 // ALI per frequency (Eq. 3): weights w_b = 1 - Lambda_b [nl][n], the
-// right-hand side A - sum_b Lambda_b emitted_b and the cells that use it
+// right-hand side A - sum_b Lambda_b emitted_b and the cells that use it;
+// kabs [nl] orders the bins for the cells' unsampled bins
 cudaError_t ali_weights(const double* A, const double* self, const double* emitted, const unsigned int* count,
-                        unsigned int min_count, double lam_max, int nl, long long n, double* rhs, double* w,
-                        uint8_t* use, cudaStream_t s);
+                        const double* kabs, unsigned int min_count, double lam_max, int nl, long long n, double* rhs,
+                        double* w, uint8_t* use, cudaStream_t s);
 // the ALI cells' temperatures from sum_b w_b E_b(T) = rhs (starts from T)
 cudaError_t dust_temperature_weighted(const double* rhs, const double* w, const uint8_t* use, long long n,
                                       const uint32_t* child, const double* rho64, const uint8_t* level, double h0,

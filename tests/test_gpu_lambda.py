@@ -161,19 +161,23 @@ def test_subiterations_automatic_small_disc(rt, ctx):
     assert all(a >= 0 and b >= 0 for a, b in res["imbalance"])
 
 
-def test_ali_matches_oracle_fp64(rt, ctx, orc):
+@pytest.mark.parametrize("min_pk", [100, 3])
+def test_ali_matches_oracle_fp64(rt, ctx, orc, min_pk):
     """The accelerated Lambda iteration (diagonal operator, Eq. 3) with full
-    steps and subiterations, against the oracle's."""
+    steps and subiterations, against the oracle's.  With ALI in every cell
+    that sent 3 packages, most ALI cells have bins they did not sample, which
+    take the opacity envelope of their sampled bins."""
     desc, optics, star = _sub_model(tau=4.0)
     g = rt.Grid(ctx, desc)
     T = torch.zeros(g.n_cells, dtype=torch.float64, device=DEV)
     sched = ["full", "sub", "full"]
     npk = 2000
     res = rt.rt_lambda_subiterate(ctx, g, [star], optics, T, sub_level=1, schedule=sched, ali=True, min_hits=0.0,
-                                  dust_packets_per_bin=npk, seed=34, precision=64, packets_per_bin=npk)
+                                  dust_packets_per_bin=npk, seed=34, precision=64, packets_per_bin=npk,
+                                  ali_min_packages=min_pk)
     tree = orc.Tree(desc)
     T_o, hist_o, _ = orc.lambda_subiterate(tree, star, optics, npk, npk, seed=34, schedule=sched, sub_level=1,
-                                           min_hits=0.0, dust_per_bin=True, ali=True)
+                                           min_hits=0.0, dust_per_bin=True, ali=True, ali_min_packages=min_pk)
     _, leaf = tree.cells()
     np.testing.assert_allclose(T.cpu().numpy()[leaf], T_o[leaf], rtol=1e-7)
     np.testing.assert_allclose(res["history"], hist_o, rtol=1e-4)
