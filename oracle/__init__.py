@@ -52,7 +52,7 @@ class _TreeDesc(C.Structure):
 class _Source(C.Structure):
     _fields_ = [("kind", C.c_int), ("pos", C.c_double * 3), ("dir", C.c_double * 3),
                 ("bin_energy", C.POINTER(C.c_double)), ("packets", C.POINTER(C.c_int64)),
-                ("emission", C.POINTER(C.c_double))]
+                ("emission", C.POINTER(C.c_double)), ("sampling", C.POINTER(C.c_double))]
 
 
 class _Optics(C.Structure):
@@ -294,6 +294,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
         if s.kind == "dust":
             em = emission if emission is not None else s.emission
             S.emission = _dp(keep.arr(em, np.float64), C.c_double)
+            if getattr(s, "sampling", None) is not None:
+                S.sampling = _dp(keep.arr(s.sampling, np.float64), C.c_double)
     o = _optics(optics, keep)
     prm = _Params(seed=seed, job=job, iter=iter_, estimator=estimator, rr_wmin=rr_wmin, rr_p=rr_p,
                   step_limit=step_limit, peel_tau_max=peel_tau_max, per_lambda=int(per_lambda),
@@ -416,10 +418,14 @@ def packets_by_energy(energy: np.ndarray, total: int) -> np.ndarray:
 
 
 class _DustSource:
+    """Dust emission [n_lambda][n_cells]; ``sampling`` (same shape, > 0
+    wherever the emission is) draws the emission cells by other weights, each
+    package carrying emission_c / (N p_c)."""
     kind = "dust"
 
-    def __init__(self, emission):
+    def __init__(self, emission, sampling=None):
         self.emission = emission
+        self.sampling = sampling
         self.bin_energy = None
 
 

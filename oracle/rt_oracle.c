@@ -1077,6 +1077,11 @@ static void trace_one(trace_worker* w, int64_t p) {
     double u0 = uni(&rs);
     int64_t c = search_cdf(cdf, nc, u0 * cdf[nc - 1]);
     origin = c;
+    if (S->sampling) {
+      /* importance-sampled cell: weight emission_c / (N p_c) */
+      W0 = S->emission[(int64_t)bin * nc + c] * cdf[nc - 1] / ((double)npk * S->sampling[(int64_t)bin * nc + c]);
+      W = W0;
+    }
     if (prm->self_emitted) atomic_add_double(&prm->self_emitted[(int64_t)bin * nc + c], W0);
     if (prm->self_count) atomic_add_double(&prm->self_count[c], 1.0);
     const orc_node* n = &t->nodes[c];
@@ -1174,9 +1179,21 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
       J.seg_begin[i + 1] = J.seg_begin[i] + src[s].packets[b];
       if (src[s].kind == ORC_SRC_DUST && src[s].packets[b] > 0) {
         double* c = (double*)malloc((size_t)nc * sizeof(double));
+        const double* tab = src[s].sampling ? src[s].sampling : src[s].emission;
         double acc = 0.0;
-        for (int64_t k = 0; k < nc; ++k) { acc += src[s].emission[(int64_t)b * nc + k]; c[k] = acc; }
+        int bad = 0;
+        for (int64_t k = 0; k < nc; ++k) {
+          const int64_t q = (int64_t)b * nc + k;
+          if (src[s].sampling && src[s].emission[q] > 0.0 && !(src[s].sampling[q] > 0.0)) bad = 1;
+          acc += tab[q];
+          c[k] = acc;
+        }
         J.cdf[i] = c;
+        if (bad) {
+          for (int64_t j = 0; j <= i; ++j) free(J.cdf[j]);
+          free(J.cdf); free(J.seg_begin);
+          return -1;
+        }
       }
     }
   J.n_packets = J.seg_begin[(int64_t)n_src * nl];

@@ -67,6 +67,11 @@ typedef struct {
   const double* bin_energy;    /* [n_lambda] (point, external, beam) */
   const int64_t* packets;      /* [n_lambda] packets per bin */
   const double* emission;      /* dust: [n_lambda][n_cells] energy per cell per bin */
+  const double* sampling;      /* dust, optional: [n_lambda][n_cells] weights the emission cell is
+                                * drawn by (NULL: the emission itself); a package from cell c then
+                                * carries emission_c / (N p_c), p_c = sampling_c / sum, so every cell
+                                * still emits its energy in expectation; sampling_c must be > 0
+                                * wherever emission_c > 0 */
 } orc_source;
 
 typedef struct {
