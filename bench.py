@@ -31,18 +31,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell crossings/s & packets/s on 1 GB300 vs roofline; p50/p99 job latency"
 UNIT = "cell crossings/s"
-# algorithmic bytes per unit of tracer work (the packed node word replaces
-# the separate density + child reads: 4 B per visit)
-BYTES_TRACE_CROSS = 4 + 16      # node word + FP64 accumulator read-modify-write
-BYTES_PEEL_CROSS = 4            # node word
-BYTES_IMAGE_DEPOSIT = 16        # FP64 pixel read-modify-write
+# algorithmic bytes per unit of tracer work, as the method moves them: a
+# trace crossing reads the leaf's density (4 B) and child word (4 B) and
+# updates its FP64 accumulator (16 B read-modify-write); a peel-off crossing
+# reads density and child word; an image deposit updates an FP64 pixel
+BYTES_TRACE_CROSS = 4 + 4 + 16
+BYTES_PEEL_CROSS = 4 + 4
+BYTES_IMAGE_DEPOSIT = 16
+# the same with the packed node word of this implementation (density or
+# child index in one 32-bit word: one 4-byte read per visit)
+BYTES_TRACE_CROSS_PACKED = 4 + 16
+BYTES_PEEL_CROSS_PACKED = 4
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per step of the
 # tracer (all its launches: the emission round and the tiled rounds) and of
 # the deferred peel-off kernel on the default molecular cloud workload, from
 # a single-pass ncu capture of the current kernels (set to None whenever a
 # kernel changes until it is captured again)
-NCU_TRAFFIC_PER_LAUNCH = (181.41e9 + 153.30e9 + 0.00e9 + 33.21e9) / 2
-NCU_PEEL_TRAFFIC_PER_LAUNCH = (102.73e9 + 1.17e9) / 2
+NCU_TRAFFIC_PER_LAUNCH = None
+NCU_PEEL_TRAFFIC_PER_LAUNCH = None
 
 
 def parse():
@@ -161,6 +167,26 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def l2_read_gbs(dev):
+    """L2 read bandwidth measured here: a sum over a 48 MB tensor that stays
+    in the 129 MB L2, repeated (CUDA events, best of 5 runs of 50)."""
+    import torch
+    x = torch.ones(48 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    out = torch.empty((), dtype=torch.float32, device=dev)
+    for _ in range(10):
+        torch.sum(x, out=out)
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(50):
+            torch.sum(x, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 50 * x.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
 def make_model(a):
     from paper_1206_3710_gb300 import synth
     return synth.cloud(n_root=a.n_root, levels=a.levels, n_lambda=a.n_lambda, packets_per_bin=a.packets_per_bin,
@@ -182,30 +208,51 @@ def dust_arrays(m):
     return m.optics.lambda_um, kabs, m.optics.dnu
 
 
-def cpu_baseline(a, m, packets_per_bin=None, want_seconds=15.0):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the workload."""
+def oracle_sample_size(a, m, tree, cores, want_seconds=12.0):
+    """Packages per wavelength for which one oracle trace of the workload on
+    `cores` threads takes about want_seconds (grown from a small probe)."""
+    import oracle
+    ppb = 50
+    while True:
+        t1 = time.perf_counter()
+        oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, observers=m.observers, n_threads=cores,
+                     rr_wmin=a.rr_wmin, rr_p=a.rr_p)
+        dt = time.perf_counter() - t1
+        if dt > 0.2 * want_seconds or ppb >= a.packets_per_bin:
+            break
+        ppb = int(ppb * min(8.0, max(2.0, 0.5 * want_seconds / max(dt, 1e-3))))
+    return max(1, min(a.packets_per_bin, int(ppb * want_seconds / max(dt, 1e-3))))
+
+
+def _oracle_rate(a, m, tree, ppb, cores, seed=1002, iter_=0):
+    import oracle
+    t1 = time.perf_counter()
+    r = oracle.trace(tree, m.sources, m.optics, ppb, seed=seed, iter_=iter_, observers=m.observers,
+                     n_threads=cores, rr_wmin=a.rr_wmin, rr_p=a.rr_p)
+    dt = time.perf_counter() - t1
+    L = r["ledger"]
+    return L["n_cross"] + L["n_peel_cross"], L["n_packets"], dt
+
+
+def cpu_baseline(a, m, packets_per_bin=None):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the
+    workload: all host cores, and one core on a smaller sample."""
     import oracle
     t0 = time.perf_counter()
     tree = oracle.Tree(m.tree)
     t_build = time.perf_counter() - t0
     cores = os.cpu_count() or 1
-    ppb = packets_per_bin or 50
-    # grow the sample until it takes a few seconds, capped at want_seconds total
-    while True:
-        t1 = time.perf_counter()
-        r = oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, observers=m.observers, n_threads=cores,
-                         rr_wmin=a.rr_wmin, rr_p=a.rr_p)
-        dt = time.perf_counter() - t1
-        if packets_per_bin or dt > 0.25 * want_seconds or ppb >= a.packets_per_bin:
-            break
-        ppb = int(ppb * min(8.0, max(2.0, 0.5 * want_seconds / max(dt, 1e-3))))
-    L = r["ledger"]
-    cross = L["n_cross"] + L["n_peel_cross"]
+    ppb = packets_per_bin or oracle_sample_size(a, m, tree, cores)
+    cross, npk, dt = _oracle_rate(a, m, tree, ppb, cores)
+    ppb1 = max(1, ppb // (2 * cores))
+    cross1, npk1, dt1 = _oracle_rate(a, m, tree, ppb1, 1)
     return {"value": cross / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "packets_per_s": L["n_packets"] / dt,
+            "packets_per_s": npk / dt,
             "sample": f"{ppb} packages per wavelength x {a.n_lambda} wavelengths on the full grid with "
-                      f"{m.observers.n_obs} peel-off observers ({int(L['n_packets'])} packages, "
-                      f"{int(cross)} crossings, {dt:.2f} s; tree build {t_build:.1f} s excluded)"}
+                      f"{m.observers.n_obs} peel-off observers ({int(npk)} packages, "
+                      f"{int(cross)} crossings, {dt:.2f} s; tree build {t_build:.1f} s excluded)",
+            "single_thread": {"value": cross1 / dt1, "unit": UNIT, "cores": 1, "packets_per_s": npk1 / dt1,
+                              "sample": f"{ppb1} packages per wavelength ({int(npk1)} packages, {dt1:.2f} s)"}}
 
 
 def run_reference(a):
@@ -216,18 +263,17 @@ def run_reference(a):
     import oracle
     tree = oracle.Tree(m.tree)
     cores = os.cpu_count() or 1
-    ppb = a.cpu_packets_per_bin or max(10, min(200, a.packets_per_bin))
+    # the same sample size as the cpu_baseline leg of the GPU arm: one step
+    # is about 12 s of oracle work on all host cores
+    ppb = a.cpu_packets_per_bin or oracle_sample_size(a, m, tree, cores)
     for _ in range(a.warmup):
-        oracle.trace(tree, m.sources, m.optics, max(1, ppb // 10), seed=1002, observers=m.observers, n_threads=cores,
-                     rr_wmin=a.rr_wmin, rr_p=a.rr_p)
+        _oracle_rate(a, m, tree, max(1, ppb // 10), cores)
     tot_cross, tot_pk, t = 0.0, 0.0, 0.0
     for s in range(a.steps):
-        t0 = time.perf_counter()
-        r = oracle.trace(tree, m.sources, m.optics, ppb, seed=1002, iter_=s, observers=m.observers, n_threads=cores,
-                         rr_wmin=a.rr_wmin, rr_p=a.rr_p)
-        t += time.perf_counter() - t0
-        tot_cross += r["ledger"]["n_cross"] + r["ledger"]["n_peel_cross"]
-        tot_pk += r["ledger"]["n_packets"]
+        c, p, dt = _oracle_rate(a, m, tree, ppb, cores, iter_=s)
+        t += dt
+        tot_cross += c
+        tot_pk += p
     v = tot_cross / t
     sample = f"{ppb} packages per wavelength x {a.n_lambda} wavelengths per step, full grid, peel-off"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
@@ -337,23 +383,35 @@ def main():
     peel_ms = statistics.mean(L["peel_ms"] for L in leds)
     deposits = L0["n_scatter"] * obs.n_obs - L0["n_peel_out"]
     peak, peak_kind = peaks()
+    l2_peak = l2_read_gbs(dev)
     trace_bytes = BYTES_TRACE_CROSS * L0["n_cross"]
     peel_bytes = BYTES_PEEL_CROSS * L0["n_peel_cross"] + BYTES_IMAGE_DEPOSIT * deposits
+    trace_packed = BYTES_TRACE_CROSS_PACKED * L0["n_cross"]
+    peel_packed = BYTES_PEEL_CROSS_PACKED * L0["n_peel_cross"] + BYTES_IMAGE_DEPOSIT * deposits
     if L0["n_peel_deferred"] < L0["n_scatter"]:  # some peel-offs ran inline in the tracer
         trace_bytes, peel_bytes = trace_bytes + peel_bytes, 0
+        trace_packed, peel_packed = trace_packed + peel_packed, 0
     achieved = trace_bytes / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": NCU_TRAFFIC_PER_LAUNCH, "peak_kind": peak_kind, "kernel": "trace_kernel<float,1,0,0>",
             "kernel_ms": kern_ms, "alg_bytes_per_launch": trace_bytes,
             "bytes_per_unit": {"trace_crossing": BYTES_TRACE_CROSS, "peel_crossing": BYTES_PEEL_CROSS,
-                               "image_deposit": BYTES_IMAGE_DEPOSIT}}
+                               "image_deposit": BYTES_IMAGE_DEPOSIT},
+            "packed_node_word": {"bytes_per_trace_crossing": BYTES_TRACE_CROSS_PACKED,
+                                 "frac": trace_packed / (kern_ms * 1e-3) / 1e9 / peak},
+            # the tiled rounds keep each round's cells in L2: the same bytes
+            # against the L2 read bandwidth measured in this run
+            "l2": {"peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
+                   "peak_kind": "measured (torch.sum over a 48 MB L2-resident tensor)"}}
     peel_roof = None
     if peel_ms > 0:
         pa = peel_bytes / (peel_ms * 1e-3) / 1e9
         peel_roof = {"kernel": "peel_kernel<float>", "bound": "hbm", "achieved": pa, "peak": peak, "unit": "GB/s",
                      "frac": pa / peak, "kernel_ms": peel_ms, "alg_bytes_per_launch": peel_bytes,
                      "traffic": NCU_PEEL_TRAFFIC_PER_LAUNCH,
-                     "crossings_per_s": L0["n_peel_cross"] / (peel_ms * 1e-3)}
+                     "crossings_per_s": L0["n_peel_cross"] / (peel_ms * 1e-3),
+                     "packed_node_word": {"frac": peel_packed / (peel_ms * 1e-3) / 1e9 / peak},
+                     "l2": {"peak": l2_peak, "frac": pa / l2_peak}}
 
     out = None
     if rank == 0:

@@ -20,6 +20,11 @@
  *  - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Kernels
  *    run on that stream; calls that return a ledger wait for their own work
  *    on the stream (bounded by params.timeout_s, RT_ERR_TIMEOUT on expiry).
+ *    Results are copied into the context's pinned memory and read only
+ *    after the wait succeeded.  After RT_ERR_TIMEOUT the call's kernels keep
+ *    running on the stream (they end by themselves, bounded by the step
+ *    limit) and still use the context's scratch: until they have finished,
+ *    every call on that context returns RT_ERR_BUSY.
  *  - Lengths are cm, densities g/cm^3, opacities cm^2/g (per unit mass).
  *    The model box is [0, box[0]] x [0, box[1]] x [0, box[2]].
  *  - Random numbers: Philox4x32-10 (Salmon et al. 2011) with
@@ -43,7 +48,8 @@ enum {
   RT_ERR_CUDA = -3,       /* CUDA runtime error */
   RT_ERR_STEP_LIMIT = -4, /* some package hit the per-package step limit */
   RT_ERR_TIMEOUT = -5,    /* bounded wait for the device expired */
-  RT_ERR_BUSY = -6        /* server: job does not fit the free budget/slots now */
+  RT_ERR_BUSY = -6        /* server: job does not fit the free budget/slots now;
+                             context: an earlier call's timed-out work still runs */
 };
 
 typedef struct rt_ctx rt_ctx;
@@ -72,9 +78,17 @@ int rt_ctx_set_peel_queue(rt_ctx* ctx, int64_t max_records);
  * histories; only the order of the FP64 additions differs).  tile_edge < 0:
  * automatic (tiles whose node words plus one bin's accumulators take at most
  * 48 MB, only when the whole grid's take more); 0: off.  Uses two record
- * buffers of up to 2^26 (FP32, 80 B each) or 2^25 (FP64, 128 B each)
+ * buffers of up to 2^26 (FP32, 80 B each) or 2^25 (FP64, 144 B each)
  * records.  Returns RT_ERR_INVALID if tile_edge is not a power of two. */
 int rt_ctx_set_tiles(rt_ctx* ctx, int tile_edge);
+/* Capacity of the tiled tracer's record buffers, in records: the packages of
+ * a launch are emitted in chunks of this many records (a quarter of it with
+ * resampling) and traced round by round before the next chunk.  <= 0
+ * restores the default (2^26 in FP32, 2^25 in FP64); larger values are
+ * capped there.  Results do not depend on it (the same package histories);
+ * small values let a small launch go through the many-chunk path of a large
+ * one. */
+int rt_ctx_set_tile_records(rt_ctx* ctx, int64_t max_records);
 /* Message of the last failing call on this thread (static storage, valid
  * until the next call on the same thread). */
 const char* rt_last_error(void);
@@ -147,7 +161,8 @@ enum {
 typedef struct {
   int n_lambda;
   const double* lambda_um; /* host [n_lambda] */
-  const double* kappa_abs; /* host [n_lambda], cm^2/g */
+  const double* kappa_abs; /* host [n_lambda], cm^2/g; NULL in rt_lambda_iterate /
+                              rt_lambda_subiterate: (1 - albedo) kappa_ext of their optics */
   const double* dnu;       /* host [n_lambda], Hz, bin widths */
   double T_min, T_max;     /* K, bracket of the temperature solve */
 } rt_dust;
@@ -557,10 +572,18 @@ int rt_philox(rt_ctx* ctx, int64_t n, const uint32_t* ctr_dev, const uint32_t* k
  * 1..4 sources, 1..256 wavelength bins, point/external/beam sources only (a
  * dust source needs a cumulative-emission table larger than the scratch),
  * no observers.  The first call on a device looks up the scratch address
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  The scratch is cleared at the start of every call and shared by
- * all calls: calls whose work overlaps on the GPU race on it and must be
- * serialised by the caller.  ledger->kernel_ms is 0 (no timing events). */
+ * (cudaGetSymbolAddress) with that device current.  The call cannot be made
+ * on a stream that is capturing a graph (RT_ERR_INVALID): it uploads the job
+ * table from host memory, polls the stream and reads the ledger back.  It
+ * waits (bounded by params->timeout_s) for the earlier work on the stream
+ * before the upload and for its kernel after the launch; on RT_ERR_TIMEOUT
+ * the kernel is still running and still uses the scratch, and the ledger is
+ * not filled.  The scratch is cleared at the start of every call and shared
+ * by all calls, which are serialised on the host: calls whose work overlaps
+ * on the GPU (several streams, or a call after a timeout on another stream
+ * before the first one's kernel finished) race on it and must be ordered by
+ * the caller.  The host side uses a static staging area, not the stack.
+ * ledger->kernel_ms is 0 (no timing events). */
 int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source* src, const rt_optics* optics,
                      const rt_trace_params* params, double* absorbed_dev, rt_ledger* ledger,
                      void* cuda_stream);

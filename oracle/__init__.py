@@ -72,7 +72,8 @@ class _Params(C.Structure):
                 ("n_threads", C.c_int), ("packet_offset", C.c_int64), ("peel_block", C.c_int),
                 ("peel_tiles", C.c_int), ("per_level", C.c_int), ("confine_level", C.c_int),
                 ("self_absorbed", C.c_void_p), ("self_emitted", C.c_void_p), ("self_count", C.c_void_p),
-                ("split_factor", C.c_int), ("split_max_level", C.c_int), ("poly_group", C.c_int)]
+                ("split_factor", C.c_int), ("split_max_level", C.c_int), ("poly_group", C.c_int),
+                ("image_sumsq", C.c_void_p)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled",
@@ -314,6 +315,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
         images = np.zeros((observers.n_obs, bins, observers.ny, observers.nx))
     sumsq = np.zeros((bins, nc)) if validation else None
     hits = np.zeros((bins, nc)) if validation else None
+    image_sumsq = np.zeros_like(images) if (validation and images is not None) else None
+    prm.image_sumsq = None if image_sumsq is None else image_sumsq.ctypes.data
     npk = int(pk.sum())
     rec = np.zeros((npk, 10)) if record else None
     led = _Ledger()
@@ -324,7 +327,7 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
                          _p(rec) if record else None, C.byref(led))
     if rc != 0:
         raise RuntimeError(f"orc_trace failed: {rc}")
-    return dict(absorbed=absorbed, images=images, sumsq=sumsq, hits=hits, rec=rec,
+    return dict(absorbed=absorbed, images=images, sumsq=sumsq, hits=hits, rec=rec, image_sumsq=image_sumsq,
                 ledger={n: getattr(led, n) for n in LEDGER_FIELDS})
 
 

@@ -375,6 +375,12 @@ typedef struct {
   int64_t* stamp;
   int64_t* touched;
   int64_t n_touched, cap_touched;
+  double* img_sumsq;             /* per-pixel sum of squared package contributions, or NULL */
+  double* img_acc;               /* the current package's contribution per pixel */
+  int64_t* img_stamp;
+  int64_t* img_touched;
+  int64_t n_img_touched, cap_img_touched;
+  int64_t cur_pkt;               /* package being traced (for the per-package image tallies) */
   orc_path* stack;               /* copies waiting to be followed (package splitting) */
   int64_t n_stack, cap_stack;
   orc_ledger led;
@@ -416,6 +422,31 @@ static void flush_packet(trace_worker* w) {
     w->hits[s] += 1.0;
   }
   w->n_touched = 0;
+  if (w->img_acc) {
+    for (int64_t i = 0; i < w->n_img_touched; ++i) {
+      int64_t s = w->img_touched[i];
+      w->img_sumsq[s] += w->img_acc[s] * w->img_acc[s];
+    }
+    w->n_img_touched = 0;
+  }
+}
+
+/* a peel-off contribution c to image pixel `slot` */
+static void image_add(trace_worker* w, int64_t slot, double c) {
+  if (w->job->shared_atomic) atomic_add_double(&w->job->images_shared[slot], c);
+  else w->images[slot] += c;
+  if (w->img_acc && c != 0.0) {
+    if (w->img_stamp[slot] != w->cur_pkt) {
+      w->img_stamp[slot] = w->cur_pkt;
+      w->img_acc[slot] = 0.0;
+      if (w->n_img_touched == w->cap_img_touched) {
+        w->cap_img_touched = w->cap_img_touched ? 2 * w->cap_img_touched : 256;
+        w->img_touched = (int64_t*)realloc(w->img_touched, (size_t)w->cap_img_touched * sizeof(int64_t));
+      }
+      w->img_touched[w->n_img_touched++] = slot;
+    }
+    w->img_acc[slot] += c;
+  }
 }
 
 /* Optical depth along x + s k to the root boundary (Sect. 2.4 peel-off). */
@@ -583,8 +614,7 @@ static void peel(trace_worker* w, const double x[3], const double din[3], double
       continue;
     }
     int64_t slot = (((int64_t)o * w->job->bins + ob) * obs->ny + (int64_t)fy) * obs->nx + (int64_t)fx;
-    if (w->job->shared_atomic) atomic_add_double(&w->job->images_shared[slot], c);
-    else w->images[slot] += c;
+    image_add(w, slot, c);
     w->led.peeled += c;
   }
 }
@@ -865,8 +895,7 @@ static void peel_poly(trace_worker* w, const double x[3], const double din[3], c
       double c = W[j] * orc_hg_phase(op->g_hg[b], mu) * exp(-op->kappa_ext[b] * t->h0 * col);
       int ob = w->job->bins > 1 ? b : 0;
       int64_t slot = (((int64_t)o * w->job->bins + ob) * obs->ny + (int64_t)fy) * obs->nx + (int64_t)fx;
-      if (w->job->shared_atomic) atomic_add_double(&w->job->images_shared[slot], c);
-      else w->images[slot] += c;
+      image_add(w, slot, c);
       w->led.peeled += c;
     }
   }
@@ -1127,7 +1156,10 @@ static void trace_one(trace_worker* w, int64_t p) {
 
 static void* trace_thread(void* arg) {
   trace_worker* w = (trace_worker*)arg;
-  for (int64_t p = w->p0; p < w->p1; ++p) trace_one(w, p);
+  for (int64_t p = w->p0; p < w->p1; ++p) {
+    w->cur_pkt = p;
+    trace_one(w, p);
+  }
   return NULL;
 }
 
@@ -1208,6 +1240,7 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
   int64_t n_img = obs && obs->n_obs > 0 ? (int64_t)obs->n_obs * bins * obs->ny * obs->nx : 0;
   double per_thread_bytes = 8.0 * ((double)bins * nc + (double)n_img);
   int validation = sumsq && hits;
+  const int img_var = validation && n_img > 0 && prm->image_sumsq;
   J.shared_atomic = T > 1 && per_thread_bytes * T > 2.0e9;
   if (validation && J.shared_atomic) T = 1, J.shared_atomic = 0;
   J.absorbed_shared = absorbed;
@@ -1238,6 +1271,12 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
       w->stamp = (int64_t*)malloc((size_t)bins * nc * sizeof(int64_t));
       for (int64_t k = 0; k < (int64_t)bins * nc; ++k) w->stamp[k] = -1;
     }
+    if (img_var) {
+      w->img_sumsq = T == 1 ? prm->image_sumsq : (double*)calloc((size_t)n_img, sizeof(double));
+      w->img_acc = (double*)calloc((size_t)n_img, sizeof(double));
+      w->img_stamp = (int64_t*)malloc((size_t)n_img * sizeof(int64_t));
+      for (int64_t k = 0; k < n_img; ++k) w->img_stamp[k] = -1;
+    }
   }
   if (T == 1) trace_thread(&ws[0]);
   else {
@@ -1256,6 +1295,11 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
         for (int64_t k = 0; k < (int64_t)bins * nc; ++k) { sumsq[k] += w->sumsq[k]; hits[k] += w->hits[k]; }
       free(w->absorbed); free(w->images); free(w->sumsq); free(w->hits);
     }
+    if (img_var && T > 1) {
+      for (int64_t k = 0; k < n_img; ++k) prm->image_sumsq[k] += w->img_sumsq[k];
+      free(w->img_sumsq);
+    }
+    free(w->img_acc); free(w->img_stamp); free(w->img_touched);
     free(w->pkt_acc); free(w->stamp); free(w->touched); free(w->stack);
   }
   if (ledger) *ledger = L;

@@ -130,6 +130,10 @@ typedef struct {
    * the likelihood ratio of that path.  Packages are counted per group, at
    * the group's first bin of `packets`. */
   int poly_group;
+  /* Optional [n_obs][bins][ny][nx], with observers: per pixel, the sum over
+   * packages of the square of each package's total contribution to it (the
+   * Monte Carlo variance of the images, as sumsq is for absorbed). */
+  double* image_sumsq;
 } orc_params;
 
 typedef struct {

@@ -89,8 +89,17 @@ struct rt_ctx {
   DevBuf peel_q;                          // deferred peel-off records
   long long peel_q_max = 1ll << 27;       // records; 0: peel-off inline
   int tile_edge = -1;                     // tiled tracing: -1 auto, 0 off, > 0 tile edge in root cells
+  long long tile_rec_max = 0;             // tiled tracing: record buffer capacity (0: default)
   DevBuf tile_a, tile_b, tile_key, tile_hist;
   unsigned long long* pin_count = nullptr;  // pinned: record count read back per round
+  // the event of a wait that ran out of time: that call's kernels and its
+  // copies into the pinned buffers may still be running, so the context
+  // takes no new work until the event has completed (RT_ERR_BUSY)
+  cudaEvent_t busy = nullptr;
+  // pinned landing area of the results read back at the end of a call
+  // (ledgers, tile status, scalars); only grown while the context is idle
+  void* pin_rb = nullptr;
+  size_t pin_rb_n = 0;
   // launch defaults chosen by rt_autotune, per [FP64][peel-off]
   struct Tuned {
     bool set = false;
@@ -143,6 +152,18 @@ static int ensure_pinned(rt_ctx* c, size_t bytes) {
   return RT_OK;
 }
 
+static int ensure_pin_rb(rt_ctx* c, size_t bytes) {
+  if (bytes <= c->pin_rb_n) return RT_OK;
+  if (c->pin_rb) cudaFreeHost(c->pin_rb);
+  c->pin_rb = nullptr;
+  c->pin_rb_n = 0;
+  size_t want = std::max(bytes, (size_t)4096);
+  cudaError_t e = cudaMallocHost(&c->pin_rb, want);
+  if (e != cudaSuccess) return fail(RT_ERR_OOM, "cudaMallocHost(%zu): %s", want, cudaGetErrorString(e));
+  c->pin_rb_n = want;
+  return RT_OK;
+}
+
 extern "C" int rt_ctx_create(int device, rt_ctx** out) {
   if (!out) return fail(RT_ERR_INVALID, "rt_ctx_create: out is NULL");
   *out = nullptr;
@@ -178,6 +199,7 @@ extern "C" void rt_ctx_destroy(rt_ctx* c) {
   c->lam.release();
   for (auto& b : c->cdf) b.release();
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->pin_rb) cudaFreeHost(c->pin_rb);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->ev_b) cudaEventDestroy(c->ev_b);
   if (c->ev_c) cudaEventDestroy(c->ev_c);
@@ -197,6 +219,13 @@ extern "C" int rt_ctx_set_tiles(rt_ctx* c, int tile_edge) {
     return fail(RT_ERR_INVALID, "rt_ctx_set_tiles: tile edge must be a power of two");
   std::lock_guard<std::mutex> lk(c->mu);
   c->tile_edge = tile_edge < 0 ? -1 : tile_edge;
+  return RT_OK;
+}
+
+extern "C" int rt_ctx_set_tile_records(rt_ctx* c, int64_t max_records) {
+  if (!c) return fail(RT_ERR_INVALID, "rt_ctx_set_tile_records: NULL context");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->tile_rec_max = max_records > 0 ? (long long)max_records : 0;
   return RT_OK;
 }
 
@@ -241,6 +270,36 @@ static int wait_event(cudaEvent_t ev, double timeout_s) {
     if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
 }
+
+// wait_event for work of the context: on a timeout the context remembers
+// the event, because the device may still write into the context's pinned
+// buffers and device scratch until that event has completed
+static int ctx_wait(rt_ctx* c, cudaEvent_t ev, double timeout_s) {
+  const int rc = wait_event(ev, timeout_s);
+  if (rc == RT_ERR_TIMEOUT) c->busy = ev;
+  return rc;
+}
+
+// RT_ERR_BUSY while the work of an earlier call that timed out is still
+// running (its kernels use the context's scratch and its copies land in the
+// context's pinned buffers)
+static int ctx_idle(rt_ctx* c) {
+  if (!c->busy) return RT_OK;
+  const cudaError_t e = cudaEventQuery(c->busy);
+  if (e == cudaErrorNotReady)
+    return fail(RT_ERR_BUSY, "the device work of an earlier call that timed out is still running");
+  c->busy = nullptr;
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, "device error in the work of an earlier call: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+// lock the context for one call and check that it is idle
+#define CTX_ENTER(c)                       \
+  std::lock_guard<std::mutex> lk((c)->mu); \
+  do {                                     \
+    const int rc_idle_ = ctx_idle(c);      \
+    if (rc_idle_) return rc_idle_;         \
+  } while (0)
 
 namespace rtk {
 int ctx_device(const rt_ctx* c) { return c->device; }
@@ -294,7 +353,7 @@ extern "C" int rt_build_grid(rt_ctx* ctx, const rt_tree_desc* d, rt_grid** out) 
       return fail(RT_ERR_INVALID, "rt_build_grid: level %d has %lld refined cells, n_refined says %lld", l, cnt,
                   (long long)d->n_refined[l]);
   }
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   rt_grid* g = new rt_grid();
   g->ctx = ctx;
@@ -449,6 +508,18 @@ static int check_dust(const rt_dust* du, int nl) {
     if (!(du->lambda_um[b] > 0.0) || !(du->kappa_abs[b] >= 0.0) || !(du->dnu[b] > 0.0) || !std::isfinite(du->kappa_abs[b]))
       return fail(RT_ERR_INVALID, "dust: bad lambda/kappa_abs/dnu at bin %d", b);
   return RT_OK;
+}
+
+// The Lambda drivers' dust: the absorbing part of the optics' extinction,
+// kappa_abs = (1 - albedo) kappa_ext (a single dust component, Sect. 3.2),
+// when the dust model leaves kappa_abs NULL; else the model as given.
+static const rt_dust* resolve_dust(const rt_dust* du, const rt_optics* op, std::vector<double>& kabs, rt_dust& out) {
+  if (!du || du->kappa_abs || !op || !op->kappa_ext || !op->albedo || du->n_lambda != op->n_lambda) return du;
+  kabs.resize(op->n_lambda);
+  for (int b = 0; b < op->n_lambda; ++b) kabs[b] = (1.0 - op->albedo[b]) * op->kappa_ext[b];
+  out = *du;
+  out.kappa_abs = kabs.data();
+  return &out;
 }
 
 // upload lambda, kappa_abs, dnu into ctx->dust_arrays (+ table of n_table)
@@ -939,7 +1010,8 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
                      const LaunchCfg& cfg, const PeelQueue& q, unsigned long long* counter,
                      unsigned long long* n_out, int* status, double timeout_s, cudaStream_t s,
                      long long* launches, int* rounds, bool levels, bool split, unsigned long long* n_split) {
-  const long long cap = precision == 64 ? (1ll << 25) : (1ll << 26);
+  const long long cap_max = precision == 64 ? (1ll << 25) : (1ll << 26);
+  const long long cap = c->tile_rec_max > 0 ? std::min(c->tile_rec_max, cap_max) : cap_max;
   const long long chunk = std::min<long long>(total, split ? cap / 4 : cap);
   const long long rec_cap = split ? std::min(cap, std::max(16 * chunk, 1ll << 20)) : chunk;
   const size_t rb = tile_record_bytes(precision, levels || split);
@@ -974,7 +1046,7 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
       if (round > 10000000) return fail(RT_ERR_CUDA, "tiled tracing did not finish");
       CK(cudaMemcpyAsync(c->pin_count, n_out, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
       CK(cudaEventRecord(c->ev_c, s));
-      rc = wait_event(c->ev_c, timeout_s);
+      rc = ctx_wait(c, c->ev_c, timeout_s);
       if (rc) return rc;
       const long long n = (long long)c->pin_count[0];
       if (n == 0) break;
@@ -1073,13 +1145,22 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
                      max_observers(n_jobs, jobs), cfg.refill, s));
   }
   CK(cudaEventRecord(c->ev_b, s));
-  std::vector<LedgerDev> hl(n_jobs);
-  CK(cudaMemcpyAsync(hl.data(), led, sizeof(LedgerDev) * n_jobs, cudaMemcpyDeviceToHost, s));
-  int tstat = 0;
-  if (tiled) CK(cudaMemcpyAsync(&tstat, tile_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaEventRecord(c->ev_c, s));
-  rc = wait_event(c->ev_c, to);
+  // ledgers and tile status land in the context's pinned read-back area and
+  // are read only after the event behind the copies has completed: a wait
+  // that runs out leaves no copy pending into caller or stack memory
+  const size_t led_bytes = sizeof(LedgerDev) * (size_t)n_jobs;
+  rc = ensure_pin_rb(c, led_bytes + sizeof(int));
   if (rc) return rc;
+  CK(cudaMemcpyAsync(c->pin_rb, led, led_bytes, cudaMemcpyDeviceToHost, s));
+  if (tiled)
+    CK(cudaMemcpyAsync(static_cast<char*>(c->pin_rb) + led_bytes, tile_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(c->ev_c, s));
+  rc = ctx_wait(c, c->ev_c, to);
+  if (rc) return rc;
+  std::vector<LedgerDev> hl(n_jobs);
+  memcpy(hl.data(), c->pin_rb, led_bytes);
+  int tstat = 0;
+  if (tiled) memcpy(&tstat, static_cast<const char*>(c->pin_rb) + led_bytes, sizeof(int));
   if (tstat) return fail(RT_ERR_CUDA, "tile record buffer overflow");
   float ms = 0.f, ms_peel = 0.f;
   cudaEventElapsedTime(&ms, c->ev_a, c->ev_m);
@@ -1121,7 +1202,7 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
 extern "C" int rt_trace(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_source* src, const rt_optics* optics,
                         const rt_trace_params* params, double* absorbed_dev, rt_ledger* ledger, void* cuda_stream) {
   if (!ctx || !grid || !params) return fail(RT_ERR_INVALID, "rt_trace: NULL argument");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   TraceArgs T{grid, n_src, src, optics, params, nullptr, nullptr, absorbed_dev};
   if (ledger) memset(ledger, 0, sizeof *ledger);
@@ -1132,7 +1213,7 @@ extern "C" int rt_peel(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_sou
                        const rt_trace_params* params, const rt_observers* obs, double* images_dev,
                        double* absorbed_dev, rt_ledger* ledger, void* cuda_stream) {
   if (!ctx || !grid || !params || !obs) return fail(RT_ERR_INVALID, "rt_peel: NULL argument");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   TraceArgs T{grid, n_src, src, optics, params, obs, images_dev, absorbed_dev};
   if (ledger) memset(ledger, 0, sizeof *ledger);
@@ -1148,7 +1229,7 @@ extern "C" int rt_peel_tables_create(rt_ctx* ctx, const rt_grid* grid, const rt_
     return fail(RT_ERR_INVALID, "rt_peel_tables_create: block_edge and tiles_per_edge must be powers of two");
   if (obs->n_obs < 1 || obs->n_obs > RT_MAX_OBS || !obs->dir)
     return fail(RT_ERR_INVALID, "rt_peel_tables_create: 1..%d observers", RT_MAX_OBS);
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   if (grid->device != ctx->device) return fail(RT_ERR_INVALID, "rt_peel_tables_create: grid on another device");
   rt_peel_tables* t = new rt_peel_tables();
@@ -1205,7 +1286,7 @@ extern "C" int rt_peel_tables_create(rt_ctx* ctx, const rt_grid* grid, const rt_
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_c, s);
     if (e != cudaSuccess) rc = fail(RT_ERR_CUDA, "rt_peel_tables_create: %s", cudaGetErrorString(e));
   }
-  if (!rc) rc = wait_event(ctx->ev_c, 3600.0);
+  if (!rc) rc = ctx_wait(ctx, ctx->ev_c, 3600.0);
   if (rc) {
     t->buf.release();
     delete t;
@@ -1236,7 +1317,7 @@ extern "C" int rt_peel_tabulated(rt_ctx* ctx, const rt_grid* grid, int n_src, co
                                  const rt_peel_tables* tables, double* images_dev, double* absorbed_dev,
                                  rt_ledger* ledger, void* cuda_stream) {
   if (!ctx || !grid || !params || !obs || !tables) return fail(RT_ERR_INVALID, "rt_peel_tabulated: NULL argument");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   TraceArgs T{grid, n_src, src, optics, params, obs, images_dev, absorbed_dev, tables};
   if (ledger) memset(ledger, 0, sizeof *ledger);
@@ -1253,7 +1334,7 @@ extern "C" int rt_dust_temperature(rt_ctx* ctx, const rt_grid* g, const double* 
   int rc = check_dust(dust, dust->n_lambda);
   if (rc) return rc;
   if (dust->n_lambda < 1 || dust->n_lambda > RT_MAX_LAMBDA) return fail(RT_ERR_INVALID, "dust: n_lambda out of range");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int n_table = 8192;
@@ -1264,7 +1345,7 @@ extern "C" int rt_dust_temperature(rt_ctx* ctx, const rt_grid* g, const double* 
   CK(dust_temperature(absorbed_dev, n_bins, g->n_cells, g->child, g->rho64, g->level, g->h0, lam, kab, dnu,
                       dust->n_lambda, dust->T_min, dust->T_max, tab, n_table, T_dev, s));
   CK(cudaEventRecord(ctx->ev_b, s));
-  return wait_event(ctx->ev_b, 3600.0);
+  return ctx_wait(ctx, ctx->ev_b, 3600.0);
 }
 
 extern "C" int rt_dust_emission(rt_ctx* ctx, const rt_grid* g, const double* T_dev, const rt_dust* dust,
@@ -1273,22 +1354,27 @@ extern "C" int rt_dust_emission(rt_ctx* ctx, const rt_grid* g, const double* T_d
   int rc = check_dust(dust, dust->n_lambda);
   if (rc) return rc;
   if (dust->n_lambda < 1 || dust->n_lambda > RT_MAX_LAMBDA) return fail(RT_ERR_INVALID, "dust: n_lambda out of range");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   double *lam, *kab, *dnu, *tab;
   rc = upload_dust(ctx, dust, 0, &lam, &kab, &dnu, &tab, s);
   if (rc) return rc;
   CK(dust_emission(T_dev, g->n_cells, g->child, g->rho64, g->level, g->h0, lam, kab, dnu, dust->n_lambda, emission_dev, s));
+  const size_t tb = sizeof(double) * (size_t)dust->n_lambda;
   if (bin_total_host) {
-    rc = ctx->small.ensure(sizeof(double) * dust->n_lambda + 256);
+    rc = ctx->small.ensure(tb + 256);
+    if (!rc) rc = ensure_pin_rb(ctx, tb);
     if (rc) return rc;
     double* tot = reinterpret_cast<double*>(ctx->small.p);
     CK(row_sums_f64(emission_dev, dust->n_lambda, g->n_cells, tot, s));
-    CK(cudaMemcpyAsync(bin_total_host, tot, sizeof(double) * dust->n_lambda, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->pin_rb, tot, tb, cudaMemcpyDeviceToHost, s));
   }
   CK(cudaEventRecord(ctx->ev_b, s));
-  return wait_event(ctx->ev_b, 3600.0);
+  rc = ctx_wait(ctx, ctx->ev_b, 3600.0);
+  if (rc) return rc;
+  if (bin_total_host) memcpy(bin_total_host, ctx->pin_rb, tb);
+  return RT_OK;
 }
 
 // ------------------------------------------------------------------------
@@ -1301,7 +1387,7 @@ extern "C" int rt_walk(rt_ctx* ctx, const rt_grid* g, int64_t n_rays, const doub
       (max_seg > 0 && (!cells_dev || !lengths_dev)))
     return fail(RT_ERR_INVALID, "rt_walk: bad argument");
   if (precision != 32 && precision != 64) return fail(RT_ERR_INVALID, "rt_walk: precision must be 32 or 64");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   JobDev J;
@@ -1323,26 +1409,29 @@ extern "C" int rt_walk(rt_ctx* ctx, const rt_grid* g, int64_t n_rays, const doub
   CK(launch_walk(precision, reinterpret_cast<const JobDev*>(ctx->table.p), n_rays, origins_dev, dirs_dev, max_seg,
                  reinterpret_cast<long long*>(cells_dev), lengths_dev, reinterpret_cast<long long*>(counts_dev), s));
   CK(cudaEventRecord(ctx->ev_b, s));
-  return wait_event(ctx->ev_b, 3600.0);
+  return ctx_wait(ctx, ctx->ev_b, 3600.0);
 }
 
 extern "C" int rt_philox(rt_ctx* ctx, int64_t n, const uint32_t* ctr_dev, const uint32_t* key_dev, uint32_t* out_dev,
                          void* cuda_stream) {
   if (!ctx || n < 0 || (n > 0 && (!ctr_dev || !key_dev || !out_dev))) return fail(RT_ERR_INVALID, "rt_philox: bad argument");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   CK(launch_philox(n, ctr_dev, key_dev, out_dev, s));
   CK(cudaEventRecord(ctx->ev_b, s));
-  return wait_event(ctx->ev_b, 3600.0);
+  return ctx_wait(ctx, ctx->ev_b, 3600.0);
 }
 
 // ------------------------------------------------------------------------
 // Lambda iteration (Eq. 2, Sect. 3.2)
 // ------------------------------------------------------------------------
 extern "C" int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* g, int n_src, const rt_source* src, const rt_optics* op,
-                                 const rt_dust* du, const rt_trace_params* prm, const rt_lambda_params* lp,
+                                 const rt_dust* du_in, const rt_trace_params* prm, const rt_lambda_params* lp,
                                  double* T_dev, rt_lambda_result* res, void* cuda_stream) {
+  std::vector<double> kabs_store;
+  rt_dust du_res;
+  const rt_dust* du = resolve_dust(du_in, op, kabs_store, du_res);
   if (!ctx || !g || !src || !op || !du || !prm || !lp || !T_dev || !res)
     return fail(RT_ERR_INVALID, "rt_lambda_iterate: NULL argument");
   if (lp->max_iter < 1 || lp->max_iter > 64) return fail(RT_ERR_INVALID, "rt_lambda_iterate: max_iter must be 1..64");
@@ -1353,7 +1442,7 @@ extern "C" int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* g, int n_src, const
   rc = check_dust(du, op->n_lambda);
   if (rc) return rc;
   memset(res, 0, sizeof *res);
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const auto t0 = std::chrono::steady_clock::now();
@@ -1416,11 +1505,12 @@ extern "C" int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* g, int n_src, const
     rc = solve(A);
     if (rc) return rc;
     CK(max_rel_change(T_dev, T_prev, hits, g->child, nc, lp->min_hits, scal, s));
-    double v = 0.0;
-    CK(cudaMemcpyAsync(&v, scal, sizeof v, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->pin_count, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(ctx->ev_c, s));
-    rc = wait_event(ctx->ev_c, to);
+    rc = ctx_wait(ctx, ctx->ev_c, to);
     if (rc) return rc;
+    double v = 0.0;
+    memcpy(&v, ctx->pin_count, sizeof v);
     res->history[it - 1] = v;
     res->n_iter = it;
     if (v < lp->tol) break;
@@ -1433,9 +1523,12 @@ extern "C" int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* g, int n_src, const
 // Lambda iteration with subiterations (Sect. 3.2, App. B)
 // ------------------------------------------------------------------------
 extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, const rt_source* src,
-                                    const rt_optics* op, const rt_dust* du, const rt_trace_params* prm,
+                                    const rt_optics* op, const rt_dust* du_in, const rt_trace_params* prm,
                                     const rt_lambda_params* lp, const rt_subiter_params* sp, double* T_dev,
                                     rt_subiter_result* res, void* cuda_stream) {
+  std::vector<double> kabs_store;
+  rt_dust du_res;
+  const rt_dust* du = resolve_dust(du_in, op, kabs_store, du_res);
   if (!ctx || !g || !src || !op || !du || !prm || !lp || !sp || !T_dev || !res)
     return fail(RT_ERR_INVALID, "rt_lambda_subiterate: NULL argument");
   const int n_steps = sp->n_steps > 0 ? sp->n_steps : lp->max_iter;
@@ -1450,7 +1543,7 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   rc = check_dust(du, op->n_lambda);
   if (rc) return rc;
   memset(res, 0, sizeof *res);
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const auto t0 = std::chrono::steady_clock::now();
@@ -1515,7 +1608,7 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   auto read_scalars = [&](double* out, int n) -> int {
     CK(cudaMemcpyAsync(ctx->pin_count, scal, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(ctx->ev_c, s));
-    int r = wait_event(ctx->ev_c, to);
+    int r = ctx_wait(ctx, ctx->ev_c, to);
     if (r) return r;
     memcpy(out, ctx->pin_count, sizeof(double) * n);
     return RT_OK;
@@ -1648,7 +1741,7 @@ extern "C" int rt_trace_batch(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_le
   std::vector<TraceArgs> args;
   int rc = jobs_to_args(n_jobs, jobs, args);
   if (rc) return rc;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   if (ledgers) memset(ledgers, 0, sizeof(rt_ledger) * n_jobs);
   return run_jobs(ctx, n_jobs, args.data(), ledgers, (cudaStream_t)cuda_stream, jobs[0].params);
@@ -1689,7 +1782,7 @@ extern "C" int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_b
   std::vector<TraceArgs> args;
   int rc = jobs_to_args(n_jobs, jobs, args);
   if (rc) return rc;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   rt_batch* b = new rt_batch();
   b->ctx = ctx;
@@ -1761,13 +1854,13 @@ extern "C" int rt_batch_create(rt_ctx* ctx, int n_jobs, const rt_job* jobs, rt_b
 
 extern "C" int rt_batch_run(rt_batch* b, rt_ledger* ledgers, double timeout_s, void* cuda_stream) {
   if (!b) return fail(RT_ERR_INVALID, "rt_batch_run: NULL batch");
-  std::lock_guard<std::mutex> lk(b->ctx->mu);
+  CTX_ENTER(b->ctx);
   DeviceGuard dg(b->ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   CK(cudaEventRecord(b->ev0, s));
   CK(cudaGraphLaunch(b->exec, s));
   CK(cudaEventRecord(b->ev1, s));
-  int rc = wait_event(b->ev1, timeout_s > 0 ? timeout_s : 3600.0);
+  int rc = ctx_wait(b->ctx, b->ev1, timeout_s > 0 ? timeout_s : 3600.0);
   if (rc) return rc;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, b->ev0, b->ev1);
@@ -1798,7 +1891,7 @@ extern "C" int rt_autotune(rt_ctx* ctx, int n_jobs, const rt_job* jobs, double s
   std::vector<TraceArgs> args;
   int rc = jobs_to_args(n_jobs, jobs, args);
   if (rc) return rc;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   // trial copies of the jobs with scaled package counts and private outputs
   std::vector<rt_trace_params> prm(n_jobs);
@@ -1929,7 +2022,7 @@ extern "C" int rt_merge_uniform(rt_ctx* ctx, const int* root, const double* box,
     if (std::fabs(box[a] / root[a] - h0) > 1e-12 * h0) return fail(RT_ERR_INVALID, "rt_merge_uniform: cells are not cubic");
   if (!(kappa >= 0.0) || !std::isfinite(kappa) || !(tau_max > 0.0) || !(contrast_max >= 1.0))
     return fail(RT_ERR_INVALID, "rt_merge_uniform: need kappa >= 0, tau_max > 0, contrast_max >= 1");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  CTX_ENTER(ctx);
   DeviceGuard dg(ctx->device);
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   long long nref[24] = {0};

@@ -27,8 +27,32 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[RT_NOALLOC_SCRA
 
 namespace {
 
-std::mutex g_setup_mu;
+// Held for the whole host side of a call: the calls share the device
+// scratch and the host staging area below, so they are serialised on the
+// host (their kernels may still overlap on the GPU if the caller uses
+// several streams; see rt.h).
+std::mutex g_call_mu;
 void* g_scratch_addr[RT_NOALLOC_MAX_DEVICES] = {};
+// host image of the job table, uploaded at every call (a static array rather
+// than a stack one: the call needs only a few hundred bytes of stack)
+alignas(256) unsigned char g_host_stage[RT_NOALLOC_SCRATCH_BYTES];
+long long g_pk[RT_NOALLOC_MAX_SOURCES][RT_MAX_LAMBDA];
+
+// Poll the stream until its work is done, at most timeout seconds.  The
+// upload before the launch and the read-back after it use pageable host
+// memory, and such copies wait for the stream's earlier work inside the
+// copy call, unbounded; polling first keeps every wait of the call bounded.
+int wait_stream(cudaStream_t st, double timeout, const char* what) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int spins = 0;; ++spins) {
+    const cudaError_t q = cudaStreamQuery(st);
+    if (q == cudaSuccess) return RT_OK;
+    if (q != cudaErrorNotReady) return rtk::set_error(RT_ERR_CUDA, "rt_trace_noalloc: device error while waiting");
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > timeout)
+      return rtk::set_error(RT_ERR_TIMEOUT, what);
+    if (spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
 
 // Device address of the scratch array on `device`, looked up once per device
 // with that device current (in host code the array's name is only a
@@ -36,7 +60,6 @@ void* g_scratch_addr[RT_NOALLOC_MAX_DEVICES] = {};
 int scratch_address(int device, unsigned char** out) {
   if (device < 0 || device >= RT_NOALLOC_MAX_DEVICES)
     return rtk::set_error(RT_ERR_INVALID, "rt_trace_noalloc: device index out of range");
-  std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_addr[device]) {
     int prev = -1;
     cudaGetDevice(&prev);
@@ -90,6 +113,15 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     if (S.kind == RT_SRC_BEAM && !(S.dir[0] * S.dir[0] + S.dir[1] * S.dir[1] + S.dir[2] * S.dir[2] > 0.0))
       return set_error(RT_ERR_INVALID, "rt_trace_noalloc: beam direction is zero");
   }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the call uploads from and reads back into host memory and polls the
+  // stream: none of this can be captured into a graph
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess)
+    return set_error(RT_ERR_CUDA, "rt_trace_noalloc: cannot query the stream");
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(RT_ERR_INVALID, "rt_trace_noalloc: the stream is capturing a graph");
+  std::lock_guard<std::mutex> lk(g_call_mu);
   rt_grid_info gi;
   if (rt_grid_get_info(grid, &gi) != RT_OK) return RT_ERR_INVALID;
   cudaPointerAttributes pa;
@@ -98,7 +130,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
   const int device = pa.device;
 
   // packages per (source, bin)
-  long long pk[RT_NOALLOC_MAX_SOURCES][RT_MAX_LAMBDA];
+  long long (&pk)[RT_NOALLOC_MAX_SOURCES][RT_MAX_LAMBDA] = g_pk;
   double energy_tot = 0.0;
   for (int s = 0; s < n_src; ++s)
     for (int b = 0; b < nl; ++b) energy_tot += src[s].bin_energy[b];
@@ -135,7 +167,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
   int rc = scratch_address(device, &dev);
   if (rc) return rc;
 
-  alignas(256) unsigned char host[RT_NOALLOC_SCRATCH_BYTES];
+  unsigned char* host = g_host_stage;
   memset(host, 0, bytes);  // ledger and package counter start at zero
   JobDev& J = *reinterpret_cast<JobDev*>(host + o_job);
   J.node = gi.node;
@@ -218,7 +250,6 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
   }
   J.led_shift = ledger_shift(w0_max, p->rr_wmin, p->rr_p);
 
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != device) cudaSetDevice(device);
@@ -226,6 +257,9 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     if (prev >= 0 && prev != device) cudaSetDevice(prev);
     return code;
   };
+  const double timeout = p->timeout_s > 0 ? p->timeout_s : 3600.0;
+  rc = wait_stream(st, timeout, "rt_trace_noalloc: earlier work on the stream did not finish in time");
+  if (rc) return restore(rc);
   if (cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return restore(set_error(RT_ERR_CUDA, "rt_trace_noalloc: upload of the job table failed"));
   if (total > 0) {
@@ -249,20 +283,15 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
                      reinterpret_cast<unsigned long long*>(dev + o_cnt), total, cfg, q, st) != cudaSuccess)
       return restore(set_error(RT_ERR_CUDA, "rt_trace_noalloc: kernel launch failed"));
   }
+  // bounded wait on the stream (no event objects), then the ledger: the
+  // copy is issued only once the kernel has finished, so a timeout leaves
+  // no copy pending into this call's memory
+  rc = wait_stream(st, timeout, "rt_trace_noalloc: device work did not finish in time");
+  if (rc) return restore(rc);
   LedgerDev hl;
-  if (cudaMemcpyAsync(&hl, dev + o_led, sizeof hl, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (cudaMemcpyAsync(&hl, dev + o_led, sizeof hl, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
     return restore(set_error(RT_ERR_CUDA, "rt_trace_noalloc: ledger read-back failed"));
-  // bounded wait on the stream (no event objects)
-  const double timeout = p->timeout_s > 0 ? p->timeout_s : 3600.0;
-  const auto t0 = std::chrono::steady_clock::now();
-  for (int spins = 0;; ++spins) {
-    const cudaError_t q = cudaStreamQuery(st);
-    if (q == cudaSuccess) break;
-    if (q != cudaErrorNotReady) return restore(set_error(RT_ERR_CUDA, "rt_trace_noalloc: device error while waiting"));
-    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > timeout)
-      return restore(set_error(RT_ERR_TIMEOUT, "rt_trace_noalloc: device work did not finish in time"));
-    if (spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
-  }
   if (ledger) {
     ledger->emitted = hl.emitted;
     ledger->absorbed = hl.absorbed;

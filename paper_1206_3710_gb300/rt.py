@@ -27,6 +27,7 @@ EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "r
             "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load", "rt_server_create",
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
             "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles",
+            "rt_ctx_set_tile_records",
             "rt_peel_tables_create", "rt_peel_tables_destroy", "rt_peel_tables_size", "rt_peel_tables_read",
             "rt_peel_tabulated", "rt_lambda_subiterate", "rt_merge_uniform"]
 
@@ -270,6 +271,11 @@ class Context:
         < 0 automatic."""
         _check(lib().rt_ctx_set_tiles(self.handle, int(tile_edge)))
 
+    def set_tile_records(self, max_records: int) -> None:
+        """Capacity of the tiled tracer's record buffers (the emission chunk);
+        <= 0: the default."""
+        _check(lib().rt_ctx_set_tile_records(self.handle, C.c_int64(int(max_records))))
+
     def close(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.rt_ctx_destroy(self.handle)
@@ -326,7 +332,8 @@ def make_dust(lambda_um, kappa_abs, dnu, T_min, T_max, keep: _Keep) -> rt_dust:
     d = rt_dust()
     d.n_lambda = int(len(lambda_um))
     d.lambda_um = keep.dp(lambda_um, np.float64, C.c_double)
-    d.kappa_abs = keep.dp(kappa_abs, np.float64, C.c_double)
+    # None: the Lambda drivers take kappa_abs = (1 - albedo) kappa_ext of the optics
+    d.kappa_abs = None if kappa_abs is None else keep.dp(kappa_abs, np.float64, C.c_double)
     d.dnu = keep.dp(dnu, np.float64, C.c_double)
     d.T_min, d.T_max = float(T_min), float(T_max)
     return d
@@ -492,8 +499,7 @@ def rt_lambda_iterate(ctx: Context, grid: Grid, sources, optics, T_out, *, max_i
     keep = _Keep()
     src = make_sources(sources, len(optics.kappa_ext), keep)
     op = make_optics(optics, keep)
-    kabs = (1.0 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
-    du = make_dust(optics.lambda_um, kabs, optics.dnu, T_min, T_max, keep)
+    du = make_dust(optics.lambda_um, None, optics.dnu, T_min, T_max, keep)
     prm = make_params(keep, **params)
     lp = rt_lambda_params(max_iter=int(max_iter), tol=float(tol), min_hits=float(min_hits),
                           dust_packets_total=int(dust_packets_total), dust_packets_per_bin=int(dust_packets_per_bin))
@@ -517,8 +523,7 @@ def rt_lambda_subiterate(ctx: Context, grid: Grid, sources, optics, T_out, *, su
     keep = _Keep()
     src = make_sources(sources, len(optics.kappa_ext), keep)
     op = make_optics(optics, keep)
-    kabs = (1.0 - np.asarray(optics.albedo)) * np.asarray(optics.kappa_ext)
-    du = make_dust(optics.lambda_um, kabs, optics.dnu, T_min, T_max, keep)
+    du = make_dust(optics.lambda_um, None, optics.dnu, T_min, T_max, keep)
     prm = make_params(keep, **params)
     lp = rt_lambda_params(max_iter=int(max_iter), tol=float(tol), min_hits=float(min_hits),
                           dust_packets_total=int(dust_packets_total), dust_packets_per_bin=int(dust_packets_per_bin))

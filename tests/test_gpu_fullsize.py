@@ -1,0 +1,197 @@
+"""GPU against the FP64 oracle at the size of the headline workload: the
+molecular cloud of 256^3 root cells refined 3 levels (2.76e7 cells), 20
+wavelengths from 0.1 to 1000 um, an isotropic external field, peel-off to six
+256^2 images along the coordinate axes, Russian roulette below 1e-4 W0.
+
+* FP32 in the launch configuration of the benchmark (1e7 packages per
+  wavelength: three emission chunks of tile records, 8 tiles of 128^3 root
+  cells traced in rounds, the deferred peel-off queue) against the oracle's
+  independent estimate: per wavelength, the absorbed energy summed over each
+  grid level and each observer's image total, within the combined Monte
+  Carlo error; the energy ledger closed to 1e-5.
+* FP64 with the oracle's random streams, on a window of package indices
+  deep into the stream: every package's history (escaped weight, scatterings,
+  fate, exit point), absorbed energy per cell and image pixels.
+* The chunked emission and an overflowing peel-off queue, forced at small
+  size through the context's capacity knobs, package by package against
+  the oracle.
+
+The full-size cases hold about 22 GB of device memory, the benchmark's own
+footprint (absorbed energy for 20 wavelengths, two tile record buffers, the
+peel-off queue).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1206_3710_gb300 import synth  # noqa: E402
+
+DEV = "cuda:0"
+RR = dict(rr_wmin=1e-4, rr_p=0.9)
+
+
+@pytest.fixture(scope="module")
+def rt():
+    from paper_1206_3710_gb300 import build
+    build.build()
+    from paper_1206_3710_gb300 import rt as _rt
+    return _rt
+
+
+@pytest.fixture(scope="module")
+def cloud():
+    return synth.cloud(n_root=256, levels=3, n_lambda=20, packets_per_bin=10_000_000, n_pix=256)
+
+
+@pytest.fixture(scope="module")
+def otree(orc, cloud):
+    return orc.Tree(cloud.tree)
+
+
+def _level_sums(a, off):
+    """[bins][levels] sums of absorbed energy (cells are in level order)."""
+    return np.stack([a[:, off[l]:off[l + 1]].sum(axis=1) for l in range(len(off) - 1)], axis=1)
+
+
+def test_headline_fp32_against_oracle(rt, orc, cloud, otree):
+    m = cloud
+    off = m.tree.level_offsets()
+    nl, obs = m.optics.n_lambda, m.observers
+    ctx = rt.Context(0)
+    g = rt.Grid(ctx, m.tree)
+    absorbed = torch.zeros((nl, g.n_cells), dtype=torch.float64, device=DEV)
+    images = torch.zeros((obs.n_obs, nl, obs.ny, obs.nx), dtype=torch.float64, device=DEV)
+    npk = 10_000_000
+    led = rt.rt_peel(ctx, g, m.sources, m.optics, obs, images, absorbed, seed=1002, precision=32,
+                     packets_per_bin=npk, **RR)
+    torch.cuda.synchronize()
+    # the launch configuration of the benchmark
+    assert led["n_tiles"] == 8 and led["n_rounds"] > 8
+    assert led["n_packets"] == npk * nl
+    assert led["n_peel_deferred"] > 0.9 * led["n_scatter"]
+    bal = led["emitted"] + led["rr_gain"] - led["absorbed"] - led["escaped"] - led["rr_loss"] - led["killed"]
+    assert abs(bal) <= 1e-5 * led["emitted"]
+    gl = torch.stack([absorbed[:, off[l]:off[l + 1]].sum(dim=1) for l in range(len(off) - 1)], dim=1)
+    g_lev = gl.cpu().numpy()
+    g_img = images.sum(dim=(2, 3)).cpu().numpy()          # [obs][bins]
+    assert abs(g_lev.sum() - led["absorbed"]) <= 1e-6 * led["absorbed"]
+    del absorbed, images
+    ctx.close()
+
+    # the oracle's estimate from K independent batches (their own seed)
+    K, n = 16, 400
+    lev, img = [], []
+    for k in range(K):
+        r = orc.trace(otree, m.sources, m.optics, n, seed=7001, packet_offset=k * n, observers=obs,
+                      n_threads=16, **RR)
+        lev.append(_level_sums(r["absorbed"], off))
+        img.append(r["images"].sum(axis=(2, 3)))
+    lev, img = np.array(lev), np.array(img)
+    for name, gv, ov in (("levels", g_lev, lev), ("images", g_img, img)):
+        mean = ov.mean(axis=0)
+        se = ov.std(axis=0, ddof=1) / math.sqrt(K)
+        se_g = se * math.sqrt(K * n / npk)               # the GPU's own error, same estimator
+        sig = np.sqrt(se ** 2 + se_g ** 2)
+        ok = sig > 0
+        z = (gv[ok] - mean[ok]) / sig[ok]
+        # Student t with K-1 = 15 degrees of freedom: |t| > 3 in 0.9 %
+        assert np.mean(np.abs(z) > 3) < 0.05, (name, np.sort(np.abs(z))[-5:])
+        assert np.abs(z).max() < 6, (name, np.abs(z).max())
+        # where the oracle is precise (relative error < 3 %: the two upper
+        # levels, the short-wavelength images), no bias: the signed mean
+        # relative deviation stays below 1 %
+        good = ok & (se < 0.03 * np.abs(mean))
+        assert good.sum() >= (20 if name == "levels" else 5), (name, good.sum())
+        assert abs(np.mean(gv[good] / mean[good] - 1)) < 0.01, name
+
+
+def test_headline_fp64_packages_match_oracle(rt, orc, cloud, otree):
+    """A window of package indices 4e6..4e6+500 of every wavelength, traced
+    tiled in FP64 over the full-size grid with peel-off and roulette."""
+    m = cloud
+    obs, nl = m.observers, m.optics.n_lambda
+    ctx = rt.Context(0)
+    g = rt.Grid(ctx, m.tree)
+    npk, off = 500, 4_000_000
+    absorbed = torch.zeros((1, g.n_cells), dtype=torch.float64, device=DEV)
+    images = torch.zeros((obs.n_obs, 1, obs.ny, obs.nx), dtype=torch.float64, device=DEV)
+    log = torch.zeros((npk * nl, 10), dtype=torch.float64, device=DEV)
+    led = rt.rt_peel(ctx, g, m.sources, m.optics, obs, images, absorbed, seed=1002, precision=64,
+                     packets_per_bin=npk, packet_offset=off, packet_log=log, per_lambda=False, **RR)
+    torch.cuda.synchronize()
+    assert led["n_tiles"] == 8 and led["n_rounds"] > 1
+    ref = orc.trace(otree, m.sources, m.optics, npk, seed=1002, packet_offset=off, observers=obs, record=True,
+                    per_lambda=False, n_threads=16, **RR)
+    g_rec, o_rec = log.cpu().numpy(), ref["rec"]
+    same = (np.isclose(g_rec[:, 0], o_rec[:, 0], rtol=1e-9, atol=0)
+            | (np.abs(g_rec[:, 0] - o_rec[:, 0]) <= 1e-12 * np.abs(o_rec[:, 0]).max()))
+    same &= (g_rec[:, 1] == o_rec[:, 1]) & (g_rec[:, 3] == o_rec[:, 3])
+    same &= np.all(np.isclose(g_rec[:, 4:7], o_rec[:, 4:7], rtol=1e-9, atol=1e-6 * np.abs(o_rec[:, 4:7]).max()),
+                   axis=1)
+    # boundary-tie divergences: at most 1e-4 of the packages (here: one)
+    assert (~same).sum() <= max(1, int(1e-4 * same.size)), np.nonzero(~same)[0][:5]
+    ol = ref["ledger"]
+    assert led["n_scatter"] == ol["n_scatter"] or (~same).any()
+    if same.all():
+        assert led["n_cross"] == ol["n_cross"] and led["n_peel_cross"] == ol["n_peel_cross"]
+        a, ra = absorbed.cpu().numpy(), ref["absorbed"]
+        np.testing.assert_allclose(a, ra, rtol=1e-8, atol=1e-9 * np.abs(ra).max())
+        im, ri = images.cpu().numpy(), ref["images"]
+        np.testing.assert_allclose(im, ri, rtol=1e-8, atol=1e-9 * np.abs(ri).max())
+        for k in ("emitted", "absorbed", "escaped", "rr_gain", "rr_loss"):
+            assert led[k] == pytest.approx(ol[k], rel=1e-9, abs=1e-12 * ol["emitted"]), k
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_chunked_emission_and_overflowing_queue(rt, orc, precision):
+    """Emission in many chunks of tile records (a 2000-record buffer for
+    18000 packages), 64 tiles, and a peel-off queue of 300 records that most
+    scatterings overflow (their peel-off runs inline): FP64 package by package
+    against the oracle; FP32 identical to the untiled, unchunked FP32 run."""
+    m = synth.cloud(n_root=32, levels=2, seed=5, n_lambda=6, packets_per_bin=0, n_pix=32)
+    nl, obs = m.optics.n_lambda, m.observers
+    npk = 3000
+    kw = dict(seed=51, precision=precision, packets_per_bin=npk, rr_wmin=1e-3, rr_p=0.5)
+
+    def run(tiles, records, queue):
+        c = rt.Context(0)
+        c.set_tiles(tiles)
+        c.set_tile_records(records)
+        c.set_peel_queue(queue)
+        g = rt.Grid(c, m.tree)
+        ab = torch.zeros((nl, g.n_cells), dtype=torch.float64, device=DEV)
+        im = torch.zeros((obs.n_obs, nl, obs.ny, obs.nx), dtype=torch.float64, device=DEV)
+        log = torch.zeros((npk * nl, 10), dtype=torch.float64, device=DEV)
+        led = rt.rt_peel(c, g, m.sources, m.optics, obs, im, ab, packet_log=log, **kw)
+        torch.cuda.synchronize()
+        out = (ab.cpu().numpy(), im.cpu().numpy(), log.cpu().numpy(), led)
+        c.close()
+        return out
+
+    ab, im, log, led = run(8, 2000, 300)
+    assert led["n_tiles"] == 64 and led["n_scatter"] > 1000
+    assert led["n_peel_deferred"] == 300
+    assert led["n_launches"] >= 1 + 9 * 2            # nine emission chunks, each traced in rounds
+    if precision == 64:
+        tree = orc.Tree(m.tree)
+        ref = orc.trace(tree, m.sources, m.optics, npk, seed=51, observers=obs, record=True, rr_wmin=1e-3,
+                        rr_p=0.5)
+        o = ref["rec"]
+        same = np.isclose(log[:, 0], o[:, 0], rtol=1e-9, atol=1e-12 * np.abs(o[:, 0]).max())
+        same &= (log[:, 1] == o[:, 1]) & (log[:, 3] == o[:, 3])
+        assert (~same).sum() <= max(1, int(1e-4 * same.size))
+        np.testing.assert_allclose(ab, ref["absorbed"], rtol=1e-8, atol=1e-9 * np.abs(ref["absorbed"]).max())
+        np.testing.assert_allclose(im, ref["images"], rtol=1e-8, atol=1e-9 * np.abs(ref["images"]).max())
+        assert led["n_peel_cross"] == ref["ledger"]["n_peel_cross"]
+    else:
+        ab0, im0, log0, led0 = run(0, 0, 0)               # untiled, all peel-off inline
+        np.testing.assert_array_equal(log, log0)
+        np.testing.assert_allclose(ab, ab0, rtol=1e-12, atol=1e-14 * np.abs(ab0).max())
+        np.testing.assert_allclose(im, im0, rtol=1e-12, atol=1e-14 * np.abs(im0).max())
+        for k in ("n_cross", "n_scatter", "n_peel_cross", "n_peel_out"):
+            assert led[k] == led0[k], k

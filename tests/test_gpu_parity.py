@@ -309,31 +309,62 @@ def test_fp64_clump_per_packet_and_cells(rt, ctx, orc):
     _close(out["images"], out["ref"]["images"])
 
 
-def _statistical(gpu, ref, sumsq, hits, npk_total):
+def _statistical(gpu, ref, sumsq, hits, npk_total, min_hits=1000):
+    """Independent runs of the same estimator with npk_total packages each:
+    z = difference / sqrt(2 var), var from the oracle's per-element sum of
+    squared package contributions (a Gaussian leaves 0.27 % beyond 3 sigma;
+    1 % allowed); signed mean relative deviation below 1 % over elements with
+    at least min_hits contributions."""
     var = np.maximum(sumsq - ref * ref / npk_total, 0)
-    sig = np.sqrt(2 * var)          # same-variance estimate for both sides
+    sig = np.sqrt(2 * var)
     ok = sig > 0
     z = (gpu[ok] - ref[ok]) / sig[ok]
     assert np.mean(np.abs(z) > 3) < 0.01, np.mean(np.abs(z) > 3)
-    well = hits >= 1000
-    if well.sum():
-        assert abs((gpu[well] / ref[well] - 1).mean()) < 0.01
+    if hits is not None:
+        well = hits >= min_hits
+        if well.sum():
+            assert abs((gpu[well] / ref[well] - 1).mean()) < 0.01
+
+
+def _shared_stream_error(gpu, ref, sumsq, npk_total, hits=None):
+    """FP32 against FP64 with the same random streams: only the packages whose
+    paths part ways through FP32 rounding contribute to the difference, so it
+    stays far below the Monte Carlo error of one run (sigma = sqrt(var)).
+    Returns (max, mean) relative error over the elements with >= 1e3
+    contributions (all nonzero elements when hits is None)."""
+    var = np.maximum(sumsq - ref * ref / npk_total, 0)
+    sig = np.sqrt(var)
+    ok = sig > 0
+    d = np.abs(gpu[ok] - ref[ok]) / sig[ok]
+    # independent runs would leave 16 % of elements beyond 2 sigma
+    assert np.mean(d > 2) < 0.01, np.mean(d > 2)
+    sel = (hits >= 1000) if hits is not None else (ref != 0)
+    rel = np.abs(gpu[sel] / ref[sel] - 1)
+    return float(rel.max()), float(rel.mean())
 
 
 def test_fp32_clump_statistical(rt, ctx, orc):
+    """FP32 tracing against the FP64 oracle, per cell and per image pixel:
+    within 3 sigma of an independent oracle run, and close to the oracle run
+    with the same streams."""
     m = synth.tiny_clump()
     npk = 100000
     out = _run_pair(rt, ctx, orc, m, npk, 32, seed=12)
     led = out["led"]
     assert abs(led["absorbed"] + led["escaped"] - led["emitted"]) <= 1e-5 * led["emitted"]
     ref = out["ref"]
-    _statistical(out["absorbed"][0], ref["absorbed"][0], ref["sumsq"][0], ref["hits"][0], npk)
-    # peel-off image totals agree within MC error of the image sum
-    gi, oi = out["images"].sum(), ref["images"].sum()
-    assert abs(gi / oi - 1) < 0.02
-    # same streams: most packages follow the same path in f32
+    tree = orc.Tree(m.tree)
+    ind = orc.trace(tree, m.sources, m.optics, npk, seed=112, observers=m.observers, validation=True, n_threads=8)
+    _statistical(out["absorbed"][0], ind["absorbed"][0], ind["sumsq"][0], ind["hits"][0], npk)
+    _statistical(out["images"], ind["images"], ind["image_sumsq"], None, npk)
+    # same streams: FP32 rounding changes few paths
     g, o = out["log"], ref["rec"]
     assert np.mean(g[:, 1] == o[:, 1]) > 0.95
+    a_max, a_mean = _shared_stream_error(out["absorbed"][0], ref["absorbed"][0], ref["sumsq"][0], npk,
+                                         ref["hits"][0])
+    assert a_mean < 2e-3, (a_max, a_mean)
+    i_max, i_mean = _shared_stream_error(out["images"], ref["images"], ref["image_sumsq"], npk)
+    assert np.isfinite(i_max) and i_mean < 0.1, (i_max, i_mean)
 
 
 def _small_cloud(n_root=32, levels=2, n_lambda=6, seed=5):

@@ -1,0 +1,66 @@
+"""Bounded waits: a call whose deadline (params.timeout_s) runs out returns
+RT_ERR_TIMEOUT while its kernels keep running, the context refuses new work
+with RT_ERR_BUSY until they have finished, and the work, once finished, is
+complete and equal to an untimed run.  The deadline is a host-side limit on
+a finite kernel (its packages end by themselves): nothing faults or hangs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1206_3710_gb300 import synth  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def rt():
+    from paper_1206_3710_gb300 import build
+    build.build()
+    from paper_1206_3710_gb300 import rt as _rt
+    return _rt
+
+
+def _long_job(rt, ctx, grid, m, kw, want_ms=300.0):
+    """Package count for which the FP64 trace takes about want_ms."""
+    npk = 20000
+    out = torch.zeros((1, grid.n_cells), dtype=torch.float64, device=DEV)
+    led = rt.rt_trace(ctx, grid, m.sources, m.optics, out, packets_per_bin=npk, **kw)
+    per_pk = max(led["kernel_ms"], 0.05) / npk
+    return int(min(2e8, max(npk, want_ms / per_pk)))
+
+
+def test_trace_timeout_then_busy_then_complete(rt):
+    ctx = rt.Context(0)
+    m = synth.tiny_clump()
+    grid = rt.Grid(ctx, m.tree)
+    kw = dict(seed=21, precision=64, per_lambda=False)
+    npk = _long_job(rt, ctx, grid, m, kw)
+    ref = torch.zeros((1, grid.n_cells), dtype=torch.float64, device=DEV)
+    led_ref = rt.rt_trace(ctx, grid, m.sources, m.optics, ref, packets_per_bin=npk, **kw)
+    assert led_ref["kernel_ms"] > 50.0, led_ref["kernel_ms"]
+
+    stream = torch.cuda.Stream(device=DEV)
+    out = torch.zeros_like(ref)
+    torch.cuda.synchronize()
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace(ctx, grid, m.sources, m.optics, out, packets_per_bin=npk, timeout_s=1e-4, stream=stream, **kw)
+    assert e.value.code == rt.RT_ERR_TIMEOUT
+    # the kernel (hundreds of ms) is still running: the context takes no work
+    assert not stream.query()
+    other = torch.zeros_like(ref)
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace(ctx, grid, m.sources, m.optics, other, packets_per_bin=100, **kw)
+    assert e.value.code == rt.RT_ERR_BUSY
+    # once the stream has drained, the timed-out run is complete and the
+    # context works again
+    stream.synchronize()
+    got = out.cpu().numpy()
+    want = ref.cpu().numpy()
+    np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-9 * np.abs(want).max())
+    led = rt.rt_trace(ctx, grid, m.sources, m.optics, other, packets_per_bin=npk, **kw)
+    assert led["n_cross"] == led_ref["n_cross"] and led["n_scatter"] == led_ref["n_scatter"]
+    assert led["emitted"] == pytest.approx(led_ref["emitted"], rel=1e-12)

@@ -424,3 +424,34 @@ def test_peel_tabulated_exact_along_axes(orc):
     assert exact["images"].sum() > 0
     np.testing.assert_allclose(tab["images"], exact["images"], rtol=1e-11, atol=1e-14 * exact["images"].max())
     assert tab["ledger"]["n_peel_cross"] < exact["ledger"]["n_peel_cross"]
+
+
+def test_image_variance_tally_sums_whole_packages(orc):
+    """The per-pixel variance tally squares each package's whole
+    contribution to a pixel (all its scatterings together): a run of N
+    packages gives sum_k c_k^2 with c_k the image of package k traced on its
+    own (packet_offset k, whose weight is N times the joint run's)."""
+    m = synth.tiny_clump()
+    tree = orc.Tree(m.tree)
+    opt = synth.Optics(lambda_um=m.optics.lambda_um, kappa_ext=m.optics.kappa_ext * 3.0,
+                       albedo=np.full(1, 0.9), g_hg=np.full(1, 0.3), dnu=m.optics.dnu)
+    # few pixels, so that one package often lands in a pixel more than once
+    obs = synth.Observers(dirs=np.array([[0.0, 0.0, 1.0], [0.6, 0.8, 0.0]]),
+                          ups=np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]), nx=3, ny=3, fov=m.observers.fov)
+    n = 40
+    joint = orc.trace(tree, m.sources, opt, n, seed=31, observers=obs, validation=True, n_threads=4)
+    assert joint["ledger"]["n_scatter"] > 3 * n
+    sq = np.zeros_like(joint["images"])
+    tot = np.zeros_like(joint["images"])
+    repeat = False
+    for k in range(n):
+        one = orc.trace(tree, m.sources, opt, 1, seed=31, observers=obs, packet_offset=k)
+        c = one["images"] / n
+        tot += c
+        sq += c * c
+        repeat |= one["ledger"]["n_scatter"] > 4
+    assert repeat
+    np.testing.assert_allclose(tot, joint["images"], rtol=1e-12, atol=1e-15 * joint["images"].max())
+    np.testing.assert_allclose(joint["image_sumsq"], sq, rtol=1e-12, atol=1e-15 * sq.max())
+    # squaring each scattering's contribution instead would give less
+    assert (joint["image_sumsq"] >= joint["images"] ** 2 / n - 1e-15).all()

@@ -76,3 +76,62 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(rt):
     with pytest.raises(rt.RtError) as e:
         rt.rt_trace_noalloc(grid, [dust], m.optics, out, seed=1, packets_per_bin=10)
     assert e.value.code == rt.RT_ERR_INVALID
+
+
+def test_noalloc_allocates_no_device_memory(rt):
+    """The entry point's one property: after the first call on the device
+    (which loads the module), further calls leave the device's free memory
+    unchanged."""
+    ctx = rt.Context(0)
+    m = synth.tiny_clump()
+    grid = rt.Grid(ctx, m.tree)
+    outs = [torch.zeros((1, grid.n_cells), dtype=torch.float64, device=DEV) for _ in range(3)]
+    kw = dict(seed=5, precision=32, packets_per_bin=20000)
+    rt.rt_trace_noalloc(grid, m.sources, m.optics, outs[0], **kw)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for o in outs[1:]:
+        rt.rt_trace_noalloc(grid, m.sources, m.optics, o, **kw)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_refuses_a_capturing_stream(rt):
+    ctx = rt.Context(0)
+    m = synth.tiny_clump()
+    grid = rt.Grid(ctx, m.tree)
+    out = torch.zeros((1, grid.n_cells), dtype=torch.float64, device=DEV)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream(device=DEV)
+    g = torch.cuda.CUDAGraph()
+    code = None
+    with torch.cuda.graph(g, stream=s):
+        try:
+            rt.rt_trace_noalloc(grid, m.sources, m.optics, out, seed=1, packets_per_bin=10, stream=s)
+        except rt.RtError as e:
+            code = e.code
+    assert code == rt.RT_ERR_INVALID
+
+
+def test_noalloc_timeout_then_complete(rt):
+    """A deadline that runs out returns RT_ERR_TIMEOUT with the kernel still
+    running; once the stream has drained the result is complete."""
+    ctx = rt.Context(0)
+    m = synth.tiny_clump()
+    grid = rt.Grid(ctx, m.tree)
+    kw = dict(seed=22, precision=64, per_lambda=False)
+    probe = torch.zeros((1, grid.n_cells), dtype=torch.float64, device=DEV)
+    led = rt.rt_trace(ctx, grid, m.sources, m.optics, probe, packets_per_bin=20000, **kw)
+    npk = int(min(2e8, max(20000, 300.0 / (max(led["kernel_ms"], 0.05) / 20000))))
+    ref = torch.zeros_like(probe)
+    led_ref = rt.rt_trace(ctx, grid, m.sources, m.optics, ref, packets_per_bin=npk, **kw)
+    assert led_ref["kernel_ms"] > 50.0, led_ref["kernel_ms"]
+    stream = torch.cuda.Stream(device=DEV)
+    out = torch.zeros_like(ref)
+    torch.cuda.synchronize()
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace_noalloc(grid, m.sources, m.optics, out, packets_per_bin=npk, timeout_s=1e-4, stream=stream, **kw)
+    assert e.value.code == rt.RT_ERR_TIMEOUT
+    stream.synchronize()
+    _close(out.cpu().numpy(), ref.cpu().numpy())
