@@ -79,9 +79,13 @@ def parse():
     ap.add_argument("--flux-frac", type=float, default=0.05,
                     help="disc subiterations: full step once the emission below the level changed by this fraction")
     ap.add_argument("--models", type=int, default=64, help="batch: models per launch")
-    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve: seconds of Poisson arrivals")
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-max-packets", type=float, default=1e7)
+    ap.add_argument("--serve-max-packets", type=float, default=1e8)
+    ap.add_argument("--serve-slots", type=int, default=2)
+    ap.add_argument("--serve-batch", type=int, default=64)
+    ap.add_argument("--line-serve-seconds", type=float, default=15.0,
+                    help="seconds of Poisson arrivals for the serving figures of the default line (0: none)")
     ap.add_argument("--n-root", type=int, default=256)
     ap.add_argument("--levels", type=int, default=3)
     ap.add_argument("--n-lambda", type=int, default=20)
@@ -172,15 +176,14 @@ def l2_read_gbs(dev):
     in the 129 MB L2, repeated (CUDA events, best of 5 runs of 50)."""
     import torch
     x = torch.ones(48 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
-    out = torch.empty((), dtype=torch.float32, device=dev)
     for _ in range(10):
-        torch.sum(x, out=out)
+        x.sum()
     best = 0.0
     for _ in range(5):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(50):
-            torch.sum(x, out=out)
+            x.sum()
         e1.record()
         torch.cuda.synchronize()
         best = max(best, 50 * x.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
@@ -421,6 +424,9 @@ def main():
         cpu = None
         if not a.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(a, m, a.cpu_packets_per_bin or None)
+        serving = None
+        if a.line_serve_seconds > 0 and world == 1:
+            serving = serving_figures(a, ctx, dev)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32" if a.precision == 32 else "f64",
@@ -428,7 +434,7 @@ def main():
                "config": workload_config(a, m), "packets_per_s": pk / (t_ms * 1e-3),
                "crossings_per_step": {"trace": L0["n_cross"], "peel": L0["n_peel_cross"]},
                "scatterings_per_step": L0["n_scatter"], "roofline": roof, "roofline_peel_kernel": peel_roof,
-               "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "serving": serving,
                "gpu_launches": sum(int(L["n_launches"]) + 2 for L in leds),  # + dust table and temperature
                "tiling": {"tiles": L0["n_tiles"], "rounds_per_step": L0["n_rounds"]},
                "energy_balance": (L0["emitted"] - L0["absorbed"] - L0["escaped"]) / L0["emitted"],
@@ -437,6 +443,21 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def serving_figures(a, ctx, dev):
+    """The serving pattern on a bounded stream: Poisson arrivals of jobs drawn
+    from the cloud, disc, clump and batch model families (1e5..1e8 packages,
+    1..30 wavelengths), p50/p99 latency, packages/s served, the same jobs one
+    at a time, and all of them submitted at once."""
+    import torch
+
+    import bench_families
+    from paper_1206_3710_gb300 import rt, synth
+    res = bench_families.serve_measure(rt, synth, ctx, torch, a.line_serve_seconds, a.serve_rate,
+                                       a.serve_max_packets, slots=a.serve_slots, max_batch_jobs=a.serve_batch)
+    res.pop("library", None)
+    return res
 
 
 def e2e_run(a, m, ctx, dev, stream, kw, lam, kabs, dnu):

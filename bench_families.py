@@ -231,27 +231,53 @@ def _optics_subset(synth, m, nl, rng):
     return opt, src
 
 
-def run_serve(a, rt, synth, ctx, torch):
-    rng = np.random.default_rng(1005)
-    t0 = time.perf_counter()
+def serve_jobs(synth, seconds, rate, max_packets, seed=1005):
+    """A seeded Poisson stream of jobs drawn from the serving library's model
+    families: (arrival time, model id, sources, optics, trace parameters)."""
+    rng = np.random.default_rng(seed)
     library = _serve_library(synth)
-    t_gen = time.perf_counter() - t0
-    n_jobs = max(1, int(a.serve_seconds * a.serve_rate))
-    arrivals = np.cumsum(rng.exponential(1.0 / a.serve_rate, n_jobs))
+    n_jobs = max(1, int(seconds * rate))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
     jobs = []
     for i in range(n_jobs):
         mid = int(rng.integers(len(library)))
         m = library[mid]
         nl = int(rng.integers(1, min(30, m.optics.n_lambda) + 1))
         opt, src = _optics_subset(synth, m, nl, rng)
-        total = math.exp(rng.uniform(math.log(1e5), math.log(a.serve_max_packets)))
+        total = math.exp(rng.uniform(math.log(1e5), math.log(max_packets)))
         ppb = max(1, int(total / nl))
         jobs.append((arrivals[i], mid, src, opt, dict(seed=5000 + i, job=i, precision=32, packets_per_bin=ppb,
                                                       rr_wmin=1e-4, rr_p=0.9, per_lambda=False)))
+    return library, jobs
+
+
+def serve_measure(rt, synth, ctx, torch, seconds, rate, max_packets, slots=2, max_batch_jobs=64,
+                  batch_window_ms=2.0):
+    """Serving under Poisson arrivals (latency p50/p99 from submission to the
+    result being ready on the device, packages/s), the same jobs one at a
+    time with their own launches, and the burst capacity (all jobs submitted
+    at once).  Results stay on the device and are released, in all three."""
+    library, jobs = serve_jobs(synth, seconds, rate, max_packets)
+    n_jobs = len(jobs)
+    arrivals = np.array([j[0] for j in jobs])
     free = torch.cuda.mem_get_info()[0]
-    srv = rt.Server(ctx, hbm_budget=int(0.5 * free), slots=2, max_batch_jobs=64, batch_window_ms=2.0)
-    for mid, m in enumerate(library):
-        srv.add_model(mid, m.tree)
+
+    def server():
+        srv = rt.Server(ctx, hbm_budget=int(0.5 * free), slots=slots, max_batch_jobs=max_batch_jobs,
+                        batch_window_ms=batch_window_ms)
+        for mid, m in enumerate(library):
+            srv.add_model(mid, m.tree)
+        # warm-up: the first job of each model makes its grid resident
+        first = {}
+        for (t_arr, mid, src, opt, prm) in jobs:
+            first.setdefault(mid, (src, opt, prm))
+        for mid, (src, opt, prm) in first.items():
+            t = srv.submit(mid, src, opt, **dict(prm, packets_per_bin=100))
+            srv.wait(t, 600)
+            srv.release(t)
+        return srv
+
+    srv = server()
     tickets = [None] * n_jobs
     done_lat = [None] * n_jobs
     leds = [None] * n_jobs
@@ -259,15 +285,14 @@ def run_serve(a, rt, synth, ctx, torch):
     def collector():
         for i in range(n_jobs):
             while tickets[i] is None:
-                time.sleep(0.001)
+                time.sleep(0.0005)
             srv.wait(tickets[i], 3600)
             _, led, lat = srv.poll(tickets[i])
-            srv.fetch(tickets[i])
+            srv.release(tickets[i])
             done_lat[i], leds[i] = lat, led
 
     th = threading.Thread(target=collector, daemon=True)
     th.start()
-    clk = _clock_start()
     start = time.perf_counter()
     for i, (t_arr, mid, src, opt, prm) in enumerate(jobs):
         dt = start + t_arr - time.perf_counter()
@@ -276,41 +301,51 @@ def run_serve(a, rt, synth, ctx, torch):
         tickets[i] = srv.submit(mid, src, opt, **prm)
     th.join()
     wall = time.perf_counter() - start
-    clocks = clk.stop()
     srv.close()
     lat = np.array(done_lat)
     pk = sum(x["n_packets"] for x in leds)
     # the same jobs one at a time, each with its own launch (no overlap, no batching)
     grids = [rt.Grid(ctx, m.tree) for m in library]
+    bufs = [torch.zeros((1, g.n_cells), dtype=torch.float64, device="cuda") for g in grids]
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for (t_arr, mid, src, opt, prm) in jobs:
-        ab = torch.zeros((1, grids[mid].n_cells), dtype=torch.float64, device="cuda")
-        rt.rt_trace(ctx, grids[mid], src, opt, ab, **prm)
+        bufs[mid].zero_()
+        rt.rt_trace(ctx, grids[mid], src, opt, bufs[mid], **prm)
     torch.cuda.synchronize()
     serial = time.perf_counter() - t1
-    offered = pk / float(arrivals[-1])
+    for g in grids:
+        g.close()
+    del bufs
     # capacity: the same jobs submitted at once (served back to back, batched)
-    srv = rt.Server(ctx, hbm_budget=int(0.5 * free), slots=2, max_batch_jobs=64, batch_window_ms=2.0)
-    for mid, m in enumerate(library):
-        srv.add_model(mid, m.tree)
+    srv = server()
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     ts = [srv.submit(mid, src, opt, **prm) for (t_arr, mid, src, opt, prm) in jobs]
     for t in ts:
         srv.wait(t, 3600)
-        srv.fetch(t)
+        srv.release(t)
     burst = time.perf_counter() - t2
     srv.close()
+    return {"jobs": n_jobs, "seconds": float(arrivals[-1]), "rate_per_s": rate,
+            "packets_per_job": f"log-uniform 1e5..{max_packets:.0e}", "wavelengths_per_job": "uniform 1..30",
+            "slots": slots, "max_batch_jobs": max_batch_jobs, "packets_total": int(pk),
+            "offered_packets_per_s": pk / float(arrivals[-1]),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "served_packets_per_s": pk / wall, "served_wall_s": wall,
+            "burst_packets_per_s": pk / burst, "burst_wall_s": burst,
+            "serial_packets_per_s": pk / serial, "serial_busy_s": serial,
+            "burst_over_serial": serial / burst, "library": [m.name for m in library]}
+
+
+def run_serve(a, rt, synth, ctx, torch):
+    t0 = time.perf_counter()
+    clk = _clock_start()
+    res = serve_measure(rt, synth, ctx, torch, a.serve_seconds, a.serve_rate, a.serve_max_packets,
+                        slots=a.serve_slots, max_batch_jobs=a.serve_batch)
+    clocks = clk.stop()
     line = {"metric": "serving: p50/p99 job latency and packages/s under Poisson arrivals",
-            "workload": "serve", "jobs": n_jobs, "rate_per_s": a.serve_rate, "arrival_window_s": float(arrivals[-1]),
-            "packets_total": int(pk), "offered_packets_per_s": offered,
-            "served": {"wall_s": wall, "packets_per_s": pk / wall, "p50_ms": float(np.percentile(lat, 50)),
-                       "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())},
-            "one_at_a_time": {"busy_s": serial, "packets_per_s": pk / serial},
-            "burst_capacity": {"wall_s": burst, "packets_per_s": pk / burst},
-            "library": [m.name for m in library], "model_generation_s": t_gen, "clocks": clocks,
-            "packets_per_job": f"log-uniform 1e5..{a.serve_max_packets:.0e}", "wavelengths_per_job": "uniform 1..30"}
+            "workload": "serve", **res, "clocks": clocks, "wall_s": time.perf_counter() - t0}
     print(json.dumps(line))
 
 

@@ -95,6 +95,11 @@ struct rt_server {
   std::vector<std::thread> workers;
   std::vector<rt_ctx*> slot_ctx;
   std::vector<cudaStream_t> slot_stream;
+  // results leave through this stream and job memory is released on it
+  // (cudaFreeAsync): a plain cudaFree would wait for the whole device,
+  // i.e. for the other slots' launches, and serialise them
+  cudaStream_t io_stream = nullptr;
+  std::mutex io_mu;
   std::mutex build_mu;
 
   // evict idle resident grids (least recently used first) until `need` fits
@@ -256,6 +261,21 @@ extern "C" int rt_server_create(rt_ctx* ctx, const rt_server_config* cfg, rt_ser
     S->slot_ctx.push_back(c);
     S->slot_stream.push_back(st);
   }
+  if (cudaStreamCreateWithFlags(&S->io_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    for (size_t i = 0; i < S->slot_ctx.size(); ++i) {
+      cudaStreamDestroy(S->slot_stream[i]);
+      rt_ctx_destroy(S->slot_ctx[i]);
+    }
+    delete S;
+    return set_error(RT_ERR_CUDA, "rt_server_create: stream creation failed");
+  }
+  // keep the memory of finished jobs in the device's stream-ordered pool for
+  // the next ones instead of returning it at every synchronisation
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   for (int i = 0; i < cfg->max_slots; ++i) S->workers.emplace_back([S, i] { S->worker(i); });
   *out = S;
   return RT_OK;
@@ -280,6 +300,7 @@ extern "C" void rt_server_destroy(rt_server* S) {
     cudaStreamDestroy(S->slot_stream[i]);
     rt_ctx_destroy(S->slot_ctx[i]);
   }
+  if (S->io_stream) cudaStreamDestroy(S->io_stream);
   delete S;
 }
 
@@ -416,16 +437,25 @@ extern "C" int rt_server_fetch(rt_server* S, uint64_t ticket, double* absorbed_h
   Job* j = owned.get();
   cudaSetDevice(S->device);
   int rc = RT_OK;
-  if (j->state == Job::DONE) {
-    if (absorbed_host && j->absorbed &&
-        cudaMemcpy(absorbed_host, j->absorbed, j->acc_bytes - j->img_bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
-      rc = set_error(RT_ERR_CUDA, "rt_server_fetch: copy of absorbed energy failed");
-    if (rc == RT_OK && images_host && j->images &&
-        cudaMemcpy(images_host, j->images, j->img_bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
-      rc = set_error(RT_ERR_CUDA, "rt_server_fetch: copy of images failed");
+  {
+    // the job's launch has finished (its slot waited for it before marking
+    // it done): copy out and release its memory on the server's own stream
+    std::lock_guard<std::mutex> lk(S->io_mu);
+    cudaStream_t io = S->io_stream;
+    if (j->state == Job::DONE) {
+      if (absorbed_host && j->absorbed &&
+          cudaMemcpyAsync(absorbed_host, j->absorbed, j->acc_bytes - j->img_bytes, cudaMemcpyDeviceToHost, io) !=
+              cudaSuccess)
+        rc = set_error(RT_ERR_CUDA, "rt_server_fetch: copy of absorbed energy failed");
+      if (rc == RT_OK && images_host && j->images &&
+          cudaMemcpyAsync(images_host, j->images, j->img_bytes, cudaMemcpyDeviceToHost, io) != cudaSuccess)
+        rc = set_error(RT_ERR_CUDA, "rt_server_fetch: copy of images failed");
+      if (rc == RT_OK && (absorbed_host || images_host) && cudaStreamSynchronize(io) != cudaSuccess)
+        rc = set_error(RT_ERR_CUDA, "rt_server_fetch: copy failed");
+    }
+    if (j->absorbed) cudaFreeAsync(j->absorbed, io);
+    if (j->images) cudaFreeAsync(j->images, io);
   }
-  if (j->absorbed) cudaFree(j->absorbed);
-  if (j->images) cudaFree(j->images);
   {
     std::lock_guard<std::mutex> lk(S->mu);
     S->used -= j->acc_bytes;

@@ -746,6 +746,11 @@ class Server:
                                      img.ctypes.data_as(C.c_void_p) if img is not None else None))
         return ab, img
 
+    def release(self, ticket: int) -> None:
+        """Drop a finished job's results without copying them out."""
+        self.shapes.pop(ticket, None)
+        _check(lib().rt_server_fetch(self.handle, ticket, None, None))
+
     def stats(self):
         used = C.c_size_t()
         q = C.c_int()

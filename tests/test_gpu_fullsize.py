@@ -97,7 +97,12 @@ def test_headline_fp32_against_oracle(rt, orc, cloud, otree):
         se = ov.std(axis=0, ddof=1) / math.sqrt(K)
         se_g = se * math.sqrt(K * n / npk)               # the GPU's own error, same estimator
         sig = np.sqrt(se ** 2 + se_g ** 2)
-        ok = sig > 0
+        # entries the oracle sampled with a handful of events (deep-level
+        # cells, scattered light at wavelengths of albedo 0.01) have no
+        # usable error estimate from the batches: compared where the
+        # relative error is below 25 % (about 16 events or more)
+        ok = (sig > 0) & (se < 0.25 * np.abs(mean))
+        assert ok.sum() >= (40 if name == "levels" else 20), (name, ok.sum())
         z = (gv[ok] - mean[ok]) / sig[ok]
         # Student t with K-1 = 15 degrees of freedom: |t| > 3 in 0.9 %
         assert np.mean(np.abs(z) > 3) < 0.05, (name, np.sort(np.abs(z))[-5:])
