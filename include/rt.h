@@ -368,16 +368,21 @@ int rt_tune_load(rt_ctx* ctx, const char* path);
  * recently used first, never while a running job uses them).  A request is
  * admitted, in arrival order, when its footprint -- its grid unless resident
  * plus its accumulators -- fits the free part of hbm_budget.  max_slots
- * dispatcher threads, each with its own context and stream, run every
- * admitted request (up to max_batch_jobs, after waiting batch_window_ms for
- * company) as one batched persistent launch; requests arriving meanwhile
- * join the next launch of whichever slot frees first.  Results stay on the
- * device (counted in the budget) until rt_server_fetch. */
+ * dispatcher threads, each with its own context and stream, run the
+ * admitted requests in arrival order as batched persistent launches: a free
+ * slot takes the next request and, after waiting batch_window_ms for
+ * company, the requests behind it while the launch holds at most
+ * max_batch_jobs jobs and max_batch_packets packages (a request larger than
+ * that runs alone); requests arriving meanwhile join the next launch of
+ * whichever slot frees first, so the slots' work overlaps on the device.
+ * Results stay on the device (counted in the budget) until
+ * rt_server_fetch. */
 typedef struct {
   size_t hbm_budget;
   int max_slots;          /* 1..16 */
   int max_batch_jobs;
   double batch_window_ms;
+  int64_t max_batch_packets; /* <= 0: no limit */
 } rt_server_config;
 
 typedef struct {
@@ -397,6 +402,11 @@ int rt_server_submit(rt_server* srv, const rt_serve_job* job, uint64_t* ticket);
 /* done = 1 once finished; latency_ms = submit to completion of its launch. */
 int rt_server_poll(rt_server* srv, uint64_t ticket, int* done, rt_ledger* ledger, double* latency_ms);
 int rt_server_wait(rt_server* srv, uint64_t ticket, double timeout_s);
+/* Device time of the launch a finished request ran in, in ms after the
+ * server's creation (CUDA events around the slot's launch): launches of
+ * different slots whose intervals intersect ran on the device at the same
+ * time.  -1 for a request not run (yet). */
+int rt_server_job_times(rt_server* srv, uint64_t ticket, double* t_start_ms, double* t_end_ms);
 /* Copies results to host arrays (either may be NULL) and releases the job. */
 int rt_server_fetch(rt_server* srv, uint64_t ticket, double* absorbed_host, double* images_host);
 int rt_server_stats(rt_server* srv, size_t* used_bytes, int* queued, int* running);
@@ -551,6 +561,13 @@ int rt_merge_uniform(rt_ctx* ctx, const int* root, const double* box, int n_fine
 int rt_walk(rt_ctx* ctx, const rt_grid* grid, int64_t n_rays, const double* origins_dev,
             const double* dirs_dev, int precision, int64_t max_seg, int64_t* cells_dev,
             double* lengths_dev, int64_t* counts_dev, void* cuda_stream);
+
+/* L2 read bandwidth in GB/s (diagnostic for the rooflines of L2-resident
+ * work; no counterpart in the paper): buf_dev is a zeroed device buffer of
+ * `bytes` (16-byte aligned, smaller than the L2), read `reps` times per
+ * launch with 16-byte loads cached in L2 only; best of 5 timed launches
+ * after one warm-up launch. */
+int rt_l2_read_bandwidth(rt_ctx* ctx, void* buf_dev, int64_t bytes, int reps, double* gbs, void* cuda_stream);
 
 /* Philox4x32-10 blocks for n (counter, key) pairs: ctr_dev [n][4], key_dev
  * [n][2], out_dev [n][4] (device uint32). */

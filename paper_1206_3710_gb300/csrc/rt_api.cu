@@ -1412,6 +1412,29 @@ extern "C" int rt_walk(rt_ctx* ctx, const rt_grid* g, int64_t n_rays, const doub
   return ctx_wait(ctx, ctx->ev_b, 3600.0);
 }
 
+extern "C" int rt_l2_read_bandwidth(rt_ctx* ctx, void* buf_dev, int64_t bytes, int reps, double* gbs,
+                                    void* cuda_stream) {
+  if (!ctx || !buf_dev || !gbs || bytes < 16 || reps < 1 || ((uintptr_t)buf_dev & 15))
+    return fail(RT_ERR_INVALID, "rt_l2_read_bandwidth: bad argument");
+  CTX_ENTER(ctx);
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CK(launch_l2_read(buf_dev, bytes, reps, ctx->sm_count, s));  // warm-up: fills L2
+  double best = 0.0;
+  for (int k = 0; k < 5; ++k) {
+    CK(cudaEventRecord(ctx->ev_a, s));
+    CK(launch_l2_read(buf_dev, bytes, reps, ctx->sm_count, s));
+    CK(cudaEventRecord(ctx->ev_b, s));
+    const int rc = ctx_wait(ctx, ctx->ev_b, 60.0);
+    if (rc) return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b);
+    if (ms > 0.f) best = std::max(best, (double)(bytes / 16 * 16) * reps / (ms * 1e-3) / 1e9);
+  }
+  *gbs = best;
+  return RT_OK;
+}
+
 extern "C" int rt_philox(rt_ctx* ctx, int64_t n, const uint32_t* ctr_dev, const uint32_t* key_dev, uint32_t* out_dev,
                          void* cuda_stream) {
   if (!ctx || n < 0 || (n > 0 && (!ctr_dev || !key_dev || !out_dev))) return fail(RT_ERR_INVALID, "rt_philox: bad argument");

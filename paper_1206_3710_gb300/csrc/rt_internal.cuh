@@ -271,6 +271,8 @@ cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, 
                         long long* counts, cudaStream_t s);
 cudaError_t launch_philox(long long n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                           cudaStream_t s);
+// reads a zeroed device buffer `reps` times through L2 (bandwidth diagnostic)
+cudaError_t launch_l2_read(const void* buf, long long bytes, int reps, int sm_count, cudaStream_t s);
 
 // grid build kernels
 cudaError_t scan_flags_u8(const uint8_t* flags, long long n, unsigned long long* excl, void* tmp,

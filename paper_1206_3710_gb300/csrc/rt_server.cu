@@ -58,6 +58,7 @@ struct Job {
   rt_observers obs;
   std::vector<double> obs_dir, obs_up;
   // accounting
+  int64_t n_packets = 0;
   size_t acc_bytes = 0, img_bytes = 0;
   int bins = 1;
   int64_t n_cells = 0;
@@ -69,6 +70,9 @@ struct Job {
   int rc = RT_OK;
   rt_ledger ledger;
   Clock::time_point t_submit, t_done;
+  // device time of the launch the job ran in, ms after the server's
+  // reference event (-1: not run)
+  double dev_t0 = -1.0, dev_t1 = -1.0;
 };
 
 int64_t tree_cells(const rt_tree_desc& d) {
@@ -100,6 +104,9 @@ struct rt_server {
   // i.e. for the other slots' launches, and serialise them
   cudaStream_t io_stream = nullptr;
   std::mutex io_mu;
+  // device-time bracket of each slot's launches, against one reference event
+  cudaEvent_t ref_ev = nullptr;
+  std::vector<cudaEvent_t> slot_ev0, slot_ev1;
   std::mutex build_mu;
 
   // evict idle resident grids (least recently used first) until `need` fits
@@ -155,8 +162,12 @@ void rt_server::worker(int slot) {
         std::this_thread::sleep_for(std::chrono::microseconds((long)(cfg.batch_window_ms * 1000)));
         lk.lock();
       }
+      int64_t pk = 0;
       while (!admitted.empty() && (int)batch.size() < cfg.max_batch_jobs) {
-        batch.push_back(admitted.front());
+        Job* nx = admitted.front();
+        if (!batch.empty() && cfg.max_batch_packets > 0 && pk + nx->n_packets > cfg.max_batch_packets) break;
+        pk += nx->n_packets;
+        batch.push_back(nx);
         admitted.pop_front();
       }
       for (Job* j : batch) j->state = Job::RUNNING;
@@ -215,13 +226,27 @@ void rt_server::worker(int slot) {
     }
     int rc = RT_OK;
     std::vector<rt_ledger> leds(ok.size());
-    if (!ok.empty()) rc = rt_trace_batch(c, (int)ok.size(), rj.data(), leds.data(), s);
+    double t0 = -1.0, t1 = -1.0;
+    if (!ok.empty()) {
+      cudaEventRecord(slot_ev0[slot], s);
+      rc = rt_trace_batch(c, (int)ok.size(), rj.data(), leds.data(), s);
+      cudaEventRecord(slot_ev1[slot], s);
+      float a = 0.f, b = 0.f;
+      if (cudaEventSynchronize(slot_ev1[slot]) == cudaSuccess &&
+          cudaEventElapsedTime(&a, ref_ev, slot_ev0[slot]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, ref_ev, slot_ev1[slot]) == cudaSuccess) {
+        t0 = a;
+        t1 = b;
+      }
+    }
     const auto t = Clock::now();
     {
       std::lock_guard<std::mutex> lk(mu);
       for (size_t i = 0; i < ok.size(); ++i) {
         Job* j = ok[i];
         j->ledger = leds[i];
+        j->dev_t0 = t0;
+        j->dev_t1 = t1;
         j->rc = rc;
         j->state = (rc == RT_OK || rc == RT_ERR_STEP_LIMIT) ? Job::DONE : Job::FAILED;
         j->t_done = t;
@@ -269,6 +294,15 @@ extern "C" int rt_server_create(rt_ctx* ctx, const rt_server_config* cfg, rt_ser
     delete S;
     return set_error(RT_ERR_CUDA, "rt_server_create: stream creation failed");
   }
+  bool ev_ok = cudaEventCreate(&S->ref_ev) == cudaSuccess && cudaEventRecord(S->ref_ev, S->io_stream) == cudaSuccess;
+  S->slot_ev0.assign(cfg->max_slots, nullptr);
+  S->slot_ev1.assign(cfg->max_slots, nullptr);
+  for (int i = 0; i < cfg->max_slots && ev_ok; ++i)
+    ev_ok = cudaEventCreate(&S->slot_ev0[i]) == cudaSuccess && cudaEventCreate(&S->slot_ev1[i]) == cudaSuccess;
+  if (!ev_ok || cudaEventSynchronize(S->ref_ev) != cudaSuccess) {
+    rt_server_destroy(S);
+    return set_error(RT_ERR_CUDA, "rt_server_create: event creation failed");
+  }
   // keep the memory of finished jobs in the device's stream-ordered pool for
   // the next ones instead of returning it at every synchronisation
   cudaMemPool_t pool;
@@ -301,6 +335,11 @@ extern "C" void rt_server_destroy(rt_server* S) {
     rt_ctx_destroy(S->slot_ctx[i]);
   }
   if (S->io_stream) cudaStreamDestroy(S->io_stream);
+  if (S->ref_ev) cudaEventDestroy(S->ref_ev);
+  for (cudaEvent_t e : S->slot_ev0)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : S->slot_ev1)
+    if (e) cudaEventDestroy(e);
   delete S;
 }
 
@@ -363,6 +402,10 @@ extern "C" int rt_server_submit(rt_server* S, const rt_serve_job* r, uint64_t* t
   if (r->params->packets && r->params->packets_per_bin <= 0 && r->params->packets_total <= 0) {
     j->packets.assign(r->params->packets, r->params->packets + (size_t)r->n_src * nl);
     j->params.packets = j->packets.data();
+    for (int64_t v : j->packets) j->n_packets += v > 0 ? v : 0;
+  } else {
+    j->n_packets = r->params->packets_per_bin > 0 ? r->params->packets_per_bin * (int64_t)nl * r->n_src
+                                                  : r->params->packets_total;
   }
   j->bins = r->params->per_lambda ? nl : 1;
   j->acc_bytes = sizeof(double) * (size_t)j->bins * (size_t)j->n_cells;
@@ -405,6 +448,17 @@ extern "C" int rt_server_poll(rt_server* S, uint64_t ticket, int* done, rt_ledge
     if (latency_ms) *latency_ms = 1e3 * std::chrono::duration<double>(j->t_done - j->t_submit).count();
     if (j->state == Job::FAILED) return set_error(j->rc ? j->rc : RT_ERR_CUDA, "rt_server_poll: the job failed");
   }
+  return RT_OK;
+}
+
+extern "C" int rt_server_job_times(rt_server* S, uint64_t ticket, double* t_start_ms, double* t_end_ms) {
+  using namespace rtk;
+  if (!S || !t_start_ms || !t_end_ms) return set_error(RT_ERR_INVALID, "rt_server_job_times: NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(ticket);
+  if (it == S->jobs.end()) return set_error(RT_ERR_INVALID, "rt_server_job_times: unknown ticket");
+  *t_start_ms = it->second->dev_t0;
+  *t_end_ms = it->second->dev_t1;
   return RT_OK;
 }
 

@@ -221,6 +221,37 @@ __device__ __forceinline__ void ledger_flush(WarpLedger& SL, const JobDev* jobs,
 enum { ST_DEAD = 0, ST_TRACE = 1, ST_PEEL = 2, ST_DONE = 3 };
 enum { EV_NONE = 0, EV_IDLE, EV_INTERACT, EV_ESCAPE, EV_CUT, EV_KILL, EV_DEGEN, EV_TILE, EV_SPLIT };
 
+// A lane that meets an event (scattering, escape, tile change, ...) waits in
+// the stepping loop until `batch` lanes of its warp have one, or until no
+// lane is stepping any more; the warp then leaves the loop and serves the
+// waiting events together.  Each visit to the event code costs the warp the
+// same whatever the number of lanes it serves, so serving one event per
+// visit (batch 1) spends most issue slots on lanes that do nothing.
+#ifndef RT_EV_BATCH
+#define RT_EV_BATCH 4
+#endif
+#ifndef RT_PEEL_EV_BATCH
+#define RT_PEEL_EV_BATCH 4
+#endif
+// counter slot for each calling lane with one atomic per group of lanes
+// that arrive together (the tile-record and peel-off queues have one
+// counter each, which every lane of the device increments)
+__device__ __forceinline__ unsigned long long claim_slot(unsigned long long* ctr) {
+  const unsigned m = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0ull;
+  if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ bool keep_stepping(int ev, int batch) {
+  const unsigned waiting = __ballot_sync(0xFFFFFFFFu, ev > EV_IDLE);
+  const unsigned stepping = __ballot_sync(0xFFFFFFFFu, ev == EV_NONE);
+  return stepping != 0u && __popc(waiting) < batch;
+}
+
 // ------------------------------------------------------------------------
 // deferred peel-off records
 // ------------------------------------------------------------------------
@@ -504,7 +535,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
   // current position, direction, weight, optical depth to the next
   // interaction, random-number position and counters)
   auto tile_push = [&]() {
-    const unsigned long long slot = atomicAdd(T.n_out, 1ull);
+    const unsigned long long slot = claim_slot(T.n_out);
     if (slot < (unsigned long long)T.cap_out) {
       TRec rr;
       auto& r = IO::b(rr);
@@ -898,7 +929,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           }
         }
       }
-    } while (__all_sync(FULL, ev == EV_NONE || ev == EV_IDLE));
+    } while (keep_stepping(ev, RT_EV_BATCH));
 
     // ------------------------------------------------------------- slow path
     if (ev == EV_NONE || ev == EV_IDLE) continue;
@@ -1007,7 +1038,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
         bool inline_peel = PEEL && jobs[job].n_obs > 0;
         if (inline_peel && Q.cap > 0) {
           // defer: the peel-off kernel marches this record to every observer
-          const unsigned long long slot = atomicAdd(Q.count, 1ull);
+          const unsigned long long slot = claim_slot(Q.count);
           if (slot < (unsigned long long)Q.cap) {
             PeelIO<R>::put(Q.rec, slot, g, dx, dy, dz, W, peel_meta(g.lev, C.bin[t], job));
             book_u(SL, jobs, job, wid, U_DEFER, 1ull);
@@ -1280,7 +1311,7 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
           }
         }
       }
-    } while (__all_sync(FULL, ev == EV_NONE || ev == EV_IDLE));
+    } while (keep_stepping(ev, RT_PEEL_EV_BATCH));
 
     if (ev == EV_ESCAPE) {
       const R c = pw * Num<R>::exp_(-taup);
@@ -1666,6 +1697,29 @@ cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, 
   if (G == 0) return cudaSuccess;
   if (precision == 64) walk_kernel<double><<<G, B, 0, s>>>(job_dev, n_rays, origins, dirs, max_seg, cells, lengths, counts);
   else walk_kernel<float><<<G, B, 0, s>>>(job_dev, n_rays, origins, dirs, max_seg, cells, lengths, counts);
+  return cudaGetLastError();
+}
+
+// L2 read bandwidth (diagnostic for the rooflines): every thread streams
+// 16-byte loads cached in L2 only (ld.global.cg) over a buffer that fits in
+// L2, `reps` times; the XOR of the words is stored only if it equals a value
+// a zeroed buffer cannot give, which keeps the loads
+__global__ void l2_read_kernel(const uint4* __restrict__ p, long long n, int reps, unsigned* __restrict__ sink) {
+  unsigned acc = 0u;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int r = 0; r < reps; ++r)
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const uint4 v = __ldcg(p + i);
+      acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+  if (acc == 0x9E3779B9u) sink[0] = acc;
+}
+
+cudaError_t launch_l2_read(const void* buf, long long bytes, int reps, int sm_count, cudaStream_t s) {
+  const long long n = bytes / 16;
+  if (n <= 0) return cudaSuccess;
+  l2_read_kernel<<<sm_count * 8, 256, 0, s>>>(static_cast<const uint4*>(buf), n, reps,
+                                              const_cast<unsigned*>(static_cast<const unsigned*>(buf)));
   return cudaGetLastError();
 }
 

@@ -26,8 +26,8 @@ EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "r
             "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate", "rt_trace_batch", "rt_batch_create",
             "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load", "rt_server_create",
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
-            "rt_server_stats", "rt_server_destroy", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles",
-            "rt_ctx_set_tile_records",
+            "rt_server_stats", "rt_server_destroy", "rt_server_job_times", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles",
+            "rt_ctx_set_tile_records", "rt_l2_read_bandwidth",
             "rt_peel_tables_create", "rt_peel_tables_destroy", "rt_peel_tables_size", "rt_peel_tables_read",
             "rt_peel_tabulated", "rt_lambda_subiterate", "rt_merge_uniform"]
 
@@ -128,7 +128,7 @@ class rt_job(C.Structure):
 
 class rt_server_config(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("max_batch_jobs", C.c_int),
-                ("batch_window_ms", C.c_double)]
+                ("batch_window_ms", C.c_double), ("max_batch_packets", C.c_int64)]
 
 
 class rt_serve_job(C.Structure):
@@ -204,6 +204,7 @@ def lib():
     L.rt_server_submit.argtypes = [vp, C.POINTER(rt_serve_job), C.POINTER(C.c_uint64)]
     L.rt_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(rt_ledger), C.POINTER(C.c_double)]
     L.rt_server_wait.argtypes = [vp, C.c_uint64, C.c_double]
+    L.rt_server_job_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.rt_server_fetch.argtypes = [vp, C.c_uint64, vp, vp]
     L.rt_server_stats.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.rt_server_destroy.argtypes = [vp]
@@ -580,6 +581,14 @@ def rt_merge_uniform(ctx: Context, rho, root, box, kappa: float, tau_max: float 
                           n_refined=n_ref[: n_lev.value].copy(), refine_flags=flags[:n].copy(), density=dens[:n].copy())
 
 
+def rt_l2_read_bandwidth(ctx: Context, buf, reps: int = 40, stream=None) -> float:
+    """L2 read bandwidth (GB/s) over a zeroed device tensor that fits in L2."""
+    gbs = C.c_double()
+    _check(lib().rt_l2_read_bandwidth(ctx.handle, _ptr(buf), C.c_int64(buf.numel() * buf.element_size()),
+                                      int(reps), C.byref(gbs), _stream(stream)))
+    return gbs.value
+
+
 def rt_philox(ctx: Context, ctr, key, out, stream=None) -> None:
     n = int(ctr.shape[0])
     _check(lib().rt_philox(ctx.handle, n, _ptr(ctr), _ptr(key), _ptr(out), _stream(stream)))
@@ -692,9 +701,9 @@ class Server:
     continuous batching over `slots` streams (rt_server_* in librt)."""
 
     def __init__(self, ctx: Context, hbm_budget: int, slots: int = 2, max_batch_jobs: int = 64,
-                 batch_window_ms: float = 1.0):
+                 batch_window_ms: float = 1.0, max_batch_packets: int = 0):
         cfg = rt_server_config(hbm_budget=int(hbm_budget), max_slots=int(slots), max_batch_jobs=int(max_batch_jobs),
-                               batch_window_ms=float(batch_window_ms))
+                               batch_window_ms=float(batch_window_ms), max_batch_packets=int(max_batch_packets))
         h = C.c_void_p()
         _check(lib().rt_server_create(ctx.handle, C.byref(cfg), C.byref(h)))
         self.handle, self.ctx = h, ctx
@@ -726,6 +735,12 @@ class Server:
         img = None if observers is None else (observers.n_obs, bins, observers.ny, observers.nx)
         self.shapes[t.value] = ((bins, self.cells[int(model_id)]), img)
         return t.value
+
+    def device_times(self, ticket: int):
+        """(start, end) in ms of device time of the launch the request ran in."""
+        a, b = C.c_double(), C.c_double()
+        _check(lib().rt_server_job_times(self.handle, ticket, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def poll(self, ticket: int):
         done = C.c_int()

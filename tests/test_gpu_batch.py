@@ -106,3 +106,17 @@ def test_autotune_and_persistence(rt, ctx, models, tmp_path):
     rt.rt_tune_load(ctx2, path)
     leds = rt.rt_trace_batch(ctx2, jobs)
     assert all(x["n_packets"] > 0 for x in leds)
+
+
+def test_batched_fp64_jobs_match_oracle(rt, ctx, models, orc):
+    """Inside one batched launch, FP64 jobs (with and without peel-off) give
+    the oracle's absorbed energy and images for their own (seed, job) key."""
+    grids, jobs = _jobs(rt, ctx, models, 64, peel_every=2)
+    rt.rt_trace_batch(ctx, jobs)
+    for i in (0, 1, 4):
+        j, m = jobs[i], models[i]
+        ref = orc.trace(orc.Tree(m.tree), m.sources, m.optics, m.packets_per_bin, seed=m.seed, job=i,
+                        observers=j.observers, n_threads=8)
+        _close(j.absorbed.cpu().numpy(), ref["absorbed"])
+        if j.observers is not None:
+            _close(j.images.cpu().numpy(), ref["images"])

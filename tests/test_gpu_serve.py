@@ -99,3 +99,48 @@ def test_admission_waits_for_memory(rt, ctx, library):
         srv.submit(7, m.sources, m.optics, big, seed=1, packets_per_bin=10)
     assert e.value.code == rt.RT_ERR_BUSY
     srv.close()
+
+
+def test_served_fp64_request_matches_oracle(rt, ctx, library, orc):
+    """A request served among others gives the oracle's absorbed energy and
+    images for its (seed, job) key."""
+    srv = rt.Server(ctx, hbm_budget=4 << 30, slots=2, max_batch_jobs=8, batch_window_ms=2.0)
+    for mid, m in enumerate(library):
+        srv.add_model(mid, m.tree)
+    m = library[1]
+    obs = synth.axis_observers(16, m.tree.box[0], "+z")
+    p = dict(seed=77, job=5, precision=64, packets_per_bin=3000, rr_wmin=1e-3, rr_p=0.5)
+    others = [srv.submit(k % len(library), library[k % len(library)].sources, library[k % len(library)].optics,
+                         seed=300 + k, job=10 + k, precision=32, packets_per_bin=20000) for k in range(6)]
+    t = srv.submit(1, m.sources, m.optics, obs, **p)
+    srv.wait(t)
+    ab, img = srv.fetch(t)
+    for o in others:
+        srv.wait(o)
+        srv.release(o)
+    srv.close()
+    ref = orc.trace(orc.Tree(m.tree), m.sources, m.optics, 3000, seed=77, job=5, observers=obs, rr_wmin=1e-3,
+                    rr_p=0.5, n_threads=8)
+    _close(ab, ref["absorbed"])
+    _close(img, ref["images"])
+
+
+def test_slots_work_at_the_same_time(rt, ctx, library):
+    """With two slots and one job per launch, the device-time intervals of
+    launches from the two slots intersect: a request's work starts while
+    another slot's launch is still on the device."""
+    srv = rt.Server(ctx, hbm_budget=4 << 30, slots=2, max_batch_jobs=1, batch_window_ms=0.0)
+    m = library[1]
+    srv.add_model(0, m.tree)
+    ts = [srv.submit(0, m.sources, m.optics, seed=500 + k, job=k, precision=32, packets_per_bin=200000)
+          for k in range(12)]
+    iv = []
+    for t in ts:
+        srv.wait(t)
+        iv.append(srv.device_times(t))
+        srv.release(t)
+    srv.close()
+    assert all(a >= 0 and b > a for a, b in iv)
+    overlaps = sum(1 for i in range(len(iv)) for k in range(i + 1, len(iv))
+                   if max(iv[i][0], iv[k][0]) < min(iv[i][1], iv[k][1]))
+    assert overlaps >= 3, iv
