@@ -162,13 +162,22 @@ void rt_server::worker(int slot) {
         std::this_thread::sleep_for(std::chrono::microseconds((long)(cfg.batch_window_ms * 1000)));
         lk.lock();
       }
+      // the oldest admitted request, then the ones behind it that can share
+      // its launch (one launch runs one precision and one estimator)
       int64_t pk = 0;
-      while (!admitted.empty() && (int)batch.size() < cfg.max_batch_jobs) {
-        Job* nx = admitted.front();
-        if (!batch.empty() && cfg.max_batch_packets > 0 && pk + nx->n_packets > cfg.max_batch_packets) break;
+      for (auto it = admitted.begin(); it != admitted.end() && (int)batch.size() < cfg.max_batch_jobs;) {
+        Job* nx = *it;
+        if (!batch.empty()) {
+          if (cfg.max_batch_packets > 0 && pk + nx->n_packets > cfg.max_batch_packets) break;
+          if (nx->params.precision != batch[0]->params.precision ||
+              nx->params.estimator != batch[0]->params.estimator) {
+            ++it;
+            continue;
+          }
+        }
         pk += nx->n_packets;
         batch.push_back(nx);
-        admitted.pop_front();
+        it = admitted.erase(it);
       }
       for (Job* j : batch) j->state = Job::RUNNING;
     }

@@ -228,10 +228,10 @@ enum { EV_NONE = 0, EV_IDLE, EV_INTERACT, EV_ESCAPE, EV_CUT, EV_KILL, EV_DEGEN, 
 // same whatever the number of lanes it serves, so serving one event per
 // visit (batch 1) spends most issue slots on lanes that do nothing.
 #ifndef RT_EV_BATCH
-#define RT_EV_BATCH 4
+#define RT_EV_BATCH 8
 #endif
 #ifndef RT_PEEL_EV_BATCH
-#define RT_PEEL_EV_BATCH 4
+#define RT_PEEL_EV_BATCH 8
 #endif
 // counter slot for each calling lane with one atomic per group of lanes
 // that arrive together (the tile-record and peel-off queues have one

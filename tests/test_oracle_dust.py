@@ -92,18 +92,51 @@ def test_p12_lambda_iteration_thin_limit(orc):
 
 def test_p12_lambda_iteration_self_heating(orc):
     """With dust optically thick to its own emission, the iteration raises
-    the temperatures (dust heats dust) and dT/T shrinks with each step; at
-    the end the per-cell balance holds, emission(T) = absorbed."""
+    the temperatures (dust heats dust) and dT/T shrinks with each step.  At
+    convergence the fixed point of Eq. 2 holds, checked with random numbers
+    the iteration never used:
+      * per cell, the dust's emission at the final T equals the energy it
+        absorbs from the star plus from a fresh trace of that emission
+        (independent streams), within the Monte Carlo error;
+      * in total, everything the star emits leaves the box: the energy the
+        dust absorbed from the star equals what its own emission loses
+        through the boundary (emitted minus re-absorbed)."""
     desc, optics, star = _small_star_model(3.0)
     tree = orc.Tree(desc)
+    level, leaf = tree.cells()
     kabs = (1 - optics.albedo) * optics.kappa_ext
-    r = orc.trace(tree, [star], optics, 5000, seed=4, per_lambda=False)
-    T0 = orc.dust_temperature(tree, r["absorbed"][0], optics.lambda_um, kabs, optics.dnu)
-    T, hist = orc.lambda_iterate(tree, star, optics, 5000, 5000, seed=4, tol=1e-3, max_iter=6, min_hits=50,
-                                 n_threads=4)
-    assert np.median(T / T0) > 1.01
-    assert hist[-1] < hist[0]
-    assert len(hist) >= 2
+    lam, dnu = optics.lambda_um, optics.dnu
+    n = 40000
+    r = orc.trace(tree, [star], optics, n, seed=4, per_lambda=False, validation=True, n_threads=8)
+    T0 = orc.dust_temperature(tree, r["absorbed"][0], lam, kabs, dnu)
+    T, hist = orc.lambda_iterate(tree, star, optics, n, n, seed=4, tol=1e-4, max_iter=40, min_hits=50,
+                                 n_threads=8)
+    assert np.median(T[leaf] / T0[leaf]) > 1.01
+    assert hist[-1] < hist[0] and hist[-1] < 1e-4 and len(hist) >= 2
+    # a fresh dust trace at the final temperatures (another seed)
+    em = orc.dust_emission(tree, T, lam, kabs, dnu)
+    npk = orc.packets_by_energy(em.sum(axis=1), n)
+    rd = orc.trace(tree, [orc._DustSource(em)], optics, npk, seed=1234, iter_=1, per_lambda=False,
+                   validation=True, n_threads=8)
+    A = r["absorbed"][0] + rd["absorbed"][0]
+    E = em.sum(axis=0)                       # emission per cell (energy per unit time)
+    n_d = int(npk.sum())
+    var = (np.maximum(r["sumsq"][0] - r["absorbed"][0] ** 2 / (n * lam.size), 0)
+           + np.maximum(rd["sumsq"][0] - rd["absorbed"][0] ** 2 / n_d, 0))
+    hits = r["hits"][0] + rd["hits"][0]
+    ok = leaf & (hits >= 1000) & (var > 0)
+    assert ok.sum() > 0.8 * leaf.sum()
+    z = (E[ok] - A[ok]) / np.sqrt(var[ok])
+    assert np.mean(np.abs(z) > 3) < 0.02, np.sort(np.abs(z))[-5:]
+    assert abs(np.mean(E[ok] / A[ok] - 1)) < 0.01
+    # global: absorbed from the star = dust emission that escapes
+    Ld = rd["ledger"]
+    absorbed_star = r["ledger"]["absorbed"]
+    escaped_dust = Ld["emitted"] - Ld["absorbed"]
+    assert abs(escaped_dust / absorbed_star - 1) < 0.01, (escaped_dust, absorbed_star)
+    # the pin has teeth: the star's field alone is far from this balance
+    E0 = orc.dust_emission(tree, T0, lam, kabs, dnu).sum(axis=0)
+    assert np.mean(np.abs(E0[ok] / A[ok] - 1)) > 0.05
 
 
 # P13: subiterations (Sect. 3.2, App. B) --------------------------------------
@@ -298,3 +331,45 @@ def test_p13_ali_sparse_packages(orc):
         bias[total] = abs(np.mean(m) / ref - 1.0)
     assert bias[2000] < 0.12
     assert bias[8000] < 0.04 and bias[8000] < bias[2000]
+
+
+def test_p13_ali_reaches_the_plain_fixed_point(orc):
+    """ALI (Eq. 3) changes how fast the iteration gets there, not where it
+    goes.  A refined cube thick to its own emission (its cells re-absorb over
+    a third of what they emit): eight ALI steps end at the mass-weighted
+    temperature of sixty plain Lambda steps (Eq. 2, whose fixed point the
+    self-heating pin checks) to 0.2 %, where eight plain steps are still
+    several times further away; per cell the two fixed points agree to the
+    Monte Carlo noise that ALI's solve amplifies in such cells."""
+    L = 20 * synth.AU_CM
+    desc = synth.random_refined_tree((4, 4, 4), (L,) * 3, 3, 0.35, 17,
+                                     rho_fn=lambda l, x, y, z: np.random.default_rng(l + 5).uniform(0.5e-18, 2e-18,
+                                                                                                    x.size))
+    tree = orc.Tree(desc)
+    level, leaf = tree.cells()
+    lam = synth.log_lambda_grid(8)
+    o = synth.powerlaw_dust(lam, 200.0 / (1e-18 * L), 1.0)
+    optics = synth.Optics(o.lambda_um, o.kappa_ext, np.zeros(lam.size), np.zeros(lam.size), o.dnu)
+    star = synth.Source("point", bin_energy=synth.blackbody_star_bins(lam, 4000.0, 2 * synth.RSUN_CM),
+                        pos=(0.47 * L, 0.52 * L, 0.49 * L))
+    kw = dict(seed=6, sub_level=0, min_hits=0.0, dust_per_bin=True, n_threads=8)
+    T_long, _, _ = orc.lambda_subiterate(tree, star, optics, 40000, 4000, schedule=["full"] * 60, **kw)
+    T_8, _, _ = orc.lambda_subiterate(tree, star, optics, 40000, 4000, schedule=["full"] * 8, **kw)
+    T_ali, _, _ = orc.lambda_subiterate(tree, star, optics, 40000, 4000, schedule=["full"] * 8, ali=True,
+                                        ali_min_packages=20, **kw)
+    h = (desc.box[0] / desc.root[0]) * 0.5 ** level
+    mass = np.where(leaf, desc.density * h ** 3, 0.0)
+    mw = lambda T: float(np.sum(mass * T) / mass.sum())
+    d_ali = abs(mw(T_ali) / mw(T_long) - 1)
+    d_plain = abs(mw(T_8) / mw(T_long) - 1)
+    assert d_ali < 2e-3, (mw(T_ali), mw(T_long))
+    assert d_plain > 3 * d_ali, (mw(T_8), mw(T_ali), mw(T_long))
+    assert np.median(np.abs(T_ali[leaf] / T_long[leaf] - 1)) < 0.05
+    # the diagonal of Lambda at the fixed point: the share of their emission
+    # the cells re-absorb themselves
+    kabs = (1 - optics.albedo) * optics.kappa_ext
+    em = orc.dust_emission(tree, T_long, lam, kabs, optics.dnu)
+    sa, se, sn = np.zeros_like(em), np.zeros_like(em), np.zeros(tree.n_cells)
+    orc.trace(tree, [orc._DustSource(em)], optics, np.where(em.sum(axis=1) > 0, 4000, 0), seed=8, iter_=1,
+              per_lambda=False, per_level=True, self_absorbed=sa, self_emitted=se, self_count=sn, n_threads=8)
+    assert sa.sum() / se.sum() > 0.3, sa.sum() / se.sum()
