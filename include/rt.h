@@ -30,6 +30,13 @@
  *  - Random numbers: Philox4x32-10 (Salmon et al. 2011) with
  *    key = (seed_lo ^ job, seed_hi ^ iter), counter = (pkt_lo, pkt_hi,
  *    draw >> 2, (source << 16) | bin); draw j of a package is word j & 3.
+ *    Dust sources send their packages per cell (Sect. 4.2): every package
+ *    of bin b carries w_b (the bin's emission over its packages), and cell c
+ *    sends floor(E_bc / w_b + u_bc) of them, u_bc from word 0 of counter
+ *    (c, 0x80000000, 0, (source << 16) | b); package j of cell c draws from
+ *    counter (j + packet_offset, 0x40000000 | c, draw >> 2, (source << 16) |
+ *    b): position in the cell (3 draws), direction (2), then the flight.
+ *    A package keeps its random numbers when other cells' emission changes.
  */
 #ifndef RT_H
 #define RT_H
@@ -154,7 +161,8 @@ typedef struct {
 enum {
   RT_SRC_POINT = 0,        /* isotropic point source at pos */
   RT_SRC_EXTERNAL = 1,     /* isotropic external field entering the root box */
-  RT_SRC_DUST = 2,         /* thermal dust emission from temperatures T_dev */
+  RT_SRC_DUST = 2,         /* thermal dust emission from temperatures T_dev,
+                              packages per cell (< 2^30 cells) */
   RT_SRC_BEAM = 3          /* parallel beam from pos along dir */
 };
 
@@ -428,7 +436,8 @@ int rt_dust_temperature(rt_ctx* ctx, const rt_grid* grid, const double* absorbed
  * temperatures (packages per bin in proportion to the bin emission, Sect. 4.2,
  * or an equal count), traces them and solves the new temperatures from the
  * sum of both fields.  The dust packages reuse the same random streams in
- * every iteration (key iter = params.iter + 1), so the change in T measures
+ * every iteration (key iter = params.iter + 1), and a package stays with its
+ * cell (packages are sent per cell), so the change in T measures
  * convergence rather than Monte Carlo noise.  Stops when max |dT|/T over
  * leaves with at least min_hits deposits (counted during the constant-source
  * trace and the first dust trace) falls below tol, or after max_iter
@@ -470,9 +479,9 @@ int rt_lambda_iterate(rt_ctx* ctx, const rt_grid* grid, int n_src, const rt_sour
  *             sub_level = L: dust emitted by the cells of level > L, packages
  *             leave the run where they reach a grid of level <= L (booked as
  *             escaped), the level arrays > L replaced.
- * A subiteration sends from each cell the packages a full step would: with
- * lp->dust_packets_total its total is scaled by the fraction of the dust
- * emission that comes from below L (per-bin counts stay as given).
+ * A subiteration sends from each cell the packages a full step would, with
+ * the same random streams: the package energy w_b is the full step's (the
+ * whole model's emission in bin b over its packages).
  * After each step T follows from the summed field.  The dust packages reuse
  * the same random streams every step (key iter = params.iter + 1).  With an
  * explicit schedule the steps run as given (the run stops early when max

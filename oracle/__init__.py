@@ -52,7 +52,7 @@ class _TreeDesc(C.Structure):
 class _Source(C.Structure):
     _fields_ = [("kind", C.c_int), ("pos", C.c_double * 3), ("dir", C.c_double * 3),
                 ("bin_energy", C.POINTER(C.c_double)), ("packets", C.POINTER(C.c_int64)),
-                ("emission", C.POINTER(C.c_double)), ("sampling", C.POINTER(C.c_double))]
+                ("emission", C.POINTER(C.c_double)), ("package_energy", C.POINTER(C.c_double))]
 
 
 class _Optics(C.Structure):
@@ -112,6 +112,9 @@ def lib():
         L.orc_trace.argtypes = [C.c_void_p, C.c_int, C.POINTER(_Source), C.POINTER(_Optics),
                                 C.POINTER(_Params), C.POINTER(_Observers), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Ledger)]
+        L.orc_dust_packages.restype = C.c_int64
+        L.orc_dust_packages.argtypes = [C.c_void_p, C.POINTER(_Source), C.c_int, C.c_int, C.POINTER(_Params),
+                                        C.c_void_p]
         L.orc_peel_table.restype = C.c_int64
         L.orc_peel_table.argtypes = [C.c_void_p, C.POINTER(_Observers), C.c_int, C.c_int, C.c_void_p]
         L.orc_peel_point.restype = C.c_int
@@ -295,8 +298,8 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
         if s.kind == "dust":
             em = emission if emission is not None else s.emission
             S.emission = _dp(keep.arr(em, np.float64), C.c_double)
-            if getattr(s, "sampling", None) is not None:
-                S.sampling = _dp(keep.arr(s.sampling, np.float64), C.c_double)
+            if getattr(s, "package_energy", None) is not None:
+                S.package_energy = _dp(keep.arr(s.package_energy, np.float64), C.c_double)
     o = _optics(optics, keep)
     prm = _Params(seed=seed, job=job, iter=iter_, estimator=estimator, rr_wmin=rr_wmin, rr_p=rr_p,
                   step_limit=step_limit, peel_tau_max=peel_tau_max, per_lambda=int(per_lambda),
@@ -317,7 +320,17 @@ def trace(tree: Tree, sources: Sequence, optics, packets, *, seed: int, job: int
     hits = np.zeros((bins, nc)) if validation else None
     image_sumsq = np.zeros_like(images) if (validation and images is not None) else None
     prm.image_sumsq = None if image_sumsq is None else image_sumsq.ctypes.data
-    npk = int(pk.sum())
+    # a dust source sends its packages per cell: their number is known only
+    # from the emission (within one per cell of packets * E_bc / E_b)
+    traced = pk.copy()
+    for i, s in enumerate(sources):
+        if s.kind == "dust":
+            actual = np.zeros(nl, np.int64)
+            if lib().orc_dust_packages(tree.handle, C.byref(src_arr[i]), i, nl, C.byref(prm),
+                                       actual.ctypes.data) < 0:
+                raise RuntimeError("orc_dust_packages failed")
+            traced[i] = actual
+    npk = int(traced.sum())
     rec = np.zeros((npk, 10)) if record else None
     led = _Ledger()
     rc = lib().orc_trace(tree.handle, ns, src_arr, C.byref(o), C.byref(prm),
@@ -421,14 +434,15 @@ def packets_by_energy(energy: np.ndarray, total: int) -> np.ndarray:
 
 
 class _DustSource:
-    """Dust emission [n_lambda][n_cells]; ``sampling`` (same shape, > 0
-    wherever the emission is) draws the emission cells by other weights, each
-    package carrying emission_c / (N p_c)."""
+    """Dust emission [n_lambda][n_cells]: each cell sends packages in
+    proportion to its emission in each bin (see orc_dust_packages);
+    ``package_energy`` [n_lambda], if given, fixes the energy of one package
+    (else the bin's emission / packages)."""
     kind = "dust"
 
-    def __init__(self, emission, sampling=None):
+    def __init__(self, emission, package_energy=None):
         self.emission = emission
-        self.sampling = sampling
+        self.package_energy = package_energy
         self.bin_energy = None
 
 
@@ -517,23 +531,23 @@ def lambda_subiterate(tree: Tree, star, optics, packets_star, packets_dust, *, s
     history = []
     for step in schedule:
         em = dust_emission(tree, T, lam, kabs, dnu)
-        total = packets_dust
+        e_bin = em.sum(axis=1)
+        if dust_per_bin:
+            npk = np.where(e_bin > 0, packets_dust, 0).astype(np.int64)
+        else:
+            npk = packets_by_energy(e_bin, packets_dust)
+        # the package energy of a full step; a subiteration sends from its
+        # cells the packages a full step would (App. B), with the same streams
+        w = np.where(npk > 0, e_bin / np.maximum(npk, 1), 0.0)
         if step == "sub":
-            e_all = em.sum()
             em = em * (level > L)[None, :]
-            # each cell sends the packages a full step would (App. B)
-            total = max(1, int(np.rint(packets_dust * (em.sum() / e_all if e_all > 0 else 1.0))))
         elif step != "full":
             raise ValueError("schedule entries are 'full' or 'sub'")
-        if dust_per_bin:
-            npk = np.where(em.sum(axis=1) > 0, packets_dust, 0).astype(np.int64)
-        else:
-            npk = packets_by_energy(em.sum(axis=1), total)
         nlam = len(optics.kappa_ext)
         self_abs = np.zeros((nlam, tree.n_cells)) if ali else None
         self_emit = np.zeros((nlam, tree.n_cells)) if ali else None
         self_n = np.zeros(tree.n_cells) if ali else None
-        rd = trace(tree, [_DustSource(em)], optics, npk, seed=seed, iter_=1, per_lambda=False,
+        rd = trace(tree, [_DustSource(em, package_energy=w)], optics, npk, seed=seed, iter_=1, per_lambda=False,
                    n_threads=n_threads, validation=True, per_level=True,
                    confine_level=L if step == "sub" else -1, self_absorbed=self_abs, self_emitted=self_emit,
                    self_count=self_n,

@@ -346,7 +346,8 @@ typedef struct {
   int bins;
   int64_t n_packets;
   int64_t* seg_begin;      /* [n_src*n_lambda + 1] global packet offset of each (src,bin) */
-  double** cdf;            /* dust: [n_src][n_lambda] -> cumulative emission over cells */
+  int64_t** first;         /* dust: [n_src][n_lambda] -> first package of each cell, [n_cells + 1] */
+  double* w_dust;          /* dust: [n_src][n_lambda] energy of one package */
   double* rec;
   int shared_atomic;
   double* absorbed_shared;
@@ -632,15 +633,54 @@ static int visited_level(const orc_node* a, const orc_node* b) {
   return 0;
 }
 
-static int64_t search_cdf(const double* cdf, int64_t n, double target) {
-  /* first index with cdf[i] > target */
+/* the cell whose packages include package k: the last c with first[c] <= k */
+static int64_t search_first(const int64_t* first, int64_t n, int64_t k) {
   int64_t lo = 0, hi = n - 1;
   while (lo < hi) {
-    int64_t mid = lo + (hi - lo) / 2;
-    if (cdf[mid] > target) hi = mid;
-    else lo = mid + 1;
+    int64_t mid = lo + (hi - lo + 1) / 2;
+    if (first[mid] <= k) lo = mid;
+    else hi = mid - 1;
   }
   return lo;
+}
+
+/* Dust packages of one (source, bin) per cell, in the form of the first
+ * package index of each cell (first[n_cells] = their total); w_out: the
+ * energy of one package.  Returns the total, -1 on a bad argument. */
+static int64_t dust_first(const orc_tree* t, const orc_source* S, int src_index, int bin, const orc_params* prm,
+                          int64_t* first, double* w_out) {
+  const int64_t nc = t->n_cells;
+  if (nc >= ((int64_t)1 << 30)) return -1;
+  const double* em = S->emission + (int64_t)bin * nc;
+  double E = 0.0;
+  for (int64_t c = 0; c < nc; ++c) E += em[c];
+  const int64_t N = S->packets[bin];
+  double w = S->package_energy ? S->package_energy[bin] : (N > 0 ? E / (double)N : 0.0);
+  if (w_out) *w_out = w;
+  const uint32_t stream = ((uint32_t)src_index << 16) | (uint32_t)bin;
+  int64_t tot = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    if (first) first[c] = tot;
+    if (!(w > 0.0) || !(em[c] > 0.0)) continue;
+    const uint64_t pk = ((uint64_t)0x80000000u << 32) | (uint64_t)c;
+    const double u = ((double)orc_draw_u32(prm->seed, prm->job, prm->iter, stream, pk, 0) + 0.5) / 4294967296.0;
+    tot += (int64_t)floor(em[c] / w + u);
+  }
+  if (first) first[nc] = tot;
+  return tot;
+}
+
+int64_t orc_dust_packages(const orc_tree* t, const orc_source* src, int src_index, int n_lambda,
+                          const orc_params* prm, int64_t* per_bin) {
+  if (!t || !src || !prm || src->kind != ORC_SRC_DUST || !src->emission || !src->packets) return -1;
+  int64_t tot = 0;
+  for (int b = 0; b < n_lambda; ++b) {
+    const int64_t n = src->packets[b] > 0 ? dust_first(t, src, src_index, b, prm, NULL, NULL) : 0;
+    if (n < 0) return -1;
+    if (per_bin) per_bin[b] = n;
+    tot += n;
+  }
+  return tot;
 }
 
 static uint32_t raw_word(rstream* s) {
@@ -1069,9 +1109,14 @@ static void trace_one(trace_worker* w, int64_t p) {
 
   double x[3], d[3], E;
   int64_t origin = -1;  /* emission cell of a dust package */
-  if (S->kind == ORC_SRC_DUST) E = J->cdf[seg][nc - 1];
-  else E = S->bin_energy[bin];
-  double W0 = E / (double)npk, W = W0;
+  double W0;
+  if (S->kind == ORC_SRC_DUST) {
+    W0 = J->w_dust[seg];
+  } else {
+    E = S->bin_energy[bin];
+    W0 = E / (double)npk;
+  }
+  double W = W0;
 
   /* emission (Sect. 2.3: packages from internal sources; root inwards
    * array for the external field) */
@@ -1101,16 +1146,11 @@ static void trace_one(trace_worker* w, int64_t p) {
     d[a] = (face & 1) ? -mu : mu;
     d[a1] = st * cos(phi);
     d[a2] = st * sin(phi);
-  } else { /* dust emission: cell by the cumulative emission of this bin */
-    const double* cdf = J->cdf[seg];
-    double u0 = uni(&rs);
-    int64_t c = search_cdf(cdf, nc, u0 * cdf[nc - 1]);
+  } else { /* dust emission: package j of its cell, with the cell's own stream */
+    const int64_t c = search_first(J->first[seg], nc + 1, k);
+    const int64_t j = k - J->first[seg][c];
+    rs.pkt = ((uint64_t)(0x40000000u | (uint32_t)c) << 32) | (uint32_t)(j + prm->packet_offset);
     origin = c;
-    if (S->sampling) {
-      /* importance-sampled cell: weight emission_c / (N p_c) */
-      W0 = S->emission[(int64_t)bin * nc + c] * cdf[nc - 1] / ((double)npk * S->sampling[(int64_t)bin * nc + c]);
-      W = W0;
-    }
     if (prm->self_emitted) atomic_add_double(&prm->self_emitted[(int64_t)bin * nc + c], W0);
     if (prm->self_count) atomic_add_double(&prm->self_count[c], 1.0);
     const orc_node* n = &t->nodes[c];
@@ -1204,29 +1244,25 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
   memset(&J, 0, sizeof J);
   J.t = t; J.n_src = n_src; J.src = src; J.op = op; J.prm = prm; J.obs = obs; J.bins = bins; J.rec = rec;
   J.seg_begin = (int64_t*)calloc((size_t)n_src * nl + 1, sizeof(int64_t));
-  J.cdf = (double**)calloc((size_t)n_src * nl, sizeof(double*));
+  J.first = (int64_t**)calloc((size_t)n_src * nl, sizeof(int64_t*));
+  J.w_dust = (double*)calloc((size_t)n_src * nl, sizeof(double));
   for (int s = 0; s < n_src; ++s)
     for (int b = 0; b < nl; ++b) {
       int64_t i = (int64_t)s * nl + b;
-      J.seg_begin[i + 1] = J.seg_begin[i] + src[s].packets[b];
-      if (src[s].kind == ORC_SRC_DUST && src[s].packets[b] > 0) {
-        double* c = (double*)malloc((size_t)nc * sizeof(double));
-        const double* tab = src[s].sampling ? src[s].sampling : src[s].emission;
-        double acc = 0.0;
-        int bad = 0;
-        for (int64_t k = 0; k < nc; ++k) {
-          const int64_t q = (int64_t)b * nc + k;
-          if (src[s].sampling && src[s].emission[q] > 0.0 && !(src[s].sampling[q] > 0.0)) bad = 1;
-          acc += tab[q];
-          c[k] = acc;
-        }
-        J.cdf[i] = c;
-        if (bad) {
-          for (int64_t j = 0; j <= i; ++j) free(J.cdf[j]);
-          free(J.cdf); free(J.seg_begin);
-          return -1;
+      int64_t n = src[s].packets[b];
+      if (src[s].kind == ORC_SRC_DUST) {
+        n = 0;
+        if (src[s].packets[b] > 0) {
+          J.first[i] = (int64_t*)malloc((size_t)(nc + 1) * sizeof(int64_t));
+          n = dust_first(t, &src[s], s, b, prm, J.first[i], &J.w_dust[i]);
+          if (n < 0) {
+            for (int64_t j = 0; j <= i; ++j) free(J.first[j]);
+            free(J.first); free(J.w_dust); free(J.seg_begin);
+            return -1;
+          }
         }
       }
+      J.seg_begin[i + 1] = J.seg_begin[i] + n;
     }
   J.n_packets = J.seg_begin[(int64_t)n_src * nl];
   if (obs && obs->n_obs > 0 && prm->peel_block > 0) {
@@ -1303,8 +1339,8 @@ int orc_trace(const orc_tree* t, int n_src, const orc_source* src, const orc_opt
     free(w->pkt_acc); free(w->stamp); free(w->touched); free(w->stack);
   }
   if (ledger) *ledger = L;
-  for (int64_t i = 0; i < (int64_t)n_src * nl; ++i) free(J.cdf[i]);
-  free(J.cdf); free(J.seg_begin); free(ws); free(th); free(J.peel_tab);
+  for (int64_t i = 0; i < (int64_t)n_src * nl; ++i) free(J.first[i]);
+  free(J.first); free(J.w_dust); free(J.seg_begin); free(ws); free(th); free(J.peel_tab);
   return 0;
 }
 

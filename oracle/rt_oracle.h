@@ -65,13 +65,10 @@ typedef struct {
   double pos[3];               /* cm: point / beam origin */
   double dir[3];               /* beam direction */
   const double* bin_energy;    /* [n_lambda] (point, external, beam) */
-  const int64_t* packets;      /* [n_lambda] packets per bin */
+  const int64_t* packets;      /* [n_lambda] packets per bin (dust: the expected number) */
   const double* emission;      /* dust: [n_lambda][n_cells] energy per cell per bin */
-  const double* sampling;      /* dust, optional: [n_lambda][n_cells] weights the emission cell is
-                                * drawn by (NULL: the emission itself); a package from cell c then
-                                * carries emission_c / (N p_c), p_c = sampling_c / sum, so every cell
-                                * still emits its energy in expectation; sampling_c must be > 0
-                                * wherever emission_c > 0 */
+  const double* package_energy; /* dust, optional: [n_lambda] energy of one package (default: the
+                                 * bin's emission / packets) */
 } orc_source;
 
 typedef struct {
@@ -135,6 +132,20 @@ typedef struct {
    * Monte Carlo variance of the images, as sumsq is for absorbed). */
   double* image_sumsq;
 } orc_params;
+
+/* Dust packages per cell (Sect. 4.2: the number of packages a cell sends at
+ * a frequency follows its emission there, and every package of the
+ * frequency carries the same energy w_b = E_b / N_b).  Cell c sends
+ * floor(E_bc / w_b + u_bc) packages, u_bc the uniform of word 0 of Philox
+ * counter (c, 0x80000000 | (c >> 32), 0, (source << 16) | bin) under the
+ * run's key: the expected count is E_bc / w_b, the count is within one of
+ * it, and it does not change between runs with the same key unless E_bc / w_b
+ * moves past the threshold.  Package j of cell c draws from counter
+ * (j + packet_offset, 0x40000000 | c, draw >> 2, (source << 16) | bin).
+ * Writes the packages per bin into per_bin (may be NULL); returns their
+ * total, or -1 for a bad argument (cells beyond 2^30). */
+int64_t orc_dust_packages(const orc_tree* t, const orc_source* src, int src_index, int n_lambda,
+                          const orc_params* prm, int64_t* per_bin);
 
 typedef struct {
   double emitted, absorbed, escaped, rr_gain, rr_loss, killed, peeled;

@@ -510,6 +510,18 @@ static int check_dust(const rt_dust* du, int nl) {
   return RT_OK;
 }
 
+// Packages per bin in proportion to the bins' energies, at least one in
+// every bin that has energy (near-equal package weights, Sect. 4.2).
+static void packages_by_energy(const double* e, int n, long long total, long long* out) {
+  double tot = 0.0;
+  for (int i = 0; i < n; ++i) tot += e[i];
+  for (int i = 0; i < n; ++i) {
+    long long v = tot > 0 ? (long long)std::floor((double)total * e[i] / tot) : 0;
+    if (e[i] > 0 && v == 0) v = 1;
+    out[i] = v;
+  }
+}
+
 // The Lambda drivers' dust: the absorbing part of the optics' extinction,
 // kappa_abs = (1 - albedo) kappa_ext (a single dust component, Sect. 3.2),
 // when the dust model leaves kappa_abs NULL; else the model as given.
@@ -559,6 +571,7 @@ struct TraceArgs {
   double* self_abs = nullptr;           // ALI: self-absorption tally per cell (levels only)
   double* self_emit = nullptr;          // ALI: energy of the dust packages each cell emitted
   unsigned int* self_cnt = nullptr;     // ALI: their number
+  const double* dust_package_energy = nullptr;  // dust sources: host [n_lambda] energy of one package
 };
 
 // accelerated peel-off tables (Sect. 2.4)
@@ -675,34 +688,34 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     }
     const rt_grid* G = T.grid;
     const long long nc = G->n_cells;
-    // energies and dust CDFs
+    // energies; dust sources: emission per cell and bin (and its totals)
     std::vector<double> energy((size_t)T.n_src * nl, 0.0);
-    std::vector<double*> cdfs(T.n_src, nullptr);
+    std::vector<DevBuf*> dust_buf(T.n_src, nullptr);
     for (int si = 0; si < T.n_src; ++si) {
       const rt_source& S = T.src[si];
       if (S.kind == RT_SRC_DUST) {
         if (!S.T_dev) return fail(RT_ERR_INVALID, "job %d source %d: dust source needs T_dev", j, si);
         rc = check_dust(S.dust, nl);
         if (rc) return rc;
+        if (nc >= (1ll << 30)) return fail(RT_ERR_INVALID, "job %d source %d: dust sources need < 2^30 cells", j, si);
         if ((int)cdfv.size() <= dust_used) cdfv.resize(dust_used + 1);
         DevBuf& cb = cdfv[dust_used++];
-        rc = cb.ensure(sizeof(double) * (size_t)nl * nc);
+        // [emission nl x nc f64 | first package per cell nl x (nc + 1) i64 | totals nl | w nl]
+        rc = cb.ensure(sizeof(double) * ((size_t)nl * nc + (size_t)nl * (nc + 1) + 2 * (size_t)nl) + 256);
         if (rc) return rc;
         double *lam, *kab, *dnu, *tab;
         rc = upload_dust(c, S.dust, 0, &lam, &kab, &dnu, &tab, s);
         if (rc) return rc;
-        double* cdf = reinterpret_cast<double*>(cb.p);
-        CK(dust_emission(S.T_dev, nc, G->child, G->rho64, G->level, G->h0, lam, kab, dnu, nl, cdf, s));
-        const size_t tb = scan_rows_tmp_bytes(nl, nc);
-        rc = c->scan_tmp.ensure(tb);
+        double* em = reinterpret_cast<double*>(cb.p);
+        double* tot = em + (size_t)nl * nc + (size_t)nl * (nc + 1);
+        CK(dust_emission(S.T_dev, nc, G->child, G->rho64, G->level, G->h0, lam, kab, dnu, nl, em, s));
+        CK(row_sums_f64(em, nl, nc, tot, s));
+        rc = ensure_pin_rb(c, sizeof(double) * (size_t)nl);
         if (rc) return rc;
-        CK(scan_rows_f64(cdf, nl, nc, c->scan_tmp.p, c->scan_tmp.n, s));
-        std::vector<double> last(nl);
-        for (int b = 0; b < nl; ++b)
-          CK(cudaMemcpyAsync(&last[b], cdf + (size_t)b * nc + (nc - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(c->pin_rb, tot, sizeof(double) * (size_t)nl, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        for (int b = 0; b < nl; ++b) energy[(size_t)si * nl + b] = last[b];
-        cdfs[si] = cdf;
+        for (int b = 0; b < nl; ++b) energy[(size_t)si * nl + b] = static_cast<const double*>(c->pin_rb)[b];
+        dust_buf[si] = &cb;
       } else if (S.kind == RT_SRC_POINT || S.kind == RT_SRC_EXTERNAL || S.kind == RT_SRC_BEAM) {
         if (!S.bin_energy) return fail(RT_ERR_INVALID, "job %d source %d: bin_energy is NULL", j, si);
         for (int b = 0; b < nl; ++b) {
@@ -725,13 +738,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     if (p->packets_per_bin > 0) {
       std::fill(pk.begin(), pk.end(), (long long)p->packets_per_bin);
     } else if (p->packets_total > 0) {
-      double tot = 0.0;
-      for (double v : energy) tot += v;
-      for (size_t i = 0; i < pk.size(); ++i) {
-        long long v = tot > 0 ? (long long)std::floor((double)p->packets_total * energy[i] / tot) : 0;
-        if (energy[i] > 0 && v == 0) v = 1;
-        pk[i] = v;
-      }
+      packages_by_energy(energy.data(), (int)energy.size(), p->packets_total, pk.data());
     } else if (p->packets) {
       for (size_t i = 0; i < pk.size(); ++i) {
         if (p->packets[i] < 0) return fail(RT_ERR_INVALID, "job %d: negative package count", j);
@@ -754,11 +761,40 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
           }
           for (int b = f; b < f + size; ++b) pk[(size_t)si * nl + b] = b == f ? n : 0;
         }
-    // a dust bin that emits nothing has no cell to sample from: no packages
-    for (int si = 0; si < T.n_src; ++si)
-      if (T.src[si].kind == RT_SRC_DUST)
-        for (int b = 0; b < nl; ++b)
-          if (!(energy[(size_t)si * nl + b] > 0.0)) pk[(size_t)si * nl + b] = 0;
+    // Dust sources (Sect. 4.2): every package of a bin carries the same
+    // energy w_b (the bin's emission over its packages, or the energy given
+    // by the caller), and each cell sends floor(E_bc / w_b + u_bc) of them;
+    // pk becomes the packages actually sent
+    std::vector<double> w_dust((size_t)T.n_src * nl, 0.0);
+    for (int si = 0; si < T.n_src; ++si) {
+      if (T.src[si].kind != RT_SRC_DUST) continue;
+      double* em = reinterpret_cast<double*>(dust_buf[si]->p);
+      long long* first = reinterpret_cast<long long*>(em + (size_t)nl * nc);
+      double* wd = em + (size_t)nl * nc + (size_t)nl * (nc + 1) + nl;
+      for (int b = 0; b < nl; ++b) {
+        const size_t q = (size_t)si * nl + b;
+        const double e = energy[q];
+        double w = 0.0;
+        if (e > 0.0 && pk[q] > 0) w = T.dust_package_energy ? T.dust_package_energy[b] : e / (double)pk[q];
+        w_dust[q] = w > 0.0 && std::isfinite(w) ? w : 0.0;
+      }
+      rc = ensure_pinned(c, sizeof(double) * (size_t)nl);
+      if (rc) return rc;
+      memcpy(c->pinned, w_dust.data() + (size_t)si * nl, sizeof(double) * (size_t)nl);
+      CK(cudaMemcpyAsync(wd, c->pinned, sizeof(double) * (size_t)nl, cudaMemcpyHostToDevice, s));
+      CK(dust_counts(em, nc, nl, wd, (uint32_t)p->seed ^ p->job, (uint32_t)(p->seed >> 32) ^ p->iter, (uint32_t)si,
+                     first, s));
+      rc = c->scan_tmp.ensure(scan_rows_tmp_bytes(nl, nc + 1));
+      if (rc) return rc;
+      CK(scan_rows_i64_excl(first, nl, nc + 1, c->scan_tmp.p, c->scan_tmp.n, s));
+      rc = ensure_pin_rb(c, sizeof(long long) * (size_t)nl);
+      if (rc) return rc;
+      for (int b = 0; b < nl; ++b)
+        CK(cudaMemcpyAsync(static_cast<long long*>(c->pin_rb) + b, first + (size_t)b * (nc + 1) + nc, sizeof(long long),
+                           cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int b = 0; b < nl; ++b) pk[(size_t)si * nl + b] = static_cast<const long long*>(c->pin_rb)[b];
+    }
     // job entry
     JobDev J;
     memset(&J, 0, sizeof J);
@@ -902,12 +938,15 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
         // polychromatic: every bin of a group shares the group's packages
         const long long ng = poly > 1 ? pk[(size_t)si * nl + (b / poly) * poly] : np_;
         w0[b] = ng > 0 ? energy[(size_t)si * nl + b] / (double)ng : 0.0;
+        if (S.kind == RT_SRC_DUST) w0[b] = w_dust[(size_t)si * nl + b];
         w0f[b] = (float)w0[b];
       }
       I.pkt_begin = total;
       I.pkt_end = total + pref[nl];
       I.log_offset = log_off;
-      I.cdf = cdfs[si];
+      I.dust_first = S.kind == RT_SRC_DUST
+                         ? reinterpret_cast<const long long*>(reinterpret_cast<double*>(dust_buf[si]->p) + (size_t)nl * nc)
+                         : nullptr;
       total += pref[nl];
       log_off += pref[nl];
       const size_t po = A.put(pref.data(), sizeof(long long) * (nl + 1));
@@ -1579,7 +1618,8 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   // cells each), right-hand side, package count, use flag
   const int nlb = op->n_lambda;
   const size_t ali_bytes = sp->ali ? 3 * al(fb * nlb) + al(fb) + al(hb) + al((size_t)nc) : 0;
-  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024 + ali_bytes);
+  const size_t scal_bytes = al(sizeof(double) * (16 + RT_MAX_LAMBDA));  // + per-bin emission totals at scal + 16
+  rc = ctx->lam.ensure(4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + scal_bytes + ali_bytes);
   if (rc) return rc;
   char* base = reinterpret_cast<char*>(ctx->lam.p);
   double* A_star = reinterpret_cast<double*>(base);
@@ -1591,7 +1631,7 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
   unsigned int* hits_star = reinterpret_cast<unsigned int*>(base + 4 * al(fb) + 2 * al(fb * nlev));
   unsigned int* hits_step = reinterpret_cast<unsigned int*>(base + 4 * al(fb) + 2 * al(fb * nlev) + al(hb));
   double* scal = reinterpret_cast<double*>(base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb));
-  char* ali_base = base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + 1024;
+  char* ali_base = base + 4 * al(fb) + 2 * al(fb * nlev) + 2 * al(hb) + scal_bytes;
   double* self_abs = reinterpret_cast<double*>(ali_base);
   double* self_emit = reinterpret_cast<double*>(ali_base + al(fb * nlb));
   double* ali_w = reinterpret_cast<double*>(ali_base + 2 * al(fb * nlb));
@@ -1687,14 +1727,32 @@ extern "C" int rt_lambda_subiterate(rt_ctx* ctx, const rt_grid* g, int n_src, co
     CK(cudaMemcpyAsync(hits_step, hits_star, hb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(I_step, 0, fb * nlev, s));
     // a subiteration sends from each cell the packages a full step would
-    // (App. B): with a package total, the total scales with the emission of
-    // the subtrees
-    dp.packets_total = lp->dust_packets_per_bin > 0 ? 0 : lp->dust_packets_total;
-    if (kind == 1 && dp.packets_total > 0) {
-      const double f = e[5] + e[6] > 0 ? e[6] / (e[5] + e[6]) : 1.0;
-      dp.packets_total = std::max<int64_t>(1, (int64_t)std::llround((double)lp->dust_packets_total * f));
+    // (App. B): the package energy of the full step's emission, so every
+    // cell of the subtrees sends the packages, with the streams, it would
+    // send in a full step
+    std::vector<double> w_full;
+    if (kind == 1) {
+      rc = upload();
+      if (rc) return rc;
+      CK(dust_emission_totals(T_dev, nc, g->child, g->rho64, g->level, g->h0, lam, kab, dnu, nlb, scal + 16, s));
+      rc = ensure_pin_rb(ctx, sizeof(double) * (size_t)nlb);
+      if (rc) return rc;
+      CK(cudaMemcpyAsync(ctx->pin_rb, scal + 16, sizeof(double) * (size_t)nlb, cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(ctx->ev_c, s));
+      rc = ctx_wait(ctx, ctx->ev_c, to);
+      if (rc) return rc;
+      std::vector<double> ef(static_cast<const double*>(ctx->pin_rb), static_cast<const double*>(ctx->pin_rb) + nlb);
+      std::vector<long long> nf(nlb);
+      if (lp->dust_packets_per_bin > 0) {
+        for (int b = 0; b < nlb; ++b) nf[b] = ef[b] > 0 ? lp->dust_packets_per_bin : 0;
+      } else {
+        packages_by_energy(ef.data(), nlb, lp->dust_packets_total, nf.data());
+      }
+      w_full.assign(nlb, 0.0);
+      for (int b = 0; b < nlb; ++b) w_full[b] = nf[b] > 0 ? ef[b] / (double)nf[b] : 0.0;
     }
     TraceArgs TD{g, 1, &ds, op, &dp, nullptr, nullptr, I_step};
+    TD.dust_package_energy = kind == 1 ? w_full.data() : nullptr;
     TD.levels = 1;
     TD.confine = kind == 1 ? L : -1;
     if (sp->ali) {

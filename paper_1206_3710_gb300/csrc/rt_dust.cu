@@ -10,6 +10,7 @@
 // Hermite interpolant, so no leaf evaluates the Planck sum (GB300's FP64
 // pipe is narrow); where E underflows at the cold end the exact sum is
 // solved by safeguarded Newton instead.
+#include "philox.cuh"
 #include "rt_internal.cuh"
 
 namespace rtk {
@@ -194,6 +195,44 @@ cudaError_t dust_emission(const double* T, long long n_cells, const uint32_t* ch
   return cudaGetLastError();
 }
 
+// per-bin totals of the emission of emission_kernel, without storing it
+__global__ void emission_totals_kernel(const double* __restrict__ T, long long n, const uint32_t* __restrict__ child,
+                                       const double* __restrict__ rho64, const uint8_t* __restrict__ level, double h0,
+                                       const double* __restrict__ lam, const double* __restrict__ kabs,
+                                       const double* __restrict__ dnu, int nl, double* __restrict__ tot) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double pref = 0.0, Tc = 0.0;
+  if (c < n) {
+    Tc = T[c];
+    if (!child[c] && Tc > 0.0) {
+      const double h = ldexp(h0, -(int)level[c]);
+      pref = FOUR_PI * rho64[c] * h * h * h;
+    }
+  }
+  for (int b = 0; b < nl; ++b) {
+    double v = 0.0;
+    if (pref > 0.0) {
+      double B, dB;
+      planck_and_deriv(C_CGS / (lam[b] * 1e-4), Tc, &B, &dB);
+      v = pref * kabs[b] * B * dnu[b];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(tot + b, v);
+  }
+}
+
+cudaError_t dust_emission_totals(const double* T, long long n_cells, const uint32_t* child, const double* rho64,
+                                 const uint8_t* level, double h0, const double* lam, const double* kabs,
+                                 const double* dnu, int nl, double* tot, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(tot, 0, sizeof(double) * (size_t)nl, s);
+  if (e != cudaSuccess || n_cells <= 0) return e;
+  const unsigned B = 128;
+  emission_totals_kernel<<<(unsigned)((n_cells + B - 1) / B), B, 0, s>>>(T, n_cells, child, rho64, level, h0, lam,
+                                                                         kabs, dnu, nl, tot);
+  return cudaGetLastError();
+}
+
 __global__ void max_rel_change_kernel(const double* __restrict__ T, const double* __restrict__ Tp,
                                       const unsigned int* __restrict__ hits, const uint32_t* __restrict__ child,
                                       long long n, double min_hits, double* out) {
@@ -215,6 +254,36 @@ cudaError_t max_rel_change(const double* T, const double* T_prev, const unsigned
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;
   max_rel_change_kernel<<<1024, 256, 0, s>>>(T, T_prev, hits, child, n, min_hits, out);
+  return cudaGetLastError();
+}
+
+__global__ void dust_counts_kernel(const double* __restrict__ em, long long n, const double* __restrict__ w,
+                                   uint32_t k0, uint32_t k1, uint32_t src, long long* __restrict__ first) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (c > n) return;
+  long long* row = first + (long long)b * (n + 1);
+  if (c == n) {
+    row[n] = 0;
+    return;
+  }
+  const double e = em[(long long)b * n + c];
+  const double wb = w[b];
+  long long k = 0;
+  if (e > 0.0 && wb > 0.0) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)c, 0x80000000u, 0u, (src << 16) | (uint32_t)b), k0, k1);
+    const double u = ((double)r.x + 0.5) * 2.3283064365386963e-10;
+    k = (long long)floor(e / wb + u);
+  }
+  row[c] = k;
+}
+
+cudaError_t dust_counts(const double* emission, long long n, int nl, const double* w, uint32_t k0, uint32_t k1,
+                        uint32_t src, long long* first, cudaStream_t s) {
+  if (n <= 0 || nl <= 0) return cudaSuccess;
+  const unsigned B = 256;
+  dust_counts_kernel<<<dim3((unsigned)((n + 1 + B - 1) / B), (unsigned)nl), B, 0, s>>>(emission, n, w, k0, k1, src,
+                                                                                      first);
   return cudaGetLastError();
 }
 

@@ -130,6 +130,13 @@ cudaError_t scan_flags_u8(const uint8_t* flags, long long n, unsigned long long*
 
 size_t scan_rows_tmp_bytes(int n_rows, long long n) { return scan_tmp<double>(n_rows, n) + 512; }
 
+cudaError_t scan_rows_i64_excl(long long* data, int n_rows, long long n, void* tmp, size_t tmp_bytes, cudaStream_t s) {
+  if (tmp_bytes < scan_rows_tmp_bytes(n_rows, n)) return cudaErrorInvalidValue;
+  char* t = reinterpret_cast<char*>(tmp);
+  t += (256 - ((uintptr_t)t & 255)) & 255;
+  return scan_rows<long long, long long, false>(data, data, n_rows, n, t, s);
+}
+
 cudaError_t scan_rows_f64(double* data, int n_rows, long long n, void* tmp, size_t tmp_bytes, cudaStream_t s) {
   if (tmp_bytes < scan_rows_tmp_bytes(n_rows, n)) return cudaErrorInvalidValue;
   char* t = reinterpret_cast<char*>(tmp);

@@ -201,7 +201,7 @@ struct ItemDev {
   double dir[3];
   const long long* bin_prefix;  // [n_lambda + 1] package prefix within the item
   const double* W0;             // [n_lambda]
-  const double* cdf;            // dust: [n_lambda][n_cells] inclusive cumulative emission
+  const long long* dust_first;  // dust: [n_lambda][n_cells + 1] first package of each cell
   const float* W0f;             // [n_lambda] f32 copy of W0
   float posf[3], dirf[3];       // f32 copies of pos, dir
   int pad2;
@@ -312,6 +312,10 @@ cudaError_t dust_temperature(const double* absorbed, int n_bins, long long n_cel
 cudaError_t dust_emission(const double* T, long long n_cells, const uint32_t* child, const double* rho64,
                           const uint8_t* level, double h0, const double* lam_um, const double* kabs,
                           const double* dnu, int nl, double* emission, cudaStream_t s);
+// per-bin totals of dust_emission's emission into tot [nl] (device)
+cudaError_t dust_emission_totals(const double* T, long long n_cells, const uint32_t* child, const double* rho64,
+                                 const uint8_t* level, double h0, const double* lam, const double* kabs,
+                                 const double* dnu, int nl, double* tot, cudaStream_t s);
 // max over leaves with hits >= min_hits of |T - T_prev| / T_prev into *out
 cudaError_t max_rel_change(const double* T, const double* T_prev, const unsigned int* hits, const uint32_t* child,
                            long long n, double min_hits, double* out, cudaStream_t s);
@@ -341,5 +345,15 @@ cudaError_t row_sums_f64(const double* data, int n_rows, long long n, double* ou
 cudaError_t scan_rows_f64(double* data, int n_rows, long long n, void* tmp, size_t tmp_bytes,
                           cudaStream_t s);
 size_t scan_rows_tmp_bytes(int n_rows, long long n);
+// exclusive prefix sums of n_rows rows of length n (int64), in place
+cudaError_t scan_rows_i64_excl(long long* data, int n_rows, long long n, void* tmp, size_t tmp_bytes,
+                               cudaStream_t s);
+// Dust packages per cell (Sect. 4.2): row b of first [nl][n + 1] gets, for
+// each cell, floor(emission[b][c] / w[b] + u_bc) (u_bc: word 0 of Philox
+// counter (c, 0x80000000, 0, (src << 16) | b) under key (k0, k1)), and 0 in
+// the last column; an exclusive scan of the rows then gives each cell's
+// first package and the bin's total.  w: device [nl]; w[b] <= 0: no packages
+cudaError_t dust_counts(const double* emission, long long n, int nl, const double* w, uint32_t k0, uint32_t k1,
+                        uint32_t src, long long* first, cudaStream_t s);
 
 }  // namespace rtk

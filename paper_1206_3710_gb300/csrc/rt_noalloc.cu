@@ -245,7 +245,7 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
       it.posf[a] = (float)it.pos[a];
       it.dirf[a] = (float)it.dir[a];
     }
-    it.cdf = nullptr;
+    it.dust_first = nullptr;
     total += pr[nl];
   }
   J.led_shift = ledger_shift(w0_max, p->rr_wmin, p->rr_p);

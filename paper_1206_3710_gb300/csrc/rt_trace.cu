@@ -427,6 +427,28 @@ __device__ __forceinline__ int crossed_grid_level(const Geo<R>& g, int a, R dx, 
   return g.lev > b ? g.lev - b : 0;
 }
 
+// Dust packages (Sect. 4.2): package p of an item (counted over its bins)
+// is number j of the packages its cell sends in bin `bin`; the cell is the
+// last one whose first package is <= the package's index within the bin.
+// The package draws from the cell's own stream, counter (j + offset,
+// 0x40000000 | cell), so it keeps its random numbers when the emission of
+// other cells changes.  Sets the lane's stream words; returns the cell.
+template <typename R>
+__device__ __forceinline__ long long dust_stream(const ItemDev& I, const JobDev& J, int bin, long long p,
+                                                 ColdState<R>& C, int t) {
+  const long long* fb = I.dust_first + (long long)bin * (J.n_cells + 1);
+  const long long kb = p - I.bin_prefix[bin];
+  long long lo = 0, hi = J.n_cells - 1;
+  while (lo < hi) {
+    const long long mid = (lo + hi + 1) >> 1;
+    if (__ldg(fb + mid) <= kb) lo = mid;
+    else hi = mid - 1;
+  }
+  C.c0[t] = (uint32_t)(kb - __ldg(fb + lo) + J.pkt_offset);
+  C.c1[t] = 0x40000000u | (uint32_t)lo;
+  return lo;
+}
+
 #ifndef RT_FP32_MIN_BLOCKS
 #define RT_FP32_MIN_BLOCKS 4
 #endif
@@ -617,6 +639,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           C.c0[t] = (uint32_t)k;
           C.c1[t] = (uint32_t)(k >> 32);
           C.c3[t] = (I.src_index << 16) | (uint32_t)bin;
+          if (I.kind == RT_SRC_DUST) dust_stream(I, J, bin, p, C, t);
           if (SPLIT && (s3 & 0x80000000u)) {
             // a copy from a split: its own stream, no package log
             C.c0[t] = s0;
@@ -767,19 +790,9 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
             }
             inside = place_root(G, g, cur, px, py, pz, dx, dy, dz);
           } else {
-            // dust emission: cell from this bin's cumulative emission
-            const double* cdf = I.cdf + (long long)bin * J.n_cells;
-            const double totE = cdf[J.n_cells - 1];
-            const double target = (double)draw(C, t) * totE;
-            // non-negative doubles order as their bit patterns: the search
-            // compares integers
-            const long long tb = __double_as_longlong(target);
-            long long clo = 0, chi = J.n_cells - 1;
-            while (clo < chi) {
-              const long long mid = clo + ((chi - clo) >> 1);
-              if (__double_as_longlong(cdf[mid]) > tb) chi = mid;
-              else clo = mid + 1;
-            }
+            // dust emission (Sect. 4.2): the package is one of the packages
+            // its cell sends in this bin, and draws from that cell's stream
+            const long long clo = dust_stream(I, J, bin, p, C, t);
             const uint64_t cw = J.coord[clo];
             g.cx = (uint32_t)(cw & RT_COORD_MASK);
             g.cy = (uint32_t)((cw >> RT_COORD_BITS) & RT_COORD_MASK);
