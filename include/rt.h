@@ -199,9 +199,10 @@ typedef struct {
   int64_t packets_per_bin;  /* > 0: packages for every (source, bin) */
   const int64_t* packets;   /* host [n_src][n_lambda] when packets_per_bin <= 0 and packets_total <= 0 */
   int64_t packets_total;    /* > 0: spread over (source, bin) in proportion to energy */
-  double* packet_log_dev;   /* optional device [n_packets][10]: w_escaped, n_scatter, n_cross,
-                               fate (0 escaped, 1 roulette, 2 step limit, 3 analog absorption),
-                               x_exit[3] (cm), d_exit[3] */
+  double* packet_log_dev;   /* optional device [packet_log_rows][10], one row per package in
+                               package order: w_escaped, n_scatter, n_cross, fate (0 escaped,
+                               1 roulette, 2 step limit, 3 analog absorption), x_exit[3] (cm),
+                               d_exit[3] */
   double timeout_s;         /* bounded wait for completion; <= 0: 3600 s */
   int block_size;           /* 0: tuned default */
   int refill_threshold;     /* 0: tuned default; dead lanes per warp before a refill */
@@ -246,6 +247,11 @@ typedef struct {
    * The ledger sums the bins; per package its energy balance holds in
    * expectation only (the likelihood ratios change the weights).  <= 1: off. */
   int poly_group;
+  /* Rows of packet_log_dev (required with it): a launch whose packages
+   * exceed it is refused (RT_ERR_INVALID) before anything runs.  A dust
+   * source's package count depends on the emission (within one per emitting
+   * cell and bin of the budget), so give its log room beyond the budget. */
+  int64_t packet_log_rows;
 } rt_trace_params;
 
 typedef struct {

@@ -433,6 +433,26 @@ def packets_by_energy(energy: np.ndarray, total: int) -> np.ndarray:
     return n
 
 
+def dust_packages(tree: Tree, emission, packets, *, seed: int, job: int = 0, iter_: int = 0, src_index: int = 0,
+                  package_energy=None) -> np.ndarray:
+    """Packages per bin that a dust source with this emission sends (see
+    orc_dust_packages): within one per emitting cell of ``packets``."""
+    keep = _Keep()
+    em = keep.arr(emission, np.float64)
+    nl = em.shape[0]
+    pk = keep.arr(np.broadcast_to(np.asarray(packets, np.int64), (nl,)), np.int64)
+    S = _Source(kind=SRC_DUST)
+    S.packets = _dp(pk, C.c_int64)
+    S.emission = _dp(em, C.c_double)
+    if package_energy is not None:
+        S.package_energy = _dp(keep.arr(package_energy, np.float64), C.c_double)
+    prm = _Params(seed=seed, job=job, iter=iter_)
+    out = np.zeros(nl, np.int64)
+    if lib().orc_dust_packages(tree.handle, C.byref(S), src_index, nl, C.byref(prm), out.ctypes.data) < 0:
+        raise RuntimeError("orc_dust_packages failed")
+    return out
+
+
 class _DustSource:
     """Dust emission [n_lambda][n_cells]: each cell sends packages in
     proportion to its emission in each bin (see orc_dust_packages);

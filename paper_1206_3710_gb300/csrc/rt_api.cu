@@ -747,6 +747,8 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     } else {
       return fail(RT_ERR_INVALID, "job %d: set packets_per_bin, packets_total or packets", j);
     }
+    if (p->packet_log_dev && p->packet_log_rows <= 0)
+      return fail(RT_ERR_INVALID, "job %d: packet_log_rows must give the rows of packet_log_dev", j);
     // polychromatic: packages per group, counted at the group's first bin
     const int poly = p->poly_group > 1 ? p->poly_group : 1;
     if (poly > 1)
@@ -910,6 +912,14 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
       }
       const size_t oo = A.put(ob.data(), sizeof(ObsDev) * ob.size());
       patches.push_back({jo + offsetof(JobDev, obs), oo});
+    }
+    // the package log must have a row for every package
+    if (p->packet_log_dev) {
+      long long n_job = 0;
+      for (long long v : pk) n_job += v;
+      if (n_job > p->packet_log_rows)
+        return fail(RT_ERR_INVALID, "job %d: the launch has %lld packages, packet_log_rows is %lld", j, n_job,
+                    (long long)p->packet_log_rows);
     }
     // items
     long long log_off = 0;

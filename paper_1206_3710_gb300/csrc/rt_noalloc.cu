@@ -249,6 +249,8 @@ extern "C" int rt_trace_noalloc(const rt_grid* grid, int n_src, const rt_source*
     total += pr[nl];
   }
   J.led_shift = ledger_shift(w0_max, p->rr_wmin, p->rr_p);
+  if (p->packet_log_dev && total > p->packet_log_rows)
+    return set_error(RT_ERR_INVALID, "rt_trace_noalloc: packet_log_rows is smaller than the launch's packages");
 
   int prev = -1;
   cudaGetDevice(&prev);

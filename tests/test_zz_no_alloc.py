@@ -122,11 +122,15 @@ def test_noalloc_timeout_then_complete(rt):
     grid = rt.Grid(ctx, m.tree)
     kw = dict(seed=22, precision=64, per_lambda=False)
     probe = torch.zeros((1, grid.n_cells), dtype=torch.float64, device=DEV)
-    led = rt.rt_trace(ctx, grid, m.sources, m.optics, probe, packets_per_bin=20000, **kw)
-    npk = int(min(2e8, max(20000, 300.0 / (max(led["kernel_ms"], 0.05) / 20000))))
+    npk = 20000
+    for _ in range(3):  # grow the job to a few hundred ms (small launches overstate the time per package)
+        led = rt.rt_trace(ctx, grid, m.sources, m.optics, probe, packets_per_bin=npk, **kw)
+        if led["kernel_ms"] >= 150.0 or npk >= 2e8:
+            break
+        npk = int(min(2e8, npk * min(100.0, 300.0 / max(led["kernel_ms"], 0.05))))
     ref = torch.zeros_like(probe)
     led_ref = rt.rt_trace(ctx, grid, m.sources, m.optics, ref, packets_per_bin=npk, **kw)
-    assert led_ref["kernel_ms"] > 50.0, led_ref["kernel_ms"]
+    assert led_ref["kernel_ms"] > 20.0, led_ref["kernel_ms"]
     stream = torch.cuda.Stream(device=DEV)
     out = torch.zeros_like(ref)
     torch.cuda.synchronize()
