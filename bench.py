@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--serve-max-packets", type=float, default=1e8)
     ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--serve-batch", type=int, default=64)
+    ap.add_argument("--serve-batch-packets", type=float, default=1e7,
+                    help="serve: a launch takes jobs while their packages sum to at most this (0: no limit)")
     ap.add_argument("--line-serve-seconds", type=float, default=15.0,
                     help="seconds of Poisson arrivals for the serving figures of the default line (0: none)")
     ap.add_argument("--n-root", type=int, default=256)
@@ -446,7 +448,8 @@ def serving_figures(a, ctx, dev):
     import bench_families
     from paper_1206_3710_gb300 import rt, synth
     res = bench_families.serve_measure(rt, synth, ctx, torch, a.line_serve_seconds, a.serve_rate,
-                                       a.serve_max_packets, slots=a.serve_slots, max_batch_jobs=a.serve_batch)
+                                       a.serve_max_packets, slots=a.serve_slots, max_batch_jobs=a.serve_batch,
+                                       max_batch_packets=a.serve_batch_packets)
     res.pop("library", None)
     return res
 

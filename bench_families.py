@@ -252,7 +252,7 @@ def serve_jobs(synth, seconds, rate, max_packets, seed=1005):
 
 
 def serve_measure(rt, synth, ctx, torch, seconds, rate, max_packets, slots=2, max_batch_jobs=64,
-                  batch_window_ms=2.0):
+                  batch_window_ms=1.0, max_batch_packets=1e7):
     """Serving under Poisson arrivals (latency p50/p99 from submission to the
     result being ready on the device, packages/s), the same jobs one at a
     time with their own launches, and the burst capacity (all jobs submitted
@@ -264,7 +264,7 @@ def serve_measure(rt, synth, ctx, torch, seconds, rate, max_packets, slots=2, ma
 
     def server():
         srv = rt.Server(ctx, hbm_budget=int(0.5 * free), slots=slots, max_batch_jobs=max_batch_jobs,
-                        batch_window_ms=batch_window_ms)
+                        batch_window_ms=batch_window_ms, max_batch_packets=int(max_batch_packets))
         for mid, m in enumerate(library):
             srv.add_model(mid, m.tree)
         # warm-up: the first job of each model makes its grid resident
@@ -329,7 +329,8 @@ def serve_measure(rt, synth, ctx, torch, seconds, rate, max_packets, slots=2, ma
     srv.close()
     return {"jobs": n_jobs, "seconds": float(arrivals[-1]), "rate_per_s": rate,
             "packets_per_job": f"log-uniform 1e5..{max_packets:.0e}", "wavelengths_per_job": "uniform 1..30",
-            "slots": slots, "max_batch_jobs": max_batch_jobs, "packets_total": int(pk),
+            "slots": slots, "max_batch_jobs": max_batch_jobs, "max_batch_packets": int(max_batch_packets),
+            "batch_window_ms": batch_window_ms, "packets_total": int(pk),
             "offered_packets_per_s": pk / float(arrivals[-1]),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "served_packets_per_s": pk / wall, "served_wall_s": wall,
@@ -342,7 +343,7 @@ def run_serve(a, rt, synth, ctx, torch):
     t0 = time.perf_counter()
     clk = _clock_start()
     res = serve_measure(rt, synth, ctx, torch, a.serve_seconds, a.serve_rate, a.serve_max_packets,
-                        slots=a.serve_slots, max_batch_jobs=a.serve_batch)
+                        slots=a.serve_slots, max_batch_jobs=a.serve_batch, max_batch_packets=a.serve_batch_packets)
     clocks = clk.stop()
     line = {"metric": "serving: p50/p99 job latency and packages/s under Poisson arrivals",
             "workload": "serve", **res, "clocks": clocks, "wall_s": time.perf_counter() - t0}

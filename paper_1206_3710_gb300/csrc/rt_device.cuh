@@ -218,29 +218,41 @@ __device__ __forceinline__ R clamp01(R v) {
 // sibling in the same octet or the root-level neighbour with one load,
 // otherwise a descent from the root).  False when the package leaves the
 // root grid.  Written with selects only: lanes crossing different axes do
-// not diverge.
+// not diverge.  `moved` gets the bits of the lattice coordinate on axis a
+// that changed (bit l + s set: the crossing left a block of 2^s cells of
+// level l on that axis, e.g. a tile).
 template <typename R>
-__device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, R t, R dx, R dy, R dz) {
-  const bool a0 = a == 0, a1 = a == 1, a2 = a == 2;
-  const bool px = dx > R(0), py = dy > R(0), pz = dz > R(0);
+__device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, R t, R dx, R dy, R dz,
+                                        uint32_t& moved) {
+  const bool a0 = a == 0, a1 = a == 1;
+  const R da = a0 ? dx : (a1 ? dy : dz);
+  const bool plus = da > R(0);
+  const R fnew = plus ? R(0) : R(1);
   const R nfx = clamp01(g.fx + t * dx), nfy = clamp01(g.fy + t * dy), nfz = clamp01(g.fz + t * dz);
-  g.fx = a0 ? (px ? R(0) : R(1)) : nfx;
-  g.fy = a1 ? (py ? R(0) : R(1)) : nfy;
-  g.fz = a2 ? (pz ? R(0) : R(1)) : nfz;
-  const bool plus = a0 ? px : (a1 ? py : pz);
+  g.fx = a0 ? fnew : nfx;
+  g.fy = a1 ? fnew : nfy;
+  g.fz = (!a0 && !a1) ? fnew : nfz;
   const uint32_t cold = a0 ? g.cx : (a1 ? g.cy : g.cz);
   const uint32_t cnew = plus ? cold + 1u : cold - 1u;
   g.cx = a0 ? cnew : g.cx;
   g.cy = a1 ? cnew : g.cy;
-  g.cz = a2 ? cnew : g.cz;
+  g.cz = (!a0 && !a1) ? cnew : g.cz;
+  moved = cold ^ cnew;
   const bool root_level = g.lev == 0;
-  const bool near = root_level || ((cold >> 1) == (cnew >> 1));  // root-level neighbour or sibling
+  const bool near = root_level || moved < 2u;  // root-level neighbour or sibling
   const uint32_t step = root_level ? (a0 ? 1u : (a1 ? G.rx : G.rx * G.ry)) : (1u << a);
+  // only axis a moved: inside while its root coordinate stays below the
+  // root grid's size (a step below 0 wraps to a huge unsigned value)
+  const bool inside = (cnew >> g.lev) < (a0 ? G.rx : (a1 ? G.ry : G.rz));
   const uint32_t rx = g.cx >> g.lev, ry = g.cy >> g.lev, rz = g.cz >> g.lev;
-  const bool inside = rx < G.rx && ry < G.ry && rz < G.rz;
   cur.pending = near ? (plus ? g.idx + step : g.idx - step) : rx + G.rx * (ry + G.ry * rz);
   cur.k = near ? g.lev : 0;
   return inside;
+}
+template <typename R>
+__device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, R t, R dx, R dy, R dz) {
+  uint32_t moved;
+  return advance(G, g, cur, a, t, dx, dy, dz, moved);
 }
 
 // advance() for a direction along axis a (the other two components zero):
@@ -248,21 +260,21 @@ __device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cu
 // (the same results as advance() with that direction)
 template <typename R>
 __device__ __forceinline__ bool advance_axis(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, bool plus) {
-  const bool a0 = a == 0, a1 = a == 1, a2 = a == 2;
+  const bool a0 = a == 0, a1 = a == 1;
   const R fnew = plus ? R(0) : R(1);
   g.fx = a0 ? fnew : g.fx;
   g.fy = a1 ? fnew : g.fy;
-  g.fz = a2 ? fnew : g.fz;
+  g.fz = (!a0 && !a1) ? fnew : g.fz;
   const uint32_t cold = a0 ? g.cx : (a1 ? g.cy : g.cz);
   const uint32_t cnew = plus ? cold + 1u : cold - 1u;
   g.cx = a0 ? cnew : g.cx;
   g.cy = a1 ? cnew : g.cy;
-  g.cz = a2 ? cnew : g.cz;
+  g.cz = (!a0 && !a1) ? cnew : g.cz;
   const bool root_level = g.lev == 0;
-  const bool near = root_level || ((cold >> 1) == (cnew >> 1));
+  const bool near = root_level || (cold ^ cnew) < 2u;
   const uint32_t step = root_level ? (a0 ? 1u : (a1 ? G.rx : G.rx * G.ry)) : (1u << a);
+  const bool inside = (cnew >> g.lev) < (a0 ? G.rx : (a1 ? G.ry : G.rz));
   const uint32_t rx = g.cx >> g.lev, ry = g.cy >> g.lev, rz = g.cz >> g.lev;
-  const bool inside = rx < G.rx && ry < G.ry && rz < G.rz;
   cur.pending = near ? (plus ? g.idx + step : g.idx - step) : rx + G.rx * (ry + G.ry * rz);
   cur.k = near ? g.lev : 0;
   return inside;
@@ -367,15 +379,9 @@ __device__ __forceinline__ void red_acc(double* p, double v) {
 #endif
 }
 
-// f32 -> f64 on the integer pipe (GB300's FP64 pipe is narrow); positive
-// normal values only, denormals map to 0
-__device__ __forceinline__ double widen(float v) {
-  const uint32_t b = __float_as_uint(v);
-  const uint32_t e = b >> 23;
-  const uint32_t hi = e ? (((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)) : 0u;
-  const uint32_t lo = e ? (b << 29) : 0u;
-  return __hiloint2double((int)hi, (int)lo);
-}
+// f32 -> f64 for the accumulator reductions (one conversion per deposit;
+// measured as fast as assembling the f64 bits on the integer pipe)
+__device__ __forceinline__ double widen(float v) { return (double)v; }
 __device__ __forceinline__ double widen(double v) { return v; }
 
 template <typename R>

@@ -27,6 +27,7 @@
 #include <math_constants.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 
 #include "philox.cuh"
@@ -245,6 +246,10 @@ __device__ __forceinline__ unsigned long long claim_slot(unsigned long long* ctr
   base = __shfl_sync(m, base, leader);
   return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
 }
+
+#ifndef RT_TRACE_ONLY_LOOP
+#define RT_TRACE_ONLY_LOOP 1
+#endif
 
 __device__ __forceinline__ bool keep_stepping(int ev, int batch) {
   const unsigned waiting = __ballot_sync(0xFFFFFFFFu, ev > EV_IDLE);
@@ -520,7 +525,6 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
   double* absb = nullptr;
   unsigned int* hitp = nullptr;
   uint32_t step_limit = 0u, ncross = 0u, npeel = 0u;
-  uint32_t tile_cur = 0u;  // tiled rounds: the tile this lane traces in
   int mlev = 0;            // subiterations: shallowest grid level reached
   double* selfb = nullptr; // ALI: self-absorption tally (LEVELS kernels)
   int plev = -1;           // resampling: grid level of the last cell (capped), -1: none yet
@@ -687,7 +691,6 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           // descend from that root cell
           cur.pending = (g.cx >> g.lev) + G.rx * ((g.cy >> g.lev) + G.ry * (g.cz >> g.lev));
           cur.k = 0;
-          tile_cur = tile_of(g, T);
           st = ST_TRACE;
         } else {
           // ------------------------------------------------ emission (Sect. 2.3)
@@ -856,93 +859,106 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
     // is loaded per lane per pass: a refined node advances the descent by a
     // level, a leaf gets one segment (Sect. 2.3) and a face crossing.
     int ev = (st == ST_TRACE || st == ST_PEEL) ? EV_NONE : EV_IDLE;
-    do {
-      if (ev == EV_NONE) {
-        const uint32_t w = ld_node(G.node + cur.pending);
-        const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
-        if (w & RT_INTERIOR) {
-          descend_step(g, cur, w, dx, dy, dz);
-        } else {
-          settle_leaf(g, cur, w, r64);
-          const bool tr = st == ST_TRACE;
-          int a;
-          const R tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
-          int lvs = 0;
-          if (SPLIT && tr) {
-            lvs = min(g.lev, splt_lmax);
-            if (plev < 0) plev = lvs;
-          }
-          if (tr && ncross >= step_limit) {
-            ev = EV_KILL;
-          } else if (a < 0) {
-            ev = EV_DEGEN;  // cannot happen for |d| = 1
-          } else if (SPLIT && tr && lvs != plev) {
-            ev = EV_SPLIT;  // entered a grid of another level: resample first
+    // one pass of the loop; a warp none of whose lanes marches an inline
+    // peel-off (the deferred queue had room) runs the tracing-only form
+    auto pass = [&](auto trace_only) {
+      constexpr bool TRACE_ONLY = decltype(trace_only)::value;
+        if (ev == EV_NONE) {
+          const uint32_t w = ld_node(G.node + cur.pending);
+          const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
+          if (w & RT_INTERIOR) {
+            descend_step(g, cur, w, dx, dy, dz);
           } else {
-            const R kl = kext * g.rho * Num<R>::pow2m(g.lev);  // extinction per local unit
-            bool inside_event = false;
-            R tseg = tx;
-            if (EST == RT_EST_CONTINUOUS) {
-              // free path drawn in scattering optical depth; the weight
-              // decays by the absorbed fraction along the segment
-              const R ksca = alb * kl;
-              const R tsc = ksca * tx;
-              inside_event = tr && ksca > R(0) && tsc >= tau;
-              if (inside_event) tseg = tau / ksca;
-              if (tr) {
-                R q, e;
-                Num<R>::absorb_pair((kl - ksca) * tseg, q, e);
-                tau = inside_event ? R(0) : tau - tsc;
-                const R dep = W * q;
-                W = W * e;
-                if (dep > R(0)) {
-                  pkt_abs += dep;
-                  if (absb) red_acc(absb + g.idx, widen(dep));
-                  if (HITS && hitp) atomicAdd(hitp + g.idx, 1u);
-                  if (LEVELS && selfb && g.idx == orig_t) atomicAdd(selfb + g.idx, widen(dep));
+            settle_leaf(g, cur, w, r64);
+            const bool tr = TRACE_ONLY || st == ST_TRACE;
+            int a;
+            uint32_t moved = 0u;
+            const R tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
+            int lvs = 0;
+            if (SPLIT && tr) {
+              lvs = min(g.lev, splt_lmax);
+              if (plev < 0) plev = lvs;
+            }
+            if (tr && ncross >= step_limit) {
+              ev = EV_KILL;
+            } else if (a < 0) {
+              ev = EV_DEGEN;  // cannot happen for |d| = 1
+            } else if (SPLIT && tr && lvs != plev) {
+              ev = EV_SPLIT;  // entered a grid of another level: resample first
+            } else {
+              const R kl = kext * g.rho * Num<R>::pow2m(g.lev);  // extinction per local unit
+              bool inside_event = false;
+              R tseg = tx;
+              if (EST == RT_EST_CONTINUOUS) {
+                // free path drawn in scattering optical depth; the weight
+                // decays by the absorbed fraction along the segment
+                const R ksca = alb * kl;
+                const R tsc = ksca * tx;
+                inside_event = tr && ksca > R(0) && tsc >= tau;
+                if (inside_event) tseg = tau / ksca;
+                if (tr) {
+                  R q, e;
+                  Num<R>::absorb_pair((kl - ksca) * tseg, q, e);
+                  tau = inside_event ? R(0) : tau - tsc;
+                  const R dep = W * q;
+                  W = W * e;
+                  if (dep > R(0)) {
+                    pkt_abs += dep;
+                    if (absb) red_acc(absb + g.idx, widen(dep));
+                    if (HITS && hitp) atomicAdd(hitp + g.idx, 1u);
+                    if (LEVELS && selfb && g.idx == orig_t) atomicAdd(selfb + g.idx, widen(dep));
+                  }
                 }
-              }
-            } else {
-              // analog: free path drawn in extinction optical depth
-              const R te = kl * tx;
-              inside_event = tr && kl > R(0) && te >= tau;
-              if (inside_event) tseg = tau / kl;
-              if (tr) tau = inside_event ? R(0) : tau - te;
-            }
-            if (tr) {
-              ncross += tseg > R(0) ? 1u : 0u;
-            } else {
-              taup += kl * tx;
-              npeel += tx > R(0) ? 1u : 0u;
-            }
-            if (inside_event) {
-              g.fx = clamp01(g.fx + tseg * dx);
-              g.fy = clamp01(g.fy + tseg * dy);
-              g.fz = clamp01(g.fz + tseg * dz);
-              cur.pending = g.idx;
-              cur.k = g.lev;
-              ev = EV_INTERACT;
-            } else if (!tr && taup > tau_cut) {
-              ev = EV_CUT;
-            } else if (!advance(G, g, cur, a, tx, dx, dy, dz)) {
-              ev = EV_ESCAPE;
-            } else if (LEVELS && tr && cur.k == 0 && crossed_grid_level(g, a, dx, dy, dz) < mlev) {
-              const JobDev& J = jobs[C.job[t]];
-              const int v = crossed_grid_level(g, a, dx, dy, dz);
-              if (v <= J.sub_conf) {
-                ev = EV_ESCAPE;  // left the subtree of this subiteration
               } else {
-                mlev = v;
-                absb = J.absorbed ? J.absorbed + (long long)mlev * J.n_cells : nullptr;
-                if (MODE == 2 && tile_of(g, T) != tile_cur) ev = EV_TILE;
+                // analog: free path drawn in extinction optical depth
+                const R te = kl * tx;
+                inside_event = tr && kl > R(0) && te >= tau;
+                if (inside_event) tseg = tau / kl;
+                if (tr) tau = inside_event ? R(0) : tau - te;
               }
-            } else if (MODE == 2 && tr && cur.k == 0 && tile_of(g, T) != tile_cur) {
-              ev = EV_TILE;  // entered another tile: next round
+              if (tr) {
+                ncross += tseg > R(0) ? 1u : 0u;
+              } else {
+                taup += kl * tx;
+                npeel += tx > R(0) ? 1u : 0u;
+              }
+              if (inside_event) {
+                g.fx = clamp01(g.fx + tseg * dx);
+                g.fy = clamp01(g.fy + tseg * dy);
+                g.fz = clamp01(g.fz + tseg * dz);
+                cur.pending = g.idx;
+                cur.k = g.lev;
+                ev = EV_INTERACT;
+              } else if (!tr && taup > tau_cut) {
+                ev = EV_CUT;
+              } else if (!advance(G, g, cur, a, tx, dx, dy, dz, moved)) {
+                ev = EV_ESCAPE;
+              } else if (LEVELS && tr && cur.k == 0 && crossed_grid_level(g, a, dx, dy, dz) < mlev) {
+                const JobDev& J = jobs[C.job[t]];
+                const int v = crossed_grid_level(g, a, dx, dy, dz);
+                if (v <= J.sub_conf) {
+                  ev = EV_ESCAPE;  // left the subtree of this subiteration
+                } else {
+                  mlev = v;
+                  absb = J.absorbed ? J.absorbed + (long long)mlev * J.n_cells : nullptr;
+                  if (MODE == 2 && (moved >> (g.lev + T.tsh)) != 0u) ev = EV_TILE;
+                }
+              } else if (MODE == 2 && tr && (moved >> (g.lev + T.tsh)) != 0u) {
+                ev = EV_TILE;  // entered another tile: next round
+              }
             }
           }
         }
-      }
-    } while (keep_stepping(ev, RT_EV_BATCH));
+    };
+    if (RT_TRACE_ONLY_LOOP && (!PEEL || __ballot_sync(FULL, st == ST_PEEL) == 0u)) {
+      do {
+        pass(std::true_type{});
+      } while (keep_stepping(ev, RT_EV_BATCH));
+    } else {
+      do {
+        pass(std::false_type{});
+      } while (keep_stepping(ev, RT_EV_BATCH));
+    }
 
     // ------------------------------------------------------------- slow path
     if (ev == EV_NONE || ev == EV_IDLE) continue;
