@@ -1165,7 +1165,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
 // Persistent warps refill finished lanes from a global counter.
 // ------------------------------------------------------------------------
 #ifndef RT_PEEL_MIN_BLOCKS
-#define RT_PEEL_MIN_BLOCKS 4
+#define RT_PEEL_MIN_BLOCKS 5
 #endif
 template <typename R>
 struct PeelMinBlocks {
