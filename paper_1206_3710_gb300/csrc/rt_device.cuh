@@ -280,109 +280,6 @@ __device__ __forceinline__ bool advance_axis(const GridRegs& G, Geo<R>& g, Curso
   return inside;
 }
 
-// ------------------------------------------------------------------------
-// The stepping loop's form of the in-leaf position: along each axis the
-// fraction of the cell still ahead in the direction of travel, r = 1 - f
-// for d >= 0 and r = f for d < 0.  The exit distance is then r / |d| on
-// every axis, and a crossing lowers every r by t |d| and sets the crossing
-// axis's r to 1 (the whole next cell ahead), so the loop needs no sign
-// selects.  flip_r converts in either direction (the map is its own
-// inverse).
-template <typename R>
-__device__ __forceinline__ void flip_r(Geo<R>& g, R dx, R dy, R dz) {
-  g.fx = dx >= R(0) ? R(1) - g.fx : g.fx;
-  g.fy = dy >= R(0) ? R(1) - g.fy : g.fy;
-  g.fz = dz >= R(0) ? R(1) - g.fz : g.fz;
-}
-
-// descend_step() on the r form: the child on the upper side along an axis
-// is the one with r <= 1/2 when moving up, r > 1/2 when moving down (a point
-// on the mid face belongs to the child the direction points into); its r
-// is 2r, less 1 if r > 1/2
-template <typename R>
-__device__ __forceinline__ void descend_r(Geo<R>& g, Cursor& cur, uint32_t w, R dx, R dy, R dz) {
-  const bool by_lattice = cur.k < g.lev;
-  const int sh = by_lattice ? g.lev - cur.k - 1 : 0;
-  const uint32_t ol = ((g.cx >> sh) & 1u) | (((g.cy >> sh) & 1u) << 1) | (((g.cz >> sh) & 1u) << 2);
-  const bool hx = g.fx > R(0.5), hy = g.fy > R(0.5), hz = g.fz > R(0.5);
-  const uint32_t bx = hx != (dx >= R(0)), by = hy != (dy >= R(0)), bz = hz != (dz >= R(0));
-  if (!by_lattice) {
-    g.fx = R(2) * g.fx - (hx ? R(1) : R(0));
-    g.fy = R(2) * g.fy - (hy ? R(1) : R(0));
-    g.fz = R(2) * g.fz - (hz ? R(1) : R(0));
-    g.cx = 2u * g.cx + bx;
-    g.cy = 2u * g.cy + by;
-    g.cz = 2u * g.cz + bz;
-    g.lev += 1;
-  }
-  const uint32_t o = by_lattice ? ol : (bx | (by << 1) | (bz << 2));
-  cur.pending = (w & RT_CHILD_MASK) + o;
-  cur.k += 1;
-}
-
-// settle_leaf() on the r form: in a leaf kk levels coarser than the lattice
-// level, the cell ahead of the point along an axis is ((c & m) or its
-// complement in m, when moving up) lattice cells plus the fraction r
-template <typename R>
-__device__ __forceinline__ void settle_r(Geo<R>& g, const Cursor& cur, uint32_t w, double r64, R dx, R dy, R dz) {
-  if (cur.k < g.lev) {
-    const int kk = g.lev - cur.k;
-    const uint32_t m = (1u << kk) - 1u;
-    const R s = Num<R>::pow2m(kk);
-    g.fx = (R((g.cx ^ (dx >= R(0) ? m : 0u)) & m) + g.fx) * s;
-    g.fy = (R((g.cy ^ (dy >= R(0) ? m : 0u)) & m) + g.fy) * s;
-    g.fz = (R((g.cz ^ (dz >= R(0) ? m : 0u)) & m) + g.fz) * s;
-    g.cx >>= kk;
-    g.cy >>= kk;
-    g.cz >>= kk;
-    g.lev = cur.k;
-  }
-  g.idx = cur.pending;
-  g.rho = Num<R>::leaf_rho(w, r64);
-}
-
-// exit_dist() on the r form: r / |d| per axis; ties -> lowest axis; an axis
-// the direction does not move along gives inf or NaN and never wins
-template <typename R>
-__device__ __forceinline__ R exit_r(const Geo<R>& g, R ix, R iy, R iz, int& axis) {
-  const R tx = g.fx * ix, ty = g.fy * iy, tz = g.fz * iz;
-  R t = Num<R>::inf();
-  int a = -1;
-  if (tx < t) { t = tx; a = 0; }
-  if (ty < t) { t = ty; a = 1; }
-  if (tz < t) { t = tz; a = 2; }
-  axis = a;
-  return t;
-}
-
-// advance() on the r form (same cursor and lattice results)
-template <typename R>
-__device__ __forceinline__ bool advance_r(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, R t, R dx, R dy, R dz,
-                                          uint32_t& moved) {
-  const bool a0 = a == 0, a1 = a == 1;
-  const R nrx = fmax(g.fx - t * fabs(dx), R(0)), nry = fmax(g.fy - t * fabs(dy), R(0)),
-          nrz = fmax(g.fz - t * fabs(dz), R(0));
-  g.fx = a0 ? R(1) : nrx;
-  g.fy = a1 ? R(1) : nry;
-  g.fz = (!a0 && !a1) ? R(1) : nrz;
-  const R da = a0 ? dx : (a1 ? dy : dz);
-  const bool plus = da > R(0);
-  const uint32_t cold = a0 ? g.cx : (a1 ? g.cy : g.cz);
-  const uint32_t cnew = plus ? cold + 1u : cold - 1u;
-  g.cx = a0 ? cnew : g.cx;
-  g.cy = a1 ? cnew : g.cy;
-  g.cz = (!a0 && !a1) ? cnew : g.cz;
-  moved = cold ^ cnew;
-  const bool root_level = g.lev == 0;
-  const bool near = root_level || moved < 2u;
-  const uint32_t step = root_level ? (a0 ? 1u : (a1 ? G.rx : G.rx * G.ry)) : (1u << a);
-  const bool inside = (cnew >> g.lev) < (a0 ? G.rx : (a1 ? G.ry : G.rz));
-  const uint32_t rx = g.cx >> g.lev, ry = g.cy >> g.lev, rz = g.cz >> g.lev;
-  cur.pending = near ? (plus ? g.idx + step : g.idx - step) : rx + G.rx * (ry + G.ry * rz);
-  cur.k = near ? g.lev : 0;
-  return inside;
-}
-
 template <typename R>
 __device__ __forceinline__ R hg_mu(R g, R u) {
   R mu;

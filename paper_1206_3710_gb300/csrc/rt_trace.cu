@@ -250,9 +250,6 @@ __device__ __forceinline__ unsigned long long claim_slot(unsigned long long* ctr
 #ifndef RT_TRACE_ONLY_LOOP
 #define RT_TRACE_ONLY_LOOP 1
 #endif
-#ifndef RT_R_FORM
-#define RT_R_FORM 1
-#endif
 
 __device__ __forceinline__ bool keep_stepping(int ev, int batch) {
   const unsigned waiting = __ballot_sync(0xFFFFFFFFu, ev > EV_IDLE);
@@ -870,25 +867,13 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           const uint32_t w = ld_node(G.node + cur.pending);
           const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
           if (w & RT_INTERIOR) {
-#if RT_R_FORM
-            descend_r(g, cur, w, dx, dy, dz);
-#else
             descend_step(g, cur, w, dx, dy, dz);
-#endif
           } else {
-#if RT_R_FORM
-            settle_r(g, cur, w, r64, dx, dy, dz);
-#else
             settle_leaf(g, cur, w, r64);
-#endif
             const bool tr = TRACE_ONLY || st == ST_TRACE;
             int a;
             uint32_t moved = 0u;
-#if RT_R_FORM
-            const R tx = exit_r(g, ix, iy, iz, a);
-#else
             const R tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
-#endif
             int lvs = 0;
             if (SPLIT && tr) {
               lvs = min(g.lev, splt_lmax);
@@ -938,25 +923,15 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
                 npeel += tx > R(0) ? 1u : 0u;
               }
               if (inside_event) {
-#if RT_R_FORM
-                g.fx = fmax(g.fx - tseg * fabs(dx), R(0));
-                g.fy = fmax(g.fy - tseg * fabs(dy), R(0));
-                g.fz = fmax(g.fz - tseg * fabs(dz), R(0));
-#else
                 g.fx = clamp01(g.fx + tseg * dx);
                 g.fy = clamp01(g.fy + tseg * dy);
                 g.fz = clamp01(g.fz + tseg * dz);
-#endif
                 cur.pending = g.idx;
                 cur.k = g.lev;
                 ev = EV_INTERACT;
               } else if (!tr && taup > tau_cut) {
                 ev = EV_CUT;
-#if RT_R_FORM
-              } else if (!advance_r(G, g, cur, a, tx, dx, dy, dz, moved)) {
-#else
               } else if (!advance(G, g, cur, a, tx, dx, dy, dz, moved)) {
-#endif
                 ev = EV_ESCAPE;
               } else if (LEVELS && tr && cur.k == 0 && crossed_grid_level(g, a, dx, dy, dz) < mlev) {
                 const JobDev& J = jobs[C.job[t]];
@@ -975,8 +950,6 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           }
         }
     };
-    // inside the loop the position is held in the r form (see flip_r)
-    if (RT_R_FORM) flip_r(g, dx, dy, dz);
     if (RT_TRACE_ONLY_LOOP && (!PEEL || __ballot_sync(FULL, st == ST_PEEL) == 0u)) {
       do {
         pass(std::true_type{});
@@ -986,7 +959,6 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
         pass(std::false_type{});
       } while (keep_stepping(ev, RT_EV_BATCH));
     }
-    if (RT_R_FORM) flip_r(g, dx, dy, dz);
 
     // ------------------------------------------------------------- slow path
     if (ev == EV_NONE || ev == EV_IDLE) continue;
