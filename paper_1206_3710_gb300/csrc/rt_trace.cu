@@ -1167,6 +1167,11 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
 #ifndef RT_PEEL_MIN_BLOCKS
 #define RT_PEEL_MIN_BLOCKS 5
 #endif
+// work item gi = (record, observer): record-major (the observers of a
+// record on neighbouring lanes) or observer-major
+#ifndef RT_PEEL_OBS_MAJOR
+#define RT_PEEL_OBS_MAJOR 0
+#endif
 template <typename R>
 struct PeelMinBlocks {
   static constexpr int value = sizeof(R) == 4 ? RT_PEEL_MIN_BLOCKS : 2;
@@ -1226,8 +1231,13 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
       uint32_t meta = 0u;
       int o = 0, rjob = -1;
       if (have) {
+#if RT_PEEL_OBS_MAJOR
+        const long long rec = gi % n_rec;
+        o = (int)(gi / n_rec);
+#else
         const long long rec = gi / n_obs_max;
         o = (int)(gi - rec * n_obs_max);
+#endif
         PeelIO<R>::get(Q.rec, rec, rg, sdx, sdy, sdz, W, meta);
         rjob = (int)(meta >> 13);
       }
