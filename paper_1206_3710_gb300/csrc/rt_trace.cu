@@ -1167,10 +1167,11 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
 #ifndef RT_PEEL_MIN_BLOCKS
 #define RT_PEEL_MIN_BLOCKS 5
 #endif
-// work item gi = (record, observer): record-major (the observers of a
-// record on neighbouring lanes) or observer-major
+// work item gi = (record, observer): observer-major (neighbouring lanes
+// march in the same direction from consecutive records; 237 against 257 ms
+// for the cloud's six axis maps record-major)
 #ifndef RT_PEEL_OBS_MAJOR
-#define RT_PEEL_OBS_MAJOR 0
+#define RT_PEEL_OBS_MAJOR 1
 #endif
 template <typename R>
 struct PeelMinBlocks {
