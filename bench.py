@@ -63,6 +63,8 @@ def parse():
                          "peeltab: accelerated against exact peel-off")
     ap.add_argument("--iters", type=int, default=30, help="disc: Lambda-iteration cap")
     ap.add_argument("--disc-packets", type=int, default=100_000_000)
+    ap.add_argument("--disc-min-hits", type=float, default=1000.0,
+                    help="disc: cells with fewer deposits are left out of the stop rule")
     ap.add_argument("--sub-level", type=int, default=-1,
                     help="disc: compare full Lambda iterations with subiterations below this level")
     ap.add_argument("--ali", action="store_true", help="disc subiterations: also 30 full ALI steps")

@@ -136,7 +136,7 @@ def run_disc(a, rt, synth, ctx, torch):
     T = torch.zeros(g.n_cells, dtype=torch.float64, device="cuda")
     kw = dict(seed=1003, precision=32, packets_total=a.disc_packets, rr_wmin=1e-4, rr_p=0.9)
     clk = _clock_start()
-    res = rt.rt_lambda_iterate(ctx, g, m.sources, m.optics, T, max_iter=a.iters, tol=1e-3, min_hits=1000,
+    res = rt.rt_lambda_iterate(ctx, g, m.sources, m.optics, T, max_iter=a.iters, tol=1e-3, min_hits=a.disc_min_hits,
                                dust_packets_total=a.disc_packets, **kw)
     clocks = clk.stop()
     src, dust = res["source_ledger"], res["dust_ledger"]
@@ -145,6 +145,7 @@ def run_disc(a, rt, synth, ctx, torch):
     line = {"metric": "Lambda iteration: cell crossings/s and iterations to max dT/T < 1e-3",
             "workload": "disc", "n_cells": int(m.tree.n_cells), "n_levels": int(m.tree.n_levels),
             "tau_cell_threshold": m.tau_cell_thr, "iterations": res["n_iter"], "history": res["history"],
+            "packages_per_trace": a.disc_packets, "min_hits": a.disc_min_hits,
             "total_ms": res["ms"], "ms_per_iteration": res["ms"] / max(1, res["n_iter"] + 1),
             "source_trace": {k: src[k] for k in ("n_packets", "n_cross", "n_scatter", "kernel_ms")},
             "dust_trace_last": {k: dust[k] for k in ("n_packets", "n_cross", "n_scatter", "kernel_ms")},
