@@ -92,6 +92,8 @@ def parse():
                     help="seconds of Poisson arrivals for the serving figures of the default line (0: none)")
     ap.add_argument("--n-root", type=int, default=256)
     ap.add_argument("--levels", type=int, default=3)
+    ap.add_argument("--threshold-scale", type=float, default=1.0,
+                    help="cloud: refine where density > c x 4^l x mean (0.067: 8%% of the equivalent uniform cells)")
     ap.add_argument("--n-lambda", type=int, default=20)
     ap.add_argument("--packets-per-bin", type=int, default=10_000_000)
     ap.add_argument("--n-pix", type=int, default=256)
@@ -188,15 +190,18 @@ def l2_read_gbs(ctx, dev):
 def make_model(a):
     from paper_1206_3710_gb300 import synth
     return synth.cloud(n_root=a.n_root, levels=a.levels, n_lambda=a.n_lambda, packets_per_bin=a.packets_per_bin,
-                       n_pix=a.n_pix)
+                       n_pix=a.n_pix, threshold_scale=a.threshold_scale)
 
 
 def workload_config(a, m):
-    return {"workload": f"molecular cloud: {a.n_root}^3 root, {a.levels} levels (threshold 4^l x mean), "
+    thr = "4^l x mean" if a.threshold_scale == 1.0 else f"{a.threshold_scale:g} x 4^l x mean"
+    uniform = m.tree.n_cells / float(a.n_root << a.levels) ** 3
+    return {"workload": f"molecular cloud: {a.n_root}^3 root, {a.levels} levels (threshold {thr}), "
                         f"lognormal sigma_ln=1.5, {a.n_lambda} wavelengths, external isotropic field, "
                         f"{a.packets_per_bin:.0e} packages/wavelength, peel-off {m.observers.n_obs}x"
                         f"{a.n_pix}^2, FP32 trace + FP64 accumulators",
             "n_cells": int(m.tree.n_cells), "n_levels": int(m.tree.n_levels),
+            "fraction_of_uniform_cells": uniform,
             "packets_per_step": int(a.packets_per_bin * a.n_lambda * len(m.sources)),
             "l2_policy": "inputs larger than L2 (grid + per-wavelength FP64 absorbed arrays)"}
 
@@ -291,6 +296,19 @@ def shard_params(rank: int, packets_per_bin: int) -> dict:
     return dict(job=0, packet_offset=rank * packets_per_bin)
 
 
+def combine_shards(dist, world: int, *fields):
+    """The one exchange step of a sharded run (Sect. 5.2: results combine
+    only at the end): every rank's FP64 fields (absorbed energy, images)
+    become the mean over the ranks, i.e. the single run of world*n packages
+    per bin, on every rank (the temperature solve and the next Lambda step
+    need the combined field)."""
+    if world <= 1:
+        return
+    for f in fields:
+        dist.all_reduce(f)
+        f.mul_(1.0 / world)
+
+
 def reduce_over_ranks(dist, t_ms: float, counts, device):
     """Max of the ranks' timed spans and sums of their work counters."""
     import torch
@@ -347,6 +365,7 @@ def main():
         absorbed.zero_()
         images.zero_()
         led = rt.rt_peel(ctx, grid, m.sources, m.optics, obs, images, absorbed, stream=stream, **kw)
+        combine_shards(dist, world, absorbed, images)
         rt.rt_dust_temperature(ctx, grid, absorbed, nl, lam, kabs, dnu, T, stream=stream)
         return led
 

@@ -38,14 +38,18 @@ def _rank_main(rank, world, port, n):
         shard = bench.shard_params(rank, n)
         assert shard["job"] == 0
         res = oracle.trace(tree, m.sources, m.optics, n, seed=1002, packet_offset=shard["packet_offset"],
-                           rr_wmin=1e-2, rr_p=0.5)
+                           observers=m.observers, rr_wmin=1e-2, rr_p=0.5)
         ab = torch.from_numpy(res["absorbed"].copy())
-        dist.all_reduce(ab)
-        mean = ab.numpy() / world
+        im = torch.from_numpy(res["images"].copy())
+        bench.combine_shards(dist, world, ab, im)
         t, (cross, pk) = bench.reduce_over_ranks(dist, 10.0 + rank, [res["ledger"]["n_cross"], n], "cpu")
+        one = oracle.trace(tree, m.sources, m.optics, world * n, seed=1002, observers=m.observers,
+                           rr_wmin=1e-2, rr_p=0.5)
+        # every rank holds the combined single run
+        np.testing.assert_allclose(ab.numpy(), one["absorbed"], rtol=1e-12, atol=1e-15 * one["absorbed"].max())
+        np.testing.assert_allclose(im.numpy(), one["images"], rtol=1e-12, atol=1e-15 * one["images"].max())
+        assert one["images"].max() > 0
         if rank == 0:
-            one = oracle.trace(tree, m.sources, m.optics, world * n, seed=1002, rr_wmin=1e-2, rr_p=0.5)
-            np.testing.assert_allclose(mean, one["absorbed"], rtol=1e-12, atol=1e-15 * one["absorbed"].max())
             assert t == 10.0 + world - 1
             assert pk == world * n
             assert cross == one["ledger"]["n_cross"]
