@@ -111,6 +111,30 @@ struct Cursor {
   int k;
 };
 
+// The path above the current leaf (Sect. 2.3: a package that leaves a grid
+// goes up to the enclosing grid and from there down into its neighbour):
+// a[l * stride] is the index of the node of level l on the leaf's path from
+// its root cell, kept for the levels l < cap.  n is cap while the stored
+// path is the current leaf's (it was reached by a descent from its root
+// cell or from a stored ancestor) and 0 for a package placed directly in a
+// leaf; a move out of an octet then re-descends from the root cell, which
+// stores the path again.  cap = 0 keeps no path.
+struct AncPath {
+  uint32_t* a;
+  int stride;
+  int cap;
+  int n;
+};
+
+__device__ __forceinline__ AncPath no_path() {
+  AncPath P;
+  P.a = nullptr;
+  P.stride = 0;
+  P.cap = 0;
+  P.n = 0;
+  return P;
+}
+
 // grid geometry needed on the hot path, held in registers
 struct GridRegs {
   const uint32_t* node;
@@ -145,6 +169,44 @@ __device__ __forceinline__ void descend_step(Geo<R>& g, Cursor& cur, uint32_t w,
   const uint32_t o = by_lattice ? ol : (bx | (by << 1) | (bz << 2));
   cur.pending = (w & RT_CHILD_MASK) + o;
   cur.k += 1;
+}
+
+// descend_step() that also records the refined node on the path
+template <typename R>
+__device__ __forceinline__ void descend_step(Geo<R>& g, Cursor& cur, uint32_t w, R dx, R dy, R dz, const AncPath& P) {
+  if (P.cap > 0 && cur.k < P.cap) P.a[cur.k * P.stride] = cur.pending;
+  descend_step(g, cur, w, dx, dy, dz);
+}
+
+// Where the search for the neighbour starts after a crossing on axis a that
+// changed the lattice coordinate from cold to cnew (only bits below hb + 1
+// changed, hb the highest): the neighbour shares the ancestors above level
+// lev - hb, and its ancestor at that level m is the sibling of ours on axis a
+// (index +-2^a, the octet's children being in octant order).  hb = 0 is the
+// sibling of the leaf itself; m <= 0 (the root coordinate changed) starts at
+// the root cell.  Sets cur; the path stays the leaf's (a search from a stored
+// ancestor or the root cell rewrites the levels below its start).
+__device__ __forceinline__ void neighbour_start(const GridRegs& G, int lev, uint32_t idx, uint32_t cx, uint32_t cy,
+                                                uint32_t cz, int a, bool plus, uint32_t moved, AncPath& P,
+                                                Cursor& cur) {
+  const bool a0 = a == 0, a1 = a == 1;
+  const bool root_level = lev == 0;
+  const bool near = root_level || moved < 2u;  // root-level neighbour or sibling: one load
+  const uint32_t rx = cx >> lev, ry = cy >> lev, rz = cz >> lev;
+  if (P.cap > 0 && !near) {
+    // a branch, not selects: few crossings leave their octet on most grids
+    // (with no path, cap = 0 at compile time, this block is not compiled)
+    const int m = lev - (31 - __clz((int)moved));
+    const bool up = m >= 1 && m < P.n;
+    const uint32_t am = up ? P.a[m * P.stride] : 0u;
+    cur.pending = up ? (plus ? am + (1u << a) : am - (1u << a)) : rx + G.rx * (ry + G.ry * rz);
+    cur.k = up ? m : 0;
+    P.n = up ? P.n : P.cap;
+  } else {
+    const uint32_t step = root_level ? (a0 ? 1u : (a1 ? G.rx : G.rx * G.ry)) : (1u << a);
+    cur.pending = near ? (plus ? idx + step : idx - step) : rx + G.rx * (ry + G.ry * rz);
+    cur.k = near ? lev : 0;
+  }
 }
 
 // the node at the cursor is a leaf: if it is coarser than the lattice level,
@@ -216,14 +278,15 @@ __device__ __forceinline__ R clamp01(R v) {
 
 // Cross the exit face on axis a; aim the cursor at the neighbour (the
 // sibling in the same octet or the root-level neighbour with one load,
-// otherwise a descent from the root).  False when the package leaves the
-// root grid.  Written with selects only: lanes crossing different axes do
-// not diverge.  `moved` gets the bits of the lattice coordinate on axis a
+// otherwise a descent from the sibling of the deepest stored ancestor the
+// neighbour does not share, or from the root cell: neighbour_start).  False
+// when the package leaves the root grid.  Written with selects only: lanes
+// crossing different axes do not diverge.  `moved` gets the bits of the lattice coordinate on axis a
 // that changed (bit l + s set: the crossing left a block of 2^s cells of
 // level l on that axis, e.g. a tile).
 template <typename R>
 __device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, R t, R dx, R dy, R dz,
-                                        uint32_t& moved) {
+                                        uint32_t& moved, AncPath& P) {
   const bool a0 = a == 0, a1 = a == 1;
   const R da = a0 ? dx : (a1 ? dy : dz);
   const bool plus = da > R(0);
@@ -238,16 +301,17 @@ __device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cu
   g.cy = a1 ? cnew : g.cy;
   g.cz = (!a0 && !a1) ? cnew : g.cz;
   moved = cold ^ cnew;
-  const bool root_level = g.lev == 0;
-  const bool near = root_level || moved < 2u;  // root-level neighbour or sibling
-  const uint32_t step = root_level ? (a0 ? 1u : (a1 ? G.rx : G.rx * G.ry)) : (1u << a);
   // only axis a moved: inside while its root coordinate stays below the
   // root grid's size (a step below 0 wraps to a huge unsigned value)
   const bool inside = (cnew >> g.lev) < (a0 ? G.rx : (a1 ? G.ry : G.rz));
-  const uint32_t rx = g.cx >> g.lev, ry = g.cy >> g.lev, rz = g.cz >> g.lev;
-  cur.pending = near ? (plus ? g.idx + step : g.idx - step) : rx + G.rx * (ry + G.ry * rz);
-  cur.k = near ? g.lev : 0;
+  neighbour_start(G, g.lev, g.idx, g.cx, g.cy, g.cz, a, plus, moved, P, cur);
   return inside;
+}
+template <typename R>
+__device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, R t, R dx, R dy, R dz,
+                                        uint32_t& moved) {
+  AncPath P = no_path();
+  return advance(G, g, cur, a, t, dx, dy, dz, moved, P);
 }
 template <typename R>
 __device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, R t, R dx, R dy, R dz) {
@@ -259,7 +323,8 @@ __device__ __forceinline__ bool advance(const GridRegs& G, Geo<R>& g, Cursor& cu
 // the offsets on the other axes do not move, so only axis a is updated
 // (the same results as advance() with that direction)
 template <typename R>
-__device__ __forceinline__ bool advance_axis(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, bool plus) {
+__device__ __forceinline__ bool advance_axis(const GridRegs& G, Geo<R>& g, Cursor& cur, int a, bool plus,
+                                             AncPath& P) {
   const bool a0 = a == 0, a1 = a == 1;
   const R fnew = plus ? R(0) : R(1);
   g.fx = a0 ? fnew : g.fx;
@@ -270,13 +335,8 @@ __device__ __forceinline__ bool advance_axis(const GridRegs& G, Geo<R>& g, Curso
   g.cx = a0 ? cnew : g.cx;
   g.cy = a1 ? cnew : g.cy;
   g.cz = (!a0 && !a1) ? cnew : g.cz;
-  const bool root_level = g.lev == 0;
-  const bool near = root_level || (cold ^ cnew) < 2u;
-  const uint32_t step = root_level ? (a0 ? 1u : (a1 ? G.rx : G.rx * G.ry)) : (1u << a);
   const bool inside = (cnew >> g.lev) < (a0 ? G.rx : (a1 ? G.ry : G.rz));
-  const uint32_t rx = g.cx >> g.lev, ry = g.cy >> g.lev, rz = g.cz >> g.lev;
-  cur.pending = near ? (plus ? g.idx + step : g.idx - step) : rx + G.rx * (ry + G.ry * rz);
-  cur.k = near ? g.lev : 0;
+  neighbour_start(G, g.lev, g.idx, g.cx, g.cy, g.cz, a, plus, cold ^ cnew, P, cur);
   return inside;
 }
 

@@ -223,11 +223,16 @@ inline int ledger_shift(double w0_max, double rr_wmin, double rr_p) {
 // ------------------------------------------------------------------------
 namespace rtk {
 
+// levels of the path above a leaf a tracer lane keeps in shared memory (a
+// crossing out of a deeper octet re-descends from the root cell)
+#define RT_ANC_MAX 12
+
 struct LaunchCfg {
   int block;
   int blocks;        // grid of the untiled and emission launches
   int refill;
   int blocks_tiled;  // grid of the tiled rounds (their tracer is sized for fewer blocks per SM)
+  int anc = 0;       // levels of the stored path per lane (0..RT_ANC_MAX): the grids' depth
 };
 
 // launch the persistent tracer over n_items items of total packages;
@@ -245,15 +250,15 @@ cudaError_t launch_poly(int precision, int group, bool peel, const JobDev* jobs,
 // into out; hist_dev holds n_keys + 1 counters
 cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_bytes, int n_keys,
                       unsigned long long* hist_dev, void* out, cudaStream_t s);
-cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm, int mode = 0);
+cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm, int mode = 0, int anc = 0);
 // march the queued peel-off records (n_obs_max observers each); work_dev is a
 // zeroed counter
 cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
-                        int n_obs_max, int refill, cudaStream_t s);
+                        int n_obs_max, int refill, cudaStream_t s, int anc = 0);
 size_t peel_record_bytes(int precision);
 // peel-off kernel with the extinction tables of JobDev::ptab
 cudaError_t launch_peel_tab(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
-                            int n_obs_max, int refill, cudaStream_t s);
+                            int n_obs_max, int refill, cudaStream_t s, int anc = 0);
 // the extinction tables: column density from each block-face tile centre
 // along each observer direction to the border of the model (FP64 marches)
 struct PeelTabSpec {

@@ -247,6 +247,12 @@ __device__ __forceinline__ unsigned long long claim_slot(unsigned long long* ctr
   return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
 }
 
+// peel-off marches of warps whose live lanes all march along one axis in one
+// direction run a form of the loop with the axis and direction as constants
+#ifndef RT_PEEL_AXIS
+#define RT_PEEL_AXIS 1
+#endif
+
 #ifndef RT_TRACE_ONLY_LOOP
 #define RT_TRACE_ONLY_LOOP 1
 #endif
@@ -480,13 +486,17 @@ struct MaxThreads {
   static constexpr int value = (sizeof(R) == 4 && MODE == 2) ? RT_FP32_TILED_BLOCK : 256;
 };
 
-template <typename R, bool PEEL, int EST, bool HITS, int MODE, bool LEVELS = false, bool SPLIT = false>
+// PATH: lanes keep the path above their leaf (n_anc levels) and start the
+// search for a neighbour outside their octet at the deepest stored ancestor
+// it shares, else at the root cell
+template <typename R, bool PEEL, int EST, bool HITS, int MODE, bool LEVELS = false, bool SPLIT = false,
+          bool PATH = false>
 __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>::value) trace_kernel(const JobDev* __restrict__ jobs,
                                                                          const ItemDev* __restrict__ items,
                                                                          int n_items,
                                                                          unsigned long long* __restrict__ counter,
                                                                          long long total, int refill_thr,
-                                                                         PeelQueue Q, TileRun T) {
+                                                                         PeelQueue Q, TileRun T, int n_anc) {
   typedef TileIO<R, LEVELS || SPLIT> IO;
   typedef typename IO::Rec TRec;
   const unsigned FULL = 0xFFFFFFFFu;
@@ -503,6 +513,14 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
   uint32_t& orig_t = s_orig[(LEVELS || SPLIT) ? t : 0];
   int& sexp_t = s_sexp[SPLIT ? t : 0];
   if (LEVELS || SPLIT) orig_t = 0xFFFFFFFFu;
+  // the path above the current leaf, n_anc levels per lane (dynamic shared
+  // memory, n_anc x MaxThreads words)
+  extern __shared__ uint32_t s_anc[];
+  AncPath P;
+  P.a = s_anc + t;
+  P.stride = MaxThreads<R, MODE>::value;
+  P.cap = PATH ? n_anc : 0;
+  P.n = 0;
   __syncwarp();
 
   // hot per-lane state
@@ -691,6 +709,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           // descend from that root cell
           cur.pending = (g.cx >> g.lev) + G.rx * ((g.cy >> g.lev) + G.ry * (g.cz >> g.lev));
           cur.k = 0;
+          P.n = P.cap;
           st = ST_TRACE;
         } else {
           // ------------------------------------------------ emission (Sect. 2.3)
@@ -755,6 +774,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
               dz = Num<R>::dir(I, 2);
             }
             inside = place_root(G, g, cur, Num<R>::pos(I, 0), Num<R>::pos(I, 1), Num<R>::pos(I, 2), dx, dy, dz);
+            P.n = P.cap;
           } else if (I.kind == RT_SRC_EXTERNAL) {
             // face by area, uniform point on it, cosine-weighted inward direction
             const R ax = (R)G.ry * (R)G.rz, ay = (R)G.rx * (R)G.rz, az = (R)G.rx * (R)G.ry;
@@ -792,6 +812,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
               dz = dn; dx = st_ * cp; dy = st_ * sp;
             }
             inside = place_root(G, g, cur, px, py, pz, dx, dy, dz);
+            P.n = P.cap;
           } else {
             // dust emission (Sect. 4.2): the package is one of the packages
             // its cell sends in this bin, and draws from that cell's stream
@@ -806,6 +827,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
             g.fz = draw(C, t);
             cur.pending = (uint32_t)clo;
             cur.k = g.lev;
+            P.n = 0;  // placed in its leaf: no path above it yet
             const R u4 = draw(C, t), u5 = draw(C, t);
             iso_dir(u4, u5, dx, dy, dz);
             inside = true;
@@ -867,7 +889,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           const uint32_t w = ld_node(G.node + cur.pending);
           const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
           if (w & RT_INTERIOR) {
-            descend_step(g, cur, w, dx, dy, dz);
+            descend_step(g, cur, w, dx, dy, dz, P);
           } else {
             settle_leaf(g, cur, w, r64);
             const bool tr = TRACE_ONLY || st == ST_TRACE;
@@ -931,9 +953,11 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
                 ev = EV_INTERACT;
               } else if (!tr && taup > tau_cut) {
                 ev = EV_CUT;
-              } else if (!advance(G, g, cur, a, tx, dx, dy, dz, moved)) {
+              } else if (!advance(G, g, cur, a, tx, dx, dy, dz, moved, P)) {
                 ev = EV_ESCAPE;
-              } else if (LEVELS && tr && cur.k == 0 && crossed_grid_level(g, a, dx, dy, dz) < mlev) {
+              } else if (LEVELS && tr && cur.k < mlev && crossed_grid_level(g, a, dx, dy, dz) < mlev) {
+                // (the search for the neighbour starts at or above the level
+                // of the crossed face: cur.k <= that level)
                 const JobDev& J = jobs[C.job[t]];
                 const int v = crossed_grid_level(g, a, dx, dy, dz);
                 if (v <= J.sub_conf) {
@@ -1100,6 +1124,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
       g.fx = C.sfx[t]; g.fy = C.sfy[t]; g.fz = C.sfz[t];
       cur.pending = g.idx;
       cur.k = g.lev;
+      P.n = 0;  // the stored path may be an inline peel-off march's
       const R sdx = C.sdx[t], sdy = C.sdy[t], sdz = C.sdz[t];
       int o = C.obs_i[t];
       bool started = false;
@@ -1178,16 +1203,24 @@ struct PeelMinBlocks {
   static constexpr int value = sizeof(R) == 4 ? RT_PEEL_MIN_BLOCKS : 2;
 };
 
-template <typename R, bool TAB>
+template <typename R, bool TAB, bool PATH = false>
 __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(const JobDev* __restrict__ jobs,
                                                                            PeelQueue Q,
                                                                            unsigned long long* __restrict__ work,
-                                                                           int n_obs_max, int refill_thr) {
+                                                                           int n_obs_max, int refill_thr,
+                                                                           int n_anc) {
   const unsigned FULL = 0xFFFFFFFFu;
   enum { P_DEAD = 0, P_LIVE = 1, P_DONE = 2 };
   __shared__ WarpLedger SL;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   ledger_init<R>(SL, wid, lane);
+  // the path above the current leaf (dynamic shared memory, n_anc x 256 words)
+  extern __shared__ uint32_t s_anc[];
+  AncPath P;
+  P.a = s_anc + t;
+  P.stride = 256;
+  P.cap = PATH ? n_anc : 0;
+  P.n = 0;
   const long long n_rec = min((long long)*Q.count, Q.cap);
   const long long total = n_rec * (long long)n_obs_max;
 
@@ -1265,6 +1298,7 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
             g = rg;
             cur.pending = g.idx;
             cur.k = g.lev;
+            P.n = 0;  // starts in its leaf: no path above it yet
             G.node = J.node;
             G.rho64 = J.rho64;
             G.rx = J.root[0];
@@ -1295,63 +1329,98 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
 
     // ----------------------------------------------------------------- march
     int ev = st == P_LIVE ? EV_NONE : EV_IDLE;
-    do {
-      if (ev == EV_NONE) {
-        const uint32_t w = ld_node(G.node + cur.pending);
-        const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
-        if (w & RT_INTERIOR) {
-          descend_step(g, cur, w, dx, dy, dz);
-        } else {
-          settle_leaf(g, cur, w, r64);
-          int a;
-          R tx;
-          if (pax >= 0) {
-            // along an axis: the exit distance is the offset to the face ahead
-            const R f = pax == 0 ? g.fx : (pax == 1 ? g.fy : g.fz);
-            tx = pplus ? R(1) - f : f;
-            a = pax;
+    // one pass per lane and iteration.  AX >= 0: every live lane of the warp
+    // marches along axis AX in direction PL (an axis observer; the work items
+    // are observer-major, so this is the common case) and the axis and the
+    // direction are constants; AX = -1: any direction
+    auto march = [&](auto ax_c, auto pl_c) {
+      constexpr int AX = decltype(ax_c)::value;
+      constexpr bool PL = decltype(pl_c)::value;
+      const R KA = PL ? R(1) : R(-1);
+      do {
+        if (ev == EV_NONE) {
+          const uint32_t w = ld_node(G.node + cur.pending);
+          const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
+          if (w & RT_INTERIOR) {
+            if (AX >= 0)
+              descend_step(g, cur, w, AX == 0 ? KA : R(0), AX == 1 ? KA : R(0), AX == 2 ? KA : R(0), P);
+            else
+              descend_step(g, cur, w, dx, dy, dz, P);
           } else {
-            tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
-          }
-          if (a < 0) {
-            ev = EV_CUT;  // cannot happen for |k| = 1
-          } else {
-            taup += kext * g.rho * Num<R>::pow2m(g.lev) * tx;
-            npeel += tx > R(0) ? 1u : 0u;
-            if (taup > tau_cut) {
-              ev = EV_CUT;
-            } else if (!(pax >= 0 ? advance_axis(G, g, cur, a, pplus) : advance(G, g, cur, a, tx, dx, dy, dz))) {
-              ev = EV_ESCAPE;
-            } else if (TAB && cur.k == 0) {
-              const JobDev& J = jobs[job];
-              const int sh = g.lev + J.ptab_bsh;
-              const uint32_t bx = g.cx >> sh, by = g.cy >> sh, bz = g.cz >> sh;
-              if ((bx | (by << 10) | (bz << 20)) != tab_blk) {
-                // left the scattering point's block through the face on
-                // axis a: add the tabulated column of the tile it crossed
-                const uint32_t cu = a == 0 ? g.cy : (a == 1 ? g.cz : g.cx);
-                const uint32_t cv = a == 0 ? g.cz : (a == 1 ? g.cx : g.cy);
-                const R fu = a == 0 ? g.fy : (a == 1 ? g.fz : g.fx);
-                const R fv = a == 0 ? g.fz : (a == 1 ? g.fx : g.fy);
-                const uint32_t mask = (1u << sh) - 1u;
-                const R scale = Num<R>::pow2m(g.lev) * (R)(1 << J.ptab_ssh) / (R)(1 << J.ptab_bsh);
-                const int S = 1 << J.ptab_ssh;
-                int iu = (int)Num<R>::floor_(((R)(cu & mask) + fu) * scale);
-                int iv = (int)Num<R>::floor_(((R)(cv & mask) + fv) * scale);
-                iu = iu < 0 ? 0 : (iu >= S ? S - 1 : iu);
-                iv = iv < 0 ? 0 : (iv >= S ? S - 1 : iv);
-                const ObsDev& O = J.obs[tab_o];
-                const uint32_t b0x = tab_blk & 1023u, b0y = (tab_blk >> 10) & 1023u, b0z = tab_blk >> 20;
-                const long long blk = (long long)b0x + (long long)J.ptab_nbx * ((long long)b0y + (long long)J.ptab_nby * b0z);
-                const long long i = O.tab_off + ((blk * O.tab_naxes + O.tab_slot[a]) * S + iv) * (long long)S + iu;
-                taup += ktab * (R)__ldg(J.ptab + i);
-                ev = taup > tau_cut ? EV_CUT : EV_ESCAPE;
+            settle_leaf(g, cur, w, r64);
+            int a;
+            R tx;
+            if (AX >= 0) {
+              const R f = AX == 0 ? g.fx : (AX == 1 ? g.fy : g.fz);
+              tx = PL ? R(1) - f : f;
+              a = AX;
+            } else if (pax >= 0) {
+              // along an axis: the exit distance is the offset to the face ahead
+              const R f = pax == 0 ? g.fx : (pax == 1 ? g.fy : g.fz);
+              tx = pplus ? R(1) - f : f;
+              a = pax;
+            } else {
+              tx = exit_dist(g, dx, dy, dz, ix, iy, iz, a);
+            }
+            uint32_t moved;
+            if (a < 0) {
+              ev = EV_CUT;  // cannot happen for |k| = 1
+            } else {
+              taup += kext * g.rho * Num<R>::pow2m(g.lev) * tx;
+              npeel += tx > R(0) ? 1u : 0u;
+              if (taup > tau_cut) {
+                ev = EV_CUT;
+              } else if (!(AX >= 0     ? advance_axis(G, g, cur, AX, PL, P)
+                           : pax >= 0 ? advance_axis(G, g, cur, a, pplus, P)
+                                      : advance(G, g, cur, a, tx, dx, dy, dz, moved, P))) {
+                ev = EV_ESCAPE;
+              } else if (TAB && cur.k == 0) {
+                const JobDev& J = jobs[job];
+                const int sh = g.lev + J.ptab_bsh;
+                const uint32_t bx = g.cx >> sh, by = g.cy >> sh, bz = g.cz >> sh;
+                if ((bx | (by << 10) | (bz << 20)) != tab_blk) {
+                  // left the scattering point's block through the face on
+                  // axis a: add the tabulated column of the tile it crossed
+                  const uint32_t cu = a == 0 ? g.cy : (a == 1 ? g.cz : g.cx);
+                  const uint32_t cv = a == 0 ? g.cz : (a == 1 ? g.cx : g.cy);
+                  const R fu = a == 0 ? g.fy : (a == 1 ? g.fz : g.fx);
+                  const R fv = a == 0 ? g.fz : (a == 1 ? g.fx : g.fy);
+                  const uint32_t mask = (1u << sh) - 1u;
+                  const R scale = Num<R>::pow2m(g.lev) * (R)(1 << J.ptab_ssh) / (R)(1 << J.ptab_bsh);
+                  const int S = 1 << J.ptab_ssh;
+                  int iu = (int)Num<R>::floor_(((R)(cu & mask) + fu) * scale);
+                  int iv = (int)Num<R>::floor_(((R)(cv & mask) + fv) * scale);
+                  iu = iu < 0 ? 0 : (iu >= S ? S - 1 : iu);
+                  iv = iv < 0 ? 0 : (iv >= S ? S - 1 : iv);
+                  const ObsDev& O = J.obs[tab_o];
+                  const uint32_t b0x = tab_blk & 1023u, b0y = (tab_blk >> 10) & 1023u, b0z = tab_blk >> 20;
+                  const long long blk = (long long)b0x + (long long)J.ptab_nbx * ((long long)b0y + (long long)J.ptab_nby * b0z);
+                  const long long i = O.tab_off + ((blk * O.tab_naxes + O.tab_slot[a]) * S + iv) * (long long)S + iu;
+                  taup += ktab * (R)__ldg(J.ptab + i);
+                  ev = taup > tau_cut ? EV_CUT : EV_ESCAPE;
+                }
               }
             }
           }
         }
-      }
-    } while (keep_stepping(ev, RT_PEEL_EV_BATCH));
+      } while (keep_stepping(ev, RT_PEEL_EV_BATCH));
+    };
+    const int key = (st == P_LIVE && pax >= 0) ? 2 * pax + (pplus ? 1 : 0) : -1;
+    const int k0 = __shfl_sync(FULL, key, __ffs(__ballot_sync(FULL, st == P_LIVE)) - 1);
+    const bool same = __all_sync(FULL, st != P_LIVE || key == k0);
+    if (RT_PEEL_AXIS && !TAB && same && k0 >= 0) {
+      using A0 = std::integral_constant<int, 0>;
+      using A1 = std::integral_constant<int, 1>;
+      using A2 = std::integral_constant<int, 2>;
+      if (k0 == 0) march(A0{}, std::false_type{});
+      else if (k0 == 1) march(A0{}, std::true_type{});
+      else if (k0 == 2) march(A1{}, std::false_type{});
+      else if (k0 == 3) march(A1{}, std::true_type{});
+      else if (k0 == 4) march(A2{}, std::false_type{});
+      else march(A2{}, std::true_type{});
+    } else {
+      march(std::integral_constant<int, -1>{}, std::false_type{});
+    }
 
     if (ev == EV_ESCAPE) {
       const R c = pw * Num<R>::exp_(-taup);
@@ -1394,12 +1463,20 @@ __global__ void walk_kernel(const JobDev* __restrict__ job, long long n_rays, co
     return;
   }
   const R ix = inv_abs(dx), iy = inv_abs(dy), iz = inv_abs(dz);
+  // the tracers' stored path above the leaf, here in local memory
+  uint32_t path[RT_ANC_MAX];
+  AncPath P;
+  P.a = path;
+  P.stride = 1;
+  P.cap = RT_ANC_MAX;
+  P.n = RT_ANC_MAX;  // placed at the root: the descent stores the path
+  uint32_t moved;
   long long k = 0;
   for (long long guard = 0; guard < 64ll * (1ll << 22); ++guard) {
     const uint32_t w = __ldg(G.node + cur.pending);
     const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
     if (w & RT_INTERIOR) {
-      descend_step(g, cur, w, dx, dy, dz);
+      descend_step(g, cur, w, dx, dy, dz, P);
       continue;
     }
     settle_leaf(g, cur, w, r64);
@@ -1413,7 +1490,7 @@ __global__ void walk_kernel(const JobDev* __restrict__ job, long long n_rays, co
       }
       ++k;
     }
-    if (!advance(G, g, cur, a, t, dx, dy, dz)) break;
+    if (!advance(G, g, cur, a, t, dx, dy, dz, moved, P)) break;
   }
   counts[r] = k;
 }
@@ -1433,6 +1510,31 @@ __global__ void philox_kernel(long long n, const uint32_t* __restrict__ ctr, con
 // ------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------
+// dynamic shared memory of the stored paths (anc levels x the kernel's
+// maximum block size, its path stride); the tracers' static shared memory
+// plus this may exceed the default 48 KB, so the kernel is allowed that much
+template <typename K>
+static cudaError_t path_smem(K kernel, int max_block, int anc, size_t* bytes) {
+  *bytes = (size_t)anc * (size_t)max_block * sizeof(uint32_t);
+  if (*bytes == 0) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
+}
+
+template <typename R, bool PEEL, int EST, bool HITS, int MODE, bool LEVELS, bool SPLIT>
+static cudaError_t launch_mode(const JobDev* jobs, const ItemDev* items, int n_items, unsigned long long* counter,
+                               long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s,
+                               const TileRun& T) {
+  auto k = cfg.anc > 0 ? trace_kernel<R, PEEL, EST, HITS, MODE, LEVELS, SPLIT, true>
+                       : trace_kernel<R, PEEL, EST, HITS, MODE, LEVELS, SPLIT, false>;
+  const int block = std::min(cfg.block, MaxThreads<R, MODE>::value);
+  size_t dyn = 0;
+  cudaError_t e = path_smem(k, MaxThreads<R, MODE>::value, cfg.anc, &dyn);
+  if (e != cudaSuccess) return e;
+  k<<<MODE == 2 ? cfg.blocks_tiled : cfg.blocks, block, dyn, s>>>(jobs, items, n_items, counter, total, cfg.refill,
+                                                                  q, T, cfg.anc);
+  return cudaGetLastError();
+}
+
 template <typename R, bool PEEL, int EST, bool HITS, bool LEVELS = false>
 static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_items, unsigned long long* counter,
                             long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode,
@@ -1440,16 +1542,9 @@ static cudaError_t launch_t(const JobDev* jobs, const ItemDev* items, int n_item
   TileRun T;
   memset(&T, 0, sizeof T);
   if (tr) T = *tr;
-  if (mode == 1)
-    trace_kernel<R, PEEL, EST, HITS, 1, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
-                                                                                total, cfg.refill, q, T);
-  else if (mode == 2)
-    trace_kernel<R, PEEL, EST, HITS, 2, LEVELS><<<cfg.blocks_tiled, std::min(cfg.block, MaxThreads<R, 2>::value), 0, s>>>(
-        jobs, items, n_items, counter, total, cfg.refill, q, T);
-  else
-    trace_kernel<R, PEEL, EST, HITS, 0, LEVELS><<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter,
-                                                                                total, cfg.refill, q, T);
-  return cudaGetLastError();
+  if (mode == 1) return launch_mode<R, PEEL, EST, HITS, 1, LEVELS, false>(jobs, items, n_items, counter, total, cfg, q, s, T);
+  if (mode == 2) return launch_mode<R, PEEL, EST, HITS, 2, LEVELS, false>(jobs, items, n_items, counter, total, cfg, q, s, T);
+  return launch_mode<R, PEEL, EST, HITS, 0, LEVELS, false>(jobs, items, n_items, counter, total, cfg, q, s, T);
 }
 
 // resampling tracers: tiled modes only, continuous estimator, no hit counts
@@ -1458,13 +1553,10 @@ static cudaError_t launch_split(const JobDev* jobs, const ItemDev* items, int n_
                                 long long total, const LaunchCfg& cfg, const PeelQueue& q, cudaStream_t s, int mode,
                                 const TileRun* tr) {
   if (mode == 1)
-    trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 1, false, true>
-        <<<cfg.blocks, cfg.block, 0, s>>>(jobs, items, n_items, counter, total, cfg.refill, q, *tr);
-  else
-    trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2, false, true>
-        <<<cfg.blocks_tiled, std::min(cfg.block, MaxThreads<R, 2>::value), 0, s>>>(jobs, items, n_items, counter,
-                                                                                  total, cfg.refill, q, *tr);
-  return cudaGetLastError();
+    return launch_mode<R, PEEL, RT_EST_CONTINUOUS, false, 1, false, true>(jobs, items, n_items, counter, total, cfg,
+                                                                          q, s, *tr);
+  return launch_mode<R, PEEL, RT_EST_CONTINUOUS, false, 2, false, true>(jobs, items, n_items, counter, total, cfg, q,
+                                                                        s, *tr);
 }
 
 template <typename R, int EST>
@@ -1620,28 +1712,31 @@ size_t peel_record_bytes(int precision) { return precision == 64 ? sizeof(PeelRe
 
 template <typename R, bool TAB>
 static cudaError_t launch_peel_t(const JobDev* jobs, const PeelQueue& q, unsigned long long* work, int n_obs_max,
-                                 int refill, cudaStream_t s) {
+                                 int refill, cudaStream_t s, int anc) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, peel_kernel<R, TAB>, 256, 0) != cudaSuccess || occ < 1)
-    occ = 1;
-  peel_kernel<R, TAB><<<sms * occ, 256, 0, s>>>(jobs, q, work, n_obs_max, refill);
+  auto k = anc > 0 ? peel_kernel<R, TAB, true> : peel_kernel<R, TAB, false>;
+  size_t dyn = 0;
+  cudaError_t e = path_smem(k, 256, anc, &dyn);
+  if (e != cudaSuccess) return e;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, dyn) != cudaSuccess || occ < 1) occ = 1;
+  k<<<sms * occ, 256, dyn, s>>>(jobs, q, work, n_obs_max, refill, anc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
-                        int n_obs_max, int refill, cudaStream_t s) {
+                        int n_obs_max, int refill, cudaStream_t s, int anc) {
   if (q.cap <= 0 || n_obs_max <= 0) return cudaSuccess;
-  return precision == 64 ? launch_peel_t<double, false>(jobs_dev, q, work_dev, n_obs_max, refill, s)
-                         : launch_peel_t<float, false>(jobs_dev, q, work_dev, n_obs_max, refill, s);
+  return precision == 64 ? launch_peel_t<double, false>(jobs_dev, q, work_dev, n_obs_max, refill, s, anc)
+                         : launch_peel_t<float, false>(jobs_dev, q, work_dev, n_obs_max, refill, s, anc);
 }
 
 cudaError_t launch_peel_tab(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
-                            int n_obs_max, int refill, cudaStream_t s) {
+                            int n_obs_max, int refill, cudaStream_t s, int anc) {
   if (q.cap <= 0 || n_obs_max <= 0) return cudaSuccess;
-  return precision == 64 ? launch_peel_t<double, true>(jobs_dev, q, work_dev, n_obs_max, refill, s)
-                         : launch_peel_t<float, true>(jobs_dev, q, work_dev, n_obs_max, refill, s);
+  return precision == 64 ? launch_peel_t<double, true>(jobs_dev, q, work_dev, n_obs_max, refill, s, anc)
+                         : launch_peel_t<float, true>(jobs_dev, q, work_dev, n_obs_max, refill, s, anc);
 }
 
 // ------------------------------------------------------------------------
@@ -1715,18 +1810,27 @@ cudaError_t build_peel_table(const JobDev* job_dev, const PeelTabSpec& spec, dou
 }
 
 template <typename R, bool PEEL>
-static cudaError_t occ_t(int block, int* n, int mode) {
-  return mode == 2
-             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2>,
-                                                             std::min(block, MaxThreads<R, 2>::value), 0)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 0>,
-                                                             block, 0);
+static cudaError_t occ_t(int block, int* n, int mode, int anc) {
+  size_t dyn = 0;
+  if (mode == 2) {
+    auto k = anc > 0 ? trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2, false, false, true>
+                     : trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 2, false, false, false>;
+    const int b = std::min(block, MaxThreads<R, 2>::value);
+    cudaError_t e = path_smem(k, MaxThreads<R, 2>::value, anc, &dyn);
+    return e != cudaSuccess ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k, b, dyn);
+  }
+  auto k = anc > 0 ? trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 0, false, false, true>
+                   : trace_kernel<R, PEEL, RT_EST_CONTINUOUS, false, 0, false, false, false>;
+  cudaError_t e = path_smem(k, MaxThreads<R, 0>::value, anc, &dyn);
+  return e != cudaSuccess ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k, block, dyn);
 }
 
-cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm, int mode) {
+cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per_sm, int mode, int anc) {
   if (precision == 64)
-    return peel ? occ_t<double, true>(block, blocks_per_sm, mode) : occ_t<double, false>(block, blocks_per_sm, mode);
-  return peel ? occ_t<float, true>(block, blocks_per_sm, mode) : occ_t<float, false>(block, blocks_per_sm, mode);
+    return peel ? occ_t<double, true>(block, blocks_per_sm, mode, anc)
+                : occ_t<double, false>(block, blocks_per_sm, mode, anc);
+  return peel ? occ_t<float, true>(block, blocks_per_sm, mode, anc)
+              : occ_t<float, false>(block, blocks_per_sm, mode, anc);
 }
 
 cudaError_t launch_walk(int precision, const JobDev* job_dev, long long n_rays, const double* origins,

@@ -163,19 +163,23 @@ def test_grid_rejects_invalid(rt, ctx):
 
 # ----------------------------------------------------------------- walks
 
-def _walk_compare(rt, ctx, orc, desc, n_rays, precision, seed, length_rtol):
+def _walk_compare(rt, ctx, orc, desc, n_rays, precision, seed, length_rtol, max_seg=None, aim=None,
+                  length_atol=0.0):
     g = rt.Grid(ctx, desc)
     tree = orc.Tree(desc)
     rng = np.random.default_rng(seed)
     h0 = desc.box[0] / desc.root[0]
     o = rng.uniform(0, 1, (n_rays, 3)) * np.array(desc.box)
     d = rng.normal(size=(n_rays, 3))
+    if aim is not None:   # (point, spread): rays through a small box around the point
+        d = np.asarray(aim[0]) + rng.uniform(-1, 1, (n_rays, 3)) * aim[1] - o
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     if precision == 32:   # both sides walk the same f32-representable ray
         o = (o / h0).astype(np.float32).astype(np.float64) * h0
         o = np.minimum(o, np.array(desc.box) * (1 - 1e-7))
         d = d.astype(np.float32).astype(np.float64)
-    max_seg = 4 * int(sum(desc.root)) * 2 ** (desc.n_levels - 1) + 16
+    if max_seg is None:
+        max_seg = 4 * int(sum(desc.root)) * 2 ** (desc.n_levels - 1) + 16
     to = torch.from_numpy(o).to(DEV)
     td = torch.from_numpy(d).to(DEV)
     cells = torch.zeros((n_rays, max_seg), dtype=torch.int64, device=DEV)
@@ -199,7 +203,7 @@ def _walk_compare(rt, ctx, orc, desc, n_rays, precision, seed, length_rtol):
         # lengths relative to the segment, with an absolute floor of the same
         # relative size of the cell (very short corner segments)
         h_leaf = h0 * 0.5 ** lev_of[oc].astype(float)
-        assert np.all(np.abs(lens[r, :k] - ol) <= length_rtol * np.maximum(ol, h_leaf)), r
+        assert np.all(np.abs(lens[r, :k] - ol) <= length_rtol * np.maximum(ol, h_leaf) + length_atol), r
     return ties
 
 
@@ -218,9 +222,14 @@ def test_walks_clump_grid(rt, ctx, orc, precision, rtol):
     assert ties <= 2000 * (1e-4 if precision == 64 else 0.05)
 
 
-def test_walks_deep_grid(rt, ctx, orc):
-    """Ten refinement levels around one point: FP32 local coordinates keep
-    bit-exact cell sequences where global FP32 coordinates could not."""
+@pytest.mark.parametrize("depth", [10, 15])
+def test_walks_deep_grid(rt, ctx, orc, depth):
+    """Ten and fifteen refinement levels around one point.  FP64, rays aimed
+    through the deepest cells: most moves out of an octet start their search
+    at a stored ancestor; at fifteen levels the deepest ones lie below the
+    stored path (12 levels) and start at the root cell.  FP32, rays in random
+    directions (ten levels): local coordinates keep bit-exact cell sequences
+    where global FP32 coordinates could not."""
     def rho_fn(l, x, y, z):
         return np.ones(x.size)
 
@@ -229,11 +238,18 @@ def test_walks_deep_grid(rt, ctx, orc):
         c = np.array([2.3, 1.7, 2.9]) * s
         return (np.abs(x + 0.5 - c[0]) < 1.5) & (np.abs(y + 0.5 - c[1]) < 1.5) & (np.abs(z + 0.5 - c[2]) < 1.5)
 
-    desc = synth.grow_tree((4, 4, 4), (4.0,) * 3, 10, rho_fn, refine_fn)
-    assert desc.n_levels == 11
-    for precision, rtol in ((64, 1e-12), (32, 1e-5)):
-        ties = _walk_compare(rt, ctx, orc, desc, 300, precision, 9, rtol)
-        assert ties <= 300 * (0 if precision == 64 else 0.1)
+    desc = synth.grow_tree((4, 4, 4), (4.0,) * 3, depth, rho_fn, refine_fn)
+    assert desc.n_levels == depth + 1
+    # a ray crosses at most ~20 cells of each level's 6^3 refined block.
+    # Lengths: the oracle's global FP64 positions (coordinates ~2 root
+    # cells) carry ~1e-15 absolute error, above a relative 1e-12 of the
+    # deepest cells: an absolute floor of 1e-13 h0
+    ties = _walk_compare(rt, ctx, orc, desc, 300, 64, 9, 1e-12, max_seg=4096,
+                         aim=((2.3, 1.7, 2.9), 2.0 ** -(depth + 1)), length_atol=1e-13)
+    assert ties <= 3      # exits within 1e-9 h0 of another face: rare even in 2^-15 cells
+    if depth == 10:
+        ties = _walk_compare(rt, ctx, orc, desc, 300, 32, 9, 1e-5)
+        assert ties <= 300 * 0.1
 
 
 # ----------------------------------------------------------------- tracing
