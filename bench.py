@@ -42,13 +42,17 @@ BYTES_IMAGE_DEPOSIT = 16
 # child index in one 32-bit word: one 4-byte read per visit)
 BYTES_TRACE_CROSS_PACKED = 4 + 16
 BYTES_PEEL_CROSS_PACKED = 4
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per step of the
-# tracer (all its launches: the emission round and the tiled rounds) and of
-# the deferred peel-off kernel on the default molecular cloud workload, from
-# a single-pass ncu capture of the current kernels (set to None whenever a
-# kernel changes until it is captured again)
-NCU_TRAFFIC_PER_LAUNCH = None
-NCU_PEEL_TRAFFIC_PER_LAUNCH = None
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per crossing of
+# the tracer (all its launches in a step: the emission round and the tiled
+# rounds) and of the deferred peel-off kernel, from an ncu capture of every
+# launch of one step of the same cloud at 128^3 root cells (tiles of 64^3,
+# 1e6 packages per wavelength: 11.37 GB for 2.704e9 trace crossings, 1.249 GB
+# for 1.809e9 peel-off crossings).  The bench line scales them by its own
+# crossings on the default 256^3 workload (None whenever a kernel changes
+# until it is captured again).  The tracer's figure is an upper bound there:
+# the 128^3 case crosses tile faces twice as often per cell crossing.
+NCU_TRACE_BYTES_PER_CROSSING = 11.37e9 / 2.704457093e9
+NCU_PEEL_BYTES_PER_CROSSING = 1.249e9 / 1.808753762e9
 
 
 def parse():
@@ -409,8 +413,16 @@ def main():
         trace_bytes, peel_bytes = trace_bytes + peel_bytes, 0
         trace_packed, peel_packed = trace_packed + peel_packed, 0
     achieved = trace_bytes / (kern_ms * 1e-3) / 1e9
+    default_cloud = (a.n_root, a.levels, a.threshold_scale, a.n_lambda) == (256, 3, 1.0, 20)
+    trace_traffic = peel_traffic = None
+    if default_cloud and NCU_TRACE_BYTES_PER_CROSSING is not None:
+        trace_traffic = NCU_TRACE_BYTES_PER_CROSSING * L0["n_cross"]
+    if default_cloud and NCU_PEEL_BYTES_PER_CROSSING is not None:
+        peel_traffic = NCU_PEEL_BYTES_PER_CROSSING * L0["n_peel_cross"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": NCU_TRAFFIC_PER_LAUNCH, "peak_kind": peak_kind, "kernel": "trace_kernel<float,1,0,0>",
+            "traffic": trace_traffic,
+            "traffic_basis": "per step: ncu DRAM bytes per crossing of a 128^3 step, times this step's crossings",
+            "peak_kind": peak_kind, "kernel": "trace_kernel<float,1,0,0>",
             "kernel_ms": kern_ms, "alg_bytes_per_launch": trace_bytes,
             "bytes_per_unit": {"trace_crossing": BYTES_TRACE_CROSS, "peel_crossing": BYTES_PEEL_CROSS,
                                "image_deposit": BYTES_IMAGE_DEPOSIT},
@@ -425,7 +437,7 @@ def main():
         pa = peel_bytes / (peel_ms * 1e-3) / 1e9
         peel_roof = {"kernel": "peel_kernel<float>", "bound": "hbm", "achieved": pa, "peak": peak, "unit": "GB/s",
                      "frac": pa / peak, "kernel_ms": peel_ms, "alg_bytes_per_launch": peel_bytes,
-                     "traffic": NCU_PEEL_TRAFFIC_PER_LAUNCH,
+                     "traffic": peel_traffic,
                      "crossings_per_s": L0["n_peel_cross"] / (peel_ms * 1e-3),
                      "packed_node_word": {"frac": peel_packed / (peel_ms * 1e-3) / 1e9 / peak},
                      "l2": {"peak": l2_peak, "frac": pa / l2_peak}}
