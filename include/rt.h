@@ -124,8 +124,9 @@ typedef struct {
 /* Flatten the tree into level-ordered device arrays (structure of arrays):
  * density (f32; refined cells hold the mean of their children), child
  * (u32; 0 = leaf, else index of the first of 8 contiguous children), level
- * (u8), plus the tracer's packed node word (leaf: f32 density scaled to
- * [0,1]; refined: 0x80000000 | child) and an f64 density copy.  The library
+ * (u8), plus the tracer's packed node word (leaf: f32 density / rho_scale,
+ * rho_scale = 2^-64 x the densest leaf; refined: 0x80000000 | child) and an
+ * f64 density copy.  The library
  * owns the arrays; free with rt_grid_free.  Errors: RT_ERR_INVALID for
  * inconsistent counts, negative/NaN densities, non-cubic cells, more than
  * 2^31 cells or a finest lattice above 2^21 cells per axis; RT_ERR_OOM. */
@@ -147,6 +148,23 @@ typedef struct {
 } rt_grid_info;
 int rt_grid_get_info(const rt_grid* grid, rt_grid_info* out);
 void rt_grid_free(rt_grid* grid);
+
+/* New densities for an existing grid, the tree unchanged (Sect. 2.1: the
+ * density arrays of the grids; a sequence of models on one mesh, or the same
+ * model uploaded again each run).  density: host [n_cells] f64 in the
+ * grid's level order, refined cells' values ignored (they get the mean of
+ * their children); pinned host memory makes the copy asynchronous.  Work is
+ * issued on cuda_stream (NULL = legacy default stream): the upload,
+ * validation and densest leaf are read back (the call waits for them and
+ * for earlier work on that stream), then the node words are rebuilt
+ * stream-ordered; work on other streams that uses the grid must be ordered
+ * after the stream by the caller.  Nothing is allocated.  Afterwards the
+ * grid's arrays equal those rt_build_grid gives for the same tree and
+ * densities.  Errors: RT_ERR_INVALID for NULL arguments, a grid of another
+ * context, or a negative, NaN or infinite leaf density (the grid's
+ * densities are then undefined until a successful call); RT_ERR_TIMEOUT,
+ * RT_ERR_BUSY, RT_ERR_CUDA as for the other calls. */
+int rt_grid_set_density(rt_ctx* ctx, rt_grid* grid, const double* density, void* cuda_stream);
 
 /* ------------------------------------------------------------------------ */
 /* Tracing (Sects. 2.3, 2.4)                                                 */

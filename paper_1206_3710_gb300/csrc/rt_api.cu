@@ -123,6 +123,7 @@ struct rt_grid {
   uint32_t* node = nullptr;
   double* rho64 = nullptr;
   uint64_t* coord = nullptr;
+  double* scratch = nullptr;  // [0] densest leaf, [1] invalid-density flag (rt_grid_set_density)
   double rho_scale = 1.0;
   size_t bytes = 0;
 };
@@ -391,6 +392,7 @@ extern "C" int rt_build_grid(rt_ctx* ctx, const rt_tree_desc* d, rt_grid** out) 
   ALLOC(g->node, n * sizeof(uint32_t));
   ALLOC(g->rho64, n * sizeof(double));
   ALLOC(g->coord, n * sizeof(uint64_t));
+  ALLOC(g->scratch, 2 * sizeof(double));
   g->bytes = n * (sizeof(float) + sizeof(uint32_t) * 2 + sizeof(uint8_t) + sizeof(double) + sizeof(uint64_t));
   ALLOC(flags, n);
   ALLOC(excl, n * sizeof(unsigned long long));
@@ -465,7 +467,43 @@ extern "C" void rt_grid_free(rt_grid* g) {
   cudaFree(g->node);
   cudaFree(g->rho64);
   cudaFree(g->coord);
+  cudaFree(g->scratch);
   delete g;
+}
+
+// New densities for an existing grid (same tree): upload on the caller's
+// stream, validate, interior means, densest leaf (read back: the node words'
+// scale), node words.  Nothing is allocated, so work on other streams keeps
+// running; the node words are rebuilt stream-ordered after the return.
+extern "C" int rt_grid_set_density(rt_ctx* ctx, rt_grid* g, const double* density, void* cuda_stream) {
+  if (!ctx || !g || !density) return fail(RT_ERR_INVALID, "rt_grid_set_density: NULL argument");
+  if (g->ctx != ctx) return fail(RT_ERR_INVALID, "rt_grid_set_density: the grid belongs to another context");
+  CTX_ENTER(ctx);
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const long long n = g->n_cells;
+  int* bad = reinterpret_cast<int*>(g->scratch + 1);
+  int rc = ensure_pin_rb(ctx, 2 * sizeof(double));
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(g->rho64, density, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(validate_leaf_density(g->rho64, g->child, n, bad, s));
+  for (int l = g->n_levels - 2; l >= 0; --l)
+    CK(build_density(nullptr, g->child, g->level_off[l], g->level_off[l + 1], g->rho64, s));
+  CK(reduce_max_leaf(g->rho64, g->child, n, g->scratch, s));
+  CK(cudaMemcpyAsync(ctx->pin_rb, g->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev_c, s));
+  rc = ctx_wait(ctx, ctx->ev_c, 3600.0);
+  if (rc) return rc;
+  double hmax = 0.0;
+  int hbad = 0;
+  memcpy(&hmax, ctx->pin_rb, sizeof(double));
+  memcpy(&hbad, static_cast<char*>(ctx->pin_rb) + sizeof(double), sizeof(int));
+  if (hbad)
+    return fail(RT_ERR_INVALID, "rt_grid_set_density: negative, NaN or infinite leaf density (the grid's "
+                                "densities are undefined until a successful call)");
+  g->rho_scale = hmax > 0.0 ? std::ldexp(hmax, -64) : 1.0;
+  CK(build_nodes(g->rho64, g->child, n, 1.0 / g->rho_scale, g->density, g->node, s));
+  return RT_OK;
 }
 
 // ------------------------------------------------------------------------

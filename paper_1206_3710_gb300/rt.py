@@ -22,7 +22,8 @@ RT_EST_CONTINUOUS, RT_EST_ANALOG = 0, 1
 SOURCE_KINDS = {"point": RT_SRC_POINT, "external": RT_SRC_EXTERNAL, "dust": RT_SRC_DUST, "beam": RT_SRC_BEAM}
 
 EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "rt_build_grid", "rt_grid_get_info",
-            "rt_grid_free", "rt_trace", "rt_peel", "rt_dust_temperature", "rt_dust_emission", "rt_walk",
+            "rt_grid_free", "rt_grid_set_density", "rt_trace", "rt_peel", "rt_dust_temperature", "rt_dust_emission",
+            "rt_walk",
             "rt_philox", "rt_trace_noalloc", "rt_lambda_iterate", "rt_trace_batch", "rt_batch_create",
             "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load", "rt_server_create",
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
@@ -168,6 +169,7 @@ def lib():
     L.rt_grid_get_info.argtypes = [vp, C.POINTER(rt_grid_info)]
     L.rt_grid_free.argtypes = [vp]
     L.rt_grid_free.restype = None
+    L.rt_grid_set_density.argtypes = [vp, vp, C.POINTER(C.c_double), vp]
     L.rt_trace.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics), C.POINTER(rt_trace_params),
                            vp, C.POINTER(rt_ledger), vp]
     L.rt_peel.argtypes = [vp, vp, C.c_int, C.POINTER(rt_source), C.POINTER(rt_optics), C.POINTER(rt_trace_params),
@@ -312,6 +314,15 @@ class Grid:
         self.desc = desc
         self.info = self.get_info()
         self.n_cells = int(self.info.n_cells)
+
+    def set_density(self, density, stream=None):
+        """rt_grid_set_density: new densities (host, f64, level order) for
+        this grid's tree; a pinned array makes the copy asynchronous."""
+        d = np.asarray(density)
+        if d.dtype != np.float64 or d.ndim != 1 or d.size != self.n_cells or not d.flags["C_CONTIGUOUS"]:
+            raise ValueError("set_density: a contiguous float64 array of n_cells values")
+        _check(lib().rt_grid_set_density(self.ctx.handle, self.handle, d.ctypes.data_as(C.POINTER(C.c_double)),
+                                         _stream(stream)))
 
     def get_info(self) -> rt_grid_info:
         inf = rt_grid_info()

@@ -108,6 +108,55 @@ def test_grid_build_arrays(rt, ctx, seed):
         np.testing.assert_array_equal(xyz, (lo * 2 ** lev).round().astype(int))
 
 
+def test_grid_set_density_equals_a_fresh_build(rt, ctx):
+    """rt_grid_set_density on a grid built from density A gives, array by
+    array and bit for bit, the grid rt_build_grid builds from density B (same
+    tree), also from a pinned host array on a side stream; a NaN leaf
+    density is refused, and a later valid call restores the grid."""
+    desc = synth.random_refined_tree((5, 3, 4), (5.0, 3.0, 4.0), 3, 0.35, 1)
+    rng = np.random.default_rng(4)
+    dens_b = rng.lognormal(0.0, 2.0, desc.n_cells) * 1e-20
+    desc_b = synth.TreeDesc(desc.root, desc.box, desc.n_refined, desc.refine_flags, dens_b)
+    ref = rt.Grid(ctx, desc_b)
+    n = desc.n_cells
+
+    def arrays(g):
+        inf = g.get_info()
+        return (inf.rho_scale, _copy_dev(inf.density64, n, np.float64), _copy_dev(inf.density, n, np.float32),
+                _copy_dev(inf.node, n, np.uint32), _copy_dev(inf.child, n, np.uint32),
+                _copy_dev(inf.coord, n, np.uint64))
+
+    want = arrays(ref)
+    g = rt.Grid(ctx, desc)
+    g.set_density(dens_b)
+    got = arrays(g)
+    assert got[0] == want[0]
+    for a, b in zip(got[1:], want[1:]):
+        np.testing.assert_array_equal(a, b)
+    # pinned host memory, a side stream
+    pin = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    pin.numpy()[:] = desc.density
+    side = torch.cuda.Stream()
+    g.set_density(pin.numpy(), stream=side)
+    side.synchronize()
+    fresh = arrays(rt.Grid(ctx, desc))
+    got = arrays(g)
+    assert got[0] == fresh[0]
+    for a, b in zip(got[1:], fresh[1:]):
+        np.testing.assert_array_equal(a, b)
+    bad = dens_b.copy()
+    bad[np.nonzero(desc.refine_flags == 0)[0][3]] = np.nan
+    with pytest.raises(rt.RtError) as e:
+        g.set_density(bad)
+    assert e.value.code == rt.RT_ERR_INVALID
+    g.set_density(dens_b)
+    got = arrays(g)
+    for a, b in zip(got[1:], want[1:]):
+        np.testing.assert_array_equal(a, b)
+    with pytest.raises(ValueError):
+        g.set_density(dens_b[:-1])
+
+
 def _copy_dev(ptr, count, np_dtype):
     """Copy `count` elements at a library-owned device address into numpy."""
     import ctypes
