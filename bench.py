@@ -492,9 +492,11 @@ def e2e_run(a, m, ctx, dev, stream, kw, lam, kabs, dnu):
     uploaded once (rt_build_grid, before the timed region); every step then
     uploads the density from pinned host memory (rt_grid_set_density), traces
     (rt_peel), solves the temperatures (rt_dust_temperature) and copies the
-    absorbed energy, images and temperatures to pinned host memory.  A step's
-    copies run on a second stream while the next step traces (two sets of
-    device and host outputs); one untimed step first."""
+    step's results, the dust temperatures and the peel-off images (Sects.
+    4.1-4.2), to pinned host memory; the absorbed energy per bin stays on the
+    device, as between the steps of a Lambda iteration.  A step's copies run
+    on a second stream while the next step traces (two sets of device and
+    host outputs); one untimed step first."""
     import torch
 
     from paper_1206_3710_gb300 import rt
@@ -510,7 +512,7 @@ def e2e_run(a, m, ctx, dev, stream, kw, lam, kabs, dnu):
     for _ in range(2):
         shapes = ((nl, nc), (obs.n_obs, nl, obs.ny, obs.nx), (nc,))
         bufs.append({"dev": [torch.empty(sh, dtype=torch.float64, device=dev) for sh in shapes],
-                     "host": [torch.empty(sh, dtype=torch.float64, pin_memory=True) for sh in shapes],
+                     "host": [torch.empty(sh, dtype=torch.float64, pin_memory=True) for sh in shapes[1:]],
                      "done": torch.cuda.Event(), "copied": torch.cuda.Event()})
     steps = max(1, a.steps)
     cross = 0
@@ -531,7 +533,7 @@ def e2e_run(a, m, ctx, dev, stream, kw, lam, kabs, dnu):
         b["done"].record(comp)
         copy.wait_event(b["done"])
         with torch.cuda.stream(copy):
-            for h, d in zip(b["host"], b["dev"]):
+            for h, d in zip(b["host"], b["dev"][1:]):    # images, temperatures
                 h.copy_(d, non_blocking=True)
         b["copied"].record(copy)
         if i >= 1:
@@ -544,7 +546,7 @@ def e2e_run(a, m, ctx, dev, stream, kw, lam, kabs, dnu):
     return {"value": cross / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "steps": steps, "ms_per_step": 1e3 * dt / steps,
             "pattern": "mesh uploaded once; per step: density up from pinned memory, trace, temperatures, "
-                       "results down to pinned memory overlapped with the next step"}
+                       "temperatures and images down to pinned memory overlapped with the next step"}
 
 if __name__ == "__main__":
     main()

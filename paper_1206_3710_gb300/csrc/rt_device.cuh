@@ -23,8 +23,6 @@ struct Num<float> {
   }
   static __device__ __forceinline__ float log_(float x) { return logf(x); }
   static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
-  // 1 - exp(-x) for x >= 0: Taylor series through x^6 below 1/8 (relative
-  // remainder < 1e-9), 1 - expf(-x) above (where it is >= 0.117)
   // q = 1 - exp(-x) and e = exp(-x) for x >= 0, both without cancellation:
   // Taylor series of q through x^6 below 1/8 (relative remainder < 1e-9)
   // with e = 1 - q; expf above, where q = 1 - e >= 0.117
