@@ -28,8 +28,12 @@ struct Num<float> {
   // with e = 1 - q; expf above, where q = 1 - e >= 0.117
   static __device__ __forceinline__ void absorb_pair(float x, float& q, float& e) {
     const float p = x * (1.0f - x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x * (1.0f / 720.0f))))));
-    const float ex = expf(-x);
     const bool small = x < 0.125f;
+    // expf only where some lane needs it (most segments are thin): a branch,
+    // so a warp without thick segments skips it (tracer 1 % faster on the
+    // 256^3 cloud than computing it for every segment)
+    float ex = 0.0f;
+    if (!small) ex = expf(-x);
     q = small ? p : 1.0f - ex;
     e = small ? 1.0f - p : ex;
   }
