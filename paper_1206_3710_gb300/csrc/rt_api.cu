@@ -87,6 +87,7 @@ struct rt_ctx {
   size_t pinned_n = 0;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr, ev_m = nullptr;
   DevBuf peel_q;                          // deferred peel-off records
+  DevBuf peel_q2;                         // the same sorted by block of root cells
   long long peel_q_max = 1ll << 27;       // records; 0: peel-off inline
   int tile_edge = -1;                     // tiled tracing: -1 auto, 0 off, > 0 tile edge in root cells
   long long tile_rec_max = 0;             // tiled tracing: record buffer capacity (0: default)
@@ -207,6 +208,7 @@ extern "C" void rt_ctx_destroy(rt_ctx* c) {
   if (c->ev_m) cudaEventDestroy(c->ev_m);
   if (c->pin_count) cudaFreeHost(c->pin_count);
   c->peel_q.release();
+  c->peel_q2.release();
   c->tile_a.release();
   c->tile_b.release();
   c->tile_key.release();
@@ -1177,6 +1179,39 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
   return RT_OK;
 }
 
+// Deferred peel-off records sorted by block of root cells (at most 4096
+// blocks of the first job's root grid), so that the lanes of a warp march
+// from nearby points: the queue length is read back (the tracer has
+// finished), the records are counting-sorted into a second buffer.
+#ifndef RT_PEEL_SORT
+#define RT_PEEL_SORT 1
+#endif
+static int sort_peel_queue(rt_ctx* c, const PeelQueue& q, int precision, const rt_grid* G, double timeout_s,
+                           cudaStream_t s, PeelQueue* out) {
+  *out = q;
+  CK(cudaMemcpyAsync(c->pin_count, q.count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(c->ev_c, s));
+  int rc = ctx_wait(c, c->ev_c, timeout_s);
+  if (rc) return rc;
+  const long long n = std::min<long long>((long long)c->pin_count[0], q.cap);
+  if (n < 64) return RT_OK;
+  int bs = 0;
+  auto nb = [&](int r) { return (r + (1 << bs) - 1) >> bs; };
+  while ((long long)nb(G->root[0]) * nb(G->root[1]) * nb(G->root[2]) > 4096) ++bs;
+  const int n_keys = nb(G->root[0]) * nb(G->root[1]) * nb(G->root[2]);
+  const size_t rb = peel_record_bytes(precision);
+  rc = c->peel_q2.ensure(rb * (size_t)n);
+  if (!rc) rc = c->tile_key.ensure(sizeof(uint32_t) * (size_t)n);
+  if (!rc) rc = c->tile_hist.ensure(sizeof(unsigned long long) * ((size_t)n_keys + 1));
+  if (rc) return rc;
+  uint32_t* key = reinterpret_cast<uint32_t*>(c->tile_key.p);
+  CK(peel_keys(precision, q.rec, n, bs, nb(G->root[0]), nb(G->root[1]), nb(G->root[2]), key, c->sm_count, s));
+  CK(tile_sort(q.rec, key, n, (int)rb, n_keys, reinterpret_cast<unsigned long long*>(c->tile_hist.p), c->peel_q2.p,
+               s));
+  out->rec = c->peel_q2.p;
+  return RT_OK;
+}
+
 static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* ledgers, cudaStream_t s,
                     const rt_trace_params* launch_prm) {
   // ledgers + package counter
@@ -1245,11 +1280,16 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   if (total > 0 && n_items > 0 && q.cap > 0) n_launch += 1;  // the deferred peel-off
   CK(cudaEventRecord(c->ev_m, s));
   if (total > 0 && n_items > 0 && q.cap > 0) {
+    PeelQueue qs = q;
+#if RT_PEEL_SORT
+    rc = sort_peel_queue(c, q, precision, jobs[0].grid, to, s, &qs);
+    if (rc) return rc;
+#endif
     if (n_jobs == 1 && jobs[0].tab)
-      CK(launch_peel_tab(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
+      CK(launch_peel_tab(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), qs, counter + 2,
                          max_observers(n_jobs, jobs), cfg.refill, s, cfg.anc));
     else
-      CK(launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), q, counter + 2,
+      CK(launch_peel(precision, reinterpret_cast<const JobDev*>(base + job_off[0]), qs, counter + 2,
                      max_observers(n_jobs, jobs), cfg.refill, s, cfg.anc));
   }
   CK(cudaEventRecord(c->ev_b, s));

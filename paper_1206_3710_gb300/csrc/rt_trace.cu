@@ -1710,6 +1710,42 @@ cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_
 
 size_t peel_record_bytes(int precision) { return precision == 64 ? sizeof(PeelRec64) : sizeof(PeelRec32); }
 
+// sort key of a deferred peel-off record: the block of 2^bs root cells
+// holding the scattering point, x fastest, clamped to the nbx x nby x nbz
+// blocks of the first job's root grid
+template <typename R>
+__global__ void peel_key_kernel(const void* __restrict__ rec, long long n, int bs, int nbx, int nby, int nbz,
+                                uint32_t* __restrict__ key) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    uint4 a;
+    uint32_t meta;
+    if (sizeof(R) == 4) {
+      const uint4* p = reinterpret_cast<const uint4*>(static_cast<const PeelRec32*>(rec) + i);
+      a = __ldg(p);
+      meta = __ldg(&p[2].w);
+    } else {
+      const PeelRec64* r = static_cast<const PeelRec64*>(rec) + i;
+      a = __ldg(reinterpret_cast<const uint4*>(&r->cx));
+      meta = __ldg(&r->meta);
+    }
+    const int sh = (int)(meta & 31u) + bs;
+    const uint32_t bx = min(a.x >> sh, (uint32_t)(nbx - 1));
+    const uint32_t by = min(a.y >> sh, (uint32_t)(nby - 1));
+    const uint32_t bz = min(a.z >> sh, (uint32_t)(nbz - 1));
+    key[i] = bx + (uint32_t)nbx * (by + (uint32_t)nby * bz);
+  }
+}
+
+cudaError_t peel_keys(int precision, const void* rec, long long n, int bs, int nbx, int nby, int nbz, uint32_t* key,
+                      int sm_count, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int B = 256;
+  const int G = (int)std::min<long long>((n + B - 1) / B, (long long)sm_count * 8);
+  if (precision == 64) peel_key_kernel<double><<<G, B, 0, s>>>(rec, n, bs, nbx, nby, nbz, key);
+  else peel_key_kernel<float><<<G, B, 0, s>>>(rec, n, bs, nbx, nby, nbz, key);
+  return cudaGetLastError();
+}
+
 template <typename R, bool TAB>
 static cudaError_t launch_peel_t(const JobDev* jobs, const PeelQueue& q, unsigned long long* work, int n_obs_max,
                                  int refill, cudaStream_t s, int anc) {
