@@ -1187,7 +1187,7 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
 #define RT_PEEL_SORT 1
 #endif
 static int sort_peel_queue(rt_ctx* c, const PeelQueue& q, int precision, const rt_grid* G, double timeout_s,
-                           cudaStream_t s, PeelQueue* out) {
+                           cudaStream_t s, PeelQueue* out, long long* launches) {
   *out = q;
   CK(cudaMemcpyAsync(c->pin_count, q.count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(c->ev_c, s));
@@ -1209,6 +1209,7 @@ static int sort_peel_queue(rt_ctx* c, const PeelQueue& q, int precision, const r
   CK(tile_sort(q.rec, key, n, (int)rb, n_keys, reinterpret_cast<unsigned long long*>(c->tile_hist.p), c->peel_q2.p,
                s));
   out->rec = c->peel_q2.p;
+  *launches += 4;  // keys, histogram, scan, scatter
   return RT_OK;
 }
 
@@ -1282,7 +1283,7 @@ static int run_jobs(rt_ctx* c, int n_jobs, const TraceArgs* jobs, rt_ledger* led
   if (total > 0 && n_items > 0 && q.cap > 0) {
     PeelQueue qs = q;
 #if RT_PEEL_SORT
-    rc = sort_peel_queue(c, q, precision, jobs[0].grid, to, s, &qs);
+    rc = sort_peel_queue(c, q, precision, jobs[0].grid, to, s, &qs, &n_launch);
     if (rc) return rc;
 #endif
     if (n_jobs == 1 && jobs[0].tab)

@@ -1224,23 +1224,23 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
   const long long n_rec = min((long long)*Q.count, Q.cap);
   const long long total = n_rec * (long long)n_obs_max;
 
-  int st = P_DEAD, job = -1;
+  // per lane: the work item (record, observer); the march direction, the
+  // record's weighted phase function and its pixel are derived again where
+  // needed instead of held (registers: the kernel runs 5 blocks per SM)
+  int st = P_DEAD, job = -1, obs_o = 0;
+  uint32_t rec_i = 0u;
   Geo<R> g;
   Cursor cur;
   GridRegs G;
-  R dx = R(0), dy = R(0), dz = R(1), ix = R(0), iy = R(0), iz = R(1);
-  R kext = R(0), taup = R(0), tau_cut = R(0), pw = R(0);
-  long long pix = 0;
+  R kext = R(0), taup = R(0), tau_cut = R(0);
   uint32_t npeel = 0u;
   // accelerated peel-off: block of the scattering point (x | y << 10 | z << 20),
-  // the observer, kappa_ext h0 of the bin
+  // kappa_ext h0 of the bin
   uint32_t tab_blk = 0u;
-  int tab_o = 0;
   R ktab = R(0);
   // an observer along a coordinate axis (the paper's maps, Sect. 4.1): the
-  // march moves on that axis only (pax, pplus); -1 otherwise
-  int pax = -1;
-  bool pplus = false;
+  // march moves on that axis only; akey = 2 x axis + (direction > 0), else -1
+  int akey = -1;
   g.lev = 0;
   cur.pending = 0u;
   cur.k = 0;
@@ -1264,12 +1264,13 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
       R sdx = R(0), sdy = R(0), sdz = R(0), W = R(0);
       uint32_t meta = 0u;
       int o = 0, rjob = -1;
+      long long rec = 0;
       if (have) {
 #if RT_PEEL_OBS_MAJOR
-        const long long rec = gi % n_rec;
+        rec = gi % n_rec;
         o = (int)(gi / n_rec);
 #else
-        const long long rec = gi / n_obs_max;
+        rec = gi / n_obs_max;
         o = (int)(gi - rec * n_obs_max);
 #endif
         PeelIO<R>::get(Q.rec, rec, rg, sdx, sdy, sdz, W, meta);
@@ -1283,18 +1284,18 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
           rg.lev = (int)(meta & 31u);
           const int bin = (int)((meta >> 5) & 255u);
           const BinDev& B = J.bins[bin];
+          R pw;
+          long long pix;
           if (peel_setup<R>(J, o, rg, sdx, sdy, sdz, W, Num<R>::gg(B), bin, pw, pix)) {
             const ObsDev& O = J.obs[o];
-            dx = ObsGeom<R>::k(O, 0);
-            dy = ObsGeom<R>::k(O, 1);
-            dz = ObsGeom<R>::k(O, 2);
-            ix = inv_abs(dx);
-            iy = inv_abs(dy);
-            iz = inv_abs(dz);
-            pax = TAB ? -1
-                      : ((dy == R(0) && dz == R(0)) ? 0
-                                                     : ((dx == R(0) && dz == R(0)) ? 1 : ((dx == R(0) && dy == R(0)) ? 2 : -1)));
-            pplus = (pax == 0 ? dx : (pax == 1 ? dy : dz)) > R(0);
+            const R kx = ObsGeom<R>::k(O, 0), ky = ObsGeom<R>::k(O, 1), kz = ObsGeom<R>::k(O, 2);
+            const int pax = TAB ? -1
+                                : ((ky == R(0) && kz == R(0)) ? 0
+                                                               : ((kx == R(0) && kz == R(0)) ? 1
+                                                                                             : ((kx == R(0) && ky == R(0)) ? 2 : -1)));
+            akey = pax < 0 ? -1 : 2 * pax + ((pax == 0 ? kx : (pax == 1 ? ky : kz)) > R(0) ? 1 : 0);
+            obs_o = o;
+            rec_i = (uint32_t)rec;
             g = rg;
             cur.pending = g.idx;
             cur.k = g.lev;
@@ -1312,7 +1313,6 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
             if (TAB) {
               const int sh = g.lev + J.ptab_bsh;
               tab_blk = (g.cx >> sh) | ((g.cy >> sh) << 10) | ((g.cz >> sh) << 20);
-              tab_o = o;
               ktab = (R)B.kext_d;
             }
             st = P_LIVE;
@@ -1337,6 +1337,21 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
       constexpr int AX = decltype(ax_c)::value;
       constexpr bool PL = decltype(pl_c)::value;
       const R KA = PL ? R(1) : R(-1);
+      // any direction: the observer's, from the job table
+      R dx = R(0), dy = R(0), dz = R(1), ix = R(0), iy = R(0), iz = R(1);
+      int pax = -1;
+      bool pplus = false;
+      if (AX < 0 && st == P_LIVE) {
+        const ObsDev& O = jobs[job].obs[obs_o];
+        dx = ObsGeom<R>::k(O, 0);
+        dy = ObsGeom<R>::k(O, 1);
+        dz = ObsGeom<R>::k(O, 2);
+        ix = inv_abs(dx);
+        iy = inv_abs(dy);
+        iz = inv_abs(dz);
+        pax = akey >> 1;
+        pplus = (akey & 1) != 0;
+      }
       do {
         if (ev == EV_NONE) {
           const uint32_t w = ld_node(G.node + cur.pending);
@@ -1392,7 +1407,7 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
                   int iv = (int)Num<R>::floor_(((R)(cv & mask) + fv) * scale);
                   iu = iu < 0 ? 0 : (iu >= S ? S - 1 : iu);
                   iv = iv < 0 ? 0 : (iv >= S ? S - 1 : iv);
-                  const ObsDev& O = J.obs[tab_o];
+                  const ObsDev& O = J.obs[obs_o];
                   const uint32_t b0x = tab_blk & 1023u, b0y = (tab_blk >> 10) & 1023u, b0z = tab_blk >> 20;
                   const long long blk = (long long)b0x + (long long)J.ptab_nbx * ((long long)b0y + (long long)J.ptab_nby * b0z);
                   const long long i = O.tab_off + ((blk * O.tab_naxes + O.tab_slot[a]) * S + iv) * (long long)S + iu;
@@ -1405,7 +1420,7 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
         }
       } while (keep_stepping(ev, RT_PEEL_EV_BATCH));
     };
-    const int key = (st == P_LIVE && pax >= 0) ? 2 * pax + (pplus ? 1 : 0) : -1;
+    const int key = st == P_LIVE ? akey : -1;
     const int k0 = __shfl_sync(FULL, key, __ffs(__ballot_sync(FULL, st == P_LIVE)) - 1);
     const bool same = __all_sync(FULL, st != P_LIVE || key == k0);
     if (RT_PEEL_AXIS && !TAB && same && k0 >= 0) {
@@ -1423,8 +1438,19 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
     }
 
     if (ev == EV_ESCAPE) {
+      // the record's weighted phase function and pixel, as at the setup
+      Geo<R> rg;
+      R sdx, sdy, sdz, W;
+      uint32_t meta;
+      PeelIO<R>::get(Q.rec, (long long)rec_i, rg, sdx, sdy, sdz, W, meta);
+      rg.lev = (int)(meta & 31u);
+      const int bin = (int)((meta >> 5) & 255u);
+      const JobDev& J = jobs[job];
+      R pw = R(0);
+      long long pix = 0;
+      peel_setup<R>(J, obs_o, rg, sdx, sdy, sdz, W, Num<R>::gg(J.bins[bin]), bin, pw, pix);
       const R c = pw * Num<R>::exp_(-taup);
-      if (c > R(0)) atomicAdd(jobs[job].images + pix, widen(c));
+      if (c > R(0)) atomicAdd(J.images + pix, widen(c));
       book_d(SL, jobs, job, wid, L_PEEL, c);
     }
     if (ev == EV_ESCAPE || ev == EV_CUT) {
