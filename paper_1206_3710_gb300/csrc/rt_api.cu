@@ -1179,12 +1179,16 @@ static int run_tiled(rt_ctx* c, TileRun T, int n_lambda, int precision, bool pee
   return RT_OK;
 }
 
-// Deferred peel-off records sorted by block of root cells (at most 4096
-// blocks of the first job's root grid), so that the lanes of a warp march
-// from nearby points: the queue length is read back (the tracer has
-// finished), the records are counting-sorted into a second buffer.
+// Deferred peel-off records sorted by block of root cells (at most
+// RT_PEEL_SORT_KEYS blocks of the first job's root grid: 4^3 root cells on a
+// 256^3 root), so that the lanes of a warp march from nearby points: the
+// queue length is read back (the tracer has finished), the records are
+// counting-sorted into a second buffer.
 #ifndef RT_PEEL_SORT
 #define RT_PEEL_SORT 1
+#endif
+#ifndef RT_PEEL_SORT_KEYS
+#define RT_PEEL_SORT_KEYS 262144
 #endif
 static int sort_peel_queue(rt_ctx* c, const PeelQueue& q, int precision, const rt_grid* G, double timeout_s,
                            cudaStream_t s, PeelQueue* out, long long* launches) {
@@ -1197,7 +1201,7 @@ static int sort_peel_queue(rt_ctx* c, const PeelQueue& q, int precision, const r
   if (n < 64) return RT_OK;
   int bs = 0;
   auto nb = [&](int r) { return (r + (1 << bs) - 1) >> bs; };
-  while ((long long)nb(G->root[0]) * nb(G->root[1]) * nb(G->root[2]) > 4096) ++bs;
+  while ((long long)nb(G->root[0]) * nb(G->root[1]) * nb(G->root[2]) > RT_PEEL_SORT_KEYS) ++bs;
   const int n_keys = nb(G->root[0]) * nb(G->root[1]) * nb(G->root[2]);
   const size_t rb = peel_record_bytes(precision);
   rc = c->peel_q2.ensure(rb * (size_t)n);
