@@ -270,6 +270,13 @@ typedef struct {
    * source's package count depends on the emission (within one per emitting
    * cell and bin of the budget), so give its log room beyond the budget. */
   int64_t packet_log_rows;
+  /* FP32 tracing: a near-vacuum cell, whose extinction per unit length lies
+   * below the f32 normal range (about 1e-43 of the densest leaf's), takes
+   * its deposit from the f64 density in the thin limit q = x instead of
+   * none, so its temperature follows from its absorbed energy per unit mass
+   * as in FP64.  Costs a read of the f64 density and FP64 arithmetic per
+   * such crossing (the 9.2e6-cell disc traces 30 % slower).  0: off. */
+  int thin_f64;
 } rt_trace_params;
 
 typedef struct {

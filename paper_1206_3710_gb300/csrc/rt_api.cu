@@ -870,6 +870,7 @@ static int build_tables(rt_ctx* c, int n_jobs, const TraceArgs* jobs, LedgerDev*
     J.peel_tau_max_f = (float)p->peel_tau_max;
     J.pkt_offset = p->packet_offset;
     J.sub_conf = T.confine;
+    J.thin64 = p->thin_f64 ? 1 : 0;
     J.split_n = p->split_factor > 1 ? p->split_factor : 1;
     J.poly_n = poly;
     J.split_lmax = p->split_max_level < 0 ? G->n_levels - 1 : std::min(p->split_max_level, G->n_levels - 1);

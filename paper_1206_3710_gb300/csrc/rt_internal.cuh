@@ -162,7 +162,7 @@ struct JobDev {
   float rr_wmin_f, rr_p_f, peel_tau_max_f;
   // the f32 tracer books ledger energies in 64-bit fixed point: value * 2^led_shift
   int led_shift;
-  int pad1;
+  int thin64;  // f32 tracer: near-vacuum cells' deposits from the f64 density
   long long pkt_offset;  // added to the package index of the random streams
   // accelerated peel-off: column densities on block faces (NULL: exact
   // marches); blocks of 2^ptab_bsh root cells, 2^ptab_ssh tiles per face edge

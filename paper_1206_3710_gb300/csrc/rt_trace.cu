@@ -27,6 +27,7 @@
 #include <math_constants.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <type_traits>
 #include <cstring>
 
@@ -924,11 +925,27 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
                   tau = inside_event ? R(0) : tau - tsc;
                   const R dep = W * q;
                   W = W * e;
-                  if (dep > R(0)) {
+                  const bool thin = sizeof(R) == 4 && !(kl >= R(FLT_MIN));
+                  if (dep > R(0) && !thin) {
                     pkt_abs += dep;
                     if (absb) red_acc(absb + g.idx, widen(dep));
                     if (HITS && hitp) atomicAdd(hitp + g.idx, 1u);
                     if (LEVELS && selfb && g.idx == orig_t) atomicAdd(selfb + g.idx, widen(dep));
+                  } else if (thin && tseg > R(0) && jobs[C.job[t]].thin64) {
+                    // a near-vacuum cell: its extinction per unit length is
+                    // below the f32 normal range, so the deposit is taken
+                    // from the f64 density in the thin limit q = x (x <
+                    // 1e-38; the weight and the free path do not change)
+                    const JobDev& J = jobs[C.job[t]];
+                    const BinDev& B = J.bins[C.bin[t]];
+                    const double x = (1.0 - B.albedo_d) * B.kext_d * __ldg(J.rho64 + g.idx) *
+                                     Num<double>::pow2m(g.lev) * (double)tseg;
+                    const double d64 = widen(W) * x;
+                    if (d64 > 0.0) {
+                      if (absb) red_acc(absb + g.idx, d64);
+                      if (HITS && hitp) atomicAdd(hitp + g.idx, 1u);
+                      if (LEVELS && selfb && g.idx == orig_t) atomicAdd(selfb + g.idx, d64);
+                    }
                   }
                 }
               } else {

@@ -75,7 +75,7 @@ class rt_trace_params(C.Structure):
                 ("timeout_s", C.c_double), ("block_size", C.c_int), ("refill_threshold", C.c_int),
                 ("blocks_per_sm", C.c_int), ("hits_dev", C.c_void_p), ("packet_offset", C.c_int64),
                 ("split_factor", C.c_int), ("split_max_level", C.c_int), ("poly_group", C.c_int),
-                ("packet_log_rows", C.c_int64)]
+                ("packet_log_rows", C.c_int64), ("thin_f64", C.c_int)]
 
 
 LEDGER_FIELDS = ["emitted", "absorbed", "escaped", "rr_gain", "rr_loss", "killed", "peeled", "n_packets", "n_cross",
@@ -382,7 +382,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
                 packets_total: int = 0, packet_log=None, timeout_s: float = 0.0, block_size: int = 0,
                 refill_threshold: int = 0, blocks_per_sm: int = 0, hits=None,
                 packet_offset: int = 0, split_factor: int = 1, split_max_level: int = -1,
-                poly_group: int = 1) -> rt_trace_params:
+                poly_group: int = 1, thin_f64: bool = False) -> rt_trace_params:
     p = rt_trace_params()
     p.seed, p.job, p.iter = int(seed), int(job), int(iter_)
     p.precision, p.estimator = int(precision), int(estimator)
@@ -398,6 +398,7 @@ def make_params(keep: _Keep, *, seed: int, job: int = 0, iter_: int = 0, precisi
     p.hits_dev = _ptr(hits)
     p.packet_offset = int(packet_offset)
     p.split_factor, p.split_max_level = int(split_factor), int(split_max_level)
+    p.thin_f64 = int(bool(thin_f64))
     p.poly_group = int(poly_group)
     return p
 

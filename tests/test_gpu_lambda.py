@@ -92,6 +92,38 @@ def test_lambda_iteration_small_disc_fp32(rt, ctx):
     assert abs(L["emitted"] - L["absorbed"] - L["escaped"] - L["rr_loss"] + L["rr_gain"]) < 1e-4 * L["emitted"]
 
 
+def test_fp32_thin_cells_take_their_deposit(rt, ctx):
+    """Near-vacuum cells of the disc, whose extinction per unit length lies
+    below the f32 normal range, take their deposit from the f64 density in
+    the thin limit when asked (thin_f64): with the same random streams FP32
+    and FP64 agree on those cells' absorbed energy; by default FP32 gives
+    them nothing."""
+    m = synth.disc(n_root=16, max_level=6, n_lambda=12, packets=0, target_cells=3e4, max_cells=200000)
+    g = rt.Grid(ctx, m.tree)
+    nl = m.optics.n_lambda
+    out = {}
+    for key, prec, thin in (("f32", 32, False), (32, 32, True), (64, 64, False)):
+        ab = torch.zeros((nl, g.n_cells), dtype=torch.float64, device=DEV)
+        rt.rt_trace(ctx, g, m.sources, m.optics, ab, seed=11, precision=prec, packets_per_bin=20000, thin_f64=thin)
+        out[key] = ab.cpu().numpy()
+    tree = m.tree
+    h0 = tree.box[0] / tree.root[0]
+    kl = m.optics.kappa_ext[:, None] * h0 * tree.density[None, :] * 0.5 ** tree.cell_levels()[None, :]
+    leaf = (tree.refine_flags == 0)[None, :]
+    # clearly below the f32 normal range (cells at the threshold may round
+    # either way in the kernel's f32 product)
+    thin = (kl < 0.5 * np.finfo(np.float32).tiny) & leaf & (out[64] > 0)
+    assert thin.sum() > 50, thin.sum()
+    a32, a64 = out[32][thin], out[64][thin]
+    assert np.all(a32 > 0)
+    rel = np.abs(a32 / a64 - 1)
+    assert np.median(rel) < 1e-3 and np.quantile(rel, 0.9) < 0.05, (np.median(rel), np.quantile(rel, 0.9))
+    assert np.all(out["f32"][thin] == 0)
+    # elsewhere the option changes nothing
+    normal = kl >= 2 * np.finfo(np.float32).tiny
+    np.testing.assert_allclose(out["f32"][normal], out[32][normal], rtol=1e-12, atol=0)
+
+
 # ----------------------------------------------------------------- subiterations (Sect. 3.2, App. B)
 
 def _sub_model(tau=2.0):
