@@ -46,13 +46,13 @@ BYTES_PEEL_CROSS_PACKED = 4
 # the tracer (all its launches in a step: the emission round and the tiled
 # rounds) and of the deferred peel-off kernel, from an ncu capture of every
 # launch of one step of the same cloud at 128^3 root cells (tiles of 64^3,
-# 1e6 packages per wavelength: 11.385 GB for 2.704e9 trace crossings, 1.205 GB
+# 1e6 packages per wavelength: 11.33 GB for 2.704e9 trace crossings, 1.206 GB
 # for 1.809e9 peel-off crossings).  The bench line scales them by its own
 # crossings on the default 256^3 workload (None whenever a kernel changes
 # until it is captured again).  The tracer's figure is an upper bound there:
 # the 128^3 case crosses tile faces twice as often per cell crossing.
-NCU_TRACE_BYTES_PER_CROSSING = 11.385e9 / 2.704457093e9
-NCU_PEEL_BYTES_PER_CROSSING = 1.205e9 / 1.808753762e9
+NCU_TRACE_BYTES_PER_CROSSING = 11.329e9 / 2.704457093e9
+NCU_PEEL_BYTES_PER_CROSSING = 1.206e9 / 1.808753762e9
 
 
 def parse():
