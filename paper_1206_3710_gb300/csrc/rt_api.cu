@@ -1208,6 +1208,10 @@ static int sort_peel_queue(rt_ctx* c, const PeelQueue& q, int precision, const r
   rc = c->peel_q2.ensure(rb * (size_t)n);
   if (!rc) rc = c->tile_key.ensure(sizeof(uint32_t) * (size_t)n);
   if (!rc) rc = c->tile_hist.ensure(sizeof(unsigned long long) * ((size_t)n_keys + 1));
+  if (rc == RT_ERR_OOM) {
+    cudaGetLastError();  // no room for the sorted copy: march the queue as it is
+    return RT_OK;
+  }
   if (rc) return rc;
   uint32_t* key = reinterpret_cast<uint32_t*>(c->tile_key.p);
   CK(peel_keys(precision, q.rec, n, bs, nb(G->root[0]), nb(G->root[1]), nb(G->root[2]), key, c->sm_count, s));
