@@ -304,7 +304,7 @@ def gaussian_random_field(n: int, seed: int, slope: float = -4.0) -> np.ndarray:
     amp = k2 ** (slope / 4.0)
     amp[0, 0, 0] = 0.0
     f *= amp
-    g = np.fft.irfftn(f, s=(n, n, n))
+    g = np.fft.irfftn(f, s=(n, n, n), axes=(0, 1, 2))
     g -= g.mean()
     g /= g.std()
     return g
