@@ -484,6 +484,13 @@ def serving_figures(a, ctx, dev):
                                        a.serve_max_packets, slots=a.serve_slots, max_batch_jobs=a.serve_batch,
                                        max_batch_packets=a.serve_batch_packets)
     res.pop("library", None)
+    # the same pattern with small jobs (1e5..1e6 packages), where one job
+    # leaves most of the GPU idle and continuous batching pays
+    small = bench_families.serve_measure(rt, synth, ctx, torch, a.line_serve_seconds, a.serve_rate, 1e6,
+                                         slots=a.serve_slots, max_batch_jobs=a.serve_batch,
+                                         max_batch_packets=a.serve_batch_packets)
+    res["small_jobs"] = {k: small[k] for k in ("jobs", "packets_per_job", "p50_ms", "p99_ms", "served_packets_per_s",
+                                               "burst_packets_per_s", "serial_packets_per_s", "burst_over_serial")}
     return res
 
 
