@@ -51,6 +51,14 @@ BYTES_PEEL_CROSS_PACKED = 4
 # crossings on the default 256^3 workload (None whenever a kernel changes
 # until it is captured again).  The tracer's figure is an upper bound there:
 # the 128^3 case crosses tile faces twice as often per cell crossing.
+# node descents per step of the default 256^3 cloud (a global read of an
+# interior cell's child word each: 4 B in the roofline unit), counted with a
+# build compiled with RT_COUNT_DESCENTS=1 (rt_descent_counts; the package
+# histories are deterministic, so every run of this workload makes as many:
+# its crossings matched the normal build's to the crossing)
+BYTES_DESCENT = 4
+DESCENTS_TRACE_DEFAULT = 3004187455
+DESCENTS_PEEL_DEFAULT = 5202007659
 NCU_TRACE_BYTES_PER_CROSSING = 11.329e9 / 2.704457093e9
 NCU_PEEL_BYTES_PER_CROSSING = 1.206e9 / 1.808753762e9
 
@@ -412,8 +420,16 @@ def main():
     if L0["n_peel_deferred"] < L0["n_scatter"]:  # some peel-offs ran inline in the tracer
         trace_bytes, peel_bytes = trace_bytes + peel_bytes, 0
         trace_packed, peel_packed = trace_packed + peel_packed, 0
+    default_cloud = ((a.n_root, a.levels, a.threshold_scale, a.n_lambda, a.packets_per_bin, a.precision)
+                     == (256, 3, 1.0, 20, 10_000_000, 32) and world == 1
+                     and L0["n_peel_deferred"] == L0["n_scatter"])
+    descents = (DESCENTS_TRACE_DEFAULT, DESCENTS_PEEL_DEFAULT) if default_cloud else (None, None)
+    if default_cloud:  # the descent term of the unit, counted once for this workload
+        trace_bytes += BYTES_DESCENT * DESCENTS_TRACE_DEFAULT
+        trace_packed += BYTES_DESCENT * DESCENTS_TRACE_DEFAULT
+        peel_bytes += BYTES_DESCENT * DESCENTS_PEEL_DEFAULT
+        peel_packed += BYTES_DESCENT * DESCENTS_PEEL_DEFAULT
     achieved = trace_bytes / (kern_ms * 1e-3) / 1e9
-    default_cloud = (a.n_root, a.levels, a.threshold_scale, a.n_lambda) == (256, 3, 1.0, 20)
     trace_traffic = peel_traffic = None
     if default_cloud and NCU_TRACE_BYTES_PER_CROSSING is not None:
         trace_traffic = NCU_TRACE_BYTES_PER_CROSSING * L0["n_cross"]
@@ -425,7 +441,8 @@ def main():
             "peak_kind": peak_kind, "kernel": "trace_kernel<float,1,0,0>",
             "kernel_ms": kern_ms, "alg_bytes_per_launch": trace_bytes,
             "bytes_per_unit": {"trace_crossing": BYTES_TRACE_CROSS, "peel_crossing": BYTES_PEEL_CROSS,
-                               "image_deposit": BYTES_IMAGE_DEPOSIT},
+                               "image_deposit": BYTES_IMAGE_DEPOSIT, "descent": BYTES_DESCENT},
+            "descents_per_step": {"trace": descents[0], "peel": descents[1]},
             "packed_node_word": {"bytes_per_trace_crossing": BYTES_TRACE_CROSS_PACKED,
                                  "frac": trace_packed / (kern_ms * 1e-3) / 1e9 / peak},
             # the tiled rounds keep each round's cells in L2: the same bytes

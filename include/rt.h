@@ -609,6 +609,15 @@ int rt_walk(rt_ctx* ctx, const rt_grid* grid, int64_t n_rays, const double* orig
  * after one warm-up launch. */
 int rt_l2_read_bandwidth(rt_ctx* ctx, void* buf_dev, int64_t bytes, int reps, double* gbs, void* cuda_stream);
 
+/* Diagnostic: node descents since the last reset, counts[0] in the tracers'
+ * own walks, counts[1] in peel-off marches; a descent is a global read of an
+ * interior cell's child word (the 4 B per descent of the roofline unit).
+ * Only builds compiled with RT_COUNT_DESCENTS=1 count (an atomic per
+ * descent; the crossings and histories are those of the normal build);
+ * others answer RT_ERR_INVALID.  Waits for the device; reset != 0 zeroes the
+ * counters after reading.  counts: host [2]. */
+int rt_descent_counts(rt_ctx* ctx, uint64_t* counts, int reset);
+
 /* Philox4x32-10 blocks for n (counter, key) pairs: ctr_dev [n][4], key_dev
  * [n][2], out_dev [n][4] (device uint32). */
 int rt_philox(rt_ctx* ctx, int64_t n, const uint32_t* ctr_dev, const uint32_t* key_dev,

@@ -1570,6 +1570,20 @@ extern "C" int rt_walk(rt_ctx* ctx, const rt_grid* g, int64_t n_rays, const doub
   return ctx_wait(ctx, ctx->ev_b, 3600.0);
 }
 
+extern "C" int rt_descent_counts(rt_ctx* ctx, uint64_t* counts, int reset) {
+  if (!ctx || !counts) return fail(RT_ERR_INVALID, "rt_descent_counts: NULL argument");
+  if (!descents_counted())
+    return fail(RT_ERR_INVALID, "rt_descent_counts: this build does not count descents (RT_COUNT_DESCENTS=1)");
+  CTX_ENTER(ctx);
+  DeviceGuard dg(ctx->device);
+  unsigned long long v[2] = {0ull, 0ull};
+  CK(cudaDeviceSynchronize());
+  CK(descent_counts(v, reset != 0));
+  counts[0] = v[0];
+  counts[1] = v[1];
+  return RT_OK;
+}
+
 extern "C" int rt_l2_read_bandwidth(rt_ctx* ctx, void* buf_dev, int64_t bytes, int reps, double* gbs,
                                     void* cuda_stream) {
   if (!ctx || !buf_dev || !gbs || bytes < 16 || reps < 1 || ((uintptr_t)buf_dev & 15))

@@ -256,6 +256,9 @@ cudaError_t trace_occupancy(int precision, bool peel, int block, int* blocks_per
 cudaError_t launch_peel(int precision, const JobDev* jobs_dev, const PeelQueue& q, unsigned long long* work_dev,
                         int n_obs_max, int refill, cudaStream_t s, int anc = 0);
 size_t peel_record_bytes(int precision);
+// node-descent counters of builds compiled with RT_COUNT_DESCENTS=1
+bool descents_counted();
+cudaError_t descent_counts(unsigned long long out[2], bool reset);
 // sort keys of n queued peel-off records: block of 2^bs root cells (x fastest)
 cudaError_t peel_keys(int precision, const void* rec, long long n, int bs, int nbx, int nby, int nbz, uint32_t* key,
                       int sm_count, cudaStream_t s);

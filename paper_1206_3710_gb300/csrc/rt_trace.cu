@@ -248,6 +248,15 @@ __device__ __forceinline__ unsigned long long claim_slot(unsigned long long* ctr
   return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
 }
 
+// device counters of node descents (a global read of an interior cell's
+// child word each: the 4 B per descent of the roofline unit), kept only in
+// builds compiled with RT_COUNT_DESCENTS=1 (an atomic per descent): [0] the
+// tracer's own walk, [1] peel-off marches
+#ifndef RT_COUNT_DESCENTS
+#define RT_COUNT_DESCENTS 0
+#endif
+__device__ unsigned long long g_descents[2];
+
 // peel-off marches of warps whose live lanes all march along one axis in one
 // direction run a form of the loop with the axis and direction as constants
 #ifndef RT_PEEL_AXIS
@@ -891,6 +900,7 @@ __global__ void __launch_bounds__(MaxThreads<R, MODE>::value, MinBlocks<R, MODE>
           const double r64 = Num<R>::load_rho64(G.rho64, cur.pending);
           if (w & RT_INTERIOR) {
             descend_step(g, cur, w, dx, dy, dz, P);
+            if (RT_COUNT_DESCENTS) atomicAdd(&g_descents[(TRACE_ONLY || st == ST_TRACE) ? 0 : 1], 1ull);
           } else {
             settle_leaf(g, cur, w, r64);
             const bool tr = TRACE_ONLY || st == ST_TRACE;
@@ -1378,6 +1388,7 @@ __global__ void __launch_bounds__(256, PeelMinBlocks<R>::value) peel_kernel(cons
               descend_step(g, cur, w, AX == 0 ? KA : R(0), AX == 1 ? KA : R(0), AX == 2 ? KA : R(0), P);
             else
               descend_step(g, cur, w, dx, dy, dz, P);
+            if (RT_COUNT_DESCENTS) atomicAdd(&g_descents[1], 1ull);
           } else {
             settle_leaf(g, cur, w, r64);
             int a;
@@ -1749,6 +1760,17 @@ cudaError_t tile_sort(const void* in, const uint32_t* key, long long n, int rec_
   tile_scatter_kernel<<<G, B, 0, s>>>(static_cast<const uint4*>(in), key, n, rec_bytes / 16, hist_dev,
                                       static_cast<uint4*>(out));
   return cudaGetLastError();
+}
+
+bool descents_counted() { return RT_COUNT_DESCENTS != 0; }
+
+cudaError_t descent_counts(unsigned long long out[2], bool reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_descents, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess && reset) {
+    const unsigned long long z[2] = {0ull, 0ull};
+    e = cudaMemcpyToSymbol(g_descents, z, sizeof z);
+  }
+  return e;
 }
 
 size_t peel_record_bytes(int precision) { return precision == 64 ? sizeof(PeelRec64) : sizeof(PeelRec32); }

@@ -28,7 +28,7 @@ EXPORTED = ["rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_version", "r
             "rt_batch_run", "rt_batch_destroy", "rt_autotune", "rt_tune_save", "rt_tune_load", "rt_server_create",
             "rt_server_add_model", "rt_server_submit", "rt_server_poll", "rt_server_wait", "rt_server_fetch",
             "rt_server_stats", "rt_server_destroy", "rt_server_job_times", "rt_ctx_set_peel_queue", "rt_ctx_set_tiles",
-            "rt_ctx_set_tile_records", "rt_l2_read_bandwidth",
+            "rt_ctx_set_tile_records", "rt_l2_read_bandwidth", "rt_descent_counts",
             "rt_peel_tables_create", "rt_peel_tables_destroy", "rt_peel_tables_size", "rt_peel_tables_read",
             "rt_peel_tabulated", "rt_lambda_subiterate", "rt_merge_uniform"]
 
@@ -213,6 +213,7 @@ def lib():
     L.rt_server_wait.argtypes = [vp, C.c_uint64, C.c_double]
     L.rt_server_job_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.rt_l2_read_bandwidth.argtypes = [vp, vp, C.c_int64, C.c_int, C.POINTER(C.c_double), vp]
+    L.rt_descent_counts.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int]
     L.rt_ctx_set_tile_records.argtypes = [vp, C.c_int64]
     L.rt_server_fetch.argtypes = [vp, C.c_uint64, vp, vp]
     L.rt_server_stats.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -607,6 +608,14 @@ def rt_l2_read_bandwidth(ctx: Context, buf, reps: int = 40, stream=None) -> floa
     _check(lib().rt_l2_read_bandwidth(ctx.handle, _ptr(buf), C.c_int64(buf.numel() * buf.element_size()),
                                       int(reps), C.byref(gbs), _stream(stream)))
     return gbs.value
+
+
+def rt_descent_counts(ctx: Context, reset: bool = True):
+    """(tracer, peel-off) node descents since the last reset; builds
+    compiled with RT_COUNT_DESCENTS=1 only."""
+    out = (C.c_uint64 * 2)()
+    _check(lib().rt_descent_counts(ctx.handle, out, int(bool(reset))))
+    return int(out[0]), int(out[1])
 
 
 def rt_philox(ctx: Context, ctr, key, out, stream=None) -> None:
